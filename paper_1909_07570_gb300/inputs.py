@@ -1,0 +1,132 @@
+"""Seeded synthetic inputs for nnCANDELINC, shared by the tests, the benchmark
+and the oracle checks.
+
+This module draws random numbers and nothing else: it holds none of the
+method's arithmetic. Both the CUDA path and the FP64 oracle receive the same
+arrays from it (the data tensor X and the initial factors), so parity never
+depends on two random generators agreeing.
+
+The workloads stand in for the paper's synthetic experiments (Sec. 4.3: a
+planted nonnegative CP with uniform factor entries); the paper's fluorescence
+and copolymer data sets (Secs. 4.4, 4.5) are not available, so no real data is
+used anywhere.
+
+Recipe of a planted tensor:
+  * factor entries A^(i)[n, q] i.i.d. from ``dist`` (uniform [0, 1) or
+    exponential(1)); with ``zero_frac`` > 0 each entry is zeroed independently
+    with that probability (sparse factors);
+  * X0 = sum_q a^(1)_q o a^(2)_q o ... (outer products);
+  * X = X0 + eta * E, with E i.i.d. uniform [0, 1) and eta chosen so that
+    ||eta E||_F = noise * ||X0||_F.
+Initial factors and cores are i.i.d. uniform on (0, 1]: strictly positive,
+because a multiplicative update never moves an exact zero.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    """One synthetic nnCANDELINC problem: shapes, ranks, iteration counts."""
+
+    name: str
+    dims: tuple
+    planted_rank: int
+    m: tuple                 # Tucker multirank
+    r: int                   # nnCP rank of the core
+    iters: int               # nnTD sweeps
+    cp_iters: int            # nnCP sweeps on the core
+    dtype: str               # storage / arithmetic type of the plain path
+    dist: str = "uniform"
+    zero_frac: float = 0.0
+    noise: float = 0.01
+    seed: int = 1000
+    refine_iters: int = 0    # FP32 refinement sweeps of the BF16 path
+    extra: dict = field(default_factory=dict)
+
+
+# The five workload shapes. Names state the content; sizes follow the task's
+# synthetic configurations.
+WORKLOADS = {
+    "cp3_40x40x40_m5_fp64": Workload(
+        "cp3_40x40x40_m5_fp64", (40, 40, 40), 3, (5, 5, 5), 3, 200, 200, "f64",
+        noise=0.01, seed=1000),
+    "cp10_256x256x256_m20_fp32": Workload(
+        "cp10_256x256x256_m20_fp32", (256, 256, 256), 10, (20, 20, 20), 10, 500, 500, "f32",
+        zero_frac=0.2, noise=0.02, seed=1001),
+    "cp16_512x512x512_m32_bf16": Workload(
+        "cp16_512x512x512_m32_bf16", (512, 512, 512), 16, (32, 32, 32), 16, 200, 200, "bf16",
+        dist="exponential", noise=0.01, seed=1002, refine_iters=20),
+    "cp12_128x128x128x64_m24_fp32": Workload(
+        "cp12_128x128x128x64_m24_fp32", (128, 128, 128, 64), 12, (24, 24, 24, 16), 12, 300, 300,
+        "f32", noise=0.01, seed=1004),
+}
+
+
+def planted_factors(dims, rank, rng, dist="uniform", zero_frac=0.0):
+    """Factor matrices A^(i) (N_i x rank) of a planted nonnegative CP."""
+    A = []
+    for n in dims:
+        if dist == "uniform":
+            a = rng.random((n, rank))
+        elif dist == "exponential":
+            a = rng.exponential(1.0, (n, rank))
+        else:
+            raise ValueError(f"unknown distribution {dist!r}")
+        if zero_frac > 0.0:
+            a = a * (rng.random((n, rank)) >= zero_frac)
+        A.append(a)
+    return A
+
+
+def _outer_sum(A):
+    """sum_q a^(1)_q o ... o a^(d)_q, built mode by mode in float64."""
+    d = len(A)
+    letters = "abcdefgh"[:d]
+    spec = ",".join(f"{c}z" for c in letters) + "->" + letters
+    return np.einsum(spec, *A, optimize=True)
+
+
+def planted_tensor(dims, rank, seed, dist="uniform", zero_frac=0.0, noise=0.01):
+    """X = X0 + eta E in float64, plus the planted factors (see module doc)."""
+    rng = np.random.default_rng(seed)
+    A = planted_factors(dims, rank, rng, dist, zero_frac)
+    X = _outer_sum(A)
+    if noise > 0.0:
+        E = rng.random(X.shape)
+        x0 = np.sqrt(np.sum(X * X))
+        e = np.sqrt(np.sum(E * E))
+        X += (noise * x0 / e) * E
+    return X, A
+
+
+def initial_tucker(dims, m, seed):
+    """Initial F^(i) (N_i x m_i) and core G (m_1 x ... x m_d), i.i.d. U(0, 1]."""
+    rng = np.random.default_rng(seed)
+    F = [1.0 - rng.random((n, k)) for n, k in zip(dims, m)]
+    G = 1.0 - rng.random(tuple(m))
+    return F, G
+
+
+def initial_cp(m, r, seed):
+    """Initial B^(i) (m_i x r), i.i.d. U(0, 1]."""
+    rng = np.random.default_rng(seed)
+    return [1.0 - rng.random((k, r)) for k in m]
+
+
+def make_problem(w: Workload):
+    """X (float64), planted factors, initial (F, G) and initial B for ``w``."""
+    X, A = planted_tensor(w.dims, w.planted_rank, w.seed, w.dist, w.zero_frac, w.noise)
+    F0, G0 = initial_tucker(w.dims, w.m, w.seed + 7919)
+    B0 = initial_cp(w.m, w.r, w.seed + 104729)
+    return X, A, F0, G0, B0
+
+
+def small_problem(dims, planted_rank, m, r, seed, dist="uniform", zero_frac=0.0, noise=0.01):
+    """A planted problem of arbitrary shape, for tests."""
+    w = Workload("custom", tuple(dims), planted_rank, tuple(m), r, 1, 1, "f64",
+                 dist=dist, zero_frac=zero_frac, noise=noise, seed=seed)
+    return make_problem(w)

@@ -1,0 +1,297 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the worked
+examples printed in the paper (tests/golden/), brute-force sums written from
+the definitions, central finite differences of the objective, exact fixed
+points built as in Thm. "canonical preserve rank", and invariants (monotone
+objective, nonnegativity, column span). A dropped term, a wrong sign, a wrong
+index or a transposed operand in the oracle fails at least one of them.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from _golden import load
+from paper_1909_07570_gb300 import inputs
+
+RNG = np.random.default_rng(12345)
+
+
+# ---------------------------------------------------------------------------
+# n-mode product, unfolding, Khatri-Rao: brute force from the definitions
+# ---------------------------------------------------------------------------
+
+def _mode_product_loops(X, A, n):
+    """Appendix A, Def. of n-mode multiplication, summed index by index."""
+    out_shape = list(X.shape)
+    out_shape[n] = A.shape[0]
+    Y = np.zeros(out_shape)
+    for idx in itertools.product(*[range(s) for s in out_shape]):
+        s = 0.0
+        for l in range(X.shape[n]):
+            src = list(idx)
+            src[n] = l
+            s += X[tuple(src)] * A[idx[n], l]
+        Y[idx] = s
+    return Y
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 2), (2, 3, 4, 2)])
+def test_mode_product_matches_definition(shape):
+    X = RNG.standard_normal(shape)
+    for n in range(len(shape)):
+        A = RNG.standard_normal((3, shape[n]))
+        np.testing.assert_allclose(orc.mode_product(X, A, n), _mode_product_loops(X, A, n),
+                                   rtol=0, atol=1e-12)
+
+
+def test_mode_products_commute_and_distribute():
+    # Appendix A: (X x_i A) x_j B = (X x_j B) x_i A for i != j, and X x_i (AB) = (X x_i B) x_i A.
+    X = RNG.standard_normal((3, 4, 5))
+    A = RNG.standard_normal((2, 3))
+    B = RNG.standard_normal((6, 4))
+    np.testing.assert_allclose(orc.mode_product(orc.mode_product(X, A, 0), B, 1),
+                               orc.mode_product(orc.mode_product(X, B, 1), A, 0), atol=1e-12)
+    C = RNG.standard_normal((2, 7))
+    D = RNG.standard_normal((7, 5))
+    np.testing.assert_allclose(orc.mode_product(X, C @ D, 2),
+                               orc.mode_product(orc.mode_product(X, D, 2), C, 2), atol=1e-12)
+
+
+def test_unfold_column_order():
+    # Sec. 3.1: column m(j, k) = j + N_2 (k - 1) of unfold_1 holds the fibre X[:, j, k];
+    # likewise for modes 2 and 3 the first remaining index varies fastest.
+    N1, N2, N3 = 3, 4, 5
+    X = RNG.standard_normal((N1, N2, N3))
+    U1, U2, U3 = (orc.unfold(X, n) for n in range(3))
+    for i, j, k in itertools.product(range(N1), range(N2), range(N3)):
+        assert U1[i, j + N2 * k] == X[i, j, k]
+        assert U2[j, i + N1 * k] == X[i, j, k]
+        assert U3[k, i + N1 * j] == X[i, j, k]
+    for n in range(3):
+        np.testing.assert_array_equal(orc.fold(orc.unfold(X, n), n, X.shape), X)
+
+
+def test_khatri_rao_matches_unfolding_identity():
+    # Eq. unfolding:property with a superdiagonal core: unfold_n(I x_k A^(k)) = A^(n) KR^T,
+    # checked against a CP tensor summed term by term (Eq. pd).
+    dims, r = (3, 4, 2, 3), 2
+    A = [RNG.random((n, r)) for n in dims]
+    X = np.zeros(dims)
+    for q in range(r):
+        for idx in itertools.product(*[range(s) for s in dims]):
+            X[idx] += np.prod([A[t][idx[t], q] for t in range(len(dims))])
+    np.testing.assert_allclose(orc.cp_reconstruct(A), X, atol=1e-13)
+    for n in range(len(dims)):
+        others = [k for k in range(len(dims)) if k != n]
+        np.testing.assert_allclose(orc.unfold(X, n), A[n] @ orc.khatri_rao([A[k] for k in others]).T,
+                                   atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Worked examples printed in the paper (exact integer arithmetic)
+# ---------------------------------------------------------------------------
+
+def test_example_not_in_cones():
+    g = load("ex_not_in_cones.txt")
+    X = orc.fold(g["unfold1_X"], 0, g["shape"]["X"])
+    np.testing.assert_array_equal(orc.unfold(X, 1), g["unfold2_X"])
+    np.testing.assert_array_equal(orc.unfold(X, 2), g["unfold3_X"])
+    G = orc.fold(g["unfold1_G"], 0, g["shape"]["G"])
+    np.testing.assert_array_equal(orc.tucker_reconstruct(G, [g["W1"], g["W2"], g["W3"]]), X)
+    assert G.min() < 0  # the printed core has a negative entry: X is not in C1 x C2 x C3
+
+
+def test_example_equal():
+    g = load("ex_equal.txt")
+    X = orc.cp_reconstruct([g["A1"], g["A2"], g["A3"]])
+    np.testing.assert_array_equal(orc.unfold(X, 0), g["unfold1_X"])
+    np.testing.assert_array_equal(g["F1"] @ g["unfold1_G"], g["unfold1_X"])
+    G = orc.fold(g["unfold1_G"], 0, g["shape"]["G"])
+    np.testing.assert_array_equal(orc.tucker_reconstruct(G, [g["F1"], np.eye(4), np.eye(4)]), X)
+    ranks = [np.linalg.matrix_rank(orc.unfold(X, n)) for n in range(3)]
+    assert ranks == list(g["unfold_ranks"].astype(int))
+
+
+def test_example_cones_dne():
+    g = load("ex_cones_dne.txt")
+    X = orc.fold(g["unfold1_X"], 0, g["shape"]["X"])
+    np.testing.assert_array_equal(orc.unfold(X, 1), g["unfold2_X"])
+    np.testing.assert_array_equal(orc.unfold(X, 2), g["unfold3_X"])
+    np.testing.assert_array_equal(g["W2"] @ g["H2"], g["unfold2_X"])
+    np.testing.assert_array_equal(g["W"] @ g["unfold1_H"], g["unfold1_X"])
+    H = orc.fold(g["unfold1_H"], 0, g["shape"]["H"])
+    np.testing.assert_array_equal(orc.mode_product(H, g["W"], 0), X)
+    np.testing.assert_array_equal(orc.unfold(H, 1), g["unfold2_H"])
+
+
+def test_example_rank_one_with_rank_two_core():
+    # Sec. 2.1: the 2x2x2 all-ones tensor equals a rank-2 core times the all-ones matrix in mode 1.
+    G = orc.fold(np.array([[1.0, 0, 1, 0], [0, 1, 0, 1]]), 0, (2, 2, 2))
+    np.testing.assert_array_equal(orc.mode_product(G, np.ones((2, 2)), 0), np.ones((2, 2, 2)))
+
+
+def test_example_rank_of_V():
+    # Appendix B, Example mrank_mrank+: rank(V) = 3 since v1 + v4 = v2 + v3.
+    V = np.array([[1.0, 1, 0, 0], [1, 0, 1, 0], [0, 1, 0, 1], [0, 0, 1, 1]])
+    assert np.linalg.matrix_rank(V) == 3
+    np.testing.assert_array_equal(V[:, 0] + V[:, 3], V[:, 1] + V[:, 2])
+
+
+# ---------------------------------------------------------------------------
+# Multiplicative updates: gradients by central differences
+# ---------------------------------------------------------------------------
+
+def _tucker_loss(X, F, G):
+    R = X - orc.tucker_reconstruct(G, F)
+    return 0.5 * np.sum(R * R)
+
+
+def _fd_grad(fun, P, h=1e-5):
+    g = np.zeros_like(P)
+    for idx in np.ndindex(P.shape):
+        old = P[idx]
+        P[idx] = old + h
+        fp = fun()
+        P[idx] = old - h
+        fm = fun()
+        P[idx] = old
+        g[idx] = (fp - fm) / (2 * h)
+    return g
+
+
+@pytest.mark.parametrize("dims,m", [((4, 3, 5), (2, 3, 2)), ((3, 4, 2, 3), (2, 2, 2, 3))])
+def test_ntd_terms_are_the_gradient(dims, m):
+    X = RNG.random(dims)
+    F = [RNG.random((n, k)) for n, k in zip(dims, m)]
+    G = RNG.random(m)
+    for n in range(len(dims)):
+        num, den = orc.ntd_factor_terms(X, F, G, n)
+        fd = _fd_grad(lambda: _tucker_loss(X, F, G), F[n])
+        np.testing.assert_allclose(den - num, fd, rtol=1e-7, atol=1e-7)
+        assert (num >= 0).all() and (den >= 0).all()
+    M, D = orc.ntd_core_terms(X, F, G)
+    fd = _fd_grad(lambda: _tucker_loss(X, F, G), G)
+    np.testing.assert_allclose(D - M, fd, rtol=1e-7, atol=1e-7)
+
+
+def test_nncp_terms_are_the_gradient():
+    m, r = (3, 4, 2), 3
+    G = RNG.random(m)
+    B = [RNG.random((k, r)) for k in m]
+
+    def loss():
+        R = G - orc.cp_reconstruct(B)
+        return 0.5 * np.sum(R * R)
+
+    for n in range(3):
+        num, den = orc.nncp_terms(G, B, n)
+        np.testing.assert_allclose(den - num, _fd_grad(loss, B[n]), rtol=1e-7, atol=1e-7)
+
+
+@pytest.mark.parametrize("dims,m,r", [((4, 3, 5), (2, 3, 2), 2), ((3, 3, 2, 4), (2, 2, 2, 3), 3)])
+def test_lifted_loss_gradient(dims, m, r):
+    X = RNG.random(dims)
+    F = [RNG.random((n, k)) for n, k in zip(dims, m)]
+    B = [RNG.random((k, r)) for k in m]
+    gF, gB = orc.lifted_loss_grad(X, F, B)
+    for n in range(len(dims)):
+        np.testing.assert_allclose(gF[n], _fd_grad(lambda: orc.lifted_loss(X, F, B), F[n]),
+                                   rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(gB[n], _fd_grad(lambda: orc.lifted_loss(X, F, B), B[n]),
+                                   rtol=1e-6, atol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# Fixed points (Thm. "canonical preserve rank"), residual identity, invariants
+# ---------------------------------------------------------------------------
+
+def _canonical_solution(dims, kappa, r, seed):
+    rng = np.random.default_rng(seed)
+    W = [rng.random((n, k)) + 0.1 for n, k in zip(dims, kappa)]
+    H = [rng.random((k, r)) + 0.1 for k in kappa]
+    G = orc.cp_reconstruct(H)          # G = D x_i H^(i)
+    X = orc.tucker_reconstruct(G, W)   # X = G x_i W^(i) = D x_i W^(i) H^(i)
+    return X, W, H, G
+
+
+def test_exact_canonical_tucker_is_a_fixed_point():
+    X, W, H, G = _canonical_solution((9, 8, 7), (3, 4, 5), 5, 7)
+    F1, G1, _ = orc.ntd_sweep(X, W, G)
+    for a, b in zip(F1, W):
+        np.testing.assert_allclose(a, b, rtol=1e-12)
+    np.testing.assert_allclose(G1, G, rtol=1e-12)
+    B1 = orc.nncp_sweep(G, H)
+    for a, b in zip(B1, H):
+        np.testing.assert_allclose(a, b, rtol=1e-12)
+    A = orc.lift(W, H)
+    assert orc.rel_err_cp(X, A) < 1e-14
+
+
+def test_residual_identity_matches_brute_force():
+    X, _, F0, G0, _ = inputs.small_problem((7, 6, 5), 3, (3, 3, 2), 3, seed=3)
+    F, G, _ = orc.ntd_sweep(X, F0, G0)
+    M, _ = orc.ntd_core_terms(X, F, G)
+    x2 = np.sum(X * X)
+    r2 = orc.residual_sq_identity(x2, M, G, F)
+    brute = np.sum((X - orc.tucker_reconstruct(G, F)) ** 2)
+    np.testing.assert_allclose(r2, brute, rtol=1e-10)
+
+
+def test_ntd_fit_trace_is_the_relative_error_and_monotone():
+    X, _, F0, G0, _ = inputs.small_problem((10, 9, 8), 3, (4, 4, 3), 3, seed=11, noise=0.05)
+    F, G, trace = orc.ntd_fit(X, F0, G0, 60)
+    np.testing.assert_allclose(trace[-1], orc.rel_err_tucker(X, G, F), rtol=1e-9)
+    assert np.all(np.diff(trace) <= 1e-12 * trace[:-1])
+    assert all((f >= 0).all() for f in F) and (G >= 0).all()
+
+
+def test_nncp_fit_monotone_and_nonnegative():
+    G = np.random.default_rng(5).random((4, 5, 3))
+    B0 = inputs.initial_cp((4, 5, 3), 3, 9)
+    B, trace = orc.nncp_fit(G, B0, 80)
+    assert np.all(np.diff(trace) <= 1e-12 * trace[:-1])
+    assert all((b >= 0).all() for b in B)
+
+
+def test_lift_substitution_and_column_span():
+    # Proof of Lemma "rank and min exists": (I x_i B^(i)) x_i F^(i) = I x_i (F^(i) B^(i)),
+    # and by Prop. tdspaces every lifted factor lies in col(F^(i)).
+    dims, m, r = (6, 5, 7), (3, 2, 4), 3
+    F = [RNG.random((n, k)) for n, k in zip(dims, m)]
+    B = [RNG.random((k, r)) for k in m]
+    A = orc.lift(F, B)
+    np.testing.assert_allclose(orc.tucker_reconstruct(orc.cp_reconstruct(B), F),
+                               orc.cp_reconstruct(A), rtol=1e-12)
+    for Fn, An in zip(F, A):
+        P = Fn @ np.linalg.pinv(Fn)
+        assert np.linalg.norm(An - P @ An) <= 1e-12 * np.linalg.norm(An)
+
+
+def test_congruence_is_permutation_invariant():
+    A = [RNG.random((n, 4)) for n in (5, 6, 7)]
+    perm = [2, 0, 3, 1]
+    A_hat = [a[:, perm] * 3.0 for a in A]
+    assert orc.mean_congruence(A, A_hat) == pytest.approx(1.0, abs=1e-12)
+    C = orc.congruence_matrix(A, A)
+    for q in range(4):
+        for p in range(4):
+            expect = np.prod([A[i][:, q] @ A[i][:, p] / np.linalg.norm(A[i][:, q]) /
+                              np.linalg.norm(A[i][:, p]) for i in range(3)])
+            assert C[q, p] == pytest.approx(expect, rel=1e-12)
+
+
+def test_recovery_of_a_planted_canonical_tucker():
+    # Sec. 4.3 in miniature: noise-free planted rank-3 data, multirank above the
+    # canonical one. A quality check of the whole Alg. 1 (MU is a local method),
+    # not a tolerance gate.
+    X, A, F0, G0, B0 = inputs.small_problem((12, 11, 10), 3, (4, 4, 4), 3, seed=21, noise=0.0)
+    F, G, trace = orc.ntd_fit(X, F0, G0, 1000)
+    assert trace[-1] < 1e-2
+    B, cp_trace = orc.nncp_fit(G, B0, 300)
+    assert cp_trace[-1] < cp_trace[0]
+    A_hat = orc.lift(F, B)
+    assert orc.rel_err_cp(X, A_hat) < 0.15
+    assert orc.mean_congruence(A, A_hat) > 0.8
