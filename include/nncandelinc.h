@@ -1,0 +1,169 @@
+/*
+ * nncandelinc.h - C ABI of the GB300 nnCANDELINC library (libnncandelinc.so).
+ *
+ * nnCANDELINC (arXiv 1909.07570) approximates a nonnegative d-way tensor X by
+ * the lifted model I x_1 F^(1)B^(1) x_2 ... x_d F^(d)B^(d) (Eq. nnCANDELINC,
+ * Sec. 4). Alg. 1 (Sec. 4.1) computes it in two steps, nnTD of X followed by
+ * nnCPD of the Tucker core; the lift A^(i) = F^(i) B^(i) is the substitution
+ * in the proof of Lemma "rank and min exists" (Sec. 2.1).
+ *
+ * Conventions shared by every call:
+ *  - Tensors are dense and C-ordered (the last index is contiguous); index 0
+ *    is mode 1 of the paper. Matrices are row-major.
+ *  - F^(n) is dims[n] x m[n], G is m[0] x ... x m[d-1], B^(n) is m[n] x r,
+ *    A^(n) is dims[n] x r.
+ *  - Array pointers (X, F, G, B, A, traces) are DEVICE pointers owned by the
+ *    caller; arrays of pointers (F, B, A, factors) and shape arrays (dims, m)
+ *    are HOST arrays. Pointers marked "host" are host memory.
+ *  - The element type follows `precision`: double for NNC_FP64, float for
+ *    NNC_FP32 and NNC_BF16_REFINE (the BF16 copy of X is made internally).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *    stream-ordered. A call returns after its host outputs are written; it
+ *    synchronises `stream` only when it has host outputs to write.
+ *  - Scratch memory is taken from the stream-ordered allocator
+ *    (cudaMallocAsync) on `stream` and released before the call returns.
+ *  - Every call returns NNC_OK (0) or a negative NNC_ERR_* code; on error the
+ *    caller's arrays may hold partial results. nnc_status_string() names it.
+ *  - Update rule: multiplicative updates with a Gauss-Seidel order, guarded
+ *    denominators max(den, eps) and a projection max(., 0) (see ntd_fit).
+ */
+#ifndef NNCANDELINC_H
+#define NNCANDELINC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NNC_OK 0
+#define NNC_ERR_INVALID_ARG (-1)    /* bad shape, rank, pointer or option      */
+#define NNC_ERR_NEGATIVE_INPUT (-2) /* X holds a negative entry                */
+#define NNC_ERR_NONFINITE (-3)      /* X holds NaN/Inf, or a result overflowed */
+#define NNC_ERR_CUDA (-4)           /* a CUDA runtime call failed              */
+#define NNC_ERR_ALLOC (-5)          /* scratch allocation failed               */
+#define NNC_ERR_UNSUPPORTED (-6)    /* valid request this build does not serve */
+
+typedef enum {
+  NNC_FP64 = 0,        /* double storage and arithmetic                      */
+  NNC_FP32 = 1,        /* float storage and arithmetic                       */
+  NNC_BF16_REFINE = 2  /* float storage; the two passes over X per sweep use
+                          a BF16 copy of X on the tensor cores with FP32
+                          accumulation, then `refine_iters` FP32 sweeps      */
+} nnc_precision;
+
+typedef struct {
+  int iters;         /* number of MU sweeps, >= 0                          */
+  int refine_iters;  /* NNC_BF16_REFINE only: the last refine_iters of the
+                        iters sweeps run in FP32 (0 <= refine_iters <= iters) */
+  double eps;        /* denominator guard, > 0 (1e-12 in the tests)         */
+} nnc_opts;
+
+/*
+ * ntd_fit - nonnegative Tucker decomposition X ~ G x_1 F^(1) ... x_d F^(d)
+ * (Alg. 1, step 1; model Eq. TD:matrix-format with F, G >= 0, Sec. 3).
+ *
+ * Runs opts->iters sweeps. A sweep updates F^(1), ..., F^(d) and then G, each
+ * by theta <- max(theta * Num / max(Den, eps), 0), where Den - Num is the
+ * gradient of 1/2 ||X - X_hat||_F^2 wrt theta:
+ *   Num_n = unfold_n(X x_{k!=n} F^(k)T) unfold_n(G)^T
+ *   Den_n = F^(n) unfold_n(G x_{k!=n} F^(k)T F^(k)) unfold_n(G)^T
+ *   Num_G = X x_1 F^(1)T ... x_d F^(d)T,  Den_G = G x_1 F^(1)T F^(1) ...
+ * (the unfoldings follow Eq. unfolding:property).
+ *
+ *  X          device, dims[0] x ... x dims[d-1], entries >= 0 and finite
+ *  d          3 (this build)
+ *  dims, m    host arrays of d entries; 1 <= m[n] <= 64, dims[n] >= 1
+ *  F          host array of d device pointers: initial F^(n) (> 0) in,
+ *             fitted F^(n) out
+ *  G          device: initial core (> 0) in, fitted core out
+ *  rel_err_trace  device array of opts->iters doubles, or NULL: relative
+ *             error ||X - X_hat||_F / ||X||_F (Sec. 4.1) after each sweep,
+ *             from the FP64 identity ||X||^2 - 2<Num_G, G> + <G, Den_G(G)>
+ *  rel_err    host, or NULL: final relative error from one explicit FP64
+ *             pass over X (as recon_residual)
+ * Errors: INVALID_ARG, NEGATIVE_INPUT, NONFINITE (checked on X before any
+ * sweep), UNSUPPORTED (d != 3), CUDA, ALLOC.
+ */
+int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precision,
+            const nnc_opts* opts, void* const* F, void* G, double* rel_err_trace,
+            double* rel_err, void* stream);
+
+/*
+ * nncp_core_fit - nonnegative CP decomposition G ~ I x_1 B^(1) ... x_d B^(d)
+ * of a core (Alg. 1, step 2; model Eq. npd). opts->iters sweeps over
+ * B^(1), ..., B^(d) of
+ *   B^(n) <- max(B^(n) * (unfold_n(G) KR_{k!=n} B^(k)) / max(B^(n) V_n, eps), 0),
+ *   V_n = Hadamard product over k != n of B^(k)T B^(k),
+ * with the Khatri-Rao rows ordered like the unfolding columns (Sec. 3.1).
+ *
+ *  G          device core, m[0] x ... x m[d-1], entries >= 0
+ *  d          3 or 4;  1 <= m[n] <= 64;  1 <= r <= 32
+ *  precision  NNC_FP64 or NNC_FP32 (NNC_BF16_REFINE is taken as NNC_FP32)
+ *  B          host array of d device pointers: initial B^(n) (> 0) in,
+ *             fitted B^(n) out
+ *  rel_err    host, or NULL: final ||G - I x_n B^(n)||_F / ||G||_F (FP64 sums)
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA, ALLOC.
+ */
+int nncp_core_fit(const void* G, int d, const int* m, int r, int precision, const nnc_opts* opts,
+                  void* const* B, double* rel_err, void* stream);
+
+/* One independent core fit of nncp_core_fit_batched. */
+typedef struct {
+  const void* G;  /* device core, m[0] x ... x m[d-1]             */
+  int d;          /* 3 or 4                                        */
+  int m[4];       /* core dimensions, 1 <= m[n] <= 64              */
+  int r;          /* CP rank, 1 <= r <= 32                         */
+  void* B[4];     /* device B^(n), m[n] x r: initial in, fitted out */
+} nncp_job;
+
+/*
+ * nncp_core_fit_batched - many independent nncp_core_fit problems (uneven
+ * shapes and ranks: restarts, candidate ranks, several tensors) in one
+ * launch, one thread block per job. Same update rule and options as
+ * nncp_core_fit.
+ *
+ *  jobs       host array of n_jobs descriptors (copied by the call)
+ *  rel_errs   device array of n_jobs doubles, or NULL: final relative error
+ *             of each job
+ * Errors: INVALID_ARG (any job), CUDA, ALLOC. No host synchronisation.
+ */
+int nncp_core_fit_batched(int n_jobs, const nncp_job* jobs, int precision, const nnc_opts* opts,
+                          double* rel_errs, void* stream);
+
+/*
+ * candelinc_lift - A^(n) = F^(n) B^(n) for every mode: the CPD of the core
+ * substituted into the Tucker model (proof of Lemma "rank and min exists",
+ * Sec. 2.1), giving the CP factors of the nnCANDELINC model.
+ *
+ *  F, B, A    host arrays of d device pointers (A^(n) is dims[n] x r)
+ * Errors: INVALID_ARG, CUDA.
+ */
+int candelinc_lift(int d, const int64_t* dims, const int* m, int r, int precision,
+                   const void* const* F, const void* const* B, void* const* A, void* stream);
+
+/*
+ * recon_residual - ||X - X_hat||_F and ||X||_F in one pass over X with FP64
+ * accumulation (the relative error of Sec. 4.1 is their ratio).
+ *
+ *  model 0: Tucker X_hat = G x_1 F^(1) ... (factors = F, dims[n] x m[n])
+ *  model 1: CP     X_hat = I x_1 A^(1) ... (factors = A, dims[n] x r; G and m
+ *           unused)
+ *  resid_norm, x_norm  host
+ * Errors: INVALID_ARG, UNSUPPORTED (d != 3), CUDA, ALLOC.
+ */
+int recon_residual(const void* X, int d, const int64_t* dims, int precision, int model,
+                   const int* m, int r, const void* const* factors, const void* G,
+                   double* resid_norm, double* x_norm, void* stream);
+
+/* Static string naming a status code. */
+const char* nnc_status_string(int status);
+
+/* Text of the last CUDA error seen by this thread's calls (empty if none). */
+const char* nnc_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NNCANDELINC_H */

@@ -1,0 +1,241 @@
+// C ABI of the nnCANDELINC library: argument checks and the stream-ordered
+// orchestration of the kernels (Alg. 1 of arXiv 1909.07570).
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "kernels.cuh"
+#include "nncp.cuh"
+#include "ntd.cuh"
+#include "residual.cuh"
+
+namespace nnc {
+
+namespace {
+thread_local std::string g_detail;
+}
+
+void set_error_detail(const char* what, cudaError_t e) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  g_detail = buf;
+}
+
+void set_error_detail_text(const std::string& s) { g_detail = s; }
+
+int device_sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 148;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+namespace {
+
+int check_opts(const nnc_opts* o) {
+  if (o == nullptr) return NNC_ERR_INVALID_ARG;
+  if (o->iters < 0 || !(o->eps > 0.0)) return NNC_ERR_INVALID_ARG;
+  if (o->refine_iters < 0 || o->refine_iters > o->iters) return NNC_ERR_INVALID_ARG;
+  return NNC_OK;
+}
+
+int check_shape(int d, const int64_t* dims, const int* m, int max_m) {
+  if (dims == nullptr || m == nullptr) return NNC_ERR_INVALID_ARG;
+  for (int n = 0; n < d; ++n) {
+    if (dims[n] < 1 || dims[n] > (1LL << 31) - 1) return NNC_ERR_INVALID_ARG;
+    if (m[n] < 1 || m[n] > max_m) return NNC_ERR_INVALID_ARG;
+  }
+  return NNC_OK;
+}
+
+template <typename T>
+int nncp_run(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel_errs,
+             cudaStream_t s) {
+  size_t smem = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    const nncp_job& j = jobs[i];
+    if (j.G == nullptr || (j.d != 3 && j.d != 4) || j.r < 1 || j.r > 32)
+      return NNC_ERR_INVALID_ARG;
+    for (int k = 0; k < j.d; ++k)
+      if (j.m[k] < 1 || j.m[k] > 64 || j.B[k] == nullptr) return NNC_ERR_INVALID_ARG;
+    const size_t b = nncp_smem_bytes(j, sizeof(T));
+    smem = b > smem ? b : smem;
+  }
+  if (smem > 200 * 1024) return NNC_ERR_UNSUPPORTED;
+  Scratch sc(s);
+  nncp_job* dev = nullptr;
+  NNC_TRY(sc.get(&dev, (size_t)n_jobs));
+  // A private pageable copy: the runtime stages it before cudaMemcpyAsync
+  // returns, so neither buffer has to outlive this call.
+  std::vector<nncp_job> host(jobs, jobs + n_jobs);
+  NNC_CUDA_TRY(cudaMemcpyAsync(dev, host.data(), sizeof(nncp_job) * n_jobs,
+                               cudaMemcpyHostToDevice, s));
+  NNC_CUDA_TRY(launch_nncp<T>(dev, n_jobs, smem, o->iters, o->eps, rel_errs, s));
+  return NNC_OK;
+}
+
+}  // namespace
+}  // namespace nnc
+
+using namespace nnc;
+
+extern "C" {
+
+const char* nnc_status_string(int status) {
+  switch (status) {
+    case NNC_OK: return "ok";
+    case NNC_ERR_INVALID_ARG: return "invalid argument";
+    case NNC_ERR_NEGATIVE_INPUT: return "input tensor has a negative entry";
+    case NNC_ERR_NONFINITE: return "non-finite value";
+    case NNC_ERR_CUDA: return "CUDA error";
+    case NNC_ERR_ALLOC: return "scratch allocation failed";
+    case NNC_ERR_UNSUPPORTED: return "unsupported by this build";
+    default: return "unknown status";
+  }
+}
+
+const char* nnc_last_error_detail(void) { return g_detail.c_str(); }
+
+int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precision,
+            const nnc_opts* opts, void* const* F, void* G, double* rel_err_trace,
+            double* rel_err, void* stream) {
+  g_detail.clear();
+  NNC_TRY(check_opts(opts));
+  if (X == nullptr || F == nullptr || G == nullptr) return NNC_ERR_INVALID_ARG;
+  if (d != 3) return d == 4 ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
+  NNC_TRY(check_shape(d, dims, m, 64));
+  for (int n = 0; n < d; ++n)
+    if (F[n] == nullptr) return NNC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (precision) {
+    case NNC_FP64:
+      return ntd_fit3<double>(static_cast<const double*>(X), dims, m, opts,
+                              reinterpret_cast<double* const*>(F), static_cast<double*>(G),
+                              rel_err_trace, rel_err, s);
+    case NNC_FP32:
+      return ntd_fit3<float>(static_cast<const float*>(X), dims, m, opts,
+                             reinterpret_cast<float* const*>(F), static_cast<float*>(G),
+                             rel_err_trace, rel_err, s);
+    case NNC_BF16_REFINE:
+      return ntd_fit3_bf16(static_cast<const float*>(X), dims, m, opts,
+                           reinterpret_cast<float* const*>(F), static_cast<float*>(G),
+                           rel_err_trace, rel_err, s);
+    default:
+      return NNC_ERR_INVALID_ARG;
+  }
+}
+
+int nncp_core_fit(const void* G, int d, const int* m, int r, int precision, const nnc_opts* opts,
+                  void* const* B, double* rel_err, void* stream) {
+  g_detail.clear();
+  NNC_TRY(check_opts(opts));
+  if (G == nullptr || B == nullptr || m == nullptr || (d != 3 && d != 4)) return NNC_ERR_INVALID_ARG;
+  nncp_job job;
+  memset(&job, 0, sizeof(job));
+  job.G = G;
+  job.d = d;
+  job.r = r;
+  for (int k = 0; k < d; ++k) {
+    job.m[k] = m[k];
+    job.B[k] = B[k];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Scratch sc(s);
+  double* dev_err = nullptr;
+  if (rel_err) NNC_TRY(sc.get(&dev_err, 1));
+  int st;
+  if (precision == NNC_FP64)
+    st = nncp_run<double>(1, &job, opts, dev_err, s);
+  else if (precision == NNC_FP32 || precision == NNC_BF16_REFINE)
+    st = nncp_run<float>(1, &job, opts, dev_err, s);
+  else
+    return NNC_ERR_INVALID_ARG;
+  if (st != NNC_OK) return st;
+  if (rel_err) {
+    NNC_CUDA_TRY(cudaMemcpyAsync(rel_err, dev_err, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NNC_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return NNC_OK;
+}
+
+int nncp_core_fit_batched(int n_jobs, const nncp_job* jobs, int precision, const nnc_opts* opts,
+                          double* rel_errs, void* stream) {
+  g_detail.clear();
+  NNC_TRY(check_opts(opts));
+  if (n_jobs < 0 || (n_jobs > 0 && jobs == nullptr)) return NNC_ERR_INVALID_ARG;
+  if (n_jobs == 0) return NNC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == NNC_FP64) return nncp_run<double>(n_jobs, jobs, opts, rel_errs, s);
+  if (precision == NNC_FP32 || precision == NNC_BF16_REFINE)
+    return nncp_run<float>(n_jobs, jobs, opts, rel_errs, s);
+  return NNC_ERR_INVALID_ARG;
+}
+
+int candelinc_lift(int d, const int64_t* dims, const int* m, int r, int precision,
+                   const void* const* F, const void* const* B, void* const* A, void* stream) {
+  g_detail.clear();
+  if (d < 1 || d > 8 || F == nullptr || B == nullptr || A == nullptr || r < 1)
+    return NNC_ERR_INVALID_ARG;
+  NNC_TRY(check_shape(d, dims, m, 1 << 20));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int n = 0; n < d; ++n) {
+    if (F[n] == nullptr || B[n] == nullptr || A[n] == nullptr) return NNC_ERR_INVALID_ARG;
+    if (precision == NNC_FP64) {
+      NNC_CUDA_TRY(launch_lift<double>(static_cast<const double*>(F[n]),
+                                       static_cast<const double*>(B[n]), dims[n], m[n], r,
+                                       static_cast<double*>(A[n]), s));
+    } else if (precision == NNC_FP32 || precision == NNC_BF16_REFINE) {
+      NNC_CUDA_TRY(launch_lift<float>(static_cast<const float*>(F[n]),
+                                      static_cast<const float*>(B[n]), dims[n], m[n], r,
+                                      static_cast<float*>(A[n]), s));
+    } else {
+      return NNC_ERR_INVALID_ARG;
+    }
+  }
+  return NNC_OK;
+}
+
+int recon_residual(const void* X, int d, const int64_t* dims, int precision, int model,
+                   const int* m, int r, const void* const* factors, const void* G,
+                   double* resid_norm, double* x_norm, void* stream) {
+  g_detail.clear();
+  if (X == nullptr || factors == nullptr || dims == nullptr) return NNC_ERR_INVALID_ARG;
+  if (model != 0 && model != 1) return NNC_ERR_INVALID_ARG;
+  if (d != 3) return d == 4 ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
+  for (int n = 0; n < d; ++n) {
+    if (dims[n] < 1 || factors[n] == nullptr) return NNC_ERR_INVALID_ARG;
+    if (model == 0 && (m == nullptr || m[n] < 1 || m[n] > 64)) return NNC_ERR_INVALID_ARG;
+  }
+  if (model == 0 && G == nullptr) return NNC_ERR_INVALID_ARG;
+  if (model == 1 && (r < 1 || r > 64)) return NNC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Scratch sc(s);
+  double* out2 = nullptr;
+  NNC_TRY(sc.get(&out2, 2));
+  if (precision == NNC_FP64) {
+    NNC_TRY(residual3_device<double>(static_cast<const double*>(X), dims, model, m, r,
+                                     reinterpret_cast<const double* const*>(factors),
+                                     static_cast<const double*>(G), out2, sc, s));
+  } else if (precision == NNC_FP32 || precision == NNC_BF16_REFINE) {
+    NNC_TRY(residual3_device<float>(static_cast<const float*>(X), dims, model, m, r,
+                                    reinterpret_cast<const float* const*>(factors),
+                                    static_cast<const float*>(G), out2, sc, s));
+  } else {
+    return NNC_ERR_INVALID_ARG;
+  }
+  double h[2];
+  NNC_CUDA_TRY(cudaMemcpyAsync(h, out2, sizeof(h), cudaMemcpyDeviceToHost, s));
+  NNC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (resid_norm) *resid_norm = sqrt(h[0]);
+  if (x_norm) *x_norm = sqrt(h[1]);
+  return NNC_OK;
+}
+
+}  // extern "C"

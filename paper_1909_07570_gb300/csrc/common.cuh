@@ -1,0 +1,109 @@
+// Shared host/device helpers of the nnCANDELINC CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/nncandelinc.h"
+
+namespace nnc {
+
+// Records the text of a failed CUDA call for nnc_last_error_detail().
+void set_error_detail(const char* what, cudaError_t e);
+void set_error_detail_text(const std::string& s);
+
+#define NNC_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t e__ = (expr);                               \
+    if (e__ != cudaSuccess) {                               \
+      ::nnc::set_error_detail(#expr, e__);                  \
+      return NNC_ERR_CUDA;                                  \
+    }                                                       \
+  } while (0)
+
+#define NNC_TRY(expr)                                       \
+  do {                                                      \
+    int st__ = (expr);                                      \
+    if (st__ != NNC_OK) return st__;                        \
+  } while (0)
+
+// Stream-ordered scratch: every block is taken with cudaMallocAsync on the
+// call's stream and returned with cudaFreeAsync when the arena dies.
+class Scratch {
+ public:
+  explicit Scratch(cudaStream_t s) : stream_(s) {}
+  ~Scratch() { release(); }
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+
+  template <typename T>
+  int get(T** out, size_t count) {
+    *out = nullptr;
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), stream_);
+    if (e != cudaSuccess) {
+      set_error_detail("cudaMallocAsync", e);
+      (void)cudaGetLastError();
+      return NNC_ERR_ALLOC;
+    }
+    if (n_ == kMax) {
+      cudaFreeAsync(p, stream_);
+      set_error_detail_text("scratch arena: too many blocks");
+      return NNC_ERR_ALLOC;
+    }
+    blocks_[n_++] = p;
+    *out = static_cast<T*>(p);
+    return NNC_OK;
+  }
+
+  void release() {
+    for (int i = n_ - 1; i >= 0; --i) cudaFreeAsync(blocks_[i], stream_);
+    n_ = 0;
+  }
+
+ private:
+  static constexpr int kMax = 64;
+  cudaStream_t stream_;
+  void* blocks_[kMax] = {};
+  int n_ = 0;
+};
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int device_sm_count();
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; every thread gets the result. `sh` holds >= 32 values.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  T t = (threadIdx.x < nwarps) ? sh[threadIdx.x] : T(0);
+  if (warp == 0) {
+    t = warp_sum(t);
+    if (lane == 0) sh[0] = t;
+  }
+  __syncthreads();
+  T r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+}  // namespace nnc

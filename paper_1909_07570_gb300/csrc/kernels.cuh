@@ -1,0 +1,57 @@
+// Launchers of the SIMT kernels (definitions in ttm.cu, small.cu, nncp.cu,
+// residual.cu). T is float or double; every launcher is stream-ordered and
+// returns the launch status.
+#pragma once
+
+#include "common.cuh"
+
+namespace nnc {
+
+// Mode product on a tensor viewed as (L, J, C) in C order (Appendix A, Def. of
+// n-mode multiplication, with A = Fm^T):
+//   out[l, q, c] = sum_j Fm[j * fs_j + q * fs_q] * Y[(l * J + j) * C + c]
+// out is (L, Q, C). When the launch would not fill the GPU, the J range is
+// split over blocks that write partial sums to `split_buf` (capacity
+// `split_cap` elements), which a second kernel adds in a fixed order.
+template <typename T>
+cudaError_t launch_ttm(const T* Y, int64_t L, int J, int64_t C, const T* Fm, int64_t fs_j,
+                       int64_t fs_q, int Q, T* out, T* split_buf, size_t split_cap,
+                       cudaStream_t s);
+
+// out[i, a] = sum_{l, c} Y[(l * NI + i) * C + c] * G[(l * MA + a) * C + c]
+// Y is (L, NI, C), G is (L, MA, C), out is NI x MA. It is the product of the
+// mode-n unfoldings unfold_n(Y) unfold_n(G)^T when the tensors are viewed
+// with mode n in the middle.
+template <typename T>
+cudaError_t launch_pair_contract(const T* Y, const T* G, int64_t L, int NI, int MA, int64_t C,
+                                 T* out, cudaStream_t s);
+
+// F[i, a] <- max(F[i, a] * Num[i, a] / max(sum_b F[i, b] H[b, a], eps), 0),
+// F and Num N x M, H M x M.
+template <typename T>
+cudaError_t launch_factor_mu(T* F, const T* Num, const T* H, int64_t N, int M, double eps,
+                             cudaStream_t s);
+
+// theta <- max(theta * num / max(den, eps), 0), elementwise over n entries.
+template <typename T>
+cudaError_t launch_elementwise_mu(T* theta, const T* num, const T* den, int64_t n, double eps,
+                                  cudaStream_t s);
+
+// trace_out[0] = sqrt(max(x2 - 2 <M, G> + <G, Dn>, 0) / x2), FP64 sums over
+// n core entries (one block).
+template <typename T>
+cudaError_t launch_residual_identity(const T* M, const T* G, const T* Dn, int64_t n,
+                                     const double* x2, double* trace_out, cudaStream_t s);
+
+// One pass over X: sum of squares (FP64) and counts of negative and
+// non-finite entries. part holds >= 3 * kStatBlocks doubles, out 3 doubles:
+// {sum x^2, #negative, #non-finite}.
+constexpr int kStatBlocks = 1024;
+template <typename T>
+cudaError_t launch_tensor_stats(const T* X, int64_t n, double* part, double* out, cudaStream_t s);
+
+// Per-element conversion: dst = (U)src.
+template <typename T, typename U>
+cudaError_t launch_convert(const T* src, U* dst, int64_t n, cudaStream_t s);
+
+}  // namespace nnc

@@ -1,0 +1,221 @@
+// nnCPD of Tucker cores (Alg. 1, step 2): multiplicative updates of
+// B^(1), ..., B^(d) for 1/2 ||G - I x_n B^(n)||_F^2, one thread block per fit.
+//
+// A block keeps every B^(k) (m_k x r) and its Gram B^(k)T B^(k) (r x r) in
+// shared memory and reads the core G through L1. A sweep, for n = 1..d:
+//   V   = Hadamard product over k != n of Gram_k
+//   Num = unfold_n(G) KR_{k!=n} B^(k)   (MTTKRP, factored loop over the modes)
+//   B^(n) <- max(B^(n) * Num / max(B^(n) V, eps), 0);  Gram_n <- B^(n)T B^(n)
+// The same kernel serves one fit (nncp_core_fit) and many uneven fits in one
+// launch (nncp_core_fit_batched); no block waits on another.
+#include "kernels.cuh"
+#include "nncp.cuh"
+
+namespace nnc {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T, int D>
+__device__ T mttkrp_entry(const T* __restrict__ G, const int* m, const int64_t* st,
+                          T* const* Bs, int r, int n, int i, int q) {
+  int o[D - 1];
+  {
+    int t = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k != n) o[t++] = k;
+  }
+  const T* g0 = G + (int64_t)i * st[n];
+  T s = T(0);
+  if constexpr (D == 3) {
+    for (int j0 = 0; j0 < m[o[0]]; ++j0) {
+      const T* g1 = g0 + j0 * st[o[0]];
+      T inner = T(0);
+      for (int j1 = 0; j1 < m[o[1]]; ++j1)
+        inner = fma(g1[j1 * st[o[1]]], Bs[o[1]][j1 * r + q], inner);
+      s = fma(Bs[o[0]][j0 * r + q], inner, s);
+    }
+  } else {
+    for (int j0 = 0; j0 < m[o[0]]; ++j0) {
+      const T* g1 = g0 + j0 * st[o[0]];
+      T mid = T(0);
+      for (int j1 = 0; j1 < m[o[1]]; ++j1) {
+        const T* g2 = g1 + j1 * st[o[1]];
+        T inner = T(0);
+        for (int j2 = 0; j2 < m[o[2]]; ++j2)
+          inner = fma(g2[j2 * st[o[2]]], Bs[o[2]][j2 * r + q], inner);
+        mid = fma(Bs[o[1]][j1 * r + q], inner, mid);
+      }
+      s = fma(Bs[o[0]][j0 * r + q], mid, s);
+    }
+  }
+  return s;
+}
+
+template <typename T, int D>
+__device__ void fit_one(const nncp_job& job, int iters, T eps, unsigned char* smem,
+                        double* rel_err_out) {
+  __shared__ double red[32];
+  const int r = job.r;
+  int m[D];
+  int64_t st[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) m[k] = job.m[k];
+  st[D - 1] = 1;
+#pragma unroll
+  for (int k = D - 2; k >= 0; --k) st[k] = st[k + 1] * m[k + 1];
+  int mmax = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) mmax = m[k] > mmax ? m[k] : mmax;
+
+  // Shared memory: B^(k) | Gram_k | V | Num
+  T* p = reinterpret_cast<T*>(smem);
+  T* Bs[D];
+  T* Gram[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    Bs[k] = p;
+    p += m[k] * r;
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    Gram[k] = p;
+    p += r * r;
+  }
+  T* V = p;
+  p += r * r;
+  T* Num = p;
+
+  const T* G = static_cast<const T*>(job.G);
+  const int tid = threadIdx.x;
+
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const T* src = static_cast<const T*>(job.B[k]);
+    for (int e = tid; e < m[k] * r; e += blockDim.x) Bs[k][e] = src[e];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    for (int e = tid; e < r * r; e += blockDim.x) {
+      const int a = e / r, b = e % r;
+      T s = T(0);
+      for (int i = 0; i < m[k]; ++i) s = fma(Bs[k][i * r + a], Bs[k][i * r + b], s);
+      Gram[k][e] = s;
+    }
+  __syncthreads();
+
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int n = 0; n < D; ++n) {
+      for (int e = tid; e < r * r; e += blockDim.x) {
+        T v = T(1);
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          if (k != n) v *= Gram[k][e];
+        V[e] = v;
+      }
+      for (int e = tid; e < m[n] * r; e += blockDim.x)
+        Num[e] = mttkrp_entry<T, D>(G, m, st, Bs, r, n, e / r, e % r);
+      __syncthreads();
+      // New values go to Num first: every row of the old B^(n) is still read.
+      for (int e = tid; e < m[n] * r; e += blockDim.x) {
+        const int i = e / r, q = e % r;
+        T den = T(0);
+        for (int pp = 0; pp < r; ++pp) den = fma(Bs[n][i * r + pp], V[pp * r + q], den);
+        const T v = Bs[n][e] * Num[e] / (den > eps ? den : eps);
+        Num[e] = v > T(0) ? v : T(0);
+      }
+      __syncthreads();
+      for (int e = tid; e < m[n] * r; e += blockDim.x) Bs[n][e] = Num[e];
+      __syncthreads();
+      for (int e = tid; e < r * r; e += blockDim.x) {
+        const int a = e / r, b = e % r;
+        T s = T(0);
+        for (int i = 0; i < m[n]; ++i) s = fma(Bs[n][i * r + a], Bs[n][i * r + b], s);
+        Gram[n][e] = s;
+      }
+      __syncthreads();
+    }
+  }
+
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    T* dst = static_cast<T*>(job.B[k]);
+    for (int e = tid; e < m[k] * r; e += blockDim.x) dst[e] = Bs[k][e];
+  }
+
+  if (rel_err_out != nullptr) {
+    int64_t total = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) total *= m[k];
+    double d2 = 0.0, g2 = 0.0;
+    for (int64_t e = tid; e < total; e += blockDim.x) {
+      int idx[D];
+      int64_t rem = e;
+#pragma unroll
+      for (int k = D - 1; k >= 0; --k) {
+        idx[k] = (int)(rem % m[k]);
+        rem /= m[k];
+      }
+      T hat = T(0);
+      for (int q = 0; q < r; ++q) {
+        T prod = T(1);
+#pragma unroll
+        for (int k = 0; k < D; ++k) prod *= Bs[k][idx[k] * r + q];
+        hat += prod;
+      }
+      const double g = (double)G[e];
+      const double dd = g - (double)hat;
+      d2 += dd * dd;
+      g2 += g * g;
+    }
+    d2 = block_sum(d2, red);
+    g2 = block_sum(g2, red);
+    if (tid == 0) *rel_err_out = g2 > 0.0 ? sqrt(d2 / g2) : sqrt(d2);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+nncp_kernel(const nncp_job* __restrict__ jobs, int iters, T eps, double* rel_errs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const nncp_job job = jobs[blockIdx.x];
+  double* out = rel_errs ? rel_errs + blockIdx.x : nullptr;
+  if (job.d == 3)
+    fit_one<T, 3>(job, iters, eps, smem_raw, out);
+  else
+    fit_one<T, 4>(job, iters, eps, smem_raw, out);
+}
+
+}  // namespace
+
+size_t nncp_smem_bytes(const nncp_job& j, size_t elem) {
+  int mmax = 0, msum = 0;
+  for (int k = 0; k < j.d; ++k) {
+    msum += j.m[k];
+    mmax = j.m[k] > mmax ? j.m[k] : mmax;
+  }
+  const size_t n = (size_t)msum * j.r + (size_t)(j.d + 1) * j.r * j.r + (size_t)mmax * j.r;
+  return n * elem;
+}
+
+template <typename T>
+cudaError_t launch_nncp(const nncp_job* jobs_dev, int n_jobs, size_t smem, int iters, double eps,
+                        double* rel_errs, cudaStream_t s) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(nncp_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  nncp_kernel<T><<<n_jobs, kThreads, smem, s>>>(jobs_dev, iters, (T)eps, rel_errs);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_nncp<float>(const nncp_job*, int, size_t, int, double, double*,
+                                        cudaStream_t);
+template cudaError_t launch_nncp<double>(const nncp_job*, int, size_t, int, double, double*,
+                                         cudaStream_t);
+
+}  // namespace nnc

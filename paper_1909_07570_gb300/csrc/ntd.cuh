@@ -1,0 +1,18 @@
+// nnTD of a 3-way tensor (ntd.cu): the body of ntd_fit.
+#pragma once
+
+#include "common.cuh"
+
+namespace nnc {
+
+// FP64 (T = double) and FP32 (T = float) paths. Arguments as ntd_fit with
+// d = 3, already validated.
+template <typename T>
+int ntd_fit3(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T* const* F, T* G,
+             double* trace, double* rel_err, cudaStream_t s);
+
+// NNC_BF16_REFINE path.
+int ntd_fit3_bf16(const float* X, const int64_t* dims, const int* m, const nnc_opts* o,
+                  float* const* F, float* G, double* trace, double* rel_err, cudaStream_t s);
+
+}  // namespace nnc

@@ -1,0 +1,177 @@
+// The lift A^(n) = F^(n) B^(n) and the one-pass reconstruction residual.
+//
+// recon_residual streams X once. For a 3-way X the model is first reduced to
+// rows U[i, j, :] (length K = m_3 for Tucker, r for CP):
+//   Tucker: U = G x_1 F^(1) x_2 F^(2)        X_hat[i, j, k] = sum_c U[i, j, c] F^(3)[k, c]
+//   CP:     U[i, j, q] = A^(1)[i, q] A^(2)[j, q]   X_hat[i, j, k] = sum_q U[i, j, q] A^(3)[k, q]
+// (Eq. TD:matrix-format and Eq. CPD:matrix-format, contracted mode by mode).
+// The streaming kernel holds the last factor transposed in shared memory,
+// gives each thread one k of a row, forms X_hat in T and accumulates
+// (x - x_hat)^2 and x^2 in FP64; per-block partials are added in block order.
+#include "kernels.cuh"
+#include "residual.cuh"
+
+namespace nnc {
+namespace {
+
+template <typename T>
+__global__ void lift_kernel(const T* __restrict__ F, const T* __restrict__ B, int64_t N, int M,
+                            int r, T* __restrict__ A) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * r;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / r;
+    const int q = (int)(e % r);
+    T s = T(0);
+    for (int a = 0; a < M; ++a) s = fma(F[i * M + a], B[(int64_t)a * r + q], s);
+    A[e] = s;
+  }
+}
+
+// out[l, q, c] = sum_j A[q, j] Y[l, j, c] for any Q (one thread per output).
+template <typename T>
+__global__ void mode_product_any_kernel(const T* __restrict__ Y, int64_t L, int J, int64_t C,
+                                        const T* __restrict__ A, int Q, T* __restrict__ out) {
+  const int64_t n = L * Q * C;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e % C;
+    const int64_t q = (e / C) % Q;
+    const int64_t l = e / (C * Q);
+    const T* y = Y + l * J * C + c;
+    const T* a = A + q * J;
+    T s = T(0);
+    for (int j = 0; j < J; ++j) s = fma(a[j], y[(int64_t)j * C], s);
+    out[e] = s;
+  }
+}
+
+template <typename T>
+__global__ void cp_rows_kernel(const T* __restrict__ A1, const T* __restrict__ A2, int64_t N1,
+                               int64_t N2, int r, T* __restrict__ U) {
+  const int64_t n = N1 * N2 * r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e % r);
+    const int64_t j = (e / r) % N2;
+    const int64_t i = e / (r * N2);
+    U[e] = A1[i * r + q] * A2[j * r + q];
+  }
+}
+
+constexpr int kResThreads = 256;
+constexpr int kResRows = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(kResThreads)
+residual_stream_kernel(const T* __restrict__ X, int64_t R, int64_t N3, const T* __restrict__ U,
+                       int K, const T* __restrict__ F3, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ft = reinterpret_cast<T*>(smem_raw);  // K x kResThreads, transposed chunk of F3
+  __shared__ double red[32];
+  const int64_t k = (int64_t)blockIdx.x * kResThreads + threadIdx.x;
+  const bool act = k < N3;
+  for (int c = 0; c < K; ++c) ft[c * kResThreads + threadIdx.x] = act ? F3[k * K + c] : T(0);
+  __syncthreads();
+  double d2 = 0.0, x2 = 0.0;
+  const int64_t r0 = (int64_t)blockIdx.y * kResRows;
+  const int64_t r1 = r0 + kResRows < R ? r0 + kResRows : R;
+  if (act) {
+    for (int64_t row = r0; row < r1; ++row) {
+      const T* u = U + row * K;
+      T hat = T(0);
+      for (int c = 0; c < K; ++c) hat = fma(u[c], ft[c * kResThreads + threadIdx.x], hat);
+      const double x = (double)X[row * N3 + k];
+      const double dd = x - (double)hat;
+      d2 += dd * dd;
+      x2 += x * x;
+    }
+  }
+  d2 = block_sum(d2, red);
+  x2 = block_sum(x2, red);
+  if (threadIdx.x == 0) {
+    const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    part[2 * b] = d2;
+    part[2 * b + 1] = x2;
+  }
+}
+
+__global__ void residual_final_kernel(const double* __restrict__ part, int64_t nblocks,
+                                      double* out) {
+  __shared__ double red[32];
+  double d2 = 0.0, x2 = 0.0;
+  for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    d2 += part[2 * b];
+    x2 += part[2 * b + 1];
+  }
+  d2 = block_sum(d2, red);
+  x2 = block_sum(x2, red);
+  if (threadIdx.x == 0) {
+    out[0] = d2;
+    out[1] = x2;
+  }
+}
+
+unsigned grid_cap(int64_t n, int threads) {
+  int64_t b = ceil_div(n, threads);
+  if (b > 8192) b = 8192;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_lift(const T* F, const T* B, int64_t N, int M, int r, T* A, cudaStream_t s) {
+  lift_kernel<T><<<grid_cap(N * r, 256), 256, 0, s>>>(F, B, N, M, r, A);
+  return cudaGetLastError();
+}
+
+template <typename T>
+int residual3_device(const T* X, const int64_t* dims, int model, const int* m, int r,
+                     const T* const* factors, const T* G, double* out2, Scratch& sc,
+                     cudaStream_t s) {
+  const int64_t N1 = dims[0], N2 = dims[1], N3 = dims[2];
+  const int K = model == 0 ? m[2] : r;
+  T* U = nullptr;
+  NNC_TRY(sc.get(&U, (size_t)(N1 * N2 * K)));
+  if (model == 0) {
+    T* T1 = nullptr;
+    NNC_TRY(sc.get(&T1, (size_t)(N1 * m[1] * m[2])));
+    // T1[i, b, c] = sum_a F1[i, a] G[a, b, c];  U[i, j, c] = sum_b F2[j, b] T1[i, b, c]
+    mode_product_any_kernel<T><<<grid_cap(N1 * m[1] * m[2], 256), 256, 0, s>>>(
+        G, 1, m[0], (int64_t)m[1] * m[2], factors[0], (int)N1, T1);
+    mode_product_any_kernel<T><<<grid_cap(N1 * N2 * m[2], 256), 256, 0, s>>>(
+        T1, N1, m[1], m[2], factors[1], (int)N2, U);
+  } else {
+    cp_rows_kernel<T><<<grid_cap(N1 * N2 * r, 256), 256, 0, s>>>(factors[0], factors[1], N1, N2,
+                                                                   r, U);
+  }
+  NNC_CUDA_TRY(cudaGetLastError());
+  const T* F3 = factors[2];  // F^(3) (Tucker) or A^(3) (CP): N3 x K
+  const int64_t R = N1 * N2;
+  dim3 grid((unsigned)ceil_div(N3, kResThreads), (unsigned)ceil_div(R, kResRows));
+  const int64_t nblocks = (int64_t)grid.x * grid.y;
+  double* part = nullptr;
+  NNC_TRY(sc.get(&part, (size_t)(2 * nblocks)));
+  const size_t smem = (size_t)K * kResThreads * sizeof(T);
+  if (smem > 48 * 1024)
+    NNC_CUDA_TRY(cudaFuncSetAttribute(residual_stream_kernel<T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  residual_stream_kernel<T><<<grid, kResThreads, smem, s>>>(X, R, N3, U, K, F3, part);
+  residual_final_kernel<<<1, 1024, 0, s>>>(part, nblocks, out2);
+  NNC_CUDA_TRY(cudaGetLastError());
+  return NNC_OK;
+}
+
+template cudaError_t launch_lift<float>(const float*, const float*, int64_t, int, int, float*,
+                                        cudaStream_t);
+template cudaError_t launch_lift<double>(const double*, const double*, int64_t, int, int, double*,
+                                         cudaStream_t);
+template int residual3_device<float>(const float*, const int64_t*, int, const int*, int,
+                                     const float* const*, const float*, double*, Scratch&,
+                                     cudaStream_t);
+template int residual3_device<double>(const double*, const int64_t*, int, const int*, int,
+                                      const double* const*, const double*, double*, Scratch&,
+                                      cudaStream_t);
+
+}  // namespace nnc

@@ -1,0 +1,20 @@
+// Launchers of the lift and of the one-pass residual (residual.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace nnc {
+
+// A = F B with F N x M, B M x r, A N x r (row-major).
+template <typename T>
+cudaError_t launch_lift(const T* F, const T* B, int64_t N, int M, int r, T* A, cudaStream_t s);
+
+// out2[0] = ||X - X_hat||_F^2, out2[1] = ||X||_F^2 (device, FP64) for a 3-way
+// X; model 0 = Tucker (factors F, core G, multirank m), 1 = CP (factors A,
+// rank r). Scratch comes from `sc`.
+template <typename T>
+int residual3_device(const T* X, const int64_t* dims, int model, const int* m, int r,
+                     const T* const* factors, const T* G, double* out2, Scratch& sc,
+                     cudaStream_t s);
+
+}  // namespace nnc

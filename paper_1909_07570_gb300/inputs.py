@@ -87,7 +87,7 @@ def _outer_sum(A):
     d = len(A)
     letters = "abcdefgh"[:d]
     spec = ",".join(f"{c}z" for c in letters) + "->" + letters
-    return np.einsum(spec, *A, optimize=True)
+    return np.ascontiguousarray(np.einsum(spec, *A, optimize=True))
 
 
 def planted_tensor(dims, rank, seed, dist="uniform", zero_frac=0.0, noise=0.01):

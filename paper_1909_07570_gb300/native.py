@@ -1,0 +1,222 @@
+"""Thin ctypes binding of libnncandelinc.so (include/nncandelinc.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. Tensors are torch CUDA tensors; the binding passes their data
+pointers and the current torch stream. If the library is missing, every call
+raises - there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+NNC_FP64, NNC_FP32, NNC_BF16_REFINE = 0, 1, 2
+
+_STATUS = {
+    0: "ok", -1: "invalid argument", -2: "negative input", -3: "non-finite value",
+    -4: "CUDA error", -5: "allocation failed", -6: "unsupported",
+}
+
+# Every symbol include/nncandelinc.h declares.
+EXPORTED = ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched", "candelinc_lift",
+            "recon_residual", "nnc_status_string", "nnc_last_error_detail")
+
+
+class NncError(RuntimeError):
+    def __init__(self, fn, status, detail):
+        self.status = status
+        super().__init__(f"{fn} failed: {_STATUS.get(status, status)} ({status}) {detail}".rstrip())
+
+
+class nnc_opts(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("refine_iters", ctypes.c_int), ("eps", ctypes.c_double)]
+
+
+class nncp_job(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_void_p), ("d", ctypes.c_int), ("m", ctypes.c_int * 4),
+                ("r", ctypes.c_int), ("B", ctypes.c_void_p * 4)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the library (once). Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libnncandelinc.so not found at {path}: run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(path)
+    vp, i64p, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int), \
+        ctypes.POINTER(ctypes.c_double)
+    vpp = ctypes.POINTER(ctypes.c_void_p)
+    lib.ntd_fit.argtypes = [vp, ctypes.c_int, i64p, ip, ctypes.c_int, ctypes.POINTER(nnc_opts), vpp,
+                            vp, vp, dp, vp]
+    lib.nncp_core_fit.argtypes = [vp, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(nnc_opts), vpp, dp, vp]
+    lib.nncp_core_fit_batched.argtypes = [ctypes.c_int, ctypes.POINTER(nncp_job), ctypes.c_int,
+                                          ctypes.POINTER(nnc_opts), vp, vp]
+    lib.candelinc_lift.argtypes = [ctypes.c_int, i64p, ip, ctypes.c_int, ctypes.c_int, vpp, vpp,
+                                   vpp, vp]
+    lib.recon_residual.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, ip,
+                                   ctypes.c_int, vpp, vp, dp, dp, vp]
+    for fn in ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched", "candelinc_lift",
+               "recon_residual"):
+        getattr(lib, fn).restype = ctypes.c_int
+    lib.nnc_status_string.argtypes = [ctypes.c_int]
+    lib.nnc_status_string.restype = ctypes.c_char_p
+    lib.nnc_last_error_detail.argtypes = []
+    lib.nnc_last_error_detail.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(fn, status):
+    if status != 0:
+        detail = load().nnc_last_error_detail().decode()
+        raise NncError(fn, status, detail)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _require(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _precision(X, precision):
+    if precision is None:
+        precision = "fp64" if X.dtype == torch.float64 else "fp32"
+    code = {"fp64": NNC_FP64, "fp32": NNC_FP32, "bf16": NNC_BF16_REFINE}[precision]
+    dtype = torch.float64 if code == NNC_FP64 else torch.float32
+    return code, dtype
+
+
+def _i64(vals):
+    return (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+def _i32(vals):
+    return (ctypes.c_int * len(vals))(*[int(v) for v in vals])
+
+
+def _ptrs(ts):
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+def ntd_fit(X, F, G, iters, precision=None, eps=1e-12, refine_iters=0, trace=True,
+            rel_err=True, stream=None):
+    """nnTD of X in place on F (list of N_n x m_n) and G. Returns
+    (final relative error or None, per-sweep relative-error trace or None)."""
+    code, dtype = _precision(X, precision)
+    _require(X, dtype, "X")
+    for n, f in enumerate(F):
+        _require(f, dtype, f"F[{n}]")
+    _require(G, dtype, "G")
+    d = X.dim()
+    m = [f.shape[1] for f in F]
+    tr = torch.empty(max(iters, 1), dtype=torch.float64, device=X.device) if trace else None
+    err = ctypes.c_double(float("nan"))
+    opts = nnc_opts(int(iters), int(refine_iters), float(eps))
+    st = load().ntd_fit(_ptr(X), d, _i64(X.shape), _i32(m), code, ctypes.byref(opts), _ptrs(F),
+                        _ptr(G), _ptr(tr) if trace else None,
+                        ctypes.byref(err) if rel_err else None, _stream(stream))
+    _check("ntd_fit", st)
+    return (err.value if rel_err else None), (tr[:iters] if trace else None)
+
+
+def nncp_core_fit(G, B, iters, precision=None, eps=1e-12, rel_err=True, stream=None):
+    """nnCPD of the core G in place on B (list of m_n x r). Returns the final
+    relative error (or None)."""
+    code, dtype = _precision(G, precision)
+    _require(G, dtype, "G")
+    for n, b in enumerate(B):
+        _require(b, dtype, f"B[{n}]")
+    err = ctypes.c_double(float("nan"))
+    opts = nnc_opts(int(iters), 0, float(eps))
+    st = load().nncp_core_fit(_ptr(G), G.dim(), _i32(G.shape), B[0].shape[1], code,
+                              ctypes.byref(opts), _ptrs(B),
+                              ctypes.byref(err) if rel_err else None, _stream(stream))
+    _check("nncp_core_fit", st)
+    return err.value if rel_err else None
+
+
+def nncp_core_fit_batched(problems, iters, precision=None, eps=1e-12, stream=None):
+    """Many core fits in one launch. ``problems`` is a list of (G, [B^(n)]);
+    every B is updated in place. Returns a float64 CUDA tensor of the final
+    relative errors."""
+    if not problems:
+        return None
+    G0 = problems[0][0]
+    code, dtype = _precision(G0, precision)
+    jobs = (nncp_job * len(problems))()
+    for i, (G, B) in enumerate(problems):
+        _require(G, dtype, f"problems[{i}].G")
+        j = jobs[i]
+        j.G = G.data_ptr()
+        j.d = G.dim()
+        j.r = B[0].shape[1]
+        for n in range(G.dim()):
+            _require(B[n], dtype, f"problems[{i}].B[{n}]")
+            j.m[n] = G.shape[n]
+            j.B[n] = B[n].data_ptr()
+    errs = torch.empty(len(problems), dtype=torch.float64, device=G0.device)
+    opts = nnc_opts(int(iters), 0, float(eps))
+    st = load().nncp_core_fit_batched(len(problems), jobs, code, ctypes.byref(opts), _ptr(errs),
+                                      _stream(stream))
+    _check("nncp_core_fit_batched", st)
+    return errs
+
+
+def candelinc_lift(F, B, out=None, stream=None):
+    """A^(n) = F^(n) B^(n) for every mode; returns the list of A^(n)."""
+    dtype = F[0].dtype
+    code = NNC_FP64 if dtype == torch.float64 else NNC_FP32
+    for n in range(len(F)):
+        _require(F[n], dtype, f"F[{n}]")
+        _require(B[n], dtype, f"B[{n}]")
+    r = B[0].shape[1]
+    A = out if out is not None else [torch.empty(f.shape[0], r, dtype=dtype, device=f.device)
+                                     for f in F]
+    st = load().candelinc_lift(len(F), _i64([f.shape[0] for f in F]), _i32([f.shape[1] for f in F]),
+                               r, code, _ptrs(F), _ptrs(B), _ptrs(A), _stream(stream))
+    _check("candelinc_lift", st)
+    return A
+
+
+def recon_residual(X, factors, G=None, stream=None):
+    """(||X - X_hat||_F, ||X||_F): Tucker model when G is given, else CP."""
+    dtype = X.dtype
+    code = NNC_FP64 if dtype == torch.float64 else NNC_FP32
+    _require(X, dtype, "X")
+    for n, f in enumerate(factors):
+        _require(f, dtype, f"factors[{n}]")
+    model = 0 if G is not None else 1
+    if G is not None:
+        _require(G, dtype, "G")
+    m = [f.shape[1] for f in factors]
+    r = factors[0].shape[1]
+    rn, xn = ctypes.c_double(), ctypes.c_double()
+    st = load().recon_residual(_ptr(X), X.dim(), _i64(X.shape), code, model, _i32(m), r,
+                               _ptrs(factors), _ptr(G) if G is not None else None,
+                               ctypes.byref(rn), ctypes.byref(xn), _stream(stream))
+    _check("recon_residual", st)
+    return rn.value, xn.value

@@ -1,0 +1,73 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads without
+a GPU and exports every function include/nncandelinc.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([a-z_][a-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1909_07570_gb300 import build as b
+    path = b.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_four_calls():
+    names = _declared_functions()
+    for fn in ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched", "candelinc_lift",
+               "recon_residual", "nnc_status_string"):
+        assert fn in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for fn in sorted(_declared_functions()):
+        assert hasattr(lib, fn), fn
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1909_07570_gb300 import native
+    assert set(native.EXPORTED) == _declared_functions()
+
+
+def test_status_strings_without_gpu(lib):
+    lib.nnc_status_string.restype = ctypes.c_char_p
+    assert lib.nnc_status_string(0) == b"ok"
+    assert b"negative" in lib.nnc_status_string(-2)
+
+
+def test_argument_checks_need_no_gpu(lib):
+    # Invalid options are rejected before any CUDA call.
+    from paper_1909_07570_gb300 import native
+    native.load()
+    opts = native.nnc_opts(-1, 0, 1e-12)
+    dims = (ctypes.c_int64 * 3)(4, 4, 4)
+    m = (ctypes.c_int * 3)(2, 2, 2)
+    ptrs = (ctypes.c_void_p * 3)(1, 1, 1)
+    st = native._lib.ntd_fit(ctypes.c_void_p(1), 3, dims, m, 1, ctypes.byref(opts), ptrs,
+                             ctypes.c_void_p(1), None, None, None)
+    assert st == -1
+    opts = native.nnc_opts(3, 0, 1e-12)
+    st = native._lib.ntd_fit(ctypes.c_void_p(1), 5, dims, m, 1, ctypes.byref(opts), ptrs,
+                             ctypes.c_void_p(1), None, None, None)
+    assert st == -1
+    bad_m = (ctypes.c_int * 3)(2, 0, 2)
+    st = native._lib.ntd_fit(ctypes.c_void_p(1), 3, dims, bad_m, 1, ctypes.byref(opts), ptrs,
+                             ctypes.c_void_p(1), None, None, None)
+    assert st == -1
