@@ -1,0 +1,442 @@
+"""Benchmark of the nnCANDELINC hot path (Alg. 1) on one GB300.
+
+A step is one whole Alg. 1 run on one synthetic problem: nnTD of X (all its
+sweeps, with the per-sweep FP64 relative-error trace), nnCP of the core, the
+lift A^(n) = F^(n) B^(n) and the final one-pass residual of the lifted model.
+Every step restarts from the same initial factors. The value is nnTD sweeps
+per second over the timed steps (device time, inputs resident in HBM).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl native|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this project
+has) on the host cores, one bounded sample of the same workload per step.
+Under torchrun (N > 1) every rank runs an independent replica (weak scaling,
+no data-path collective); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "cp10_256x256x256_m20_fp32"
+METRIC = "nnCANDELINC iters/s & TTM TFLOP/s (% roofline), BF16 vs FP32 at equal rel-error"
+L2_FLUSH_BYTES = 512 << 20
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "native" else "gloo"
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                return json.load(fh), "measured"
+        except Exception:
+            pass
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def peak_value(peaks, *keys):
+    for k in keys:
+        v = peaks.get(k)
+        if isinstance(v, (int, float)):
+            return float(v)
+        if isinstance(v, dict):
+            for kk in ("value", "gbs", "tflops"):
+                if isinstance(v.get(kk), (int, float)):
+                    return float(v[kk])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def stored_traffic(kernel_name, source_files):
+    """DRAM bytes per launch of `kernel_name` from the committed ncu summary, if
+    the kernel's sources are unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as fh:
+            rec = json.load(fh).get(kernel_name)
+    except Exception:
+        return None
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for f in source_files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+
+def run_native(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_1909_07570_gb300 import inputs, native
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = inputs.WORKLOADS[args.workload]
+    if w.dtype == "bf16":
+        precision, dt, dname = "bf16", torch.float32, "bf16"
+    elif w.dtype == "f64":
+        precision, dt, dname = "fp64", torch.float64, "f64"
+    else:
+        precision, dt, dname = "fp32", torch.float32, "f32"
+    X64, _, F0, G0, B0 = inputs.make_problem(
+        inputs.Workload(**{**w.__dict__, "seed": w.seed + 17 * rank}))
+    Xh = torch.tensor(X64, dtype=dt).pin_memory()
+    X = Xh.to(dev)
+    F0d = [torch.tensor(f, dtype=dt, device=dev) for f in F0]
+    G0d = torch.tensor(G0, dtype=dt, device=dev)
+    B0d = [torch.tensor(b, dtype=dt, device=dev) for b in B0]
+    F = [f.clone() for f in F0d]
+    G = G0d.clone()
+    B = [b.clone() for b in B0d]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def step():
+        for a, b in zip(F, F0d):
+            a.copy_(b)
+        G.copy_(G0d)
+        for a, b in zip(B, B0d):
+            a.copy_(b)
+        _, tr = native.ntd_fit(X, F, G, w.iters, precision=precision, refine_iters=w.refine_iters,
+                               trace=True, rel_err=False)
+        native.nncp_core_fit(G, B, w.cp_iters, precision=precision, rel_err=False)
+        A = native.candelinc_lift(F, B)
+        rn, xn = native.recon_residual(X, A)
+        out["tucker_rel_err"] = tr
+        out["lifted_rel_err"] = rn / xn
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    native.nnc_profile_enable(True)
+    launches0 = native.nnc_kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush between timed steps, outside the events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    gpu_launches = native.nnc_kernel_launches() - launches0
+    prof = {k: native.nnc_profile_read(k) for k in native.PASS_KINDS}
+    native.nnc_profile_enable(False)
+
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    ms_per_step = total_ms / args.steps
+    value = world * w.iters * args.steps / (total_ms / 1e3)
+
+    # Dominant kernel: the pass over X with the largest total event time.
+    nX = int(np.prod(w.dims))
+    elem = 2 if precision == "bf16" else (8 if dt == torch.float64 else 4)
+    kinds = sorted(prof, key=lambda k: prof[k][1], reverse=True)
+    dom = kinds[0]
+    n_l, ms_l = prof[dom]
+    avg_s = (ms_l / n_l) / 1e3 if n_l else float("nan")
+    mdim = w.m[2] if dom in (0, 2) else w.m[0]
+    alg_bytes = nX * elem  # one read of X per pass
+    alg_flops = 2.0 * nX * mdim
+    peaks, peak_src = load_peaks()
+    hbm = peak_value(peaks, "hbm_gbs", "hbm_GBps", "hbm") or FALLBACK_PEAKS["hbm_gbs"]
+    achieved = alg_bytes / avg_s / 1e9
+    kernel_names = {0: "ttm_rows_kernel", 1: "ttm_cols_kernel", 2: "ttm_tc_kernel",
+                    3: "ttm_tc_kernel"}
+    traffic = stored_traffic(f"{kernel_names[dom]}:{args.workload}",
+                             ["paper_1909_07570_gb300/csrc/ttm.cu"])
+    # TTM TFLOP/s over both passes: 2 * prod(N) * m_n flops per launch.
+    pass_flops = {0: 2.0 * nX * w.m[2], 1: 2.0 * nX * w.m[0], 2: 2.0 * nX * w.m[2],
+                  3: 2.0 * nX * w.m[0]}
+    pass_ms = sum(v[1] for v in prof.values())
+    flops_all = sum(prof[k][0] * pass_flops[k] for k in prof)
+    ttm_tflops = flops_all / (pass_ms / 1e3) / 1e12 if pass_ms else None
+    roofline = {
+        "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+        "frac": round(achieved / hbm, 4), "traffic": traffic,
+        "kernel": kernel_names[dom], "pass": native.PASS_KINDS[dom],
+        "launches": n_l, "avg_launch_us": round(avg_s * 1e6, 3),
+        "algorithmic_bytes_per_launch": alg_bytes, "flops_per_launch": alg_flops,
+        "achieved_tflops": round(alg_flops / avg_s / 1e12, 3),
+        "peak_source": f"{peak_src} ({'of measured' if peak_src == 'measured' else 'of fallback'})",
+        "stream": "private capture stream of ntd_fit (events recorded in the replayed graph)",
+    }
+
+    # End to end through the public API with host buffers: H2D of X and the
+    # initial factors from pinned memory, the whole step, D2H of the lifted
+    # factors and the scalar result.
+    F0h = [torch.tensor(f, dtype=dt).pin_memory() for f in F0]
+    G0h = torch.tensor(G0, dtype=dt).pin_memory()
+    B0h = [torch.tensor(b, dtype=dt).pin_memory() for b in B0]
+    A_h = [torch.empty(n, w.r, dtype=dt).pin_memory() for n in w.dims]
+    h2d = Xh.numel() * Xh.element_size() + sum(f.numel() * f.element_size() for f in F0h) + \
+        G0h.numel() * G0h.element_size() + sum(b.numel() * b.element_size() for b in B0h)
+    d2h = sum(a.numel() * a.element_size() for a in A_h) + 8
+
+    def e2e_step():
+        Xd = Xh.to(dev, non_blocking=True)
+        Fd = [f.to(dev, non_blocking=True) for f in F0h]
+        Gd = G0h.to(dev, non_blocking=True)
+        Bd = [b.to(dev, non_blocking=True) for b in B0h]
+        native.ntd_fit(Xd, Fd, Gd, w.iters, precision=precision, refine_iters=w.refine_iters,
+                       trace=True, rel_err=False)
+        native.nncp_core_fit(Gd, Bd, w.cp_iters, precision=precision, rel_err=False)
+        A = native.candelinc_lift(Fd, Bd)
+        rn, xn = native.recon_residual(Xd, A)
+        for a, ah in zip(A, A_h):
+            ah.copy_(a, non_blocking=True)
+        torch.cuda.synchronize()
+        return rn / xn
+
+    e2e_step()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_value = world * w.iters * args.steps / e2e_s
+
+    result = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "iters/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": dname,
+        "data": "synthetic (seeded planted nonnegative CP + uniform noise)",
+        "config": {
+            "workload": args.workload, "dims": list(w.dims), "m": list(w.m), "r": w.r,
+            "planted_rank": w.planted_rank, "ntd_sweeps_per_step": w.iters,
+            "nncp_sweeps_per_step": w.cp_iters, "refine_sweeps": w.refine_iters,
+            "step": "ntd_fit (with FP64 trace) + nncp_core_fit + candelinc_lift + recon_residual",
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        },
+        "e2e": {"value": round(e2e_value, 3), "unit": "iters/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(gpu_launches),
+        "roofline": roofline,
+        "ttm_tflops": round(ttm_tflops, 3) if ttm_tflops else None,
+        "final_tucker_rel_err": float(out["tucker_rel_err"][-1].item()),
+        "final_lifted_rel_err": out["lifted_rel_err"],
+        "clocks": clk,
+    }
+    return result, (X64, F0, G0, w)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(X64, F0, G0, sweeps):
+    """Time `sweeps` oracle nnTD sweeps on the full X; returns (seconds, sweeps)."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.ntd_fit(X64, F0, G0, sweeps)
+    return time.perf_counter() - t0
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(X64, F0, G0, budget_s=20.0):
+    secs = oracle_sample(X64, F0, G0, 1)
+    n = max(1, min(20, int(budget_s / max(secs, 1e-3)) - 1))
+    secs_n = oracle_sample(X64, F0, G0, n)
+    return {"value": round(n / secs_n, 4), "unit": "iters/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{n} FP64 oracle nnTD sweeps (numpy) on the full workload tensor; "
+                      f"nnCP/lift/residual not included"}
+
+
+def run_reference(args, rank, world):
+    from paper_1909_07570_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    X64, _, F0, G0, _ = inputs.make_problem(w)
+    secs = oracle_sample(X64, F0, G0, 1)
+    sweeps = max(1, min(10, int(20.0 / max(secs, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_sample(X64, F0, G0, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample(X64, F0, G0, sweeps)
+    total = time.perf_counter() - t0
+    value = args.steps * sweeps / total
+    sample = f"{sweeps} FP64 oracle nnTD sweeps per step on the full workload tensor"
+    return {
+        "metric": METRIC, "value": round(value, 4), "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded planted nonnegative CP + uniform noise)",
+        "config": {"workload": args.workload, "dims": list(w.dims), "m": list(w.m), "r": w.r},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(value, 4), "unit": "iters/s", "cores": cpu_cores(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "iters/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args)
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args, rank, 1)))
+        return 0
+    result, problem = run_native(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            X64, F0, G0, _ = problem
+            result["cpu_baseline"] = cpu_baseline(X64, F0, G0)
+        print(json.dumps(result))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

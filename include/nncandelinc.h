@@ -156,6 +156,27 @@ int recon_residual(const void* X, int d, const int64_t* dims, int precision, int
                    const int* m, int r, const void* const* factors, const void* G,
                    double* resid_norm, double* x_norm, void* stream);
 
+/*
+ * Tracing aid: CUDA-event timing of the two passes over X of every nnTD
+ * sweep, the kernels that dominate ntd_fit. While enabled, ntd_fit records an
+ * event pair around each pass on the stream that launches it and adds the
+ * elapsed times to per-kind totals when the call ends. Kinds:
+ *   0  X x_3 F^(3)T, SIMT path (NNC_FP32, NNC_FP64 and the FP32 refinement sweeps)
+ *   1  X x_1 F^(1)T, SIMT path
+ *   2  X x_3 F^(3)T, BF16 tensor-core path
+ *   3  X x_1 F^(1)T, BF16 tensor-core path
+ * nnc_profile_enable(on) switches it and clears the totals; nnc_profile_read
+ * returns the number of timed launches and their total milliseconds of a
+ * kind. Meant for one thread of control: concurrent ntd_fit calls while it is
+ * enabled share one event pool and give meaningless totals.
+ */
+int nnc_profile_enable(int on);
+int nnc_profile_read(int kind, long long* launches, double* total_ms);
+
+/* Running count of the CUDA kernels this library has launched in this
+ * process (a kernel node of a replayed graph counts once per replay). */
+long long nnc_kernel_launches(void);
+
 /* Static string naming a status code. */
 const char* nnc_status_string(int status);
 

@@ -1,5 +1,6 @@
 // C ABI of the nnCANDELINC library: argument checks and the stream-ordered
 // orchestration of the kernels (Alg. 1 of arXiv 1909.07570).
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -23,6 +24,20 @@ void set_error_detail(const char* what, cudaError_t e) {
 }
 
 void set_error_detail_text(const std::string& s) { g_detail = s; }
+
+namespace {
+std::atomic<long long> g_kernel_launches{0};
+}
+
+void note_launch(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) return;
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void note_graph_launches(long long kernels) {
+  g_kernel_launches.fetch_add(kernels, std::memory_order_relaxed);
+}
 
 int device_sm_count() {
   static int cache[64] = {0};
@@ -102,6 +117,8 @@ const char* nnc_status_string(int status) {
 }
 
 const char* nnc_last_error_detail(void) { return g_detail.c_str(); }
+
+long long nnc_kernel_launches(void) { return g_kernel_launches.load(); }
 
 int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precision,
             const nnc_opts* opts, void* const* F, void* G, double* rel_err_trace,

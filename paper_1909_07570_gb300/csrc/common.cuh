@@ -75,6 +75,12 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int device_sm_count();
 
+// Counts one kernel launch of this library (nnc_kernel_launches). Launches
+// made while `s` is being captured into a graph are counted when the graph is
+// replayed instead (note_graph_launches).
+void note_launch(cudaStream_t s);
+void note_graph_launches(long long kernels);
+
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------

@@ -37,11 +37,12 @@ template <typename T>
 cudaError_t launch_elementwise_mu(T* theta, const T* num, const T* den, int64_t n, double eps,
                                   cudaStream_t s);
 
-// trace_out[0] = sqrt(max(x2 - 2 <M, G> + <G, Dn>, 0) / x2), FP64 sums over
-// n core entries (one block).
+// trace[(*counter) * stride] = sqrt(max(x2 - 2 <M, G> + <G, Dn>, 0) / x2), FP64
+// sums over n core entries (one block); then *counter += 1.
 template <typename T>
 cudaError_t launch_residual_identity(const T* M, const T* G, const T* Dn, int64_t n,
-                                     const double* x2, double* trace_out, cudaStream_t s);
+                                     const double* x2, double* trace, int stride, int* counter,
+                                     cudaStream_t s);
 
 // One pass over X: sum of squares (FP64) and counts of negative and
 // non-finite entries. part holds >= 3 * kStatBlocks doubles, out 3 doubles:

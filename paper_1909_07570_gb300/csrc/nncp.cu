@@ -210,6 +210,7 @@ cudaError_t launch_nncp(const nncp_job* jobs_dev, int n_jobs, size_t smem, int i
     if (e != cudaSuccess) return e;
   }
   nncp_kernel<T><<<n_jobs, kThreads, smem, s>>>(jobs_dev, iters, (T)eps, rel_errs);
+  note_launch(s);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,44 @@
+// CUDA-event timing of the two passes over X of every nnTD sweep (the
+// dominant kernels), for nnc_profile_enable / nnc_profile_read.
+//
+// The sweep is a CUDA graph replayed once per sweep. While profiling is on,
+// the captured sweep holds an external event-record node before and after
+// each pass; before every replay the nodes are pointed at fresh events from a
+// per-device pool, and after the loop every (start, stop) pair is read with
+// cudaEventElapsedTime and added to the totals of its kind.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace nnc {
+
+constexpr int kProfileKinds = 4;
+
+struct PassEvents {
+  cudaEvent_t start[2];
+  cudaEvent_t stop[2];
+};
+
+bool profile_enabled();
+
+class PassProfiler {
+ public:
+  // kind_base: 0 for the SIMT passes (kinds 0, 1), 2 for the tensor-core
+  // passes (kinds 2, 3).
+  explicit PassProfiler(int kind_base = 0) : kind_base_(kind_base) {}
+  int init(int launches);                        // reserve 4 events per launch
+  const PassEvents* capture_events() const { return &cap_; }
+  int bind(cudaGraph_t graph);                   // find the 4 event-record nodes
+  int set_launch(cudaGraphExec_t exec, int t);   // point them at launch t's events
+  int collect(int launches);                     // add elapsed times to the totals
+
+ private:
+  int kind_base_;
+  std::vector<cudaEvent_t> ev_;
+  PassEvents cap_{};
+  cudaGraphNode_t node_[4] = {};
+};
+
+}  // namespace nnc

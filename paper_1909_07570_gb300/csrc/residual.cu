@@ -123,6 +123,7 @@ unsigned grid_cap(int64_t n, int threads) {
 template <typename T>
 cudaError_t launch_lift(const T* F, const T* B, int64_t N, int M, int r, T* A, cudaStream_t s) {
   lift_kernel<T><<<grid_cap(N * r, 256), 256, 0, s>>>(F, B, N, M, r, A);
+  note_launch(s);
   return cudaGetLastError();
 }
 
@@ -140,11 +141,14 @@ int residual3_device(const T* X, const int64_t* dims, int model, const int* m, i
     // T1[i, b, c] = sum_a F1[i, a] G[a, b, c];  U[i, j, c] = sum_b F2[j, b] T1[i, b, c]
     mode_product_any_kernel<T><<<grid_cap(N1 * m[1] * m[2], 256), 256, 0, s>>>(
         G, 1, m[0], (int64_t)m[1] * m[2], factors[0], (int)N1, T1);
+    note_launch(s);
     mode_product_any_kernel<T><<<grid_cap(N1 * N2 * m[2], 256), 256, 0, s>>>(
         T1, N1, m[1], m[2], factors[1], (int)N2, U);
+    note_launch(s);
   } else {
     cp_rows_kernel<T><<<grid_cap(N1 * N2 * r, 256), 256, 0, s>>>(factors[0], factors[1], N1, N2,
                                                                    r, U);
+    note_launch(s);
   }
   NNC_CUDA_TRY(cudaGetLastError());
   const T* F3 = factors[2];  // F^(3) (Tucker) or A^(3) (CP): N3 x K
@@ -158,7 +162,9 @@ int residual3_device(const T* X, const int64_t* dims, int model, const int* m, i
     NNC_CUDA_TRY(cudaFuncSetAttribute(residual_stream_kernel<T>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   residual_stream_kernel<T><<<grid, kResThreads, smem, s>>>(X, R, N3, U, K, F3, part);
+  note_launch(s);
   residual_final_kernel<<<1, 1024, 0, s>>>(part, nblocks, out2);
+  note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
   return NNC_OK;
 }

@@ -71,7 +71,8 @@ __global__ void elementwise_mu_kernel(T* __restrict__ th, const T* __restrict__ 
 template <typename T>
 __global__ void residual_identity_kernel(const T* __restrict__ M, const T* __restrict__ G,
                                          const T* __restrict__ Dn, int64_t n,
-                                         const double* __restrict__ x2, double* out) {
+                                         const double* __restrict__ x2, double* trace,
+                                         int stride, int* counter) {
   __shared__ double sh[32];
   double mg = 0.0, gd = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -85,7 +86,9 @@ __global__ void residual_identity_kernel(const T* __restrict__ M, const T* __res
     const double xx = *x2;
     double r2 = xx - 2.0 * mg + gd;
     if (r2 < 0.0) r2 = 0.0;
-    out[0] = sqrt(r2 / xx);
+    const int t = *counter;
+    trace[(int64_t)t * stride] = sqrt(r2 / xx);
+    *counter = t + 1;
   }
 }
 
@@ -152,6 +155,7 @@ cudaError_t launch_pair_contract(const T* Y, const T* G, int64_t L, int NI, int 
     if (e != cudaSuccess) return e;
   }
   pair_contract_kernel<T><<<NI, 256, smem, s>>>(Y, G, L, NI, MA, C, out);
+  note_launch(s);
   return cudaGetLastError();
 }
 
@@ -164,6 +168,7 @@ cudaError_t launch_factor_mu(T* F, const T* Num, const T* H, int64_t N, int M, d
   const size_t smem = ((size_t)M * M + (size_t)rows * M) * sizeof(T);
   factor_mu_kernel<T><<<(unsigned)ceil_div(N, rows), threads, smem, s>>>(F, Num, H, N, M, MP,
                                                                           (T)eps);
+  note_launch(s);
   return cudaGetLastError();
 }
 
@@ -171,13 +176,16 @@ template <typename T>
 cudaError_t launch_elementwise_mu(T* theta, const T* num, const T* den, int64_t n, double eps,
                                   cudaStream_t s) {
   elementwise_mu_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(theta, num, den, n, (T)eps);
+  note_launch(s);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_residual_identity(const T* M, const T* G, const T* Dn, int64_t n,
-                                     const double* x2, double* trace_out, cudaStream_t s) {
-  residual_identity_kernel<T><<<1, 1024, 0, s>>>(M, G, Dn, n, x2, trace_out);
+                                     const double* x2, double* trace, int stride, int* counter,
+                                     cudaStream_t s) {
+  residual_identity_kernel<T><<<1, 1024, 0, s>>>(M, G, Dn, n, x2, trace, stride, counter);
+  note_launch(s);
   return cudaGetLastError();
 }
 
@@ -185,13 +193,16 @@ template <typename T>
 cudaError_t launch_tensor_stats(const T* X, int64_t n, double* part, double* out, cudaStream_t s) {
   const unsigned blocks = grid_for(n, 256, kStatBlocks);
   tensor_stats_kernel<T><<<blocks, 256, 0, s>>>(X, n, part);
+  note_launch(s);
   tensor_stats_final_kernel<<<1, 256, 0, s>>>(part, (int)blocks, out);
+  note_launch(s);
   return cudaGetLastError();
 }
 
 template <typename T, typename U>
 cudaError_t launch_convert(const T* src, U* dst, int64_t n, cudaStream_t s) {
   convert_kernel<T, U><<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+  note_launch(s);
   return cudaGetLastError();
 }
 
@@ -203,7 +214,8 @@ cudaError_t launch_convert(const T* src, U* dst, int64_t n, cudaStream_t s) {
   template cudaError_t launch_elementwise_mu<T>(T*, const T*, const T*, int64_t, double,       \
                                                 cudaStream_t);                                 \
   template cudaError_t launch_residual_identity<T>(const T*, const T*, const T*, int64_t,      \
-                                                   const double*, double*, cudaStream_t);      \
+                                                   const double*, double*, int, int*,          \
+                                                   cudaStream_t);                              \
   template cudaError_t launch_tensor_stats<T>(const T*, int64_t, double*, double*, cudaStream_t);
 NNC_INST(float)
 NNC_INST(double)

@@ -199,6 +199,7 @@ cudaError_t ttm_dispatch(const T* Y, int64_t L, int J, int64_t C, const T* Fm, i
     T* dst = splits > 1 ? split_buf : out;
     dim3 grid((unsigned)blocks, (unsigned)splits);
     ttm_rows_kernel<T, QP, TR><<<grid, kRowsThreads, 0, s>>>(Y, L, J, per, Fm, fs_j, fs_q, Q, dst);
+    note_launch(s);
   } else {
     const int64_t ncols = L * C;
     const bool wide = (QP <= 32) && ceil_div(ncols, 2 * kColsThreads) >= 2LL * device_sm_count();
@@ -208,18 +209,21 @@ cudaError_t ttm_dispatch(const T* Y, int64_t L, int J, int64_t C, const T* Fm, i
       T* dst = splits > 1 ? split_buf : out;
       dim3 grid((unsigned)blocks, (unsigned)splits);
       ttm_cols_kernel<T, QP, 2><<<grid, kColsThreads, 0, s>>>(Y, L, J, C, per, Fm, fs_j, fs_q, Q, dst);
+      note_launch(s);
     } else {
       const int64_t blocks = ceil_div(ncols, kColsThreads);
       splits = choose_splits(blocks, J, out_elems, split_cap, kColsBJ, &per);
       T* dst = splits > 1 ? split_buf : out;
       dim3 grid((unsigned)blocks, (unsigned)splits);
       ttm_cols_kernel<T, QP, 1><<<grid, kColsThreads, 0, s>>>(Y, L, J, C, per, Fm, fs_j, fs_q, Q, dst);
+      note_launch(s);
     }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   const int64_t blocks = ceil_div(out_elems, 256) < 4096 ? ceil_div(out_elems, 256) : 4096;
   reduce_splits_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(split_buf, splits, out_elems, out);
+  note_launch(s);
   return cudaGetLastError();
 }
 

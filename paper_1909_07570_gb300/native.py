@@ -23,7 +23,8 @@ _STATUS = {
 
 # Every symbol include/nncandelinc.h declares.
 EXPORTED = ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched", "candelinc_lift",
-            "recon_residual", "nnc_status_string", "nnc_last_error_detail")
+            "recon_residual", "nnc_status_string", "nnc_last_error_detail",
+            "nnc_profile_enable", "nnc_profile_read", "nnc_kernel_launches")
 
 
 class NncError(RuntimeError):
@@ -74,6 +75,13 @@ def load(path: str | None = None):
     lib.nnc_status_string.restype = ctypes.c_char_p
     lib.nnc_last_error_detail.argtypes = []
     lib.nnc_last_error_detail.restype = ctypes.c_char_p
+    lib.nnc_profile_enable.argtypes = [ctypes.c_int]
+    lib.nnc_profile_enable.restype = ctypes.c_int
+    lib.nnc_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(ctypes.c_double)]
+    lib.nnc_profile_read.restype = ctypes.c_int
+    lib.nnc_kernel_launches.argtypes = []
+    lib.nnc_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
     return lib
 
@@ -220,3 +228,23 @@ def recon_residual(X, factors, G=None, stream=None):
                                ctypes.byref(rn), ctypes.byref(xn), _stream(stream))
     _check("recon_residual", st)
     return rn.value, xn.value
+
+
+PASS_KINDS = {0: "simt_x3", 1: "simt_x1", 2: "tc_x3", 3: "tc_x1"}
+
+
+def nnc_profile_enable(on=True):
+    """Switch event timing of the passes over X on or off (clears the totals)."""
+    _check("nnc_profile_enable", load().nnc_profile_enable(1 if on else 0))
+
+
+def nnc_profile_read(kind):
+    """(timed launches, total ms) of one pass kind (see PASS_KINDS)."""
+    n, ms = ctypes.c_longlong(), ctypes.c_double()
+    _check("nnc_profile_read", load().nnc_profile_read(int(kind), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+def nnc_kernel_launches():
+    """Kernels this library has launched in this process so far."""
+    return int(load().nnc_kernel_launches())
