@@ -132,6 +132,35 @@ int nncp_core_fit_batched(int n_jobs, const nncp_job* jobs, int precision, const
                           double* rel_errs, void* stream);
 
 /*
+ * nncp_core_fit_batched_noalloc - nncp_core_fit_batched for callers that must
+ * not allocate device memory. The paper has no counterpart: this is a service
+ * of the library, not a step of the method.
+ *
+ * Who needs it: a host runtime that owns all device memory through its own
+ * pool and forbids a library to allocate behind its back; a latency-critical
+ * loop where an allocation may stall, or fail when the GPU's memory is nearly
+ * all handed out. The allocating call takes its job table from cudaMallocAsync;
+ * this one keeps the table in a fixed array inside the library's device memory
+ * (4096 descriptors, 256 KiB, held on every GPU that loads the library until
+ * the process exits) and calls no allocator at all.
+ *
+ * Same kernel, arguments, results and errors as nncp_core_fit_batched, except:
+ *  - n_jobs > 4096 is rejected with NNC_ERR_INVALID_ARG (nnc_last_error_detail
+ *    says so);
+ *  - the first call on a device looks up the table's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture;
+ *  - every call writes the one shared table: calls whose work may overlap on
+ *    the GPU (other streams, other threads) race and must be ordered by the
+ *    caller;
+ *  - the descriptors are copied with cudaMemcpyAsync on `stream`; from
+ *    pageable host memory the copy is done when the call returns, from
+ *    page-locked memory keep `jobs` unchanged until `stream` has reached it.
+ */
+int nncp_core_fit_batched_noalloc(int n_jobs, const nncp_job* jobs, int precision,
+                                  const nnc_opts* opts, double* rel_errs, void* stream);
+
+/*
  * candelinc_lift - A^(n) = F^(n) B^(n) for every mode: the CPD of the core
  * substituted into the Tucker model (proof of Lemma "rank and min exists",
  * Sec. 2.1), giving the CP factors of the nnCANDELINC model.

@@ -22,7 +22,8 @@ _STATUS = {
 }
 
 # Every symbol include/nncandelinc.h declares.
-EXPORTED = ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched", "candelinc_lift",
+EXPORTED = ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched",
+            "nncp_core_fit_batched_noalloc", "candelinc_lift",
             "recon_residual", "nnc_status_string", "nnc_last_error_detail",
             "nnc_profile_enable", "nnc_profile_read", "nnc_kernel_launches")
 
@@ -68,8 +69,9 @@ def load(path: str | None = None):
                                    vpp, vp]
     lib.recon_residual.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, ip,
                                    ctypes.c_int, vpp, vp, dp, dp, vp]
-    for fn in ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched", "candelinc_lift",
-               "recon_residual"):
+    lib.nncp_core_fit_batched_noalloc.argtypes = lib.nncp_core_fit_batched.argtypes
+    for fn in ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched",
+               "nncp_core_fit_batched_noalloc", "candelinc_lift", "recon_residual"):
         getattr(lib, fn).restype = ctypes.c_int
     lib.nnc_status_string.argtypes = [ctypes.c_int]
     lib.nnc_status_string.restype = ctypes.c_char_p
@@ -167,7 +169,8 @@ def nncp_core_fit(G, B, iters, precision=None, eps=1e-12, rel_err=True, stream=N
     return err.value if rel_err else None
 
 
-def nncp_core_fit_batched(problems, iters, precision=None, eps=1e-12, stream=None):
+def nncp_core_fit_batched(problems, iters, precision=None, eps=1e-12, stream=None,
+                          _entry="nncp_core_fit_batched"):
     """Many core fits in one launch. ``problems`` is a list of (G, [B^(n)]);
     every B is updated in place. Returns a float64 CUDA tensor of the final
     relative errors."""
@@ -188,10 +191,19 @@ def nncp_core_fit_batched(problems, iters, precision=None, eps=1e-12, stream=Non
             j.B[n] = B[n].data_ptr()
     errs = torch.empty(len(problems), dtype=torch.float64, device=G0.device)
     opts = nnc_opts(int(iters), 0, float(eps))
-    st = load().nncp_core_fit_batched(len(problems), jobs, code, ctypes.byref(opts), _ptr(errs),
-                                      _stream(stream))
-    _check("nncp_core_fit_batched", st)
+    st = getattr(load(), _entry)(len(problems), jobs, code, ctypes.byref(opts), _ptr(errs),
+                                 _stream(stream))
+    _check(_entry, st)
     return errs
+
+
+def nncp_core_fit_batched_noalloc(problems, iters, precision=None, eps=1e-12, stream=None):
+    """As nncp_core_fit_batched, through the entry point that allocates no
+    device memory (its job table is a fixed array of 4096 descriptors inside the
+    library). For callers whose memory manager forbids allocations by a
+    library."""
+    return nncp_core_fit_batched(problems, iters, precision, eps, stream,
+                                 _entry="nncp_core_fit_batched_noalloc")
 
 
 def candelinc_lift(F, B, out=None, stream=None):
