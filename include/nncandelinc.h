@@ -43,6 +43,7 @@ extern "C" {
 #define NNC_ERR_CUDA (-4)           /* a CUDA runtime call failed              */
 #define NNC_ERR_ALLOC (-5)          /* scratch allocation failed               */
 #define NNC_ERR_UNSUPPORTED (-6)    /* valid request this build does not serve */
+#define NNC_ERR_TIMEOUT (-7)        /* a bounded device-side wait ran out      */
 
 typedef enum {
   NNC_FP64 = 0,        /* double storage and arithmetic                      */
@@ -159,6 +160,26 @@ int nncp_core_fit_batched(int n_jobs, const nncp_job* jobs, int precision, const
  */
 int nncp_core_fit_batched_noalloc(int n_jobs, const nncp_job* jobs, int precision,
                                   const nnc_opts* opts, double* rel_errs, void* stream);
+
+/*
+ * nnc_mode_product - the n-mode product of Appendix A (Def. of n-mode
+ * multiplication) with A = F^T, for a 3-way X:
+ *   Y[.., q, ..] = sum_l X[.., l, ..] F[l, q]     (mode `mode` of size Q in Y)
+ * These are the contractions of the two passes over X of every nnTD sweep
+ * (mode 2 = X x_3 F^(3)T, mode 0 = X x_1 F^(1)T), exposed on their own.
+ *
+ *  X          device, dims[0] x dims[1] x dims[2]
+ *  mode       0, 1 or 2 (index 0 is mode 1 of the paper)
+ *  F          device, dims[mode] x Q row-major; 1 <= Q <= 64
+ *  out        device, dims with dims[mode] replaced by Q, C order
+ *  precision  NNC_FP64 (double) or NNC_FP32 (float): SIMT kernels.
+ *             NNC_BF16_REFINE (float X, F, out): tensor cores on BF16 copies
+ *             of X and F (X scaled per mode-1 slice by a power of two, which
+ *             changes no rounding) with FP32 accumulation; modes 0 and 2 only.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA, ALLOC, TIMEOUT.
+ */
+int nnc_mode_product(const void* X, int d, const int64_t* dims, int mode, const void* F, int Q,
+                     int precision, void* out, void* stream);
 
 /*
  * candelinc_lift - A^(n) = F^(n) B^(n) for every mode: the CPD of the core

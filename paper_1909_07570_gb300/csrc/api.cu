@@ -10,6 +10,7 @@
 #include "nncp.cuh"
 #include "ntd.cuh"
 #include "residual.cuh"
+#include "tc_ttm.cuh"
 
 namespace nnc {
 
@@ -112,6 +113,7 @@ const char* nnc_status_string(int status) {
     case NNC_ERR_CUDA: return "CUDA error";
     case NNC_ERR_ALLOC: return "scratch allocation failed";
     case NNC_ERR_UNSUPPORTED: return "unsupported by this build";
+    case NNC_ERR_TIMEOUT: return "device-side wait timed out";
     default: return "unknown status";
   }
 }
@@ -193,6 +195,48 @@ int nncp_core_fit_batched(int n_jobs, const nncp_job* jobs, int precision, const
   if (precision == NNC_FP32 || precision == NNC_BF16_REFINE)
     return nncp_run<float>(n_jobs, jobs, opts, rel_errs, s);
   return NNC_ERR_INVALID_ARG;
+}
+
+int nnc_mode_product(const void* X, int d, const int64_t* dims, int mode, const void* F, int Q,
+                     int precision, void* out, void* stream) {
+  g_detail.clear();
+  if (X == nullptr || F == nullptr || out == nullptr || dims == nullptr) return NNC_ERR_INVALID_ARG;
+  if (d != 3 || mode < 0 || mode > 2 || Q < 1 || Q > 64) return NNC_ERR_INVALID_ARG;
+  for (int n = 0; n < 3; ++n)
+    if (dims[n] < 1 || dims[n] > (1LL << 31) - 1) return NNC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t L = 1, C = 1;
+  for (int n = 0; n < mode; ++n) L *= dims[n];
+  for (int n = mode + 1; n < 3; ++n) C *= dims[n];
+  const int J = static_cast<int>(dims[mode]);
+  Scratch sc(s);
+  if (precision == NNC_BF16_REFINE) {
+    if (mode == 1) return NNC_ERR_UNSUPPORTED;
+    tc::TcPlan plan;
+    NNC_TRY(plan.init(static_cast<const float*>(X), dims[0], dims[1], dims[2], Q, Q, sc, s));
+    if (mode == 2)
+      NNC_TRY(plan.pass3(static_cast<const float*>(F), static_cast<float*>(out), s));
+    else
+      NNC_TRY(plan.pass1(static_cast<const float*>(F), static_cast<float*>(out), s));
+    return plan.check(s);
+  }
+  const size_t cap = static_cast<size_t>(L * Q * C) * 8;
+  if (precision == NNC_FP64) {
+    double* split = nullptr;
+    NNC_TRY(sc.get(&split, cap));
+    NNC_CUDA_TRY(launch_ttm<double>(static_cast<const double*>(X), L, J, C,
+                                    static_cast<const double*>(F), Q, 1, Q,
+                                    static_cast<double*>(out), split, cap, s));
+  } else if (precision == NNC_FP32) {
+    float* split = nullptr;
+    NNC_TRY(sc.get(&split, cap));
+    NNC_CUDA_TRY(launch_ttm<float>(static_cast<const float*>(X), L, J, C,
+                                   static_cast<const float*>(F), Q, 1, Q, static_cast<float*>(out),
+                                   split, cap, s));
+  } else {
+    return NNC_ERR_INVALID_ARG;
+  }
+  return NNC_OK;
 }
 
 int candelinc_lift(int d, const int64_t* dims, const int* m, int r, int precision,

@@ -20,12 +20,19 @@
 //
 // The sweep is captured once as a CUDA graph on a private stream and replayed
 // `iters` times; the trace slot advances through a device counter.
+//
+// NNC_BF16_REFINE: the two passes over X run on the tensor cores from a BF16
+// copy of X (tc_ttm.cu) for the first iters - refine_iters sweeps; the last
+// refine_iters sweeps replay the FP32 graph on X itself. Everything but the two
+// passes is FP32 in both.
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
 #include "ntd.cuh"
 #include "profile.cuh"
 #include "residual.cuh"
+#include "tc_ttm.cuh"
 
 namespace nnc {
 
@@ -40,8 +47,29 @@ struct NtdBuffers {
 };
 
 template <typename T>
+int pass_x3(const T* X, int64_t N1, int64_t N2, int64_t N3, int m3, const T* F3, T* P3,
+            NtdBuffers<T>& b, const tc::TcPlan* tcp, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (tcp) return tcp->pass3(F3, P3, s);
+  }
+  NNC_CUDA_TRY(launch_ttm<T>(X, N1 * N2, (int)N3, 1, F3, m3, 1, m3, P3, b.split, b.split_cap, s));
+  return NNC_OK;
+}
+
+template <typename T>
+int pass_x1(const T* X, int64_t N1, int64_t N2, int64_t N3, int m1, const T* F1, T* P1,
+            NtdBuffers<T>& b, const tc::TcPlan* tcp, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (tcp) return tcp->pass1(F1, P1, s);
+  }
+  NNC_CUDA_TRY(launch_ttm<T>(X, 1, (int)N1, N2 * N3, F1, m1, 1, m1, P1, b.split, b.split_cap, s));
+  return NNC_OK;
+}
+
+template <typename T>
 int sweep3(const T* X, const int64_t* N, const int* m, T* const* F, T* G, NtdBuffers<T>& b,
-           double eps, double* trace, int trace_stride, const PassEvents* ev, cudaStream_t s) {
+           double eps, double* trace, int trace_stride, const PassEvents* ev,
+           const tc::TcPlan* tcp, cudaStream_t s) {
   const int64_t N1 = N[0], N2 = N[1], N3 = N[2];
   const int m1 = m[0], m2 = m[1], m3 = m[2];
   const int64_t nc = (int64_t)m1 * m2 * m3;
@@ -51,7 +79,7 @@ int sweep3(const T* X, const int64_t* N, const int* m, T* const* F, T* G, NtdBuf
   // ---- mode 1 ------------------------------------------------------------
   // P3[i, j, c] = sum_k X[i, j, k] F3[k, c]
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->start[0], s, cudaEventRecordExternal));
-  NNC_CUDA_TRY(launch_ttm<T>(X, N1 * N2, (int)N3, 1, F[2], m3, 1, m3, b.P3, sp, cap, s));
+  NNC_TRY(pass_x3<T>(X, N1, N2, N3, m3, F[2], b.P3, b, tcp, s));
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->stop[0], s, cudaEventRecordExternal));
   // Y1[i, b, c] = sum_j F2[j, b] P3[i, j, c]
   NNC_CUDA_TRY(launch_ttm<T>(b.P3, N1, (int)N2, m3, F[1], m2, 1, m2, b.Y1, sp, cap, s));
@@ -77,7 +105,7 @@ int sweep3(const T* X, const int64_t* N, const int* m, T* const* F, T* G, NtdBuf
   // ---- mode 3 ------------------------------------------------------------
   // P1[a, j, k] = sum_i F1[i, a] X[i, j, k]
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->start[1], s, cudaEventRecordExternal));
-  NNC_CUDA_TRY(launch_ttm<T>(X, 1, (int)N1, N2 * N3, F[0], m1, 1, m1, b.P1, sp, cap, s));
+  NNC_TRY(pass_x1<T>(X, N1, N2, N3, m1, F[0], b.P1, b, tcp, s));
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->stop[1], s, cudaEventRecordExternal));
   // Y3[a, b, k] = sum_j F2[j, b] P1[a, j, k]
   NNC_CUDA_TRY(launch_ttm<T>(b.P1, m1, (int)N2, N3, F[1], m2, 1, m2, b.Y3, sp, cap, s));
@@ -135,11 +163,51 @@ struct GraphRun {
   }
 };
 
-}  // namespace
+// Captures one sweep on a private stream and replays it `count` times after
+// the work already queued on `s`; `s` then waits for the replays.
+template <typename T>
+int run_sweeps(const T* X, const int64_t* dims, const int* m, T* const* F, T* G,
+               NtdBuffers<T>& b, double eps, double* trace, int count, const tc::TcPlan* tcp,
+               cudaStream_t s) {
+  if (count <= 0) return NNC_OK;
+  GraphRun g;
+  NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
+  NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming));
+  NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming));
+  NNC_CUDA_TRY(cudaEventRecord(g.fork, s));
+  NNC_CUDA_TRY(cudaStreamWaitEvent(g.cs, g.fork, 0));
+
+  PassProfiler prof(tcp ? 2 : 0);
+  const PassEvents* capture_ev = nullptr;
+  if (profile_enabled()) {
+    NNC_TRY(prof.init(count));
+    capture_ev = prof.capture_events();
+  }
+  NNC_CUDA_TRY(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
+  const int cap_st = sweep3<T>(X, dims, m, F, G, b, eps, trace ? trace : b.trace_dummy,
+                               trace ? 1 : 0, capture_ev, tcp, g.cs);
+  const cudaError_t end_e = cudaStreamEndCapture(g.cs, &g.graph);
+  if (cap_st != NNC_OK) return cap_st;
+  NNC_CUDA_TRY(end_e);
+  NNC_CUDA_TRY(cudaGraphInstantiate(&g.exec, g.graph, 0));
+  long long kernel_nodes = 0;
+  NNC_TRY(count_kernel_nodes(g.graph, &kernel_nodes));
+  if (capture_ev) NNC_TRY(prof.bind(g.graph));
+  for (int t = 0; t < count; ++t) {
+    if (capture_ev) NNC_TRY(prof.set_launch(g.exec, t));
+    NNC_CUDA_TRY(cudaGraphLaunch(g.exec, g.cs));
+  }
+  note_graph_launches(kernel_nodes * count);
+  NNC_CUDA_TRY(cudaEventRecord(g.join, g.cs));
+  NNC_CUDA_TRY(cudaStreamWaitEvent(s, g.join, 0));
+  NNC_CUDA_TRY(cudaStreamSynchronize(g.cs));
+  if (capture_ev) NNC_TRY(prof.collect(count));
+  return NNC_OK;
+}
 
 template <typename T>
-int ntd_fit3(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T* const* F, T* G,
-             double* trace, double* rel_err, cudaStream_t s) {
+int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T* const* F,
+                  T* G, double* trace, double* rel_err, bool use_tc, cudaStream_t s) {
   const int64_t N1 = dims[0], N2 = dims[1], N3 = dims[2];
   const int m1 = m[0], m2 = m[1], m3 = m[2];
   const int64_t nX = N1 * N2 * N3;
@@ -182,6 +250,15 @@ int ntd_fit3(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T
   NNC_TRY(sc.get(&b.Num, (size_t)(Nmax * mmax)));
   NNC_TRY(sc.get(&b.split, b.split_cap));
 
+  tc::TcPlan plan;
+  const tc::TcPlan* tcp = nullptr;
+  if constexpr (std::is_same<T, float>::value) {
+    if (use_tc && o->iters > o->refine_iters) {
+      NNC_TRY(plan.init(X, N1, N2, N3, m1, m3, sc, s));
+      tcp = &plan;
+    }
+  }
+
   // Prologue: Grams, W1 = G x_2 S2 x_3 S3, trace counter.
   for (int k = 0; k < 3; ++k)
     NNC_CUDA_TRY(launch_ttm<T>(F[k], 1, (int)dims[k], m[k], F[k], m[k], 1, m[k], b.S[k], b.split,
@@ -191,40 +268,10 @@ int ntd_fit3(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T
                              b.split_cap, s));
   NNC_CUDA_TRY(cudaMemsetAsync(b.counter, 0, sizeof(int), s));
 
-  if (o->iters > 0) {
-    GraphRun g;
-    NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
-    NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming));
-    NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming));
-    NNC_CUDA_TRY(cudaEventRecord(g.fork, s));
-    NNC_CUDA_TRY(cudaStreamWaitEvent(g.cs, g.fork, 0));
-
-    PassProfiler prof;
-    const PassEvents* capture_ev = nullptr;
-    if (profile_enabled()) {
-      NNC_TRY(prof.init(o->iters));
-      capture_ev = prof.capture_events();
-    }
-    NNC_CUDA_TRY(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
-    const int cap_st = sweep3<T>(X, dims, m, F, G, b, o->eps, trace ? trace : b.trace_dummy,
-                                 trace ? 1 : 0, capture_ev, g.cs);
-    const cudaError_t end_e = cudaStreamEndCapture(g.cs, &g.graph);
-    if (cap_st != NNC_OK) return cap_st;
-    NNC_CUDA_TRY(end_e);
-    NNC_CUDA_TRY(cudaGraphInstantiate(&g.exec, g.graph, 0));
-    long long kernel_nodes = 0;
-    NNC_TRY(count_kernel_nodes(g.graph, &kernel_nodes));
-    if (capture_ev) NNC_TRY(prof.bind(g.graph));
-    for (int t = 0; t < o->iters; ++t) {
-      if (capture_ev) NNC_TRY(prof.set_launch(g.exec, t));
-      NNC_CUDA_TRY(cudaGraphLaunch(g.exec, g.cs));
-    }
-    note_graph_launches(kernel_nodes * o->iters);
-    NNC_CUDA_TRY(cudaEventRecord(g.join, g.cs));
-    NNC_CUDA_TRY(cudaStreamWaitEvent(s, g.join, 0));
-    NNC_CUDA_TRY(cudaStreamSynchronize(g.cs));
-    if (capture_ev) NNC_TRY(prof.collect(o->iters));
-  }
+  const int n_fast = tcp ? o->iters - o->refine_iters : 0;
+  NNC_TRY(run_sweeps<T>(X, dims, m, F, G, b, o->eps, trace, n_fast, tcp, s));
+  if (tcp) NNC_TRY(plan.check(s));
+  NNC_TRY(run_sweeps<T>(X, dims, m, F, G, b, o->eps, trace, o->iters - n_fast, nullptr, s));
 
   if (rel_err) {
     const T* fac[3] = {F[0], F[1], F[2]};
@@ -237,11 +284,17 @@ int ntd_fit3(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T
   return NNC_OK;
 }
 
+}  // namespace
+
+template <typename T>
+int ntd_fit3(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T* const* F, T* G,
+             double* trace, double* rel_err, cudaStream_t s) {
+  return ntd_fit3_impl<T>(X, dims, m, o, F, G, trace, rel_err, false, s);
+}
+
 int ntd_fit3_bf16(const float* X, const int64_t* dims, const int* m, const nnc_opts* o,
                   float* const* F, float* G, double* trace, double* rel_err, cudaStream_t s) {
-  (void)X; (void)dims; (void)m; (void)o; (void)F; (void)G; (void)trace; (void)rel_err; (void)s;
-  set_error_detail_text("NNC_BF16_REFINE: tensor-core path not built yet");
-  return NNC_ERR_UNSUPPORTED;
+  return ntd_fit3_impl<float>(X, dims, m, o, F, G, trace, rel_err, true, s);
 }
 
 template int ntd_fit3<float>(const float*, const int64_t*, const int*, const nnc_opts*,

@@ -18,12 +18,12 @@ NNC_FP64, NNC_FP32, NNC_BF16_REFINE = 0, 1, 2
 
 _STATUS = {
     0: "ok", -1: "invalid argument", -2: "negative input", -3: "non-finite value",
-    -4: "CUDA error", -5: "allocation failed", -6: "unsupported",
+    -4: "CUDA error", -5: "allocation failed", -6: "unsupported", -7: "device wait timed out",
 }
 
 # Every symbol include/nncandelinc.h declares.
 EXPORTED = ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched",
-            "nncp_core_fit_batched_noalloc", "candelinc_lift",
+            "nncp_core_fit_batched_noalloc", "nnc_mode_product", "candelinc_lift",
             "recon_residual", "nnc_status_string", "nnc_last_error_detail",
             "nnc_profile_enable", "nnc_profile_read", "nnc_kernel_launches")
 
@@ -70,8 +70,10 @@ def load(path: str | None = None):
     lib.recon_residual.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, ip,
                                    ctypes.c_int, vpp, vp, dp, dp, vp]
     lib.nncp_core_fit_batched_noalloc.argtypes = lib.nncp_core_fit_batched.argtypes
+    lib.nnc_mode_product.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_int, vp, ctypes.c_int,
+                                     ctypes.c_int, vp, vp]
     for fn in ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched",
-               "nncp_core_fit_batched_noalloc", "candelinc_lift", "recon_residual"):
+               "nncp_core_fit_batched_noalloc", "nnc_mode_product", "candelinc_lift", "recon_residual"):
         getattr(lib, fn).restype = ctypes.c_int
     lib.nnc_status_string.argtypes = [ctypes.c_int]
     lib.nnc_status_string.restype = ctypes.c_char_p
@@ -204,6 +206,21 @@ def nncp_core_fit_batched_noalloc(problems, iters, precision=None, eps=1e-12, st
     library."""
     return nncp_core_fit_batched(problems, iters, precision, eps, stream,
                                  _entry="nncp_core_fit_batched_noalloc")
+
+
+def mode_product(X, F, mode, precision=None, stream=None):
+    """Y = X x_mode F^T for a 3-way X (F is dims[mode] x Q); returns Y."""
+    code, dtype = _precision(X, precision)
+    _require(X, dtype, "X")
+    _require(F, dtype, "F")
+    Q = F.shape[1]
+    shape = list(X.shape)
+    shape[mode] = Q
+    out = torch.empty(shape, dtype=dtype, device=X.device)
+    st = load().nnc_mode_product(_ptr(X), X.dim(), _i64(X.shape), int(mode), _ptr(F), int(Q), code,
+                                 _ptr(out), _stream(stream))
+    _check("nnc_mode_product", st)
+    return out
 
 
 def candelinc_lift(F, B, out=None, stream=None):

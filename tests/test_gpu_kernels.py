@@ -1,0 +1,95 @@
+"""Parity of the mode-product kernels (the passes over X) with the oracle's
+n-mode product, and of the BF16 + FP32-refinement nnTD path with the oracle.
+
+SIMT kernels: FP64 to 1e-12 and FP32 to 1e-5 (relative to the largest entry).
+Tensor-core kernels: X and F are rounded to BF16 on the host (round to nearest
+even, as the device does) and the oracle multiplies the rounded values in FP64;
+the device accumulates the same products in FP32, so the bound is the FP32
+accumulation error, 1e-5 relative to the largest entry. The per-slice scales of
+the BF16 copy are powers of two, which change no rounding.
+BF16 path of ntd_fit: |rel_err - rel_err_oracle| <= 1e-3.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_1909_07570_gb300 import inputs, native
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16_round(a):
+    return torch.tensor(a, dtype=torch.float32).bfloat16().double().numpy()
+
+
+def _close(got, ref, rtol):
+    scale = np.abs(ref).max()
+    err = np.abs(got - ref).max()
+    assert err <= rtol * scale, f"max err {err:.3e} vs scale {scale:.3e}"
+
+
+@pytest.mark.parametrize("dims", [(37, 29, 23), (70, 45, 133), (5, 300, 2)])
+@pytest.mark.parametrize("Q", [1, 7, 20, 64])
+def test_mode_product_simt(dims, Q):
+    rng = np.random.default_rng(sum(dims) + Q)
+    X = rng.random(dims)
+    for mode in range(3):
+        F = rng.random((dims[mode], Q))
+        ref = orc.mode_product(X, F.T, mode)
+        for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+            Y = native.mode_product(torch.tensor(X, dtype=dt, device="cuda"),
+                                    torch.tensor(F, dtype=dt, device="cuda"), mode)
+            _close(Y.double().cpu().numpy(), ref, tol)
+
+
+@pytest.mark.parametrize("dims,Q", [((37, 29, 23), 5), ((200, 150, 130), 20), ((256, 256, 256), 32),
+                                    ((70, 45, 600), 64), ((129, 3, 64), 17)])
+def test_mode_product_tensor_cores(dims, Q):
+    rng = np.random.default_rng(11 + Q)
+    # Slices of very different magnitude exercise the per-slice scales.
+    X = rng.random(dims) * np.exp2(rng.integers(-6, 7, size=(dims[0], 1, 1)))
+    Xb = _bf16_round(X)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    for mode in (0, 2):
+        F = rng.random((dims[mode], Q))
+        ref = orc.mode_product(Xb, _bf16_round(F).T, mode)
+        Y = native.mode_product(Xd, torch.tensor(F, dtype=torch.float32, device="cuda"), mode,
+                                precision="bf16")
+        _close(Y.double().cpu().numpy(), ref, 1e-5)
+
+
+def test_mode_product_tensor_cores_rejects_middle_mode():
+    X = torch.rand(8, 8, 8, device="cuda")
+    F = torch.rand(8, 4, device="cuda")
+    with pytest.raises(native.NncError) as ei:
+        native.mode_product(X, F, 1, precision="bf16")
+    assert ei.value.status == -6
+
+
+@pytest.mark.parametrize("dims,m,iters,refine", [((96, 80, 128), (8, 10, 12), 60, 10),
+                                                 ((150, 64, 200), (16, 12, 20), 40, 0)])
+def test_ntd_bf16_refine_parity(dims, m, iters, refine):
+    X, _, F0, G0, _ = inputs.small_problem(dims, 6, m, 4, seed=606, dist="exponential")
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    F = [torch.tensor(f, dtype=torch.float32, device="cuda") for f in F0]
+    G = torch.tensor(G0, dtype=torch.float32, device="cuda")
+    err, tr = native.ntd_fit(Xd, F, G, iters, precision="bf16", refine_iters=refine)
+    Fo, Go, tro = orc.ntd_fit(X, F0, G0, iters)
+    tr = tr.cpu().numpy()
+    assert np.max(np.abs(tr - tro)) <= 1e-3
+    assert abs(err - orc.rel_err_tucker(X, Go, Fo)) <= 1e-3
+    assert all((f >= 0).all() for f in F) and (G >= 0).all()
+
+
+def test_ntd_bf16_full_size_cp16_512cube():
+    # The 512^3 precision workload at full size in the benchmark's launch
+    # configuration; the oracle runs its first 4 sweeps.
+    w = inputs.WORKLOADS["cp16_512x512x512_m32_bf16"]
+    X, _, F0, G0, _ = inputs.make_problem(w)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    F = [torch.tensor(f, dtype=torch.float32, device="cuda") for f in F0]
+    G = torch.tensor(G0, dtype=torch.float32, device="cuda")
+    _, tr = native.ntd_fit(Xd, F, G, 4, precision="bf16", refine_iters=0, rel_err=False)
+    _, _, tro = orc.ntd_fit(X, F0, G0, 4)
+    assert np.max(np.abs(tr.cpu().numpy() - tro)) <= 1e-3
