@@ -1,30 +1,27 @@
 // nnTD of a 3-way tensor (Alg. 1, step 1) on the GPU: the sweep loop.
 //
-// One sweep (Gauss-Seidel: F^(1), F^(2), F^(3), then G), with S_k = F^(k)T F^(k)
-// and the unfolding identity Eq. unfolding:property:
-//   P3 = X x_3 F^(3)T                       first pass over X
-//   Y1 = P3 x_2 F^(2)T        Num_1 = unfold_1(Y1) unfold_1(G)^T
-//   H1 = unfold_1(G x_2 S2 x_3 S3) unfold_1(G)^T,  Den_1 = F^(1) H1;  MU on F^(1)
-//   Y2 = P3 x_1 F^(1)T (new F^(1))          Num_2, H2 likewise;   MU on F^(2)
-//   P1 = X x_1 F^(1)T                       second pass over X (new F^(1))
-//   Y3 = P1 x_2 F^(2)T (new F^(2))          Num_3, H3;            MU on F^(3)
-//   M  = Y3 x_3 F^(3)T = X x_1 F^(1)T x_2 F^(2)T x_3 F^(3)T
-//   G <- max(G * M / max(G x_1 S1 x_2 S2 x_3 S3, eps), 0)
-//   trace = sqrt(||X||^2 - 2<M, G> + <G, G x_k S_k>) / ||X||   (FP64 sums)
-// X is read twice per sweep; every other array is at most N^2 m.
+// One sweep updates F^(1), F^(2), F^(3) and then G (Gauss-Seidel), each by the
+// multiplicative rule theta <- max(theta * Num / max(Den, eps), 0) whose
+// Den - Num is the gradient of 1/2 ||X - G x_k F^(k)||^2 (Eq. unfolding:property):
 //
-// Core-sized products are shared where the factors they use have not changed:
-// W3 = G x_1 S1 x_2 S2 serves H3 and, times S3, the core denominator; and
-// W1 = G_new x_2 S2 x_3 S3 serves the residual (times S1) and the next
-// sweep's H1.
+//   pass 1   P3 = X x_3 F3^T                          (first read of X)
+//   upd 1    Num1 = unfold_1(P3 x_2 F2^T) unfold_1(G)^T,  Den1 = F1 H1
+//   hmat 2   H2 = unfold_2(G x_1 S1 x_3 S3) unfold_2(G)^T
+//   upd 2    Num2 from P3 x_1 F1^T (new F1),  Den2 = F2 H2
+//   hmat 3   H3 from W3 = G x_1 S1 x_2 S2 (W3 kept)
+//   pass 2   P1 = X x_1 F1^T (new F1)                 (second read of X)
+//   y3, upd3 Y3 = P1 x_2 F2^T (new F2);  Num3 = unfold_3(Y3) unfold_3(G)^T;  Den3 = F3 H3
+//   core_m   M = Y3 x_3 F3^T = X x_1 F1^T x_2 F2^T x_3 F3^T
+//   core     G <- MU(G, M, W3 x_3 S3); trace; next H1       (one 8-CTA cluster)
+// with S_k = F_k^T F_k. The kernels are in sweep.cu; the passes are SIMT mode
+// products (ttm.cu) or, on the BF16 path, tensor-core mode products from a
+// BF16 copy of X (tc_ttm.cu). Two reads of X per sweep is the minimum under
+// the Gauss-Seidel order: pass 2 needs the F^(1) that pass 1 leads to.
 //
-// The sweep is captured once as a CUDA graph on a private stream and replayed
-// `iters` times; the trace slot advances through a device counter.
-//
-// NNC_BF16_REFINE: the two passes over X run on the tensor cores from a BF16
-// copy of X (tc_ttm.cu) for the first iters - refine_iters sweeps; the last
-// refine_iters sweeps replay the FP32 graph on X itself. Everything but the two
-// passes is FP32 in both.
+// The sweep is captured once as a CUDA graph on a private stream and replayed;
+// the trace slot advances through a device counter. NNC_BF16_REFINE replays
+// the tensor-core sweep for iters - refine_iters sweeps and then the FP32
+// sweep for the rest.
 #include <type_traits>
 #include <vector>
 
@@ -32,6 +29,7 @@
 #include "ntd.cuh"
 #include "profile.cuh"
 #include "residual.cuh"
+#include "sweep.cuh"
 #include "tc_ttm.cuh"
 
 namespace nnc {
@@ -39,97 +37,123 @@ namespace nnc {
 namespace {
 
 template <typename T>
-struct NtdBuffers {
-  T *P3, *P1, *Y1, *Y2, *Y3, *M, *W1, *W, *Wt, *D, *S[3], *H, *Num, *split;
-  size_t split_cap;
-  double *stats_part, *stats, *trace_dummy, *resid2;
+struct NtdState {
+  int64_t N[3];
+  int m[3];
+  T *P3, *P1, *Y3, *Mpart, *M, *W1, *W3, *H[3], *S[3], *num3part;
+  int rpb[2], n3splits, msplits;
+  double *stats_part, *stats, *trace_dummy, *resid2, *dots;
   int* counter;
 };
 
 template <typename T>
-int pass_x3(const T* X, int64_t N1, int64_t N2, int64_t N3, int m3, const T* F3, T* P3,
-            NtdBuffers<T>& b, const tc::TcPlan* tcp, cudaStream_t s) {
+int pass_x3(const T* X, const NtdState<T>& b, const T* F3, const tc::TcPlan* tcp,
+            cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
-    if (tcp) return tcp->pass3(F3, P3, s);
+    if (tcp) return tcp->pass3(F3, b.P3, s, /*convert=*/false);
   }
-  NNC_CUDA_TRY(launch_ttm<T>(X, N1 * N2, (int)N3, 1, F3, m3, 1, m3, P3, b.split, b.split_cap, s));
+  // No split buffer: the passes fill the GPU without splitting the contraction.
+  NNC_CUDA_TRY(launch_ttm<T>(X, b.N[0] * b.N[1], (int)b.N[2], 1, F3, b.m[2], 1, b.m[2], b.P3,
+                             nullptr, 0, s));
   return NNC_OK;
 }
 
 template <typename T>
-int pass_x1(const T* X, int64_t N1, int64_t N2, int64_t N3, int m1, const T* F1, T* P1,
-            NtdBuffers<T>& b, const tc::TcPlan* tcp, cudaStream_t s) {
+int pass_x1(const T* X, const NtdState<T>& b, const T* F1, const tc::TcPlan* tcp,
+            cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
-    if (tcp) return tcp->pass1(F1, P1, s);
+    if (tcp) return tcp->pass1(F1, b.P1, s, /*convert=*/false);
   }
-  NNC_CUDA_TRY(launch_ttm<T>(X, 1, (int)N1, N2 * N3, F1, m1, 1, m1, P1, b.split, b.split_cap, s));
+  NNC_CUDA_TRY(launch_ttm<T>(X, 1, (int)b.N[0], b.N[1] * b.N[2], F1, b.m[0], 1, b.m[0], b.P1,
+                             nullptr, 0, s));
   return NNC_OK;
 }
 
 template <typename T>
-int sweep3(const T* X, const int64_t* N, const int* m, T* const* F, T* G, NtdBuffers<T>& b,
-           double eps, double* trace, int trace_stride, const PassEvents* ev,
-           const tc::TcPlan* tcp, cudaStream_t s) {
-  const int64_t N1 = N[0], N2 = N[1], N3 = N[2];
-  const int m1 = m[0], m2 = m[1], m3 = m[2];
-  const int64_t nc = (int64_t)m1 * m2 * m3;
-  T* sp = b.split;
-  const size_t cap = b.split_cap;
+int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* trace,
+           int trace_stride, const PassEvents* ev, const tc::TcPlan* tcp, cudaStream_t s) {
+  const int64_t N1 = b.N[0], N2 = b.N[1], N3 = b.N[2];
+  const int m1 = b.m[0], m2 = b.m[1], m3 = b.m[2];
 
-  // ---- mode 1 ------------------------------------------------------------
-  // P3[i, j, c] = sum_k X[i, j, k] F3[k, c]
+  // ---- mode 1 ----------------------------------------------------------------
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->start[0], s, cudaEventRecordExternal));
-  NNC_TRY(pass_x3<T>(X, N1, N2, N3, m3, F[2], b.P3, b, tcp, s));
+  NNC_TRY(pass_x3<T>(X, b, F[2], tcp, s));
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->stop[0], s, cudaEventRecordExternal));
-  // Y1[i, b, c] = sum_j F2[j, b] P3[i, j, c]
-  NNC_CUDA_TRY(launch_ttm<T>(b.P3, N1, (int)N2, m3, F[1], m2, 1, m2, b.Y1, sp, cap, s));
-  // H1 = unfold_1(W1) unfold_1(G)^T with W1 = G x_2 S2 x_3 S3 (kept from the last sweep)
-  NNC_CUDA_TRY(launch_pair_contract<T>(b.W1, G, 1, m1, m1, (int64_t)m2 * m3, b.H, s));
-  // Num_1[i, a] = sum_{b,c} Y1[i, b, c] G[a, b, c]
-  NNC_CUDA_TRY(launch_pair_contract<T>(b.Y1, G, 1, (int)N1, m1, (int64_t)m2 * m3, b.Num, s));
-  NNC_CUDA_TRY(launch_factor_mu<T>(F[0], b.Num, b.H, N1, m1, eps, s));
-  NNC_CUDA_TRY(launch_ttm<T>(F[0], 1, (int)N1, m1, F[0], m1, 1, m1, b.S[0], sp, cap, s));
-
-  // ---- mode 2 ------------------------------------------------------------
-  // Y2[a, j, c] = sum_i F1[i, a] P3[i, j, c]
-  NNC_CUDA_TRY(launch_ttm<T>(b.P3, 1, (int)N1, N2 * m3, F[0], m1, 1, m1, b.Y2, sp, cap, s));
-  // W = G x_1 S1 x_3 S3;  H2 = unfold_2(W) unfold_2(G)^T
-  NNC_CUDA_TRY(launch_ttm<T>(G, 1, m1, (int64_t)m2 * m3, b.S[0], m1, 1, m1, b.Wt, sp, cap, s));
-  NNC_CUDA_TRY(launch_ttm<T>(b.Wt, (int64_t)m1 * m2, m3, 1, b.S[2], m3, 1, m3, b.W, sp, cap, s));
-  NNC_CUDA_TRY(launch_pair_contract<T>(b.W, G, m1, m2, m2, m3, b.H, s));
-  // Num_2[j, b] = sum_{a,c} Y2[a, j, c] G[a, b, c]
-  NNC_CUDA_TRY(launch_pair_contract<T>(b.Y2, G, m1, (int)N2, m2, m3, b.Num, s));
-  NNC_CUDA_TRY(launch_factor_mu<T>(F[1], b.Num, b.H, N2, m2, eps, s));
-  NNC_CUDA_TRY(launch_ttm<T>(F[1], 1, (int)N2, m2, F[1], m2, 1, m2, b.S[1], sp, cap, s));
-
-  // ---- mode 3 ------------------------------------------------------------
-  // P1[a, j, k] = sum_i F1[i, a] X[i, j, k]
+  {
+    UpdArgs<T> u{};
+    u.P = b.P3;  u.prow = N2 * m3;  u.pstride = m3;  // P3[i, j, c]
+    u.Fc = F[1]; u.len = (int)N2;   u.mu = m2;  u.mc = m3;
+    u.G = G;     u.gs_v = (int64_t)m2 * m3;  u.gs_u = m3;
+    u.F = F[0];  u.nrows = N1;  u.mv = m1;  u.H = b.H[0];  u.eps = eps;
+    u.rows_per_block = b.rpb[0];
+    if constexpr (std::is_same<T, float>::value) {
+      if (tcp) {
+        u.bt = tcp->Bt1;
+        u.bt_ld = tcp->kp1;
+        u.bt_scale = tcp->scale;
+      }
+    }
+    NNC_TRY(launch_upd12<T>(u, s));
+  }
+  {  // H2 from S1 = F1^T F1 (new F1) and S3
+    HArgs<T> h{};
+    h.G = G;  h.mp = m2;  h.mu = m1;  h.mv = m3;
+    h.sp = m3;  h.su_s = (int64_t)m2 * m3;  h.sv_s = 1;
+    h.fu = F[0];  h.nu = N1;  h.su_out = b.S[0];
+    h.sv = b.S[2];
+    h.H = b.H[1];
+    NNC_TRY(launch_hmat<T>(h, s));
+  }
+  // ---- mode 2 ----------------------------------------------------------------
+  {
+    UpdArgs<T> u{};
+    u.P = b.P3;  u.prow = m3;  u.pstride = N2 * m3;  // row j, contraction over i
+    u.Fc = F[0]; u.len = (int)N1;  u.mu = m1;  u.mc = m3;
+    u.G = G;     u.gs_v = m3;  u.gs_u = (int64_t)m2 * m3;
+    u.F = F[1];  u.nrows = N2;  u.mv = m2;  u.H = b.H[1];  u.eps = eps;
+    u.rows_per_block = b.rpb[1];
+    NNC_TRY(launch_upd12<T>(u, s));
+  }
+  {  // H3 and W3 = G x_1 S1 x_2 S2, with S2 = F2^T F2 (new F2)
+    HArgs<T> h{};
+    h.G = G;  h.mp = m3;  h.mu = m1;  h.mv = m2;
+    h.sp = 1;  h.su_s = (int64_t)m2 * m3;  h.sv_s = m3;
+    h.su = b.S[0];
+    h.fv = F[1];  h.nv = N2;  h.sv_out = b.S[1];
+    h.H = b.H[2];
+    h.Wout = b.W3;
+    NNC_TRY(launch_hmat<T>(h, s));
+  }
+  // ---- mode 3 ----------------------------------------------------------------
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->start[1], s, cudaEventRecordExternal));
-  NNC_TRY(pass_x1<T>(X, N1, N2, N3, m1, F[0], b.P1, b, tcp, s));
+  NNC_TRY(pass_x1<T>(X, b, F[0], tcp, s));
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->stop[1], s, cudaEventRecordExternal));
-  // Y3[a, b, k] = sum_j F2[j, b] P1[a, j, k]
-  NNC_CUDA_TRY(launch_ttm<T>(b.P1, m1, (int)N2, N3, F[1], m2, 1, m2, b.Y3, sp, cap, s));
-  // W3 = G x_1 S1 x_2 S2 (into W);  H3 = unfold_3(W3) unfold_3(G)^T
-  NNC_CUDA_TRY(launch_ttm<T>(G, 1, m1, (int64_t)m2 * m3, b.S[0], m1, 1, m1, b.Wt, sp, cap, s));
-  NNC_CUDA_TRY(launch_ttm<T>(b.Wt, m1, m2, m3, b.S[1], m2, 1, m2, b.W, sp, cap, s));
-  NNC_CUDA_TRY(launch_pair_contract<T>(b.W, G, (int64_t)m1 * m2, m3, m3, 1, b.H, s));
-  // Num_3[k, c] = sum_{a,b} Y3[a, b, k] G[a, b, c]
-  NNC_CUDA_TRY(launch_pair_contract<T>(b.Y3, G, (int64_t)m1 * m2, (int)N3, m3, 1, b.Num, s));
-  NNC_CUDA_TRY(launch_factor_mu<T>(F[2], b.Num, b.H, N3, m3, eps, s));
-  NNC_CUDA_TRY(launch_ttm<T>(F[2], 1, (int)N3, m3, F[2], m3, 1, m3, b.S[2], sp, cap, s));
-
-  // ---- core --------------------------------------------------------------
-  // M[a, b, c] = sum_k Y3[a, b, k] F3[k, c]
-  NNC_CUDA_TRY(launch_ttm<T>(b.Y3, (int64_t)m1 * m2, (int)N3, 1, F[2], m3, 1, m3, b.M, sp, cap, s));
-  // D = W3 x_3 S3 = G x_1 S1 x_2 S2 x_3 S3
-  NNC_CUDA_TRY(launch_ttm<T>(b.W, (int64_t)m1 * m2, m3, 1, b.S[2], m3, 1, m3, b.D, sp, cap, s));
-  NNC_CUDA_TRY(launch_elementwise_mu<T>(G, b.M, b.D, nc, eps, s));
-  // W1 = G x_2 S2 x_3 S3 with the new G (next sweep's H1); D = W1 x_1 S1
-  NNC_CUDA_TRY(launch_ttm<T>(G, m1, m2, m3, b.S[1], m2, 1, m2, b.Wt, sp, cap, s));
-  NNC_CUDA_TRY(launch_ttm<T>(b.Wt, (int64_t)m1 * m2, m3, 1, b.S[2], m3, 1, m3, b.W1, sp, cap, s));
-  NNC_CUDA_TRY(launch_ttm<T>(b.W1, 1, m1, (int64_t)m2 * m3, b.S[0], m1, 1, m1, b.D, sp, cap, s));
-  NNC_CUDA_TRY(launch_residual_identity<T>(b.M, G, b.D, nc, b.stats, trace, trace_stride,
-                                           b.counter, s));
+  NNC_TRY(launch_y3<T>(b.P1, F[1], m1, (int)N2, (int)N3, m2, b.Y3, s));
+  {
+    UpdArgs<T> u{};
+    u.P = b.Y3;  u.mu = m1 * m2;
+    u.G = G;
+    u.F = F[2];  u.nrows = N3;  u.mv = m3;  u.H = b.H[2];  u.eps = eps;
+    if constexpr (std::is_same<T, float>::value) {
+      if (tcp) {
+        u.bt = tcp->Bt3;
+        u.bt_ld = tcp->kp3;
+      }
+    }
+    NNC_TRY(launch_mode3<T>(u, b.num3part, b.n3splits, s));
+  }
+  // ---- core ------------------------------------------------------------------
+  int used = 1;
+  NNC_TRY(launch_core_m<T>(b.Y3, F[2], m1 * m2, (int)N3, m3, b.Mpart, b.msplits, &used, s));
+  {
+    CoreArgs<T> c{};
+    c.G = G;  c.M = b.Mpart;  c.M_splits = used;  c.Mout = b.M;  c.W3 = b.W3;
+    c.S1 = b.S[0];  c.S2 = b.S[1];  c.F3 = F[2];  c.n3 = N3;  c.S3_out = b.S[2];
+    c.W1 = b.W1;  c.H1 = b.H[0];  c.dots = b.dots;  c.x2 = b.stats;
+    c.trace = trace;  c.trace_stride = trace_stride;  c.counter = b.counter;
+    c.m1 = m1;  c.m2 = m2;  c.m3 = m3;  c.eps = eps;
+    NNC_TRY(launch_core<T>(c, s));
+  }
   return NNC_OK;
 }
 
@@ -148,7 +172,7 @@ int count_kernel_nodes(cudaGraph_t graph, long long* n_kernels) {
   return NNC_OK;
 }
 
-// RAII holder of the private stream, graph and events of one ntd_fit call.
+// RAII holder of the private stream, graph and events of one replay loop.
 struct GraphRun {
   cudaStream_t cs = nullptr;
   cudaGraph_t graph = nullptr;
@@ -166,9 +190,8 @@ struct GraphRun {
 // Captures one sweep on a private stream and replays it `count` times after
 // the work already queued on `s`; `s` then waits for the replays.
 template <typename T>
-int run_sweeps(const T* X, const int64_t* dims, const int* m, T* const* F, T* G,
-               NtdBuffers<T>& b, double eps, double* trace, int count, const tc::TcPlan* tcp,
-               cudaStream_t s) {
+int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* trace,
+               int count, const tc::TcPlan* tcp, cudaStream_t s) {
   if (count <= 0) return NNC_OK;
   GraphRun g;
   NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
@@ -184,8 +207,8 @@ int run_sweeps(const T* X, const int64_t* dims, const int* m, T* const* F, T* G,
     capture_ev = prof.capture_events();
   }
   NNC_CUDA_TRY(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
-  const int cap_st = sweep3<T>(X, dims, m, F, G, b, eps, trace ? trace : b.trace_dummy,
-                               trace ? 1 : 0, capture_ev, tcp, g.cs);
+  const int cap_st = sweep3<T>(X, F, G, b, eps, trace ? trace : b.trace_dummy, trace ? 1 : 0,
+                               capture_ev, tcp, g.cs);
   const cudaError_t end_e = cudaStreamEndCapture(g.cs, &g.graph);
   if (cap_st != NNC_OK) return cap_st;
   NNC_CUDA_TRY(end_e);
@@ -211,22 +234,20 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   const int64_t N1 = dims[0], N2 = dims[1], N3 = dims[2];
   const int m1 = m[0], m2 = m[1], m3 = m[2];
   const int64_t nX = N1 * N2 * N3;
-  Scratch sc(s);
-  NtdBuffers<T> b{};
   const int64_t nc = (int64_t)m1 * m2 * m3;
-  const int64_t mmax = m1 > m2 ? (m1 > m3 ? m1 : m3) : (m2 > m3 ? m2 : m3);
-  const int64_t Nmax = N1 > N2 ? (N1 > N3 ? N1 : N3) : (N2 > N3 ? N2 : N3);
-  const int64_t nY1 = N1 * m2 * m3, nY2 = (int64_t)m1 * N2 * m3, nY3 = (int64_t)m1 * m2 * N3;
-  int64_t ymax = nY1 > nY2 ? nY1 : nY2;
-  ymax = ymax > nY3 ? ymax : nY3;
-  ymax = ymax > nc ? ymax : nc;
-  b.split_cap = (size_t)(8 * ymax > (1 << 20) ? 8 * ymax : (1 << 20));
+  Scratch sc(s);
+  NtdState<T> b{};
+  for (int k = 0; k < 3; ++k) {
+    b.N[k] = dims[k];
+    b.m[k] = m[k];
+  }
 
   NNC_TRY(sc.get(&b.stats_part, 3 * kStatBlocks));
   NNC_TRY(sc.get(&b.stats, 3));
   NNC_TRY(sc.get(&b.trace_dummy, 1));
   NNC_TRY(sc.get(&b.resid2, 2));
   NNC_TRY(sc.get(&b.counter, 1));
+  NNC_TRY(sc.get(&b.dots, 2 * kCoreCtas));
   NNC_CUDA_TRY(launch_tensor_stats<T>(X, nX, b.stats_part, b.stats, s));
   double st[3];
   NNC_CUDA_TRY(cudaMemcpyAsync(st, b.stats, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -235,20 +256,23 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   if (st[1] > 0.0) return NNC_ERR_NEGATIVE_INPUT;
   if (!(st[0] > 0.0)) return NNC_ERR_INVALID_ARG;  // X == 0: the relative error is undefined
 
+  b.rpb[0] = upd_rows_per_block<T>(m2, m3, N1);
+  b.rpb[1] = upd_rows_per_block<T>(m1, m3, N2);
+  b.n3splits = num3_splits<T>(m1 * m2, (int)N3);
+  b.msplits = core_m_splits<T>(m1 * m2, (int)N3);
+
   NNC_TRY(sc.get(&b.P3, (size_t)(N1 * N2 * m3)));
   NNC_TRY(sc.get(&b.P1, (size_t)(m1 * N2 * N3)));
-  NNC_TRY(sc.get(&b.Y1, (size_t)nY1));
-  NNC_TRY(sc.get(&b.Y2, (size_t)nY2));
-  NNC_TRY(sc.get(&b.Y3, (size_t)nY3));
+  NNC_TRY(sc.get(&b.Y3, (size_t)((int64_t)m1 * m2 * N3)));
+  NNC_TRY(sc.get(&b.num3part, (size_t)b.n3splits * N3 * m3));
+  NNC_TRY(sc.get(&b.Mpart, (size_t)b.msplits * nc));
   NNC_TRY(sc.get(&b.M, (size_t)nc));
   NNC_TRY(sc.get(&b.W1, (size_t)nc));
-  NNC_TRY(sc.get(&b.W, (size_t)nc));
-  NNC_TRY(sc.get(&b.Wt, (size_t)nc));
-  NNC_TRY(sc.get(&b.D, (size_t)nc));
-  for (int k = 0; k < 3; ++k) NNC_TRY(sc.get(&b.S[k], (size_t)(m[k] * m[k])));
-  NNC_TRY(sc.get(&b.H, (size_t)(mmax * mmax)));
-  NNC_TRY(sc.get(&b.Num, (size_t)(Nmax * mmax)));
-  NNC_TRY(sc.get(&b.split, b.split_cap));
+  NNC_TRY(sc.get(&b.W3, (size_t)nc));
+  for (int k = 0; k < 3; ++k) {
+    NNC_TRY(sc.get(&b.S[k], (size_t)(m[k] * m[k])));
+    NNC_TRY(sc.get(&b.H[k], (size_t)(m[k] * m[k])));
+  }
 
   tc::TcPlan plan;
   const tc::TcPlan* tcp = nullptr;
@@ -259,19 +283,25 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
     }
   }
 
-  // Prologue: Grams, W1 = G x_2 S2 x_3 S3, trace counter.
-  for (int k = 0; k < 3; ++k)
-    NNC_CUDA_TRY(launch_ttm<T>(F[k], 1, (int)dims[k], m[k], F[k], m[k], 1, m[k], b.S[k], b.split,
-                               b.split_cap, s));
-  NNC_CUDA_TRY(launch_ttm<T>(G, m1, m2, m3, b.S[1], m2, 1, m2, b.Wt, b.split, b.split_cap, s));
-  NNC_CUDA_TRY(launch_ttm<T>(b.Wt, (int64_t)m1 * m2, m3, 1, b.S[2], m3, 1, m3, b.W1, b.split,
-                             b.split_cap, s));
+  // Prologue: S_k = F_k^T F_k, H1 = unfold_1(G x_2 S2 x_3 S3) unfold_1(G)^T,
+  // the BF16 operand of F^(3), the trace counter.
+  for (int k = 0; k < 3; ++k) NNC_TRY(launch_gram<T>(F[k], dims[k], m[k], b.S[k], s));
+  {
+    HArgs<T> h{};
+    h.G = G;  h.mp = m1;  h.mu = m2;  h.mv = m3;
+    h.sp = (int64_t)m2 * m3;  h.su_s = m3;  h.sv_s = 1;
+    h.su = b.S[1];  h.sv = b.S[2];  h.H = b.H[0];
+    NNC_TRY(launch_hmat<T>(h, s));
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (tcp) NNC_TRY(tcp->pass3(F[2], b.P3, s, /*convert=*/true));  // builds Bt3
+  }
   NNC_CUDA_TRY(cudaMemsetAsync(b.counter, 0, sizeof(int), s));
 
   const int n_fast = tcp ? o->iters - o->refine_iters : 0;
-  NNC_TRY(run_sweeps<T>(X, dims, m, F, G, b, o->eps, trace, n_fast, tcp, s));
+  NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, n_fast, tcp, s));
   if (tcp) NNC_TRY(plan.check(s));
-  NNC_TRY(run_sweeps<T>(X, dims, m, F, G, b, o->eps, trace, o->iters - n_fast, nullptr, s));
+  NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, o->iters - n_fast, nullptr, s));
 
   if (rel_err) {
     const T* fac[3] = {F[0], F[1], F[2]};

@@ -1,0 +1,105 @@
+// Fused kernels of one nnTD sweep (sweep.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace nnc {
+
+constexpr int kCoreCtas = 8;  // CTAs of the cluster that updates the core
+
+// One factor update (mode 1 or 2: Y from P3 by a small GEMM; mode 3: Y3 given).
+template <typename T>
+struct UpdArgs {
+  // Y_r[u, c] = sum_{t < len} Fc[t, u] P[r prow + t pstride + c]  (modes 1, 2)
+  // mode 3: P = Y3 (mu = m1 m2 rows of length nrows = N3)
+  const T* P;
+  int64_t prow, pstride;
+  const T* Fc;
+  int len;      // contraction length (modes 1, 2)
+  int mu, mc;   // Y_r is mu x mc
+  // Num[r, v] = sum_{u,c} Y_r[u, c] G[v gs_v + u gs_u + c]
+  const T* G;
+  int64_t gs_v, gs_u;
+  // MU on F (nrows x mv) with Den = F H (H mv x mv)
+  T* F;
+  int64_t nrows;
+  int mv;
+  const T* H;
+  double eps;
+  int rows_per_block;
+  // Optional BF16 operand of the next tensor-core pass: bt[v bt_ld + r] = bf16(F[r, v] scale[r])
+  __nv_bfloat16* bt;
+  int64_t bt_ld;
+  const float* bt_scale;
+};
+
+// H_n = unfold_n(G x_u S_u x_v S_v) unfold_n(G)^T, one block per index p of mode n.
+// Slice p of G: element (u, v) at G[p sp + u su_s + v sv_s]. Each Gram comes
+// either ready (su / sv) or is formed from its factor (fu: nu x mu, fv: nv x mv).
+template <typename T>
+struct HArgs {
+  const T* G;
+  int mp, mu, mv;
+  int64_t sp, su_s, sv_s;
+  const T* su;
+  const T* fu;
+  int64_t nu;
+  const T* sv;
+  const T* fv;
+  int64_t nv;
+  T* su_out;            // optional: the Gram formed from fu (written by block 0)
+  T* sv_out;
+  T* H;                 // mp x mp
+  T* Wout;              // optional: the W slices, laid out like G
+};
+
+template <typename T>
+struct CoreArgs {
+  T* G;
+  const T* M;           // M_splits partial numerators, each m1 x m2 x m3
+  int M_splits;
+  T* Mout;              // their sum
+  const T* W3;          // G x_1 S1 x_2 S2
+  const T* S1;
+  const T* S2;
+  const T* F3;          // S3 = F3^T F3 is formed here
+  int64_t n3;
+  T* S3_out;
+  T* W1;                // out: G_new x_2 S2 x_3 S3
+  T* H1;                // out: unfold_1(W1) unfold_1(G_new)^T
+  double* dots;         // 2 x kCoreCtas scratch
+  const double* x2;
+  double* trace;
+  int trace_stride;
+  int* counter;
+  int m1, m2, m3;
+  double eps;
+};
+
+template <typename T>
+int upd_rows_per_block(int mu, int mc, int64_t nrows);
+template <typename T>
+int launch_upd12(const UpdArgs<T>& a, cudaStream_t s);
+template <typename T>
+int launch_hmat(const HArgs<T>& a, cudaStream_t s);
+template <typename T>
+int launch_y3(const T* P1, const T* F2, int m1, int N2, int N3, int m2, T* Y3, cudaStream_t s);
+// Mode 3: Num3 split over (a, b) into `part` (splits x N3 x m3), then MU.
+template <typename T>
+int num3_splits(int UC, int N3);
+template <typename T>
+int launch_mode3(const UpdArgs<T>& a, T* part, int splits, cudaStream_t s);
+// M = Y3 x_3 F3^T split over k into `part` (splits x UC x m3).
+template <typename T>
+int core_m_splits(int UC, int N3);
+template <typename T>
+int launch_core_m(const T* Y3, const T* F3, int UC, int N3, int m3, T* part, int splits,
+                  int* used_splits, cudaStream_t s);
+template <typename T>
+int launch_core(const CoreArgs<T>& a, cudaStream_t s);
+template <typename T>
+int launch_gram(const T* F, int64_t N, int m, T* S, cudaStream_t s);
+
+}  // namespace nnc

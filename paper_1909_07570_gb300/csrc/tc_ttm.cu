@@ -422,6 +422,8 @@ int TcPlan::init(const float* X, int64_t N1_, int64_t N2_, int64_t N3_, int m1_,
   NNC_TRY(sc.get(&Bt3, static_cast<size_t>(np3) * kp3));
   NNC_TRY(sc.get(&err, 1));
   NNC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+  NNC_CUDA_TRY(cudaMemsetAsync(Bt1, 0, sizeof(__nv_bfloat16) * np1 * kp1, s));
+  NNC_CUDA_TRY(cudaMemsetAsync(Bt3, 0, sizeof(__nv_bfloat16) * np3 * kp3, s));
   slice_scale_kernel<<<static_cast<unsigned>(N1), 256, 0, s>>>(X, N2 * N3, scale, inv_scale);
   note_launch(s);
   const int64_t n = rows * kp3;
@@ -438,10 +440,12 @@ int TcPlan::init(const float* X, int64_t N1_, int64_t N2_, int64_t N3_, int m1_,
   return NNC_OK;
 }
 
-int TcPlan::pass3(const float* F3, float* P3, cudaStream_t s) const {
-  factor_bt_kernel<<<64, 256, 0, s>>>(F3, static_cast<int>(N3), m3, kp3, np3, nullptr, Bt3);
-  note_launch(s);
-  NNC_CUDA_TRY(cudaGetLastError());
+int TcPlan::pass3(const float* F3, float* P3, cudaStream_t s, bool convert) const {
+  if (convert) {
+    factor_bt_kernel<<<64, 256, 0, s>>>(F3, static_cast<int>(N3), m3, kp3, np3, nullptr, Bt3);
+    note_launch(s);
+    NNC_CUDA_TRY(cudaGetLastError());
+  }
   TcEpilogue ep{};
   ep.out = P3;
   ep.q = m3;
@@ -453,10 +457,12 @@ int TcPlan::pass3(const float* F3, float* P3, cudaStream_t s) const {
   return launch_pass<false, 64>(mapA3, mapB3, kp3 / 64, tiles, ep, err, s);
 }
 
-int TcPlan::pass1(const float* F1, float* P1, cudaStream_t s) const {
-  factor_bt_kernel<<<64, 256, 0, s>>>(F1, static_cast<int>(N1), m1, kp1, np1, scale, Bt1);
-  note_launch(s);
-  NNC_CUDA_TRY(cudaGetLastError());
+int TcPlan::pass1(const float* F1, float* P1, cudaStream_t s, bool convert) const {
+  if (convert) {
+    factor_bt_kernel<<<64, 256, 0, s>>>(F1, static_cast<int>(N1), m1, kp1, np1, scale, Bt1);
+    note_launch(s);
+    NNC_CUDA_TRY(cudaGetLastError());
+  }
   TcEpilogue ep{};
   ep.out = P1;
   ep.q = m1;

@@ -37,10 +37,11 @@ struct TcPlan {
   // shared memory).
   int init(const float* X, int64_t N1, int64_t N2, int64_t N3, int m1, int m3, Scratch& sc,
            cudaStream_t s);
-  // P3 = X x_3 F3^T ((N1 N2) x m3, FP32) from the current F3.
-  int pass3(const float* F3, float* P3, cudaStream_t s) const;
-  // P1 = X x_1 F1^T (m1 x N2 x N3, FP32) from the current F1.
-  int pass1(const float* F1, float* P1, cudaStream_t s) const;
+  // P3 = X x_3 F3^T ((N1 N2) x m3, FP32). With convert, Bt3 is first built
+  // from F3; without, Bt3 already holds bf16(F3^T) (written by the sweep).
+  int pass3(const float* F3, float* P3, cudaStream_t s, bool convert = true) const;
+  // P1 = X x_1 F1^T (m1 x N2 x N3, FP32); Bt1 as above, from diag(s) F1.
+  int pass1(const float* F1, float* P1, cudaStream_t s, bool convert = true) const;
   // Synchronises s and turns a device-side pipeline time-out into NNC_ERR_TIMEOUT.
   int check(cudaStream_t s) const;
 };
