@@ -12,7 +12,7 @@
 //   pass 2   P1 = X x_1 F1^T (new F1)                 (second read of X)
 //   y3, upd3 Y3 = P1 x_2 F2^T (new F2);  Num3 = unfold_3(Y3) unfold_3(G)^T;  Den3 = F3 H3
 //   core_m   M = Y3 x_3 F3^T = X x_1 F1^T x_2 F2^T x_3 F3^T
-//   core     G <- MU(G, M, W3 x_3 S3); trace; next H1       (one 8-CTA cluster)
+//   core     G <- MU(G, M, W3 x_3 S3); trace; next H1       (core_a, core_b)
 // with S_k = F_k^T F_k. The kernels are in sweep.cu; the passes are SIMT mode
 // products (ttm.cu) or, on the BF16 path, tensor-core mode products from a
 // BF16 copy of X (tc_ttm.cu). Two reads of X per sweep is the minimum under
@@ -40,10 +40,11 @@ template <typename T>
 struct NtdState {
   int64_t N[3];
   int m[3];
-  T *P3, *P1, *Y3, *Mpart, *M, *W1, *W3, *H[3], *S[3], *num3part;
+  T *P3, *P1, *Y3, *Mpart, *M, *W1, *W3, *G2, *G3, *H[3], *S[3], *num3part;
   int rpb[2], n3splits, msplits;
   double *stats_part, *stats, *trace_dummy, *resid2, *dots;
   int* counter;
+  int* done;
 };
 
 template <typename T>
@@ -83,7 +84,7 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     UpdArgs<T> u{};
     u.P = b.P3;  u.prow = N2 * m3;  u.pstride = m3;  // P3[i, j, c]
     u.Fc = F[1]; u.len = (int)N2;   u.mu = m2;  u.mc = m3;
-    u.G = G;     u.gs_v = (int64_t)m2 * m3;  u.gs_u = m3;
+    u.Gn = G;    // rows a of G are (b, c)-contiguous
     u.F = F[0];  u.nrows = N1;  u.mv = m1;  u.H = b.H[0];  u.eps = eps;
     u.rows_per_block = b.rpb[0];
     if constexpr (std::is_same<T, float>::value) {
@@ -97,8 +98,7 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
   }
   {  // H2 from S1 = F1^T F1 (new F1) and S3
     HArgs<T> h{};
-    h.G = G;  h.mp = m2;  h.mu = m1;  h.mv = m3;
-    h.sp = m3;  h.su_s = (int64_t)m2 * m3;  h.sv_s = 1;
+    h.Gn = b.G2;  h.mp = m2;  h.mu = m1;  h.mv = m3;
     h.fu = F[0];  h.nu = N1;  h.su_out = b.S[0];
     h.sv = b.S[2];
     h.H = b.H[1];
@@ -109,15 +109,15 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     UpdArgs<T> u{};
     u.P = b.P3;  u.prow = m3;  u.pstride = N2 * m3;  // row j, contraction over i
     u.Fc = F[0]; u.len = (int)N1;  u.mu = m1;  u.mc = m3;
-    u.G = G;     u.gs_v = m3;  u.gs_u = (int64_t)m2 * m3;
+    u.Gn = b.G2;  // rows b of G2 are (a, c)-contiguous
     u.F = F[1];  u.nrows = N2;  u.mv = m2;  u.H = b.H[1];  u.eps = eps;
     u.rows_per_block = b.rpb[1];
     NNC_TRY(launch_upd12<T>(u, s));
   }
   {  // H3 and W3 = G x_1 S1 x_2 S2, with S2 = F2^T F2 (new F2)
     HArgs<T> h{};
-    h.G = G;  h.mp = m3;  h.mu = m1;  h.mv = m2;
-    h.sp = 1;  h.su_s = (int64_t)m2 * m3;  h.sv_s = m3;
+    h.Gn = b.G3;  h.mp = m3;  h.mu = m1;  h.mv = m2;
+    h.w_sp = 1;  h.w_su = (int64_t)m2 * m3;  h.w_sv = m3;  // W3 in the layout of G
     h.su = b.S[0];
     h.fv = F[1];  h.nv = N2;  h.sv_out = b.S[1];
     h.H = b.H[2];
@@ -147,9 +147,9 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
   NNC_TRY(launch_core_m<T>(b.Y3, F[2], m1 * m2, (int)N3, m3, b.Mpart, b.msplits, &used, s));
   {
     CoreArgs<T> c{};
-    c.G = G;  c.M = b.Mpart;  c.M_splits = used;  c.Mout = b.M;  c.W3 = b.W3;
+    c.G = G;  c.G2 = b.G2;  c.G3 = b.G3;  c.M = b.Mpart;  c.M_splits = used;  c.Mout = b.M;  c.W3 = b.W3;
     c.S1 = b.S[0];  c.S2 = b.S[1];  c.F3 = F[2];  c.n3 = N3;  c.S3_out = b.S[2];
-    c.W1 = b.W1;  c.H1 = b.H[0];  c.dots = b.dots;  c.x2 = b.stats;
+    c.W1 = b.W1;  c.H1 = b.H[0];  c.dots = b.dots;  c.done = b.done;  c.x2 = b.stats;
     c.trace = trace;  c.trace_stride = trace_stride;  c.counter = b.counter;
     c.m1 = m1;  c.m2 = m2;  c.m3 = m3;  c.eps = eps;
     NNC_TRY(launch_core<T>(c, s));
@@ -247,7 +247,8 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   NNC_TRY(sc.get(&b.trace_dummy, 1));
   NNC_TRY(sc.get(&b.resid2, 2));
   NNC_TRY(sc.get(&b.counter, 1));
-  NNC_TRY(sc.get(&b.dots, 2 * kCoreCtas));
+  NNC_TRY(sc.get(&b.dots, 2 * (size_t)m[0]));
+  NNC_TRY(sc.get(&b.done, 1));
   NNC_CUDA_TRY(launch_tensor_stats<T>(X, nX, b.stats_part, b.stats, s));
   double st[3];
   NNC_CUDA_TRY(cudaMemcpyAsync(st, b.stats, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -269,6 +270,8 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   NNC_TRY(sc.get(&b.M, (size_t)nc));
   NNC_TRY(sc.get(&b.W1, (size_t)nc));
   NNC_TRY(sc.get(&b.W3, (size_t)nc));
+  NNC_TRY(sc.get(&b.G2, (size_t)nc));
+  NNC_TRY(sc.get(&b.G3, (size_t)nc));
   for (int k = 0; k < 3; ++k) {
     NNC_TRY(sc.get(&b.S[k], (size_t)(m[k] * m[k])));
     NNC_TRY(sc.get(&b.H[k], (size_t)(m[k] * m[k])));
@@ -286,10 +289,10 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   // Prologue: S_k = F_k^T F_k, H1 = unfold_1(G x_2 S2 x_3 S3) unfold_1(G)^T,
   // the BF16 operand of F^(3), the trace counter.
   for (int k = 0; k < 3; ++k) NNC_TRY(launch_gram<T>(F[k], dims[k], m[k], b.S[k], s));
+  NNC_TRY(launch_permute_core<T>(G, m1, m2, m3, b.G2, b.G3, s));
   {
     HArgs<T> h{};
-    h.G = G;  h.mp = m1;  h.mu = m2;  h.mv = m3;
-    h.sp = (int64_t)m2 * m3;  h.su_s = m3;  h.sv_s = 1;
+    h.Gn = G;  h.mp = m1;  h.mu = m2;  h.mv = m3;
     h.su = b.S[1];  h.sv = b.S[2];  h.H = b.H[0];
     NNC_TRY(launch_hmat<T>(h, s));
   }
@@ -297,6 +300,7 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
     if (tcp) NNC_TRY(tcp->pass3(F[2], b.P3, s, /*convert=*/true));  // builds Bt3
   }
   NNC_CUDA_TRY(cudaMemsetAsync(b.counter, 0, sizeof(int), s));
+  NNC_CUDA_TRY(cudaMemsetAsync(b.done, 0, sizeof(int), s));
 
   const int n_fast = tcp ? o->iters - o->refine_iters : 0;
   NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, n_fast, tcp, s));

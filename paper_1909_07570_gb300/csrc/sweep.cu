@@ -14,26 +14,23 @@
 //   num3 + tail3:               Num3[k, c] = sum_{a,b} Y3[a, b, k] G[a, b, c] (split over
 //                               (a, b), added in split order); MU on F3
 //   core_m:                     M = Y3 x_3 F3^T (split over k)
-//   core (cluster of 8 CTAs, one slice of mode 1 each):
-//                               S3 = F3^T F3; D = W3 x_3 S3; G <- MU(G, M, D)
-//                               W1 = G x_2 S2 x_3 S3  [cluster barrier]
-//                               Dn = W1 x_1 S1; trace = sqrt(||X||^2 - 2<M,G> + <G,Dn>)/||X||
-//                               H1 = unfold_1(W1) unfold_1(G)^T for the next sweep
+//   core_a (one block per a):   S3 = F3^T F3; D = W3 x_3 S3; G <- MU(G, M, D);
+//                               W1 = G x_2 S2 x_3 S3
+//   core_b (one block per a):   H1 = unfold_1(W1) unfold_1(G)^T for the next sweep;
+//                               trace = sqrt(||X||^2 - 2<M,G> + <G, G x_k S_k>)/||X||
+//                               with <G, G x_k S_k> = sum S1 .* H1^T (last block)
 //
 // The contractions are SIMT GEMMs on 4 x 4 register tiles whose operands are
 // staged in shared memory by cp.async, two chunks in flight. Every reduction
 // runs in a fixed order, so results are deterministic. The BF16 path also
 // writes, from the mode-1 and mode-3 updates, the BF16 operand of the next
 // pass over X.
-#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include <type_traits>
 
 #include "kernels.cuh"
 #include "sweep.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace nnc {
 namespace {
@@ -71,6 +68,65 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// 16-byte cp.async of one vector (16 / sizeof(T) elements); the first `valid`
+// elements are copied, the rest of the vector is zero.
+template <typename T>
+__device__ __forceinline__ void cp_vec(T* dst, const T* src, int valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  const int n = valid * (int)sizeof(T);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n)
+               : "memory");
+}
+
+// Stages rows [0, nrows) x cols [0, ncols) of a tile into shared memory:
+// dst[r * lds + c] = src[r * ldg + c] for r < vrows and c < vcols, else 0.
+// ncols and lds are multiples of 4. With vec (src and ldg 16-byte aligned)
+// whole 16-byte vectors are copied; otherwise single elements. Indices advance
+// by increments, without divisions in the loop.
+template <typename T>
+__device__ __forceinline__ void stage_tile(T* dst, int lds, const T* __restrict__ src, int64_t ldg,
+                                           int nrows, int ncols, int vrows, int vcols, bool vec) {
+  if (vec) {
+    constexpr int W = 16 / (int)sizeof(T);
+    const int vpr = ncols / W;  // vectors per row
+    const int total = nrows * vpr;
+    const int step = blockDim.x;
+    int r = threadIdx.x / vpr, cv = threadIdx.x % vpr;
+    const int dr = step / vpr, dc = step % vpr;
+    for (int v = threadIdx.x; v < total; v += step) {
+      const int c = cv * W;
+      int valid = (r < vrows) ? vcols - c : 0;
+      valid = valid < 0 ? 0 : (valid > W ? W : valid);
+      cp_vec(dst + r * lds + c, valid ? src + (int64_t)r * ldg + c : src, valid);
+      r += dr;
+      cv += dc;
+      if (cv >= vpr) {
+        cv -= vpr;
+        ++r;
+      }
+    }
+  } else {
+    const int total = nrows * ncols;
+    const int step = blockDim.x;
+    int r = threadIdx.x / ncols, c = threadIdx.x % ncols;
+    const int dr = step / ncols, dc = step % ncols;
+    for (int e = threadIdx.x; e < total; e += step) {
+      const bool ok = r < vrows && c < vcols;
+      cp_elem(dst + r * lds + c, ok ? src + (int64_t)r * ldg + c : src, ok);
+      r += dr;
+      c += dc;
+      if (c >= ncols) {
+        c -= ncols;
+        ++r;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool aligned16(const void* p, int64_t ld_elems, int elem) {
+  return ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && (((ld_elems * elem) & 15) == 0);
+}
+
 // ---- 4-wide shared-memory loads (16-byte aligned rows) ----------------------
 __device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
   const float4 t = *reinterpret_cast<const float4*>(p);
@@ -105,31 +161,36 @@ __device__ __forceinline__ void zero4x4(T (&acc)[4][4]) {
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 }
 
+// Rows of F staged per chunk by gram_block: up to 32 KB of shared memory.
+__host__ __device__ constexpr int gram_rows(int m, int elem) {
+  return (32 * 1024) / (r4(m) * elem) < 1 ? 1 : (32 * 1024) / (r4(m) * elem);
+}
+
 // S = F^T F (n rows of width m) into shared s (m x m), computed by the whole
 // block: groups of threads take interleaved rows with 4 x 4 tiles of S and are
-// added in group order. `stage` holds >= KC * r4(m) + groups * m * m elements.
+// added in group order. F is staged by cp.async in chunks of gram_rows rows;
+// `stage` holds gram_stage_elems(m) elements (chunk + per-group partials).
 template <typename T>
 __device__ void gram_block(const T* __restrict__ F, int64_t n, int m, T* s, T* stage) {
   const int mq = r4(m) / 4, tiles = mq * mq;
   const int groups = max(1, (int)blockDim.x / tiles);
   const int g = threadIdx.x / tiles, t = threadIdx.x % tiles;
   const int x0 = (t / mq) * 4, y0 = (t % mq) * 4;
-  T* fs = stage;                       // KC x r4(m)
-  T* red = stage + KC * r4(m);         // groups x m x m
+  const int RC = gram_rows(m, (int)sizeof(T));
+  T* fs = stage;                             // RC x r4(m)
+  T* red = stage + al4((size_t)RC * r4(m));  // groups x m x m
   T acc[4][4];
   zero4x4(acc);
-  for (int64_t r0 = 0; r0 < n; r0 += KC) {
-    const int rn = (int)((n - r0) < (int64_t)KC ? (n - r0) : (int64_t)KC);
-    for (int e = threadIdx.x; e < KC * r4(m); e += blockDim.x) {
-      const int rr = e / r4(m), c = e % r4(m);
-      fs[e] = (rr < rn && c < m) ? F[(r0 + rr) * m + c] : T(0);
-    }
+  for (int64_t r0 = 0; r0 < n; r0 += RC) {
+    const int rn = (int)((n - r0) < (int64_t)RC ? (n - r0) : (int64_t)RC);
+    stage_tile(fs, r4(m), F + r0 * m, m, rn, r4(m), rn, m, aligned16(F + r0 * m, m, sizeof(T)));
+    cp_commit();
+    cp_wait<0>();
     __syncthreads();
     if (g < groups) {
       for (int rr = g; rr < rn; rr += groups) {
-        T a[4];
+        T a[4], b[4];
         ld4(fs + rr * r4(m) + x0, a);
-        T b[4];
         ld4(fs + rr * r4(m) + y0, b);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -153,6 +214,21 @@ __device__ void gram_block(const T* __restrict__ F, int64_t n, int m, T* s, T* s
     s[e] = v;
   }
   __syncthreads();
+}
+
+// sum_e x[e] y[e] over e = lane, lane + 32, ... < n, then over the warp.
+template <typename T>
+__device__ __forceinline__ T warp_dot(const T* x, const T* __restrict__ y, int n, int lane) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int e = lane;
+  for (; e + 96 < n; e += 128) {
+    s0 = fma(x[e], y[e], s0);
+    s1 = fma(x[e + 32], y[e + 32], s1);
+    s2 = fma(x[e + 64], y[e + 64], s2);
+    s3 = fma(x[e + 96], y[e + 96], s3);
+  }
+  for (; e < n; e += 32) s0 = fma(x[e], y[e], s0);
+  return warp_sum((s0 + s1) + (s2 + s3));
 }
 
 // ---------------------------------------------------------------------------
@@ -180,21 +256,18 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
   }
 
   const int nchunks = (a.len + KC - 1) / KC;
+  const bool vecA = aligned16(a.Fc, MU_, sizeof(T));
+  const bool vecB = aligned16(a.P, a.prow, sizeof(T)) && aligned16(a.P, a.pstride, sizeof(T));
   auto issue = [&](int c, int buf) {
     const int t0 = c * KC;
+    const int tn = min(KC, a.len - t0);
     T* A = As + buf * KC * mu4;
     T* B = Bs + buf * S * KC * mc4;
-    for (int e = threadIdx.x; e < KC * mu4; e += blockDim.x) {
-      const int tt = e / mu4, u = e % mu4;
-      const bool ok = (t0 + tt < a.len) && (u < MU_);
-      cp_elem(A + e, ok ? a.Fc + (int64_t)(t0 + tt) * MU_ + u : a.Fc, ok);
-    }
-    for (int e = threadIdx.x; e < S * KC * mc4; e += blockDim.x) {
-      const int rr = e / (KC * mc4), rem = e % (KC * mc4);
-      const int tt = rem / mc4, c4 = rem % mc4;
+    stage_tile(A, mu4, a.Fc + (int64_t)t0 * MU_, MU_, KC, mu4, tn, MU_, vecA);
+    for (int rr = 0; rr < S; ++rr) {
       const int64_t r = r0 + rr;
-      const bool ok = (r < a.nrows) && (t0 + tt < a.len) && (c4 < MC);
-      cp_elem(B + e, ok ? a.P + r * a.prow + (int64_t)(t0 + tt) * a.pstride + c4 : a.P, ok);
+      stage_tile(B + rr * KC * mc4, mc4, a.P + (r < a.nrows ? r : 0) * a.prow +
+                 (int64_t)t0 * a.pstride, a.pstride, KC, mc4, r < a.nrows ? tn : 0, MC, vecB);
     }
     cp_commit();
   };
@@ -229,21 +302,12 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
   }
   __syncthreads();
 
-  // Num[r, v] = sum_{u,c} Y_r[u, c] G[v gs_v + u gs_u + c]: one warp per (r, v).
+  // Num[r, v] = <Y_r, Gn[v, :]>: one warp per (r, v); Gn rows are contiguous.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int UC = MU_ * MC;
   for (int task = warp; task < S * MV; task += nw) {
     const int rr = task / MV, v = task % MV;
-    const T* y = ys + rr * MU_ * MC;
-    const T* g = a.G + (int64_t)v * a.gs_v;
-    T s = T(0);
-    int u = 0, cc = lane;
-    while (cc >= MC && u < MU_) { cc -= MC; ++u; }
-    for (; u < MU_;) {
-      s = fma(y[u * MC + cc], g[(int64_t)u * a.gs_u + cc], s);
-      cc += 32;
-      while (cc >= MC && u < MU_) { cc -= MC; ++u; }
-    }
-    s = warp_sum(s);
+    const T s = warp_dot(ys + rr * UC, a.Gn + (int64_t)v * UC, UC, lane);
     if (lane == 0) nm[task] = s;
   }
   __syncthreads();
@@ -289,10 +353,7 @@ __global__ void __launch_bounds__(kThreads) hmat_kernel(HArgs<T> a) {
   } else {
     for (int e = threadIdx.x; e < V * V; e += blockDim.x) sv[e] = a.sv[e];
   }
-  for (int e = threadIdx.x; e < U * V; e += blockDim.x) {
-    const int u = e / V, v = e % V;
-    gp[e] = a.G[(int64_t)p * a.sp + (int64_t)u * a.su_s + (int64_t)v * a.sv_s];
-  }
+  for (int e = threadIdx.x; e < U * V; e += blockDim.x) gp[e] = a.Gn[(int64_t)p * U * V + e];
   __syncthreads();
   if (p == 0 && a.su_out && a.fu)
     for (int e = threadIdx.x; e < U * U; e += blockDim.x) a.su_out[e] = su[e];
@@ -310,17 +371,12 @@ __global__ void __launch_bounds__(kThreads) hmat_kernel(HArgs<T> a) {
     T s = T(0);
     for (int w = 0; w < V; ++w) s = fma(tp[u * V + w], sv[w * V + v], s);
     wp[e] = s;
-    if (a.Wout) a.Wout[(int64_t)p * a.sp + (int64_t)u * a.su_s + (int64_t)v * a.sv_s] = s;
+    if (a.Wout) a.Wout[(int64_t)p * a.w_sp + (int64_t)u * a.w_su + (int64_t)v * a.w_sv] = s;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int q = warp; q < P; q += kThreads / 32) {  // H[p, q] = <wp, G_q>
-    T s = T(0);
-    for (int e = lane; e < U * V; e += 32) {
-      const int u = e / V, v = e % V;
-      s = fma(wp[e], a.G[(int64_t)q * a.sp + (int64_t)u * a.su_s + (int64_t)v * a.sv_s], s);
-    }
-    s = warp_sum(s);
+    const T s = warp_dot(wp, a.Gn + (int64_t)q * U * V, U * V, lane);
     if (lane == 0) a.H[p * P + q] = s;
   }
 }
@@ -341,20 +397,13 @@ __global__ void __launch_bounds__(kThreads) y3_kernel(const T* __restrict__ P1,
   const int ai = blockIdx.y, k0 = blockIdx.x * MT;
   const T* p1 = P1 + (int64_t)ai * N2 * N3;
   const int nchunks = (N2 + KC - 1) / KC;
+  const bool vecA = aligned16(p1 + k0, N3, sizeof(T));
+  const bool vecB = aligned16(F2, m2, sizeof(T));
   auto issue = [&](int c, int buf) {
     const int j0 = c * KC;
-    T* A = As + buf * KC * MT;
-    T* B = Bs + buf * KC * m24;
-    for (int e = threadIdx.x; e < KC * MT; e += blockDim.x) {
-      const int jj = e / MT, kk = e % MT;
-      const bool ok = (j0 + jj < N2) && (k0 + kk < N3);
-      cp_elem(A + e, ok ? p1 + (int64_t)(j0 + jj) * N3 + k0 + kk : p1, ok);
-    }
-    for (int e = threadIdx.x; e < KC * m24; e += blockDim.x) {
-      const int jj = e / m24, b = e % m24;
-      const bool ok = (j0 + jj < N2) && (b < m2);
-      cp_elem(B + e, ok ? F2 + (int64_t)(j0 + jj) * m2 + b : F2, ok);
-    }
+    const int jn = min(KC, N2 - j0);
+    stage_tile(As + buf * KC * MT, MT, p1 + (int64_t)j0 * N3 + k0, N3, KC, MT, jn, N3 - k0, vecA);
+    stage_tile(Bs + buf * KC * m24, m24, F2 + (int64_t)j0 * m2, m2, KC, m24, jn, m2, vecB);
     cp_commit();
   };
   const int tiles = (MT / 4) * (m24 / 4);
@@ -407,20 +456,13 @@ __global__ void __launch_bounds__(kThreads) num3_kernel(const T* __restrict__ Y3
   const int k0 = blockIdx.x * MT;
   const int ub = blockIdx.y * u_per_split, ue = min(UC, ub + u_per_split);
   const int nchunks = (ue - ub + KC - 1) / KC;
+  const bool vecA = aligned16(Y3 + k0, N3, sizeof(T));
+  const bool vecB = aligned16(G, m3, sizeof(T));
   auto issue = [&](int c, int buf) {
     const int u0 = ub + c * KC;
-    T* A = As + buf * KC * MT;
-    T* B = Bs + buf * KC * m34;
-    for (int e = threadIdx.x; e < KC * MT; e += blockDim.x) {
-      const int uu = e / MT, kk = e % MT;
-      const bool ok = (u0 + uu < ue) && (k0 + kk < N3);
-      cp_elem(A + e, ok ? Y3 + (int64_t)(u0 + uu) * N3 + k0 + kk : Y3, ok);
-    }
-    for (int e = threadIdx.x; e < KC * m34; e += blockDim.x) {
-      const int uu = e / m34, cc = e % m34;
-      const bool ok = (u0 + uu < ue) && (cc < m3);
-      cp_elem(B + e, ok ? G + (int64_t)(u0 + uu) * m3 + cc : G, ok);
-    }
+    const int un = min(KC, ue - u0);
+    stage_tile(As + buf * KC * MT, MT, Y3 + (int64_t)u0 * N3 + k0, N3, KC, MT, un, N3 - k0, vecA);
+    stage_tile(Bs + buf * KC * m34, m34, G + (int64_t)u0 * m3, m3, KC, m34, un, m3, vecB);
     cp_commit();
   };
   const int tiles = (MT / 4) * (m34 / 4);
@@ -504,20 +546,18 @@ __global__ void __launch_bounds__(kThreads) core_m_kernel(const T* __restrict__ 
   const int u0 = blockIdx.x * MT;
   const int kb = blockIdx.y * k_per_split, ke = min(N3, kb + k_per_split);
   const int nchunks = (ke - kb + KC - 1) / KC;
+  const bool vecB = aligned16(F3, m3, sizeof(T));
   auto issue = [&](int c, int buf) {
     const int kc0 = kb + c * KC;
     T* A = As + buf * KC * LDA;
-    T* B = Bs + buf * KC * m34;
+    // A[k][u] = Y3[u0 + u, kc0 + k]: consecutive threads take consecutive k of one row.
     for (int e = threadIdx.x; e < KC * MT; e += blockDim.x) {
-      const int uu = e / KC, kk = e % KC;  // consecutive threads: consecutive k of one row
+      const int uu = e >> 5, kk = e & (KC - 1);
       const bool ok = (u0 + uu < UC) && (kc0 + kk < ke);
       cp_elem(A + kk * LDA + uu, ok ? Y3 + (int64_t)(u0 + uu) * N3 + kc0 + kk : Y3, ok);
     }
-    for (int e = threadIdx.x; e < KC * m34; e += blockDim.x) {
-      const int kk = e / m34, cc = e % m34;
-      const bool ok = (kc0 + kk < ke) && (cc < m3);
-      cp_elem(B + e, ok ? F3 + (int64_t)(kc0 + kk) * m3 + cc : F3, ok);
-    }
+    stage_tile(Bs + buf * KC * m34, m34, F3 + (int64_t)kc0 * m3, m3, KC, m34,
+               min(KC, ke - kc0), m3, vecB);
     cp_commit();
   };
   const int tiles = (MT / 4) * (m34 / 4);
@@ -553,109 +593,119 @@ __global__ void __launch_bounds__(kThreads) core_m_kernel(const T* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// core: core update, residual identity and next H1; one cluster of kCoreCtas.
+// core_a: one block per mode-1 index a (no block depends on another):
+//   S3 = F3^T F3;  M[a] = sum of the k splits;  D[a] = W3[a] x_3 S3;
+//   G[a] <- MU(G[a], M[a], D[a]);  W1[a] = S2 G[a] S3
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) core_kernel(CoreArgs<T> a) {
+__global__ void __launch_bounds__(kThreads) core_a_kernel(CoreArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = static_cast<int>(cluster.block_rank());
-  const int nct = static_cast<int>(cluster.num_blocks());
   const int m1 = a.m1, m2 = a.m2, m3 = a.m3;
   const int bc = m2 * m3;
-  T* s1 = sm;                   // m1 x m1
-  T* s2 = s1 + al4(m1 * m1);    // m2 x m2
+  T* s2 = sm;                   // m2 x m2
   T* s3 = s2 + al4(m2 * m2);    // m3 x m3
   T* ga = s3 + al4(m3 * m3);    // bc: G[a] (updated)
   T* wa = ga + al4(bc);         // bc: W3[a], then scratch
   T* stage = wa + al4(bc);      // Gram staging
-  __shared__ double red[32];
-
-  for (int e = threadIdx.x; e < m1 * m1; e += blockDim.x) s1[e] = a.S1[e];
+  const int aa = blockIdx.x;
+  const int64_t off = (int64_t)aa * bc;
   for (int e = threadIdx.x; e < m2 * m2; e += blockDim.x) s2[e] = a.S2[e];
-  gram_block(a.F3, a.n3, m3, s3, stage);
-  if (rank == 0)
+  for (int e = threadIdx.x; e < bc; e += blockDim.x) wa[e] = a.W3[off + e];
+  gram_block(a.F3, a.n3, m3, s3, stage);  // ends with a barrier
+  if (aa == 0)
     for (int e = threadIdx.x; e < m3 * m3; e += blockDim.x) a.S3_out[e] = s3[e];
-  const int per = (m1 + nct - 1) / nct;
-  const int a0 = rank * per, a1 = min(m1, a0 + per);
-
-  for (int aa = a0; aa < a1; ++aa) {
-    const int64_t off = (int64_t)aa * bc;
-    for (int e = threadIdx.x; e < bc; e += blockDim.x) wa[e] = a.W3[off + e];
-    __syncthreads();
-    // D[a] = W3[a] S3;  G[a] <- MU(G[a], M[a], D[a])  (M summed over its k splits)
-    for (int e = threadIdx.x; e < bc; e += blockDim.x) {
-      const int b = e / m3, c = e % m3;
-      T d = T(0);
-      for (int w = 0; w < m3; ++w) d = fma(wa[b * m3 + w], s3[w * m3 + c], d);
-      T mv = T(0);
-      for (int s = 0; s < a.M_splits; ++s) mv += a.M[(int64_t)s * m1 * bc + off + e];
-      const T gv = mu_step(a.G[off + e], mv, d, (T)a.eps);
-      ga[e] = gv;
-      a.G[off + e] = gv;
-      a.Mout[off + e] = mv;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < bc; e += blockDim.x) {  // scratch = S2 G[a]
-      const int b = e / m3, c = e % m3;
-      T s = T(0);
-      for (int w = 0; w < m2; ++w) s = fma(s2[b * m2 + w], ga[w * m3 + c], s);
-      wa[e] = s;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < bc; e += blockDim.x) {  // W1[a] = scratch S3
-      const int b = e / m3, c = e % m3;
-      T s = T(0);
-      for (int w = 0; w < m3; ++w) s = fma(wa[b * m3 + w], s3[w * m3 + c], s);
-      a.W1[off + e] = s;
-    }
-    __syncthreads();
+  for (int e = threadIdx.x; e < bc; e += blockDim.x) {
+    const int b = e / m3, c = e % m3;
+    T d = T(0);
+    for (int w = 0; w < m3; ++w) d = fma(wa[b * m3 + w], s3[w * m3 + c], d);
+    T mv = T(0);
+    for (int s = 0; s < a.M_splits; ++s) mv += a.M[(int64_t)s * m1 * bc + off + e];
+    const T gv = mu_step(a.G[off + e], mv, d, (T)a.eps);
+    ga[e] = gv;
+    a.G[off + e] = gv;
+    a.G2[((int64_t)b * m1 + aa) * m3 + c] = gv;  // G permuted to (m2, m1, m3)
+    a.G3[((int64_t)c * m1 + aa) * m2 + b] = gv;  // G permuted to (m3, m1, m2)
+    a.Mout[off + e] = mv;
   }
-  __threadfence();
-  cluster.sync();
-
-  double mg = 0.0, gd = 0.0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int aa = a0; aa < a1; ++aa) {
-    const int64_t off = (int64_t)aa * bc;
-    for (int e = threadIdx.x; e < bc; e += blockDim.x) {
-      T dn = T(0);
-      for (int w = 0; w < m1; ++w) dn = fma(s1[aa * m1 + w], a.W1[(int64_t)w * bc + e], dn);
-      const double g = (double)a.G[off + e];
-      mg += (double)a.Mout[off + e] * g;
-      gd += g * (double)dn;
-      wa[e] = a.W1[off + e];
-    }
-    __syncthreads();
-    for (int q = warp; q < m1; q += kThreads / 32) {  // H1[a, q] = <W1[a], G[q]>
-      T s = T(0);
-      for (int e = lane; e < bc; e += 32) s = fma(wa[e], a.G[(int64_t)q * bc + e], s);
-      s = warp_sum(s);
-      if (lane == 0) a.H1[aa * m1 + q] = s;
-    }
-    __syncthreads();
+  __syncthreads();
+  for (int e = threadIdx.x; e < bc; e += blockDim.x) {  // scratch = S2 G[a]
+    const int b = e / m3, c = e % m3;
+    T s = T(0);
+    for (int w = 0; w < m2; ++w) s = fma(s2[b * m2 + w], ga[w * m3 + c], s);
+    wa[e] = s;
   }
+  __syncthreads();
+  for (int e = threadIdx.x; e < bc; e += blockDim.x) {  // W1[a] = scratch S3
+    const int b = e / m3, c = e % m3;
+    T s = T(0);
+    for (int w = 0; w < m3; ++w) s = fma(wa[b * m3 + w], s3[w * m3 + c], s);
+    a.W1[off + e] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// core_b: one block per a: H1[a, q] = <W1[a], G[q]> (next sweep's H1) and
+// <M[a], G[a]>. The residual also needs <G, G x_k S_k> = sum_{a,w} S1[a, w]
+// H1[w, a] (Dn[a] = sum_w S1[a, w] W1[w], so <G[a], Dn[a]> = sum_w S1[a, w]
+// <W1[w], G[a]>). The last block to finish adds the terms in a fixed order
+// and writes the trace entry.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) core_b_kernel(CoreArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red[32];
+  __shared__ int last;
+  const int m1 = a.m1, m2 = a.m2, m3 = a.m3;
+  const int bc = m2 * m3;
+  T* wa = sm;  // bc: W1[a]
+  const int aa = blockIdx.x;
+  const int64_t off = (int64_t)aa * bc;
+  for (int e = threadIdx.x; e < bc; e += blockDim.x) wa[e] = a.W1[off + e];
+  __syncthreads();
+  double mg = 0.0;
+  for (int e = threadIdx.x; e < bc; e += blockDim.x)
+    mg += (double)a.Mout[off + e] * (double)a.G[off + e];
   mg = block_sum(mg, red);
-  gd = block_sum(gd, red);
-  if (threadIdx.x == 0) {
-    a.dots[2 * rank] = mg;
-    a.dots[2 * rank + 1] = gd;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = warp; q < m1; q += kThreads / 32) {
+    const T s = warp_dot(wa, a.G + (int64_t)q * bc, bc, lane);
+    if (lane == 0) a.H1[aa * m1 + q] = s;
   }
-  __threadfence();
-  cluster.sync();
-  if (rank == 0 && threadIdx.x == 0) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.dots[aa] = mg;
+    __threadfence();
+    last = (atomicAdd(a.done, 1) == m1 - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const volatile T* H1 = a.H1;
     double sm_mg = 0.0, sm_gd = 0.0;
-    for (int r = 0; r < nct; ++r) {
-      sm_mg += a.dots[2 * r];
-      sm_gd += a.dots[2 * r + 1];
-    }
+    for (int r = 0; r < m1; ++r) sm_mg += ((volatile double*)a.dots)[r];
+    for (int r = 0; r < m1; ++r)
+      for (int w = 0; w < m1; ++w) sm_gd += (double)a.S1[r * m1 + w] * (double)H1[w * m1 + r];
     const double xx = *a.x2;
     double r2 = xx - 2.0 * sm_mg + sm_gd;
     if (r2 < 0.0) r2 = 0.0;
     const int t = *a.counter;
     a.trace[(int64_t)t * a.trace_stride] = sqrt(r2 / xx);
     *a.counter = t + 1;
+    *a.done = 0;  // ready for the next sweep
+  }
+}
+
+// G2[b, a, c] = G[a, b, c], G3[c, a, b] = G[a, b, c] (the initial core).
+template <typename T>
+__global__ void permute_core_kernel(const T* __restrict__ G, int m1, int m2, int m3,
+                                    T* __restrict__ G2, T* __restrict__ G3) {
+  const int n = m1 * m2 * m3;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int c = e % m3, b = (e / m3) % m2, aa = e / (m2 * m3);
+    G2[((int64_t)b * m1 + aa) * m3 + c] = G[e];
+    G3[((int64_t)c * m1 + aa) * m2 + b] = G[e];
   }
 }
 
@@ -669,10 +719,11 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ F,
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) S[e] = sm[e];
 }
 
+template <typename T>
 size_t gram_stage_elems(int m) {
   const int mq = r4(m) / 4, tiles = mq * mq;
   const int groups = kThreads / tiles > 1 ? kThreads / tiles : 1;
-  return (size_t)KC * r4(m) + (size_t)groups * m * m;
+  return al4((size_t)gram_rows(m, (int)sizeof(T)) * r4(m)) + (size_t)groups * m * m;
 }
 
 int split_count(int64_t blocks, int64_t len, int chunk) {
@@ -718,8 +769,8 @@ int launch_upd12(const UpdArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 int launch_hmat(const HArgs<T>& a, cudaStream_t s) {
-  const size_t g = gram_stage_elems(a.mu) > gram_stage_elems(a.mv) ? gram_stage_elems(a.mu)
-                                                                    : gram_stage_elems(a.mv);
+  const size_t g = gram_stage_elems<T>(a.mu) > gram_stage_elems<T>(a.mv) ? gram_stage_elems<T>(a.mu)
+                                                                          : gram_stage_elems<T>(a.mv);
   const size_t smem = sizeof(T) * (al4((size_t)a.mu * a.mu) + al4((size_t)a.mv * a.mv) +
                                    3 * al4((size_t)a.mu * a.mv) + g);
   NNC_CUDA_TRY(cudaFuncSetAttribute(hmat_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -799,34 +850,38 @@ int launch_core_m(const T* Y3, const T* F3, int UC, int N3, int m3, T* part, int
 
 template <typename T>
 int launch_core(const CoreArgs<T>& a, cudaStream_t s) {
-  const size_t smem = sizeof(T) * (al4((size_t)a.m1 * a.m1) + al4((size_t)a.m2 * a.m2) +
-                                   al4((size_t)a.m3 * a.m3) + 2 * al4((size_t)a.m2 * a.m3) +
-                                   gram_stage_elems(a.m3));
-  NNC_CUDA_TRY(cudaFuncSetAttribute(core_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kCoreCtas, 1, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kCoreCtas;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  NNC_CUDA_TRY(cudaLaunchKernelEx(&cfg, core_kernel<T>, a));
+  const size_t bc = (size_t)a.m2 * a.m3;
+  const size_t smem_a = sizeof(T) * (al4((size_t)a.m2 * a.m2) + al4((size_t)a.m3 * a.m3) +
+                                     2 * al4(bc) + gram_stage_elems<T>(a.m3));
+  NNC_CUDA_TRY(cudaFuncSetAttribute(core_a_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_a));
+  core_a_kernel<T><<<a.m1, kThreads, smem_a, s>>>(a);
   note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  const size_t smem_b = sizeof(T) * al4(bc);
+  NNC_CUDA_TRY(cudaFuncSetAttribute(core_b_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_b));
+  core_b_kernel<T><<<a.m1, kThreads, smem_b, s>>>(a);
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
   return NNC_OK;
 }
 
 template <typename T>
 int launch_gram(const T* F, int64_t N, int m, T* S, cudaStream_t s) {
-  const size_t smem = sizeof(T) * (al4((size_t)m * m) + gram_stage_elems(m));
+  const size_t smem = sizeof(T) * (al4((size_t)m * m) + gram_stage_elems<T>(m));
   NNC_CUDA_TRY(cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   gram_kernel<T><<<1, kThreads, smem, s>>>(F, N, m, S);
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  return NNC_OK;
+}
+
+template <typename T>
+int launch_permute_core(const T* G, int m1, int m2, int m3, T* G2, T* G3, cudaStream_t s) {
+  const int n = m1 * m2 * m3;
+  permute_core_kernel<T><<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(G, m1, m2, m3, G2, G3);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
   return NNC_OK;
@@ -843,7 +898,8 @@ int launch_gram(const T* F, int64_t N, int m, T* S, cudaStream_t s) {
   template int launch_core_m<T>(const T*, const T*, int, int, int, T*, int, int*,           \
                                 cudaStream_t);                                              \
   template int launch_core<T>(const CoreArgs<T>&, cudaStream_t);                            \
-  template int launch_gram<T>(const T*, int64_t, int, T*, cudaStream_t);
+  template int launch_gram<T>(const T*, int64_t, int, T*, cudaStream_t);                    \
+  template int launch_permute_core<T>(const T*, int, int, int, T*, T*, cudaStream_t);
 NNC_SWEEP_INST(float)
 NNC_SWEEP_INST(double)
 #undef NNC_SWEEP_INST

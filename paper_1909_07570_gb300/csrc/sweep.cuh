@@ -7,8 +7,6 @@
 
 namespace nnc {
 
-constexpr int kCoreCtas = 8;  // CTAs of the cluster that updates the core
-
 // One factor update (mode 1 or 2: Y from P3 by a small GEMM; mode 3: Y3 given).
 template <typename T>
 struct UpdArgs {
@@ -19,9 +17,9 @@ struct UpdArgs {
   const T* Fc;
   int len;      // contraction length (modes 1, 2)
   int mu, mc;   // Y_r is mu x mc
-  // Num[r, v] = sum_{u,c} Y_r[u, c] G[v gs_v + u gs_u + c]
-  const T* G;
-  int64_t gs_v, gs_u;
+  // Num[r, v] = <Y_r, Gn[v, :]> with Gn the core laid out (m_n, other two modes)
+  const T* Gn;
+  const T* G;   // mode 3: G viewed as (m1 m2) x m3
   // MU on F (nrows x mv) with Den = F H (H mv x mv)
   T* F;
   int64_t nrows;
@@ -36,13 +34,14 @@ struct UpdArgs {
 };
 
 // H_n = unfold_n(G x_u S_u x_v S_v) unfold_n(G)^T, one block per index p of mode n.
-// Slice p of G: element (u, v) at G[p sp + u su_s + v sv_s]. Each Gram comes
-// either ready (su / sv) or is formed from its factor (fu: nu x mu, fv: nv x mv).
+// Gn is the core laid out (m_n, u, v): slice p is the contiguous U x V block p.
+// Each Gram comes either ready (su / sv) or is formed from its factor
+// (fu: nu x mu, fv: nv x mv). The W slices go to Wout[p w_sp + u w_su + v w_sv].
 template <typename T>
 struct HArgs {
-  const T* G;
+  const T* Gn;
   int mp, mu, mv;
-  int64_t sp, su_s, sv_s;
+  int64_t w_sp, w_su, w_sv;
   const T* su;
   const T* fu;
   int64_t nu;
@@ -58,6 +57,8 @@ struct HArgs {
 template <typename T>
 struct CoreArgs {
   T* G;
+  T* G2;                // out: G permuted to (m2, m1, m3)
+  T* G3;                // out: G permuted to (m3, m1, m2)
   const T* M;           // M_splits partial numerators, each m1 x m2 x m3
   int M_splits;
   T* Mout;              // their sum
@@ -69,7 +70,8 @@ struct CoreArgs {
   T* S3_out;
   T* W1;                // out: G_new x_2 S2 x_3 S3
   T* H1;                // out: unfold_1(W1) unfold_1(G_new)^T
-  double* dots;         // 2 x kCoreCtas scratch
+  double* dots;         // m1 scratch
+  int* done;            // block counter of core_b, 0 between sweeps
   const double* x2;
   double* trace;
   int trace_stride;
@@ -101,5 +103,7 @@ template <typename T>
 int launch_core(const CoreArgs<T>& a, cudaStream_t s);
 template <typename T>
 int launch_gram(const T* F, int64_t N, int m, T* S, cudaStream_t s);
+template <typename T>
+int launch_permute_core(const T* G, int m1, int m2, int m3, T* G2, T* G3, cudaStream_t s);
 
 }  // namespace nnc
