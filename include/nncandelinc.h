@@ -46,11 +46,17 @@ extern "C" {
 #define NNC_ERR_TIMEOUT (-7)        /* a bounded device-side wait ran out      */
 
 typedef enum {
-  NNC_FP64 = 0,        /* double storage and arithmetic                      */
-  NNC_FP32 = 1,        /* float storage and arithmetic                       */
-  NNC_BF16_REFINE = 2  /* float storage; the two passes over X per sweep use
-                          a BF16 copy of X on the tensor cores with FP32
-                          accumulation, then `refine_iters` FP32 sweeps      */
+  NNC_FP64 = 0,        /* double storage and arithmetic (SIMT)               */
+  NNC_FP32 = 1,        /* float storage, FP32-accurate arithmetic: the two
+                          passes over X per sweep run on the tensor cores as
+                          three TF32 products per term (hi*hi + hi*lo + lo*hi
+                          of exact TF32 splits, FP32 accumulation); shapes the
+                          tensor-core path cannot take (N3 % 4 != 0) run the
+                          SIMT passes                                        */
+  NNC_BF16_REFINE = 2, /* float storage; the passes over X use a BF16 copy of
+                          X on the tensor cores (FP32 accumulation), then the
+                          last `refine_iters` sweeps are NNC_FP32 sweeps     */
+  NNC_FP32_SIMT = 3    /* as NNC_FP32 with every pass on FP32 FFMA (SIMT)    */
 } nnc_precision;
 
 typedef struct {
@@ -172,7 +178,9 @@ int nncp_core_fit_batched_noalloc(int n_jobs, const nncp_job* jobs, int precisio
  *  mode       0, 1 or 2 (index 0 is mode 1 of the paper)
  *  F          device, dims[mode] x Q row-major; 1 <= Q <= 64
  *  out        device, dims with dims[mode] replaced by Q, C order
- *  precision  NNC_FP64 (double) or NNC_FP32 (float): SIMT kernels.
+ *  precision  NNC_FP64 (double), NNC_FP32_SIMT (float): SIMT kernels.
+ *             NNC_FP32 (float): TF32x3 tensor cores for modes 0 and 2 (SIMT
+ *             for mode 1 or when N3 % 4 != 0).
  *             NNC_BF16_REFINE (float X, F, out): tensor cores on BF16 copies
  *             of X and F (X scaled per mode-1 slice by a power of two, which
  *             changes no rounding) with FP32 accumulation; modes 0 and 2 only.
@@ -211,10 +219,12 @@ int recon_residual(const void* X, int d, const int64_t* dims, int precision, int
  * sweep, the kernels that dominate ntd_fit. While enabled, ntd_fit records an
  * event pair around each pass on the stream that launches it and adds the
  * elapsed times to per-kind totals when the call ends. Kinds:
- *   0  X x_3 F^(3)T, SIMT path (NNC_FP32, NNC_FP64 and the FP32 refinement sweeps)
- *   1  X x_1 F^(1)T, SIMT path
- *   2  X x_3 F^(3)T, BF16 tensor-core path
- *   3  X x_1 F^(1)T, BF16 tensor-core path
+ *   0  X x_3 F^(3)T, SIMT passes (NNC_FP64, NNC_FP32_SIMT)
+ *   1  X x_1 F^(1)T, SIMT passes
+ *   2  X x_3 F^(3)T, BF16 tensor-core passes
+ *   3  X x_1 F^(1)T, BF16 tensor-core passes
+ *   4  X x_3 F^(3)T, TF32x3 tensor-core passes (NNC_FP32, refinement sweeps)
+ *   5  X x_1 F^(1)T, TF32x3 tensor-core passes
  * nnc_profile_enable(on) switches it and clears the totals; nnc_profile_read
  * returns the number of timed launches and their total milliseconds of a
  * kind. Meant for one thread of control: concurrent ntd_fit calls while it is

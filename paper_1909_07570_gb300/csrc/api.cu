@@ -137,11 +137,12 @@ int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precisi
     case NNC_FP64:
       return ntd_fit3<double>(static_cast<const double*>(X), dims, m, opts,
                               reinterpret_cast<double* const*>(F), static_cast<double*>(G),
-                              rel_err_trace, rel_err, s);
+                              rel_err_trace, rel_err, false, s);
     case NNC_FP32:
+    case NNC_FP32_SIMT:
       return ntd_fit3<float>(static_cast<const float*>(X), dims, m, opts,
                              reinterpret_cast<float* const*>(F), static_cast<float*>(G),
-                             rel_err_trace, rel_err, s);
+                             rel_err_trace, rel_err, precision == NNC_FP32, s);
     case NNC_BF16_REFINE:
       return ntd_fit3_bf16(static_cast<const float*>(X), dims, m, opts,
                            reinterpret_cast<float* const*>(F), static_cast<float*>(G),
@@ -172,7 +173,7 @@ int nncp_core_fit(const void* G, int d, const int* m, int r, int precision, cons
   int st;
   if (precision == NNC_FP64)
     st = nncp_run<double>(1, &job, opts, dev_err, s);
-  else if (precision == NNC_FP32 || precision == NNC_BF16_REFINE)
+  else if (precision == NNC_FP32 || precision == NNC_BF16_REFINE || precision == NNC_FP32_SIMT)
     st = nncp_run<float>(1, &job, opts, dev_err, s);
   else
     return NNC_ERR_INVALID_ARG;
@@ -192,7 +193,7 @@ int nncp_core_fit_batched(int n_jobs, const nncp_job* jobs, int precision, const
   if (n_jobs == 0) return NNC_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == NNC_FP64) return nncp_run<double>(n_jobs, jobs, opts, rel_errs, s);
-  if (precision == NNC_FP32 || precision == NNC_BF16_REFINE)
+  if (precision == NNC_FP32 || precision == NNC_BF16_REFINE || precision == NNC_FP32_SIMT)
     return nncp_run<float>(n_jobs, jobs, opts, rel_errs, s);
   return NNC_ERR_INVALID_ARG;
 }
@@ -210,15 +211,21 @@ int nnc_mode_product(const void* X, int d, const int64_t* dims, int mode, const 
   for (int n = mode + 1; n < 3; ++n) C *= dims[n];
   const int J = static_cast<int>(dims[mode]);
   Scratch sc(s);
-  if (precision == NNC_BF16_REFINE) {
+  if (precision == NNC_BF16_REFINE || (precision == NNC_FP32 && mode != 1)) {
     if (mode == 1) return NNC_ERR_UNSUPPORTED;
     tc::TcPlan plan;
-    NNC_TRY(plan.init(static_cast<const float*>(X), dims[0], dims[1], dims[2], Q, Q, sc, s));
-    if (mode == 2)
-      NNC_TRY(plan.pass3(static_cast<const float*>(F), static_cast<float*>(out), s));
-    else
-      NNC_TRY(plan.pass1(static_cast<const float*>(F), static_cast<float*>(out), s));
-    return plan.check(s);
+    const int kind = precision == NNC_BF16_REFINE ? tc::kKindBf16 : tc::kKindTf32x3;
+    const int st = plan.init(kind, static_cast<const float*>(X), dims[0], dims[1], dims[2], Q, Q,
+                             sc, s);
+    if (st == NNC_OK) {
+      if (mode == 2)
+        NNC_TRY(plan.pass3(static_cast<const float*>(F), static_cast<float*>(out), s));
+      else
+        NNC_TRY(plan.pass1(static_cast<const float*>(F), static_cast<float*>(out), s));
+      return plan.check(s);
+    }
+    if (st != NNC_ERR_UNSUPPORTED || precision == NNC_BF16_REFINE) return st;
+    // TF32x3 cannot take this shape: FP32 SIMT below.
   }
   const size_t cap = static_cast<size_t>(L * Q * C) * 8;
   if (precision == NNC_FP64) {
@@ -227,7 +234,7 @@ int nnc_mode_product(const void* X, int d, const int64_t* dims, int mode, const 
     NNC_CUDA_TRY(launch_ttm<double>(static_cast<const double*>(X), L, J, C,
                                     static_cast<const double*>(F), Q, 1, Q,
                                     static_cast<double*>(out), split, cap, s));
-  } else if (precision == NNC_FP32) {
+  } else if (precision == NNC_FP32 || precision == NNC_FP32_SIMT) {
     float* split = nullptr;
     NNC_TRY(sc.get(&split, cap));
     NNC_CUDA_TRY(launch_ttm<float>(static_cast<const float*>(X), L, J, C,
@@ -252,7 +259,8 @@ int candelinc_lift(int d, const int64_t* dims, const int* m, int r, int precisio
       NNC_CUDA_TRY(launch_lift<double>(static_cast<const double*>(F[n]),
                                        static_cast<const double*>(B[n]), dims[n], m[n], r,
                                        static_cast<double*>(A[n]), s));
-    } else if (precision == NNC_FP32 || precision == NNC_BF16_REFINE) {
+    } else if (precision == NNC_FP32 || precision == NNC_BF16_REFINE ||
+               precision == NNC_FP32_SIMT) {
       NNC_CUDA_TRY(launch_lift<float>(static_cast<const float*>(F[n]),
                                       static_cast<const float*>(B[n]), dims[n], m[n], r,
                                       static_cast<float*>(A[n]), s));
@@ -284,7 +292,8 @@ int recon_residual(const void* X, int d, const int64_t* dims, int precision, int
     NNC_TRY(residual3_device<double>(static_cast<const double*>(X), dims, model, m, r,
                                      reinterpret_cast<const double* const*>(factors),
                                      static_cast<const double*>(G), out2, sc, s));
-  } else if (precision == NNC_FP32 || precision == NNC_BF16_REFINE) {
+  } else if (precision == NNC_FP32 || precision == NNC_BF16_REFINE ||
+             precision == NNC_FP32_SIMT) {
     NNC_TRY(residual3_device<float>(static_cast<const float*>(X), dims, model, m, r,
                                     reinterpret_cast<const float* const*>(factors),
                                     static_cast<const float*>(G), out2, sc, s));

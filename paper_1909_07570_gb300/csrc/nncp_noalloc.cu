@@ -96,7 +96,7 @@ extern "C" int nncp_core_fit_batched_noalloc(int n_jobs, const nncp_job* jobs, i
   if (n_jobs == 0) return NNC_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == NNC_FP64) return run_noalloc<double>(n_jobs, jobs, opts, rel_errs, s);
-  if (precision == NNC_FP32 || precision == NNC_BF16_REFINE)
+  if (precision == NNC_FP32 || precision == NNC_BF16_REFINE || precision == NNC_FP32_SIMT)
     return run_noalloc<float>(n_jobs, jobs, opts, rel_errs, s);
   return NNC_ERR_INVALID_ARG;
 }

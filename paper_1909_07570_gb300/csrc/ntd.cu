@@ -19,9 +19,10 @@
 // the Gauss-Seidel order: pass 2 needs the F^(1) that pass 1 leads to.
 //
 // The sweep is captured once as a CUDA graph on a private stream and replayed;
-// the trace slot advances through a device counter. NNC_BF16_REFINE replays
-// the tensor-core sweep for iters - refine_iters sweeps and then the FP32
-// sweep for the rest.
+// the trace slot advances through a device counter. NNC_FP32 runs the passes
+// as FP32-accurate TF32x3 tensor-core products; NNC_BF16_REFINE replays the
+// BF16 tensor-core sweep for iters - refine_iters sweeps and then the TF32x3
+// sweep for the rest; NNC_FP32_SIMT and NNC_FP64 use the SIMT passes.
 #include <type_traits>
 #include <vector>
 
@@ -90,8 +91,10 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     if constexpr (std::is_same<T, float>::value) {
       if (tcp) {
         u.bt = tcp->Bt1;
+        u.bhi = tcp->B1hi;
+        u.blo = tcp->B1lo;
         u.bt_ld = tcp->kp1;
-        u.bt_scale = tcp->scale;
+        u.bt_scale = tcp->kind == tc::kKindBf16 ? tcp->scale : nullptr;
       }
     }
     NNC_TRY(launch_upd12<T>(u, s));
@@ -137,7 +140,9 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     if constexpr (std::is_same<T, float>::value) {
       if (tcp) {
         u.bt = tcp->Bt3;
-        u.bt_ld = tcp->kp3;
+        u.bhi = tcp->B3hi;
+        u.blo = tcp->B3lo;
+        u.bt_ld = tcp->kb3;
       }
     }
     NNC_TRY(launch_mode3<T>(u, b.num3part, b.n3splits, s));
@@ -200,7 +205,7 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
   NNC_CUDA_TRY(cudaEventRecord(g.fork, s));
   NNC_CUDA_TRY(cudaStreamWaitEvent(g.cs, g.fork, 0));
 
-  PassProfiler prof(tcp ? 2 : 0);
+  PassProfiler prof(tcp ? (tcp->kind == tc::kKindBf16 ? 2 : 4) : 0);
   const PassEvents* capture_ev = nullptr;
   if (profile_enabled()) {
     NNC_TRY(prof.init(count));
@@ -228,9 +233,12 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
   return NNC_OK;
 }
 
+// passes: 0 = SIMT for every sweep; 1 = TF32x3 tensor cores for every sweep
+// (FP32-accurate); 2 = BF16 tensor cores, then TF32x3 for the refinement sweeps.
+// A tensor-core plan that the shape does not allow falls back to SIMT passes.
 template <typename T>
 int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T* const* F,
-                  T* G, double* trace, double* rel_err, bool use_tc, cudaStream_t s) {
+                  T* G, double* trace, double* rel_err, int passes, cudaStream_t s) {
   const int64_t N1 = dims[0], N2 = dims[1], N3 = dims[2];
   const int m1 = m[0], m2 = m[1], m3 = m[2];
   const int64_t nX = N1 * N2 * N3;
@@ -277,12 +285,18 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
     NNC_TRY(sc.get(&b.H[k], (size_t)(m[k] * m[k])));
   }
 
-  tc::TcPlan plan;
-  const tc::TcPlan* tcp = nullptr;
+  tc::TcPlan plan16, plan32;
+  const tc::TcPlan* fast = nullptr;   // the first iters - refine sweeps
+  const tc::TcPlan* exact = nullptr;  // FP32-accurate sweeps
   if constexpr (std::is_same<T, float>::value) {
-    if (use_tc && o->iters > o->refine_iters) {
-      NNC_TRY(plan.init(X, N1, N2, N3, m1, m3, sc, s));
-      tcp = &plan;
+    if (passes == 2 && o->iters > o->refine_iters) {
+      NNC_TRY(plan16.init(tc::kKindBf16, X, N1, N2, N3, m1, m3, sc, s));
+      fast = &plan16;
+    }
+    if (passes >= 1 && (passes == 1 || o->refine_iters > 0)) {
+      const int st = plan32.init(tc::kKindTf32x3, X, N1, N2, N3, m1, m3, sc, s);
+      if (st == NNC_OK) exact = &plan32;
+      else if (st != NNC_ERR_UNSUPPORTED) return st;
     }
   }
 
@@ -297,15 +311,21 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
     NNC_TRY(launch_hmat<T>(h, s));
   }
   if constexpr (std::is_same<T, float>::value) {
-    if (tcp) NNC_TRY(tcp->pass3(F[2], b.P3, s, /*convert=*/true));  // builds Bt3
+    if (fast) NNC_TRY(fast->convert_b3(F[2], s));
+    if (exact && !fast) NNC_TRY(exact->convert_b3(F[2], s));
   }
   NNC_CUDA_TRY(cudaMemsetAsync(b.counter, 0, sizeof(int), s));
   NNC_CUDA_TRY(cudaMemsetAsync(b.done, 0, sizeof(int), s));
 
-  const int n_fast = tcp ? o->iters - o->refine_iters : 0;
-  NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, n_fast, tcp, s));
-  if (tcp) NNC_TRY(plan.check(s));
-  NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, o->iters - n_fast, nullptr, s));
+  const int n_fast = fast ? o->iters - o->refine_iters : 0;
+  NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, n_fast, fast, s));
+  if (fast) NNC_TRY(fast->check(s));
+  if constexpr (std::is_same<T, float>::value) {
+    // The FP32-accurate sweeps start from the factors the fast sweeps left.
+    if (exact && fast && o->iters - n_fast > 0) NNC_TRY(exact->convert_b3(F[2], s));
+  }
+  NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, o->iters - n_fast, exact, s));
+  if (exact) NNC_TRY(exact->check(s));
 
   if (rel_err) {
     const T* fac[3] = {F[0], F[1], F[2]};
@@ -322,18 +342,18 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
 
 template <typename T>
 int ntd_fit3(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T* const* F, T* G,
-             double* trace, double* rel_err, cudaStream_t s) {
-  return ntd_fit3_impl<T>(X, dims, m, o, F, G, trace, rel_err, false, s);
+             double* trace, double* rel_err, bool tensor_cores, cudaStream_t s) {
+  return ntd_fit3_impl<T>(X, dims, m, o, F, G, trace, rel_err, tensor_cores ? 1 : 0, s);
 }
 
 int ntd_fit3_bf16(const float* X, const int64_t* dims, const int* m, const nnc_opts* o,
                   float* const* F, float* G, double* trace, double* rel_err, cudaStream_t s) {
-  return ntd_fit3_impl<float>(X, dims, m, o, F, G, trace, rel_err, true, s);
+  return ntd_fit3_impl<float>(X, dims, m, o, F, G, trace, rel_err, 2, s);
 }
 
 template int ntd_fit3<float>(const float*, const int64_t*, const int*, const nnc_opts*,
-                             float* const*, float*, double*, double*, cudaStream_t);
+                             float* const*, float*, double*, double*, bool, cudaStream_t);
 template int ntd_fit3<double>(const double*, const int64_t*, const int*, const nnc_opts*,
-                              double* const*, double*, double*, double*, cudaStream_t);
+                              double* const*, double*, double*, double*, bool, cudaStream_t);
 
 }  // namespace nnc

@@ -14,7 +14,7 @@
 
 namespace nnc {
 
-constexpr int kProfileKinds = 4;
+constexpr int kProfileKinds = 6;
 
 struct PassEvents {
   cudaEvent_t start[2];
@@ -25,8 +25,8 @@ bool profile_enabled();
 
 class PassProfiler {
  public:
-  // kind_base: 0 for the SIMT passes (kinds 0, 1), 2 for the tensor-core
-  // passes (kinds 2, 3).
+  // kind_base: 0 for the SIMT passes (kinds 0, 1), 2 for the BF16
+  // tensor-core passes (kinds 2, 3), 4 for the TF32x3 ones (kinds 4, 5).
   explicit PassProfiler(int kind_base = 0) : kind_base_(kind_base) {}
   int init(int launches);                        // reserve 4 events per launch
   const PassEvents* capture_events() const { return &cap_; }

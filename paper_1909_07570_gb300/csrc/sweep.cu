@@ -43,6 +43,23 @@ __host__ __device__ constexpr int r4(int x) { return (x + 3) & ~3; }
 // (float4 / 2 x double2) stay 16-byte aligned.
 __host__ __device__ constexpr size_t al4(size_t x) { return (x + 3) & ~static_cast<size_t>(3); }
 
+// Writes the tensor-core operand entry of a new factor value (see UpdArgs).
+template <typename T>
+__device__ __forceinline__ void write_operand(const UpdArgs<T>& a, int64_t r, int v, T nv) {
+  if constexpr (std::is_same<T, float>::value) {
+    const float x = nv * (a.bt_scale ? a.bt_scale[r] : 1.f);
+    const int64_t idx = (int64_t)v * a.bt_ld + r;
+    if (a.bt) a.bt[idx] = __float2bfloat16_rn(x);
+    if (a.bhi) {
+      const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);  // exact TF32 part
+      uint32_t l;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - h));
+      a.bhi[idx] = h;
+      a.blo[idx] = __uint_as_float(l);
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T mu_step(T theta, T num, T den, T eps) {
   const T v = theta * num / (den > eps ? den : eps);
@@ -321,10 +338,7 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
     for (int w = 0; w < MV; ++w) den = fma(fo[rr * MV + w], hs[w * MV + v], den);
     const T nv = mu_step(fo[e], nm[e], den, (T)a.eps);
     a.F[r * MV + v] = nv;
-    if constexpr (std::is_same<T, float>::value) {
-      if (a.bt)
-        a.bt[(int64_t)v * a.bt_ld + r] = __float2bfloat16_rn(nv * (a.bt_scale ? a.bt_scale[r] : 1.f));
-    }
+    write_operand(a, r, v, nv);
   }
 }
 
@@ -523,9 +537,7 @@ __global__ void __launch_bounds__(kThreads) tail3_kernel(UpdArgs<T> a, const T* 
     for (int w = 0; w < MV; ++w) den = fma(fo[rr * MV + w], hs[w * MV + v], den);
     const T nv = mu_step(fo[e], num, den, (T)a.eps);
     a.F[r * MV + v] = nv;
-    if constexpr (std::is_same<T, float>::value) {
-      if (a.bt) a.bt[(int64_t)v * a.bt_ld + r] = __float2bfloat16_rn(nv);
-    }
+    write_operand(a, r, v, nv);
   }
 }
 
@@ -680,15 +692,21 @@ __global__ void __launch_bounds__(kThreads) core_b_kernel(CoreArgs<T> a) {
     last = (atomicAdd(a.done, 1) == m1 - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    const volatile T* H1 = a.H1;
-    double sm_mg = 0.0, sm_gd = 0.0;
-    for (int r = 0; r < m1; ++r) sm_mg += ((volatile double*)a.dots)[r];
-    for (int r = 0; r < m1; ++r)
-      for (int w = 0; w < m1; ++w) sm_gd += (double)a.S1[r * m1 + w] * (double)H1[w * m1 + r];
+  if (!last) return;
+  // Last block: every other block's H1 rows and dot are visible (fence +
+  // atomic above); L2 loads (__ldcg) bypass this SM's L1.
+  __threadfence();
+  double pg = 0.0, pm = 0.0;
+  for (int e = threadIdx.x; e < m1 * m1; e += blockDim.x) {
+    const int r = e / m1, w = e % m1;
+    pg += (double)a.S1[e] * (double)__ldcg(a.H1 + w * m1 + r);
+  }
+  for (int r = threadIdx.x; r < m1; r += blockDim.x) pm += __ldcg(a.dots + r);
+  pg = block_sum(pg, red);
+  pm = block_sum(pm, red);
+  if (threadIdx.x == 0) {
     const double xx = *a.x2;
-    double r2 = xx - 2.0 * sm_mg + sm_gd;
+    double r2 = xx - 2.0 * pm + pg;
     if (r2 < 0.0) r2 = 0.0;
     const int t = *a.counter;
     a.trace[(int64_t)t * a.trace_stride] = sqrt(r2 / xx);

@@ -27,8 +27,11 @@ struct UpdArgs {
   const T* H;
   double eps;
   int rows_per_block;
-  // Optional BF16 operand of the next tensor-core pass: bt[v bt_ld + r] = bf16(F[r, v] scale[r])
+  // Optional operand of the next tensor-core pass, entry [v bt_ld + r] for
+  // F[r, v] (times bt_scale[r] if given): BF16 (bt) or the TF32 pair (bhi, blo).
   __nv_bfloat16* bt;
+  float* bhi;
+  float* blo;
   int64_t bt_ld;
   const float* bt_scale;
 };

@@ -1,29 +1,35 @@
-// Tensor-core (tcgen05) mode products for the BF16 path: the two passes over X
-// of an nnTD sweep (n-mode multiplication, Appendix A).
+// Tensor-core (tcgen05) mode products: the two passes over X of an nnTD sweep
+// (n-mode multiplication, Appendix A), in two number formats.
 //
-// X is kept as a BF16 copy Xb with per-slice power-of-two scales s_i (mode-1
-// slices) and rows padded with zeros to Kp = roundup(N3, 64):
-//   Xb[(i N2 + j) Kp + k] = bf16(X[i, j, k] / s_i)            (k < N3)
-// Because s_i is a power of two, bf16(x / s_i) * s_i == bf16(x): the scaling
-// changes no rounding and only keeps slices of very different magnitude in
-// range.
+//   BF16    X is kept as a BF16 copy Xb with per-slice power-of-two scales s_i
+//           (mode-1 slices), rows padded with zeros to Kp = roundup(N3, 64):
+//             Xb[(i N2 + j) Kp + k] = bf16(X[i, j, k] / s_i)
+//           Since s_i is a power of two, bf16(x / s_i) s_i == bf16(x): the
+//           scales change no rounding. One BF16 MMA per K step, FP32 accumulate.
+//   TF32x3  FP32-accurate: X is read as FP32 and every operand is split into
+//           exact TF32 parts, x = x_hi + x_lo (x_hi: x with 13 low mantissa
+//           bits cleared; x_lo: x - x_hi rounded to TF32). Each K step issues
+//           x_hi f_hi + x_hi f_lo + x_lo f_hi into one FP32 accumulator; the
+//           dropped x_lo f_lo term and the rounding of the lo parts are about
+//           2^-21 of each product.
 //
-// Pass 1, P3 = X x_3 F3^T: D[r, q] = sum_k Xb[r, k] Bt3[q, k] with r = (i, j),
-//   A = Xb tile (128 rows x 64 k, K-major), B = Bt3 = bf16(F3^T) (NP x Kp);
-//   the epilogue multiplies row r by s_i.
-// Pass 2, P1 = X x_1 F1^T: D[c, a] = sum_i Xb[i, c] Bt1[a, i] with c = (j, k),
-//   A = Xb viewed as N1 x (N2 Kp) read MN-major (128 columns x 64 i),
-//   B = Bt1 = bf16(diag(s) F1)^T, so the scales ride on F1.
+// Pass 1, P3 = X x_3 F3^T: D[r, q] = sum_k A[r, k] B[q, k], r = (i, j), A K-major.
+// Pass 2, P1 = X x_1 F1^T: D[c, a] = sum_i A[c, i] B[a, i], c = (j, k). BF16:
+//   A read MN-major from Xb viewed as N1 x (N2 Kp). TF32x3: A read K-major
+//   from Xt, a transposed copy of X made once per fit.
+// B = F^T as operands [NP x K] (BF16: diag(s) folded into F1 for pass 2).
 //
-// One CTA computes one 128-row tile with a single tcgen05.mma accumulator of
-// NP (32 or 64) FP32 columns in tensor memory:
-//   warp 0 / lane 0  TMA producer: all of B once, then A through a 4-stage ring
-//   warp 1 / lane 0  MMA issuer: 4 MMAs (K = 16 each) per stage, tcgen05.commit
-//                    frees the stage; a final commit signals the accumulator
-//   all 4 warps      epilogue: tcgen05.ld (warp w owns TMEM lanes 32w..32w+31)
-// Shared-memory tiles use the 128-byte swizzle that TMA writes and the MMA
-// descriptors read. Every mbarrier wait is bounded; on time-out the CTA
-// records an error, waits (bounded) for its own copies and frees its TMEM.
+// Persistent CTAs, one per SM, each looping over 128-row tiles with warp roles:
+//   warp 0        TMA producer: A tile and B slice of each K stage (4-stage ring)
+//   warp 1        MMA issuer (one thread): tcgen05.mma into a double-buffered
+//                 TMEM accumulator (2 x NP FP32 columns); tcgen05.commit frees
+//                 stages and publishes finished accumulators
+//   warps 2-5     epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//                 lanes 32 (w % 4) ..), scaled stores to global memory
+//   warps 6-9     TF32x3 only: split each staged A tile into hi / lo in place
+// so a tile's epilogue overlaps the next tile's MMAs. Every mbarrier wait is
+// bounded (about 2 s); on time-out the CTA flags an error, the other roles
+// stop at their next wait, and TMEM is freed before the CTA exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -39,7 +45,8 @@ namespace tc {
 namespace {
 
 constexpr int kStages = 4;
-constexpr int kStageBytes = 128 * 64 * 2;  // one A tile: 128 x 64 bf16
+constexpr int kTileBytes = 128 * 128;  // one A stage: 128 rows x 128 bytes of K
+constexpr int kThreadsTc = 320;        // 10 warps
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -57,6 +64,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -69,11 +80,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on phase `parity`; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait on phase `parity`. False when the limit ran out or another role
+// of this CTA has already failed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (*fail) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      atomicExch(const_cast<int*>(fail), 1);
+      return false;
+    }
   }
   return true;
 }
@@ -94,8 +110,7 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: 128-byte swizzle, leading / stride byte
-// offsets as given, descriptor version 1.
+// Shared-memory matrix descriptor: 128-byte swizzle, descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
@@ -106,22 +121,33 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
-// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, M = 128, N = NP,
-// B K-major, A K-major or MN-major.
-template <bool kMN, int NP>
+// Instruction descriptor, FP32 accumulator, M = 128, N = NP, B K-major.
+// Operand format 1 = BF16 (kind::f16), 2 = TF32 (kind::tf32).
+template <int KIND, bool kMN, int NP>
 __device__ __forceinline__ uint32_t instr_desc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((kMN ? 1u : 0u) << 15) |
+  constexpr uint32_t fmt = KIND == kKindBf16 ? 1u : 2u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((kMN ? 1u : 0u) << 15) |
          (static_cast<uint32_t>(NP >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                    uint32_t idesc, uint32_t accumulate) {
+  if constexpr (KIND == kKindBf16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -146,34 +172,61 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <bool kMN, int NP>
-__global__ void __launch_bounds__(128, 1)
-ttm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              int nk, TcEpilogue ep, int* err) {
+// x_hi: x with the 13 low mantissa bits cleared (an exact TF32 value).
+__device__ __forceinline__ float tf32_hi(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+// The remainder x - x_hi rounded to TF32 (cvt.rna: to nearest, ties away).
+__device__ __forceinline__ float tf32_lo(float x, float hi) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x - hi));
+  return __uint_as_float(r);
+}
+
+template <int KIND, int NP>
+struct TcLayout {
+  static constexpr bool kTf32 = KIND == kKindTf32x3;
+  // TF32x3: K stages rotate over kAcc accumulators that the epilogue adds in
+  // FP32. The tensor core rounds its FP32 accumulation toward zero once per
+  // MMA; shorter chains shrink that bias by kAcc.
+  static constexpr int kAcc = kTf32 ? 128 / NP : 1;
+  static constexpr int kTmemCols = 2 * kAcc * NP;  // double-buffered
+  static constexpr int kKStage = kTf32 ? 32 : 64;  // K elements per stage (128 bytes)
+  static constexpr int kBBytes = NP * 128;         // one B slice
+  static constexpr int kStageBytes = kTileBytes * (kTf32 ? 2 : 1) + kBBytes * (kTf32 ? 2 : 1);
+  // Offsets inside one stage: A | A_lo | B | B_lo
+  static constexpr int kOffAlo = kTileBytes;
+  static constexpr int kOffB = kTileBytes * (kTf32 ? 2 : 1);
+  static constexpr int kOffBlo = kOffB + kBBytes;
+  static constexpr int kSmem = 1024 + kStages * kStageBytes;
+};
+
+template <int KIND, bool kMN, int NP>
+__global__ void __launch_bounds__(kThreadsTc, 1)
+tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmBlo, int nk, int64_t ntiles, TcEpilogue ep,
+               int* err) {
+  using L = TcLayout<KIND, NP>;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t bars[2 * kStages + 2];
+  __shared__ uint64_t full[kStages], empty[kStages], lofull[kStages], accfull[2], accempty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
 
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  unsigned char* sA = base;                        // kStages x 16 KB
-  unsigned char* sB = base + kStages * kStageBytes;  // nk x NP x 128 B
-  uint64_t* full = bars;
-  uint64_t* empty = bars + kStages;
-  uint64_t* bfull = bars + 2 * kStages;
-  uint64_t* accfull = bars + 2 * kStages + 1;
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * 128;
+  volatile int* vfail = &fail;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&lofull[s], 4);
     }
-    mbar_init(bfull, 1);
-    mbar_init(accfull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 4);
+    }
     fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -181,7 +234,7 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(NP)
+                 "r"(L::kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -190,98 +243,193 @@ ttm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---- TMA producer --------------------------------------------------------
-    mbar_expect_tx(bfull, static_cast<uint32_t>(nk) * NP * 128);
-    for (int c = 0; c < nk; ++c) tma_load_2d(sB + c * NP * 128, &tmB, c * 64, 0, bfull);
-    int issued = 0;
-    for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % kStages;
-      if (kc >= kStages && !mbar_wait(&empty[s], ((kc / kStages) - 1) & 1)) {
-        atomicExch(&fail, 1);
-        break;
+  if (warp == 0) {
+    // ---- TMA producer ----------------------------------------------------------
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int m0 = static_cast<int>(tile * 128);
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const int s = it % kStages;
+          if (it >= kStages && !mbar_wait(&empty[s], ((it / kStages) - 1) & 1, vfail)) {
+            ok = false;
+            break;
+          }
+          unsigned char* st = base + s * L::kStageBytes;
+          mbar_expect_tx(&full[s], kTileBytes + L::kBBytes * (L::kTf32 ? 2 : 1));
+          const int k0 = kc * L::kKStage;
+          if (!kMN) {
+            tma_load_2d(st, &tmA, k0, m0, &full[s]);
+          } else {
+            // 128 columns in 128-byte pieces: 2 (BF16) or 4 (TF32) boxes.
+            constexpr int pieces = L::kTf32 ? 4 : 2;
+            constexpr int piece_cols = 128 / pieces;
+#pragma unroll
+            for (int h = 0; h < pieces; ++h)
+              tma_load_2d(st + h * (kTileBytes / pieces), &tmA, m0 + h * piece_cols, k0, &full[s]);
+          }
+          tma_load_2d(st + L::kOffB, &tmB, k0, 0, &full[s]);
+          if constexpr (L::kTf32) tma_load_2d(st + L::kOffBlo, &tmBlo, k0, 0, &full[s]);
+        }
       }
-      mbar_expect_tx(&full[s], kStageBytes);
-      if (!kMN) {
-        tma_load_2d(sA + s * kStageBytes, &tmA, kc * 64, static_cast<int>(m0), &full[s]);
-      } else {
-        tma_load_2d(sA + s * kStageBytes, &tmA, static_cast<int>(m0), kc * 64, &full[s]);
-        tma_load_2d(sA + s * kStageBytes + kStageBytes / 2, &tmA, static_cast<int>(m0) + 64,
-                    kc * 64, &full[s]);
+      if (!ok) {
+        // Let the copies this CTA started land before it can exit (bounded).
+        for (int back = 1; back <= kStages && it - back >= 0; ++back) {
+          const int j = it - back;
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&full[j % kStages], (j / kStages) & 1) &&
+                 clock64() - t0 < kWaitCycles) {
+          }
+        }
       }
-      issued = kc + 1;
     }
-    if (fail) {
-      // Let this CTA's copies land before the CTA can exit.
-      mbar_wait(bfull, 0);
-      for (int kc = (issued > kStages ? issued - kStages : 0); kc < issued; ++kc)
-        mbar_wait(&full[kc % kStages], (kc / kStages) & 1);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer ----------------------------------------------------------
-    const uint32_t idesc = instr_desc<kMN, NP>();
-    bool ok = mbar_wait(bfull, 0);
-    for (int kc = 0; ok && kc < nk; ++kc) {
-      const int s = kc % kStages;
-      if (!mbar_wait(&full[s], (kc / kStages) & 1)) {
-        ok = false;
-        break;
+  } else if (warp == 1) {
+    // ---- MMA issuer --------------------------------------------------------------
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc<KIND, kMN, NP>();
+      int it = 0, tcount = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tcount) {
+        const int buf = tcount & 1;
+        if (tcount >= 2 && !mbar_wait(&accempty[buf], ((tcount >> 1) - 1) & 1, vfail)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc0 = tmem + buf * L::kAcc * NP;
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const uint32_t acc = acc0 + (kc % L::kAcc) * NP;
+          const int s = it % kStages;
+          const uint32_t ph = (it / kStages) & 1;
+          if (!mbar_wait(&full[s], ph, vfail) ||
+              (L::kTf32 && !mbar_wait(&lofull[s], ph, vfail))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(base + s * L::kStageBytes);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            // K-major: +32 bytes per K step inside the swizzled 128-byte rows.
+            // MN-major: +K-step rows of 128 bytes; column pieces LBO apart.
+            uint64_t adesc, alodesc;
+            if constexpr (kMN) {
+              constexpr uint32_t step = L::kTf32 ? 1024 : 2048;
+              constexpr uint32_t lbo = L::kTf32 ? kTileBytes / 4 : kTileBytes / 2;
+              adesc = smem_desc(st + kk * step, lbo, 1024);
+              alodesc = smem_desc(st + L::kOffAlo + kk * step, lbo, 1024);
+            } else {
+              adesc = smem_desc(st + kk * 32, 16, 1024);
+              alodesc = smem_desc(st + L::kOffAlo + kk * 32, 16, 1024);
+            }
+            const uint64_t bdesc = smem_desc(st + L::kOffB + kk * 32, 16, 1024);
+            const uint32_t accum = (kc >= L::kAcc || kk != 0) ? 1u : 0u;
+            mma<KIND>(acc, adesc, bdesc, idesc, accum);
+            if constexpr (L::kTf32) {
+              const uint64_t blodesc = smem_desc(st + L::kOffBlo + kk * 32, 16, 1024);
+              mma<KIND>(acc, adesc, blodesc, idesc, 1u);
+              mma<KIND>(acc, alodesc, bdesc, idesc, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&accfull[buf]);
       }
+    }
+  } else if (warp < 6) {
+    // ---- epilogue (warps 2-5) ------------------------------------------------
+    const int quarter = warp & 3;  // TMEM lanes 32 quarter .. 32 quarter + 31
+    int tcount = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
+      const int buf = tcount & 1;
+      // The warp-collective tcgen05.ld needs one decision for the whole warp.
+      if (!__all_sync(0xffffffffu, mbar_wait(&accfull[buf], (tcount >> 1) & 1, vfail))) break;
       tc_fence_after();
-      const uint32_t a0 = smem_u32(sA + s * kStageBytes);
-      const uint32_t b0 = smem_u32(sB + kc * NP * 128);
+      const int64_t row = tile * 128 + quarter * 32 + lane;
+      const int nacc = nk < L::kAcc ? nk : L::kAcc;  // accumulators this tile wrote
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        // K-major A: +32 B per K = 16 inside the swizzled 128 B row.
-        // MN-major A: +16 rows of 128 B per K = 16; the two 64-column halves
-        // of the tile are kStageBytes / 2 apart (leading byte offset).
-        const uint64_t adesc = kMN ? smem_desc(a0 + kk * 2048, kStageBytes / 2, 1024)
-                                   : smem_desc(a0 + kk * 32, 16, 1024);
-        const uint64_t bdesc = smem_desc(b0 + kk * 32, 16, 1024);
-        mma_bf16(tmem, adesc, bdesc, idesc, (kc | kk) != 0 ? 1u : 0u);
+      for (int c0 = 0; c0 < NP; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
+        tmem_ld32(tmem + buf * L::kAcc * NP + c0 + lanes, v);
+        for (int q = 1; q < nacc; ++q) {
+          uint32_t w[32];
+          tmem_ld32(tmem + (buf * L::kAcc + q) * NP + c0 + lanes, w);
+#pragma unroll
+          for (int t = 0; t < 32; ++t)
+            v[t] = __float_as_uint(__uint_as_float(v[t]) + __uint_as_float(w[t]));
+        }
+        if (!ep.p1_layout) {
+          if (row < ep.rows) {
+            const float sc = ep.row_scale ? ep.row_scale[row / ep.rows_per_slice] : 1.f;
+            float* o = ep.out + row * ep.q;
+            if ((ep.q & 3) == 0) {
+#pragma unroll
+              for (int t = 0; t < 32; t += 4)
+                if (c0 + t < ep.q)
+                  *reinterpret_cast<float4*>(o + c0 + t) =
+                      make_float4(__uint_as_float(v[t]) * sc, __uint_as_float(v[t + 1]) * sc,
+                                  __uint_as_float(v[t + 2]) * sc, __uint_as_float(v[t + 3]) * sc);
+            } else {
+#pragma unroll
+              for (int t = 0; t < 32; ++t)
+                if (c0 + t < ep.q) o[c0 + t] = __uint_as_float(v[t]) * sc;
+            }
+          }
+        } else {
+          const int64_t j = row / ep.kp, k = row % ep.kp;
+          if (j < ep.n2 && k < ep.n3) {
+            float* o = ep.out + j * ep.n3 + k;
+#pragma unroll
+            for (int t = 0; t < 32; ++t)
+              if (c0 + t < ep.q) o[static_cast<int64_t>(c0 + t) * ep.slab] = __uint_as_float(v[t]);
+          }
+        }
       }
-      mma_commit(&empty[s]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accempty[buf]);
     }
-    if (!ok) atomicExch(&fail, 1);
-    mma_commit(accfull);  // fires once every MMA issued above has completed
+  } else if (L::kTf32) {
+    // ---- TF32 split of A (warps 6-9): A <- A_hi in place, A_lo beside it -------
+    const int ct = threadIdx.x - 192;  // 0 .. 127
+    int it = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      for (int kc = 0; kc < nk; ++kc, ++it) {
+        const int s = it % kStages;
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (it / kStages) & 1, vfail))) {
+          ok = false;
+          break;
+        }
+        float4* a = reinterpret_cast<float4*>(base + s * L::kStageBytes);
+        float4* alo = reinterpret_cast<float4*>(base + s * L::kStageBytes + L::kOffAlo);
+#pragma unroll
+        for (int e = ct; e < kTileBytes / 16; e += 128) {
+          float4 x = a[e], h, l;
+          h.x = tf32_hi(x.x); l.x = tf32_lo(x.x, h.x);
+          h.y = tf32_hi(x.y); l.y = tf32_lo(x.y, h.y);
+          h.z = tf32_hi(x.z); l.z = tf32_lo(x.z, h.z);
+          h.w = tf32_hi(x.w); l.w = tf32_lo(x.w, h.w);
+          a[e] = h;
+          alo[e] = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&lofull[s]);
+      }
+    }
   }
-  __syncwarp();
 
-  // ---- epilogue: TMEM -> registers -> global ---------------------------------
-  const bool have = mbar_wait(accfull, 0);
-  tc_fence_after();
-  if (!have) atomicExch(&fail, 1);
-  __syncthreads();
-  if (!fail) {
-    const int64_t row = m0 + warp * 32 + lane;
-#pragma unroll
-    for (int c0 = 0; c0 < NP; c0 += 32) {
-      uint32_t v[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
-      if (!kMN) {
-        if (row < ep.rows) {
-          const float sc = ep.row_scale[row / ep.rows_per_slice];
-          float* o = ep.out + row * ep.q;
-#pragma unroll
-          for (int t = 0; t < 32; ++t)
-            if (c0 + t < ep.q) o[c0 + t] = __uint_as_float(v[t]) * sc;
-        }
-      } else {
-        const int64_t j = row / ep.kp, k = row % ep.kp;
-        if (j < ep.n2 && k < ep.n3) {
-          float* o = ep.out + j * ep.n3 + k;
-#pragma unroll
-          for (int t = 0; t < 32; ++t)
-            if (c0 + t < ep.q) o[static_cast<int64_t>(c0 + t) * ep.slab] = __uint_as_float(v[t]);
-        }
-      }
-    }
-  }
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && fail) atomicExch(err, 1);
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NP)
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(L::kTmemCols)
                  : "memory");
   }
 }
@@ -325,16 +473,39 @@ __global__ void x_to_bf16_kernel(const float* __restrict__ X, int64_t rows, int 
   }
 }
 
-// Bt[q, k] = bf16(F[k, q] * (scale ? scale[k] : 1)), zero outside q < m, k < n.
-__global__ void factor_bt_kernel(const float* __restrict__ F, int n, int m, int kpad, int np,
-                                 const float* __restrict__ scale, __nv_bfloat16* __restrict__ Bt) {
+// B operands of a factor F (n x m): Bt[q, k] = F[k, q] * (scale ? scale[k] : 1)
+// as BF16 (bt16), or as the TF32 pair (bhi, blo); zero outside q < m, k < n.
+__global__ void factor_b_kernel(const float* __restrict__ F, int n, int m, int kpad, int np,
+                                const float* __restrict__ scale, __nv_bfloat16* __restrict__ bt16,
+                                float* __restrict__ bhi, float* __restrict__ blo) {
   const int64_t tot = static_cast<int64_t>(np) * kpad;
   for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < tot;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int q = static_cast<int>(e / kpad), k = static_cast<int>(e % kpad);
     float v = 0.f;
     if (q < m && k < n) v = F[static_cast<int64_t>(k) * m + q] * (scale ? scale[k] : 1.f);
-    Bt[e] = __float2bfloat16_rn(v);
+    if (bt16) bt16[e] = __float2bfloat16_rn(v);
+    if (bhi) {
+      const float h = tf32_hi(v);
+      bhi[e] = h;
+      blo[e] = tf32_lo(v, h);
+    }
+  }
+}
+
+// Xt[c, i] = X[i, c] (X viewed N1 x C, Xt row length ldt >= N1, zero padded).
+__global__ void transpose_kernel(const float* __restrict__ X, int64_t N1, int64_t C, int64_t ldt,
+                                 float* __restrict__ Xt) {
+  __shared__ float tile[32][33];
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * 32, i0 = static_cast<int64_t>(blockIdx.y) * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = i0 + r, c = c0 + threadIdx.x;
+    tile[r][threadIdx.x] = (i < N1 && c < C) ? X[i * C + c] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t c = c0 + r, i = i0 + threadIdx.x;
+    if (c < C && i < ldt) Xt[c * ldt + i] = tile[threadIdx.x][r];
   }
 }
 
@@ -352,8 +523,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-int make_map(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t outer,
-             uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+int make_map(CUtensorMap* tm, CUtensorMapDataType dt, const void* base, uint64_t inner,
+             uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (enc == nullptr) {
     set_error_detail_text("cuTensorMapEncodeTiled is not available from the driver");
@@ -363,8 +534,8 @@ int make_map(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t outer,
   const cuuint64_t strides[1] = {row_bytes};
   const cuuint32_t box[2] = {box_inner, box_outer};
   const cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  CUresult r = enc(tm, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     char buf[160];
@@ -377,102 +548,157 @@ int make_map(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t outer,
   return NNC_OK;
 }
 
-size_t smem_bytes(int nk, int np) {
-  return 1024 + static_cast<size_t>(kStages) * kStageBytes + static_cast<size_t>(nk) * np * 128;
-}
-
-template <bool kMN, int NP>
-int launch_pass(const CUtensorMap& a, const CUtensorMap& b, int nk, int64_t tiles,
-                const TcEpilogue& ep, int* err, cudaStream_t s) {
-  const size_t smem = smem_bytes(nk, NP);
-  NNC_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<kMN, NP>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(smem)));
-  ttm_tc_kernel<kMN, NP><<<static_cast<unsigned>(tiles), 128, smem, s>>>(a, b, nk, ep, err);
+template <int KIND, bool kMN, int NP>
+int launch_pass(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& blo, int nk,
+                int64_t tiles, const TcEpilogue& ep, int* err, cudaStream_t s) {
+  constexpr int smem = TcLayout<KIND, NP>::kSmem;
+  NNC_CUDA_TRY(cudaFuncSetAttribute(tc_pass_kernel<KIND, kMN, NP>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int64_t grid = device_sm_count();
+  if (grid > tiles) grid = tiles;
+  tc_pass_kernel<KIND, kMN, NP><<<static_cast<unsigned>(grid), kThreadsTc, smem, s>>>(
+      a, b, blo, nk, tiles, ep, err);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
   return NNC_OK;
 }
 
+template <int KIND, bool kMN>
+int launch_np(int np, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& blo, int nk,
+              int64_t tiles, const TcEpilogue& ep, int* err, cudaStream_t s) {
+  if (np == 32) return launch_pass<KIND, kMN, 32>(a, b, blo, nk, tiles, ep, err, s);
+  return launch_pass<KIND, kMN, 64>(a, b, blo, nk, tiles, ep, err, s);
+}
+
 }  // namespace
 
-int TcPlan::init(const float* X, int64_t N1_, int64_t N2_, int64_t N3_, int m1_, int m3_,
-                 Scratch& sc, cudaStream_t s) {
+int TcPlan::init(int kind_, const float* X, int64_t N1_, int64_t N2_, int64_t N3_, int m1_,
+                 int m3_, Scratch& sc, cudaStream_t s) {
+  kind = kind_;
   N1 = N1_;
   N2 = N2_;
   N3 = N3_;
   m1 = m1_;
   m3 = m3_;
-  kp3 = static_cast<int>(ceil_div(N3, 64) * 64);
-  kp1 = static_cast<int>(ceil_div(N1, 64) * 64);
   np1 = m1 <= 32 ? 32 : 64;
   np3 = m3 <= 32 ? 32 : 64;
-  if (m1 > 64 || m3 > 64 || smem_bytes(kp3 / 64, np3) > 220 * 1024 ||
-      smem_bytes(kp1 / 64, np1) > 220 * 1024 || N1 * N2 > (1LL << 31) ||
-      N2 * kp3 > (1LL << 31)) {
-    set_error_detail_text("NNC_BF16_REFINE: shape outside the tensor-core path (m <= 64, "
-                          "N1 and N3 <= 1600)");
+  const int kstage = kind == kKindBf16 ? 64 : 32;
+  // K of pass 1 is N3 (BF16: padded rows of Xb), K of pass 2 is N1.
+  kp3 = kind == kKindBf16 ? static_cast<int>(ceil_div(N3, 64) * 64) : static_cast<int>(N3);
+  kb3 = static_cast<int>(ceil_div(N3, kstage) * kstage);
+  kp1 = static_cast<int>(ceil_div(N1, kstage) * kstage);
+  if (m1 > 64 || m3 > 64 || N1 * N2 > (1LL << 31) || N2 * kp3 > (1LL << 31)) {
+    set_error_detail_text("tensor-core pass: shape outside the path (m <= 64)");
+    return NNC_ERR_UNSUPPORTED;
+  }
+  if (kind == kKindTf32x3 && (N3 % 4) != 0) {
+    set_error_detail_text("tensor-core TF32 pass: N3 must be a multiple of 4");
     return NNC_ERR_UNSUPPORTED;
   }
   const int64_t rows = N1 * N2;
-  NNC_TRY(sc.get(&Xb, static_cast<size_t>(rows * kp3)));
-  NNC_TRY(sc.get(&scale, static_cast<size_t>(N1)));
-  NNC_TRY(sc.get(&inv_scale, static_cast<size_t>(N1)));
-  NNC_TRY(sc.get(&Bt1, static_cast<size_t>(np1) * kp1));
-  NNC_TRY(sc.get(&Bt3, static_cast<size_t>(np3) * kp3));
   NNC_TRY(sc.get(&err, 1));
   NNC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-  NNC_CUDA_TRY(cudaMemsetAsync(Bt1, 0, sizeof(__nv_bfloat16) * np1 * kp1, s));
-  NNC_CUDA_TRY(cudaMemsetAsync(Bt3, 0, sizeof(__nv_bfloat16) * np3 * kp3, s));
-  slice_scale_kernel<<<static_cast<unsigned>(N1), 256, 0, s>>>(X, N2 * N3, scale, inv_scale);
-  note_launch(s);
-  const int64_t n = rows * kp3;
-  const unsigned blocks = static_cast<unsigned>(ceil_div(n, 256) < 16384 ? ceil_div(n, 256) : 16384);
-  x_to_bf16_kernel<<<blocks, 256, 0, s>>>(X, rows, static_cast<int>(N3), kp3,
-                                         static_cast<int>(N2), inv_scale, Xb);
+  NNC_TRY(sc.get(&scale, static_cast<size_t>(N1)));
+  NNC_TRY(sc.get(&inv_scale, static_cast<size_t>(N1)));
+  if (kind == kKindBf16) {
+    NNC_TRY(sc.get(&Xb, static_cast<size_t>(rows * kp3)));
+    NNC_TRY(sc.get(&Bt1, static_cast<size_t>(np1) * kp1));
+    NNC_TRY(sc.get(&Bt3, static_cast<size_t>(np3) * kb3));
+    NNC_CUDA_TRY(cudaMemsetAsync(Bt1, 0, sizeof(__nv_bfloat16) * np1 * kp1, s));
+    NNC_CUDA_TRY(cudaMemsetAsync(Bt3, 0, sizeof(__nv_bfloat16) * np3 * kb3, s));
+    slice_scale_kernel<<<static_cast<unsigned>(N1), 256, 0, s>>>(X, N2 * N3, scale, inv_scale);
+    note_launch(s);
+    const int64_t n = rows * kp3;
+    const unsigned blocks =
+        static_cast<unsigned>(ceil_div(n, 256) < 16384 ? ceil_div(n, 256) : 16384);
+    x_to_bf16_kernel<<<blocks, 256, 0, s>>>(X, rows, static_cast<int>(N3), kp3,
+                                           static_cast<int>(N2), inv_scale, Xb);
+    note_launch(s);
+    NNC_CUDA_TRY(cudaGetLastError());
+    const CUtensorMapDataType bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    NNC_TRY(make_map(&mapA3, bf, Xb, kp3, rows, static_cast<uint64_t>(kp3) * 2, 64, 128));
+    NNC_TRY(make_map(&mapB3, bf, Bt3, kb3, np3, static_cast<uint64_t>(kb3) * 2, 64, np3));
+    NNC_TRY(make_map(&mapA1, bf, Xb, static_cast<uint64_t>(N2) * kp3, N1,
+                     static_cast<uint64_t>(N2) * kp3 * 2, 64, 64));
+    NNC_TRY(make_map(&mapB1, bf, Bt1, kp1, np1, static_cast<uint64_t>(kp1) * 2, 64, np1));
+    mapB3lo = mapB3;
+    mapB1lo = mapB1;
+  } else {
+    NNC_TRY(sc.get(&B1hi, static_cast<size_t>(np1) * kp1));
+    NNC_TRY(sc.get(&B1lo, static_cast<size_t>(np1) * kp1));
+    NNC_TRY(sc.get(&B3hi, static_cast<size_t>(np3) * kb3));
+    NNC_TRY(sc.get(&B3lo, static_cast<size_t>(np3) * kb3));
+    NNC_CUDA_TRY(cudaMemsetAsync(B1hi, 0, sizeof(float) * np1 * kp1, s));
+    NNC_CUDA_TRY(cudaMemsetAsync(B1lo, 0, sizeof(float) * np1 * kp1, s));
+    NNC_CUDA_TRY(cudaMemsetAsync(B3hi, 0, sizeof(float) * np3 * kb3, s));
+    NNC_CUDA_TRY(cudaMemsetAsync(B3lo, 0, sizeof(float) * np3 * kb3, s));
+    scale = nullptr;
+    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    NNC_TRY(make_map(&mapA3, f32, X, N3, rows, static_cast<uint64_t>(N3) * 4, 32, 128));
+    NNC_TRY(make_map(&mapB3, f32, B3hi, kb3, np3, static_cast<uint64_t>(kb3) * 4, 32, np3));
+    NNC_TRY(make_map(&mapB3lo, f32, B3lo, kb3, np3, static_cast<uint64_t>(kb3) * 4, 32, np3));
+    // Pass 2 reads Xt = X viewed (N1 x N2 N3), transposed: K-major rows of N1p.
+    const int64_t C = N2 * N3, n1p = ceil_div(N1, 4) * 4;
+    NNC_TRY(sc.get(&Xt, static_cast<size_t>(C * n1p)));
+    dim3 tgrid(static_cast<unsigned>(ceil_div(C, 32)), static_cast<unsigned>(ceil_div(n1p, 32)));
+    transpose_kernel<<<tgrid, dim3(32, 8), 0, s>>>(X, N1, C, n1p, Xt);
+    note_launch(s);
+    NNC_CUDA_TRY(cudaGetLastError());
+    NNC_TRY(make_map(&mapA1, f32, Xt, n1p, C, static_cast<uint64_t>(n1p) * 4, 32, 128));
+    NNC_TRY(make_map(&mapB1, f32, B1hi, kp1, np1, static_cast<uint64_t>(kp1) * 4, 32, np1));
+    NNC_TRY(make_map(&mapB1lo, f32, B1lo, kp1, np1, static_cast<uint64_t>(kp1) * 4, 32, np1));
+  }
+  return NNC_OK;
+}
+
+int TcPlan::convert_b3(const float* F3, cudaStream_t s) const {
+  factor_b_kernel<<<64, 256, 0, s>>>(F3, static_cast<int>(N3), m3, kb3, np3, nullptr, Bt3, B3hi,
+                                     B3lo);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
-  NNC_TRY(make_map(&mapA3, Xb, kp3, rows, static_cast<uint64_t>(kp3) * 2, 64, 128));
-  NNC_TRY(make_map(&mapB3, Bt3, kp3, np3, static_cast<uint64_t>(kp3) * 2, 64, np3));
-  NNC_TRY(make_map(&mapA1, Xb, static_cast<uint64_t>(N2) * kp3, N1,
-                   static_cast<uint64_t>(N2) * kp3 * 2, 64, 64));
-  NNC_TRY(make_map(&mapB1, Bt1, kp1, np1, static_cast<uint64_t>(kp1) * 2, 64, np1));
+  return NNC_OK;
+}
+
+int TcPlan::convert_b1(const float* F1, cudaStream_t s) const {
+  factor_b_kernel<<<64, 256, 0, s>>>(F1, static_cast<int>(N1), m1, kp1, np1,
+                                     kind == kKindBf16 ? scale : nullptr, Bt1, B1hi, B1lo);
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
   return NNC_OK;
 }
 
 int TcPlan::pass3(const float* F3, float* P3, cudaStream_t s, bool convert) const {
-  if (convert) {
-    factor_bt_kernel<<<64, 256, 0, s>>>(F3, static_cast<int>(N3), m3, kp3, np3, nullptr, Bt3);
-    note_launch(s);
-    NNC_CUDA_TRY(cudaGetLastError());
-  }
+  if (convert) NNC_TRY(convert_b3(F3, s));
   TcEpilogue ep{};
   ep.out = P3;
   ep.q = m3;
   ep.rows = N1 * N2;
   ep.rows_per_slice = N2;
-  ep.row_scale = scale;
+  ep.row_scale = kind == kKindBf16 ? scale : nullptr;
   const int64_t tiles = ceil_div(N1 * N2, 128);
-  if (np3 == 32) return launch_pass<false, 32>(mapA3, mapB3, kp3 / 64, tiles, ep, err, s);
-  return launch_pass<false, 64>(mapA3, mapB3, kp3 / 64, tiles, ep, err, s);
+  const int stagek = kind == kKindBf16 ? 64 : 32;
+  const int nk = static_cast<int>(ceil_div(N3, stagek));
+  if (kind == kKindBf16)
+    return launch_np<kKindBf16, false>(np3, mapA3, mapB3, mapB3lo, nk, tiles, ep, err, s);
+  return launch_np<kKindTf32x3, false>(np3, mapA3, mapB3, mapB3lo, nk, tiles, ep, err, s);
 }
 
 int TcPlan::pass1(const float* F1, float* P1, cudaStream_t s, bool convert) const {
-  if (convert) {
-    factor_bt_kernel<<<64, 256, 0, s>>>(F1, static_cast<int>(N1), m1, kp1, np1, scale, Bt1);
-    note_launch(s);
-    NNC_CUDA_TRY(cudaGetLastError());
-  }
+  if (convert) NNC_TRY(convert_b1(F1, s));
   TcEpilogue ep{};
   ep.out = P1;
   ep.q = m1;
+  ep.p1_layout = 1;
   ep.kp = kp3;
   ep.n2 = N2;
   ep.n3 = N3;
   ep.slab = N2 * N3;
   const int64_t tiles = ceil_div(N2 * kp3, 128);
-  if (np1 == 32) return launch_pass<true, 32>(mapA1, mapB1, kp1 / 64, tiles, ep, err, s);
-  return launch_pass<true, 64>(mapA1, mapB1, kp1 / 64, tiles, ep, err, s);
+  const int stagek = kind == kKindBf16 ? 64 : 32;
+  const int nk = static_cast<int>(ceil_div(N1, stagek));
+  if (kind == kKindBf16)
+    return launch_np<kKindBf16, true>(np1, mapA1, mapB1, mapB1lo, nk, tiles, ep, err, s);
+  return launch_np<kKindTf32x3, false>(np1, mapA1, mapB1, mapB1lo, nk, tiles, ep, err, s);
 }
 
 int TcPlan::check(cudaStream_t s) const {

@@ -1,4 +1,4 @@
-// Tensor-core passes over X for the BF16 path (tc_ttm.cu).
+// Tensor-core passes over X (tc_ttm.cu): BF16, and FP32-accurate TF32x3.
 #pragma once
 
 #include <cuda.h>
@@ -9,38 +9,53 @@
 namespace nnc {
 namespace tc {
 
+constexpr int kKindBf16 = 0;
+constexpr int kKindTf32x3 = 1;
+
 // Where and how the epilogue writes one pass's FP32 result.
 struct TcEpilogue {
   float* out;
   int q;                  // output columns written (m_n)
   // pass X x_3 F3^T: out is rows x q, row r scaled by row_scale[r / rows_per_slice]
+  // (row_scale NULL: no scaling)
   int64_t rows;
   int64_t rows_per_slice;
   const float* row_scale;
-  // pass X x_1 F1^T: tile row c = (j, k) of the padded N2 x kp layout; out is
-  // q x n2 x n3 (slab = n2 n3)
+  // pass X x_1 F1^T (p1_layout): tile row c = (j, k) of the N2 x kp layout
+  // (kp = padded row length of the operand view); out is q x n2 x n3
+  // (slab = n2 n3)
+  int p1_layout;
   int64_t kp, n2, n3, slab;
 };
 
-// The BF16 copy of a 3-way FP32 X with its slice scales, the BF16 operand
-// buffers of F^(3)T and F^(1)T, and the TMA descriptors of both passes.
+// Operands and TMA descriptors of the two passes over a 3-way FP32 X.
+//   BF16:   a BF16 copy Xb of X (per-slice power-of-two scales, rows padded to a
+//           multiple of 64) and BF16 operands Bt1, Bt3 of F^(1), F^(3).
+//   TF32x3: X itself for pass 1, a transposed copy Xt (N2 N3 x N1p, i
+//           contiguous) so that pass 2 is K-major too, and hi / lo TF32
+//           operands B1hi/B1lo, B3hi/B3lo.
+// B operands are [np x k] row-major, zero outside the factor.
 struct TcPlan {
+  int kind = kKindBf16;
   int64_t N1 = 0, N2 = 0, N3 = 0;
-  int m1 = 0, m3 = 0, kp1 = 0, kp3 = 0, np1 = 0, np3 = 0;
+  int m1 = 0, m3 = 0, kp1 = 0, kp3 = 0, kb3 = 0, np1 = 0, np3 = 0;
   __nv_bfloat16 *Xb = nullptr, *Bt1 = nullptr, *Bt3 = nullptr;
+  float *B1hi = nullptr, *B1lo = nullptr, *B3hi = nullptr, *B3lo = nullptr, *Xt = nullptr;
   float *scale = nullptr, *inv_scale = nullptr;
   int* err = nullptr;
-  CUtensorMap mapA3, mapB3, mapA1, mapB1;
+  CUtensorMap mapA3, mapB3, mapB3lo, mapA1, mapB1, mapB1lo;
 
-  // Builds Xb and the scales from X (stream-ordered). UNSUPPORTED when the
-  // shape is outside the path (m_n > 64, or a factor too long for one CTA's
-  // shared memory).
-  int init(const float* X, int64_t N1, int64_t N2, int64_t N3, int m1, int m3, Scratch& sc,
-           cudaStream_t s);
-  // P3 = X x_3 F3^T ((N1 N2) x m3, FP32). With convert, Bt3 is first built
-  // from F3; without, Bt3 already holds bf16(F3^T) (written by the sweep).
+  // Builds the operand buffers (BF16: Xb and the scales) from X, stream-ordered.
+  // UNSUPPORTED when the shape is outside the path (m_n > 64; TF32x3 also
+  // needs N3 % 4 == 0 for its TMA row strides).
+  int init(int kind, const float* X, int64_t N1, int64_t N2, int64_t N3, int m1, int m3,
+           Scratch& sc, cudaStream_t s);
+  // B operands from the current factor (BF16: F^(1) scaled by s).
+  int convert_b3(const float* F3, cudaStream_t s) const;
+  int convert_b1(const float* F1, cudaStream_t s) const;
+  // P3 = X x_3 F3^T ((N1 N2) x m3, FP32); convert first builds the B operand.
   int pass3(const float* F3, float* P3, cudaStream_t s, bool convert = true) const;
-  // P1 = X x_1 F1^T (m1 x N2 x N3, FP32); Bt1 as above, from diag(s) F1.
+  // P1 = X x_1 F1^T (m1 x N2 x N3, FP32).
   int pass1(const float* F1, float* P1, cudaStream_t s, bool convert = true) const;
   // Synchronises s and turns a device-side pipeline time-out into NNC_ERR_TIMEOUT.
   int check(cudaStream_t s) const;

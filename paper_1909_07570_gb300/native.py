@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-NNC_FP64, NNC_FP32, NNC_BF16_REFINE = 0, 1, 2
+NNC_FP64, NNC_FP32, NNC_BF16_REFINE, NNC_FP32_SIMT = 0, 1, 2, 3
 
 _STATUS = {
     0: "ok", -1: "invalid argument", -2: "negative input", -3: "non-finite value",
@@ -117,7 +117,8 @@ def _require(t, dtype, name):
 def _precision(X, precision):
     if precision is None:
         precision = "fp64" if X.dtype == torch.float64 else "fp32"
-    code = {"fp64": NNC_FP64, "fp32": NNC_FP32, "bf16": NNC_BF16_REFINE}[precision]
+    code = {"fp64": NNC_FP64, "fp32": NNC_FP32, "bf16": NNC_BF16_REFINE,
+            "fp32_simt": NNC_FP32_SIMT}[precision]
     dtype = torch.float64 if code == NNC_FP64 else torch.float32
     return code, dtype
 
@@ -259,7 +260,8 @@ def recon_residual(X, factors, G=None, stream=None):
     return rn.value, xn.value
 
 
-PASS_KINDS = {0: "simt_x3", 1: "simt_x1", 2: "tc_x3", 3: "tc_x1"}
+PASS_KINDS = {0: "simt_x3", 1: "simt_x1", 2: "tc_bf16_x3", 3: "tc_bf16_x1", 4: "tc_tf32x3_x3",
+              5: "tc_tf32x3_x1"}
 
 
 def nnc_profile_enable(on=True):

@@ -37,10 +37,27 @@ def test_mode_product_simt(dims, Q):
     for mode in range(3):
         F = rng.random((dims[mode], Q))
         ref = orc.mode_product(X, F.T, mode)
-        for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        for dt, prec, tol in ((torch.float64, "fp64", 1e-12), (torch.float32, "fp32_simt", 1e-5)):
             Y = native.mode_product(torch.tensor(X, dtype=dt, device="cuda"),
-                                    torch.tensor(F, dtype=dt, device="cuda"), mode)
+                                    torch.tensor(F, dtype=dt, device="cuda"), mode, precision=prec)
             _close(Y.double().cpu().numpy(), ref, tol)
+
+
+@pytest.mark.parametrize("dims,Q", [((37, 29, 24), 5), ((200, 150, 132), 20), ((256, 256, 256), 32),
+                                    ((70, 45, 600), 64), ((129, 3, 64), 17), ((300, 7, 36), 33)])
+def test_mode_product_tf32x3_is_fp32_accurate(dims, Q):
+    # Three TF32 products per term with FP32 accumulation: the error bound is the
+    # FP32 one (about K 2^-24 relative to the sum of |terms|), like the SIMT path.
+    rng = np.random.default_rng(23 + Q)
+    X = rng.random(dims) * np.exp2(rng.integers(-6, 7, size=(dims[0], 1, 1)))
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    X32 = Xd.double().cpu().numpy()  # the float32 values both sides see
+    for mode in (0, 2):
+        F = rng.random((dims[mode], Q)).astype(np.float32).astype(np.float64)
+        ref = orc.mode_product(X32, F.T, mode)
+        Y = native.mode_product(Xd, torch.tensor(F, dtype=torch.float32, device="cuda"), mode,
+                                precision="fp32")
+        _close(Y.double().cpu().numpy(), ref, 1e-5)
 
 
 @pytest.mark.parametrize("dims,Q", [((37, 29, 23), 5), ((200, 150, 130), 20), ((256, 256, 256), 32),
@@ -93,3 +110,18 @@ def test_ntd_bf16_full_size_cp16_512cube():
     _, tr = native.ntd_fit(Xd, F, G, 4, precision="bf16", refine_iters=0, rel_err=False)
     _, _, tro = orc.ntd_fit(X, F0, G0, 4)
     assert np.max(np.abs(tr.cpu().numpy() - tro)) <= 1e-3
+
+
+def test_ntd_fp32_tensor_cores_match_simt():
+    # NNC_FP32 (TF32x3 passes) and NNC_FP32_SIMT agree to FP32 rounding.
+    X, _, F0, G0, _ = inputs.small_problem((64, 48, 80), 5, (8, 6, 12), 4, seed=808, noise=0.02)
+    out = {}
+    for prec in ("fp32", "fp32_simt"):
+        Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+        F = [torch.tensor(f, dtype=torch.float32, device="cuda") for f in F0]
+        G = torch.tensor(G0, dtype=torch.float32, device="cuda")
+        err, tr = native.ntd_fit(Xd, F, G, 30, precision=prec)
+        out[prec] = (err, tr.cpu().numpy())
+    assert np.max(np.abs(out["fp32"][1] - out["fp32_simt"][1])) <= 5e-6
+    _, _, tro = orc.ntd_fit(X, F0, G0, 30)
+    assert np.max(np.abs(out["fp32"][1] - tro)) <= 1e-5
