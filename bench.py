@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-precision-form", action="store_true")
     return p.parse_args()
 
 
@@ -260,24 +261,26 @@ def run_native(args, rank, world):
 
     # Dominant kernel: the pass over X with the largest total event time.
     nX = int(np.prod(w.dims))
-    elem = 2 if precision == "bf16" else (8 if dt == torch.float64 else 4)
     kinds = sorted(prof, key=lambda k: prof[k][1], reverse=True)
     dom = kinds[0]
+    # Bytes of X one pass must read: BF16 copy (kinds 2, 3), else X itself.
+    elem = 2 if dom in (2, 3) else (8 if dt == torch.float64 else 4)
     n_l, ms_l = prof[dom]
     avg_s = (ms_l / n_l) / 1e3 if n_l else float("nan")
-    mdim = w.m[2] if dom in (0, 2) else w.m[0]
+    mdim = w.m[2] if dom in (0, 2, 4) else w.m[0]
     alg_bytes = nX * elem  # one read of X per pass
     alg_flops = 2.0 * nX * mdim
     peaks, peak_src = load_peaks()
     hbm = peak_value(peaks, "hbm_gbs", "hbm_GBps", "hbm") or FALLBACK_PEAKS["hbm_gbs"]
     achieved = alg_bytes / avg_s / 1e9
-    kernel_names = {0: "ttm_rows_kernel", 1: "ttm_cols_kernel", 2: "ttm_tc_kernel",
-                    3: "ttm_tc_kernel"}
-    traffic = stored_traffic(f"{kernel_names[dom]}:{args.workload}",
-                             ["paper_1909_07570_gb300/csrc/ttm.cu"])
-    # TTM TFLOP/s over both passes: 2 * prod(N) * m_n flops per launch.
-    pass_flops = {0: 2.0 * nX * w.m[2], 1: 2.0 * nX * w.m[0], 2: 2.0 * nX * w.m[2],
-                  3: 2.0 * nX * w.m[0]}
+    kernel_names = {0: "ttm_rows_kernel", 1: "ttm_cols_kernel", 2: "tc_pass_kernel<bf16>",
+                    3: "tc_pass_kernel<bf16>", 4: "tc_pass_kernel<tf32x3>",
+                    5: "tc_pass_kernel<tf32x3>"}
+    sources = ["paper_1909_07570_gb300/csrc/ttm.cu"] if dom in (0, 1) else \
+        ["paper_1909_07570_gb300/csrc/tc_ttm.cu"]
+    traffic = stored_traffic(f"{native.PASS_KINDS[dom]}:{args.workload}", sources)
+    # TTM TFLOP/s over both passes: 2 * prod(N) * m_n algorithmic flops per launch.
+    pass_flops = {k: 2.0 * nX * (w.m[2] if k % 2 == 0 else w.m[0]) for k in range(6)}
     pass_ms = sum(v[1] for v in prof.values())
     flops_all = sum(prof[k][0] * pass_flops[k] for k in prof)
     ttm_tflops = flops_all / (pass_ms / 1e3) / 1e12 if pass_ms else None
@@ -346,6 +349,9 @@ def run_native(args, rank, world):
             "planted_rank": w.planted_rank, "ntd_sweeps_per_step": w.iters,
             "nncp_sweeps_per_step": w.cp_iters, "refine_sweeps": w.refine_iters,
             "step": "ntd_fit (with FP64 trace) + nncp_core_fit + candelinc_lift + recon_residual",
+            "passes": {"fp32": "tcgen05 TF32x3 (FP32-accurate, 3 products per term)",
+                       "bf16": "tcgen05 BF16 + TF32x3 refinement sweeps",
+                       "fp64": "SIMT FP64"}[precision],
             "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
@@ -371,6 +377,43 @@ def oracle_sample(X64, F0, G0, sweeps):
     t0 = time.perf_counter()
     oracle.ntd_fit(X64, F0, G0, sweeps)
     return time.perf_counter() - t0
+
+
+def precision_form(dev):
+    """BF16 + FP32-refinement vs FP32 (TF32x3) nnTD on the 512^3 precision
+    workload: sweeps/s of device time and the final relative error of each."""
+    import torch
+
+    from paper_1909_07570_gb300 import inputs, native
+    w = inputs.WORKLOADS["cp16_512x512x512_m32_bf16"]
+    X64, _, F0, G0, _ = inputs.make_problem(w)
+    X = torch.tensor(X64, dtype=torch.float32, device=dev)
+    del X64
+    out = {"workload": w.name, "dims": list(w.dims), "m": list(w.m), "sweeps": w.iters,
+           "refine_sweeps": w.refine_iters}
+    stream = torch.cuda.current_stream()
+    for name, prec, refine in (("bf16_refine", "bf16", w.refine_iters), ("fp32", "fp32", 0),
+                               ("fp32_simt", "fp32_simt", 0)):
+        best, err = None, None
+        for _ in range(2):
+            F = [torch.tensor(f, dtype=torch.float32, device=dev) for f in F0]
+            G = torch.tensor(G0, dtype=torch.float32, device=dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            err, _ = native.ntd_fit(X, F, G, w.iters, precision=prec, refine_iters=refine,
+                                    trace=True, rel_err=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[name] = {"iters_per_s": round(w.iters / (best / 1e3), 2), "ms": round(best, 2),
+                     "final_rel_err": err}
+    out["bf16_speedup_vs_fp32"] = round(out["bf16_refine"]["iters_per_s"] /
+                                        out["fp32"]["iters_per_s"], 3)
+    out["abs_rel_err_diff_bf16_vs_fp32"] = abs(out["bf16_refine"]["final_rel_err"] -
+                                              out["fp32"]["final_rel_err"])
+    return out
 
 
 def cpu_cores():
@@ -427,6 +470,9 @@ def main():
         print(json.dumps(run_reference(args, rank, 1)))
         return 0
     result, problem = run_native(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_precision_form:
+        import torch
+        result["precision_form"] = precision_form(torch.device("cuda", 0))
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             X64, F0, G0, _ = problem

@@ -4,8 +4,8 @@
 // The sweep is a CUDA graph replayed once per sweep. While profiling is on,
 // the captured sweep holds an external event-record node before and after
 // each pass; before every replay the nodes are pointed at fresh events from a
-// per-device pool, and after the loop every (start, stop) pair is read with
-// cudaEventElapsedTime and added to the totals of its kind.
+// per-device pool. The (start, stop) pairs are only queued; nnc_profile_read
+// reads them with cudaEventElapsedTime, so timing reads never stall a fit.
 #pragma once
 
 #include <vector>
@@ -32,10 +32,11 @@ class PassProfiler {
   const PassEvents* capture_events() const { return &cap_; }
   int bind(cudaGraph_t graph);                   // find the 4 event-record nodes
   int set_launch(cudaGraphExec_t exec, int t);   // point them at launch t's events
-  int collect(int launches);                     // add elapsed times to the totals
+  int collect(int launches);                     // queue the pairs for nnc_profile_read
 
  private:
   int kind_base_;
+  int dev_ = 0;
   std::vector<cudaEvent_t> ev_;
   PassEvents cap_{};
   cudaGraphNode_t node_[4] = {};

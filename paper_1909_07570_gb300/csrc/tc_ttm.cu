@@ -20,7 +20,8 @@
 // B = F^T as operands [NP x K] (BF16: diag(s) folded into F1 for pass 2).
 //
 // Persistent CTAs, one per SM, each looping over 128-row tiles with warp roles:
-//   warp 0        TMA producer: A tile and B slice of each K stage (4-stage ring)
+//   warp 0        TMA producer: A tile and B slice of each K stage (a ring of as
+//                 many stages as fit in shared memory, at most 8)
 //   warp 1        MMA issuer (one thread): tcgen05.mma into a double-buffered
 //                 TMEM accumulator (2 x NP FP32 columns); tcgen05.commit frees
 //                 stages and publishes finished accumulators
@@ -44,7 +45,6 @@ namespace nnc {
 namespace tc {
 namespace {
 
-constexpr int kStages = 4;
 constexpr int kTileBytes = 128 * 128;  // one A stage: 128 rows x 128 bytes of K
 constexpr int kThreadsTc = 320;        // 10 warps
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
@@ -198,6 +198,9 @@ struct TcLayout {
   static constexpr int kOffAlo = kTileBytes;
   static constexpr int kOffB = kTileBytes * (kTf32 ? 2 : 1);
   static constexpr int kOffBlo = kOffB + kBBytes;
+  // As many stages as fit in about 220 KB of shared memory (at most 8).
+  static constexpr int kStagesFit = (220 * 1024 - 1024) / kStageBytes;
+  static constexpr int kStages = kStagesFit > 8 ? 8 : kStagesFit;
   static constexpr int kSmem = 1024 + kStages * kStageBytes;
 };
 
@@ -208,7 +211,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                int* err) {
   using L = TcLayout<KIND, NP>;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t full[kStages], empty[kStages], lofull[kStages], accfull[2], accempty[2];
+  __shared__ uint64_t full[L::kStages], empty[L::kStages], lofull[L::kStages], accfull[2], accempty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
 
@@ -218,7 +221,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   volatile int* vfail = &fail;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < L::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
       mbar_init(&lofull[s], 4);
@@ -251,8 +254,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const int m0 = static_cast<int>(tile * 128);
         for (int kc = 0; kc < nk; ++kc, ++it) {
-          const int s = it % kStages;
-          if (it >= kStages && !mbar_wait(&empty[s], ((it / kStages) - 1) & 1, vfail)) {
+          const int s = it % L::kStages;
+          if (it >= L::kStages && !mbar_wait(&empty[s], ((it / L::kStages) - 1) & 1, vfail)) {
             ok = false;
             break;
           }
@@ -275,10 +278,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       }
       if (!ok) {
         // Let the copies this CTA started land before it can exit (bounded).
-        for (int back = 1; back <= kStages && it - back >= 0; ++back) {
+        for (int back = 1; back <= L::kStages && it - back >= 0; ++back) {
           const int j = it - back;
           const long long t0 = clock64();
-          while (!mbar_try_wait(&full[j % kStages], (j / kStages) & 1) &&
+          while (!mbar_try_wait(&full[j % L::kStages], (j / L::kStages) & 1) &&
                  clock64() - t0 < kWaitCycles) {
           }
         }
@@ -300,8 +303,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint32_t acc0 = tmem + buf * L::kAcc * NP;
         for (int kc = 0; kc < nk; ++kc, ++it) {
           const uint32_t acc = acc0 + (kc % L::kAcc) * NP;
-          const int s = it % kStages;
-          const uint32_t ph = (it / kStages) & 1;
+          const int s = it % L::kStages;
+          const uint32_t ph = (it / L::kStages) & 1;
           if (!mbar_wait(&full[s], ph, vfail) ||
               (L::kTf32 && !mbar_wait(&lofull[s], ph, vfail))) {
             ok = false;
@@ -399,8 +402,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     bool ok = true;
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
       for (int kc = 0; kc < nk; ++kc, ++it) {
-        const int s = it % kStages;
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (it / kStages) & 1, vfail))) {
+        const int s = it % L::kStages;
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (it / L::kStages) & 1, vfail))) {
           ok = false;
           break;
         }
