@@ -215,10 +215,11 @@ int recon_residual(const void* X, int d, const int64_t* dims, int precision, int
                    double* resid_norm, double* x_norm, void* stream);
 
 /*
- * Tracing aid: CUDA-event timing of the two passes over X of every nnTD
- * sweep, the kernels that dominate ntd_fit. While enabled, ntd_fit records an
- * event pair around each pass on the stream that launches it; the pairs are
- * read (synchronising on them) by nnc_profile_read, not inside ntd_fit.
+ * Tracing aid: CUDA-event timing of the two passes over X of nnTD sweeps,
+ * the kernels that dominate ntd_fit. While enabled, ntd_fit records an event
+ * pair around each pass of every 16th sweep (the 16th, the 32nd, ...) on the
+ * stream that launches it; the pairs are read (synchronising on them) by
+ * nnc_profile_read, not inside ntd_fit.
  * Kinds:
  *   0  X x_3 F^(3)T, SIMT passes (NNC_FP64, NNC_FP32_SIMT)
  *   1  X x_1 F^(1)T, SIMT passes

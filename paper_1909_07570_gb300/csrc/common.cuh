@@ -81,9 +81,38 @@ int device_sm_count();
 void note_launch(cudaStream_t s);
 void note_graph_launches(long long kernels);
 
+// Programmatic dependent launch. A kernel launched this way may be scheduled
+// while the kernel before it on the stream is still running; it must call
+// pdl_wait() before touching global memory that kernel writes (or reads and
+// this one writes), and at least one of its threads must call it, so that its
+// own completion still implies the completion of every kernel before it.
+// Without a programmatic predecessor pdl_wait() returns at once.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------
+// Waits until the programmatic predecessor grid has completed and its memory
+// operations are visible.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the programmatic successor grid be scheduled before this one ends.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

@@ -177,20 +177,43 @@ int count_kernel_nodes(cudaGraph_t graph, long long* n_kernels) {
   return NNC_OK;
 }
 
-// RAII holder of the private stream, graph and events of one replay loop.
+// RAII holder of the private stream, graphs and events of one replay loop.
 struct GraphRun {
   cudaStream_t cs = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr, graph_p = nullptr;
+  cudaGraphExec_t exec = nullptr, exec_p = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   ~GraphRun() {
     if (exec) cudaGraphExecDestroy(exec);
+    if (exec_p) cudaGraphExecDestroy(exec_p);
     if (graph) cudaGraphDestroy(graph);
+    if (graph_p) cudaGraphDestroy(graph_p);
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
     if (cs) cudaStreamDestroy(cs);
   }
 };
+
+// While the profiler is on, one sweep in kProfileEvery runs from a second
+// capture of the sweep whose passes are bracketed by event-record nodes. Event
+// nodes cost the device a few microseconds each, so timing every sweep would
+// slow the fit it measures by about a tenth; sampled sweeps are otherwise the
+// same kernels on the same data.
+constexpr int kProfileEvery = 16;
+
+template <typename T>
+int capture_sweep(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* trace,
+                  const PassEvents* ev, const tc::TcPlan* tcp, cudaStream_t cs,
+                  cudaGraph_t* graph, cudaGraphExec_t* exec) {
+  NNC_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  const int cap_st = sweep3<T>(X, F, G, b, eps, trace ? trace : b.trace_dummy, trace ? 1 : 0, ev,
+                               tcp, cs);
+  const cudaError_t end_e = cudaStreamEndCapture(cs, graph);
+  if (cap_st != NNC_OK) return cap_st;
+  NNC_CUDA_TRY(end_e);
+  NNC_CUDA_TRY(cudaGraphInstantiate(exec, *graph, 0));
+  return NNC_OK;
+}
 
 // Captures one sweep on a private stream and replays it `count` times after
 // the work already queued on `s`; `s` then waits for the replays.
@@ -205,31 +228,35 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
   NNC_CUDA_TRY(cudaEventRecord(g.fork, s));
   NNC_CUDA_TRY(cudaStreamWaitEvent(g.cs, g.fork, 0));
 
-  PassProfiler prof(tcp ? (tcp->kind == tc::kKindBf16 ? 2 : 4) : 0);
-  const PassEvents* capture_ev = nullptr;
-  if (profile_enabled()) {
-    NNC_TRY(prof.init(count));
-    capture_ev = prof.capture_events();
-  }
-  NNC_CUDA_TRY(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
-  const int cap_st = sweep3<T>(X, F, G, b, eps, trace ? trace : b.trace_dummy, trace ? 1 : 0,
-                               capture_ev, tcp, g.cs);
-  const cudaError_t end_e = cudaStreamEndCapture(g.cs, &g.graph);
-  if (cap_st != NNC_OK) return cap_st;
-  NNC_CUDA_TRY(end_e);
-  NNC_CUDA_TRY(cudaGraphInstantiate(&g.exec, g.graph, 0));
+  NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, nullptr, tcp, g.cs, &g.graph, &g.exec));
   long long kernel_nodes = 0;
   NNC_TRY(count_kernel_nodes(g.graph, &kernel_nodes));
-  if (capture_ev) NNC_TRY(prof.bind(g.graph));
+
+  // Sampled sweeps: the last of every kProfileEvery. The instrumented graph is
+  // captured once the first plain replays are queued, so the device is busy
+  // meanwhile.
+  PassProfiler prof(tcp ? (tcp->kind == tc::kKindBf16 ? 2 : 4) : 0);
+  const int samples = profile_enabled() ? count / kProfileEvery : 0;
   for (int t = 0; t < count; ++t) {
-    if (capture_ev) NNC_TRY(prof.set_launch(g.exec, t));
-    NNC_CUDA_TRY(cudaGraphLaunch(g.exec, g.cs));
+    if (samples > 0 && t % kProfileEvery == kProfileEvery - 1) {
+      const int j = t / kProfileEvery;
+      if (j == 0) {
+        NNC_TRY(prof.init(samples));
+        NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, prof.capture_events(), tcp, g.cs,
+                                 &g.graph_p, &g.exec_p));
+        NNC_TRY(prof.bind(g.graph_p));
+      }
+      NNC_TRY(prof.set_launch(g.exec_p, j));
+      NNC_CUDA_TRY(cudaGraphLaunch(g.exec_p, g.cs));
+    } else {
+      NNC_CUDA_TRY(cudaGraphLaunch(g.exec, g.cs));
+    }
   }
   note_graph_launches(kernel_nodes * count);
   NNC_CUDA_TRY(cudaEventRecord(g.join, g.cs));
   NNC_CUDA_TRY(cudaStreamWaitEvent(s, g.join, 0));
   NNC_CUDA_TRY(cudaStreamSynchronize(g.cs));
-  if (capture_ev) NNC_TRY(prof.collect(count));
+  if (samples > 0) NNC_TRY(prof.collect(samples));
   return NNC_OK;
 }
 

@@ -1,11 +1,13 @@
 // CUDA-event timing of the two passes over X of every nnTD sweep (the
 // dominant kernels), for nnc_profile_enable / nnc_profile_read.
 //
-// The sweep is a CUDA graph replayed once per sweep. While profiling is on,
-// the captured sweep holds an external event-record node before and after
-// each pass; before every replay the nodes are pointed at fresh events from a
-// per-device pool. The (start, stop) pairs are only queued; nnc_profile_read
-// reads them with cudaEventElapsedTime, so timing reads never stall a fit.
+// The sweep is a CUDA graph replayed once per sweep. While profiling is on, a
+// second capture of the sweep holds an external event-record node before and
+// after each pass and replaces every 16th replay (sweeps 16, 32, ... of each
+// run of replays); before each of its replays
+// the nodes are pointed at fresh events from a per-device pool. The (start,
+// stop) pairs are only queued; nnc_profile_read reads them with
+// cudaEventElapsedTime, so timing reads never stall a fit.
 #pragma once
 
 #include <vector>

@@ -9,9 +9,10 @@
 //   TF32x3  FP32-accurate: X is read as FP32 and every operand is split into
 //           exact TF32 parts, x = x_hi + x_lo (x_hi: x with 13 low mantissa
 //           bits cleared; x_lo: x - x_hi rounded to TF32). Each K step issues
-//           x_hi f_hi + x_hi f_lo + x_lo f_hi into one FP32 accumulator; the
-//           dropped x_lo f_lo term and the rounding of the lo parts are about
-//           2^-21 of each product.
+//           two MMAs: x_hi [f_hi; f_lo] (N = 2 NP, the two B parts stacked) and
+//           x_lo f_hi (N = NP, into the f_hi half); the epilogue adds the two
+//           halves. The dropped x_lo f_lo term and the rounding of the lo parts
+//           are about 2^-21 of each product.
 //
 // Pass 1, P3 = X x_3 F3^T: D[r, q] = sum_k A[r, k] B[q, k], r = (i, j), A K-major.
 // Pass 2, P1 = X x_1 F1^T: D[c, a] = sum_i A[c, i] B[a, i], c = (j, k). BF16:
@@ -23,12 +24,16 @@
 //   warp 0        TMA producer: A tile and B slice of each K stage (a ring of as
 //                 many stages as fit in shared memory, at most 8)
 //   warp 1        MMA issuer (one thread): tcgen05.mma into a double-buffered
-//                 TMEM accumulator (2 x NP FP32 columns); tcgen05.commit frees
-//                 stages and publishes finished accumulators
+//                 TMEM accumulator; tcgen05.commit frees stages and publishes
+//                 finished accumulators
 //   warps 2-5     epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //                 lanes 32 (w % 4) ..), scaled stores to global memory
-//   warps 6-9     TF32x3 only: split each staged A tile into hi / lo in place
-// so a tile's epilogue overlaps the next tile's MMAs. Every mbarrier wait is
+//   warps 6-9     TF32x3 only: split each staged A tile into x_hi (in place)
+//                 and x_lo (into a 3-slot ring of its own)
+// so a tile's epilogue overlaps the next tile's MMAs. The kernel is launched
+// with programmatic stream serialization: the producer requests the first
+// stages' A tiles (X, which no earlier kernel writes) before it waits for the
+// preceding grid, and the B operands only after. Every mbarrier wait is
 // bounded (about 2 s); on time-out the CTA flags an error, the other roles
 // stop at their next wait, and TMEM is freed before the CTA exits.
 #include <cuda.h>
@@ -121,13 +126,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
-// Instruction descriptor, FP32 accumulator, M = 128, N = NP, B K-major.
+// Instruction descriptor, FP32 accumulator, M = 128, N = n, B K-major.
 // Operand format 1 = BF16 (kind::f16), 2 = TF32 (kind::tf32).
-template <int KIND, bool kMN, int NP>
-__device__ __forceinline__ uint32_t instr_desc() {
+template <int KIND, bool kMN>
+__device__ __forceinline__ uint32_t instr_desc(int n) {
   constexpr uint32_t fmt = KIND == kKindBf16 ? 1u : 2u;
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((kMN ? 1u : 0u) << 15) |
-         (static_cast<uint32_t>(NP >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
+         (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
 }
 
 template <int KIND>
@@ -190,18 +195,29 @@ struct TcLayout {
   // FP32. The tensor core rounds its FP32 accumulation toward zero once per
   // MMA; shorter chains shrink that bias by kAcc.
   static constexpr int kAcc = kTf32 ? 128 / NP : 1;
-  static constexpr int kTmemCols = 2 * kAcc * NP;  // double-buffered
-  static constexpr int kKStage = kTf32 ? 32 : 64;  // K elements per stage (128 bytes)
-  static constexpr int kBBytes = NP * 128;         // one B slice
-  static constexpr int kStageBytes = kTileBytes * (kTf32 ? 2 : 1) + kBBytes * (kTf32 ? 2 : 1);
-  // Offsets inside one stage: A | A_lo | B | B_lo
-  static constexpr int kOffAlo = kTileBytes;
-  static constexpr int kOffB = kTileBytes * (kTf32 ? 2 : 1);
-  static constexpr int kOffBlo = kOffB + kBBytes;
+  // TF32x3 accumulators are 2 NP columns wide: [0, NP) collects x_hi f_hi and
+  // x_lo f_hi, [NP, 2 NP) collects x_hi f_lo (one MMA of N = 2 NP against the
+  // stacked [f_hi; f_lo] operand).
+  static constexpr int kAccCols = kTf32 ? 2 * NP : NP;
+  static constexpr int kTmemCols = 2 * kAcc * kAccCols;  // double-buffered
+  static constexpr int kKStage = kTf32 ? 32 : 64;        // K elements per stage (128 bytes)
+  static constexpr int kBBytes = NP * 128;               // one B slice
+  // One ring stage: A | B (| B_lo right after B, so [B; B_lo] is one operand).
+  static constexpr int kStageBytes = kTileBytes + kBBytes * (kTf32 ? 2 : 1);
+  static constexpr int kOffB = kTileBytes;
+  // TF32x3: x_lo tiles live in a short ring of their own; it only has to cover
+  // the time from the split to the MMAs that read it.
+  static constexpr int kLoSlots = kTf32 ? 3 : 0;
+  static constexpr int kLoRing = kLoSlots > 0 ? kLoSlots : 1;  // index modulus
+  static constexpr int kLoBytes = kLoSlots * kTileBytes;
   // As many stages as fit in about 220 KB of shared memory (at most 8).
-  static constexpr int kStagesFit = (220 * 1024 - 1024) / kStageBytes;
+  static constexpr int kStagesFit = (220 * 1024 - 1024 - kLoBytes) / kStageBytes;
   static constexpr int kStages = kStagesFit > 8 ? 8 : kStagesFit;
-  static constexpr int kSmem = 1024 + kStages * kStageBytes;
+  static constexpr int kOffLo = kStages * kStageBytes;
+  static constexpr int kSmem = 1024 + kOffLo + kLoBytes;
+  static_assert(kTmemCols == 32 || kTmemCols == 64 || kTmemCols == 128 || kTmemCols == 256 ||
+                kTmemCols == 512, "TMEM allocation must be a power of two >= 32 columns");
+  static_assert(kStageBytes % 1024 == 0, "stages must keep 1024-byte swizzle atoms aligned");
 };
 
 template <int KIND, bool kMN, int NP>
@@ -210,8 +226,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                const __grid_constant__ CUtensorMap tmBlo, int nk, int64_t ntiles, TcEpilogue ep,
                int* err) {
   using L = TcLayout<KIND, NP>;
+  static_assert(!(L::kTf32 && kMN), "TF32x3 passes read A K-major");
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t full[L::kStages], empty[L::kStages], lofull[L::kStages], accfull[2], accempty[2];
+  __shared__ uint64_t full[L::kStages], empty[L::kStages], accfull[2], accempty[2];
+  __shared__ uint64_t lofull[L::kLoRing], loempty[L::kLoRing];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
 
@@ -219,12 +237,19 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* vfail = &fail;
+  // The successor kernel may be scheduled now; it waits for this grid itself.
+  pdl_trigger();
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < L::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&lofull[s], 4);
+    }
+    if constexpr (L::kTf32) {
+      for (int j = 0; j < L::kLoSlots; ++j) {
+        mbar_init(&lofull[j], 4);
+        mbar_init(&loempty[j], 1);
+      }
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accfull[b], 1);
@@ -249,32 +274,51 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (warp == 0) {
     // ---- TMA producer ----------------------------------------------------------
     if (lane == 0) {
-      int it = 0;
-      bool ok = true;
-      for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      // Stages this CTA runs: tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+      const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+      const int64_t total = my_tiles * nk;
+      auto load_a = [&](int it_, unsigned char* st, uint64_t* bar) {
+        const int64_t tile = blockIdx.x + static_cast<int64_t>(it_ / nk) * gridDim.x;
         const int m0 = static_cast<int>(tile * 128);
-        for (int kc = 0; kc < nk; ++kc, ++it) {
-          const int s = it % L::kStages;
-          if (it >= L::kStages && !mbar_wait(&empty[s], ((it / L::kStages) - 1) & 1, vfail)) {
-            ok = false;
-            break;
-          }
-          unsigned char* st = base + s * L::kStageBytes;
-          mbar_expect_tx(&full[s], kTileBytes + L::kBBytes * (L::kTf32 ? 2 : 1));
-          const int k0 = kc * L::kKStage;
-          if (!kMN) {
-            tma_load_2d(st, &tmA, k0, m0, &full[s]);
-          } else {
-            // 128 columns in 128-byte pieces: 2 (BF16) or 4 (TF32) boxes.
-            constexpr int pieces = L::kTf32 ? 4 : 2;
-            constexpr int piece_cols = 128 / pieces;
+        const int k0 = (it_ % nk) * L::kKStage;
+        if (!kMN) {
+          tma_load_2d(st, &tmA, k0, m0, bar);
+        } else {
+          // 128 columns in 128-byte pieces: 2 (BF16) or 4 (TF32) boxes.
+          constexpr int pieces = L::kTf32 ? 4 : 2;
+          constexpr int piece_cols = 128 / pieces;
 #pragma unroll
-            for (int h = 0; h < pieces; ++h)
-              tma_load_2d(st + h * (kTileBytes / pieces), &tmA, m0 + h * piece_cols, k0, &full[s]);
-          }
-          tma_load_2d(st + L::kOffB, &tmB, k0, 0, &full[s]);
-          if constexpr (L::kTf32) tma_load_2d(st + L::kOffBlo, &tmBlo, k0, 0, &full[s]);
+          for (int h = 0; h < pieces; ++h)
+            tma_load_2d(st + h * (kTileBytes / pieces), &tmA, m0 + h * piece_cols, k0, bar);
         }
+      };
+      auto load_b = [&](int it_, unsigned char* st, uint64_t* bar) {
+        const int k0 = (it_ % nk) * L::kKStage;
+        tma_load_2d(st + L::kOffB, &tmB, k0, 0, bar);
+        if constexpr (L::kTf32) tma_load_2d(st + L::kOffB + L::kBBytes, &tmBlo, k0, 0, bar);
+      };
+      // X does not depend on earlier kernels: the first stages' A tiles are
+      // requested before waiting for the predecessor grid, whose results (the
+      // factor operands in B) are read only after the wait.
+      const int pre = static_cast<int>(total < L::kStages ? total : L::kStages);
+      for (int it = 0; it < pre; ++it) {
+        mbar_expect_tx(&full[it], kTileBytes + L::kBBytes * (L::kTf32 ? 2 : 1));
+        load_a(it, base + it * L::kStageBytes, &full[it]);
+      }
+      pdl_wait();
+      for (int it = 0; it < pre; ++it) load_b(it, base + it * L::kStageBytes, &full[it]);
+      int it = pre;
+      bool ok = true;
+      for (; it < total; ++it) {
+        const int s = it % L::kStages;
+        if (!mbar_wait(&empty[s], ((it / L::kStages) - 1) & 1, vfail)) {
+          ok = false;
+          break;
+        }
+        unsigned char* st = base + s * L::kStageBytes;
+        mbar_expect_tx(&full[s], kTileBytes + L::kBBytes * (L::kTf32 ? 2 : 1));
+        load_a(it, st, &full[s]);
+        load_b(it, st, &full[s]);
       }
       if (!ok) {
         // Let the copies this CTA started land before it can exit (bounded).
@@ -290,7 +334,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   } else if (warp == 1) {
     // ---- MMA issuer --------------------------------------------------------------
     if (lane == 0) {
-      const uint32_t idesc = instr_desc<KIND, kMN, NP>();
+      const uint32_t idesc = instr_desc<KIND, kMN>(NP);
+      const uint32_t idesc2 = instr_desc<KIND, kMN>(2 * NP);  // TF32x3: N = 2 NP
       int it = 0, tcount = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tcount) {
@@ -300,13 +345,13 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           break;
         }
         tc_fence_after();
-        const uint32_t acc0 = tmem + buf * L::kAcc * NP;
+        const uint32_t acc0 = tmem + buf * L::kAcc * L::kAccCols;
         for (int kc = 0; kc < nk; ++kc, ++it) {
-          const uint32_t acc = acc0 + (kc % L::kAcc) * NP;
+          const uint32_t acc = acc0 + (kc % L::kAcc) * L::kAccCols;
           const int s = it % L::kStages;
-          const uint32_t ph = (it / L::kStages) & 1;
-          if (!mbar_wait(&full[s], ph, vfail) ||
-              (L::kTf32 && !mbar_wait(&lofull[s], ph, vfail))) {
+          const int j = it % L::kLoRing;
+          if (!mbar_wait(&full[s], (it / L::kStages) & 1, vfail) ||
+              (L::kTf32 && !mbar_wait(&lofull[j], (it / L::kLoRing) & 1, vfail))) {
             ok = false;
             break;
           }
@@ -316,26 +361,27 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           for (int kk = 0; kk < 4; ++kk) {
             // K-major: +32 bytes per K step inside the swizzled 128-byte rows.
             // MN-major: +K-step rows of 128 bytes; column pieces LBO apart.
-            uint64_t adesc, alodesc;
+            uint64_t adesc;
             if constexpr (kMN) {
               constexpr uint32_t step = L::kTf32 ? 1024 : 2048;
               constexpr uint32_t lbo = L::kTf32 ? kTileBytes / 4 : kTileBytes / 2;
               adesc = smem_desc(st + kk * step, lbo, 1024);
-              alodesc = smem_desc(st + L::kOffAlo + kk * step, lbo, 1024);
             } else {
               adesc = smem_desc(st + kk * 32, 16, 1024);
-              alodesc = smem_desc(st + L::kOffAlo + kk * 32, 16, 1024);
             }
             const uint64_t bdesc = smem_desc(st + L::kOffB + kk * 32, 16, 1024);
             const uint32_t accum = (kc >= L::kAcc || kk != 0) ? 1u : 0u;
-            mma<KIND>(acc, adesc, bdesc, idesc, accum);
             if constexpr (L::kTf32) {
-              const uint64_t blodesc = smem_desc(st + L::kOffBlo + kk * 32, 16, 1024);
-              mma<KIND>(acc, adesc, blodesc, idesc, 1u);
-              mma<KIND>(acc, alodesc, bdesc, idesc, 1u);
+              // x_hi [f_hi; f_lo] into columns [0, 2 NP), then x_lo f_hi into [0, NP).
+              const uint32_t lo = smem_u32(base + L::kOffLo + j * kTileBytes);
+              mma<KIND>(acc, adesc, bdesc, idesc2, accum);
+              mma<KIND>(acc, smem_desc(lo + kk * 32, 16, 1024), bdesc, idesc, 1u);
+            } else {
+              mma<KIND>(acc, adesc, bdesc, idesc, accum);
             }
           }
           mma_commit(&empty[s]);
+          if constexpr (L::kTf32) mma_commit(&loempty[j]);
         }
         if (!ok) break;
         mma_commit(&accfull[buf]);
@@ -352,17 +398,33 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       tc_fence_after();
       const int64_t row = tile * 128 + quarter * 32 + lane;
       const int nacc = nk < L::kAcc ? nk : L::kAcc;  // accumulators this tile wrote
+      const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
+      const uint32_t accb = tmem + buf * L::kAcc * L::kAccCols + lanes;
 #pragma unroll
       for (int c0 = 0; c0 < NP; c0 += 32) {
         uint32_t v[32];
-        const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
-        tmem_ld32(tmem + buf * L::kAcc * NP + c0 + lanes, v);
-        for (int q = 1; q < nacc; ++q) {
-          uint32_t w[32];
-          tmem_ld32(tmem + (buf * L::kAcc + q) * NP + c0 + lanes, w);
+        tmem_ld32(accb + c0, v);
+        for (int q = 0; q < nacc; ++q) {
+          if constexpr (L::kTf32) {
+            uint32_t w[32];
+            tmem_ld32(accb + q * L::kAccCols + NP + c0, w);  // x_hi f_lo
+            if (q > 0) {
+              uint32_t h[32];
+              tmem_ld32(accb + q * L::kAccCols + c0, h);
 #pragma unroll
-          for (int t = 0; t < 32; ++t)
-            v[t] = __float_as_uint(__uint_as_float(v[t]) + __uint_as_float(w[t]));
+              for (int t = 0; t < 32; ++t)
+                w[t] = __float_as_uint(__uint_as_float(w[t]) + __uint_as_float(h[t]));
+            }
+#pragma unroll
+            for (int t = 0; t < 32; ++t)
+              v[t] = __float_as_uint(__uint_as_float(v[t]) + __uint_as_float(w[t]));
+          } else if (q > 0) {
+            uint32_t w[32];
+            tmem_ld32(accb + q * L::kAccCols + c0, w);
+#pragma unroll
+            for (int t = 0; t < 32; ++t)
+              v[t] = __float_as_uint(__uint_as_float(v[t]) + __uint_as_float(w[t]));
+          }
         }
         if (!ep.p1_layout) {
           if (row < ep.rows) {
@@ -382,9 +444,9 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             }
           }
         } else {
-          const int64_t j = row / ep.kp, k = row % ep.kp;
-          if (j < ep.n2 && k < ep.n3) {
-            float* o = ep.out + j * ep.n3 + k;
+          const int64_t jj = row / ep.kp, k = row % ep.kp;
+          if (jj < ep.n2 && k < ep.n3) {
+            float* o = ep.out + jj * ep.n3 + k;
 #pragma unroll
             for (int t = 0; t < 32; ++t)
               if (c0 + t < ep.q) o[static_cast<int64_t>(c0 + t) * ep.slab] = __uint_as_float(v[t]);
@@ -395,33 +457,42 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       __syncwarp();
       if (lane == 0) mbar_arrive(&accempty[buf]);
     }
-  } else if (L::kTf32) {
-    // ---- TF32 split of A (warps 6-9): A <- A_hi in place, A_lo beside it -------
+  } else if constexpr (L::kTf32) {
+    // ---- TF32 split of A (warps 6-9): A <- x_hi in place, x_lo to its ring ----
     const int ct = threadIdx.x - 192;  // 0 .. 127
     int it = 0;
     bool ok = true;
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
       for (int kc = 0; kc < nk; ++kc, ++it) {
-        const int s = it % L::kStages;
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (it / L::kStages) & 1, vfail))) {
+        const int s = it % L::kStages, j = it % L::kLoRing;
+        const bool got =
+            mbar_wait(&full[s], (it / L::kStages) & 1, vfail) &&
+            (it < L::kLoRing || mbar_wait(&loempty[j], ((it / L::kLoRing) - 1) & 1, vfail));
+        if (!__all_sync(0xffffffffu, got)) {
           ok = false;
           break;
         }
         float4* a = reinterpret_cast<float4*>(base + s * L::kStageBytes);
-        float4* alo = reinterpret_cast<float4*>(base + s * L::kStageBytes + L::kOffAlo);
+        float4* alo = reinterpret_cast<float4*>(base + L::kOffLo + j * kTileBytes);
+        // All loads of the stage are issued before the first store, so their
+        // shared-memory latencies overlap instead of adding up.
+        constexpr int kPer = kTileBytes / 16 / 128;
+        float4 x[kPer];
 #pragma unroll
-        for (int e = ct; e < kTileBytes / 16; e += 128) {
-          float4 x = a[e], h, l;
-          h.x = tf32_hi(x.x); l.x = tf32_lo(x.x, h.x);
-          h.y = tf32_hi(x.y); l.y = tf32_lo(x.y, h.y);
-          h.z = tf32_hi(x.z); l.z = tf32_lo(x.z, h.z);
-          h.w = tf32_hi(x.w); l.w = tf32_lo(x.w, h.w);
-          a[e] = h;
-          alo[e] = l;
+        for (int i = 0; i < kPer; ++i) x[i] = a[ct + 128 * i];
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+          float4 h, l;
+          h.x = tf32_hi(x[i].x); l.x = tf32_lo(x[i].x, h.x);
+          h.y = tf32_hi(x[i].y); l.y = tf32_lo(x[i].y, h.y);
+          h.z = tf32_hi(x[i].z); l.z = tf32_lo(x[i].z, h.z);
+          h.w = tf32_hi(x[i].w); l.w = tf32_lo(x[i].w, h.w);
+          a[ct + 128 * i] = h;
+          alo[ct + 128 * i] = l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&lofull[s]);
+        if (lane == 0) mbar_arrive(&lofull[j]);
       }
     }
   }
@@ -559,10 +630,9 @@ int launch_pass(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& b
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int64_t grid = device_sm_count();
   if (grid > tiles) grid = tiles;
-  tc_pass_kernel<KIND, kMN, NP><<<static_cast<unsigned>(grid), kThreadsTc, smem, s>>>(
-      a, b, blo, nk, tiles, ep, err);
+  NNC_CUDA_TRY(launch_pdl(tc_pass_kernel<KIND, kMN, NP>, dim3(static_cast<unsigned>(grid)),
+                          dim3(kThreadsTc), smem, s, a, b, blo, nk, tiles, ep, err));
   note_launch(s);
-  NNC_CUDA_TRY(cudaGetLastError());
   return NNC_OK;
 }
 

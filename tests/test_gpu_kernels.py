@@ -125,3 +125,29 @@ def test_ntd_fp32_tensor_cores_match_simt():
     assert np.max(np.abs(out["fp32"][1] - out["fp32_simt"][1])) <= 5e-6
     _, _, tro = orc.ntd_fit(X, F0, G0, 30)
     assert np.max(np.abs(out["fp32"][1] - tro)) <= 1e-5
+
+
+def test_pass_profiler_samples_and_changes_nothing():
+    # The profiler times the passes of every 16th sweep through an instrumented
+    # copy of the sweep graph; the fit it measures must come out bit-identical.
+    X, _, F0, G0, _ = inputs.small_problem((64, 48, 80), 5, (8, 6, 12), 4, seed=909)
+    runs = {}
+    for on in (False, True):
+        Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+        F = [torch.tensor(f, dtype=torch.float32, device="cuda") for f in F0]
+        G = torch.tensor(G0, dtype=torch.float32, device="cuda")
+        native.nnc_profile_enable(on)
+        try:
+            _, tr = native.ntd_fit(Xd, F, G, 40, precision="fp32")
+            prof = {k: native.nnc_profile_read(k) for k in native.PASS_KINDS}
+        finally:
+            native.nnc_profile_enable(False)
+        runs[on] = (tr.cpu().numpy(), [f.cpu().numpy() for f in F], G.cpu().numpy(), prof)
+    assert np.array_equal(runs[False][0], runs[True][0])
+    assert all(np.array_equal(a, b) for a, b in zip(runs[False][1], runs[True][1]))
+    assert np.array_equal(runs[False][2], runs[True][2])
+    prof = runs[True][3]
+    assert prof[4][0] == 2 and prof[5][0] == 2  # sweeps 16 and 32 of 40
+    assert prof[4][1] > 0 and prof[5][1] > 0
+    assert all(prof[k][0] == 0 for k in (0, 1, 2, 3))
+    assert all(v[0] == 0 for v in runs[False][3].values())
