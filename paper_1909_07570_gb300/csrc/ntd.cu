@@ -11,8 +11,8 @@
 //   hmat 3   H3 from W3 = G x_1 S1 x_2 S2 (W3 kept)
 //   pass 2   P1 = X x_1 F1^T (new F1)                 (second read of X)
 //   y3, upd3 Y3 = P1 x_2 F2^T (new F2);  Num3 = unfold_3(Y3) unfold_3(G)^T;  Den3 = F3 H3
-//   core_m   M = Y3 x_3 F3^T = X x_1 F1^T x_2 F2^T x_3 F3^T
-//   core     G <- MU(G, M, W3 x_3 S3); trace; next H1       (core_a, core_b)
+//   core     M = Y3 x_3 F3^T = X x_1 F1^T x_2 F2^T x_3 F3^T;
+//            G <- MU(G, M, W3 x_3 S3); trace; next H1       (core_a, core_b)
 // with S_k = F_k^T F_k. The kernels are in sweep.cu; the passes are SIMT mode
 // products (ttm.cu) or, on the BF16 path, tensor-core mode products from a
 // BF16 copy of X (tc_ttm.cu). Two reads of X per sweep is the minimum under
@@ -41,8 +41,7 @@ template <typename T>
 struct NtdState {
   int64_t N[3];
   int m[3];
-  T *P3, *P1, *Y3, *Mpart, *M, *W1, *W3, *G2, *G3, *H[3], *S[3], *num3part;
-  int rpb[2], n3splits, msplits;
+  T *P3, *P1, *Y3, *M, *W1, *W3, *G2, *G3, *H[3], *S[3];
   double *stats_part, *stats, *trace_dummy, *resid2, *dots;
   int* counter;
   int* done;
@@ -87,7 +86,6 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     u.Fc = F[1]; u.len = (int)N2;   u.mu = m2;  u.mc = m3;
     u.Gn = G;    // rows a of G are (b, c)-contiguous
     u.F = F[0];  u.nrows = N1;  u.mv = m1;  u.H = b.H[0];  u.eps = eps;
-    u.rows_per_block = b.rpb[0];
     if constexpr (std::is_same<T, float>::value) {
       if (tcp) {
         u.bt = tcp->Bt1;
@@ -114,7 +112,6 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     u.Fc = F[0]; u.len = (int)N1;  u.mu = m1;  u.mc = m3;
     u.Gn = b.G2;  // rows b of G2 are (a, c)-contiguous
     u.F = F[1];  u.nrows = N2;  u.mv = m2;  u.H = b.H[1];  u.eps = eps;
-    u.rows_per_block = b.rpb[1];
     NNC_TRY(launch_upd12<T>(u, s));
   }
   {  // H3 and W3 = G x_1 S1 x_2 S2, with S2 = F2^T F2 (new F2)
@@ -134,8 +131,9 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
   NNC_TRY(launch_y3<T>(b.P1, F[1], m1, (int)N2, (int)N3, m2, b.Y3, s));
   {
     UpdArgs<T> u{};
-    u.P = b.Y3;  u.mu = m1 * m2;
+    u.P = b.Y3;  u.mu = m1;  u.mc = m2;  // Y3 laid out (m1, N3, m2)
     u.G = G;
+    u.rows_per_block = mode3_rows_per_block<T>(m3);
     u.F = F[2];  u.nrows = N3;  u.mv = m3;  u.H = b.H[2];  u.eps = eps;
     if constexpr (std::is_same<T, float>::value) {
       if (tcp) {
@@ -145,14 +143,12 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
         u.bt_ld = tcp->kb3;
       }
     }
-    NNC_TRY(launch_mode3<T>(u, b.num3part, b.n3splits, s));
+    NNC_TRY(launch_mode3<T>(u, s));
   }
   // ---- core ------------------------------------------------------------------
-  int used = 1;
-  NNC_TRY(launch_core_m<T>(b.Y3, F[2], m1 * m2, (int)N3, m3, b.Mpart, b.msplits, &used, s));
   {
     CoreArgs<T> c{};
-    c.G = G;  c.G2 = b.G2;  c.G3 = b.G3;  c.M = b.Mpart;  c.M_splits = used;  c.Mout = b.M;  c.W3 = b.W3;
+    c.G = G;  c.G2 = b.G2;  c.G3 = b.G3;  c.Y3 = b.Y3;  c.Mout = b.M;  c.W3 = b.W3;
     c.S1 = b.S[0];  c.S2 = b.S[1];  c.F3 = F[2];  c.n3 = N3;  c.S3_out = b.S[2];
     c.W1 = b.W1;  c.H1 = b.H[0];  c.dots = b.dots;  c.done = b.done;  c.x2 = b.stats;
     c.trace = trace;  c.trace_stride = trace_stride;  c.counter = b.counter;
@@ -292,16 +288,10 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   if (st[1] > 0.0) return NNC_ERR_NEGATIVE_INPUT;
   if (!(st[0] > 0.0)) return NNC_ERR_INVALID_ARG;  // X == 0: the relative error is undefined
 
-  b.rpb[0] = upd_rows_per_block<T>(m2, m3, N1);
-  b.rpb[1] = upd_rows_per_block<T>(m1, m3, N2);
-  b.n3splits = num3_splits<T>(m1 * m2, (int)N3);
-  b.msplits = core_m_splits<T>(m1 * m2, (int)N3);
 
   NNC_TRY(sc.get(&b.P3, (size_t)(N1 * N2 * m3)));
   NNC_TRY(sc.get(&b.P1, (size_t)(m1 * N2 * N3)));
   NNC_TRY(sc.get(&b.Y3, (size_t)((int64_t)m1 * m2 * N3)));
-  NNC_TRY(sc.get(&b.num3part, (size_t)b.n3splits * N3 * m3));
-  NNC_TRY(sc.get(&b.Mpart, (size_t)b.msplits * nc));
   NNC_TRY(sc.get(&b.M, (size_t)nc));
   NNC_TRY(sc.get(&b.W1, (size_t)nc));
   NNC_TRY(sc.get(&b.W3, (size_t)nc));

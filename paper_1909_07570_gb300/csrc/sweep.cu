@@ -10,18 +10,19 @@
 //                               H2[b, b'] = <W[:, b, :], G[:, b', :]>
 //   upd12 (mode 2) per row j:   Y2[:, j, :] = F1^T P3[:, j, :];  Num2;  MU on F2
 //   hmat  (mode 3) per c:       S2 = F2^T F2;  W3 = G x_1 S1 x_2 S2 (kept);  H3
-//   y3:                         Y3[a, b, k] = sum_j P1[a, j, k] F2[j, b]
-//   num3 + tail3:               Num3[k, c] = sum_{a,b} Y3[a, b, k] G[a, b, c] (split over
-//                               (a, b), added in split order); MU on F3
-//   core_m:                     M = Y3 x_3 F3^T (split over k)
-//   core_a (one block per a):   S3 = F3^T F3; D = W3 x_3 S3; G <- MU(G, M, D);
-//                               W1 = G x_2 S2 x_3 S3
+//   y3:                         Y3[a, k, b] = sum_j P1[a, j, k] F2[j, b]  (laid out m1, N3, m2)
+//   mode3 (rows of F3):         Num3[k, c] = sum_{a,b} Y3[a, k, b] G[a, b, c]; MU on F3
+//   core_a (one block per a):   S3 = F3^T F3; M[a] = Y3[a]^T F3; D = W3 x_3 S3;
+//                               G <- MU(G, M, D); W1 = G x_2 S2 x_3 S3
 //   core_b (one block per a):   H1 = unfold_1(W1) unfold_1(G)^T for the next sweep;
 //                               trace = sqrt(||X||^2 - 2<M,G> + <G, G x_k S_k>)/||X||
 //                               with <G, G x_k S_k> = sum S1 .* H1^T (last block)
 //
-// The contractions are SIMT GEMMs on 4 x 4 register tiles whose operands are
-// staged in shared memory by cp.async, two chunks in flight. Every reduction
+// These kernels are latency-bound (a few MFLOP each on L2-resident data), so
+// each block requests everything it needs up front (cp.async) and spreads every
+// contraction over all its threads: the block GEMM splits the contraction
+// across thread groups (4 x 4 register tiles per thread) and adds the group
+// partials in a fixed order. Every reduction
 // runs in a fixed order, so results are deterministic. The BF16 path also
 // writes, from the mode-1 and mode-3 updates, the BF16 operand of the next
 // pass over X.
@@ -155,21 +156,6 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
-// acc[i][j] += sum_{k < kn} A[k][m0 + i] B[k][n0 + j]
-template <typename T>
-__device__ __forceinline__ void tile4x4(const T* A, int lda, const T* B, int ldb, int kn, int m0,
-                                        int n0, T (&acc)[4][4]) {
-  for (int k = 0; k < kn; ++k) {
-    T a[4], b[4];
-    ld4(A + k * lda + m0, a);
-    ld4(B + k * ldb + n0, b);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-  }
-}
-
 template <typename T>
 __device__ __forceinline__ void zero4x4(T (&acc)[4][4]) {
 #pragma unroll
@@ -178,125 +164,69 @@ __device__ __forceinline__ void zero4x4(T (&acc)[4][4]) {
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 }
 
-// Rows of F staged per chunk by gram_block: up to 32 KB of shared memory.
-__host__ __device__ constexpr int gram_rows(int m, int elem) {
-  return (32 * 1024) / (r4(m) * elem) < 1 ? 1 : (32 * 1024) / (r4(m) * elem);
+// dst[e] = src[e] for e < n by cp.async (16-byte vectors when both ends allow),
+// issued by the whole block; the caller commits and waits.
+template <typename T>
+__device__ __forceinline__ void cp_flat(T* dst, const T* __restrict__ src, int64_t n) {
+  constexpr int W = 16 / (int)sizeof(T);
+  if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    const int64_t nv = n / W;
+    for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) cp_vec(dst + v * W, src + v * W, W);
+    for (int64_t e = nv * W + threadIdx.x; e < n; e += blockDim.x) cp_elem(dst + e, src + e, true);
+  } else {
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) cp_elem(dst + e, src + e, true);
+  }
 }
 
-// S = F^T F (n rows of width m) into shared s (m x m), computed by the whole
-// block: groups of threads take interleaved rows with 4 x 4 tiles of S and are
-// added in group order. F is staged by cp.async in chunks of gram_rows rows;
-// `stage` holds gram_stage_elems(m) elements (chunk + per-group partials).
+// ---- block GEMM C = A^T B ----------------------------------------------------
+// C[u][c] = sum_{t < len} A[t lda + u] B[t ldb + c], u < mu, c < mc (both <= 64),
+// computed by one block: each thread owns a 4 x 4 tile of C for one of `groups`
+// interleaved subsets of t (split-K inside the block, so every thread works
+// even for small mu, mc); the partial tiles are added in group order. A and B
+// are staged by cp.async in chunks of kch rows, two chunks in flight; `stage`
+// holds gemm_stage_elems of the dimensions kch was chosen for.
+__host__ __device__ inline int gemm_tiles(int mu, int mc) { return (r4(mu) / 4) * (r4(mc) / 4); }
+__host__ __device__ inline int gemm_groups(int mu, int mc) {
+  const int g = kThreads / gemm_tiles(mu, mc);
+  return g > 1 ? g : 1;
+}
+// Rows per chunk: two chunks of both operands in about 48 KB, a multiple of 8.
+__host__ __device__ inline int gemm_kch(int mu, int mc, int elem) {
+  int k = (48 * 1024) / (2 * (r4(mu) + r4(mc)) * elem);
+  k = k > 256 ? 256 : k;
+  k &= ~7;
+  return k < 8 ? 8 : k;
+}
+__host__ __device__ inline size_t gemm_stage_elems(int mu, int mc, int elem) {
+  const size_t st = (size_t)2 * gemm_kch(mu, mc, elem) * (r4(mu) + r4(mc));
+  const size_t red = (size_t)gemm_groups(mu, mc) * mu * mc;
+  return al4(st > red ? st : red);
+}
+
 template <typename T>
-__device__ void gram_block(const T* __restrict__ F, int64_t n, int m, T* s, T* stage) {
-  const int mq = r4(m) / 4, tiles = mq * mq;
-  const int groups = max(1, (int)blockDim.x / tiles);
+__device__ void gemm_tn_block(const T* __restrict__ A, int64_t lda, int mu,
+                              const T* __restrict__ B, int64_t ldb, int mc, int len, int kch,
+                              T* C, T* stage) {
+  const int mu4 = r4(mu), mc4 = r4(mc), tq = mc4 / 4;
+  const int tiles = gemm_tiles(mu, mc), groups = gemm_groups(mu, mc);
   const int g = threadIdx.x / tiles, t = threadIdx.x % tiles;
-  const int x0 = (t / mq) * 4, y0 = (t % mq) * 4;
-  const int RC = gram_rows(m, (int)sizeof(T));
-  T* fs = stage;                             // RC x r4(m)
-  T* red = stage + al4((size_t)RC * r4(m));  // groups x m x m
-  T acc[4][4];
-  zero4x4(acc);
-  for (int64_t r0 = 0; r0 < n; r0 += RC) {
-    const int rn = (int)((n - r0) < (int64_t)RC ? (n - r0) : (int64_t)RC);
-    stage_tile(fs, r4(m), F + r0 * m, m, rn, r4(m), rn, m, aligned16(F + r0 * m, m, sizeof(T)));
-    cp_commit();
-    cp_wait<0>();
-    __syncthreads();
-    if (g < groups) {
-      for (int rr = g; rr < rn; rr += groups) {
-        T a[4], b[4];
-        ld4(fs + rr * r4(m) + x0, a);
-        ld4(fs + rr * r4(m) + y0, b);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-      }
-    }
-    __syncthreads();
-  }
-  if (g < groups) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (x0 + i < m && y0 + j < m) red[(g * m + x0 + i) * m + y0 + j] = acc[i][j];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    T v = T(0);
-    for (int q = 0; q < groups; ++q) v += red[q * m * m + e];
-    s[e] = v;
-  }
-  __syncthreads();
-}
-
-// sum_e x[e] y[e] over e = lane, lane + 32, ... < n, then over the warp.
-template <typename T>
-__device__ __forceinline__ T warp_dot(const T* x, const T* __restrict__ y, int n, int lane) {
-  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-  int e = lane;
-  for (; e + 96 < n; e += 128) {
-    s0 = fma(x[e], y[e], s0);
-    s1 = fma(x[e + 32], y[e + 32], s1);
-    s2 = fma(x[e + 64], y[e + 64], s2);
-    s3 = fma(x[e + 96], y[e + 96], s3);
-  }
-  for (; e < n; e += 32) s0 = fma(x[e], y[e], s0);
-  return warp_sum((s0 + s1) + (s2 + s3));
-}
-
-// ---------------------------------------------------------------------------
-// upd12: factor update of mode 1 or 2 from P3.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int MU_ = a.mu, MC = a.mc, MV = a.mv, S = a.rows_per_block;
-  const int mu4 = r4(MU_), mc4 = r4(MC);
-  const int tiles = (mu4 / 4) * (mc4 / 4);
-  T* As = sm;                          // 2 x KC x mu4
-  T* Bs = As + 2 * KC * mu4;           // 2 x S x KC x mc4
-  T* ys = Bs + 2 * S * KC * mc4;       // S x MU_ x MC
-  T* fo = ys + S * MU_ * MC;           // S x MV
-  T* hs = fo + S * MV;                 // MV x MV
-  T* nm = hs + MV * MV;                // S x MV
-  const int64_t r0 = (int64_t)blockIdx.x * S;
-
-  for (int e = threadIdx.x; e < MV * MV; e += blockDim.x) hs[e] = a.H[e];
-  for (int e = threadIdx.x; e < S * MV; e += blockDim.x) {
-    const int rr = e / MV, v = e % MV;
-    fo[e] = (r0 + rr < a.nrows) ? a.F[(r0 + rr) * MV + v] : T(0);
-  }
-
-  const int nchunks = (a.len + KC - 1) / KC;
-  const bool vecA = aligned16(a.Fc, MU_, sizeof(T));
-  const bool vecB = aligned16(a.P, a.prow, sizeof(T)) && aligned16(a.P, a.pstride, sizeof(T));
+  const bool act = g < groups;
+  const int u0 = (t / tq) * 4, c0 = (t % tq) * 4;
+  T* As = stage;
+  T* Bs = stage + 2 * kch * mu4;
+  const bool vecA = aligned16(A, lda, sizeof(T)), vecB = aligned16(B, ldb, sizeof(T));
+  const int nch = (len + kch - 1) / kch;
   auto issue = [&](int c, int buf) {
-    const int t0 = c * KC;
-    const int tn = min(KC, a.len - t0);
-    T* A = As + buf * KC * mu4;
-    T* B = Bs + buf * S * KC * mc4;
-    stage_tile(A, mu4, a.Fc + (int64_t)t0 * MU_, MU_, KC, mu4, tn, MU_, vecA);
-    for (int rr = 0; rr < S; ++rr) {
-      const int64_t r = r0 + rr;
-      stage_tile(B + rr * KC * mc4, mc4, a.P + (r < a.nrows ? r : 0) * a.prow +
-                 (int64_t)t0 * a.pstride, a.pstride, KC, mc4, r < a.nrows ? tn : 0, MC, vecB);
-    }
+    const int t0 = c * kch, tn = min(kch, len - t0);
+    stage_tile(As + buf * kch * mu4, mu4, A + (int64_t)t0 * lda, lda, tn, mu4, tn, mu, vecA);
+    stage_tile(Bs + buf * kch * mc4, mc4, B + (int64_t)t0 * ldb, ldb, tn, mc4, tn, mc, vecB);
     cp_commit();
   };
-
-  const int my_s = threadIdx.x / tiles, my_t = threadIdx.x % tiles;
-  const bool act = my_s < S;
-  const int u0 = (my_t / (mc4 / 4)) * 4, c0 = (my_t % (mc4 / 4)) * 4;
   T acc[4][4];
   zero4x4(acc);
-  issue(0, 0);
-  for (int c = 0; c < nchunks; ++c) {
-    if (c + 1 < nchunks) {
+  if (nch > 0) issue(0, 0);
+  for (int c = 0; c < nch; ++c) {
+    if (c + 1 < nch) {
       issue(c + 1, (c + 1) & 1);
       cp_wait<1>();
     } else {
@@ -304,39 +234,120 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
     }
     __syncthreads();
     if (act) {
-      const int kn = min(KC, a.len - c * KC);
-      tile4x4(As + (c & 1) * KC * mu4, mu4, Bs + (c & 1) * S * KC * mc4 + my_s * KC * mc4, mc4,
-              kn, u0, c0, acc);
+      const int kn = min(kch, len - c * kch);
+      const T* a = As + (c & 1) * kch * mu4 + u0;
+      const T* b = Bs + (c & 1) * kch * mc4 + c0;
+#pragma unroll 4
+      for (int k = g; k < kn; k += groups) {
+        T x[4], y[4];
+        ld4(a + k * mu4, x);
+        ld4(b + k * mc4, y);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(x[i], y[j], acc[i][j]);
+      }
     }
     __syncthreads();
   }
+  if (nch == 0) {
+    cp_wait<0>();
+    __syncthreads();
+  }
+  T* red = stage;  // the staging buffers are free after the last barrier
   if (act) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (u0 + i < MU_ && c0 + j < MC) ys[(my_s * MU_ + u0 + i) * MC + c0 + j] = acc[i][j];
+        if (u0 + i < mu && c0 + j < mc) red[((int64_t)g * mu + u0 + i) * mc + c0 + j] = acc[i][j];
   }
   __syncthreads();
+  const int n = mu * mc;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    T v = T(0);
+    for (int q = 0; q < groups; ++q) v += red[q * n + e];
+    C[e] = v;
+  }
+  __syncthreads();
+}
 
-  // Num[r, v] = <Y_r, Gn[v, :]>: one warp per (r, v); Gn rows are contiguous.
+// C (m x n) = A (m x k) B (k x n), all row-major in shared memory; whole block.
+template <typename T>
+__device__ __forceinline__ void smem_gemm(const T* A, const T* B, T* C, int m, int k, int n) {
+  for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    T s0 = T(0), s1 = T(0);
+    int w = 0;
+    for (; w + 1 < k; w += 2) {
+      s0 = fma(A[i * k + w], B[w * n + j], s0);
+      s1 = fma(A[i * k + w + 1], B[(w + 1) * n + j], s1);
+    }
+    if (w < k) s0 = fma(A[i * k + w], B[w * n + j], s0);
+    C[e] = s0 + s1;
+  }
+}
+
+// out[q] = <x, Y[q, :]> for q < nq (rows of length n, row stride n); a warp per q.
+template <typename T>
+__device__ __forceinline__ void rows_dot(const T* x, const T* Y, int n, int nq, T* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int UC = MU_ * MC;
-  for (int task = warp; task < S * MV; task += nw) {
-    const int rr = task / MV, v = task % MV;
-    const T s = warp_dot(ys + rr * UC, a.Gn + (int64_t)v * UC, UC, lane);
-    if (lane == 0) nm[task] = s;
+  for (int q = warp; q < nq; q += nw) {
+    const T* y = Y + (int64_t)q * n;
+    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    int e = lane;
+    for (; e + 96 < n; e += 128) {
+      s0 = fma(x[e], y[e], s0);
+      s1 = fma(x[e + 32], y[e + 32], s1);
+      s2 = fma(x[e + 64], y[e + 64], s2);
+      s3 = fma(x[e + 96], y[e + 96], s3);
+    }
+    for (; e < n; e += 32) s0 = fma(x[e], y[e], s0);
+    const T v = warp_sum((s0 + s1) + (s2 + s3));
+    if (lane == 0) out[q] = v;
   }
-  __syncthreads();
+}
 
-  // MU with Den = F_old H; BF16 operand of the next pass if requested.
-  for (int e = threadIdx.x; e < S * MV; e += blockDim.x) {
-    const int rr = e / MV, v = e % MV;
-    const int64_t r = r0 + rr;
-    if (r >= a.nrows) continue;
+// Largest core copy kept in shared memory by the kernels that dot against G.
+constexpr size_t kCoreSmemBytes = 48 * 1024;
+template <typename T>
+__host__ __device__ inline bool core_in_smem(int64_t n) {
+  return (size_t)n * sizeof(T) <= kCoreSmemBytes;
+}
+
+// ---------------------------------------------------------------------------
+// upd12: factor update of mode 1 or 2 from P3, one block per row r.
+//   Y_r = Fc^T P_r (mu x mc);  Num[r, v] = <Y_r, Gn[v]>;  F[r] <- MU(F[r], Num, F[r] H)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int MU_ = a.mu, MC = a.mc, MV = a.mv, UC = MU_ * MC;
+  const bool gsm = core_in_smem<T>((int64_t)MV * UC);
+  T* stage = sm;
+  T* ys = stage + gemm_stage_elems(MU_, MC, (int)sizeof(T));
+  T* hs = ys + al4(UC);
+  T* fo = hs + al4(MV * MV);
+  T* nm = fo + al4(MV);
+  T* gs = nm + al4(MV);  // MV x UC when it fits
+  const int64_t r = blockIdx.x;
+
+  // Everything but the GEMM operands is requested first; the GEMM's waits
+  // cover this group too.
+  cp_flat(hs, a.H, MV * MV);
+  cp_flat(fo, a.F + r * MV, MV);
+  if (gsm) cp_flat(gs, a.Gn, (int64_t)MV * UC);
+  cp_commit();
+  gemm_tn_block(a.Fc, MU_, MU_, a.P + r * a.prow, a.pstride, MC, a.len,
+                gemm_kch(MU_, MC, (int)sizeof(T)), ys, stage);
+
+  rows_dot(ys, gsm ? (const T*)gs : a.Gn, UC, MV, nm);
+  __syncthreads();
+  for (int v = threadIdx.x; v < MV; v += blockDim.x) {
     T den = T(0);
-    for (int w = 0; w < MV; ++w) den = fma(fo[rr * MV + w], hs[w * MV + v], den);
-    const T nv = mu_step(fo[e], nm[e], den, (T)a.eps);
+    for (int w = 0; w < MV; ++w) den = fma(fo[w], hs[w * MV + v], den);
+    const T nv = mu_step(fo[v], nm[v], den, (T)a.eps);
     a.F[r * MV + v] = nv;
     write_operand(a, r, v, nv);
   }
@@ -344,270 +355,141 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
 
 // ---------------------------------------------------------------------------
 // hmat: H_n for one mode (and optionally the W slices), one block per p.
+//   W[p] = S_u G[p] S_v;  H[p, q] = <W[p], G[q]>
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) hmat_kernel(HArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const int U = a.mu, V = a.mv, P = a.mp;
-  T* su = sm;                  // U x U
-  T* sv = su + al4(U * U);     // V x V
-  T* gp = sv + al4(V * V);     // U x V
-  T* tp = gp + al4(U * V);     // U x V
-  T* wp = tp + al4(U * V);     // U x V
-  T* stage = wp + al4(U * V);  // Gram staging
+  const int U = a.mu, V = a.mv, P = a.mp, UV = U * V;
+  const bool gsm = core_in_smem<T>((int64_t)P * UV);
+  const size_t st_u = a.fu ? gemm_stage_elems(U, U, (int)sizeof(T)) : 0;
+  const size_t st_v = a.fv ? gemm_stage_elems(V, V, (int)sizeof(T)) : 0;
+  T* stage = sm;
+  T* su = stage + (st_u > st_v ? st_u : st_v);
+  T* sv = su + al4(U * U);
+  T* gp = sv + al4(V * V);
+  T* tp = gp + al4(UV);
+  T* wp = tp + al4(UV);
+  T* gs = wp + al4(UV);  // P x U x V when it fits
   const int p = blockIdx.x;
-  if (a.fu) {
-    gram_block(a.fu, a.nu, U, su, stage);
-  } else {
-    for (int e = threadIdx.x; e < U * U; e += blockDim.x) su[e] = a.su[e];
+
+  if (!a.fu) cp_flat(su, a.su, U * U);
+  if (!a.fv) cp_flat(sv, a.sv, V * V);
+  if (gsm) cp_flat(gs, a.Gn, (int64_t)P * UV);
+  else cp_flat(gp, a.Gn + (int64_t)p * UV, UV);
+  cp_commit();
+  if (a.fu)
+    gemm_tn_block(a.fu, U, U, a.fu, U, U, (int)a.nu, gemm_kch(U, U, (int)sizeof(T)), su, stage);
+  if (a.fv)
+    gemm_tn_block(a.fv, V, V, a.fv, V, V, (int)a.nv, gemm_kch(V, V, (int)sizeof(T)), sv, stage);
+  if (!a.fu && !a.fv) {
+    cp_wait<0>();
+    __syncthreads();
   }
-  if (a.fv) {
-    gram_block(a.fv, a.nv, V, sv, stage);
-  } else {
-    for (int e = threadIdx.x; e < V * V; e += blockDim.x) sv[e] = a.sv[e];
-  }
-  for (int e = threadIdx.x; e < U * V; e += blockDim.x) gp[e] = a.Gn[(int64_t)p * U * V + e];
-  __syncthreads();
+  const T* g = gsm ? gs + (int64_t)p * UV : gp;
   if (p == 0 && a.su_out && a.fu)
     for (int e = threadIdx.x; e < U * U; e += blockDim.x) a.su_out[e] = su[e];
   if (p == 0 && a.sv_out && a.fv)
     for (int e = threadIdx.x; e < V * V; e += blockDim.x) a.sv_out[e] = sv[e];
-  for (int e = threadIdx.x; e < U * V; e += blockDim.x) {  // tp = S_u gp
-    const int u = e / V, v = e % V;
-    T s = T(0);
-    for (int w = 0; w < U; ++w) s = fma(su[u * U + w], gp[w * V + v], s);
-    tp[e] = s;
-  }
+  smem_gemm(su, g, tp, U, U, V);  // S_u G[p]
   __syncthreads();
-  for (int e = threadIdx.x; e < U * V; e += blockDim.x) {  // wp = tp S_v
-    const int u = e / V, v = e % V;
-    T s = T(0);
-    for (int w = 0; w < V; ++w) s = fma(tp[u * V + w], sv[w * V + v], s);
-    wp[e] = s;
-    if (a.Wout) a.Wout[(int64_t)p * a.w_sp + (int64_t)u * a.w_su + (int64_t)v * a.w_sv] = s;
-  }
+  smem_gemm(tp, sv, wp, U, V, V);  // (S_u G[p]) S_v
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int q = warp; q < P; q += kThreads / 32) {  // H[p, q] = <wp, G_q>
-    const T s = warp_dot(wp, a.Gn + (int64_t)q * U * V, U * V, lane);
-    if (lane == 0) a.H[p * P + q] = s;
-  }
+  if (a.Wout)
+    for (int e = threadIdx.x; e < UV; e += blockDim.x)
+      a.Wout[(int64_t)p * a.w_sp + (int64_t)(e / V) * a.w_su + (int64_t)(e % V) * a.w_sv] = wp[e];
+  rows_dot(wp, gsm ? (const T*)gs : a.Gn, UV, P, a.H + (int64_t)p * P);
 }
 
 // ---------------------------------------------------------------------------
-// y3: Y3[a, b, k] = sum_j P1[a, j, k] F2[j, b]; block (k tile of 64, a).
+// y3: Y3[a, k, b] = sum_j P1[a, j, k] F2[j, b]; block (k tile of 32, a).
 // ---------------------------------------------------------------------------
+constexpr int kY3Tile = 32;
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) y3_kernel(const T* __restrict__ P1,
                                                       const T* __restrict__ F2, int N2, int N3,
                                                       int m2, T* __restrict__ Y3) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  constexpr int MT = 64;
-  const int m24 = r4(m2);
-  T* As = sm;                   // 2 x KC x MT
-  T* Bs = As + 2 * KC * MT;     // 2 x KC x m24
-  const int ai = blockIdx.y, k0 = blockIdx.x * MT;
-  const T* p1 = P1 + (int64_t)ai * N2 * N3;
-  const int nchunks = (N2 + KC - 1) / KC;
-  const bool vecA = aligned16(p1 + k0, N3, sizeof(T));
-  const bool vecB = aligned16(F2, m2, sizeof(T));
-  auto issue = [&](int c, int buf) {
-    const int j0 = c * KC;
-    const int jn = min(KC, N2 - j0);
-    stage_tile(As + buf * KC * MT, MT, p1 + (int64_t)j0 * N3 + k0, N3, KC, MT, jn, N3 - k0, vecA);
-    stage_tile(Bs + buf * KC * m24, m24, F2 + (int64_t)j0 * m2, m2, KC, m24, jn, m2, vecB);
-    cp_commit();
-  };
-  const int tiles = (MT / 4) * (m24 / 4);
-  const bool act = threadIdx.x < tiles;
-  const int kq = (threadIdx.x % (MT / 4)) * 4, bq = (threadIdx.x / (MT / 4)) * 4;
-  T acc[4][4];
-  zero4x4(acc);
-  issue(0, 0);
-  for (int c = 0; c < nchunks; ++c) {
-    if (c + 1 < nchunks) {
-      issue(c + 1, (c + 1) & 1);
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-    if (act)
-      tile4x4(As + (c & 1) * KC * MT, MT, Bs + (c & 1) * KC * m24, m24, min(KC, N2 - c * KC), kq,
-              bq, acc);
-    __syncthreads();
-  }
-  if (act) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int b = bq + j;
-      if (b >= m2) continue;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int k = k0 + kq + i;
-        if (k < N3) Y3[((int64_t)ai * m2 + b) * N3 + k] = acc[i][j];
+  const int ai = blockIdx.y, k0 = blockIdx.x * kY3Tile;
+  const int ku = min(kY3Tile, N3 - k0);
+  T* stage = sm;
+  T* cs = stage + gemm_stage_elems(kY3Tile, m2, (int)sizeof(T));
+  // The chunk size is the one the staging was sized for (a full tile of 32).
+  gemm_tn_block(P1 + (int64_t)ai * N2 * N3 + k0, N3, ku, F2, m2, m2, N2,
+                gemm_kch(kY3Tile, m2, (int)sizeof(T)), cs, stage);
+  T* y = Y3 + ((int64_t)ai * N3 + k0) * m2;
+  for (int e = threadIdx.x; e < ku * m2; e += blockDim.x) y[e] = cs[e];
+}
+
+// ---------------------------------------------------------------------------
+// mode3: rows k0 .. k0 + S - 1 of F3.
+//   Num3[k, c] = sum_{a, b} Y3[a, k, b] G[a, b, c];  F3[k] <- MU(F3[k], Num3, F3[k] H3)
+// UpdArgs: P = Y3 (m1 x N3 x m2), mu = m1, mc = m2, G = G (m1 x m2 x m3),
+// nrows = N3, mv = m3, H = H3, F = F3, rows_per_block = S.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) mode3_kernel(UpdArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int m1 = a.mu, m2 = a.mc, m3 = a.mv, S = a.rows_per_block;
+  const int K = m1 * m2, NO = S * m3;
+  const int kg = max(1, (int)blockDim.x / NO);  // K split per output
+  const bool gsm = core_in_smem<T>((int64_t)K * m3);
+  T* ys = sm;                       // m1 x S x m2
+  T* hs = ys + al4((size_t)m1 * S * m2);
+  T* fo = hs + al4(m3 * m3);         // S x m3
+  T* red = fo + al4(S * m3);         // kg x NO
+  T* gs = red + al4((size_t)kg * NO);  // K x m3 when it fits
+  const int64_t k0 = (int64_t)blockIdx.x * S;
+  const int sn = (int)min((int64_t)S, a.nrows - k0);
+
+  for (int aa = 0; aa < m1; ++aa)
+    cp_flat(ys + (int64_t)aa * S * m2, a.P + ((int64_t)aa * a.nrows + k0) * m2, (int64_t)sn * m2);
+  cp_flat(hs, a.H, m3 * m3);
+  cp_flat(fo, a.F + k0 * m3, (int64_t)sn * m3);
+  if (gsm) cp_flat(gs, a.G, (int64_t)K * m3);
+  cp_commit();
+  cp_wait<0>();
+  __syncthreads();
+
+  const T* g = gsm ? (const T*)gs : a.G;
+  if (threadIdx.x < kg * NO) {
+    // Thread (q, o): output o = (s, c) over the q-th contiguous range of t = (a, b).
+    const int q = threadIdx.x / NO, o = threadIdx.x % NO;
+    const int ss = o / m3, c = o % m3;
+    const int t0 = (int)((int64_t)K * q / kg), t1 = (int)((int64_t)K * (q + 1) / kg);
+    int aa = t0 / m2, b = t0 % m2;
+    T v = T(0);
+    for (int t = t0; t < t1; ++t) {
+      v = fma(ys[(aa * S + ss) * m2 + b], g[(int64_t)t * m3 + c], v);
+      if (++b == m2) {
+        b = 0;
+        ++aa;
       }
     }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// num3: part[s][k][c] = sum_{u in split s} Y3[u, k] G[u, c]; block (k tile, split).
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) num3_kernel(const T* __restrict__ Y3,
-                                                        const T* __restrict__ G, int UC, int N3,
-                                                        int m3, int u_per_split,
-                                                        T* __restrict__ part) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  constexpr int MT = 64;
-  const int m34 = r4(m3);
-  T* As = sm;
-  T* Bs = As + 2 * KC * MT;
-  const int k0 = blockIdx.x * MT;
-  const int ub = blockIdx.y * u_per_split, ue = min(UC, ub + u_per_split);
-  const int nchunks = (ue - ub + KC - 1) / KC;
-  const bool vecA = aligned16(Y3 + k0, N3, sizeof(T));
-  const bool vecB = aligned16(G, m3, sizeof(T));
-  auto issue = [&](int c, int buf) {
-    const int u0 = ub + c * KC;
-    const int un = min(KC, ue - u0);
-    stage_tile(As + buf * KC * MT, MT, Y3 + (int64_t)u0 * N3 + k0, N3, KC, MT, un, N3 - k0, vecA);
-    stage_tile(Bs + buf * KC * m34, m34, G + (int64_t)u0 * m3, m3, KC, m34, un, m3, vecB);
-    cp_commit();
-  };
-  const int tiles = (MT / 4) * (m34 / 4);
-  const bool act = threadIdx.x < tiles;
-  const int kq = (threadIdx.x % (MT / 4)) * 4, cq = (threadIdx.x / (MT / 4)) * 4;
-  T acc[4][4];
-  zero4x4(acc);
-  if (nchunks > 0) issue(0, 0);
-  for (int c = 0; c < nchunks; ++c) {
-    if (c + 1 < nchunks) {
-      issue(c + 1, (c + 1) & 1);
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-    if (act)
-      tile4x4(As + (c & 1) * KC * MT, MT, Bs + (c & 1) * KC * m34, m34,
-              min(KC, ue - ub - c * KC), kq, cq, acc);
-    __syncthreads();
-  }
-  if (act) {
-    T* o = part + (int64_t)blockIdx.y * N3 * m3;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int k = k0 + kq + i;
-      if (k >= N3) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (cq + j < m3) o[(int64_t)k * m3 + cq + j] = acc[i][j];
-    }
-  }
-}
-
-// tail3: Num3 = sum of splits; MU on F3 rows; BF16 operand of pass 1.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) tail3_kernel(UpdArgs<T> a, const T* __restrict__ part,
-                                                         int splits) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int MV = a.mv, S = a.rows_per_block;
-  T* hs = sm;             // MV x MV
-  T* fo = hs + MV * MV;   // S x MV
-  const int64_t r0 = (int64_t)blockIdx.x * S;
-  for (int e = threadIdx.x; e < MV * MV; e += blockDim.x) hs[e] = a.H[e];
-  for (int e = threadIdx.x; e < S * MV; e += blockDim.x) {
-    const int64_t r = r0 + e / MV;
-    fo[e] = r < a.nrows ? a.F[r * MV + e % MV] : T(0);
+    red[q * NO + o] = v;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < S * MV; e += blockDim.x) {
-    const int rr = e / MV, v = e % MV;
-    const int64_t r = r0 + rr;
-    if (r >= a.nrows) continue;
+  for (int o = threadIdx.x; o < sn * m3; o += blockDim.x) {
     T num = T(0);
-    for (int s = 0; s < splits; ++s) num += part[((int64_t)s * a.nrows + r) * MV + v];
+    for (int q = 0; q < kg; ++q) num += red[q * NO + o];
+    const int ss = o / m3, v = o % m3;
     T den = T(0);
-    for (int w = 0; w < MV; ++w) den = fma(fo[rr * MV + w], hs[w * MV + v], den);
-    const T nv = mu_step(fo[e], num, den, (T)a.eps);
-    a.F[r * MV + v] = nv;
+    for (int w = 0; w < m3; ++w) den = fma(fo[ss * m3 + w], hs[w * m3 + v], den);
+    const T nv = mu_step(fo[o], num, den, (T)a.eps);
+    const int64_t r = k0 + ss;
+    a.F[r * m3 + v] = nv;
     write_operand(a, r, v, nv);
   }
 }
 
 // ---------------------------------------------------------------------------
-// core_m: part[s][u][c] = sum_{k in split s} Y3[u, k] F3[k, c]; block (u tile, split).
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) core_m_kernel(const T* __restrict__ Y3,
-                                                          const T* __restrict__ F3, int UC,
-                                                          int N3, int m3, int k_per_split,
-                                                          T* __restrict__ part) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  constexpr int MT = 64, LDA = MT + 4;
-  const int m34 = r4(m3);
-  T* As = sm;                   // 2 x KC x LDA  (A[k][u], transposed from Y3)
-  T* Bs = As + 2 * KC * LDA;    // 2 x KC x m34
-  const int u0 = blockIdx.x * MT;
-  const int kb = blockIdx.y * k_per_split, ke = min(N3, kb + k_per_split);
-  const int nchunks = (ke - kb + KC - 1) / KC;
-  const bool vecB = aligned16(F3, m3, sizeof(T));
-  auto issue = [&](int c, int buf) {
-    const int kc0 = kb + c * KC;
-    T* A = As + buf * KC * LDA;
-    // A[k][u] = Y3[u0 + u, kc0 + k]: consecutive threads take consecutive k of one row.
-    for (int e = threadIdx.x; e < KC * MT; e += blockDim.x) {
-      const int uu = e >> 5, kk = e & (KC - 1);
-      const bool ok = (u0 + uu < UC) && (kc0 + kk < ke);
-      cp_elem(A + kk * LDA + uu, ok ? Y3 + (int64_t)(u0 + uu) * N3 + kc0 + kk : Y3, ok);
-    }
-    stage_tile(Bs + buf * KC * m34, m34, F3 + (int64_t)kc0 * m3, m3, KC, m34,
-               min(KC, ke - kc0), m3, vecB);
-    cp_commit();
-  };
-  const int tiles = (MT / 4) * (m34 / 4);
-  const bool act = threadIdx.x < tiles;
-  const int uq = (threadIdx.x % (MT / 4)) * 4, cq = (threadIdx.x / (MT / 4)) * 4;
-  T acc[4][4];
-  zero4x4(acc);
-  if (nchunks > 0) issue(0, 0);
-  for (int c = 0; c < nchunks; ++c) {
-    if (c + 1 < nchunks) {
-      issue(c + 1, (c + 1) & 1);
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-    if (act)
-      tile4x4(As + (c & 1) * KC * LDA, LDA, Bs + (c & 1) * KC * m34, m34,
-              min(KC, ke - kb - c * KC), uq, cq, acc);
-    __syncthreads();
-  }
-  if (act) {
-    T* o = part + (int64_t)blockIdx.y * UC * m3;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int u = u0 + uq + i;
-      if (u >= UC) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (cq + j < m3) o[(int64_t)u * m3 + cq + j] = acc[i][j];
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // core_a: one block per mode-1 index a (no block depends on another):
-//   S3 = F3^T F3;  M[a] = sum of the k splits;  D[a] = W3[a] x_3 S3;
-//   G[a] <- MU(G[a], M[a], D[a]);  W1[a] = S2 G[a] S3
+//   S3 = F3^T F3;  M[a] = Y3[a]^T F3 (= (X x_1 F1^T x_2 F2^T x_3 F3^T)[a]);
+//   D[a] = W3[a] x_3 S3;  G[a] <- MU(G[a], M[a], D[a]);  W1[a] = S2 G[a] S3
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) core_a_kernel(CoreArgs<T> a) {
@@ -615,44 +497,46 @@ __global__ void __launch_bounds__(kThreads) core_a_kernel(CoreArgs<T> a) {
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int m1 = a.m1, m2 = a.m2, m3 = a.m3;
   const int bc = m2 * m3;
-  T* s2 = sm;                   // m2 x m2
-  T* s3 = s2 + al4(m2 * m2);    // m3 x m3
-  T* ga = s3 + al4(m3 * m3);    // bc: G[a] (updated)
-  T* wa = ga + al4(bc);         // bc: W3[a], then scratch
-  T* stage = wa + al4(bc);      // Gram staging
+  const size_t st3 = gemm_stage_elems(m3, m3, (int)sizeof(T));
+  const size_t stm = gemm_stage_elems(m2, m3, (int)sizeof(T));
+  T* stage = sm;
+  T* s2 = stage + (st3 > stm ? st3 : stm);  // m2 x m2
+  T* s3 = s2 + al4(m2 * m2);                  // m3 x m3
+  T* ma = s3 + al4(m3 * m3);                  // bc: M[a]
+  T* wa = ma + al4(bc);                       // bc: W3[a], then scratch
+  T* ga = wa + al4(bc);                       // bc: G[a]
   const int aa = blockIdx.x;
   const int64_t off = (int64_t)aa * bc;
-  for (int e = threadIdx.x; e < m2 * m2; e += blockDim.x) s2[e] = a.S2[e];
-  for (int e = threadIdx.x; e < bc; e += blockDim.x) wa[e] = a.W3[off + e];
-  gram_block(a.F3, a.n3, m3, s3, stage);  // ends with a barrier
+
+  cp_flat(s2, a.S2, m2 * m2);
+  cp_flat(wa, a.W3 + off, bc);
+  cp_flat(ga, a.G + off, bc);
+  cp_commit();
+  gemm_tn_block(a.F3, m3, m3, a.F3, m3, m3, (int)a.n3, gemm_kch(m3, m3, (int)sizeof(T)), s3,
+                stage);
+  gemm_tn_block(a.Y3 + (int64_t)aa * a.n3 * m2, m2, m2, a.F3, m3, m3, (int)a.n3,
+                gemm_kch(m2, m3, (int)sizeof(T)), ma, stage);
   if (aa == 0)
     for (int e = threadIdx.x; e < m3 * m3; e += blockDim.x) a.S3_out[e] = s3[e];
   for (int e = threadIdx.x; e < bc; e += blockDim.x) {
     const int b = e / m3, c = e % m3;
     T d = T(0);
     for (int w = 0; w < m3; ++w) d = fma(wa[b * m3 + w], s3[w * m3 + c], d);
-    T mv = T(0);
-    for (int s = 0; s < a.M_splits; ++s) mv += a.M[(int64_t)s * m1 * bc + off + e];
-    const T gv = mu_step(a.G[off + e], mv, d, (T)a.eps);
+    const T gv = mu_step(ga[e], ma[e], d, (T)a.eps);
     ga[e] = gv;
     a.G[off + e] = gv;
     a.G2[((int64_t)b * m1 + aa) * m3 + c] = gv;  // G permuted to (m2, m1, m3)
     a.G3[((int64_t)c * m1 + aa) * m2 + b] = gv;  // G permuted to (m3, m1, m2)
-    a.Mout[off + e] = mv;
+    a.Mout[off + e] = ma[e];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < bc; e += blockDim.x) {  // scratch = S2 G[a]
-    const int b = e / m3, c = e % m3;
-    T s = T(0);
-    for (int w = 0; w < m2; ++w) s = fma(s2[b * m2 + w], ga[w * m3 + c], s);
-    wa[e] = s;
-  }
+  smem_gemm(s2, ga, wa, m2, m2, m3);  // S2 G[a]
   __syncthreads();
-  for (int e = threadIdx.x; e < bc; e += blockDim.x) {  // W1[a] = scratch S3
+  for (int e = threadIdx.x; e < bc; e += blockDim.x) {  // W1[a] = (S2 G[a]) S3
     const int b = e / m3, c = e % m3;
-    T s = T(0);
-    for (int w = 0; w < m3; ++w) s = fma(wa[b * m3 + w], s3[w * m3 + c], s);
-    a.W1[off + e] = s;
+    T v = T(0);
+    for (int w = 0; w < m3; ++w) v = fma(wa[b * m3 + w], s3[w * m3 + c], v);
+    a.W1[off + e] = v;
   }
 }
 
@@ -671,20 +555,21 @@ __global__ void __launch_bounds__(kThreads) core_b_kernel(CoreArgs<T> a) {
   __shared__ int last;
   const int m1 = a.m1, m2 = a.m2, m3 = a.m3;
   const int bc = m2 * m3;
-  T* wa = sm;  // bc: W1[a]
+  const bool gsm = core_in_smem<T>((int64_t)m1 * bc);
+  T* wa = sm;             // bc: W1[a]
+  T* gs = wa + al4(bc);   // m1 x bc when it fits
   const int aa = blockIdx.x;
   const int64_t off = (int64_t)aa * bc;
-  for (int e = threadIdx.x; e < bc; e += blockDim.x) wa[e] = a.W1[off + e];
-  __syncthreads();
+  cp_flat(wa, a.W1 + off, bc);
+  if (gsm) cp_flat(gs, a.G, (int64_t)m1 * bc);
+  cp_commit();
   double mg = 0.0;
   for (int e = threadIdx.x; e < bc; e += blockDim.x)
     mg += (double)a.Mout[off + e] * (double)a.G[off + e];
+  cp_wait<0>();
+  __syncthreads();
   mg = block_sum(mg, red);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int q = warp; q < m1; q += kThreads / 32) {
-    const T s = warp_dot(wa, a.G + (int64_t)q * bc, bc, lane);
-    if (lane == 0) a.H1[aa * m1 + q] = s;
-  }
+  rows_dot(wa, gsm ? (const T*)gs : a.G, bc, m1, a.H1 + (int64_t)aa * m1);
   __syncthreads();
   if (threadIdx.x == 0) {
     a.dots[aa] = mg;
@@ -733,23 +618,9 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ F,
                                                         T* __restrict__ S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  gram_block(F, N, m, sm, sm + al4(m * m));
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) S[e] = sm[e];
-}
-
-template <typename T>
-size_t gram_stage_elems(int m) {
-  const int mq = r4(m) / 4, tiles = mq * mq;
-  const int groups = kThreads / tiles > 1 ? kThreads / tiles : 1;
-  return al4((size_t)gram_rows(m, (int)sizeof(T)) * r4(m)) + (size_t)groups * m * m;
-}
-
-int split_count(int64_t blocks, int64_t len, int chunk) {
-  const int64_t target = 2LL * device_sm_count();
-  int64_t s = (target + blocks - 1) / blocks;
-  const int64_t max_s = (len + chunk - 1) / chunk;
-  if (s > max_s) s = max_s;
-  return (int)(s < 1 ? 1 : s);
+  T* c = sm + gemm_stage_elems(m, m, (int)sizeof(T));
+  gemm_tn_block(F, m, m, F, m, m, (int)N, gemm_kch(m, m, (int)sizeof(T)), c, sm);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) S[e] = c[e];
 }
 
 }  // namespace
@@ -758,28 +629,23 @@ int split_count(int64_t blocks, int64_t len, int chunk) {
 // Launchers
 // ---------------------------------------------------------------------------
 
-template <typename T>
-int upd_rows_per_block(int mu, int mc, int64_t nrows) {
-  const int tiles = (r4(mu) / 4) * (r4(mc) / 4);
-  int s = kThreads / tiles;
-  if (s < 1) s = 1;
-  // Keep about two blocks per SM in flight.
-  const int64_t want = (nrows + 2LL * device_sm_count() - 1) / (2LL * device_sm_count());
-  if (s > want) s = (int)(want < 1 ? 1 : want);
-  return s;
+namespace {
+template <typename K>
+int set_smem(K kernel, size_t bytes) {
+  NNC_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return NNC_OK;
 }
+}  // namespace
 
 template <typename T>
 int launch_upd12(const UpdArgs<T>& a, cudaStream_t s) {
-  const int tiles = (r4(a.mu) / 4) * (r4(a.mc) / 4);
-  if (tiles * a.rows_per_block > kThreads) return NNC_ERR_UNSUPPORTED;
-  const int S = a.rows_per_block;
-  const size_t smem = sizeof(T) * ((size_t)2 * KC * r4(a.mu) + (size_t)2 * S * KC * r4(a.mc) +
-                                   (size_t)S * a.mu * a.mc + (size_t)S * a.mv +
-                                   (size_t)a.mv * a.mv + (size_t)S * a.mv);
-  NNC_CUDA_TRY(cudaFuncSetAttribute(upd12_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  upd12_kernel<T><<<(unsigned)ceil_div(a.nrows, S), kThreads, smem, s>>>(a);
+  if (a.mu > 64 || a.mc > 64 || a.mv > 64) return NNC_ERR_UNSUPPORTED;
+  const int UC = a.mu * a.mc;
+  const size_t smem =
+      sizeof(T) * (gemm_stage_elems(a.mu, a.mc, (int)sizeof(T)) + al4(UC) + al4(a.mv * a.mv) +
+                   2 * al4(a.mv) + (core_in_smem<T>((int64_t)a.mv * UC) ? (size_t)a.mv * UC : 0));
+  NNC_TRY(set_smem(upd12_kernel<T>, smem));
+  upd12_kernel<T><<<(unsigned)a.nrows, kThreads, smem, s>>>(a);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
   return NNC_OK;
@@ -787,12 +653,14 @@ int launch_upd12(const UpdArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 int launch_hmat(const HArgs<T>& a, cudaStream_t s) {
-  const size_t g = gram_stage_elems<T>(a.mu) > gram_stage_elems<T>(a.mv) ? gram_stage_elems<T>(a.mu)
-                                                                          : gram_stage_elems<T>(a.mv);
-  const size_t smem = sizeof(T) * (al4((size_t)a.mu * a.mu) + al4((size_t)a.mv * a.mv) +
-                                   3 * al4((size_t)a.mu * a.mv) + g);
-  NNC_CUDA_TRY(cudaFuncSetAttribute(hmat_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  if (a.mu > 64 || a.mv > 64) return NNC_ERR_UNSUPPORTED;
+  const size_t st_u = a.fu ? gemm_stage_elems(a.mu, a.mu, (int)sizeof(T)) : 0;
+  const size_t st_v = a.fv ? gemm_stage_elems(a.mv, a.mv, (int)sizeof(T)) : 0;
+  const int64_t guv = (int64_t)a.mp * a.mu * a.mv;
+  const size_t smem = sizeof(T) * ((st_u > st_v ? st_u : st_v) + al4(a.mu * a.mu) +
+                                   al4(a.mv * a.mv) + 3 * al4(a.mu * a.mv) +
+                                   (core_in_smem<T>(guv) ? (size_t)guv : 0));
+  NNC_TRY(set_smem(hmat_kernel<T>, smem));
   hmat_kernel<T><<<a.mp, kThreads, smem, s>>>(a);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
@@ -801,11 +669,11 @@ int launch_hmat(const HArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 int launch_y3(const T* P1, const T* F2, int m1, int N2, int N3, int m2, T* Y3, cudaStream_t s) {
-  if ((64 / 4) * (r4(m2) / 4) > kThreads) return NNC_ERR_UNSUPPORTED;
-  const size_t smem = sizeof(T) * ((size_t)2 * KC * 64 + (size_t)2 * KC * r4(m2));
-  NNC_CUDA_TRY(cudaFuncSetAttribute(y3_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  dim3 grid((unsigned)ceil_div(N3, 64), (unsigned)m1);
+  if (m2 > 64) return NNC_ERR_UNSUPPORTED;
+  const size_t smem =
+      sizeof(T) * (gemm_stage_elems(kY3Tile, m2, (int)sizeof(T)) + al4((size_t)kY3Tile * m2));
+  NNC_TRY(set_smem(y3_kernel<T>, smem));
+  dim3 grid((unsigned)ceil_div(N3, kY3Tile), (unsigned)m1);
   y3_kernel<T><<<grid, kThreads, smem, s>>>(P1, F2, N2, N3, m2, Y3);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
@@ -813,72 +681,42 @@ int launch_y3(const T* P1, const T* F2, int m1, int N2, int N3, int m2, T* Y3, c
 }
 
 template <typename T>
-int num3_splits(int UC, int N3) {
-  return split_count(ceil_div(N3, 64), UC, KC);
+int mode3_rows_per_block(int m3) {
+  const int s = 128 / m3;
+  return s < 1 ? 1 : (s > 4 ? 4 : s);
 }
 
 template <typename T>
-int launch_mode3(const UpdArgs<T>& a, T* part, int splits, cudaStream_t s) {
-  const int UC = a.mu, N3 = (int)a.nrows, m3 = a.mv;
-  if ((64 / 4) * (r4(m3) / 4) > kThreads) return NNC_ERR_UNSUPPORTED;
-  int per = (int)ceil_div(UC, splits);
-  per = (int)(ceil_div(per, KC) * KC);
-  const int used = (int)ceil_div(UC, per);
-  const size_t smem = sizeof(T) * ((size_t)2 * KC * 64 + (size_t)2 * KC * r4(m3));
-  NNC_CUDA_TRY(cudaFuncSetAttribute(num3_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  dim3 grid((unsigned)ceil_div(N3, 64), (unsigned)used);
-  num3_kernel<T><<<grid, kThreads, smem, s>>>(a.P, a.G, UC, N3, m3, per, part);
+int launch_mode3(const UpdArgs<T>& a, cudaStream_t s) {
+  const int m1 = a.mu, m2 = a.mc, m3 = a.mv, S = a.rows_per_block;
+  if (m3 > 64 || S < 1 || S * m3 > kThreads) return NNC_ERR_UNSUPPORTED;
+  const int NO = S * m3, kg = kThreads / NO > 1 ? kThreads / NO : 1;
+  const int64_t K = (int64_t)m1 * m2;
+  const size_t smem = sizeof(T) * (al4((size_t)m1 * S * m2) + al4(m3 * m3) + al4(S * m3) +
+                                   al4((size_t)kg * NO) +
+                                   (core_in_smem<T>(K * m3) ? (size_t)(K * m3) : 0));
+  NNC_TRY(set_smem(mode3_kernel<T>, smem));
+  mode3_kernel<T><<<(unsigned)ceil_div(a.nrows, S), kThreads, smem, s>>>(a);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
-  const int S = 8;
-  UpdArgs<T> t = a;
-  t.rows_per_block = S;
-  const size_t smem2 = sizeof(T) * ((size_t)m3 * m3 + (size_t)S * m3);
-  NNC_CUDA_TRY(cudaFuncSetAttribute(tail3_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem2));
-  tail3_kernel<T><<<(unsigned)ceil_div(N3, S), kThreads, smem2, s>>>(t, part, used);
-  note_launch(s);
-  NNC_CUDA_TRY(cudaGetLastError());
-  return NNC_OK;
-}
-
-template <typename T>
-int core_m_splits(int UC, int N3) {
-  return split_count(ceil_div(UC, 64), N3, KC);
-}
-
-template <typename T>
-int launch_core_m(const T* Y3, const T* F3, int UC, int N3, int m3, T* part, int splits,
-                  int* used_splits, cudaStream_t s) {
-  if ((64 / 4) * (r4(m3) / 4) > kThreads) return NNC_ERR_UNSUPPORTED;
-  int per = (int)ceil_div(N3, splits);
-  per = (int)(ceil_div(per, KC) * KC);
-  const int used = (int)ceil_div(N3, per);
-  const size_t smem = sizeof(T) * ((size_t)2 * KC * 68 + (size_t)2 * KC * r4(m3));
-  NNC_CUDA_TRY(cudaFuncSetAttribute(core_m_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  dim3 grid((unsigned)ceil_div(UC, 64), (unsigned)used);
-  core_m_kernel<T><<<grid, kThreads, smem, s>>>(Y3, F3, UC, N3, m3, per, part);
-  note_launch(s);
-  NNC_CUDA_TRY(cudaGetLastError());
-  *used_splits = used;
   return NNC_OK;
 }
 
 template <typename T>
 int launch_core(const CoreArgs<T>& a, cudaStream_t s) {
-  const size_t bc = (size_t)a.m2 * a.m3;
-  const size_t smem_a = sizeof(T) * (al4((size_t)a.m2 * a.m2) + al4((size_t)a.m3 * a.m3) +
-                                     2 * al4(bc) + gram_stage_elems<T>(a.m3));
-  NNC_CUDA_TRY(cudaFuncSetAttribute(core_a_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem_a));
+  if (a.m1 > 64 || a.m2 > 64 || a.m3 > 64) return NNC_ERR_UNSUPPORTED;
+  const int bc = a.m2 * a.m3;
+  const size_t st3 = gemm_stage_elems(a.m3, a.m3, (int)sizeof(T));
+  const size_t stm = gemm_stage_elems(a.m2, a.m3, (int)sizeof(T));
+  const size_t smem_a = sizeof(T) * ((st3 > stm ? st3 : stm) + al4(a.m2 * a.m2) +
+                                     al4(a.m3 * a.m3) + 3 * al4(bc));
+  NNC_TRY(set_smem(core_a_kernel<T>, smem_a));
   core_a_kernel<T><<<a.m1, kThreads, smem_a, s>>>(a);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
-  const size_t smem_b = sizeof(T) * al4(bc);
-  NNC_CUDA_TRY(cudaFuncSetAttribute(core_b_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem_b));
+  const int64_t g = (int64_t)a.m1 * bc;
+  const size_t smem_b = sizeof(T) * (al4(bc) + (core_in_smem<T>(g) ? (size_t)g : 0));
+  NNC_TRY(set_smem(core_b_kernel<T>, smem_b));
   core_b_kernel<T><<<a.m1, kThreads, smem_b, s>>>(a);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
@@ -887,9 +725,9 @@ int launch_core(const CoreArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 int launch_gram(const T* F, int64_t N, int m, T* S, cudaStream_t s) {
-  const size_t smem = sizeof(T) * (al4((size_t)m * m) + gram_stage_elems<T>(m));
-  NNC_CUDA_TRY(cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  if (m > 64) return NNC_ERR_UNSUPPORTED;
+  const size_t smem = sizeof(T) * (gemm_stage_elems(m, m, (int)sizeof(T)) + al4((size_t)m * m));
+  NNC_TRY(set_smem(gram_kernel<T>, smem));
   gram_kernel<T><<<1, kThreads, smem, s>>>(F, N, m, S);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
@@ -906,15 +744,11 @@ int launch_permute_core(const T* G, int m1, int m2, int m3, T* G2, T* G3, cudaSt
 }
 
 #define NNC_SWEEP_INST(T)                                                                   \
-  template int upd_rows_per_block<T>(int, int, int64_t);                                    \
   template int launch_upd12<T>(const UpdArgs<T>&, cudaStream_t);                            \
   template int launch_hmat<T>(const HArgs<T>&, cudaStream_t);                               \
   template int launch_y3<T>(const T*, const T*, int, int, int, int, T*, cudaStream_t);      \
-  template int num3_splits<T>(int, int);                                                    \
-  template int launch_mode3<T>(const UpdArgs<T>&, T*, int, cudaStream_t);                   \
-  template int core_m_splits<T>(int, int);                                                  \
-  template int launch_core_m<T>(const T*, const T*, int, int, int, T*, int, int*,           \
-                                cudaStream_t);                                              \
+  template int mode3_rows_per_block<T>(int);                                                \
+  template int launch_mode3<T>(const UpdArgs<T>&, cudaStream_t);                            \
   template int launch_core<T>(const CoreArgs<T>&, cudaStream_t);                            \
   template int launch_gram<T>(const T*, int64_t, int, T*, cudaStream_t);                    \
   template int launch_permute_core<T>(const T*, int, int, int, T*, T*, cudaStream_t);

@@ -11,7 +11,7 @@ namespace nnc {
 template <typename T>
 struct UpdArgs {
   // Y_r[u, c] = sum_{t < len} Fc[t, u] P[r prow + t pstride + c]  (modes 1, 2)
-  // mode 3: P = Y3 (mu = m1 m2 rows of length nrows = N3)
+  // mode 3: P = Y3 laid out (mu = m1, nrows = N3, mc = m2)
   const T* P;
   int64_t prow, pstride;
   const T* Fc;
@@ -26,7 +26,7 @@ struct UpdArgs {
   int mv;
   const T* H;
   double eps;
-  int rows_per_block;
+  int rows_per_block;  // mode 3 only (modes 1, 2: one row per block)
   // Optional operand of the next tensor-core pass, entry [v bt_ld + r] for
   // F[r, v] (times bt_scale[r] if given): BF16 (bt) or the TF32 pair (bhi, blo).
   __nv_bfloat16* bt;
@@ -62,9 +62,8 @@ struct CoreArgs {
   T* G;
   T* G2;                // out: G permuted to (m2, m1, m3)
   T* G3;                // out: G permuted to (m3, m1, m2)
-  const T* M;           // M_splits partial numerators, each m1 x m2 x m3
-  int M_splits;
-  T* Mout;              // their sum
+  const T* Y3;          // X x_1 F1^T x_2 F2^T laid out (m1, N3, m2)
+  T* Mout;              // M = Y3 x_3 F3^T, laid out like G
   const T* W3;          // G x_1 S1 x_2 S2
   const T* S1;
   const T* S2;
@@ -82,26 +81,18 @@ struct CoreArgs {
   int m1, m2, m3;
   double eps;
 };
-
-template <typename T>
-int upd_rows_per_block(int mu, int mc, int64_t nrows);
 template <typename T>
 int launch_upd12(const UpdArgs<T>& a, cudaStream_t s);
 template <typename T>
 int launch_hmat(const HArgs<T>& a, cudaStream_t s);
+// Y3[a, k, b] = sum_j P1[a, j, k] F2[j, b], laid out (m1, N3, m2).
 template <typename T>
 int launch_y3(const T* P1, const T* F2, int m1, int N2, int N3, int m2, T* Y3, cudaStream_t s);
-// Mode 3: Num3 split over (a, b) into `part` (splits x N3 x m3), then MU.
+// Mode 3 (Num3 from Y3 and G, MU on F3), rows_per_block rows of F3 per block.
 template <typename T>
-int num3_splits(int UC, int N3);
+int mode3_rows_per_block(int m3);
 template <typename T>
-int launch_mode3(const UpdArgs<T>& a, T* part, int splits, cudaStream_t s);
-// M = Y3 x_3 F3^T split over k into `part` (splits x UC x m3).
-template <typename T>
-int core_m_splits(int UC, int N3);
-template <typename T>
-int launch_core_m(const T* Y3, const T* F3, int UC, int N3, int m3, T* part, int splits,
-                  int* used_splits, cudaStream_t s);
+int launch_mode3(const UpdArgs<T>& a, cudaStream_t s);
 template <typename T>
 int launch_core(const CoreArgs<T>& a, cudaStream_t s);
 template <typename T>
