@@ -133,7 +133,7 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     UpdArgs<T> u{};
     u.P = b.Y3;  u.mu = m1;  u.mc = m2;  // Y3 laid out (m1, N3, m2)
     u.G = G;
-    u.rows_per_block = mode3_rows_per_block<T>(m3);
+    u.rows_per_block = mode3_rows_per_block<T>(m3, N3);
     u.F = F[2];  u.nrows = N3;  u.mv = m3;  u.H = b.H[2];  u.eps = eps;
     if constexpr (std::is_same<T, float>::value) {
       if (tcp) {

@@ -21,11 +21,12 @@
 // These kernels are latency-bound (a few MFLOP each on L2-resident data), so
 // each block requests everything it needs up front (cp.async) and spreads every
 // contraction over all its threads: the block GEMM splits the contraction
-// across thread groups (4 x 4 register tiles per thread) and adds the group
-// partials in a fixed order. Every reduction
-// runs in a fixed order, so results are deterministic. The BF16 path also
-// writes, from the mode-1 and mode-3 updates, the BF16 operand of the next
-// pass over X.
+// across thread groups (4 x 4 register tiles per thread). Most blocks run
+// their code once per sweep with a cold instruction cache, so the shared
+// helpers are kept out of line and not unrolled (one copy of the code per
+// kernel). Every reduction runs in a fixed order, so results are
+// deterministic. The BF16 path also writes, from the mode-1 and mode-3
+// updates, the BF16 operand of the next pass over X.
 #include <cuda_bf16.h>
 
 #include <type_traits>
@@ -167,7 +168,7 @@ __device__ __forceinline__ void zero4x4(T (&acc)[4][4]) {
 // dst[e] = src[e] for e < n by cp.async (16-byte vectors when both ends allow),
 // issued by the whole block; the caller commits and waits.
 template <typename T>
-__device__ __forceinline__ void cp_flat(T* dst, const T* __restrict__ src, int64_t n) {
+__device__ __noinline__ void cp_flat(T* dst, const T* __restrict__ src, int64_t n) {
   constexpr int W = 16 / (int)sizeof(T);
   if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
     const int64_t nv = n / W;
@@ -190,9 +191,12 @@ __host__ __device__ inline int gemm_groups(int mu, int mc) {
   const int g = kThreads / gemm_tiles(mu, mc);
   return g > 1 ? g : 1;
 }
-// Rows per chunk: two chunks of both operands in about 48 KB, a multiple of 8.
+// Rows per chunk: two chunks of both operands take at most 96 KB (FP32) or
+// 48 KB (FP64); a multiple of 8. FP32 stages a contraction of up
+// to 256 rows in one round trip for m <= 24.
 __host__ __device__ inline int gemm_kch(int mu, int mc, int elem) {
-  int k = (48 * 1024) / (2 * (r4(mu) + r4(mc)) * elem);
+  const int budget = elem > 4 ? 3 * 1024 : 12 * 1024;  // elements of one chunk of A and B
+  int k = budget / (r4(mu) + r4(mc));
   k = k > 256 ? 256 : k;
   k &= ~7;
   return k < 8 ? 8 : k;
@@ -204,7 +208,7 @@ __host__ __device__ inline size_t gemm_stage_elems(int mu, int mc, int elem) {
 }
 
 template <typename T>
-__device__ void gemm_tn_block(const T* __restrict__ A, int64_t lda, int mu,
+__device__ __noinline__ void gemm_tn_block(const T* __restrict__ A, int64_t lda, int mu,
                               const T* __restrict__ B, int64_t ldb, int mc, int len, int kch,
                               T* C, T* stage) {
   const int mu4 = r4(mu), mc4 = r4(mc), tq = mc4 / 4;
@@ -237,7 +241,7 @@ __device__ void gemm_tn_block(const T* __restrict__ A, int64_t lda, int mu,
       const int kn = min(kch, len - c * kch);
       const T* a = As + (c & 1) * kch * mu4 + u0;
       const T* b = Bs + (c & 1) * kch * mc4 + c0;
-#pragma unroll 4
+#pragma unroll 1
       for (int k = g; k < kn; k += groups) {
         T x[4], y[4];
         ld4(a + k * mu4, x);
@@ -274,7 +278,7 @@ __device__ void gemm_tn_block(const T* __restrict__ A, int64_t lda, int mu,
 
 // C (m x n) = A (m x k) B (k x n), all row-major in shared memory; whole block.
 template <typename T>
-__device__ __forceinline__ void smem_gemm(const T* A, const T* B, T* C, int m, int k, int n) {
+__device__ __noinline__ void smem_gemm(const T* A, const T* B, T* C, int m, int k, int n) {
   for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
     T s0 = T(0), s1 = T(0);
@@ -290,7 +294,7 @@ __device__ __forceinline__ void smem_gemm(const T* A, const T* B, T* C, int m, i
 
 // out[q] = <x, Y[q, :]> for q < nq (rows of length n, row stride n); a warp per q.
 template <typename T>
-__device__ __forceinline__ void rows_dot(const T* x, const T* Y, int n, int nq, T* out) {
+__device__ __noinline__ void rows_dot(const T* x, const T* Y, int n, int nq, T* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int q = warp; q < nq; q += nw) {
     const T* y = Y + (int64_t)q * n;
@@ -681,9 +685,12 @@ int launch_y3(const T* P1, const T* F2, int m1, int N2, int N3, int m2, T* Y3, c
 }
 
 template <typename T>
-int mode3_rows_per_block(int m3) {
-  const int s = 128 / m3;
-  return s < 1 ? 1 : (s > 4 ? 4 : s);
+int mode3_rows_per_block(int m3, int64_t n3) {
+  // About 128 blocks or more, at most 128 outputs (S x m3) per block.
+  int s = (int)(n3 / 128);
+  const int cap = 128 / m3 < 4 ? 128 / m3 : 4;
+  s = s > cap ? cap : s;
+  return s < 1 ? 1 : s;
 }
 
 template <typename T>
@@ -747,7 +754,7 @@ int launch_permute_core(const T* G, int m1, int m2, int m3, T* G2, T* G3, cudaSt
   template int launch_upd12<T>(const UpdArgs<T>&, cudaStream_t);                            \
   template int launch_hmat<T>(const HArgs<T>&, cudaStream_t);                               \
   template int launch_y3<T>(const T*, const T*, int, int, int, int, T*, cudaStream_t);      \
-  template int mode3_rows_per_block<T>(int);                                                \
+  template int mode3_rows_per_block<T>(int, int64_t);                                                \
   template int launch_mode3<T>(const UpdArgs<T>&, cudaStream_t);                            \
   template int launch_core<T>(const CoreArgs<T>&, cudaStream_t);                            \
   template int launch_gram<T>(const T*, int64_t, int, T*, cudaStream_t);                    \

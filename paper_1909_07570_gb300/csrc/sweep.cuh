@@ -90,7 +90,7 @@ template <typename T>
 int launch_y3(const T* P1, const T* F2, int m1, int N2, int N3, int m2, T* Y3, cudaStream_t s);
 // Mode 3 (Num3 from Y3 and G, MU on F3), rows_per_block rows of F3 per block.
 template <typename T>
-int mode3_rows_per_block(int m3);
+int mode3_rows_per_block(int m3, int64_t n3);
 template <typename T>
 int launch_mode3(const UpdArgs<T>& a, cudaStream_t s);
 template <typename T>

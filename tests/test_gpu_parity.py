@@ -40,7 +40,7 @@ def _run_ntd(X, F0, G0, iters, dtype, **kw):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("dims,m", [((37, 29, 23), (5, 6, 7)), ((70, 45, 133), (9, 17, 20)),
-                                    ((300, 9, 65), (33, 4, 64))])
+                                    ((300, 9, 65), (33, 4, 64)), ((70, 66, 68), (64, 64, 64))])
 def test_ntd_one_sweep_fp64_elementwise(dims, m):
     X, _, F0, G0, _ = inputs.small_problem(dims, 4, m, 3, seed=101)
     err, tr, F, G = _run_ntd(X, F0, G0, 1, torch.float64)
@@ -53,7 +53,7 @@ def test_ntd_one_sweep_fp64_elementwise(dims, m):
 
 
 @pytest.mark.parametrize("dims,m", [((37, 29, 23), (5, 6, 7)), ((70, 45, 133), (9, 17, 20)),
-                                    ((257, 130, 97), (32, 24, 16))])
+                                    ((257, 130, 97), (32, 24, 16)), ((70, 66, 68), (64, 64, 64))])
 def test_ntd_one_sweep_fp32_elementwise(dims, m):
     X, _, F0, G0, _ = inputs.small_problem(dims, 5, m, 3, seed=202, zero_frac=0.2, noise=0.02)
     err, tr, F, G = _run_ntd(X, F0, G0, 1, torch.float32)
