@@ -25,8 +25,12 @@ from .nncandelinc import (  # noqa: F401
     DEFAULT_EPS,
     congruence_matrix,
     lift,
+    POWER_ITERS,
+    lifted_block_terms,
     lifted_loss,
     lifted_loss_grad,
+    lifted_pg_fit,
+    lifted_pg_step,
     mean_congruence,
     mu_step,
     nncp_fit,
@@ -36,6 +40,7 @@ from .nncandelinc import (  # noqa: F401
     ntd_factor_terms,
     ntd_fit,
     ntd_sweep,
+    power_iteration_lmax,
     rel_err_cp,
     rel_err_tucker,
     residual_sq_identity,

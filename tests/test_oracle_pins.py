@@ -295,3 +295,62 @@ def test_recovery_of_a_planted_canonical_tucker():
     A_hat = orc.lift(F, B)
     assert orc.rel_err_cp(X, A_hat) < 0.15
     assert orc.mean_congruence(A, A_hat) > 0.8
+
+
+# ---------------------------------------------------------------------------
+# Differentiation form: block projected gradient on the lifted loss
+# ---------------------------------------------------------------------------
+
+def test_power_iteration_lmax_against_eigendecomposition():
+    # Closed form: a diagonal matrix; a rank-one matrix u u^T has lmax = |u|^2.
+    assert orc.power_iteration_lmax(np.diag([1.0, 4.0, 2.5])) == pytest.approx(4.0, rel=1e-9)
+    u = RNG.random(7)
+    assert orc.power_iteration_lmax(np.outer(u, u)) == pytest.approx(u @ u, rel=1e-12)
+    assert orc.power_iteration_lmax(np.zeros((3, 3))) == 0.0
+    for n in (3, 12, 24):
+        Q = RNG.random((40, n))
+        H = Q.T @ Q  # nonnegative Gram: a dominant Perron eigenvalue
+        assert orc.power_iteration_lmax(H) == pytest.approx(np.linalg.eigvalsh(H)[-1], rel=1e-10)
+
+
+@pytest.mark.parametrize("dims,m,r", [((4, 3, 5), (2, 3, 2), 2), ((3, 3, 2, 4), (2, 2, 2, 3), 3)])
+def test_lifted_block_terms_are_the_gradient_in_A(dims, m, r):
+    # dL/dA^(n) = A^(n) V - MT, with L = 1/2 ||X - I x_k A^(k)||^2 by differences.
+    X = RNG.random(dims)
+    A = [RNG.random((n, r)) for n in dims]
+
+    def loss():
+        R = X - orc.cp_reconstruct(A)
+        return 0.5 * np.sum(R * R)
+
+    for n in range(len(dims)):
+        MT, V = orc.lifted_block_terms(X, A, n)
+        np.testing.assert_allclose(A[n] @ V - MT, _fd_grad(loss, A[n]), rtol=1e-6, atol=1e-7)
+
+
+def test_lifted_pg_exact_lift_is_a_fixed_point():
+    # X = I x_i F^(i) B^(i) exactly: every block gradient vanishes, so a step
+    # changes nothing and the loss stays 0.
+    dims, m, r = (6, 5, 7), (3, 4, 3), 3
+    rng = np.random.default_rng(77)
+    F = [rng.random((n, k)) + 0.1 for n, k in zip(dims, m)]
+    B = [rng.random((k, r)) + 0.1 for k in m]
+    X = orc.cp_reconstruct(orc.lift(F, B))
+    F1, B1 = orc.lifted_pg_step(X, F, B)
+    for a, b in zip(F1 + B1, F + B):
+        np.testing.assert_allclose(a, b, rtol=1e-11, atol=1e-13)
+    assert orc.lifted_loss(X, F1, B1) < 1e-20 * np.sum(X * X)
+
+
+@pytest.mark.parametrize("dims,m,r", [((9, 8, 7), (3, 4, 5), 4), ((6, 5, 4, 5), (3, 3, 2, 3), 3)])
+def test_lifted_pg_monotone_and_nonnegative(dims, m, r):
+    X, _, _, _, _ = inputs.small_problem(dims, 3, m, r, seed=31)
+    rng = np.random.default_rng(5)
+    F0 = [1.0 - rng.random((n, k)) for n, k in zip(dims, m)]
+    B0 = [1.0 - rng.random((k, r)) for k in m]
+    F, B, tr = orc.lifted_pg_fit(X, F0, B0, 40)
+    l0 = orc.lifted_loss(X, F0, B0)
+    assert tr[0] <= l0 * (1 + 1e-12)
+    assert np.all(np.diff(tr) <= 1e-12 * tr[:-1])
+    assert tr[-1] < 0.5 * l0
+    assert all((a >= 0).all() for a in F + B)
