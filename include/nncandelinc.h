@@ -201,6 +201,52 @@ int candelinc_lift(int d, const int64_t* dims, const int* m, int r, int precisio
                    const void* const* F, const void* const* B, void* const* A, void* stream);
 
 /*
+ * candelinc_lifted_grad - the adjoint of the nnCANDELINC objective with the
+ * CPD of the core substituted (Eq. nnCANDELINC, Sec. 4; the substitution
+ * A^(n) = F^(n) B^(n) of the proof of Lemma "rank and min exists"):
+ *   L = 1/2 ||X - I x_n F^(n) B^(n)||_F^2,
+ *   dL/dA^(n) = A^(n) V_n - unfold_n(X x_{k!=n} F^(k)T) KR_{k!=n}(B^(k)),
+ *   V_n = Hadamard_{k!=n} A^(k)T A^(k),
+ *   dL/dF^(n) = dL/dA^(n) B^(n)T,   dL/dB^(n) = F^(n)T dL/dA^(n).
+ * Reads X twice (X x_d F^(d)T and X x_1 F^(1)T; once when only the loss is
+ * asked for).
+ *
+ *  X          device, C order, d = 3 or 4 modes dims[0..d-1]
+ *  m, r       m[n] <= 64, 1 <= r <= 64
+ *  F, B       host arrays of d device pointers: F^(n) dims[n] x m[n],
+ *             B^(n) m[n] x r, row-major (read only)
+ *  gF, gB     host arrays of d device pointers shaped like F and B (written),
+ *             or both NULL for the loss alone
+ *  loss       host, L with FP64 accumulation (may be NULL when gF is given)
+ *  precision  NNC_FP64 (double); NNC_FP32 (float, TF32x3 tensor-core passes
+ *             where the shape allows, else SIMT); NNC_FP32_SIMT (float)
+ * Errors: INVALID_ARG, NONFINITE (X), UNSUPPORTED (NNC_BF16_REFINE), CUDA,
+ * ALLOC, TIMEOUT.
+ */
+int candelinc_lifted_grad(const void* X, int d, const int64_t* dims, const int* m, int r,
+                          int precision, const void* const* F, const void* const* B,
+                          void* const* gF, void* const* gB, double* loss, void* stream);
+
+/*
+ * candelinc_pg_fit - `steps` block-coordinate projected-gradient steps on the
+ * same L, in place on F and B. The paper gives no first-order method for Eq.
+ * nnCANDELINC; the reading taken: for n = 1..d,
+ *   F^(n) <- max(F^(n) - dL/dF^(n) / L_F, 0),  L_F = lmax(B^(n) V_n B^(n)T),
+ *   B^(n) <- max(B^(n) - dL/dB^(n) / L_B, 0),  L_B = lmax(F^(n)T F^(n)) lmax(V_n),
+ * the B gradient taken after the F update, lmax from 30 FP64 power iterations
+ * from the all-ones vector (Rayleigh quotient). Each block problem is a convex
+ * quadratic, so no step increases L. Two passes over X per step.
+ *
+ *  trace      device, `steps` doubles (L after each step), or NULL
+ *  loss       host, L after the last step (NaN for steps = 0), or NULL
+ *  (other arguments as candelinc_lifted_grad; F and B are read and written)
+ * Errors: as candelinc_lifted_grad.
+ */
+int candelinc_pg_fit(const void* X, int d, const int64_t* dims, const int* m, int r,
+                     int precision, int steps, void* const* F, void* const* B, double* trace,
+                     double* loss, void* stream);
+
+/*
  * recon_residual - ||X - X_hat||_F and ||X||_F in one pass over X with FP64
  * accumulation (the relative error of Sec. 4.1 is their ratio).
  *

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "lifted.cuh"
 #include "nncp.cuh"
 #include "ntd.cuh"
 #include "residual.cuh"
@@ -97,6 +98,47 @@ int nncp_run(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel_er
   return NNC_OK;
 }
 
+// Shared checks of the two lifted-loss entries.
+int check_lifted(const void* X, int d, const int64_t* dims, const int* m, int r, const void* F,
+                 const void* B) {
+  if (X == nullptr || F == nullptr || B == nullptr) return NNC_ERR_INVALID_ARG;
+  if (d != 3 && d != 4) return NNC_ERR_INVALID_ARG;
+  if (r < 1 || r > 64) return NNC_ERR_INVALID_ARG;
+  return check_shape(d, dims, m, 64);
+}
+
+template <typename T>
+int lifted_grad_call(const void* X, int d, const int64_t* dims, const int* m, int r, bool tc,
+                     const void* const* F, const void* const* B, void* const* gF,
+                     void* const* gB, double* loss, cudaStream_t s) {
+  T *f[4], *b[4], *gf[4], *gb[4];
+  for (int n = 0; n < d; ++n) {
+    if (F[n] == nullptr || B[n] == nullptr) return NNC_ERR_INVALID_ARG;
+    f[n] = static_cast<T*>(const_cast<void*>(F[n]));
+    b[n] = static_cast<T*>(const_cast<void*>(B[n]));
+    if (gF) {
+      if (gF[n] == nullptr || gB[n] == nullptr) return NNC_ERR_INVALID_ARG;
+      gf[n] = static_cast<T*>(gF[n]);
+      gb[n] = static_cast<T*>(gB[n]);
+    }
+  }
+  return lifted_grad<T>(static_cast<const T*>(X), d, dims, m, r, tc, f, b, gF ? gf : nullptr,
+                        gF ? gb : nullptr, loss, s);
+}
+
+template <typename T>
+int pg_fit_call(const void* X, int d, const int64_t* dims, const int* m, int r, bool tc,
+                int steps, void* const* F, void* const* B, double* trace, double* loss,
+                cudaStream_t s) {
+  T *f[4], *b[4];
+  for (int n = 0; n < d; ++n) {
+    if (F[n] == nullptr || B[n] == nullptr) return NNC_ERR_INVALID_ARG;
+    f[n] = static_cast<T*>(F[n]);
+    b[n] = static_cast<T*>(B[n]);
+  }
+  return lifted_pg_fit<T>(static_cast<const T*>(X), d, dims, m, r, tc, steps, f, b, trace, loss,
+                          s);
+}
 }  // namespace
 }  // namespace nnc
 
@@ -269,6 +311,37 @@ int candelinc_lift(int d, const int64_t* dims, const int* m, int r, int precisio
     }
   }
   return NNC_OK;
+}
+
+int candelinc_lifted_grad(const void* X, int d, const int64_t* dims, const int* m, int r,
+                          int precision, const void* const* F, const void* const* B,
+                          void* const* gF, void* const* gB, double* loss, void* stream) {
+  g_detail.clear();
+  NNC_TRY(check_lifted(X, d, dims, m, r, F, B));
+  if ((gF == nullptr) != (gB == nullptr)) return NNC_ERR_INVALID_ARG;
+  if (gF == nullptr && loss == nullptr) return NNC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == NNC_FP64)
+    return lifted_grad_call<double>(X, d, dims, m, r, false, F, B, gF, gB, loss, s);
+  if (precision == NNC_FP32 || precision == NNC_FP32_SIMT)
+    return lifted_grad_call<float>(X, d, dims, m, r, precision == NNC_FP32, F, B, gF, gB, loss,
+                                   s);
+  return precision == NNC_BF16_REFINE ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
+}
+
+int candelinc_pg_fit(const void* X, int d, const int64_t* dims, const int* m, int r,
+                     int precision, int steps, void* const* F, void* const* B, double* trace,
+                     double* loss, void* stream) {
+  g_detail.clear();
+  NNC_TRY(check_lifted(X, d, dims, m, r, F, B));
+  if (steps < 0) return NNC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == NNC_FP64)
+    return pg_fit_call<double>(X, d, dims, m, r, false, steps, F, B, trace, loss, s);
+  if (precision == NNC_FP32 || precision == NNC_FP32_SIMT)
+    return pg_fit_call<float>(X, d, dims, m, r, precision == NNC_FP32, steps, F, B, trace, loss,
+                              s);
+  return precision == NNC_BF16_REFINE ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
 }
 
 int recon_residual(const void* X, int d, const int64_t* dims, int precision, int model,

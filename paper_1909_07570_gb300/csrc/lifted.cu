@@ -1,0 +1,550 @@
+// Differentiation form: the adjoint of the lifted loss and a block
+// projected-gradient fit of it.
+//
+// The objective of Eq. nnCANDELINC with the CPD of the core substituted,
+//   L = 1/2 ||X - I x_n A^(n)||^2,  A^(n) = F^(n) B^(n)  (d = 3 or 4),
+// has, with V_n = Hadamard_{k!=n} A^(k)T A^(k) and
+//   MT_n = unfold_n(X) KR_{k!=n}(A^(k)) = unfold_n(Z_n) KR_{k!=n}(B^(k)),
+//   Z_n  = X x_{k!=n} F^(k)T        (the Tucker-compressed tensor),
+// the gradients dL/dA^(n) = A^(n) V_n - MT_n, dL/dF^(n) = (dL/dA^(n)) B^(n)T
+// and dL/dB^(n) = F^(n)T dL/dA^(n). The KR identity holds because
+// KR_k(F^(k) B^(k)) = (kron_k F^(k)) KR_k(B^(k)).
+//
+// X is read twice per gradient: T_last = X x_d F^(d)T serves every Z_n with
+// n < d (further mode products on the compressed tensor), and
+// T_first = X x_1 F^(1)T serves Z_d. FP32 runs both passes on the TF32x3
+// tensor-core kernel with X viewed as 3-way (N_1, N_2 ... N_{d-1}, N_d); FP64
+// and FP32_SIMT run the SIMT mode products. The loss comes out of the same
+// terms in FP64: L = 1/2 ||X||^2 - <MT_n, A^(n)> + 1/2 sum(V_n .* A^(n)T A^(n)).
+//
+// The fit (block-coordinate projected gradient, the builder's reading since
+// the paper gives no first-order method): for n = 1..d, with MT_n and V_n,
+//   F^(n) <- max(F^(n) - (A V - MT) B^(n)T / L_F, 0),  L_F = lmax(B V B^T),
+//   B^(n) <- max(B^(n) - F^(n)T (A V - MT) / L_B, 0),  L_B = lmax(F^T F) lmax(V),
+// with lmax from 30 FP64 power iterations (all-ones start, Rayleigh quotient).
+// MT_n does not involve mode n, so one Z_n serves both blocks of mode n; the
+// Gauss-Seidel order still needs only two passes over X per step (T_last before
+// mode 1, T_first after mode d-1).
+#include <cmath>
+#include <type_traits>
+
+#include "kernels.cuh"
+#include "lifted.cuh"
+#include "residual.cuh"
+#include "sweep.cuh"
+#include "tc_ttm.cuh"
+
+namespace nnc {
+namespace {
+
+constexpr int kMaxD = 4;
+constexpr int kPowerIters = 30;
+
+inline unsigned grid_for(int64_t n, int threads) {
+  const int64_t b = (n + threads - 1) / threads;
+  return (unsigned)(b < 1 ? 1 : (b > 65535 ? 65535 : b));
+}
+
+// ---- small dense kernels ------------------------------------------------------
+
+// C[i, j] = sum_k A[i as_i + k as_k] B[k bs_k + j bs_j] - (D ? D[i, j] : 0)
+// for i < M, j < N (C and D row-major, ld N). One thread per output.
+template <typename T>
+__global__ void small_gemm_kernel(int M, int N, int K, const T* __restrict__ A, int64_t as_i,
+                                  int64_t as_k, const T* __restrict__ B, int64_t bs_k,
+                                  int64_t bs_j, const T* __restrict__ D, T* __restrict__ C) {
+  const int64_t n = (int64_t)M * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N, j = e % N;
+    T acc = T(0);
+    for (int k = 0; k < K; ++k) acc = fma(A[i * as_i + k * as_k], B[k * bs_k + j * bs_j], acc);
+    C[e] = D ? acc - D[e] : acc;
+  }
+}
+
+template <typename T>
+cudaError_t small_gemm(int M, int N, int K, const T* A, int64_t as_i, int64_t as_k, const T* B,
+                       int64_t bs_k, int64_t bs_j, const T* D, T* C, cudaStream_t s) {
+  small_gemm_kernel<T><<<grid_for((int64_t)M * N, 256), 256, 0, s>>>(M, N, K, A, as_i, as_k, B,
+                                                                      bs_k, bs_j, D, C);
+  note_launch(s);
+  return cudaGetLastError();
+}
+
+// out[t, q] = prod_k B_k[idx_k(t), q], t in C order over the listed modes (the
+// last one fastest); a single row of ones when no mode is listed.
+template <typename T>
+struct KrArgs {
+  const T* B[kMaxD];
+  int m[kMaxD];
+  int nk;
+  int r;
+  int64_t rows;
+  T* out;
+};
+
+template <typename T>
+__global__ void kr_kernel(KrArgs<T> a) {
+  const int64_t n = a.rows * a.r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e % a.r);
+    int64_t t = e / a.r;
+    T v = T(1);
+    for (int k = a.nk - 1; k >= 0; --k) {
+      const int ik = (int)(t % a.m[k]);
+      t /= a.m[k];
+      v *= a.B[k][(int64_t)ik * a.r + q];
+    }
+    a.out[e] = v;
+  }
+}
+
+// MT[i, q] = sum_p W[(p N + i) r + q] Kpre[p r + q], p in order.
+template <typename T>
+__global__ void weighted_sum_p_kernel(const T* __restrict__ W, const T* __restrict__ Kpre,
+                                      int64_t P, int64_t N, int r, T* __restrict__ MT) {
+  const int64_t n = N * r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e % r);
+    T acc = T(0);
+    for (int64_t p = 0; p < P; ++p) acc = fma(W[p * n + e], Kpre[p * r + q], acc);
+    MT[e] = acc;
+  }
+}
+
+// V = Hadamard product of the listed r x r matrices (all ones if none).
+template <typename T>
+struct HadArgs {
+  const T* M[kMaxD];
+  int nk;
+  int r;
+  T* out;
+};
+
+template <typename T>
+__global__ void hadamard_kernel(HadArgs<T> a) {
+  for (int e = threadIdx.x; e < a.r * a.r; e += blockDim.x) {
+    T v = T(1);
+    for (int k = 0; k < a.nk; ++k) v *= a.M[k][e];
+    a.out[e] = v;
+  }
+}
+
+// out[0] = lmax(H) (times *mul when given): kPowerIters FP64 power iterations
+// from the normalised all-ones vector, then the Rayleigh quotient. One block,
+// n <= 64.
+template <typename T>
+__global__ void power_iter_kernel(const T* __restrict__ H, int n, const double* mul,
+                                  double* out) {
+  __shared__ double h[64 * 64];
+  __shared__ double v[64], w[64];
+  __shared__ double nrm;
+  __shared__ int zero;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) h[e] = (double)H[e];
+  if (threadIdx.x < n) v[threadIdx.x] = 1.0 / sqrt((double)n);
+  if (threadIdx.x == 0) zero = 0;
+  __syncthreads();
+  for (int it = 0; it < kPowerIters; ++it) {
+    if (threadIdx.x < n) {
+      double acc = 0.0;
+      for (int j = 0; j < n; ++j) acc += h[threadIdx.x * n + j] * v[j];
+      w[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s += w[j] * w[j];
+      nrm = sqrt(s);
+      if (nrm == 0.0) zero = 1;
+    }
+    __syncthreads();
+    if (zero) break;
+    if (threadIdx.x < n) v[threadIdx.x] = w[threadIdx.x] / nrm;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double lam = 0.0;
+    if (!zero) {
+      for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc += h[i * n + j] * v[j];
+        lam += v[i] * acc;
+      }
+    }
+    out[0] = mul ? lam * mul[0] : lam;
+  }
+}
+
+// P <- max(P - G / L, 0) when L > 0.
+template <typename T>
+__global__ void pg_update_kernel(T* __restrict__ P, const T* __restrict__ G, int64_t n,
+                                 const double* __restrict__ L) {
+  const double l = L[0];
+  if (!(l > 0.0)) return;
+  const T inv = (T)(1.0 / l);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const T v = P[e] - G[e] * inv;
+    P[e] = v > T(0) ? v : T(0);
+  }
+}
+
+// *out = 1/2 x2 - <MT, A> + 1/2 sum(V .* AtA), FP64 sums in a fixed order (one block).
+template <typename T>
+__global__ void lifted_loss_kernel(const T* __restrict__ MT, const T* __restrict__ A, int64_t n,
+                                   const T* __restrict__ V, const T* __restrict__ AtA, int rr,
+                                   const double* __restrict__ x2, double* out) {
+  __shared__ double red[32];
+  double a = 0.0, b = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) a += (double)MT[e] * (double)A[e];
+  for (int e = threadIdx.x; e < rr; e += blockDim.x) b += (double)V[e] * (double)AtA[e];
+  a = block_sum(a, red);
+  b = block_sum(b, red);
+  if (threadIdx.x == 0) out[0] = 0.5 * x2[0] - a + 0.5 * b;
+}
+
+// ---- the workspace -------------------------------------------------------------
+
+template <typename T>
+struct Work {
+  int d = 0, r = 0;
+  int64_t N[kMaxD] = {};
+  int m[kMaxD] = {};
+  const T* X = nullptr;
+  bool tc = false;
+  tc::TcPlan plan;
+  T *Tlast = nullptr, *Tfirst = nullptr, *Z0 = nullptr, *Z1 = nullptr, *W = nullptr;
+  T *Kpre = nullptr, *Kpost = nullptr, *MT = nullptr, *gA = nullptr, *tmp = nullptr;
+  T *V = nullptr, *H = nullptr, *S = nullptr;
+  T* A[kMaxD] = {};
+  T* AtA[kMaxD] = {};
+  double *stats_part = nullptr, *stats = nullptr, *Ls = nullptr;
+};
+
+int64_t prod(const int64_t* v, int a, int b) {  // v[a] ... v[b-1]
+  int64_t p = 1;
+  for (int i = a; i < b; ++i) p *= v[i];
+  return p;
+}
+
+template <typename T>
+int setup(Work<T>& w, const T* X, int d, const int64_t* dims, const int* m, int r, bool want_tc,
+          Scratch& sc, cudaStream_t s) {
+  w.d = d;
+  w.r = r;
+  w.X = X;
+  int64_t nmax = 0;
+  int mmax = 0;
+  for (int k = 0; k < d; ++k) {
+    w.N[k] = dims[k];
+    w.m[k] = m[k];
+    nmax = dims[k] > nmax ? dims[k] : nmax;
+    mmax = m[k] > mmax ? m[k] : mmax;
+  }
+  const int64_t nX = prod(dims, 0, d);
+  const int64_t tl = nX / dims[d - 1] * m[d - 1];
+  const int64_t tf = nX / dims[0] * m[0];
+  // Largest intermediate of the Z chains: the first product of each chain.
+  int64_t zmax = 1;
+  for (int n = 0; n < d; ++n) {
+    int64_t cur[kMaxD];
+    for (int k = 0; k < d; ++k) cur[k] = dims[k];
+    if (n < d - 1) cur[d - 1] = m[d - 1];
+    else cur[0] = m[0];
+    for (int k = 0; k < d; ++k) {
+      if (k == n || (n < d - 1 && k == d - 1) || (n == d - 1 && k == 0)) continue;
+      cur[k] = m[k];
+      const int64_t sz = prod(cur, 0, d);
+      zmax = sz > zmax ? sz : zmax;
+    }
+  }
+  int64_t pmax = 1;  // largest product of other modes' ranks
+  for (int n = 0; n < d; ++n) {
+    int64_t p = 1;
+    for (int k = 0; k < d; ++k)
+      if (k != n) p *= m[k];
+    pmax = p > pmax ? p : pmax;
+  }
+  NNC_TRY(sc.get(&w.Tlast, (size_t)tl));
+  NNC_TRY(sc.get(&w.Tfirst, (size_t)tf));
+  NNC_TRY(sc.get(&w.Z0, (size_t)zmax));
+  NNC_TRY(sc.get(&w.Z1, (size_t)zmax));
+  NNC_TRY(sc.get(&w.W, (size_t)(pmax * nmax * r)));
+  NNC_TRY(sc.get(&w.Kpre, (size_t)(pmax * r)));
+  NNC_TRY(sc.get(&w.Kpost, (size_t)(pmax * r)));
+  NNC_TRY(sc.get(&w.MT, (size_t)(nmax * r)));
+  NNC_TRY(sc.get(&w.gA, (size_t)(nmax * r)));
+  NNC_TRY(sc.get(&w.tmp, (size_t)(nmax * (mmax > r ? mmax : r))));
+  NNC_TRY(sc.get(&w.V, (size_t)(r * r)));
+  NNC_TRY(sc.get(&w.H, (size_t)(mmax * mmax > r * r ? mmax * mmax : r * r)));
+  NNC_TRY(sc.get(&w.S, (size_t)(mmax * mmax)));
+  for (int k = 0; k < d; ++k) {
+    NNC_TRY(sc.get(&w.A[k], (size_t)(dims[k] * r)));
+    NNC_TRY(sc.get(&w.AtA[k], (size_t)(r * r)));
+  }
+  NNC_TRY(sc.get(&w.stats_part, 3 * kStatBlocks));
+  NNC_TRY(sc.get(&w.stats, 3));
+  NNC_TRY(sc.get(&w.Ls, 4));
+  NNC_CUDA_TRY(launch_tensor_stats<T>(X, nX, w.stats_part, w.stats, s));
+  double st[3];
+  NNC_CUDA_TRY(cudaMemcpyAsync(st, w.stats, sizeof(st), cudaMemcpyDeviceToHost, s));
+  NNC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (st[2] > 0.0) return NNC_ERR_NONFINITE;
+  w.tc = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (want_tc) {
+      const int st2 = w.plan.init(tc::kKindTf32x3, X, dims[0], prod(dims, 1, d - 1),
+                                  dims[d - 1], m[0], m[d - 1], sc, s);
+      if (st2 == NNC_OK) w.tc = true;
+      else if (st2 != NNC_ERR_UNSUPPORTED) return st2;
+    }
+  }
+  return NNC_OK;
+}
+
+// T_last = X x_d F^(d)T laid out (N_1, ..., N_{d-1}, m_d).
+template <typename T>
+int pass_last(Work<T>& w, const T* Fd, cudaStream_t s) {
+  const int d = w.d;
+  if constexpr (std::is_same<T, float>::value) {
+    if (w.tc) return w.plan.pass3(Fd, w.Tlast, s, /*convert=*/true);
+  }
+  NNC_CUDA_TRY(launch_ttm<T>(w.X, prod(w.N, 0, d - 1), (int)w.N[d - 1], 1, Fd, w.m[d - 1], 1,
+                             w.m[d - 1], w.Tlast, nullptr, 0, s));
+  return NNC_OK;
+}
+
+// T_first = X x_1 F^(1)T laid out (m_1, N_2, ..., N_d).
+template <typename T>
+int pass_first(Work<T>& w, const T* F1, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (w.tc) return w.plan.pass1(F1, w.Tfirst, s, /*convert=*/true);
+  }
+  NNC_CUDA_TRY(launch_ttm<T>(w.X, 1, (int)w.N[0], prod(w.N, 1, w.d), F1, w.m[0], 1, w.m[0],
+                             w.Tfirst, nullptr, 0, s));
+  return NNC_OK;
+}
+
+// Z_n from T_last (n < d) or T_first (n = d) by mode products with the current
+// factors; returns the buffer holding Z_n, laid out (m_1 .. N_n .. m_d).
+template <typename T>
+int z_chain(Work<T>& w, int n, T* const* F, const T** zout, cudaStream_t s) {
+  const int d = w.d;
+  int64_t cur[kMaxD];
+  for (int k = 0; k < d; ++k) cur[k] = w.N[k];
+  const T* src;
+  if (n < d - 1) {
+    cur[d - 1] = w.m[d - 1];
+    src = w.Tlast;
+  } else {
+    cur[0] = w.m[0];
+    src = w.Tfirst;
+  }
+  T* bufs[2] = {w.Z0, w.Z1};
+  int b = 0;
+  for (int k = 0; k < d; ++k) {
+    if (k == n || (n < d - 1 && k == d - 1) || (n == d - 1 && k == 0)) continue;
+    NNC_CUDA_TRY(launch_ttm<T>(src, prod(cur, 0, k), (int)cur[k], prod(cur, k + 1, d), F[k],
+                               w.m[k], 1, w.m[k], bufs[b], nullptr, 0, s));
+    cur[k] = w.m[k];
+    src = bufs[b];
+    b ^= 1;
+  }
+  *zout = src;
+  return NNC_OK;
+}
+
+// MT_n = unfold_n(Z_n) KR_{k!=n}(B^(k)) into w.MT; V_n into w.V.
+template <typename T>
+int mttkrp_and_v(Work<T>& w, int n, const T* Z, T* const* B, cudaStream_t s) {
+  const int d = w.d, r = w.r;
+  KrArgs<T> pre{}, post{};
+  pre.r = post.r = r;
+  pre.out = w.Kpre;
+  post.out = w.Kpost;
+  pre.rows = post.rows = 1;
+  for (int k = 0; k < d; ++k) {
+    if (k < n) {
+      pre.B[pre.nk] = B[k];
+      pre.m[pre.nk++] = w.m[k];
+      pre.rows *= w.m[k];
+    } else if (k > n) {
+      post.B[post.nk] = B[k];
+      post.m[post.nk++] = w.m[k];
+      post.rows *= w.m[k];
+    }
+  }
+  kr_kernel<T><<<grid_for(pre.rows * r, 256), 256, 0, s>>>(pre);
+  note_launch(s);
+  kr_kernel<T><<<grid_for(post.rows * r, 256), 256, 0, s>>>(post);
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  // W[p, i, q] = sum_s Z[p, i, s] Kpost[s, q];  MT[i, q] = sum_p W[p, i, q] Kpre[p, q]
+  NNC_CUDA_TRY(launch_ttm<T>(Z, pre.rows * w.N[n], (int)post.rows, 1, w.Kpost, r, 1, r, w.W,
+                             nullptr, 0, s));
+  weighted_sum_p_kernel<T><<<grid_for(w.N[n] * r, 256), 256, 0, s>>>(w.W, w.Kpre, pre.rows,
+                                                                       w.N[n], r, w.MT);
+  note_launch(s);
+  HadArgs<T> h{};
+  h.r = r;
+  h.out = w.V;
+  for (int k = 0; k < d; ++k)
+    if (k != n) h.M[h.nk++] = w.AtA[k];
+  hadamard_kernel<T><<<1, 256, 0, s>>>(h);
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  return NNC_OK;
+}
+
+// A^(k) = F^(k) B^(k) and A^(k)T A^(k).
+template <typename T>
+int refresh_a(Work<T>& w, int k, const T* Fk, const T* Bk, cudaStream_t s) {
+  NNC_CUDA_TRY(launch_lift<T>(Fk, Bk, w.N[k], w.m[k], w.r, w.A[k], s));
+  NNC_TRY(launch_gram<T>(w.A[k], w.N[k], w.r, w.AtA[k], s));
+  return NNC_OK;
+}
+
+// gA = A^(n) V - MT (N_n x r) into w.gA.
+template <typename T>
+int grad_a(Work<T>& w, int n, cudaStream_t s) {
+  const int r = w.r;
+  NNC_CUDA_TRY(small_gemm<T>((int)w.N[n], r, r, w.A[n], r, 1, w.V, r, 1, w.MT, w.gA, s));
+  return NNC_OK;
+}
+
+// One block pair (F^(n), then B^(n)) of the projected-gradient step.
+template <typename T>
+int pg_mode(Work<T>& w, int n, T* const* F, T* const* B, cudaStream_t s) {
+  const int r = w.r, mn = w.m[n];
+  const int64_t Nn = w.N[n];
+  // L_F = lmax(B V B^T): tmp = B V (m x r), H = tmp B^T (m x m)
+  NNC_CUDA_TRY(small_gemm<T>(mn, r, r, B[n], r, 1, w.V, r, 1, nullptr, w.tmp, s));
+  NNC_CUDA_TRY(small_gemm<T>(mn, mn, r, w.tmp, r, 1, B[n], 1, r, nullptr, w.H, s));
+  power_iter_kernel<T><<<1, 64, 0, s>>>(w.H, mn, nullptr, w.Ls + 0);
+  note_launch(s);
+  NNC_TRY(grad_a(w, n, s));
+  // gF = gA B^T (N x m) into tmp
+  NNC_CUDA_TRY(small_gemm<T>((int)Nn, mn, r, w.gA, r, 1, B[n], 1, r, nullptr, w.tmp, s));
+  pg_update_kernel<T><<<grid_for(Nn * mn, 256), 256, 0, s>>>(F[n], w.tmp, Nn * mn, w.Ls + 0);
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  NNC_CUDA_TRY(launch_lift<T>(F[n], B[n], Nn, mn, r, w.A[n], s));
+  // L_B = lmax(F^T F) lmax(V)
+  NNC_TRY(launch_gram<T>(F[n], Nn, mn, w.S, s));
+  power_iter_kernel<T><<<1, 64, 0, s>>>(w.V, r, nullptr, w.Ls + 1);
+  note_launch(s);
+  power_iter_kernel<T><<<1, 64, 0, s>>>(w.S, mn, w.Ls + 1, w.Ls + 2);
+  note_launch(s);
+  NNC_TRY(grad_a(w, n, s));
+  // gB = F^T gA (m x r) into tmp
+  NNC_CUDA_TRY(small_gemm<T>(mn, r, (int)Nn, F[n], 1, mn, w.gA, r, 1, nullptr, w.tmp, s));
+  pg_update_kernel<T><<<grid_for((int64_t)mn * r, 256), 256, 0, s>>>(B[n], w.tmp,
+                                                                      (int64_t)mn * r, w.Ls + 2);
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  NNC_TRY(refresh_a(w, n, F[n], B[n], s));
+  return NNC_OK;
+}
+
+template <typename T>
+int loss_into(Work<T>& w, int n, double* out, cudaStream_t s) {
+  lifted_loss_kernel<T><<<1, 256, 0, s>>>(w.MT, w.A[n], w.N[n] * w.r, w.V, w.AtA[n], w.r * w.r,
+                                          w.stats, out);
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  return NNC_OK;
+}
+
+template <typename T>
+int check_tc(Work<T>& w, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (w.tc) return w.plan.check(s);
+  }
+  NNC_CUDA_TRY(cudaStreamSynchronize(s));
+  return NNC_OK;
+}
+
+}  // namespace
+
+template <typename T>
+int lifted_grad(const T* X, int d, const int64_t* dims, const int* m, int r, bool tensor_cores,
+                T* const* F, T* const* B, T* const* gF, T* const* gB, double* loss,
+                cudaStream_t s) {
+  Scratch sc(s);
+  Work<T> w;
+  NNC_TRY(setup(w, X, d, dims, m, r, tensor_cores, sc, s));
+  for (int k = 0; k < d; ++k) NNC_TRY(refresh_a(w, k, F[k], B[k], s));
+  const bool grads = gF != nullptr;
+  double* dloss = w.Ls + 3;
+  NNC_TRY(pass_last(w, F[d - 1], s));
+  if (grads) NNC_TRY(pass_first(w, F[0], s));
+  for (int n = 0; n < (grads ? d : 1); ++n) {
+    const T* Z = nullptr;
+    NNC_TRY(z_chain(w, n, F, &Z, s));
+    NNC_TRY(mttkrp_and_v(w, n, Z, B, s));
+    if (n == 0) NNC_TRY(loss_into(w, 0, dloss, s));
+    if (!grads) break;
+    NNC_TRY(grad_a(w, n, s));
+    const int mn = m[n];
+    NNC_CUDA_TRY(small_gemm<T>((int)dims[n], mn, r, w.gA, r, 1, B[n], 1, r, nullptr, gF[n], s));
+    NNC_CUDA_TRY(small_gemm<T>(mn, r, (int)dims[n], F[n], 1, mn, w.gA, r, 1, nullptr, gB[n], s));
+  }
+  NNC_TRY(check_tc(w, s));
+  if (loss) {
+    NNC_CUDA_TRY(cudaMemcpyAsync(loss, dloss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NNC_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return NNC_OK;
+}
+
+template <typename T>
+int lifted_pg_fit(const T* X, int d, const int64_t* dims, const int* m, int r, bool tensor_cores,
+                  int steps, T* const* F, T* const* B, double* trace, double* loss,
+                  cudaStream_t s) {
+  Scratch sc(s);
+  Work<T> w;
+  NNC_TRY(setup(w, X, d, dims, m, r, tensor_cores, sc, s));
+  for (int k = 0; k < d; ++k) NNC_TRY(refresh_a(w, k, F[k], B[k], s));
+  double* last = w.Ls + 3;
+  for (int t = 0; t < steps; ++t) {
+    NNC_TRY(pass_last(w, F[d - 1], s));
+    for (int n = 0; n < d; ++n) {
+      if (n == d - 1) NNC_TRY(pass_first(w, F[0], s));
+      const T* Z = nullptr;
+      NNC_TRY(z_chain(w, n, F, &Z, s));
+      NNC_TRY(mttkrp_and_v(w, n, Z, B, s));
+      NNC_TRY(pg_mode(w, n, F, B, s));
+    }
+    // MT_d and V_d do not involve mode d: the loss at the new point.
+    NNC_TRY(loss_into(w, d - 1, trace ? trace + t : last, s));
+    if (trace && t == steps - 1)
+      NNC_CUDA_TRY(cudaMemcpyAsync(last, trace + t, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  NNC_TRY(check_tc(w, s));
+  if (loss) {
+    if (steps == 0) {
+      *loss = NAN;
+    } else {
+      NNC_CUDA_TRY(cudaMemcpyAsync(loss, last, sizeof(double), cudaMemcpyDeviceToHost, s));
+      NNC_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+  }
+  return NNC_OK;
+}
+
+template int lifted_grad<float>(const float*, int, const int64_t*, const int*, int, bool,
+                                float* const*, float* const*, float* const*, float* const*,
+                                double*, cudaStream_t);
+template int lifted_grad<double>(const double*, int, const int64_t*, const int*, int, bool,
+                                 double* const*, double* const*, double* const*, double* const*,
+                                 double*, cudaStream_t);
+template int lifted_pg_fit<float>(const float*, int, const int64_t*, const int*, int, bool, int,
+                                  float* const*, float* const*, double*, double*, cudaStream_t);
+template int lifted_pg_fit<double>(const double*, int, const int64_t*, const int*, int, bool,
+                                   int, double* const*, double* const*, double*, double*,
+                                   cudaStream_t);
+
+}  // namespace nnc

@@ -1,0 +1,24 @@
+// Differentiation form of the lifted loss (lifted.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace nnc {
+
+// Gradients of L = 1/2 ||X - I x_n F^(n) B^(n)||^2 wrt every F^(n) (into gF)
+// and B^(n) (into gB), and L in FP64 (host, optional). gF == nullptr: the loss
+// only (one pass over X). d = 3 or 4, m_n <= 64, r <= 64.
+template <typename T>
+int lifted_grad(const T* X, int d, const int64_t* dims, const int* m, int r, bool tensor_cores,
+                T* const* F, T* const* B, T* const* gF, T* const* gB, double* loss,
+                cudaStream_t s);
+
+// `steps` block projected-gradient steps on F and B in place; trace (device,
+// `steps` doubles, optional) gets L after each step, loss (host, optional) the
+// last one.
+template <typename T>
+int lifted_pg_fit(const T* X, int d, const int64_t* dims, const int* m, int r, bool tensor_cores,
+                  int steps, T* const* F, T* const* B, double* trace, double* loss,
+                  cudaStream_t s);
+
+}  // namespace nnc

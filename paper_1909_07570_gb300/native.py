@@ -24,7 +24,8 @@ _STATUS = {
 # Every symbol include/nncandelinc.h declares.
 EXPORTED = ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched",
             "nncp_core_fit_batched_noalloc", "nnc_mode_product", "candelinc_lift",
-            "recon_residual", "nnc_status_string", "nnc_last_error_detail",
+            "recon_residual", "candelinc_lifted_grad", "candelinc_pg_fit",
+            "nnc_status_string", "nnc_last_error_detail",
             "nnc_profile_enable", "nnc_profile_read", "nnc_kernel_launches")
 
 
@@ -72,8 +73,13 @@ def load(path: str | None = None):
     lib.nncp_core_fit_batched_noalloc.argtypes = lib.nncp_core_fit_batched.argtypes
     lib.nnc_mode_product.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_int, vp, ctypes.c_int,
                                      ctypes.c_int, vp, vp]
+    lib.candelinc_lifted_grad.argtypes = [vp, ctypes.c_int, i64p, ip, ctypes.c_int, ctypes.c_int,
+                                          vpp, vpp, vpp, vpp, dp, vp]
+    lib.candelinc_pg_fit.argtypes = [vp, ctypes.c_int, i64p, ip, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, vpp, vpp, vp, dp, vp]
     for fn in ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched",
-               "nncp_core_fit_batched_noalloc", "nnc_mode_product", "candelinc_lift", "recon_residual"):
+               "nncp_core_fit_batched_noalloc", "nnc_mode_product", "candelinc_lift", "recon_residual",
+               "candelinc_lifted_grad", "candelinc_pg_fit"):
         getattr(lib, fn).restype = ctypes.c_int
     lib.nnc_status_string.argtypes = [ctypes.c_int]
     lib.nnc_status_string.restype = ctypes.c_char_p
@@ -238,6 +244,50 @@ def candelinc_lift(F, B, out=None, stream=None):
                                r, code, _ptrs(F), _ptrs(B), _ptrs(A), _stream(stream))
     _check("candelinc_lift", st)
     return A
+
+
+def candelinc_lifted_grad(X, F, B, precision=None, grads=True, stream=None):
+    """Loss and gradients of L = 1/2 ||X - I x_n F^(n) B^(n)||^2.
+
+    Returns (loss, gF, gB) with gF[n], gB[n] shaped like F[n], B[n]; with
+    grads=False only the loss is computed (gF = gB = None). precision: "fp64",
+    "fp32" (TF32x3 tensor-core passes) or "fp32_simt"."""
+    code, dtype = _precision(X, precision)
+    _require(X, dtype, "X")
+    d = X.dim()
+    for n in range(d):
+        _require(F[n], dtype, f"F[{n}]")
+        _require(B[n], dtype, f"B[{n}]")
+    r = B[0].shape[1]
+    gF = [torch.empty_like(f) for f in F] if grads else None
+    gB = [torch.empty_like(b) for b in B] if grads else None
+    loss = ctypes.c_double()
+    st = load().candelinc_lifted_grad(
+        _ptr(X), d, _i64(X.shape), _i32([f.shape[1] for f in F]), r, code, _ptrs(F), _ptrs(B),
+        _ptrs(gF) if grads else None, _ptrs(gB) if grads else None, ctypes.byref(loss),
+        _stream(stream))
+    _check("candelinc_lifted_grad", st)
+    return loss.value, gF, gB
+
+
+def candelinc_pg_fit(X, F, B, steps, precision=None, trace=True, stream=None):
+    """Block projected-gradient steps on the lifted loss, in place on F and B.
+    Returns (final loss, trace) with trace a device FP64 tensor of the loss after
+    each step (None if trace=False)."""
+    code, dtype = _precision(X, precision)
+    _require(X, dtype, "X")
+    d = X.dim()
+    for n in range(d):
+        _require(F[n], dtype, f"F[{n}]")
+        _require(B[n], dtype, f"B[{n}]")
+    r = B[0].shape[1]
+    tr = torch.empty(max(steps, 1), dtype=torch.float64, device=X.device) if trace else None
+    loss = ctypes.c_double()
+    st = load().candelinc_pg_fit(_ptr(X), d, _i64(X.shape), _i32([f.shape[1] for f in F]), r,
+                                 code, int(steps), _ptrs(F), _ptrs(B),
+                                 _ptr(tr) if trace else None, ctypes.byref(loss), _stream(stream))
+    _check("candelinc_pg_fit", st)
+    return loss.value, (tr[:steps] if trace else None)
 
 
 def recon_residual(X, factors, G=None, stream=None):
