@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-precision-form", action="store_true")
+    p.add_argument("--no-differentiation-form", action="store_true")
     return p.parse_args()
 
 
@@ -416,6 +417,43 @@ def precision_form(dev):
     return out
 
 
+def differentiation_form(dev):
+    """Block projected-gradient steps on the lifted loss (the hand-written
+    adjoint, two TF32x3 passes over X per step) on the 4-way 128^3 x 64
+    workload: steps/s of device time (marginal over the setup) and the fit."""
+    import numpy as np
+    import torch
+
+    from paper_1909_07570_gb300 import inputs, native
+    w = inputs.WORKLOADS["cp12_128x128x128x64_m24_fp32"]
+    X64, _, F0, _, B0 = inputs.make_problem(w)
+    X = torch.tensor(X64, dtype=torch.float32, device=dev)
+    xn = float(np.sqrt(np.sum(X64 * X64)))
+    del X64
+    stream = torch.cuda.current_stream()
+
+    def run(steps):
+        F = [torch.tensor(f, dtype=torch.float32, device=dev) for f in F0]
+        B = [torch.tensor(b, dtype=torch.float32, device=dev) for b in B0]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        loss, _ = native.candelinc_pg_fit(X, F, B, steps, precision="fp32")
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), loss
+
+    run(2)
+    short = min(run(10)[0] for _ in range(2))
+    full, loss = min(run(w.iters) for _ in range(2))
+    per_step = (full - short) / (w.iters - 10)
+    return {"workload": w.name, "dims": list(w.dims), "m": list(w.m), "r": w.r,
+            "steps": w.iters, "ms": round(full, 2),
+            "steps_per_s": round(1e3 / per_step, 2),
+            "x_bytes_per_step": 2 * int(np.prod(w.dims)) * 4,
+            "final_lifted_rel_err": float(np.sqrt(2 * max(loss, 0.0)) / xn)}
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -473,6 +511,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_precision_form:
         import torch
         result["precision_form"] = precision_form(torch.device("cuda", 0))
+    if rank == 0 and world == 1 and not args.no_differentiation_form:
+        import torch
+        result["differentiation_form"] = differentiation_form(torch.device("cuda", 0))
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             X64, F0, G0, _ = problem

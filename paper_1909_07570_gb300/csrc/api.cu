@@ -41,6 +41,27 @@ void note_graph_launches(long long kernels) {
   g_kernel_launches.fetch_add(kernels, std::memory_order_relaxed);
 }
 
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<int, const void*>, size_t>> set;
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& kv : set) {
+    if (kv.first.first == dev && kv.first.second == kernel) {
+      if (kv.second >= bytes) return cudaSuccess;
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e == cudaSuccess) kv.second = bytes;
+      return e;
+    }
+  }
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) set.push_back({{dev, kernel}, bytes});
+  return e;
+}
+
 int device_sm_count() {
   static int cache[64] = {0};
   int dev = 0;

@@ -75,6 +75,12 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int device_sm_count();
 
+// Raises `kernel`'s dynamic shared-memory limit on the current device to at
+// least `bytes` and never lowers it: a launch captured into a graph keeps the
+// size it was captured with while later launches of the same kernel may ask
+// for less.
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes);
+
 // Counts one kernel launch of this library (nnc_kernel_launches). Launches
 // made while `s` is being captured into a graph are counted when the graph is
 // replayed instead (note_graph_launches).

@@ -27,6 +27,7 @@
 // mode 1, T_first after mode d-1).
 #include <cmath>
 #include <type_traits>
+#include <vector>
 
 #include "kernels.cuh"
 #include "lifted.cuh"
@@ -115,6 +116,18 @@ __global__ void weighted_sum_p_kernel(const T* __restrict__ W, const T* __restri
   }
 }
 
+// out (C x R) = in^T, in R x C row-major.
+template <typename T>
+__global__ void transpose_small_kernel(const T* __restrict__ in, int R, int64_t C,
+                                       T* __restrict__ out) {
+  const int64_t n = (int64_t)R * C;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / R, rr = e % R;
+    out[e] = in[rr * C + c];
+  }
+}
+
 // V = Hadamard product of the listed r x r matrices (all ones if none).
 template <typename T>
 struct HadArgs {
@@ -133,56 +146,65 @@ __global__ void hadamard_kernel(HadArgs<T> a) {
   }
 }
 
-// out[0] = lmax(H) (times *mul when given): kPowerIters FP64 power iterations
-// from the normalised all-ones vector, then the Rayleigh quotient. One block,
-// n <= 64.
+// out_b = lmax(H_b) for the matrix b = blockIdx.x of the launch (H_0: n0 x n0,
+// H_1: n1 x n1, n <= 64): kPowerIters FP64 power iterations from the
+// normalised all-ones vector, then the Rayleigh quotient; 0 if an iterate maps
+// to zero. Rows go to warps, columns to lanes (shuffle sums in a fixed order):
+// FP64 is slow on this GPU, so no long serial chains.
 template <typename T>
-__global__ void power_iter_kernel(const T* __restrict__ H, int n, const double* mul,
-                                  double* out) {
+__global__ void power_iter_kernel(const T* __restrict__ H0, int n0, double* out0,
+                                  const T* __restrict__ H1, int n1, double* out1) {
   __shared__ double h[64 * 64];
   __shared__ double v[64], w[64];
   __shared__ double nrm;
-  __shared__ int zero;
+  const T* H = blockIdx.x == 0 ? H0 : H1;
+  const int n = blockIdx.x == 0 ? n0 : n1;
+  double* out = blockIdx.x == 0 ? out0 : out1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) h[e] = (double)H[e];
   if (threadIdx.x < n) v[threadIdx.x] = 1.0 / sqrt((double)n);
-  if (threadIdx.x == 0) zero = 0;
   __syncthreads();
-  for (int it = 0; it < kPowerIters; ++it) {
-    if (threadIdx.x < n) {
-      double acc = 0.0;
-      for (int j = 0; j < n; ++j) acc += h[threadIdx.x * n + j] * v[j];
-      w[threadIdx.x] = acc;
+  auto matvec = [&]() {  // w = h v
+    for (int i = warp; i < n; i += nw) {
+      double a = 0.0;
+      for (int j = lane; j < n; j += 32) a = fma(h[i * n + j], v[j], a);
+      a = warp_sum(a);
+      if (lane == 0) w[i] = a;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int j = 0; j < n; ++j) s += w[j] * w[j];
-      nrm = sqrt(s);
-      if (nrm == 0.0) zero = 1;
+  };
+  bool zero = false;
+  for (int it = 0; it < kPowerIters && !zero; ++it) {
+    matvec();
+    if (warp == 0) {
+      double a = 0.0;
+      for (int j = lane; j < n; j += 32) a = fma(w[j], w[j], a);
+      a = warp_sum(a);
+      if (lane == 0) nrm = sqrt(a);
     }
     __syncthreads();
-    if (zero) break;
-    if (threadIdx.x < n) v[threadIdx.x] = w[threadIdx.x] / nrm;
+    zero = !(nrm > 0.0);
+    if (!zero && threadIdx.x < n) v[threadIdx.x] = w[threadIdx.x] / nrm;
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    double lam = 0.0;
-    if (!zero) {
-      for (int i = 0; i < n; ++i) {
-        double acc = 0.0;
-        for (int j = 0; j < n; ++j) acc += h[i * n + j] * v[j];
-        lam += v[i] * acc;
-      }
-    }
-    out[0] = mul ? lam * mul[0] : lam;
+  if (zero) {
+    if (threadIdx.x == 0) out[0] = 0.0;
+    return;
+  }
+  matvec();
+  if (warp == 0) {
+    double a = 0.0;
+    for (int j = lane; j < n; j += 32) a = fma(v[j], w[j], a);
+    a = warp_sum(a);
+    if (lane == 0) out[0] = a;
   }
 }
 
-// P <- max(P - G / L, 0) when L > 0.
+// P <- max(P - G / L, 0) when L > 0, with L = L1[0] (times L2[0] if given).
 template <typename T>
 __global__ void pg_update_kernel(T* __restrict__ P, const T* __restrict__ G, int64_t n,
-                                 const double* __restrict__ L) {
-  const double l = L[0];
+                                 const double* __restrict__ L1, const double* __restrict__ L2) {
+  const double l = L2 ? L1[0] * L2[0] : L1[0];
   if (!(l > 0.0)) return;
   const T inv = (T)(1.0 / l);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -192,18 +214,28 @@ __global__ void pg_update_kernel(T* __restrict__ P, const T* __restrict__ G, int
   }
 }
 
-// *out = 1/2 x2 - <MT, A> + 1/2 sum(V .* AtA), FP64 sums in a fixed order (one block).
+// *out = 1/2 x2 - <MT, A> + 1/2 sum(V .* AtA), FP64 sums in a fixed order (one
+// block); also trace[*counter] (then *counter + 1) when a trace is given.
 template <typename T>
 __global__ void lifted_loss_kernel(const T* __restrict__ MT, const T* __restrict__ A, int64_t n,
                                    const T* __restrict__ V, const T* __restrict__ AtA, int rr,
-                                   const double* __restrict__ x2, double* out) {
+                                   const double* __restrict__ x2, double* out, double* trace,
+                                   int* counter) {
   __shared__ double red[32];
   double a = 0.0, b = 0.0;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) a += (double)MT[e] * (double)A[e];
   for (int e = threadIdx.x; e < rr; e += blockDim.x) b += (double)V[e] * (double)AtA[e];
   a = block_sum(a, red);
   b = block_sum(b, red);
-  if (threadIdx.x == 0) out[0] = 0.5 * x2[0] - a + 0.5 * b;
+  if (threadIdx.x == 0) {
+    const double v = 0.5 * x2[0] - a + 0.5 * b;
+    out[0] = v;
+    if (trace) {
+      const int t = *counter;
+      trace[t] = v;
+      *counter = t + 1;
+    }
+  }
 }
 
 // ---- the workspace -------------------------------------------------------------
@@ -216,9 +248,12 @@ struct Work {
   const T* X = nullptr;
   bool tc = false;
   tc::TcPlan plan;
-  T *Tlast = nullptr, *Tfirst = nullptr, *Z0 = nullptr, *Z1 = nullptr, *W = nullptr;
+  T *Tlast = nullptr, *Tfirst = nullptr, *U0 = nullptr, *Z0 = nullptr, *Z1 = nullptr;
+  T* W = nullptr;
   T *Kpre = nullptr, *Kpost = nullptr, *MT = nullptr, *gA = nullptr, *tmp = nullptr;
   T *V = nullptr, *H = nullptr, *S = nullptr;
+  T* split = nullptr;  // partial sums of mode products whose grid would not fill the GPU
+  size_t split_cap = 0;
   T* A[kMaxD] = {};
   T* AtA[kMaxD] = {};
   double *stats_part = nullptr, *stats = nullptr, *Ls = nullptr;
@@ -270,6 +305,7 @@ int setup(Work<T>& w, const T* X, int d, const int64_t* dims, const int* m, int 
   }
   NNC_TRY(sc.get(&w.Tlast, (size_t)tl));
   NNC_TRY(sc.get(&w.Tfirst, (size_t)tf));
+  NNC_TRY(sc.get(&w.U0, (size_t)(tl / dims[0] * m[0])));
   NNC_TRY(sc.get(&w.Z0, (size_t)zmax));
   NNC_TRY(sc.get(&w.Z1, (size_t)zmax));
   NNC_TRY(sc.get(&w.W, (size_t)(pmax * nmax * r)));
@@ -281,6 +317,8 @@ int setup(Work<T>& w, const T* X, int d, const int64_t* dims, const int* m, int 
   NNC_TRY(sc.get(&w.V, (size_t)(r * r)));
   NNC_TRY(sc.get(&w.H, (size_t)(mmax * mmax > r * r ? mmax * mmax : r * r)));
   NNC_TRY(sc.get(&w.S, (size_t)(mmax * mmax)));
+  w.split_cap = (size_t)1 << 22;
+  NNC_TRY(sc.get(&w.split, w.split_cap));
   for (int k = 0; k < d; ++k) {
     NNC_TRY(sc.get(&w.A[k], (size_t)(dims[k] * r)));
     NNC_TRY(sc.get(&w.AtA[k], (size_t)(r * r)));
@@ -328,27 +366,47 @@ int pass_first(Work<T>& w, const T* F1, cudaStream_t s) {
   return NNC_OK;
 }
 
-// Z_n from T_last (n < d) or T_first (n = d) by mode products with the current
-// factors; returns the buffer holding Z_n, laid out (m_1 .. N_n .. m_d).
+// U0 = T_last x_1 F^(1)T, laid out (m_1, N_2, ..., N_{d-1}, m_d): shared by every
+// Z_n with 1 < n < d (its F^(1) is final for the step once mode 1 is done).
+template <typename T>
+int make_u0(Work<T>& w, const T* F1, cudaStream_t s) {
+  const int d = w.d;
+  NNC_CUDA_TRY(launch_ttm<T>(w.Tlast, 1, (int)w.N[0], prod(w.N, 1, d - 1) * w.m[d - 1], F1,
+                             w.m[0], 1, w.m[0], w.U0, w.split, w.split_cap, s));
+  return NNC_OK;
+}
+
+// Z_n by mode products with the current factors, laid out (m_1 .. N_n .. m_d):
+// from T_last (n = 1), U0 (1 < n < d) or T_first (n = d).
 template <typename T>
 int z_chain(Work<T>& w, int n, T* const* F, const T** zout, cudaStream_t s) {
   const int d = w.d;
   int64_t cur[kMaxD];
   for (int k = 0; k < d; ++k) cur[k] = w.N[k];
   const T* src;
-  if (n < d - 1) {
-    cur[d - 1] = w.m[d - 1];
-    src = w.Tlast;
-  } else {
+  int first = 0;  // modes [first, last) other than n are contracted here
+  int last = d;
+  if (n == d - 1) {
     cur[0] = w.m[0];
     src = w.Tfirst;
+    first = 1;
+  } else if (n == 0) {
+    cur[d - 1] = w.m[d - 1];
+    src = w.Tlast;
+    last = d - 1;
+  } else {
+    cur[0] = w.m[0];
+    cur[d - 1] = w.m[d - 1];
+    src = w.U0;
+    first = 1;
+    last = d - 1;
   }
   T* bufs[2] = {w.Z0, w.Z1};
   int b = 0;
-  for (int k = 0; k < d; ++k) {
-    if (k == n || (n < d - 1 && k == d - 1) || (n == d - 1 && k == 0)) continue;
+  for (int k = first; k < last; ++k) {
+    if (k == n) continue;
     NNC_CUDA_TRY(launch_ttm<T>(src, prod(cur, 0, k), (int)cur[k], prod(cur, k + 1, d), F[k],
-                               w.m[k], 1, w.m[k], bufs[b], nullptr, 0, s));
+                               w.m[k], 1, w.m[k], bufs[b], w.split, w.split_cap, s));
     cur[k] = w.m[k];
     src = bufs[b];
     b ^= 1;
@@ -382,12 +440,24 @@ int mttkrp_and_v(Work<T>& w, int n, const T* Z, T* const* B, cudaStream_t s) {
   kr_kernel<T><<<grid_for(post.rows * r, 256), 256, 0, s>>>(post);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
-  // W[p, i, q] = sum_s Z[p, i, s] Kpost[s, q];  MT[i, q] = sum_p W[p, i, q] Kpre[p, q]
-  NNC_CUDA_TRY(launch_ttm<T>(Z, pre.rows * w.N[n], (int)post.rows, 1, w.Kpost, r, 1, r, w.W,
-                             nullptr, 0, s));
-  weighted_sum_p_kernel<T><<<grid_for(w.N[n] * r, 256), 256, 0, s>>>(w.W, w.Kpre, pre.rows,
-                                                                       w.N[n], r, w.MT);
-  note_launch(s);
+  if (post.rows == 1) {
+    // Last mode: MT^T (r x N) = Kpre^T unfold(Z), one mode product over p;
+    // then MT = (MT^T)^T.
+    NNC_CUDA_TRY(launch_ttm<T>(Z, 1, (int)pre.rows, w.N[n], w.Kpre, r, 1, r, w.W, w.split,
+                               w.split_cap, s));
+    transpose_small_kernel<T><<<grid_for(w.N[n] * r, 256), 256, 0, s>>>(w.W, r, w.N[n], w.MT);
+    note_launch(s);
+  } else {
+    // W[p, i, q] = sum_s Z[p, i, s] Kpost[s, q];  MT[i, q] = sum_p W[p, i, q] Kpre[p, q]
+    T* Wout = pre.rows == 1 ? w.MT : w.W;
+    NNC_CUDA_TRY(launch_ttm<T>(Z, pre.rows * w.N[n], (int)post.rows, 1, w.Kpost, r, 1, r, Wout,
+                               w.split, w.split_cap, s));
+    if (pre.rows > 1) {
+      weighted_sum_p_kernel<T><<<grid_for(w.N[n] * r, 256), 256, 0, s>>>(w.W, w.Kpre, pre.rows,
+                                                                           w.N[n], r, w.MT);
+      note_launch(s);
+    }
+  }
   HadArgs<T> h{};
   h.r = r;
   h.out = w.V;
@@ -420,29 +490,28 @@ template <typename T>
 int pg_mode(Work<T>& w, int n, T* const* F, T* const* B, cudaStream_t s) {
   const int r = w.r, mn = w.m[n];
   const int64_t Nn = w.N[n];
-  // L_F = lmax(B V B^T): tmp = B V (m x r), H = tmp B^T (m x m)
+  // L_F = lmax(B V B^T) and lmax(V) (one launch): tmp = B V (m x r), H = tmp B^T (m x m)
   NNC_CUDA_TRY(small_gemm<T>(mn, r, r, B[n], r, 1, w.V, r, 1, nullptr, w.tmp, s));
   NNC_CUDA_TRY(small_gemm<T>(mn, mn, r, w.tmp, r, 1, B[n], 1, r, nullptr, w.H, s));
-  power_iter_kernel<T><<<1, 64, 0, s>>>(w.H, mn, nullptr, w.Ls + 0);
+  power_iter_kernel<T><<<2, 256, 0, s>>>(w.H, mn, w.Ls + 0, w.V, r, w.Ls + 1);
   note_launch(s);
   NNC_TRY(grad_a(w, n, s));
   // gF = gA B^T (N x m) into tmp
   NNC_CUDA_TRY(small_gemm<T>((int)Nn, mn, r, w.gA, r, 1, B[n], 1, r, nullptr, w.tmp, s));
-  pg_update_kernel<T><<<grid_for(Nn * mn, 256), 256, 0, s>>>(F[n], w.tmp, Nn * mn, w.Ls + 0);
+  pg_update_kernel<T><<<grid_for(Nn * mn, 256), 256, 0, s>>>(F[n], w.tmp, Nn * mn, w.Ls + 0,
+                                                               nullptr);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
   NNC_CUDA_TRY(launch_lift<T>(F[n], B[n], Nn, mn, r, w.A[n], s));
   // L_B = lmax(F^T F) lmax(V)
   NNC_TRY(launch_gram<T>(F[n], Nn, mn, w.S, s));
-  power_iter_kernel<T><<<1, 64, 0, s>>>(w.V, r, nullptr, w.Ls + 1);
-  note_launch(s);
-  power_iter_kernel<T><<<1, 64, 0, s>>>(w.S, mn, w.Ls + 1, w.Ls + 2);
+  power_iter_kernel<T><<<1, 256, 0, s>>>(w.S, mn, w.Ls + 2, w.S, mn, w.Ls + 2);
   note_launch(s);
   NNC_TRY(grad_a(w, n, s));
   // gB = F^T gA (m x r) into tmp
   NNC_CUDA_TRY(small_gemm<T>(mn, r, (int)Nn, F[n], 1, mn, w.gA, r, 1, nullptr, w.tmp, s));
-  pg_update_kernel<T><<<grid_for((int64_t)mn * r, 256), 256, 0, s>>>(B[n], w.tmp,
-                                                                      (int64_t)mn * r, w.Ls + 2);
+  pg_update_kernel<T><<<grid_for((int64_t)mn * r, 256), 256, 0, s>>>(B[n], w.tmp, (int64_t)mn * r,
+                                                                      w.Ls + 2, w.Ls + 1);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
   NNC_TRY(refresh_a(w, n, F[n], B[n], s));
@@ -450,9 +519,9 @@ int pg_mode(Work<T>& w, int n, T* const* F, T* const* B, cudaStream_t s) {
 }
 
 template <typename T>
-int loss_into(Work<T>& w, int n, double* out, cudaStream_t s) {
+int loss_into(Work<T>& w, int n, double* out, double* trace, int* counter, cudaStream_t s) {
   lifted_loss_kernel<T><<<1, 256, 0, s>>>(w.MT, w.A[n], w.N[n] * w.r, w.V, w.AtA[n], w.r * w.r,
-                                          w.stats, out);
+                                          w.stats, out, trace, counter);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
   return NNC_OK;
@@ -480,12 +549,15 @@ int lifted_grad(const T* X, int d, const int64_t* dims, const int* m, int r, boo
   const bool grads = gF != nullptr;
   double* dloss = w.Ls + 3;
   NNC_TRY(pass_last(w, F[d - 1], s));
-  if (grads) NNC_TRY(pass_first(w, F[0], s));
+  if (grads) {
+    NNC_TRY(pass_first(w, F[0], s));
+    NNC_TRY(make_u0(w, F[0], s));
+  }
   for (int n = 0; n < (grads ? d : 1); ++n) {
     const T* Z = nullptr;
     NNC_TRY(z_chain(w, n, F, &Z, s));
     NNC_TRY(mttkrp_and_v(w, n, Z, B, s));
-    if (n == 0) NNC_TRY(loss_into(w, 0, dloss, s));
+    if (n == 0) NNC_TRY(loss_into(w, 0, dloss, nullptr, nullptr, s));
     if (!grads) break;
     NNC_TRY(grad_a(w, n, s));
     const int mn = m[n];
@@ -500,6 +572,43 @@ int lifted_grad(const T* X, int d, const int64_t* dims, const int* m, int r, boo
   return NNC_OK;
 }
 
+namespace {
+
+// One projected-gradient step (two passes over X), stream-ordered on s.
+template <typename T>
+int pg_step(Work<T>& w, T* const* F, T* const* B, double* last, double* trace, int* counter,
+            cudaStream_t s) {
+  const int d = w.d;
+  NNC_TRY(pass_last(w, F[d - 1], s));
+  for (int n = 0; n < d; ++n) {
+    if (n == d - 1) NNC_TRY(pass_first(w, F[0], s));
+    const T* Z = nullptr;
+    NNC_TRY(z_chain(w, n, F, &Z, s));
+    NNC_TRY(mttkrp_and_v(w, n, Z, B, s));
+    NNC_TRY(pg_mode(w, n, F, B, s));
+    if (n == 0 && d > 2) NNC_TRY(make_u0(w, F[0], s));
+  }
+  // MT_d and V_d do not involve mode d: the loss at the new point.
+  return loss_into(w, d - 1, last, trace, counter, s);
+}
+
+// Private stream, graph and events of the replay loop.
+struct PgGraph {
+  cudaStream_t cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  ~PgGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
+}  // namespace
+
 template <typename T>
 int lifted_pg_fit(const T* X, int d, const int64_t* dims, const int* m, int r, bool tensor_cores,
                   int steps, T* const* F, T* const* B, double* trace, double* loss,
@@ -509,19 +618,39 @@ int lifted_pg_fit(const T* X, int d, const int64_t* dims, const int* m, int r, b
   NNC_TRY(setup(w, X, d, dims, m, r, tensor_cores, sc, s));
   for (int k = 0; k < d; ++k) NNC_TRY(refresh_a(w, k, F[k], B[k], s));
   double* last = w.Ls + 3;
-  for (int t = 0; t < steps; ++t) {
-    NNC_TRY(pass_last(w, F[d - 1], s));
-    for (int n = 0; n < d; ++n) {
-      if (n == d - 1) NNC_TRY(pass_first(w, F[0], s));
-      const T* Z = nullptr;
-      NNC_TRY(z_chain(w, n, F, &Z, s));
-      NNC_TRY(mttkrp_and_v(w, n, Z, B, s));
-      NNC_TRY(pg_mode(w, n, F, B, s));
+  int* counter = nullptr;
+  NNC_TRY(sc.get(&counter, 1));
+  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+  if (steps > 0) {
+    // One step is captured as a CUDA graph on a private stream and replayed;
+    // the trace slot advances through the device counter.
+    PgGraph g;
+    NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming));
+    NNC_CUDA_TRY(cudaEventRecord(g.fork, s));
+    NNC_CUDA_TRY(cudaStreamWaitEvent(g.cs, g.fork, 0));
+    NNC_CUDA_TRY(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
+    const int cap = pg_step(w, F, B, last, trace, counter, g.cs);
+    const cudaError_t end_e = cudaStreamEndCapture(g.cs, &g.graph);
+    if (cap != NNC_OK) return cap;
+    NNC_CUDA_TRY(end_e);
+    NNC_CUDA_TRY(cudaGraphInstantiate(&g.exec, g.graph, 0));
+    size_t nn = 0;
+    NNC_CUDA_TRY(cudaGraphGetNodes(g.graph, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    NNC_CUDA_TRY(cudaGraphGetNodes(g.graph, nodes.data(), &nn));
+    long long kernels = 0;
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      NNC_CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
+      if (ty == cudaGraphNodeTypeKernel) ++kernels;
     }
-    // MT_d and V_d do not involve mode d: the loss at the new point.
-    NNC_TRY(loss_into(w, d - 1, trace ? trace + t : last, s));
-    if (trace && t == steps - 1)
-      NNC_CUDA_TRY(cudaMemcpyAsync(last, trace + t, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    for (int t = 0; t < steps; ++t) NNC_CUDA_TRY(cudaGraphLaunch(g.exec, g.cs));
+    note_graph_launches(kernels * steps);
+    NNC_CUDA_TRY(cudaEventRecord(g.join, g.cs));
+    NNC_CUDA_TRY(cudaStreamWaitEvent(s, g.join, 0));
+    NNC_CUDA_TRY(cudaStreamSynchronize(g.cs));
   }
   NNC_TRY(check_tc(w, s));
   if (loss) {

@@ -205,8 +205,7 @@ template <typename T>
 cudaError_t launch_nncp(const nncp_job* jobs_dev, int n_jobs, size_t smem, int iters, double eps,
                         double* rel_errs, cudaStream_t s) {
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(nncp_kernel<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)nncp_kernel<T>, smem);
     if (e != cudaSuccess) return e;
   }
   nncp_kernel<T><<<n_jobs, kThreads, smem, s>>>(jobs_dev, iters, (T)eps, rel_errs);

@@ -159,8 +159,7 @@ int residual3_device(const T* X, const int64_t* dims, int model, const int* m, i
   NNC_TRY(sc.get(&part, (size_t)(2 * nblocks)));
   const size_t smem = (size_t)K * kResThreads * sizeof(T);
   if (smem > 48 * 1024)
-    NNC_CUDA_TRY(cudaFuncSetAttribute(residual_stream_kernel<T>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NNC_CUDA_TRY(raise_smem_limit((const void*)residual_stream_kernel<T>, smem));
   residual_stream_kernel<T><<<grid, kResThreads, smem, s>>>(X, R, N3, U, K, F3, part);
   note_launch(s);
   residual_final_kernel<<<1, 1024, 0, s>>>(part, nblocks, out2);

@@ -150,8 +150,7 @@ cudaError_t launch_pair_contract(const T* Y, const T* G, int64_t L, int NI, int 
   const size_t smem = (size_t)(L * C) * sizeof(T);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(pair_contract_kernel<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)pair_contract_kernel<T>, smem);
     if (e != cudaSuccess) return e;
   }
   pair_contract_kernel<T><<<NI, 256, smem, s>>>(Y, G, L, NI, MA, C, out);

@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ F,
 namespace {
 template <typename K>
 int set_smem(K kernel, size_t bytes) {
-  NNC_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  NNC_CUDA_TRY(raise_smem_limit((const void*)kernel, bytes));
   return NNC_OK;
 }
 }  // namespace

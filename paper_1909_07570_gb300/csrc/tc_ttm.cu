@@ -626,8 +626,7 @@ template <int KIND, bool kMN, int NP>
 int launch_pass(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& blo, int nk,
                 int64_t tiles, const TcEpilogue& ep, int* err, cudaStream_t s) {
   constexpr int smem = TcLayout<KIND, NP>::kSmem;
-  NNC_CUDA_TRY(cudaFuncSetAttribute(tc_pass_kernel<KIND, kMN, NP>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  NNC_CUDA_TRY(raise_smem_limit((const void*)tc_pass_kernel<KIND, kMN, NP>, smem));
   int64_t grid = device_sm_count();
   if (grid > tiles) grid = tiles;
   NNC_CUDA_TRY(launch_pdl(tc_pass_kernel<KIND, kMN, NP>, dim3(static_cast<unsigned>(grid)),
