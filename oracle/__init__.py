@@ -23,6 +23,7 @@ from .tensor_algebra import (  # noqa: F401
 )
 from .nncandelinc import (  # noqa: F401
     DEFAULT_EPS,
+    alg2_fit,
     congruence_matrix,
     lift,
     POWER_ITERS,
@@ -39,6 +40,8 @@ from .nncandelinc import (  # noqa: F401
     ntd_core_terms,
     ntd_factor_terms,
     ntd_fit,
+    nmf_fit,
+    nmf_terms,
     ntd_sweep,
     power_iteration_lmax,
     rel_err_cp,

@@ -14,7 +14,8 @@ What it computes, in the paper's notation (X is d-way, N_1 x ... x N_d):
   nnCANDELINC objective of Eq. nnCANDELINC (Sec. 4),
 * the relative reconstruction error of Sec. 4.1,
 * the gradient of the lifted loss 1/2 ||X - I x_i F^(i) B^(i)||_F^2 and a
-  block projected-gradient fit of it (the differentiation form).
+  block projected-gradient fit of it (the differentiation form),
+* Alg. 2: nnCPD of X followed by an NMF of every CP factor.
 
 The paper names the problem and the packages it called, not their update
 rules. The rules here are the multiplicative updates (MU) obtained by splitting
@@ -338,3 +339,49 @@ def lifted_pg_fit(X, F0, B0, steps):
         F, B = lifted_pg_step(X, F, B)
         trace.append(lifted_loss(X, F, B))
     return F, B, np.array(trace)
+
+
+# ---------------------------------------------------------------------------
+# Alg. 2: nnCPD of X, then an NMF of every CP factor
+# ---------------------------------------------------------------------------
+# Alg. 2 (Sec. 4.1) computes A^(i) <- nnCPD(X, r) and then
+# F^(i), B^(i) <- NMF(A^(i), m_i). The nnCPD is :func:`nncp_fit` applied to X
+# itself. The NMF, like every other update rule here, is the MU split of its
+# gradient (Lee-Seung): for 1/2 ||A - F B||^2,
+#   F <- max(F .* (A B^T) / max(F B B^T, eps), 0),
+#   B <- max(B .* (F^T A) / max(F^T F B, eps), 0),   F first, then B.
+
+def nmf_terms(A, F, B):
+    """((num_F, den_F), (num_B, den_B)) of the NMF A ~ F B at (F, B); the
+    gradients are den - num."""
+    A, F, B = _f64(A), _f64(F), _f64(B)
+    return (A @ B.T, F @ (B @ B.T)), (F.T @ A, (F.T @ F) @ B)
+
+
+def nmf_fit(A, F0, B0, iters, eps=DEFAULT_EPS):
+    """NMF of A (N x r) with rank m by ``iters`` MU iterations (F, then B).
+    Returns (F, B, trace) with trace[t] = ||A - F B||_F / ||A||_F after t."""
+    A = _f64(A)
+    F, B = _f64(F0), _f64(B0)
+    a = frobenius(A)
+    trace = []
+    for _ in range(iters):
+        (nf, df), _ = nmf_terms(A, F, B)
+        F = mu_step(F, nf, df, eps)
+        _, (nb, db) = nmf_terms(A, F, B)
+        B = mu_step(B, nb, db, eps)
+        trace.append(frobenius(A - F @ B) / a)
+    return F, B, np.array(trace)
+
+
+def alg2_fit(X, A0, F0, B0, cp_iters, nmf_iters, eps=DEFAULT_EPS):
+    """Alg. 2: A = nnCPD(X, r) from A0, then (F^(i), B^(i)) = NMF(A^(i), m_i)
+    from (F0, B0). Returns (A, F, B, cp_trace, nmf_traces)."""
+    A, cp_trace = nncp_fit(X, A0, cp_iters, eps)
+    F, B, nmf_traces = [], [], []
+    for n in range(len(A)):
+        Fn, Bn, tr = nmf_fit(A[n], F0[n], B0[n], nmf_iters, eps)
+        F.append(Fn)
+        B.append(Bn)
+        nmf_traces.append(tr)
+    return A, F, B, cp_trace, nmf_traces

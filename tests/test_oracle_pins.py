@@ -354,3 +354,53 @@ def test_lifted_pg_monotone_and_nonnegative(dims, m, r):
     assert np.all(np.diff(tr) <= 1e-12 * tr[:-1])
     assert tr[-1] < 0.5 * l0
     assert all((a >= 0).all() for a in F + B)
+
+
+# ---------------------------------------------------------------------------
+# Alg. 2: NMF of the CP factors
+# ---------------------------------------------------------------------------
+
+def test_nmf_terms_are_the_gradient():
+    A = RNG.random((7, 4))
+    F = RNG.random((7, 3))
+    B = RNG.random((3, 4))
+
+    def loss():
+        R = A - F @ B
+        return 0.5 * np.sum(R * R)
+
+    (nf, df), (nb, db) = orc.nmf_terms(A, F, B)
+    np.testing.assert_allclose(df - nf, _fd_grad(loss, F), rtol=1e-7, atol=1e-8)
+    np.testing.assert_allclose(db - nb, _fd_grad(loss, B), rtol=1e-7, atol=1e-8)
+
+
+def test_nmf_exact_factorisation_is_a_fixed_point_and_fit_is_monotone():
+    rng = np.random.default_rng(91)
+    F = rng.random((9, 3)) + 0.1
+    B = rng.random((3, 5)) + 0.1
+    F1, B1, tr = orc.nmf_fit(F @ B, F, B, 3)
+    np.testing.assert_allclose(F1, F, rtol=1e-12)
+    np.testing.assert_allclose(B1, B, rtol=1e-12)
+    assert tr.max() < 1e-13
+    A = rng.random((30, 6))
+    F2, B2, tr = orc.nmf_fit(A, 1 - rng.random((30, 4)), 1 - rng.random((4, 6)), 60)
+    assert np.all(np.diff(tr) <= 1e-12) and tr[-1] < tr[0]
+    assert (F2 >= 0).all() and (B2 >= 0).all()
+
+
+def test_alg2_on_a_planted_canonical_tensor():
+    # X = I x_i W^(i) H^(i) with W^(i) H^(i) of rank r: Alg. 2's nnCPD fits X
+    # and each NMF of a CP factor reaches a small residual (a quality check of
+    # the composition; the pieces are pinned above).
+    dims, kappa, r = (10, 9, 8), (3, 3, 3), 3
+    rng = np.random.default_rng(123)
+    W = [rng.random((n, k)) + 0.1 for n, k in zip(dims, kappa)]
+    H = [rng.random((k, r)) + 0.1 for k in kappa]
+    X = orc.cp_reconstruct(orc.lift(W, H))
+    A0 = [1 - rng.random((n, r)) for n in dims]
+    F0 = [1 - rng.random((n, k)) for n, k in zip(dims, kappa)]
+    B0 = [1 - rng.random((k, r)) for k in kappa]
+    A, F, B, cpt, nmft = orc.alg2_fit(X, A0, F0, B0, 300, 300)
+    assert cpt[-1] < 0.05 and np.all(np.diff(cpt) <= 1e-12)
+    assert all(t[-1] < 0.05 for t in nmft)
+    assert orc.rel_err_cp(X, orc.lift(F, B)) < 0.1
