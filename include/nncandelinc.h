@@ -247,6 +247,55 @@ int candelinc_pg_fit(const void* X, int d, const int64_t* dims, const int* m, in
                      double* loss, void* stream);
 
 /*
+ * nncp_tensor_fit - nnCPD of X itself, the first step of Alg. 2 (Sec. 4.1):
+ * `opts->iters` Gauss-Seidel MU sweeps on the CP factors,
+ *   A^(n) <- max(A^(n) .* MT_n / max(A^(n) V_n, eps), 0),
+ *   MT_n = unfold_n(X) KR_{k!=n}(A^(k)),  V_n = Hadamard_{k!=n} A^(k)T A^(k)
+ * (the rule of nncp_core_fit with X in place of the core), two passes over X
+ * per sweep.
+ *
+ *  X          device, C order, d = 3 or 4 modes dims[0..d-1]
+ *  A          host array of d device pointers, A^(n) dims[n] x r (1 <= r <= 64),
+ *             initial values on entry, result on exit
+ *  trace      device, opts->iters doubles: ||X - I x_k A^(k)||_F / ||X||_F after
+ *             each sweep (FP64 identity), or NULL
+ *  rel_err    host, the last trace value (NaN for 0 sweeps), or NULL
+ *  precision  NNC_FP64, NNC_FP32 (TF32x3 tensor-core passes), NNC_FP32_SIMT
+ * Errors: INVALID_ARG, NONFINITE, UNSUPPORTED, CUDA, ALLOC, TIMEOUT.
+ */
+int nncp_tensor_fit(const void* X, int d, const int64_t* dims, int r, int precision,
+                    const nnc_opts* opts, void* const* A, double* trace, double* rel_err,
+                    void* stream);
+
+/*
+ * nmf_fit - the NMF A ~ F B of one CP factor, the second step of Alg. 2 (Sec.
+ * 4.1): `opts->iters` MU iterations (Lee-Seung),
+ *   F <- max(F .* (A B^T) / max(F B B^T, eps), 0),
+ *   B <- max(B .* (F^T A) / max(F^T F B, eps), 0).
+ *
+ *  A          device, N x r row-major (read only)
+ *  F, B       device, N x m and m x r row-major, initial values in, result out
+ *  trace      device, opts->iters doubles: ||A - F B||_F / ||A||_F, or NULL
+ *  rel_err    host, the last value (NaN for 0 iterations), or NULL
+ *  precision  NNC_FP64 (double) or NNC_FP32 / NNC_FP32_SIMT (float)
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA, ALLOC.
+ */
+int nmf_fit(const void* A, int64_t N, int r, int m, int precision, const nnc_opts* opts, void* F,
+            void* B, double* trace, double* rel_err, void* stream);
+
+/*
+ * candelinc_alg2 - Alg. 2 (Sec. 4.1): A = nnCPD(X, r) by nncp_tensor_fit
+ * (cp_opts), then F^(n), B^(n) = NMF(A^(n), m[n]) by nmf_fit (nmf_opts) for
+ * every mode. A, F, B hold the initial values on entry. cp_rel_err (host) gets
+ * the CP fit, nmf_rel_errs (host, d doubles) the NMF fits; either may be NULL.
+ * Errors: as nncp_tensor_fit and nmf_fit.
+ */
+int candelinc_alg2(const void* X, int d, const int64_t* dims, const int* m, int r, int precision,
+                   const nnc_opts* cp_opts, const nnc_opts* nmf_opts, void* const* A,
+                   void* const* F, void* const* B, double* cp_rel_err, double* nmf_rel_errs,
+                   void* stream);
+
+/*
  * recon_residual - ||X - X_hat||_F and ||X||_F in one pass over X with FP64
  * accumulation (the relative error of Sec. 4.1 is their ratio).
  *

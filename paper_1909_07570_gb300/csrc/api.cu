@@ -365,6 +365,67 @@ int candelinc_pg_fit(const void* X, int d, const int64_t* dims, const int* m, in
   return precision == NNC_BF16_REFINE ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
 }
 
+int nncp_tensor_fit(const void* X, int d, const int64_t* dims, int r, int precision,
+                    const nnc_opts* opts, void* const* A, double* trace, double* rel_err,
+                    void* stream) {
+  g_detail.clear();
+  if (X == nullptr || A == nullptr || opts == nullptr || opts->iters < 0 || !(opts->eps > 0.0))
+    return NNC_ERR_INVALID_ARG;
+  if ((d != 3 && d != 4) || r < 1 || r > 64) return NNC_ERR_INVALID_ARG;
+  int m[4] = {r, r, r, r};
+  NNC_TRY(check_shape(d, dims, m, 64));
+  for (int n = 0; n < d; ++n)
+    if (A[n] == nullptr) return NNC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == NNC_FP64) {
+    double* a[4];
+    for (int n = 0; n < d; ++n) a[n] = static_cast<double*>(A[n]);
+    return nncp_tensor_fit<double>(static_cast<const double*>(X), d, dims, r, false, opts->iters,
+                                   opts->eps, a, trace, rel_err, s);
+  }
+  if (precision == NNC_FP32 || precision == NNC_FP32_SIMT) {
+    float* a[4];
+    for (int n = 0; n < d; ++n) a[n] = static_cast<float*>(A[n]);
+    return nncp_tensor_fit<float>(static_cast<const float*>(X), d, dims, r,
+                                  precision == NNC_FP32, opts->iters, opts->eps, a, trace,
+                                  rel_err, s);
+  }
+  return precision == NNC_BF16_REFINE ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
+}
+
+int nmf_fit(const void* A, int64_t N, int r, int m, int precision, const nnc_opts* opts, void* F,
+            void* B, double* trace, double* rel_err, void* stream) {
+  g_detail.clear();
+  if (A == nullptr || F == nullptr || B == nullptr || opts == nullptr || opts->iters < 0 ||
+      !(opts->eps > 0.0))
+    return NNC_ERR_INVALID_ARG;
+  if (N < 1 || N > (1LL << 31) - 1 || r < 1 || r > 1024 || m < 1 || m > 1024)
+    return NNC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == NNC_FP64)
+    return nmf_fit<double>(static_cast<const double*>(A), N, r, m, opts->iters, opts->eps,
+                           static_cast<double*>(F), static_cast<double*>(B), trace, rel_err, s);
+  if (precision == NNC_FP32 || precision == NNC_FP32_SIMT)
+    return nmf_fit<float>(static_cast<const float*>(A), N, r, m, opts->iters, opts->eps,
+                          static_cast<float*>(F), static_cast<float*>(B), trace, rel_err, s);
+  return precision == NNC_BF16_REFINE ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
+}
+
+int candelinc_alg2(const void* X, int d, const int64_t* dims, const int* m, int r, int precision,
+                   const nnc_opts* cp_opts, const nnc_opts* nmf_opts, void* const* A,
+                   void* const* F, void* const* B, double* cp_rel_err, double* nmf_rel_errs,
+                   void* stream) {
+  g_detail.clear();
+  if (F == nullptr || B == nullptr || m == nullptr) return NNC_ERR_INVALID_ARG;
+  NNC_TRY(nncp_tensor_fit(X, d, dims, r, precision, cp_opts, A, nullptr, cp_rel_err, stream));
+  for (int n = 0; n < d; ++n) {
+    if (m[n] < 1 || m[n] > 1024) return NNC_ERR_INVALID_ARG;
+    NNC_TRY(nmf_fit(A[n], dims[n], r, m[n], precision, nmf_opts, F[n], B[n], nullptr,
+                    nmf_rel_errs ? nmf_rel_errs + n : nullptr, stream));
+  }
+  return NNC_OK;
+}
+
 int recon_residual(const void* X, int d, const int64_t* dims, int precision, int model,
                    const int* m, int r, const void* const* factors, const void* G,
                    double* resid_norm, double* x_norm, void* stream) {

@@ -128,6 +128,32 @@ __global__ void transpose_small_kernel(const T* __restrict__ in, int R, int64_t 
   }
 }
 
+// I (r x r).
+template <typename T>
+__global__ void identity_kernel(T* I, int r) {
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) I[e] = (e / r == e % r) ? T(1) : T(0);
+}
+
+// out = ||R|| / a (||R|| when a is null), n entries, FP64 sum in a fixed
+// order; also trace[*counter] (then *counter + 1) when a trace is given.
+template <typename T>
+__global__ void rel_norm_kernel(const T* __restrict__ R, int64_t n, const double* __restrict__ a,
+                                double* out, double* trace, int* counter) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s += (double)R[e] * (double)R[e];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    const double v = a ? sqrt(s) / a[0] : sqrt(s);
+    out[0] = v;
+    if (trace) {
+      const int t = *counter;
+      trace[t] = v;
+      *counter = t + 1;
+    }
+  }
+}
+
 // V = Hadamard product of the listed r x r matrices (all ones if none).
 template <typename T>
 struct HadArgs {
@@ -220,7 +246,7 @@ template <typename T>
 __global__ void lifted_loss_kernel(const T* __restrict__ MT, const T* __restrict__ A, int64_t n,
                                    const T* __restrict__ V, const T* __restrict__ AtA, int rr,
                                    const double* __restrict__ x2, double* out, double* trace,
-                                   int* counter) {
+                                   int* counter, int rel) {
   __shared__ double red[32];
   double a = 0.0, b = 0.0;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) a += (double)MT[e] * (double)A[e];
@@ -228,7 +254,8 @@ __global__ void lifted_loss_kernel(const T* __restrict__ MT, const T* __restrict
   a = block_sum(a, red);
   b = block_sum(b, red);
   if (threadIdx.x == 0) {
-    const double v = 0.5 * x2[0] - a + 0.5 * b;
+    double v = 0.5 * x2[0] - a + 0.5 * b;
+    if (rel) v = sqrt((v > 0.0 ? 2.0 * v : 0.0) / x2[0]);  // ||X - X_hat|| / ||X||
     out[0] = v;
     if (trace) {
       const int t = *counter;
@@ -519,9 +546,10 @@ int pg_mode(Work<T>& w, int n, T* const* F, T* const* B, cudaStream_t s) {
 }
 
 template <typename T>
-int loss_into(Work<T>& w, int n, double* out, double* trace, int* counter, cudaStream_t s) {
+int loss_into(Work<T>& w, int n, double* out, double* trace, int* counter, cudaStream_t s,
+              int rel = 0) {
   lifted_loss_kernel<T><<<1, 256, 0, s>>>(w.MT, w.A[n], w.N[n] * w.r, w.V, w.AtA[n], w.r * w.r,
-                                          w.stats, out, trace, counter);
+                                          w.stats, out, trace, counter, rel);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
   return NNC_OK;
@@ -664,6 +692,150 @@ int lifted_pg_fit(const T* X, int d, const int64_t* dims, const int* m, int r, b
   return NNC_OK;
 }
 
+namespace {
+
+// Captures `body` (stream-ordered work on a private stream) once as a CUDA
+// graph and replays it `count` times after the work queued on s.
+template <typename Body>
+int replay(int count, cudaStream_t s, Body body) {
+  if (count <= 0) return NNC_OK;
+  PgGraph g;
+  NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
+  NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming));
+  NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming));
+  NNC_CUDA_TRY(cudaEventRecord(g.fork, s));
+  NNC_CUDA_TRY(cudaStreamWaitEvent(g.cs, g.fork, 0));
+  NNC_CUDA_TRY(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
+  const int cap = body(g.cs);
+  const cudaError_t end_e = cudaStreamEndCapture(g.cs, &g.graph);
+  if (cap != NNC_OK) return cap;
+  NNC_CUDA_TRY(end_e);
+  NNC_CUDA_TRY(cudaGraphInstantiate(&g.exec, g.graph, 0));
+  size_t nn = 0;
+  NNC_CUDA_TRY(cudaGraphGetNodes(g.graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  NNC_CUDA_TRY(cudaGraphGetNodes(g.graph, nodes.data(), &nn));
+  long long kernels = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    NNC_CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
+    if (ty == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  for (int t = 0; t < count; ++t) NNC_CUDA_TRY(cudaGraphLaunch(g.exec, g.cs));
+  note_graph_launches(kernels * count);
+  NNC_CUDA_TRY(cudaEventRecord(g.join, g.cs));
+  NNC_CUDA_TRY(cudaStreamWaitEvent(s, g.join, 0));
+  NNC_CUDA_TRY(cudaStreamSynchronize(g.cs));
+  return NNC_OK;
+}
+
+}  // namespace
+
+// nnCPD of X itself (Alg. 2, first step): the MU sweep of the core nnCPD with
+// X in place of G, A^(n) <- max(A^(n) .* MT_n / max(A^(n) V_n, eps), 0) for
+// n = 1..d. MT_n comes from the lifted machinery with F := A and B := I_r
+// (so m := r): two passes over X per sweep, T_last = X x_d A^(d)T serving
+// modes 1..d-1 and T_first = X x_1 A^(1)T mode d. trace[t] (device, optional)
+// = ||X - I x_k A^(k)|| / ||X|| after sweep t by the identity in FP64.
+template <typename T>
+int nncp_tensor_fit(const T* X, int d, const int64_t* dims, int r, bool tensor_cores, int iters,
+                    double eps, T* const* A, double* trace, double* rel_err, cudaStream_t s) {
+  Scratch sc(s);
+  Work<T> w;
+  int m[kMaxD];
+  for (int k = 0; k < d; ++k) m[k] = r;
+  NNC_TRY(setup(w, X, d, dims, m, r, tensor_cores, sc, s));
+  T* I = nullptr;
+  NNC_TRY(sc.get(&I, (size_t)r * r));
+  identity_kernel<T><<<1, 256, 0, s>>>(I, r);
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  T* B[kMaxD];
+  for (int k = 0; k < d; ++k) B[k] = I;
+  for (int k = 0; k < d; ++k) NNC_TRY(refresh_a(w, k, A[k], B[k], s));
+  int* counter = nullptr;
+  NNC_TRY(sc.get(&counter, 1));
+  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+  double* last = w.Ls + 3;
+  NNC_TRY(replay(iters, s, [&](cudaStream_t cs) -> int {
+    NNC_TRY(pass_last(w, A[d - 1], cs));
+    for (int n = 0; n < d; ++n) {
+      if (n == d - 1) NNC_TRY(pass_first(w, A[0], cs));
+      const T* Z = nullptr;
+      NNC_TRY(z_chain(w, n, A, &Z, cs));
+      NNC_TRY(mttkrp_and_v(w, n, Z, B, cs));
+      // Den = A^(n) V_n into gA; MU in place.
+      NNC_CUDA_TRY(small_gemm<T>((int)w.N[n], r, r, A[n], r, 1, w.V, r, 1, nullptr, w.gA, cs));
+      NNC_CUDA_TRY(launch_elementwise_mu<T>(A[n], w.MT, w.gA, w.N[n] * r, eps, cs));
+      NNC_TRY(refresh_a(w, n, A[n], B[n], cs));
+      if (n == 0 && d > 2) NNC_TRY(make_u0(w, A[0], cs));
+    }
+    return loss_into(w, d - 1, last, trace, counter, cs, /*rel=*/1);
+  }));
+  NNC_TRY(check_tc(w, s));
+  if (rel_err) {
+    if (iters == 0) {
+      *rel_err = NAN;
+    } else {
+      NNC_CUDA_TRY(cudaMemcpyAsync(rel_err, last, sizeof(double), cudaMemcpyDeviceToHost, s));
+      NNC_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+  }
+  return NNC_OK;
+}
+
+// NMF A ~ F B (A N x r, F N x m, B m x r) by MU (Alg. 2, second step):
+//   F <- max(F .* (A B^T) / max(F (B B^T), eps), 0),
+//   B <- max(B .* (F^T A) / max((F^T F) B, eps), 0).
+// trace[t] (device, optional) = ||A - F B|| / ||A|| after iteration t.
+template <typename T>
+int nmf_fit(const T* A, int64_t N, int r, int m, int iters, double eps, T* F, T* B,
+            double* trace, double* rel_err, cudaStream_t s) {
+  Scratch sc(s);
+  T *numF, *denF, *BBt, *numB, *denB, *FtF, *R;
+  double *a, *last;
+  int* counter;
+  NNC_TRY(sc.get(&numF, (size_t)(N * m)));
+  NNC_TRY(sc.get(&denF, (size_t)(N * m)));
+  NNC_TRY(sc.get(&BBt, (size_t)m * m));
+  NNC_TRY(sc.get(&numB, (size_t)m * r));
+  NNC_TRY(sc.get(&denB, (size_t)m * r));
+  NNC_TRY(sc.get(&FtF, (size_t)m * m));
+  NNC_TRY(sc.get(&R, (size_t)(N * r)));
+  NNC_TRY(sc.get(&a, 1));
+  NNC_TRY(sc.get(&last, 1));
+  NNC_TRY(sc.get(&counter, 1));
+  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+  rel_norm_kernel<T><<<1, 256, 0, s>>>(A, N * r, nullptr, a, nullptr, nullptr);  // ||A||
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  NNC_TRY(replay(iters, s, [&](cudaStream_t cs) -> int {
+    NNC_CUDA_TRY(small_gemm<T>((int)N, m, r, A, r, 1, B, 1, r, nullptr, numF, cs));  // A B^T
+    NNC_CUDA_TRY(small_gemm<T>(m, m, r, B, r, 1, B, 1, r, nullptr, BBt, cs));        // B B^T
+    NNC_CUDA_TRY(small_gemm<T>((int)N, m, m, F, m, 1, BBt, m, 1, nullptr, denF, cs));
+    NNC_CUDA_TRY(launch_elementwise_mu<T>(F, numF, denF, N * m, eps, cs));
+    NNC_CUDA_TRY(small_gemm<T>(m, r, (int)N, F, 1, m, A, r, 1, nullptr, numB, cs));  // F^T A
+    NNC_CUDA_TRY(small_gemm<T>(m, m, (int)N, F, 1, m, F, m, 1, nullptr, FtF, cs));   // F^T F
+    NNC_CUDA_TRY(small_gemm<T>(m, r, m, FtF, m, 1, B, r, 1, nullptr, denB, cs));
+    NNC_CUDA_TRY(launch_elementwise_mu<T>(B, numB, denB, (int64_t)m * r, eps, cs));
+    NNC_CUDA_TRY(small_gemm<T>((int)N, r, m, F, m, 1, B, r, 1, A, R, cs));  // F B - A
+    rel_norm_kernel<T><<<1, 256, 0, cs>>>(R, N * r, a, last, trace, counter);
+    note_launch(cs);
+    NNC_CUDA_TRY(cudaGetLastError());
+    return NNC_OK;
+  }));
+  if (rel_err) {
+    if (iters == 0) {
+      *rel_err = NAN;
+    } else {
+      NNC_CUDA_TRY(cudaMemcpyAsync(rel_err, last, sizeof(double), cudaMemcpyDeviceToHost, s));
+      NNC_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+  }
+  NNC_CUDA_TRY(cudaStreamSynchronize(s));
+  return NNC_OK;
+}
+
 template int lifted_grad<float>(const float*, int, const int64_t*, const int*, int, bool,
                                 float* const*, float* const*, float* const*, float* const*,
                                 double*, cudaStream_t);
@@ -672,6 +844,14 @@ template int lifted_grad<double>(const double*, int, const int64_t*, const int*,
                                  double*, cudaStream_t);
 template int lifted_pg_fit<float>(const float*, int, const int64_t*, const int*, int, bool, int,
                                   float* const*, float* const*, double*, double*, cudaStream_t);
+template int nncp_tensor_fit<float>(const float*, int, const int64_t*, int, bool, int, double,
+                                    float* const*, double*, double*, cudaStream_t);
+template int nncp_tensor_fit<double>(const double*, int, const int64_t*, int, bool, int, double,
+                                     double* const*, double*, double*, cudaStream_t);
+template int nmf_fit<float>(const float*, int64_t, int, int, int, double, float*, float*,
+                            double*, double*, cudaStream_t);
+template int nmf_fit<double>(const double*, int64_t, int, int, int, double, double*, double*,
+                             double*, double*, cudaStream_t);
 template int lifted_pg_fit<double>(const double*, int, const int64_t*, const int*, int, bool,
                                    int, double* const*, double* const*, double*, double*,
                                    cudaStream_t);

@@ -21,4 +21,17 @@ int lifted_pg_fit(const T* X, int d, const int64_t* dims, const int* m, int r, b
                   int steps, T* const* F, T* const* B, double* trace, double* loss,
                   cudaStream_t s);
 
+// nnCPD of X itself (Alg. 2, first step): `iters` MU sweeps on the CP factors
+// A^(n) (dims[n] x r) in place; trace (device, optional) and rel_err (host,
+// optional) get ||X - I x_k A^(k)|| / ||X||.
+template <typename T>
+int nncp_tensor_fit(const T* X, int d, const int64_t* dims, int r, bool tensor_cores, int iters,
+                    double eps, T* const* A, double* trace, double* rel_err, cudaStream_t s);
+
+// NMF A ~ F B by `iters` MU iterations (Alg. 2, second step), F (N x m) and
+// B (m x r) in place; trace / rel_err get ||A - F B|| / ||A||.
+template <typename T>
+int nmf_fit(const T* A, int64_t N, int r, int m, int iters, double eps, T* F, T* B,
+            double* trace, double* rel_err, cudaStream_t s);
+
 }  // namespace nnc

@@ -25,6 +25,7 @@ _STATUS = {
 EXPORTED = ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched",
             "nncp_core_fit_batched_noalloc", "nnc_mode_product", "candelinc_lift",
             "recon_residual", "candelinc_lifted_grad", "candelinc_pg_fit",
+            "nncp_tensor_fit", "nmf_fit", "candelinc_alg2",
             "nnc_status_string", "nnc_last_error_detail",
             "nnc_profile_enable", "nnc_profile_read", "nnc_kernel_launches")
 
@@ -77,9 +78,17 @@ def load(path: str | None = None):
                                           vpp, vpp, vpp, vpp, dp, vp]
     lib.candelinc_pg_fit.argtypes = [vp, ctypes.c_int, i64p, ip, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, vpp, vpp, vp, dp, vp]
+    lib.nncp_tensor_fit.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(nnc_opts), vpp, vp, dp, vp]
+    lib.nmf_fit.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.POINTER(nnc_opts), vp, vp, vp, dp, vp]
+    lib.candelinc_alg2.argtypes = [vp, ctypes.c_int, i64p, ip, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(nnc_opts), ctypes.POINTER(nnc_opts), vpp, vpp,
+                                   vpp, dp, dp, vp]
     for fn in ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched",
                "nncp_core_fit_batched_noalloc", "nnc_mode_product", "candelinc_lift", "recon_residual",
-               "candelinc_lifted_grad", "candelinc_pg_fit"):
+               "candelinc_lifted_grad", "candelinc_pg_fit", "nncp_tensor_fit", "nmf_fit",
+               "candelinc_alg2"):
         getattr(lib, fn).restype = ctypes.c_int
     lib.nnc_status_string.argtypes = [ctypes.c_int]
     lib.nnc_status_string.restype = ctypes.c_char_p
@@ -288,6 +297,61 @@ def candelinc_pg_fit(X, F, B, steps, precision=None, trace=True, stream=None):
                                  _ptr(tr) if trace else None, ctypes.byref(loss), _stream(stream))
     _check("candelinc_pg_fit", st)
     return loss.value, (tr[:steps] if trace else None)
+
+
+def nncp_tensor_fit(X, A, iters, precision=None, eps=1e-12, trace=True, stream=None):
+    """nnCPD of X itself (Alg. 2, first step), in place on A (list of N_n x r).
+    Returns (relative error, device FP64 trace or None)."""
+    code, dtype = _precision(X, precision)
+    _require(X, dtype, "X")
+    for n, a in enumerate(A):
+        _require(a, dtype, f"A[{n}]")
+    r = A[0].shape[1]
+    opts = nnc_opts(int(iters), 0, float(eps))
+    tr = torch.empty(max(iters, 1), dtype=torch.float64, device=X.device) if trace else None
+    err = ctypes.c_double()
+    st = load().nncp_tensor_fit(_ptr(X), X.dim(), _i64(X.shape), r, code, ctypes.byref(opts),
+                                _ptrs(A), _ptr(tr) if trace else None, ctypes.byref(err),
+                                _stream(stream))
+    _check("nncp_tensor_fit", st)
+    return err.value, (tr[:iters] if trace else None)
+
+
+def nmf_fit(A, F, B, iters, precision=None, eps=1e-12, trace=True, stream=None):
+    """NMF A ~ F B by MU (Alg. 2, second step), in place on F, B.
+    Returns (relative error, device FP64 trace or None)."""
+    code, dtype = _precision(A, precision)
+    for name, t in (("A", A), ("F", F), ("B", B)):
+        _require(t, dtype, name)
+    opts = nnc_opts(int(iters), 0, float(eps))
+    tr = torch.empty(max(iters, 1), dtype=torch.float64, device=A.device) if trace else None
+    err = ctypes.c_double()
+    st = load().nmf_fit(_ptr(A), A.shape[0], A.shape[1], F.shape[1], code, ctypes.byref(opts),
+                        _ptr(F), _ptr(B), _ptr(tr) if trace else None, ctypes.byref(err),
+                        _stream(stream))
+    _check("nmf_fit", st)
+    return err.value, (tr[:iters] if trace else None)
+
+
+def candelinc_alg2(X, A, F, B, cp_iters, nmf_iters, precision=None, eps=1e-12, stream=None):
+    """Alg. 2 in place on A, F, B: nnCPD of X, then an NMF of every CP factor.
+    Returns (CP relative error, list of NMF relative errors)."""
+    code, dtype = _precision(X, precision)
+    _require(X, dtype, "X")
+    d = X.dim()
+    for n in range(d):
+        _require(A[n], dtype, f"A[{n}]")
+        _require(F[n], dtype, f"F[{n}]")
+        _require(B[n], dtype, f"B[{n}]")
+    cp = nnc_opts(int(cp_iters), 0, float(eps))
+    nm = nnc_opts(int(nmf_iters), 0, float(eps))
+    cp_err = ctypes.c_double()
+    nmf_err = (ctypes.c_double * d)()
+    st = load().candelinc_alg2(_ptr(X), d, _i64(X.shape), _i32([f.shape[1] for f in F]),
+                               A[0].shape[1], code, ctypes.byref(cp), ctypes.byref(nm), _ptrs(A),
+                               _ptrs(F), _ptrs(B), ctypes.byref(cp_err), nmf_err, _stream(stream))
+    _check("candelinc_alg2", st)
+    return cp_err.value, list(nmf_err)
 
 
 def recon_residual(X, factors, G=None, stream=None):
