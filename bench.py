@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-precision-form", action="store_true")
     p.add_argument("--no-differentiation-form", action="store_true")
+    p.add_argument("--no-batching-form", action="store_true")
     return p.parse_args()
 
 
@@ -454,6 +455,55 @@ def differentiation_form(dev):
             "final_lifted_rel_err": float(np.sqrt(2 * max(loss, 0.0)) / xn)}
 
 
+def batching_form(dev):
+    """Many uneven nnTD problems (the batching workload: 64 planted tensors with
+    modes in [32, 256], m = 2r) through ntd_fit_batched, then every core fitted
+    at CP ranks 2..8 with 8 restarts in one nncp_core_fit_batched launch. Wall
+    time around the calls (both return after their work is done)."""
+    import torch
+
+    from paper_1909_07570_gb300 import inputs, native
+    B = inputs.BATCH
+    probs = inputs.batch_problems()
+
+    def upload():
+        return [(torch.tensor(p["X"], dtype=torch.float32, device=dev),
+                 [torch.tensor(f, dtype=torch.float32, device=dev) for f in p["F0"]],
+                 torch.tensor(p["G0"], dtype=torch.float32, device=dev)) for p in probs]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    warm = upload()[:4]
+    native.ntd_fit_batched(warm, 5, precision="fp32", trace=False)
+    batch = upload()
+    t_ntd, (errs, _, _) = timed(lambda: native.ntd_fit_batched(
+        batch, B["iters"], precision="fp32", concurrency=8, trace=False))
+    seq = upload()[:8]
+    t_seq, _ = timed(lambda: native.ntd_fit_batched(seq, B["iters"], precision="fp32",
+                                                     concurrency=1, trace=False))
+    jobs = []
+    for b, (_, _, G) in enumerate(batch):
+        for _, _, B0 in inputs.batch_core_inits(probs[b]["m"], b):
+            jobs.append((G, [torch.tensor(x, dtype=torch.float32, device=dev) for x in B0]))
+    t_cp, cp_errs = timed(lambda: native.nncp_core_fit_batched(jobs, B["cp_iters"],
+                                                               precision="fp32"))
+    n = len(batch)
+    return {"workload": B["name"], "tensors": n, "ntd_sweeps": B["iters"], "concurrency": 8,
+            "ntd_ms": round(t_ntd * 1e3, 1), "tensors_per_s": round(n / t_ntd, 2),
+            "ntd_sweeps_per_s": round(n * B["iters"] / t_ntd, 1),
+            "sequential_first8_ms": round(t_seq * 1e3, 1),
+            "batched_speedup_vs_sequential": round((t_seq / 8) / (t_ntd / n), 2),
+            "core_fits": len(jobs), "cp_iters": B["cp_iters"],
+            "core_fits_ms": round(t_cp * 1e3, 1), "core_fits_per_s": round(len(jobs) / t_cp, 1),
+            "mean_tucker_rel_err": round(float(sum(errs) / n), 6),
+            "mean_core_fit_rel_err": round(float(cp_errs.mean().item()), 6)}
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -514,6 +564,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_differentiation_form:
         import torch
         result["differentiation_form"] = differentiation_form(torch.device("cuda", 0))
+    if rank == 0 and world == 1 and not args.no_batching_form:
+        import torch
+        result["batching_form"] = batching_form(torch.device("cuda", 0))
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             X64, F0, G0, _ = problem

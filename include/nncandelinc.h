@@ -96,6 +96,34 @@ int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precisi
             const nnc_opts* opts, void* const* F, void* G, double* rel_err_trace,
             double* rel_err, void* stream);
 
+/* One nnTD problem of a batch (see ntd_fit for the meaning of each field). */
+typedef struct {
+  const void* X;        /* device, C order, d = 3 modes dims[0..2]                 */
+  int d;
+  int64_t dims[4];
+  int m[4];
+  void* F[4];           /* device F^(n), dims[n] x m[n]: initial in, fitted out     */
+  void* G;              /* device core, m[0] x m[1] x m[2]: initial in, fitted out  */
+  double* trace;        /* device, opts->iters doubles, or NULL                     */
+} ntd_job;
+
+/*
+ * ntd_fit_batched - many independent ntd_fit problems of uneven shapes (the
+ * batching form: several tensors, several multiranks or restarts). The jobs
+ * are spread over `concurrency` host workers (0: 8, at most 32), each with a
+ * CUDA stream of its own that first waits for the work already queued on
+ * `stream`, so small problems overlap on the GPU; every job runs exactly the
+ * kernels of ntd_fit and gives the same bits. Returns when all jobs are done.
+ *
+ *  jobs       host array of n_jobs descriptors
+ *  rel_errs   host, n_jobs doubles (NaN for a failed job), or NULL
+ *  statuses   host, n_jobs status codes, or NULL
+ * Errors: the first failing job's status (nnc_last_error_detail names it);
+ * INVALID_ARG for bad arguments of the call itself.
+ */
+int ntd_fit_batched(int n_jobs, const ntd_job* jobs, int precision, const nnc_opts* opts,
+                    int concurrency, double* rel_errs, int* statuses, void* stream);
+
 /*
  * nncp_core_fit - nonnegative CP decomposition G ~ I x_1 B^(1) ... x_d B^(d)
  * of a core (Alg. 1, step 2; model Eq. npd). opts->iters sweeps over

@@ -4,6 +4,8 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "kernels.cuh"
@@ -63,16 +65,18 @@ cudaError_t raise_smem_limit(const void* kernel, size_t bytes) {
 }
 
 int device_sm_count() {
-  static int cache[64] = {0};
+  static std::atomic<int> cache[64];  // 0 until first read (zero-initialised static)
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
-  if (cache[dev] == 0) {
+  int c = cache[dev].load(std::memory_order_relaxed);
+  if (c == 0) {
     int n = 0;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
       n = 148;
-    cache[dev] = n;
+    cache[dev].store(n, std::memory_order_relaxed);
+    c = n;
   }
-  return cache[dev];
+  return c;
 }
 
 namespace {
@@ -213,6 +217,60 @@ int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precisi
     default:
       return NNC_ERR_INVALID_ARG;
   }
+}
+
+int ntd_fit_batched(int n_jobs, const ntd_job* jobs, int precision, const nnc_opts* opts,
+                    int concurrency, double* rel_errs, int* statuses, void* stream) {
+  g_detail.clear();
+  NNC_TRY(check_opts(opts));
+  if (n_jobs < 0 || (n_jobs > 0 && jobs == nullptr)) return NNC_ERR_INVALID_ARG;
+  if (n_jobs == 0) return NNC_OK;
+  int workers = concurrency <= 0 ? 8 : (concurrency > 32 ? 32 : concurrency);
+  if (workers > n_jobs) workers = n_jobs;
+  int dev = 0;
+  NNC_CUDA_TRY(cudaGetDevice(&dev));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t fork = nullptr;
+  NNC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  NNC_CUDA_TRY(cudaEventRecord(fork, s));
+  std::vector<int> st(n_jobs, NNC_OK);
+  std::vector<double> errs(n_jobs, 0.0);
+  std::vector<std::string> detail(n_jobs);
+  std::atomic<int> next{0};
+  std::vector<std::thread> pool;
+  pool.reserve(workers);
+  for (int w = 0; w < workers; ++w) {
+    pool.emplace_back([&]() {
+      cudaStream_t ws = nullptr;
+      if (cudaSetDevice(dev) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamWaitEvent(ws, fork, 0) != cudaSuccess) {
+        for (int j = next.fetch_add(1); j < n_jobs; j = next.fetch_add(1)) st[j] = NNC_ERR_CUDA;
+        if (ws) cudaStreamDestroy(ws);
+        return;
+      }
+      for (int j = next.fetch_add(1); j < n_jobs; j = next.fetch_add(1)) {
+        const ntd_job& jb = jobs[j];
+        st[j] = ntd_fit(jb.X, jb.d, jb.dims, jb.m, precision, opts, jb.F, jb.G, jb.trace,
+                        &errs[j], ws);
+        if (st[j] != NNC_OK) detail[j] = nnc_last_error_detail();
+      }
+      cudaStreamSynchronize(ws);
+      cudaStreamDestroy(ws);
+    });
+  }
+  for (auto& t : pool) t.join();
+  cudaEventDestroy(fork);
+  int first = NNC_OK;
+  for (int j = 0; j < n_jobs; ++j) {
+    if (statuses) statuses[j] = st[j];
+    if (rel_errs) rel_errs[j] = st[j] == NNC_OK ? errs[j] : NAN;
+    if (st[j] != NNC_OK && first == NNC_OK) {
+      first = st[j];
+      g_detail = "job " + std::to_string(j) + ": " + detail[j];
+    }
+  }
+  return first;
 }
 
 int nncp_core_fit(const void* G, int d, const int* m, int r, int precision, const nnc_opts* opts,

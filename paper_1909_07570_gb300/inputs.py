@@ -130,3 +130,43 @@ def small_problem(dims, planted_rank, m, r, seed, dist="uniform", zero_frac=0.0,
     w = Workload("custom", tuple(dims), planted_rank, tuple(m), r, 1, 1, "f64",
                  dist=dist, zero_frac=zero_frac, noise=noise, seed=seed)
     return make_problem(w)
+
+
+# The batching workload: many planted tensors of uneven shapes (each mode
+# length drawn from [32, 256]), planted rank r from [2, 8], multirank m = 2r,
+# 1 % noise; each core then fitted at CP ranks 2..8 with 8 restarts. It stands
+# in for the paper's many-small-tensor experiment (Sec. 4.3, 1000 planted
+# tensors) at the batch sizes of the task's configuration.
+BATCH = {"name": "batch64_uneven_32to256_m2r", "n_tensors": 64, "mode_range": (32, 256),
+         "rank_range": (2, 8), "noise": 0.01, "seed": 1003, "iters": 500, "cp_iters": 500,
+         "cp_ranks": tuple(range(2, 9)), "restarts": 8}
+
+
+def batch_problems(n_tensors=None, seed=None):
+    """The batching workload as a list of dicts {X (float64), dims, r, m, F0, G0}."""
+    n = BATCH["n_tensors"] if n_tensors is None else n_tensors
+    seed = BATCH["seed"] if seed is None else seed
+    rng = np.random.default_rng(seed)
+    lo, hi = BATCH["mode_range"]
+    rlo, rhi = BATCH["rank_range"]
+    out = []
+    for b in range(n):
+        dims = tuple(int(v) for v in rng.integers(lo, hi + 1, size=3))
+        r = int(rng.integers(rlo, rhi + 1))
+        m = (2 * r,) * 3
+        X, _ = planted_tensor(dims, r, seed + 17 * (b + 1), noise=BATCH["noise"])
+        F0, G0 = initial_tucker(dims, m, seed + 7919 + b)
+        out.append({"X": X, "dims": dims, "r": r, "m": m, "F0": F0, "G0": G0})
+    return out
+
+
+def batch_core_inits(m, tensor_index, seed=None):
+    """Initial B's of every (CP rank, restart) core fit of one batch tensor:
+    a list of (rank, restart, [B^(n)])."""
+    seed = BATCH["seed"] if seed is None else seed
+    out = []
+    for rk in BATCH["cp_ranks"]:
+        for rs in range(BATCH["restarts"]):
+            out.append((rk, rs, initial_cp(m, rk, seed + 104729 + 1009 * tensor_index
+                                           + 31 * rk + rs)))
+    return out

@@ -22,7 +22,7 @@ _STATUS = {
 }
 
 # Every symbol include/nncandelinc.h declares.
-EXPORTED = ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched",
+EXPORTED = ("ntd_fit", "ntd_fit_batched", "nncp_core_fit", "nncp_core_fit_batched",
             "nncp_core_fit_batched_noalloc", "nnc_mode_product", "candelinc_lift",
             "recon_residual", "candelinc_lifted_grad", "candelinc_pg_fit",
             "nncp_tensor_fit", "nmf_fit", "candelinc_alg2",
@@ -38,6 +38,12 @@ class NncError(RuntimeError):
 
 class nnc_opts(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("refine_iters", ctypes.c_int), ("eps", ctypes.c_double)]
+
+
+class ntd_job(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("d", ctypes.c_int), ("dims", ctypes.c_int64 * 4),
+                ("m", ctypes.c_int * 4), ("F", ctypes.c_void_p * 4), ("G", ctypes.c_void_p),
+                ("trace", ctypes.c_void_p)]
 
 
 class nncp_job(ctypes.Structure):
@@ -78,6 +84,8 @@ def load(path: str | None = None):
                                           vpp, vpp, vpp, vpp, dp, vp]
     lib.candelinc_pg_fit.argtypes = [vp, ctypes.c_int, i64p, ip, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, vpp, vpp, vp, dp, vp]
+    lib.ntd_fit_batched.argtypes = [ctypes.c_int, ctypes.POINTER(ntd_job), ctypes.c_int,
+                                    ctypes.POINTER(nnc_opts), ctypes.c_int, dp, ip, vp]
     lib.nncp_tensor_fit.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(nnc_opts), vpp, vp, dp, vp]
     lib.nmf_fit.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -88,7 +96,7 @@ def load(path: str | None = None):
     for fn in ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched",
                "nncp_core_fit_batched_noalloc", "nnc_mode_product", "candelinc_lift", "recon_residual",
                "candelinc_lifted_grad", "candelinc_pg_fit", "nncp_tensor_fit", "nmf_fit",
-               "candelinc_alg2"):
+               "candelinc_alg2", "ntd_fit_batched"):
         getattr(lib, fn).restype = ctypes.c_int
     lib.nnc_status_string.argtypes = [ctypes.c_int]
     lib.nnc_status_string.restype = ctypes.c_char_p
@@ -169,6 +177,41 @@ def ntd_fit(X, F, G, iters, precision=None, eps=1e-12, refine_iters=0, trace=Tru
                         ctypes.byref(err) if rel_err else None, _stream(stream))
     _check("ntd_fit", st)
     return (err.value if rel_err else None), (tr[:iters] if trace else None)
+
+
+def ntd_fit_batched(problems, iters, precision=None, eps=1e-12, refine_iters=0, concurrency=0,
+                    trace=True, stream=None):
+    """Many nnTD problems of uneven shapes, in place: problems is a list of
+    (X, F list, G). Returns (relative errors, device FP64 traces or None,
+    statuses)."""
+    if not problems:
+        return [], [], []
+    code, dtype = _precision(problems[0][0], precision)
+    n = len(problems)
+    jobs = (ntd_job * n)()
+    traces = []
+    for j, (X, F, G) in enumerate(problems):
+        _require(X, dtype, f"X[{j}]")
+        _require(G, dtype, f"G[{j}]")
+        for k, f in enumerate(F):
+            _require(f, dtype, f"F[{j}][{k}]")
+        jobs[j].X = X.data_ptr()
+        jobs[j].d = X.dim()
+        for k in range(X.dim()):
+            jobs[j].dims[k] = X.shape[k]
+            jobs[j].m[k] = F[k].shape[1]
+            jobs[j].F[k] = F[k].data_ptr()
+        jobs[j].G = G.data_ptr()
+        tr = torch.empty(max(iters, 1), dtype=torch.float64, device=X.device) if trace else None
+        jobs[j].trace = tr.data_ptr() if trace else None
+        traces.append(tr[:iters] if trace else None)
+    opts = nnc_opts(int(iters), int(refine_iters), float(eps))
+    errs = (ctypes.c_double * n)()
+    sts = (ctypes.c_int * n)()
+    st = load().ntd_fit_batched(n, jobs, code, ctypes.byref(opts), int(concurrency), errs, sts,
+                                _stream(stream))
+    _check("ntd_fit_batched", st)
+    return list(errs), traces, list(sts)
 
 
 def nncp_core_fit(G, B, iters, precision=None, eps=1e-12, rel_err=True, stream=None):
