@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-precision-form", action="store_true")
     p.add_argument("--no-differentiation-form", action="store_true")
     p.add_argument("--no-batching-form", action="store_true")
+    p.add_argument("--no-multirank-study", action="store_true")
     return p.parse_args()
 
 
@@ -504,6 +505,25 @@ def batching_form(dev):
             "mean_core_fit_rel_err": round(float(cp_errs.mean().item()), 6)}
 
 
+def multirank_study(dev, starts=1000, iters=5000):
+    """The multirank study of Sec. 4.3 on Ex. "equal": Alg. 1 and Alg. 2 from
+    `starts` random starts at multiranks [3,3,3], [3,4,4], [4,4,4], [5,5,5],
+    `iters` sweeps per stage (the paper's 5000), all starts of a stage in one
+    launch. Reports wall time and the distribution summaries."""
+    import torch
+
+    from paper_1909_07570_gb300 import study
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = study.run(starts=starts, iters=iters, device=str(dev))
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    fits = 2 * len(res) // 2 * starts
+    return {"tensor": "Ex. equal (4x4x4, rank 4)", "starts": starts, "iters": iters,
+            "seconds": round(t, 2), "decompositions_per_s": round(fits / t, 1),
+            "summary": study.summary(res)}
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -567,6 +587,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_batching_form:
         import torch
         result["batching_form"] = batching_form(torch.device("cuda", 0))
+    if rank == 0 and world == 1 and not args.no_multirank_study:
+        import torch
+        result["multirank_study"] = multirank_study(torch.device("cuda", 0))
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             X64, F0, G0, _ = problem

@@ -125,6 +125,53 @@ int ntd_fit_batched(int n_jobs, const ntd_job* jobs, int precision, const nnc_op
                     int concurrency, double* rel_errs, int* statuses, void* stream);
 
 /*
+ * Batched fits of tiny problems, one thread block per problem with all its
+ * data in shared memory: many random starts of Alg. 1 and Alg. 2 on a small
+ * tensor (the multirank study of Sec. 4.3 on Ex. "equal": a 4 x 4 x 4 tensor,
+ * several multiranks, many starts). Pointers inside the descriptors are
+ * device pointers; the descriptor arrays are host arrays copied by the call.
+ * rel_errs: device, n_jobs doubles (final relative error of each job), or
+ * NULL. Same update rules as ntd_fit and nmf_fit. Errors: INVALID_ARG,
+ * UNSUPPORTED (a job too large for shared memory), CUDA, ALLOC. No host
+ * synchronisation.
+ */
+typedef struct {
+  const void* X;        /* dims[0] x dims[1] x dims[2], C order                    */
+  int dims[3];
+  int m[3];             /* 1 <= m[n] <= 32                                        */
+  void* F[3];           /* dims[n] x m[n]: initial in, fitted out                  */
+  void* G;              /* m[0] x m[1] x m[2]: initial in, fitted out              */
+} ntd_small_job;
+
+typedef struct {
+  const void* A;        /* N x r (read only)                                       */
+  int N, r, m;
+  void* F;              /* N x m: initial in, fitted out                           */
+  void* B;              /* m x r: initial in, fitted out                           */
+} nmf_job;
+
+typedef struct {
+  const void* X;        /* dims[0] x dims[1] x dims[2]                             */
+  int dims[3];
+  int m[3];
+  int r;
+  const void* F[3];     /* dims[n] x m[n]                                          */
+  const void* B[3];     /* m[n] x r                                                */
+} lifted_job;
+
+/* nnTD (Alg. 1, step 1) of every job, opts->iters sweeps; rel_errs gets
+ * ||X - G x_k F^(k)|| / ||X||. */
+int ntd_fit_small_batched(int n_jobs, const ntd_small_job* jobs, int precision,
+                          const nnc_opts* opts, double* rel_errs, void* stream);
+/* NMF A ~ F B (Alg. 2, step 2) of every job; rel_errs gets ||A - F B|| / ||A||. */
+int nmf_fit_batched(int n_jobs, const nmf_job* jobs, int precision, const nnc_opts* opts,
+                    double* rel_errs, void* stream);
+/* rel_errs[j] = ||X - I x_k F^(k) B^(k)|| / ||X|| of every job (the
+ * nnCANDELINC objective, Eq. nnCANDELINC, of a fitted pair). */
+int lifted_rel_err_batched(int n_jobs, const lifted_job* jobs, int precision, double* rel_errs,
+                           void* stream);
+
+/*
  * nncp_core_fit - nonnegative CP decomposition G ~ I x_1 B^(1) ... x_d B^(d)
  * of a core (Alg. 1, step 2; model Eq. npd). opts->iters sweeps over
  * B^(1), ..., B^(d) of

@@ -13,6 +13,7 @@
 #include "nncp.cuh"
 #include "ntd.cuh"
 #include "residual.cuh"
+#include "small_batched.cuh"
 #include "tc_ttm.cuh"
 
 namespace nnc {
@@ -271,6 +272,46 @@ int ntd_fit_batched(int n_jobs, const ntd_job* jobs, int precision, const nnc_op
     }
   }
   return first;
+}
+
+int ntd_fit_small_batched(int n_jobs, const ntd_small_job* jobs, int precision,
+                          const nnc_opts* opts, double* rel_errs, void* stream) {
+  g_detail.clear();
+  NNC_TRY(check_opts(opts));
+  if (n_jobs < 0 || (n_jobs > 0 && jobs == nullptr)) return NNC_ERR_INVALID_ARG;
+  if (n_jobs == 0) return NNC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == NNC_FP64)
+    return ntd_small_batched<double>(n_jobs, jobs, opts->iters, opts->eps, rel_errs, s);
+  if (precision == NNC_FP32 || precision == NNC_FP32_SIMT)
+    return ntd_small_batched<float>(n_jobs, jobs, opts->iters, opts->eps, rel_errs, s);
+  return precision == NNC_BF16_REFINE ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
+}
+
+int nmf_fit_batched(int n_jobs, const nmf_job* jobs, int precision, const nnc_opts* opts,
+                    double* rel_errs, void* stream) {
+  g_detail.clear();
+  NNC_TRY(check_opts(opts));
+  if (n_jobs < 0 || (n_jobs > 0 && jobs == nullptr)) return NNC_ERR_INVALID_ARG;
+  if (n_jobs == 0) return NNC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == NNC_FP64)
+    return nmf_small_batched<double>(n_jobs, jobs, opts->iters, opts->eps, rel_errs, s);
+  if (precision == NNC_FP32 || precision == NNC_FP32_SIMT)
+    return nmf_small_batched<float>(n_jobs, jobs, opts->iters, opts->eps, rel_errs, s);
+  return precision == NNC_BF16_REFINE ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
+}
+
+int lifted_rel_err_batched(int n_jobs, const lifted_job* jobs, int precision, double* rel_errs,
+                           void* stream) {
+  g_detail.clear();
+  if (n_jobs < 0 || (n_jobs > 0 && jobs == nullptr)) return NNC_ERR_INVALID_ARG;
+  if (n_jobs == 0) return NNC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == NNC_FP64) return lifted_small_batched<double>(n_jobs, jobs, rel_errs, s);
+  if (precision == NNC_FP32 || precision == NNC_FP32_SIMT)
+    return lifted_small_batched<float>(n_jobs, jobs, rel_errs, s);
+  return precision == NNC_BF16_REFINE ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
 }
 
 int nncp_core_fit(const void* G, int d, const int* m, int r, int precision, const nnc_opts* opts,

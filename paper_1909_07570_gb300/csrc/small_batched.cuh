@@ -1,0 +1,17 @@
+// Batched fits of tiny problems, one block per problem (small_batched.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace nnc {
+
+template <typename T>
+int ntd_small_batched(int n_jobs, const ntd_small_job* jobs, int iters, double eps,
+                      double* rel_errs, cudaStream_t s);
+template <typename T>
+int nmf_small_batched(int n_jobs, const nmf_job* jobs, int iters, double eps, double* rel_errs,
+                      cudaStream_t s);
+template <typename T>
+int lifted_small_batched(int n_jobs, const lifted_job* jobs, double* rel_errs, cudaStream_t s);
+
+}  // namespace nnc

@@ -170,3 +170,31 @@ def batch_core_inits(m, tensor_index, seed=None):
             out.append((rk, rs, initial_cp(m, rk, seed + 104729 + 1009 * tensor_index
                                            + 31 * rk + rs)))
     return out
+
+
+def example_equal_factors():
+    """The factors A^(1), A^(2), A^(3) of Ex. "equal" (Sec. 3.1) as printed: X =
+    I x_1 A^(1) x_2 A^(2) x_3 A^(3) is 4 x 4 x 4 with nonnegative rank 4 and
+    nonnegative multirank (3, 4, 4); the tensor of the multirank study (Sec. 4.3)."""
+    A1 = np.array([[1, 1, 0, 0], [1, 0, 1, 0], [0, 1, 0, 1], [0, 0, 1, 1]], dtype=np.float64)
+    A2 = np.triu(np.ones((4, 4)))
+    A3 = np.triu(np.ones((4, 4)))
+    return [A1, A2, A3]
+
+
+def study_inits(dims, m, r, starts, seed):
+    """Random starts of the multirank study, i.i.d. U(0, 1]: per start the
+    Tucker inits (F, G) and core CP init B of Alg. 1, and the CP init A and
+    NMF inits (F, B) of Alg. 2."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(starts):
+        out.append({
+            "F": [1.0 - rng.random((n, k)) for n, k in zip(dims, m)],
+            "G": 1.0 - rng.random(tuple(m)),
+            "B": [1.0 - rng.random((k, r)) for k in m],
+            "A": [1.0 - rng.random((n, r)) for n in dims],
+            "F2": [1.0 - rng.random((n, k)) for n, k in zip(dims, m)],
+            "B2": [1.0 - rng.random((k, r)) for k in m],
+        })
+    return out

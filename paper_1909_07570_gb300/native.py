@@ -22,7 +22,8 @@ _STATUS = {
 }
 
 # Every symbol include/nncandelinc.h declares.
-EXPORTED = ("ntd_fit", "ntd_fit_batched", "nncp_core_fit", "nncp_core_fit_batched",
+EXPORTED = ("ntd_fit", "ntd_fit_batched", "ntd_fit_small_batched", "nmf_fit_batched",
+            "lifted_rel_err_batched", "nncp_core_fit", "nncp_core_fit_batched",
             "nncp_core_fit_batched_noalloc", "nnc_mode_product", "candelinc_lift",
             "recon_residual", "candelinc_lifted_grad", "candelinc_pg_fit",
             "nncp_tensor_fit", "nmf_fit", "candelinc_alg2",
@@ -44,6 +45,21 @@ class ntd_job(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("d", ctypes.c_int), ("dims", ctypes.c_int64 * 4),
                 ("m", ctypes.c_int * 4), ("F", ctypes.c_void_p * 4), ("G", ctypes.c_void_p),
                 ("trace", ctypes.c_void_p)]
+
+
+class ntd_small_job(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("dims", ctypes.c_int * 3), ("m", ctypes.c_int * 3),
+                ("F", ctypes.c_void_p * 3), ("G", ctypes.c_void_p)]
+
+
+class nmf_job(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("N", ctypes.c_int), ("r", ctypes.c_int),
+                ("m", ctypes.c_int), ("F", ctypes.c_void_p), ("B", ctypes.c_void_p)]
+
+
+class lifted_job(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("dims", ctypes.c_int * 3), ("m", ctypes.c_int * 3),
+                ("r", ctypes.c_int), ("F", ctypes.c_void_p * 3), ("B", ctypes.c_void_p * 3)]
 
 
 class nncp_job(ctypes.Structure):
@@ -86,6 +102,12 @@ def load(path: str | None = None):
                                      ctypes.c_int, vpp, vpp, vp, dp, vp]
     lib.ntd_fit_batched.argtypes = [ctypes.c_int, ctypes.POINTER(ntd_job), ctypes.c_int,
                                     ctypes.POINTER(nnc_opts), ctypes.c_int, dp, ip, vp]
+    lib.ntd_fit_small_batched.argtypes = [ctypes.c_int, ctypes.POINTER(ntd_small_job), ctypes.c_int,
+                                          ctypes.POINTER(nnc_opts), vp, vp]
+    lib.nmf_fit_batched.argtypes = [ctypes.c_int, ctypes.POINTER(nmf_job), ctypes.c_int,
+                                    ctypes.POINTER(nnc_opts), vp, vp]
+    lib.lifted_rel_err_batched.argtypes = [ctypes.c_int, ctypes.POINTER(lifted_job), ctypes.c_int,
+                                           vp, vp]
     lib.nncp_tensor_fit.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(nnc_opts), vpp, vp, dp, vp]
     lib.nmf_fit.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -96,7 +118,8 @@ def load(path: str | None = None):
     for fn in ("ntd_fit", "nncp_core_fit", "nncp_core_fit_batched",
                "nncp_core_fit_batched_noalloc", "nnc_mode_product", "candelinc_lift", "recon_residual",
                "candelinc_lifted_grad", "candelinc_pg_fit", "nncp_tensor_fit", "nmf_fit",
-               "candelinc_alg2", "ntd_fit_batched"):
+               "candelinc_alg2", "ntd_fit_batched", "ntd_fit_small_batched", "nmf_fit_batched",
+               "lifted_rel_err_batched"):
         getattr(lib, fn).restype = ctypes.c_int
     lib.nnc_status_string.argtypes = [ctypes.c_int]
     lib.nnc_status_string.restype = ctypes.c_char_p
@@ -212,6 +235,68 @@ def ntd_fit_batched(problems, iters, precision=None, eps=1e-12, refine_iters=0, 
                                 _stream(stream))
     _check("ntd_fit_batched", st)
     return list(errs), traces, list(sts)
+
+
+def ntd_fit_small_batched(problems, iters, precision=None, eps=1e-12, stream=None):
+    """nnTD of many tiny 3-way tensors, one block each, in place: problems is a
+    list of (X, F list, G). Returns a device FP64 tensor of relative errors."""
+    code, dtype = _precision(problems[0][0], precision)
+    n = len(problems)
+    jobs = (ntd_small_job * n)()
+    for j, (X, F, G) in enumerate(problems):
+        _require(X, dtype, f"X[{j}]")
+        _require(G, dtype, f"G[{j}]")
+        jobs[j].X = X.data_ptr()
+        for k in range(3):
+            _require(F[k], dtype, f"F[{j}][{k}]")
+            jobs[j].dims[k] = X.shape[k]
+            jobs[j].m[k] = F[k].shape[1]
+            jobs[j].F[k] = F[k].data_ptr()
+        jobs[j].G = G.data_ptr()
+    errs = torch.empty(n, dtype=torch.float64, device=problems[0][0].device)
+    opts = nnc_opts(int(iters), 0, float(eps))
+    st = load().ntd_fit_small_batched(n, jobs, code, ctypes.byref(opts), _ptr(errs), _stream(stream))
+    _check("ntd_fit_small_batched", st)
+    return errs
+
+
+def nmf_fit_batched(problems, iters, precision=None, eps=1e-12, stream=None):
+    """Many small NMFs A ~ F B in place: problems is a list of (A, F, B).
+    Returns a device FP64 tensor of relative errors."""
+    code, dtype = _precision(problems[0][0], precision)
+    n = len(problems)
+    jobs = (nmf_job * n)()
+    for j, (A, F, B) in enumerate(problems):
+        for name, t in (("A", A), ("F", F), ("B", B)):
+            _require(t, dtype, f"{name}[{j}]")
+        jobs[j].A, jobs[j].F, jobs[j].B = A.data_ptr(), F.data_ptr(), B.data_ptr()
+        jobs[j].N, jobs[j].r, jobs[j].m = A.shape[0], A.shape[1], F.shape[1]
+    errs = torch.empty(n, dtype=torch.float64, device=problems[0][0].device)
+    opts = nnc_opts(int(iters), 0, float(eps))
+    st = load().nmf_fit_batched(n, jobs, code, ctypes.byref(opts), _ptr(errs), _stream(stream))
+    _check("nmf_fit_batched", st)
+    return errs
+
+
+def lifted_rel_err_batched(problems, precision=None, stream=None):
+    """||X - I x_k F^(k) B^(k)|| / ||X|| for many small (X, F list, B list)."""
+    code, dtype = _precision(problems[0][0], precision)
+    n = len(problems)
+    jobs = (lifted_job * n)()
+    for j, (X, F, B) in enumerate(problems):
+        _require(X, dtype, f"X[{j}]")
+        jobs[j].X = X.data_ptr()
+        jobs[j].r = B[0].shape[1]
+        for k in range(3):
+            _require(F[k], dtype, f"F[{j}][{k}]")
+            _require(B[k], dtype, f"B[{j}][{k}]")
+            jobs[j].dims[k] = X.shape[k]
+            jobs[j].m[k] = F[k].shape[1]
+            jobs[j].F[k], jobs[j].B[k] = F[k].data_ptr(), B[k].data_ptr()
+    errs = torch.empty(n, dtype=torch.float64, device=problems[0][0].device)
+    st = load().lifted_rel_err_batched(n, jobs, code, _ptr(errs), _stream(stream))
+    _check("lifted_rel_err_batched", st)
+    return errs
 
 
 def nncp_core_fit(G, B, iters, precision=None, eps=1e-12, rel_err=True, stream=None):

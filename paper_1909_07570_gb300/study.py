@@ -1,0 +1,92 @@
+"""The multirank study of Sec. 4.3 on the tensor of Ex. "equal": both
+nnCANDELINC algorithms from many random starts at several assumed
+multiranks, every fit on the GPU in batched launches (one thread block per
+start):
+
+  Alg. 1: nnTD (ntd_fit_small_batched), nnCPD of each fitted core
+          (nncp_core_fit_batched), relative error of the lifted model;
+  Alg. 2: nnCPD of X itself (nncp_core_fit_batched with X as the tensor),
+          NMF of every CP factor (nmf_fit_batched), relative error of the
+          lifted model.
+
+The congruence against the planted factors (product of the cosines per
+component, averaged over components under the best permutation, Sec. 4.1) is
+a score of the results, computed on the host.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import torch
+
+from . import inputs, native
+
+
+def mean_congruence(A, A_true):
+    """Mean over components of prod_n cos(a_n, a_true_n), best permutation."""
+    r = A_true[0].shape[1]
+    C = np.ones((r, A[0].shape[1]))
+    for a, t in zip(A, A_true):
+        na = np.linalg.norm(a, axis=0)
+        nt = np.linalg.norm(t, axis=0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            cos = (t.T @ a) / np.outer(nt, na)
+        C = C * np.nan_to_num(cos)
+    best = 0.0
+    for perm in itertools.permutations(range(r)):
+        best = max(best, float(np.mean(C[np.arange(r), perm])))
+    return best
+
+
+def run(multiranks=((3, 3, 3), (3, 4, 4), (4, 4, 4), (5, 5, 5)), starts=1000, iters=500,
+        seed=2024, device="cuda"):
+    """Returns {(alg, multirank): {"rel_err": array, "congruence": array}}."""
+    dev = torch.device(device)
+    A_true = inputs.example_equal_factors()
+    dims, r = (4, 4, 4), 4
+    Xh = np.einsum("iq,jq,kq->ijk", *A_true)
+    X = torch.tensor(Xh, device=dev)
+    out = {}
+    def stack(arrs):  # one contiguous device tensor; row i is start i's array
+        return torch.tensor(np.stack(arrs), device=dev)
+
+    def congruences(Fs, Bs):
+        A = [np.einsum("snm,smr->snr", f.cpu().numpy(), b.cpu().numpy()) for f, b in zip(Fs, Bs)]
+        return np.array([mean_congruence([a[i] for a in A], A_true) for i in range(starts)])
+
+    for mi, m in enumerate(multiranks):
+        inits = inputs.study_inits(dims, m, r, starts, seed + 101 * mi)
+        # Alg. 1
+        F = [stack([s["F"][k] for s in inits]) for k in range(3)]
+        G = stack([s["G"] for s in inits])
+        B = [stack([s["B"][k] for s in inits]) for k in range(3)]
+        native.ntd_fit_small_batched([(X, [f[i] for f in F], G[i]) for i in range(starts)], iters)
+        native.nncp_core_fit_batched([(G[i], [b[i] for b in B]) for i in range(starts)], iters)
+        e1 = native.lifted_rel_err_batched(
+            [(X, [f[i] for f in F], [b[i] for b in B]) for i in range(starts)]).cpu().numpy()
+        out[("alg1", m)] = {"rel_err": e1, "congruence": congruences(F, B)}
+        # Alg. 2
+        A = [stack([s["A"][k] for s in inits]) for k in range(3)]
+        F2 = [stack([s["F2"][k] for s in inits]) for k in range(3)]
+        B2 = [stack([s["B2"][k] for s in inits]) for k in range(3)]
+        native.nncp_core_fit_batched([(X, [a[i] for a in A]) for i in range(starts)], iters)
+        native.nmf_fit_batched([(A[k][i], F2[k][i], B2[k][i]) for i in range(starts)
+                                for k in range(3)], iters)
+        e2 = native.lifted_rel_err_batched(
+            [(X, [f[i] for f in F2], [b[i] for b in B2]) for i in range(starts)]).cpu().numpy()
+        out[("alg2", m)] = {"rel_err": e2, "congruence": congruences(F2, B2)}
+    return out
+
+
+def summary(res):
+    """Medians, quartiles and the share of starts with relative error < 1e-3."""
+    rows = {}
+    for (alg, m), v in res.items():
+        e, c = v["rel_err"], v["congruence"]
+        rows[f"{alg}_{'x'.join(map(str, m))}"] = {
+            "rel_err_median": float(np.median(e)), "rel_err_q25": float(np.quantile(e, 0.25)),
+            "rel_err_q75": float(np.quantile(e, 0.75)),
+            "share_rel_err_below_1e-3": float(np.mean(e < 1e-3)),
+            "congruence_mean": float(np.mean(c)), "congruence_std": float(np.std(c))}
+    return rows
