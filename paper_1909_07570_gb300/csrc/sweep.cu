@@ -185,25 +185,33 @@ __device__ __noinline__ void cp_flat(T* dst, const T* __restrict__ src, int64_t 
 // interleaved subsets of t (split-K inside the block, so every thread works
 // even for small mu, mc); the partial tiles are added in group order. A and B
 // are staged by cp.async in chunks of kch rows, two chunks in flight; `stage`
-// holds gemm_stage_elems of the dimensions kch was chosen for.
+// holds gemm_stage_elems of the dimensions and length kch was chosen for.
 __host__ __device__ inline int gemm_tiles(int mu, int mc) { return (r4(mu) / 4) * (r4(mc) / 4); }
 __host__ __device__ inline int gemm_groups(int mu, int mc) {
   const int g = kThreads / gemm_tiles(mu, mc);
   return g > 1 ? g : 1;
 }
-// Rows per chunk: two chunks of both operands take at most 96 KB (FP32) or
-// 48 KB (FP64); a multiple of 8. FP32 stages a contraction of up
-// to 256 rows in one round trip for m <= 24.
-__host__ __device__ inline int gemm_kch(int mu, int mc, int elem) {
-  const int budget = elem > 4 ? 3 * 1024 : 12 * 1024;  // elements of one chunk of A and B
+// Rows per chunk: one chunk of A and B takes at most 64 KB (FP32) or 24 KB
+// (FP64), a multiple of 8, and no more than the contraction length needs; a
+// contraction of up to 256 rows (FP32, m <= 32) is then staged in one round
+// trip into a single buffer, which keeps enough blocks resident per SM.
+__host__ __device__ inline int gemm_kch(int mu, int mc, int elem, int len) {
+  const int budget = elem > 4 ? 3 * 1024 : 16 * 1024;  // elements of one chunk of A and B
   int k = budget / (r4(mu) + r4(mc));
   k = k > 256 ? 256 : k;
+  const int need = (len + 7) & ~7;
+  k = k > need ? need : k;
   k &= ~7;
   return k < 8 ? 8 : k;
 }
-__host__ __device__ inline size_t gemm_stage_elems(int mu, int mc, int elem) {
-  const size_t st = (size_t)2 * gemm_kch(mu, mc, elem) * (r4(mu) + r4(mc));
-  const size_t red = (size_t)gemm_groups(mu, mc) * mu * mc;
+// Staging elements for gemm_tn_block with these dimensions: one buffer when a
+// single chunk covers the contraction, two otherwise; at least the partial
+// tiles of the group reduction (at most 16 per thread).
+__host__ __device__ inline size_t gemm_stage_elems(int mu, int mc, int elem, int len) {
+  const int kch = gemm_kch(mu, mc, elem, len);
+  const size_t nbuf = len > kch ? 2 : 1;
+  const size_t st = nbuf * kch * (r4(mu) + r4(mc));
+  const size_t red = (size_t)16 * kThreads;
   return al4(st > red ? st : red);
 }
 
@@ -217,7 +225,7 @@ __device__ __noinline__ void gemm_tn_block(const T* __restrict__ A, int64_t lda,
   const bool act = g < groups;
   const int u0 = (t / tq) * 4, c0 = (t % tq) * 4;
   T* As = stage;
-  T* Bs = stage + 2 * kch * mu4;
+  T* Bs = stage + (len > kch ? 2 : 1) * kch * mu4;
   const bool vecA = aligned16(A, lda, sizeof(T)), vecB = aligned16(B, ldb, sizeof(T));
   const int nch = (len + kch - 1) / kch;
   auto issue = [&](int c, int buf) {
@@ -330,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
   const int MU_ = a.mu, MC = a.mc, MV = a.mv, UC = MU_ * MC;
   const bool gsm = core_in_smem<T>((int64_t)MV * UC);
   T* stage = sm;
-  T* ys = stage + gemm_stage_elems(MU_, MC, (int)sizeof(T));
+  T* ys = stage + gemm_stage_elems(MU_, MC, (int)sizeof(T), a.len);
   T* hs = ys + al4(UC);
   T* fo = hs + al4(MV * MV);
   T* nm = fo + al4(MV);
@@ -344,7 +352,7 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
   if (gsm) cp_flat(gs, a.Gn, (int64_t)MV * UC);
   cp_commit();
   gemm_tn_block(a.Fc, MU_, MU_, a.P + r * a.prow, a.pstride, MC, a.len,
-                gemm_kch(MU_, MC, (int)sizeof(T)), ys, stage);
+                gemm_kch(MU_, MC, (int)sizeof(T), a.len), ys, stage);
 
   rows_dot(ys, gsm ? (const T*)gs : a.Gn, UC, MV, nm);
   __syncthreads();
@@ -367,8 +375,8 @@ __global__ void __launch_bounds__(kThreads) hmat_kernel(HArgs<T> a) {
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int U = a.mu, V = a.mv, P = a.mp, UV = U * V;
   const bool gsm = core_in_smem<T>((int64_t)P * UV);
-  const size_t st_u = a.fu ? gemm_stage_elems(U, U, (int)sizeof(T)) : 0;
-  const size_t st_v = a.fv ? gemm_stage_elems(V, V, (int)sizeof(T)) : 0;
+  const size_t st_u = a.fu ? gemm_stage_elems(U, U, (int)sizeof(T), (int)a.nu) : 0;
+  const size_t st_v = a.fv ? gemm_stage_elems(V, V, (int)sizeof(T), (int)a.nv) : 0;
   T* stage = sm;
   T* su = stage + (st_u > st_v ? st_u : st_v);
   T* sv = su + al4(U * U);
@@ -384,9 +392,11 @@ __global__ void __launch_bounds__(kThreads) hmat_kernel(HArgs<T> a) {
   else cp_flat(gp, a.Gn + (int64_t)p * UV, UV);
   cp_commit();
   if (a.fu)
-    gemm_tn_block(a.fu, U, U, a.fu, U, U, (int)a.nu, gemm_kch(U, U, (int)sizeof(T)), su, stage);
+    gemm_tn_block(a.fu, U, U, a.fu, U, U, (int)a.nu, gemm_kch(U, U, (int)sizeof(T), (int)a.nu),
+                  su, stage);
   if (a.fv)
-    gemm_tn_block(a.fv, V, V, a.fv, V, V, (int)a.nv, gemm_kch(V, V, (int)sizeof(T)), sv, stage);
+    gemm_tn_block(a.fv, V, V, a.fv, V, V, (int)a.nv, gemm_kch(V, V, (int)sizeof(T), (int)a.nv),
+                  sv, stage);
   if (!a.fu && !a.fv) {
     cp_wait<0>();
     __syncthreads();
@@ -420,10 +430,10 @@ __global__ void __launch_bounds__(kThreads) y3_kernel(const T* __restrict__ P1,
   const int ai = blockIdx.y, k0 = blockIdx.x * kY3Tile;
   const int ku = min(kY3Tile, N3 - k0);
   T* stage = sm;
-  T* cs = stage + gemm_stage_elems(kY3Tile, m2, (int)sizeof(T));
+  T* cs = stage + gemm_stage_elems(kY3Tile, m2, (int)sizeof(T), N2);
   // The chunk size is the one the staging was sized for (a full tile of 32).
   gemm_tn_block(P1 + (int64_t)ai * N2 * N3 + k0, N3, ku, F2, m2, m2, N2,
-                gemm_kch(kY3Tile, m2, (int)sizeof(T)), cs, stage);
+                gemm_kch(kY3Tile, m2, (int)sizeof(T), N2), cs, stage);
   T* y = Y3 + ((int64_t)ai * N3 + k0) * m2;
   for (int e = threadIdx.x; e < ku * m2; e += blockDim.x) y[e] = cs[e];
 }
@@ -501,8 +511,8 @@ __global__ void __launch_bounds__(kThreads) core_a_kernel(CoreArgs<T> a) {
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int m1 = a.m1, m2 = a.m2, m3 = a.m3;
   const int bc = m2 * m3;
-  const size_t st3 = gemm_stage_elems(m3, m3, (int)sizeof(T));
-  const size_t stm = gemm_stage_elems(m2, m3, (int)sizeof(T));
+  const size_t st3 = gemm_stage_elems(m3, m3, (int)sizeof(T), (int)a.n3);
+  const size_t stm = gemm_stage_elems(m2, m3, (int)sizeof(T), (int)a.n3);
   T* stage = sm;
   T* s2 = stage + (st3 > stm ? st3 : stm);  // m2 x m2
   T* s3 = s2 + al4(m2 * m2);                  // m3 x m3
@@ -516,10 +526,10 @@ __global__ void __launch_bounds__(kThreads) core_a_kernel(CoreArgs<T> a) {
   cp_flat(wa, a.W3 + off, bc);
   cp_flat(ga, a.G + off, bc);
   cp_commit();
-  gemm_tn_block(a.F3, m3, m3, a.F3, m3, m3, (int)a.n3, gemm_kch(m3, m3, (int)sizeof(T)), s3,
-                stage);
+  gemm_tn_block(a.F3, m3, m3, a.F3, m3, m3, (int)a.n3,
+                gemm_kch(m3, m3, (int)sizeof(T), (int)a.n3), s3, stage);
   gemm_tn_block(a.Y3 + (int64_t)aa * a.n3 * m2, m2, m2, a.F3, m3, m3, (int)a.n3,
-                gemm_kch(m2, m3, (int)sizeof(T)), ma, stage);
+                gemm_kch(m2, m3, (int)sizeof(T), (int)a.n3), ma, stage);
   if (aa == 0)
     for (int e = threadIdx.x; e < m3 * m3; e += blockDim.x) a.S3_out[e] = s3[e];
   for (int e = threadIdx.x; e < bc; e += blockDim.x) {
@@ -622,8 +632,8 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ F,
                                                         T* __restrict__ S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  T* c = sm + gemm_stage_elems(m, m, (int)sizeof(T));
-  gemm_tn_block(F, m, m, F, m, m, (int)N, gemm_kch(m, m, (int)sizeof(T)), c, sm);
+  T* c = sm + gemm_stage_elems(m, m, (int)sizeof(T), (int)N);
+  gemm_tn_block(F, m, m, F, m, m, (int)N, gemm_kch(m, m, (int)sizeof(T), (int)N), c, sm);
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) S[e] = c[e];
 }
 
@@ -646,7 +656,7 @@ int launch_upd12(const UpdArgs<T>& a, cudaStream_t s) {
   if (a.mu > 64 || a.mc > 64 || a.mv > 64) return NNC_ERR_UNSUPPORTED;
   const int UC = a.mu * a.mc;
   const size_t smem =
-      sizeof(T) * (gemm_stage_elems(a.mu, a.mc, (int)sizeof(T)) + al4(UC) + al4(a.mv * a.mv) +
+      sizeof(T) * (gemm_stage_elems(a.mu, a.mc, (int)sizeof(T), a.len) + al4(UC) + al4(a.mv * a.mv) +
                    2 * al4(a.mv) + (core_in_smem<T>((int64_t)a.mv * UC) ? (size_t)a.mv * UC : 0));
   NNC_TRY(set_smem(upd12_kernel<T>, smem));
   upd12_kernel<T><<<(unsigned)a.nrows, kThreads, smem, s>>>(a);
@@ -658,8 +668,8 @@ int launch_upd12(const UpdArgs<T>& a, cudaStream_t s) {
 template <typename T>
 int launch_hmat(const HArgs<T>& a, cudaStream_t s) {
   if (a.mu > 64 || a.mv > 64) return NNC_ERR_UNSUPPORTED;
-  const size_t st_u = a.fu ? gemm_stage_elems(a.mu, a.mu, (int)sizeof(T)) : 0;
-  const size_t st_v = a.fv ? gemm_stage_elems(a.mv, a.mv, (int)sizeof(T)) : 0;
+  const size_t st_u = a.fu ? gemm_stage_elems(a.mu, a.mu, (int)sizeof(T), (int)a.nu) : 0;
+  const size_t st_v = a.fv ? gemm_stage_elems(a.mv, a.mv, (int)sizeof(T), (int)a.nv) : 0;
   const int64_t guv = (int64_t)a.mp * a.mu * a.mv;
   const size_t smem = sizeof(T) * ((st_u > st_v ? st_u : st_v) + al4(a.mu * a.mu) +
                                    al4(a.mv * a.mv) + 3 * al4(a.mu * a.mv) +
@@ -675,7 +685,7 @@ template <typename T>
 int launch_y3(const T* P1, const T* F2, int m1, int N2, int N3, int m2, T* Y3, cudaStream_t s) {
   if (m2 > 64) return NNC_ERR_UNSUPPORTED;
   const size_t smem =
-      sizeof(T) * (gemm_stage_elems(kY3Tile, m2, (int)sizeof(T)) + al4((size_t)kY3Tile * m2));
+      sizeof(T) * (gemm_stage_elems(kY3Tile, m2, (int)sizeof(T), N2) + al4((size_t)kY3Tile * m2));
   NNC_TRY(set_smem(y3_kernel<T>, smem));
   dim3 grid((unsigned)ceil_div(N3, kY3Tile), (unsigned)m1);
   y3_kernel<T><<<grid, kThreads, smem, s>>>(P1, F2, N2, N3, m2, Y3);
@@ -713,8 +723,8 @@ template <typename T>
 int launch_core(const CoreArgs<T>& a, cudaStream_t s) {
   if (a.m1 > 64 || a.m2 > 64 || a.m3 > 64) return NNC_ERR_UNSUPPORTED;
   const int bc = a.m2 * a.m3;
-  const size_t st3 = gemm_stage_elems(a.m3, a.m3, (int)sizeof(T));
-  const size_t stm = gemm_stage_elems(a.m2, a.m3, (int)sizeof(T));
+  const size_t st3 = gemm_stage_elems(a.m3, a.m3, (int)sizeof(T), (int)a.n3);
+  const size_t stm = gemm_stage_elems(a.m2, a.m3, (int)sizeof(T), (int)a.n3);
   const size_t smem_a = sizeof(T) * ((st3 > stm ? st3 : stm) + al4(a.m2 * a.m2) +
                                      al4(a.m3 * a.m3) + 3 * al4(bc));
   NNC_TRY(set_smem(core_a_kernel<T>, smem_a));
@@ -733,7 +743,8 @@ int launch_core(const CoreArgs<T>& a, cudaStream_t s) {
 template <typename T>
 int launch_gram(const T* F, int64_t N, int m, T* S, cudaStream_t s) {
   if (m > 64) return NNC_ERR_UNSUPPORTED;
-  const size_t smem = sizeof(T) * (gemm_stage_elems(m, m, (int)sizeof(T)) + al4((size_t)m * m));
+  const size_t smem =
+      sizeof(T) * (gemm_stage_elems(m, m, (int)sizeof(T), (int)N) + al4((size_t)m * m));
   NNC_TRY(set_smem(gram_kernel<T>, smem));
   gram_kernel<T><<<1, kThreads, smem, s>>>(F, N, m, S);
   note_launch(s);
