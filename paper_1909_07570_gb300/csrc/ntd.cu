@@ -70,16 +70,51 @@ int pass_x1(const T* X, const NtdState<T>& b, const T* F1, const tc::TcPlan* tcp
   return NNC_OK;
 }
 
+// The core update of a sweep (G, the next H1, the trace entry).
+template <typename T>
+int launch_sweep_core(T* const* F, T* G, NtdState<T>& b, double eps, double* trace,
+                      int trace_stride, cudaStream_t s) {
+  CoreArgs<T> c{};
+  c.G = G;  c.G2 = b.G2;  c.G3 = b.G3;  c.Y3 = b.Y3;  c.Mout = b.M;  c.W3 = b.W3;
+  c.S1 = b.S[0];  c.S2 = b.S[1];  c.F3 = F[2];  c.n3 = b.N[2];  c.S3_out = b.S[2];
+  c.W1 = b.W1;  c.H1 = b.H[0];  c.dots = b.dots;  c.done = b.done;  c.x2 = b.stats;
+  c.trace = trace;  c.trace_stride = trace_stride;  c.counter = b.counter;
+  c.m1 = b.m[0];  c.m2 = b.m[1];  c.m3 = b.m[2];  c.eps = eps;
+  return launch_core<T>(c, s);
+}
+
+// Side stream and fork/join events of the two concurrent branches of a sweep.
+struct Branch {
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t fork[2] = {}, join[2] = {};
+};
+
+// One sweep without its core update, which the next sweep runs (or the caller
+// after the last one). Two pieces run beside the passes on a second stream:
+//   pass 1 (X x_3 F3^T)  beside  the previous sweep's core update (G, H1, trace):
+//                        the pass needs only F3;
+//   pass 2 (X x_1 F1^T)  beside  H2, the mode-2 update and H3: the pass needs
+//                        only the new F1.
+// The passes leave SMs free when that costs them nothing (tc_ttm.cu), and the
+// small kernels run there.
 template <typename T>
 int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* trace,
-           int trace_stride, const PassEvents* ev, const tc::TcPlan* tcp, cudaStream_t s) {
+           int trace_stride, const PassEvents* ev, const tc::TcPlan* tcp, bool prev_core,
+           const Branch& br, cudaStream_t s) {
   const int64_t N1 = b.N[0], N2 = b.N[1], N3 = b.N[2];
   const int m1 = b.m[0], m2 = b.m[1], m3 = b.m[2];
 
-  // ---- mode 1 ----------------------------------------------------------------
+  // ---- previous core beside pass 1; mode 1 -----------------------------------
+  if (prev_core) {
+    NNC_CUDA_TRY(cudaEventRecord(br.fork[0], s));
+    NNC_CUDA_TRY(cudaStreamWaitEvent(br.s2, br.fork[0], 0));
+    NNC_TRY(launch_sweep_core<T>(F, G, b, eps, trace, trace_stride, br.s2));
+    NNC_CUDA_TRY(cudaEventRecord(br.join[0], br.s2));
+  }
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->start[0], s, cudaEventRecordExternal));
   NNC_TRY(pass_x3<T>(X, b, F[2], tcp, s));
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->stop[0], s, cudaEventRecordExternal));
+  if (prev_core) NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.join[0], 0));
   {
     UpdArgs<T> u{};
     u.P = b.P3;  u.prow = N2 * m3;  u.pstride = m3;  // P3[i, j, c]
@@ -97,22 +132,24 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     }
     NNC_TRY(launch_upd12<T>(u, s));
   }
+  // ---- modes 2 (side stream) beside pass 2 -------------------------------------
+  NNC_CUDA_TRY(cudaEventRecord(br.fork[1], s));
+  NNC_CUDA_TRY(cudaStreamWaitEvent(br.s2, br.fork[1], 0));
   {  // H2 from S1 = F1^T F1 (new F1) and S3
     HArgs<T> h{};
     h.Gn = b.G2;  h.mp = m2;  h.mu = m1;  h.mv = m3;
     h.fu = F[0];  h.nu = N1;  h.su_out = b.S[0];
     h.sv = b.S[2];
     h.H = b.H[1];
-    NNC_TRY(launch_hmat<T>(h, s));
+    NNC_TRY(launch_hmat<T>(h, br.s2));
   }
-  // ---- mode 2 ----------------------------------------------------------------
   {
     UpdArgs<T> u{};
     u.P = b.P3;  u.prow = m3;  u.pstride = N2 * m3;  // row j, contraction over i
     u.Fc = F[0]; u.len = (int)N1;  u.mu = m1;  u.mc = m3;
     u.Gn = b.G2;  // rows b of G2 are (a, c)-contiguous
     u.F = F[1];  u.nrows = N2;  u.mv = m2;  u.H = b.H[1];  u.eps = eps;
-    NNC_TRY(launch_upd12<T>(u, s));
+    NNC_TRY(launch_upd12<T>(u, br.s2));
   }
   {  // H3 and W3 = G x_1 S1 x_2 S2, with S2 = F2^T F2 (new F2)
     HArgs<T> h{};
@@ -122,12 +159,14 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     h.fv = F[1];  h.nv = N2;  h.sv_out = b.S[1];
     h.H = b.H[2];
     h.Wout = b.W3;
-    NNC_TRY(launch_hmat<T>(h, s));
+    NNC_TRY(launch_hmat<T>(h, br.s2));
   }
-  // ---- mode 3 ----------------------------------------------------------------
+  NNC_CUDA_TRY(cudaEventRecord(br.join[1], br.s2));
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->start[1], s, cudaEventRecordExternal));
   NNC_TRY(pass_x1<T>(X, b, F[0], tcp, s));
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->stop[1], s, cudaEventRecordExternal));
+  NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.join[1], 0));
+  // ---- mode 3 ----------------------------------------------------------------
   NNC_TRY(launch_y3<T>(b.P1, F[1], m1, (int)N2, (int)N3, m2, b.Y3, s));
   {
     UpdArgs<T> u{};
@@ -144,16 +183,6 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
       }
     }
     NNC_TRY(launch_mode3<T>(u, s));
-  }
-  // ---- core ------------------------------------------------------------------
-  {
-    CoreArgs<T> c{};
-    c.G = G;  c.G2 = b.G2;  c.G3 = b.G3;  c.Y3 = b.Y3;  c.Mout = b.M;  c.W3 = b.W3;
-    c.S1 = b.S[0];  c.S2 = b.S[1];  c.F3 = F[2];  c.n3 = N3;  c.S3_out = b.S[2];
-    c.W1 = b.W1;  c.H1 = b.H[0];  c.dots = b.dots;  c.done = b.done;  c.x2 = b.stats;
-    c.trace = trace;  c.trace_stride = trace_stride;  c.counter = b.counter;
-    c.m1 = m1;  c.m2 = m2;  c.m3 = m3;  c.eps = eps;
-    NNC_TRY(launch_core<T>(c, s));
   }
   return NNC_OK;
 }
@@ -173,19 +202,28 @@ int count_kernel_nodes(cudaGraph_t graph, long long* n_kernels) {
   return NNC_OK;
 }
 
-// RAII holder of the private stream, graphs and events of one replay loop.
+// RAII holder of the private streams, graphs and events of one replay loop.
+// Graph A is the first sweep (no earlier core update), graph B every later
+// one (with the previous sweep's core update), graph P an instrumented copy of
+// B for the profiler.
 struct GraphRun {
   cudaStream_t cs = nullptr;
-  cudaGraph_t graph = nullptr, graph_p = nullptr;
-  cudaGraphExec_t exec = nullptr, exec_p = nullptr;
+  Branch br;
+  cudaGraph_t graph[3] = {};
+  cudaGraphExec_t exec[3] = {};
   cudaEvent_t fork = nullptr, join = nullptr;
   ~GraphRun() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (exec_p) cudaGraphExecDestroy(exec_p);
-    if (graph) cudaGraphDestroy(graph);
-    if (graph_p) cudaGraphDestroy(graph_p);
+    for (int k = 0; k < 3; ++k) {
+      if (exec[k]) cudaGraphExecDestroy(exec[k]);
+      if (graph[k]) cudaGraphDestroy(graph[k]);
+    }
+    for (int k = 0; k < 2; ++k) {
+      if (br.fork[k]) cudaEventDestroy(br.fork[k]);
+      if (br.join[k]) cudaEventDestroy(br.join[k]);
+    }
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
+    if (br.s2) cudaStreamDestroy(br.s2);
     if (cs) cudaStreamDestroy(cs);
   }
 };
@@ -199,56 +237,71 @@ constexpr int kProfileEvery = 16;
 
 template <typename T>
 int capture_sweep(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* trace,
-                  const PassEvents* ev, const tc::TcPlan* tcp, cudaStream_t cs,
-                  cudaGraph_t* graph, cudaGraphExec_t* exec) {
-  NNC_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+                  const PassEvents* ev, const tc::TcPlan* tcp, bool prev_core, GraphRun& g,
+                  int slot) {
+  NNC_CUDA_TRY(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
   const int cap_st = sweep3<T>(X, F, G, b, eps, trace ? trace : b.trace_dummy, trace ? 1 : 0, ev,
-                               tcp, cs);
-  const cudaError_t end_e = cudaStreamEndCapture(cs, graph);
+                               tcp, prev_core, g.br, g.cs);
+  const cudaError_t end_e = cudaStreamEndCapture(g.cs, &g.graph[slot]);
   if (cap_st != NNC_OK) return cap_st;
   NNC_CUDA_TRY(end_e);
-  NNC_CUDA_TRY(cudaGraphInstantiate(exec, *graph, 0));
+  NNC_CUDA_TRY(cudaGraphInstantiate(&g.exec[slot], g.graph[slot], 0));
   return NNC_OK;
 }
 
-// Captures one sweep on a private stream and replays it `count` times after
-// the work already queued on `s`; `s` then waits for the replays.
+// Captures the sweep on a private stream and replays it `count` times after
+// the work already queued on `s` (graph A once, then graph B), runs the last
+// sweep's core update, and makes `s` wait for all of it.
 template <typename T>
 int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* trace,
                int count, const tc::TcPlan* tcp, cudaStream_t s) {
   if (count <= 0) return NNC_OK;
   GraphRun g;
   NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
+  NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.br.s2, cudaStreamNonBlocking));
+  for (int k = 0; k < 2; ++k) {
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.br.fork[k], cudaEventDisableTiming));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.br.join[k], cudaEventDisableTiming));
+  }
   NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming));
   NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming));
   NNC_CUDA_TRY(cudaEventRecord(g.fork, s));
   NNC_CUDA_TRY(cudaStreamWaitEvent(g.cs, g.fork, 0));
 
-  NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, nullptr, tcp, g.cs, &g.graph, &g.exec));
-  long long kernel_nodes = 0;
-  NNC_TRY(count_kernel_nodes(g.graph, &kernel_nodes));
+  NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, nullptr, tcp, false, g, 0));
+  long long kn[3] = {0, 0, 0};
+  NNC_TRY(count_kernel_nodes(g.graph[0], &kn[0]));
+  if (count > 1) {
+    NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, nullptr, tcp, true, g, 1));
+    NNC_TRY(count_kernel_nodes(g.graph[1], &kn[1]));
+  }
 
-  // Sampled sweeps: the last of every kProfileEvery. The instrumented graph is
-  // captured once the first plain replays are queued, so the device is busy
-  // meanwhile.
+  // Sampled sweeps: the last of every kProfileEvery (graph B's instrumented
+  // copy, captured once the first plain replays are queued, so the device is
+  // busy meanwhile).
   PassProfiler prof(tcp ? (tcp->kind == tc::kKindBf16 ? 2 : 4) : 0);
   const int samples = profile_enabled() ? count / kProfileEvery : 0;
+  long long kernels = 0;
   for (int t = 0; t < count; ++t) {
     if (samples > 0 && t % kProfileEvery == kProfileEvery - 1) {
       const int j = t / kProfileEvery;
       if (j == 0) {
         NNC_TRY(prof.init(samples));
-        NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, prof.capture_events(), tcp, g.cs,
-                                 &g.graph_p, &g.exec_p));
-        NNC_TRY(prof.bind(g.graph_p));
+        NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, prof.capture_events(), tcp, true, g, 2));
+        NNC_TRY(prof.bind(g.graph[2]));
+        NNC_TRY(count_kernel_nodes(g.graph[2], &kn[2]));
       }
-      NNC_TRY(prof.set_launch(g.exec_p, j));
-      NNC_CUDA_TRY(cudaGraphLaunch(g.exec_p, g.cs));
+      NNC_TRY(prof.set_launch(g.exec[2], j));
+      NNC_CUDA_TRY(cudaGraphLaunch(g.exec[2], g.cs));
+      kernels += kn[2];
     } else {
-      NNC_CUDA_TRY(cudaGraphLaunch(g.exec, g.cs));
+      const int k = t == 0 ? 0 : 1;
+      NNC_CUDA_TRY(cudaGraphLaunch(g.exec[k], g.cs));
+      kernels += kn[k];
     }
   }
-  note_graph_launches(kernel_nodes * count);
+  note_graph_launches(kernels);
+  NNC_TRY(launch_sweep_core<T>(F, G, b, eps, trace ? trace : b.trace_dummy, trace ? 1 : 0, g.cs));
   NNC_CUDA_TRY(cudaEventRecord(g.join, g.cs));
   NNC_CUDA_TRY(cudaStreamWaitEvent(s, g.join, 0));
   NNC_CUDA_TRY(cudaStreamSynchronize(g.cs));

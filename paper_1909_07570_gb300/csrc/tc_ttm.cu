@@ -20,7 +20,8 @@
 //   from Xt, a transposed copy of X made once per fit.
 // B = F^T as operands [NP x K] (BF16: diag(s) folded into F1 for pass 2).
 //
-// Persistent CTAs, one per SM, each looping over 128-row tiles with warp roles:
+// Persistent CTAs, at most one per SM, each looping over 128-row tiles with
+// warp roles:
 //   warp 0        TMA producer: A tile and B slice of each K stage (a ring of as
 //                 many stages as fit in shared memory, at most 8)
 //   warp 1        MMA issuer (one thread): tcgen05.mma into a double-buffered
@@ -627,8 +628,11 @@ int launch_pass(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& b
                 int64_t tiles, const TcEpilogue& ep, int* err, cudaStream_t s) {
   constexpr int smem = TcLayout<KIND, NP>::kSmem;
   NNC_CUDA_TRY(raise_smem_limit((const void*)tc_pass_kernel<KIND, kMN, NP>, smem));
-  int64_t grid = device_sm_count();
-  if (grid > tiles) grid = tiles;
+  // Fewest CTAs that keep the largest tile count per CTA of a full-GPU grid:
+  // the time is the same, and the SMs left over run the small kernels of the
+  // sweep that the graph places beside the pass.
+  const int64_t per = ceil_div(tiles, (int64_t)device_sm_count());
+  const int64_t grid = ceil_div(tiles, per);
   NNC_CUDA_TRY(launch_pdl(tc_pass_kernel<KIND, kMN, NP>, dim3(static_cast<unsigned>(grid)),
                           dim3(kThreadsTc), smem, s, a, b, blo, nk, tiles, ep, err));
   note_launch(s);
