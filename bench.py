@@ -27,6 +27,10 @@ import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# The batching form runs up to 8 concurrent fits of two streams each: give the
+# process enough hardware work queues (before CUDA starts) so that they do not
+# share queues and serialise.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 sys.path.insert(0, ROOT)
 
 DEFAULT_WORKLOAD = "cp10_256x256x256_m20_fp32"

@@ -114,6 +114,9 @@ typedef struct {
  * CUDA stream of its own that first waits for the work already queued on
  * `stream`, so small problems overlap on the GPU; every job runs exactly the
  * kernels of ntd_fit and gives the same bits. Returns when all jobs are done.
+ * Each worker drives two streams (the sweep graph has two branches): above 4
+ * workers, start the process with CUDA_DEVICE_MAX_CONNECTIONS raised (e.g. to
+ * 32), or the streams share hardware queues and partly serialise.
  *
  *  jobs       host array of n_jobs descriptors
  *  rel_errs   host, n_jobs doubles (NaN for a failed job), or NULL

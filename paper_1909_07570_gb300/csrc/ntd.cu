@@ -45,6 +45,7 @@ struct NtdState {
   double *stats_part, *stats, *trace_dummy, *resid2, *dots;
   int* counter;
   int* done;
+  int* gate;
 };
 
 template <typename T>
@@ -78,7 +79,7 @@ int launch_sweep_core(T* const* F, T* G, NtdState<T>& b, double eps, double* tra
   c.G = G;  c.G2 = b.G2;  c.G3 = b.G3;  c.Y3 = b.Y3;  c.Mout = b.M;  c.W3 = b.W3;
   c.S1 = b.S[0];  c.S2 = b.S[1];  c.F3 = F[2];  c.n3 = b.N[2];  c.S3_out = b.S[2];
   c.W1 = b.W1;  c.H1 = b.H[0];  c.dots = b.dots;  c.done = b.done;  c.x2 = b.stats;
-  c.trace = trace;  c.trace_stride = trace_stride;  c.counter = b.counter;
+  c.trace = trace;  c.trace_stride = trace_stride;  c.counter = b.counter;  c.gate = b.gate;
   c.m1 = b.m[0];  c.m2 = b.m[1];  c.m3 = b.m[2];  c.eps = eps;
   return launch_core<T>(c, s);
 }
@@ -173,6 +174,7 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     u.P = b.Y3;  u.mu = m1;  u.mc = m2;  // Y3 laid out (m1, N3, m2)
     u.G = G;
     u.rows_per_block = mode3_rows_per_block<T>(m3, N3);
+    u.gate_out = b.gate;
     u.F = F[2];  u.nrows = N3;  u.mv = m3;  u.H = b.H[2];  u.eps = eps;
     if constexpr (std::is_same<T, float>::value) {
       if (tcp) {
@@ -202,18 +204,16 @@ int count_kernel_nodes(cudaGraph_t graph, long long* n_kernels) {
   return NNC_OK;
 }
 
-// RAII holder of the private streams, graphs and events of one replay loop.
-// Graph A is the first sweep (no earlier core update), graph B every later
-// one (with the previous sweep's core update), graph P an instrumented copy of
-// B for the profiler.
+// RAII holder of the private streams, graphs and events of one replay loop:
+// graph 0 is the sweep, graph 1 its instrumented copy for the profiler.
 struct GraphRun {
   cudaStream_t cs = nullptr;
   Branch br;
-  cudaGraph_t graph[3] = {};
-  cudaGraphExec_t exec[3] = {};
+  cudaGraph_t graph[2] = {};
+  cudaGraphExec_t exec[2] = {};
   cudaEvent_t fork = nullptr, join = nullptr;
   ~GraphRun() {
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 2; ++k) {
       if (exec[k]) cudaGraphExecDestroy(exec[k]);
       if (graph[k]) cudaGraphDestroy(graph[k]);
     }
@@ -250,8 +250,10 @@ int capture_sweep(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, dou
 }
 
 // Captures the sweep on a private stream and replays it `count` times after
-// the work already queued on `s` (graph A once, then graph B), runs the last
-// sweep's core update, and makes `s` wait for all of it.
+// the work already queued on `s`, runs the last sweep's core update, and makes
+// `s` wait for all of it. The core update a replay runs first is the previous
+// sweep's; in the first replay there is none, and the core kernels see the
+// pending flag at 0 and return at once.
 template <typename T>
 int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* trace,
                int count, const tc::TcPlan* tcp, cudaStream_t s) {
@@ -268,17 +270,13 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
   NNC_CUDA_TRY(cudaEventRecord(g.fork, s));
   NNC_CUDA_TRY(cudaStreamWaitEvent(g.cs, g.fork, 0));
 
-  NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, nullptr, tcp, false, g, 0));
-  long long kn[3] = {0, 0, 0};
+  NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, nullptr, tcp, true, g, 0));
+  long long kn[2] = {0, 0};
   NNC_TRY(count_kernel_nodes(g.graph[0], &kn[0]));
-  if (count > 1) {
-    NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, nullptr, tcp, true, g, 1));
-    NNC_TRY(count_kernel_nodes(g.graph[1], &kn[1]));
-  }
 
-  // Sampled sweeps: the last of every kProfileEvery (graph B's instrumented
-  // copy, captured once the first plain replays are queued, so the device is
-  // busy meanwhile).
+  // Sampled sweeps: the last of every kProfileEvery (an instrumented copy,
+  // captured once the first plain replays are queued, so the device is busy
+  // meanwhile).
   PassProfiler prof(tcp ? (tcp->kind == tc::kKindBf16 ? 2 : 4) : 0);
   const int samples = profile_enabled() ? count / kProfileEvery : 0;
   long long kernels = 0;
@@ -287,17 +285,16 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
       const int j = t / kProfileEvery;
       if (j == 0) {
         NNC_TRY(prof.init(samples));
-        NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, prof.capture_events(), tcp, true, g, 2));
-        NNC_TRY(prof.bind(g.graph[2]));
-        NNC_TRY(count_kernel_nodes(g.graph[2], &kn[2]));
+        NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, prof.capture_events(), tcp, true, g, 1));
+        NNC_TRY(prof.bind(g.graph[1]));
+        NNC_TRY(count_kernel_nodes(g.graph[1], &kn[1]));
       }
-      NNC_TRY(prof.set_launch(g.exec[2], j));
-      NNC_CUDA_TRY(cudaGraphLaunch(g.exec[2], g.cs));
-      kernels += kn[2];
+      NNC_TRY(prof.set_launch(g.exec[1], j));
+      NNC_CUDA_TRY(cudaGraphLaunch(g.exec[1], g.cs));
+      kernels += kn[1];
     } else {
-      const int k = t == 0 ? 0 : 1;
-      NNC_CUDA_TRY(cudaGraphLaunch(g.exec[k], g.cs));
-      kernels += kn[k];
+      NNC_CUDA_TRY(cudaGraphLaunch(g.exec[0], g.cs));
+      kernels += kn[0];
     }
   }
   note_graph_launches(kernels);
@@ -333,6 +330,7 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   NNC_TRY(sc.get(&b.counter, 1));
   NNC_TRY(sc.get(&b.dots, 2 * (size_t)m[0]));
   NNC_TRY(sc.get(&b.done, 1));
+  NNC_TRY(sc.get(&b.gate, 1));
   NNC_CUDA_TRY(launch_tensor_stats<T>(X, nX, b.stats_part, b.stats, s));
   double st[3];
   NNC_CUDA_TRY(cudaMemcpyAsync(st, b.stats, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -386,6 +384,7 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   }
   NNC_CUDA_TRY(cudaMemsetAsync(b.counter, 0, sizeof(int), s));
   NNC_CUDA_TRY(cudaMemsetAsync(b.done, 0, sizeof(int), s));
+  NNC_CUDA_TRY(cudaMemsetAsync(b.gate, 0, sizeof(int), s));
 
   const int n_fast = fast ? o->iters - o->refine_iters : 0;
   NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, n_fast, fast, s));

@@ -498,6 +498,7 @@ __global__ void __launch_bounds__(kThreads) mode3_kernel(UpdArgs<T> a) {
     a.F[r * m3 + v] = nv;
     write_operand(a, r, v, nv);
   }
+  if (a.gate_out && blockIdx.x == 0 && threadIdx.x == 0) *a.gate_out = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -507,6 +508,7 @@ __global__ void __launch_bounds__(kThreads) mode3_kernel(UpdArgs<T> a) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) core_a_kernel(CoreArgs<T> a) {
+  if (a.gate && *a.gate == 0) return;  // no sweep since the last core update
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int m1 = a.m1, m2 = a.m2, m3 = a.m3;
@@ -563,6 +565,7 @@ __global__ void __launch_bounds__(kThreads) core_a_kernel(CoreArgs<T> a) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) core_b_kernel(CoreArgs<T> a) {
+  if (a.gate && *a.gate == 0) return;  // no sweep since the last core update
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   __shared__ double red[32];
@@ -611,6 +614,7 @@ __global__ void __launch_bounds__(kThreads) core_b_kernel(CoreArgs<T> a) {
     a.trace[(int64_t)t * a.trace_stride] = sqrt(r2 / xx);
     *a.counter = t + 1;
     *a.done = 0;  // ready for the next sweep
+    if (a.gate) *a.gate = 0;
   }
 }
 

@@ -34,6 +34,7 @@ struct UpdArgs {
   float* blo;
   int64_t bt_ld;
   const float* bt_scale;
+  int* gate_out;  // mode 3: set to 1 (the sweep's core update is pending)
 };
 
 // H_n = unfold_n(G x_u S_u x_v S_v) unfold_n(G)^T, one block per index p of mode n.
@@ -74,6 +75,9 @@ struct CoreArgs {
   T* H1;                // out: unfold_1(W1) unfold_1(G_new)^T
   double* dots;         // m1 scratch
   int* done;            // block counter of core_b, 0 between sweeps
+  // 1 when a sweep's core update is pending (set by the mode-3 update of that
+  // sweep); the core kernels do nothing while it is 0 and core_b clears it.
+  int* gate;
   const double* x2;
   double* trace;
   int trace_stride;
