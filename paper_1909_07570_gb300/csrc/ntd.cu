@@ -9,8 +9,8 @@
 //   hmat 2   H2 = unfold_2(G x_1 S1 x_3 S3) unfold_2(G)^T
 //   upd 2    Num2 from P3 x_1 F1^T (new F1),  Den2 = F2 H2
 //   hmat 3   H3 from W3 = G x_1 S1 x_2 S2 (W3 kept)
-//   pass 2   P1 = X x_1 F1^T (new F1)                 (second read of X)
-//   y3, upd3 Y3 = P1 x_2 F2^T (new F2);  Num3 = unfold_3(Y3) unfold_3(G)^T;  Den3 = F3 H3
+//   pass 2   P1 = X x_1 F1^T (new F1), rows (k, j)     (second read of X)
+//   upd 3    Y3 = P1 x_2 F2^T (new F2);  Num3 = unfold_3(Y3) unfold_3(G)^T;  Den3 = F3 H3
 //   core     M = Y3 x_3 F3^T = X x_1 F1^T x_2 F2^T x_3 F3^T;
 //            G <- MU(G, M, W3 x_3 S3); trace; next H1       (core_a, core_b)
 // with S_k = F_k^T F_k. The kernels are in sweep.cu; the passes are SIMT mode
@@ -41,7 +41,9 @@ template <typename T>
 struct NtdState {
   int64_t N[3];
   int m[3];
-  T *P3, *P1, *Y3, *M, *W1, *W3, *G2, *G3, *H[3], *S[3];
+  // P3 rows (i, j) x m3; P1 rows (k, j) x m1 (SIMT passes: P1s, laid out
+  // (m1, N2, N3), is the pass result that P1 is copied from)
+  T *P3, *P1, *P1s, *Y3, *M, *W1, *W3, *G2, *G3, *H[3], *S[3];
   double *stats_part, *stats, *trace_dummy, *resid2, *dots;
   int* counter;
   int* done;
@@ -66,9 +68,9 @@ int pass_x1(const T* X, const NtdState<T>& b, const T* F1, const tc::TcPlan* tcp
   if constexpr (std::is_same<T, float>::value) {
     if (tcp) return tcp->pass1(F1, b.P1, s, /*convert=*/false);
   }
-  NNC_CUDA_TRY(launch_ttm<T>(X, 1, (int)b.N[0], b.N[1] * b.N[2], F1, b.m[0], 1, b.m[0], b.P1,
+  NNC_CUDA_TRY(launch_ttm<T>(X, 1, (int)b.N[0], b.N[1] * b.N[2], F1, b.m[0], 1, b.m[0], b.P1s,
                              nullptr, 0, s));
-  return NNC_OK;
+  return launch_p1_rows<T>(b.P1s, b.m[0], b.N[1], b.N[2], b.P1, s);
 }
 
 // The core update of a sweep (G, the next H1, the trace entry).
@@ -168,12 +170,12 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->stop[1], s, cudaEventRecordExternal));
   NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.join[1], 0));
   // ---- mode 3 ----------------------------------------------------------------
-  NNC_TRY(launch_y3<T>(b.P1, F[1], m1, (int)N2, (int)N3, m2, b.Y3, s));
   {
     UpdArgs<T> u{};
-    u.P = b.Y3;  u.mu = m1;  u.mc = m2;  // Y3 laid out (m1, N3, m2)
-    u.G = G;
-    u.rows_per_block = mode3_rows_per_block<T>(m3, N3);
+    u.P = b.P1;  u.prow = N2 * m1;  u.pstride = m1;  // P1[k, j, a]
+    u.Fc = F[1]; u.len = (int)N2;   u.mu = m1;  u.mc = m2;  u.p_first = 1;
+    u.Gn = b.G3;  // rows c of G3 are (a, b)-contiguous
+    u.Yout = b.Y3;
     u.gate_out = b.gate;
     u.F = F[2];  u.nrows = N3;  u.mv = m3;  u.H = b.H[2];  u.eps = eps;
     if constexpr (std::is_same<T, float>::value) {
@@ -184,7 +186,7 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
         u.bt_ld = tcp->kb3;
       }
     }
-    NNC_TRY(launch_mode3<T>(u, s));
+    NNC_TRY(launch_upd12<T>(u, s));
   }
   return NNC_OK;
 }
@@ -358,15 +360,17 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   const tc::TcPlan* exact = nullptr;  // FP32-accurate sweeps
   if constexpr (std::is_same<T, float>::value) {
     if (passes == 2 && o->iters > o->refine_iters) {
-      NNC_TRY(plan16.init(tc::kKindBf16, X, N1, N2, N3, m1, m3, sc, s));
+      NNC_TRY(plan16.init(tc::kKindBf16, X, N1, N2, N3, m1, m3, sc, s, /*p1_kj=*/true));
       fast = &plan16;
     }
     if (passes >= 1 && (passes == 1 || o->refine_iters > 0)) {
-      const int st = plan32.init(tc::kKindTf32x3, X, N1, N2, N3, m1, m3, sc, s);
+      const int st = plan32.init(tc::kKindTf32x3, X, N1, N2, N3, m1, m3, sc, s, /*p1_kj=*/true);
       if (st == NNC_OK) exact = &plan32;
       else if (st != NNC_ERR_UNSUPPORTED) return st;
     }
   }
+  const int n_fast = fast ? o->iters - o->refine_iters : 0;
+  if (!exact && o->iters - n_fast > 0) NNC_TRY(sc.get(&b.P1s, (size_t)(m1 * N2 * N3)));
 
   // Prologue: S_k = F_k^T F_k, H1 = unfold_1(G x_2 S2 x_3 S3) unfold_1(G)^T,
   // the BF16 operand of F^(3), the trace counter.
@@ -386,7 +390,6 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   NNC_CUDA_TRY(cudaMemsetAsync(b.done, 0, sizeof(int), s));
   NNC_CUDA_TRY(cudaMemsetAsync(b.gate, 0, sizeof(int), s));
 
-  const int n_fast = fast ? o->iters - o->refine_iters : 0;
   NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, n_fast, fast, s));
   if (fast) NNC_TRY(fast->check(s));
   if constexpr (std::is_same<T, float>::value) {

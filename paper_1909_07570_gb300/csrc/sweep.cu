@@ -10,10 +10,10 @@
 //                               H2[b, b'] = <W[:, b, :], G[:, b', :]>
 //   upd12 (mode 2) per row j:   Y2[:, j, :] = F1^T P3[:, j, :];  Num2;  MU on F2
 //   hmat  (mode 3) per c:       S2 = F2^T F2;  W3 = G x_1 S1 x_2 S2 (kept);  H3
-//   y3:                         Y3[a, k, b] = sum_j P1[a, j, k] F2[j, b]  (laid out m1, N3, m2)
-//   mode3 (rows of F3):         Num3[k, c] = sum_{a,b} Y3[a, k, b] G[a, b, c]; MU on F3
-//   core_a (one block per a):   S3 = F3^T F3; M[a] = Y3[a]^T F3; D = W3 x_3 S3;
-//                               G <- MU(G, M, D); W1 = G x_2 S2 x_3 S3
+//   upd12 (mode 3) per slab k:  Y3[k] = P1[k, :, :]^T F2  (m1 x m2, kept; P1 has rows (k, j))
+//                               Num3[k, c] = <Y3[k], G[:, :, c]>;  MU on F3
+//   core_a (one block per a):   S3 = F3^T F3; M[a] = Y3[:, a, :]^T F3 (= (X x_1 F1^T x_2 F2^T x_3 F3^T)[a]);
+//                               D = W3 x_3 S3;  G <- MU(G, M, D); W1 = G x_2 S2 x_3 S3
 //   core_b (one block per a):   H1 = unfold_1(W1) unfold_1(G)^T for the next sweep;
 //                               trace = sqrt(||X||^2 - 2<M,G> + <G, G x_k S_k>)/||X||
 //                               with <G, G x_k S_k> = sum S1 .* H1^T (last block)
@@ -328,8 +328,9 @@ __host__ __device__ inline bool core_in_smem(int64_t n) {
 }
 
 // ---------------------------------------------------------------------------
-// upd12: factor update of mode 1 or 2 from P3, one block per row r.
-//   Y_r = Fc^T P_r (mu x mc);  Num[r, v] = <Y_r, Gn[v]>;  F[r] <- MU(F[r], Num, F[r] H)
+// upd12: factor update of one mode from a pass result, one block per row r.
+//   Y_r = Fc^T P_r or P_r^T Fc (mu x mc);  Num[r, v] = <Y_r, Gn[v]>;
+//   F[r] <- MU(F[r], Num, F[r] H)
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
@@ -351,9 +352,15 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
   cp_flat(fo, a.F + r * MV, MV);
   if (gsm) cp_flat(gs, a.Gn, (int64_t)MV * UC);
   cp_commit();
-  gemm_tn_block(a.Fc, MU_, MU_, a.P + r * a.prow, a.pstride, MC, a.len,
-                gemm_kch(MU_, MC, (int)sizeof(T), a.len), ys, stage);
+  const int kch = gemm_kch(MU_, MC, (int)sizeof(T), a.len);
+  const T* pr = a.P + r * a.prow;
+  if (a.p_first)
+    gemm_tn_block(pr, a.pstride, MU_, a.Fc, MC, MC, a.len, kch, ys, stage);
+  else
+    gemm_tn_block(a.Fc, MU_, MU_, pr, a.pstride, MC, a.len, kch, ys, stage);
 
+  if (a.Yout)
+    for (int e = threadIdx.x; e < UC; e += blockDim.x) a.Yout[r * UC + e] = ys[e];
   rows_dot(ys, gsm ? (const T*)gs : a.Gn, UC, MV, nm);
   __syncthreads();
   for (int v = threadIdx.x; v < MV; v += blockDim.x) {
@@ -363,6 +370,7 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
     a.F[r * MV + v] = nv;
     write_operand(a, r, v, nv);
   }
+  if (a.gate_out && r == 0 && threadIdx.x == 0) *a.gate_out = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -417,93 +425,8 @@ __global__ void __launch_bounds__(kThreads) hmat_kernel(HArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
-// y3: Y3[a, k, b] = sum_j P1[a, j, k] F2[j, b]; block (k tile of 32, a).
-// ---------------------------------------------------------------------------
-constexpr int kY3Tile = 32;
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) y3_kernel(const T* __restrict__ P1,
-                                                      const T* __restrict__ F2, int N2, int N3,
-                                                      int m2, T* __restrict__ Y3) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int ai = blockIdx.y, k0 = blockIdx.x * kY3Tile;
-  const int ku = min(kY3Tile, N3 - k0);
-  T* stage = sm;
-  T* cs = stage + gemm_stage_elems(kY3Tile, m2, (int)sizeof(T), N2);
-  // The chunk size is the one the staging was sized for (a full tile of 32).
-  gemm_tn_block(P1 + (int64_t)ai * N2 * N3 + k0, N3, ku, F2, m2, m2, N2,
-                gemm_kch(kY3Tile, m2, (int)sizeof(T), N2), cs, stage);
-  T* y = Y3 + ((int64_t)ai * N3 + k0) * m2;
-  for (int e = threadIdx.x; e < ku * m2; e += blockDim.x) y[e] = cs[e];
-}
-
-// ---------------------------------------------------------------------------
-// mode3: rows k0 .. k0 + S - 1 of F3.
-//   Num3[k, c] = sum_{a, b} Y3[a, k, b] G[a, b, c];  F3[k] <- MU(F3[k], Num3, F3[k] H3)
-// UpdArgs: P = Y3 (m1 x N3 x m2), mu = m1, mc = m2, G = G (m1 x m2 x m3),
-// nrows = N3, mv = m3, H = H3, F = F3, rows_per_block = S.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) mode3_kernel(UpdArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int m1 = a.mu, m2 = a.mc, m3 = a.mv, S = a.rows_per_block;
-  const int K = m1 * m2, NO = S * m3;
-  const int kg = max(1, (int)blockDim.x / NO);  // K split per output
-  const bool gsm = core_in_smem<T>((int64_t)K * m3);
-  T* ys = sm;                       // m1 x S x m2
-  T* hs = ys + al4((size_t)m1 * S * m2);
-  T* fo = hs + al4(m3 * m3);         // S x m3
-  T* red = fo + al4(S * m3);         // kg x NO
-  T* gs = red + al4((size_t)kg * NO);  // K x m3 when it fits
-  const int64_t k0 = (int64_t)blockIdx.x * S;
-  const int sn = (int)min((int64_t)S, a.nrows - k0);
-
-  for (int aa = 0; aa < m1; ++aa)
-    cp_flat(ys + (int64_t)aa * S * m2, a.P + ((int64_t)aa * a.nrows + k0) * m2, (int64_t)sn * m2);
-  cp_flat(hs, a.H, m3 * m3);
-  cp_flat(fo, a.F + k0 * m3, (int64_t)sn * m3);
-  if (gsm) cp_flat(gs, a.G, (int64_t)K * m3);
-  cp_commit();
-  cp_wait<0>();
-  __syncthreads();
-
-  const T* g = gsm ? (const T*)gs : a.G;
-  if (threadIdx.x < kg * NO) {
-    // Thread (q, o): output o = (s, c) over the q-th contiguous range of t = (a, b).
-    const int q = threadIdx.x / NO, o = threadIdx.x % NO;
-    const int ss = o / m3, c = o % m3;
-    const int t0 = (int)((int64_t)K * q / kg), t1 = (int)((int64_t)K * (q + 1) / kg);
-    int aa = t0 / m2, b = t0 % m2;
-    T v = T(0);
-    for (int t = t0; t < t1; ++t) {
-      v = fma(ys[(aa * S + ss) * m2 + b], g[(int64_t)t * m3 + c], v);
-      if (++b == m2) {
-        b = 0;
-        ++aa;
-      }
-    }
-    red[q * NO + o] = v;
-  }
-  __syncthreads();
-  for (int o = threadIdx.x; o < sn * m3; o += blockDim.x) {
-    T num = T(0);
-    for (int q = 0; q < kg; ++q) num += red[q * NO + o];
-    const int ss = o / m3, v = o % m3;
-    T den = T(0);
-    for (int w = 0; w < m3; ++w) den = fma(fo[ss * m3 + w], hs[w * m3 + v], den);
-    const T nv = mu_step(fo[o], num, den, (T)a.eps);
-    const int64_t r = k0 + ss;
-    a.F[r * m3 + v] = nv;
-    write_operand(a, r, v, nv);
-  }
-  if (a.gate_out && blockIdx.x == 0 && threadIdx.x == 0) *a.gate_out = 1;
-}
-
-// ---------------------------------------------------------------------------
 // core_a: one block per mode-1 index a (no block depends on another):
-//   S3 = F3^T F3;  M[a] = Y3[a]^T F3 (= (X x_1 F1^T x_2 F2^T x_3 F3^T)[a]);
+//   S3 = F3^T F3;  M[a] = Y3[:, a, :]^T F3 (= (X x_1 F1^T x_2 F2^T x_3 F3^T)[a]);
 //   D[a] = W3[a] x_3 S3;  G[a] <- MU(G[a], M[a], D[a]);  W1[a] = S2 G[a] S3
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -530,7 +453,7 @@ __global__ void __launch_bounds__(kThreads) core_a_kernel(CoreArgs<T> a) {
   cp_commit();
   gemm_tn_block(a.F3, m3, m3, a.F3, m3, m3, (int)a.n3,
                 gemm_kch(m3, m3, (int)sizeof(T), (int)a.n3), s3, stage);
-  gemm_tn_block(a.Y3 + (int64_t)aa * a.n3 * m2, m2, m2, a.F3, m3, m3, (int)a.n3,
+  gemm_tn_block(a.Y3 + (int64_t)aa * m2, (int64_t)m1 * m2, m2, a.F3, m3, m3, (int)a.n3,
                 gemm_kch(m2, m3, (int)sizeof(T), (int)a.n3), ma, stage);
   if (aa == 0)
     for (int e = threadIdx.x; e < m3 * m3; e += blockDim.x) a.S3_out[e] = s3[e];
@@ -630,6 +553,27 @@ __global__ void permute_core_kernel(const T* __restrict__ G, int m1, int m2, int
   }
 }
 
+// out[(k N2 + j) m1 + a] = in[(a N2 + j) N3 + k]: block (k tile of 32, j).
+template <typename T>
+__global__ void p1_rows_kernel(const T* __restrict__ in, int m1, int64_t N2, int64_t N3,
+                               T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);  // m1 x 33
+  const int64_t k0 = (int64_t)blockIdx.x * 32;
+  for (int64_t j = blockIdx.y; j < N2; j += gridDim.y) {
+    for (int e = threadIdx.x; e < m1 * 32; e += blockDim.x) {
+      const int aa = e / 32, kk = e % 32;
+      if (k0 + kk < N3) tile[aa * 33 + kk] = in[((int64_t)aa * N2 + j) * N3 + k0 + kk];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m1 * 32; e += blockDim.x) {
+      const int kk = e / m1, aa = e % m1;
+      if (k0 + kk < N3) out[((k0 + kk) * N2 + j) * m1 + aa] = tile[aa * 33 + kk];
+    }
+    __syncthreads();
+  }
+}
+
 // S = F^T F for the prologue (one block).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ F, int64_t N, int m,
@@ -686,38 +630,12 @@ int launch_hmat(const HArgs<T>& a, cudaStream_t s) {
 }
 
 template <typename T>
-int launch_y3(const T* P1, const T* F2, int m1, int N2, int N3, int m2, T* Y3, cudaStream_t s) {
-  if (m2 > 64) return NNC_ERR_UNSUPPORTED;
-  const size_t smem =
-      sizeof(T) * (gemm_stage_elems(kY3Tile, m2, (int)sizeof(T), N2) + al4((size_t)kY3Tile * m2));
-  NNC_TRY(set_smem(y3_kernel<T>, smem));
-  dim3 grid((unsigned)ceil_div(N3, kY3Tile), (unsigned)m1);
-  y3_kernel<T><<<grid, kThreads, smem, s>>>(P1, F2, N2, N3, m2, Y3);
-  note_launch(s);
-  NNC_CUDA_TRY(cudaGetLastError());
-  return NNC_OK;
-}
-
-template <typename T>
-int mode3_rows_per_block(int m3, int64_t n3) {
-  // About 128 blocks or more, at most 128 outputs (S x m3) per block.
-  int s = (int)(n3 / 128);
-  const int cap = 128 / m3 < 4 ? 128 / m3 : 4;
-  s = s > cap ? cap : s;
-  return s < 1 ? 1 : s;
-}
-
-template <typename T>
-int launch_mode3(const UpdArgs<T>& a, cudaStream_t s) {
-  const int m1 = a.mu, m2 = a.mc, m3 = a.mv, S = a.rows_per_block;
-  if (m3 > 64 || S < 1 || S * m3 > kThreads) return NNC_ERR_UNSUPPORTED;
-  const int NO = S * m3, kg = kThreads / NO > 1 ? kThreads / NO : 1;
-  const int64_t K = (int64_t)m1 * m2;
-  const size_t smem = sizeof(T) * (al4((size_t)m1 * S * m2) + al4(m3 * m3) + al4(S * m3) +
-                                   al4((size_t)kg * NO) +
-                                   (core_in_smem<T>(K * m3) ? (size_t)(K * m3) : 0));
-  NNC_TRY(set_smem(mode3_kernel<T>, smem));
-  mode3_kernel<T><<<(unsigned)ceil_div(a.nrows, S), kThreads, smem, s>>>(a);
+int launch_p1_rows(const T* in, int m1, int64_t N2, int64_t N3, T* out, cudaStream_t s) {
+  if (m1 > 64) return NNC_ERR_UNSUPPORTED;
+  const size_t smem = sizeof(T) * (size_t)m1 * 33;
+  NNC_TRY(set_smem(p1_rows_kernel<T>, smem));
+  dim3 grid((unsigned)ceil_div(N3, 32), (unsigned)(N2 < 65535 ? N2 : 65535));
+  p1_rows_kernel<T><<<grid, kThreads, smem, s>>>(in, m1, N2, N3, out);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
   return NNC_OK;
@@ -768,9 +686,7 @@ int launch_permute_core(const T* G, int m1, int m2, int m3, T* G2, T* G3, cudaSt
 #define NNC_SWEEP_INST(T)                                                                   \
   template int launch_upd12<T>(const UpdArgs<T>&, cudaStream_t);                            \
   template int launch_hmat<T>(const HArgs<T>&, cudaStream_t);                               \
-  template int launch_y3<T>(const T*, const T*, int, int, int, int, T*, cudaStream_t);      \
-  template int mode3_rows_per_block<T>(int, int64_t);                                                \
-  template int launch_mode3<T>(const UpdArgs<T>&, cudaStream_t);                            \
+  template int launch_p1_rows<T>(const T*, int, int64_t, int64_t, T*, cudaStream_t);       \
   template int launch_core<T>(const CoreArgs<T>&, cudaStream_t);                            \
   template int launch_gram<T>(const T*, int64_t, int, T*, cudaStream_t);                    \
   template int launch_permute_core<T>(const T*, int, int, int, T*, T*, cudaStream_t);

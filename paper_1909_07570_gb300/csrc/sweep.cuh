@@ -7,26 +7,28 @@
 
 namespace nnc {
 
-// One factor update (mode 1 or 2: Y from P3 by a small GEMM; mode 3: Y3 given).
+// One factor update: Y_r by a small GEMM over the slab r of a pass result,
+// then Num[r, :] from Y_r and the core, then the MU step on row r of F.
 template <typename T>
 struct UpdArgs {
-  // Y_r[u, c] = sum_{t < len} Fc[t, u] P[r prow + t pstride + c]  (modes 1, 2)
-  // mode 3: P = Y3 laid out (mu = m1, nrows = N3, mc = m2)
+  // p_first == 0: Y_r[u, c] = sum_{t < len} Fc[t, u] P[r prow + t pstride + c]
+  // p_first != 0: Y_r[u, c] = sum_{t < len} P[r prow + t pstride + u] Fc[t, c]
+  // (u < mu, c < mc; Fc is len x (mu or mc), row-major)
   const T* P;
   int64_t prow, pstride;
   const T* Fc;
-  int len;      // contraction length (modes 1, 2)
+  int len;      // contraction length
   int mu, mc;   // Y_r is mu x mc
-  // Num[r, v] = <Y_r, Gn[v, :]> with Gn the core laid out (m_n, other two modes)
+  int p_first;
+  // Num[r, v] = <Y_r, Gn[v, :]> with Gn the core laid out (m_n, u, c)
   const T* Gn;
-  const T* G;   // mode 3: G viewed as (m1 m2) x m3
   // MU on F (nrows x mv) with Den = F H (H mv x mv)
   T* F;
   int64_t nrows;
   int mv;
   const T* H;
   double eps;
-  int rows_per_block;  // mode 3 only (modes 1, 2: one row per block)
+  T* Yout;  // optional: Y_r stored at Yout[r mu mc ..]
   // Optional operand of the next tensor-core pass, entry [v bt_ld + r] for
   // F[r, v] (times bt_scale[r] if given): BF16 (bt) or the TF32 pair (bhi, blo).
   __nv_bfloat16* bt;
@@ -34,7 +36,7 @@ struct UpdArgs {
   float* blo;
   int64_t bt_ld;
   const float* bt_scale;
-  int* gate_out;  // mode 3: set to 1 (the sweep's core update is pending)
+  int* gate_out;  // optional: set to 1 (mode 3: the sweep's core update is pending)
 };
 
 // H_n = unfold_n(G x_u S_u x_v S_v) unfold_n(G)^T, one block per index p of mode n.
@@ -63,7 +65,7 @@ struct CoreArgs {
   T* G;
   T* G2;                // out: G permuted to (m2, m1, m3)
   T* G3;                // out: G permuted to (m3, m1, m2)
-  const T* Y3;          // X x_1 F1^T x_2 F2^T laid out (m1, N3, m2)
+  const T* Y3;          // X x_1 F1^T x_2 F2^T laid out (N3, m1, m2)
   T* Mout;              // M = Y3 x_3 F3^T, laid out like G
   const T* W3;          // G x_1 S1 x_2 S2
   const T* S1;
@@ -89,14 +91,9 @@ template <typename T>
 int launch_upd12(const UpdArgs<T>& a, cudaStream_t s);
 template <typename T>
 int launch_hmat(const HArgs<T>& a, cudaStream_t s);
-// Y3[a, k, b] = sum_j P1[a, j, k] F2[j, b], laid out (m1, N3, m2).
+// P1 rows (k, j): out[(k N2 + j) m1 + a] = in[(a N2 + j) N3 + k].
 template <typename T>
-int launch_y3(const T* P1, const T* F2, int m1, int N2, int N3, int m2, T* Y3, cudaStream_t s);
-// Mode 3 (Num3 from Y3 and G, MU on F3), rows_per_block rows of F3 per block.
-template <typename T>
-int mode3_rows_per_block(int m3, int64_t n3);
-template <typename T>
-int launch_mode3(const UpdArgs<T>& a, cudaStream_t s);
+int launch_p1_rows(const T* in, int m1, int64_t N2, int64_t N3, T* out, cudaStream_t s);
 template <typename T>
 int launch_core(const CoreArgs<T>& a, cudaStream_t s);
 template <typename T>

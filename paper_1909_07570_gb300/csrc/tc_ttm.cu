@@ -398,6 +398,14 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (!__all_sync(0xffffffffu, mbar_wait(&accfull[buf], (tcount >> 1) & 1, vfail))) break;
       tc_fence_after();
       const int64_t row = tile * 128 + quarter * 32 + lane;
+      // Output row of the row-major layouts (-1: padding row, nothing stored).
+      int64_t orow = -1;
+      if (ep.p1_layout == 0) {
+        if (row < ep.rows) orow = row;
+      } else if (ep.p1_layout == 2) {
+        const int64_t jj = row / ep.kp, k = row % ep.kp;
+        if (jj < ep.n2 && k < ep.n3) orow = k * ep.n2 + jj;
+      }
       const int nacc = nk < L::kAcc ? nk : L::kAcc;  // accumulators this tile wrote
       const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
       const uint32_t accb = tmem + buf * L::kAcc * L::kAccCols + lanes;
@@ -427,10 +435,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
               v[t] = __float_as_uint(__uint_as_float(v[t]) + __uint_as_float(w[t]));
           }
         }
-        if (!ep.p1_layout) {
-          if (row < ep.rows) {
-            const float sc = ep.row_scale ? ep.row_scale[row / ep.rows_per_slice] : 1.f;
-            float* o = ep.out + row * ep.q;
+        if (ep.p1_layout != 1) {
+          if (orow >= 0) {
+            const float sc = ep.row_scale ? ep.row_scale[orow / ep.rows_per_slice] : 1.f;
+            float* o = ep.out + orow * ep.q;
             if ((ep.q & 3) == 0) {
 #pragma unroll
               for (int t = 0; t < 32; t += 4)
@@ -584,6 +592,26 @@ __global__ void transpose_kernel(const float* __restrict__ X, int64_t N1, int64_
   }
 }
 
+// Xt[(k N2 + j) ldt + i] = X[i, j, k] (Xt rows (k, j), row length ldt >= N1,
+// zero padded); block (k tile, i tile) of 32 x 32, looping over j.
+__global__ void transpose_kj_kernel(const float* __restrict__ X, int64_t N1, int64_t N2,
+                                    int64_t N3, int64_t ldt, float* __restrict__ Xt) {
+  __shared__ float tile[32][33];
+  const int64_t k0 = static_cast<int64_t>(blockIdx.x) * 32, i0 = static_cast<int64_t>(blockIdx.y) * 32;
+  for (int64_t j = blockIdx.z; j < N2; j += gridDim.z) {
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int64_t i = i0 + r, k = k0 + threadIdx.x;
+      tile[r][threadIdx.x] = (i < N1 && k < N3) ? X[(i * N2 + j) * N3 + k] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int64_t k = k0 + r, i = i0 + threadIdx.x;
+      if (k < N3 && i < ldt) Xt[(k * N2 + j) * ldt + i] = tile[threadIdx.x][r];
+    }
+    __syncthreads();
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -649,8 +677,9 @@ int launch_np(int np, const CUtensorMap& a, const CUtensorMap& b, const CUtensor
 }  // namespace
 
 int TcPlan::init(int kind_, const float* X, int64_t N1_, int64_t N2_, int64_t N3_, int m1_,
-                 int m3_, Scratch& sc, cudaStream_t s) {
+                 int m3_, Scratch& sc, cudaStream_t s, bool p1_kj_) {
   kind = kind_;
+  p1_kj = p1_kj_;
   N1 = N1_;
   N2 = N2_;
   N3 = N3_;
@@ -713,11 +742,18 @@ int TcPlan::init(int kind_, const float* X, int64_t N1_, int64_t N2_, int64_t N3
     NNC_TRY(make_map(&mapA3, f32, X, N3, rows, static_cast<uint64_t>(N3) * 4, 32, 128));
     NNC_TRY(make_map(&mapB3, f32, B3hi, kb3, np3, static_cast<uint64_t>(kb3) * 4, 32, np3));
     NNC_TRY(make_map(&mapB3lo, f32, B3lo, kb3, np3, static_cast<uint64_t>(kb3) * 4, 32, np3));
-    // Pass 2 reads Xt = X viewed (N1 x N2 N3), transposed: K-major rows of N1p.
+    // Pass 2 reads Xt = X viewed (N1 x N2 N3), transposed: K-major rows of N1p
+    // in the order (j, k), or (k, j) for p1_kj.
     const int64_t C = N2 * N3, n1p = ceil_div(N1, 4) * 4;
     NNC_TRY(sc.get(&Xt, static_cast<size_t>(C * n1p)));
-    dim3 tgrid(static_cast<unsigned>(ceil_div(C, 32)), static_cast<unsigned>(ceil_div(n1p, 32)));
-    transpose_kernel<<<tgrid, dim3(32, 8), 0, s>>>(X, N1, C, n1p, Xt);
+    if (p1_kj) {
+      dim3 tgrid(static_cast<unsigned>(ceil_div(N3, 32)), static_cast<unsigned>(ceil_div(n1p, 32)),
+                 static_cast<unsigned>(N2 < 65535 ? N2 : 65535));
+      transpose_kj_kernel<<<tgrid, dim3(32, 8), 0, s>>>(X, N1, N2, N3, n1p, Xt);
+    } else {
+      dim3 tgrid(static_cast<unsigned>(ceil_div(C, 32)), static_cast<unsigned>(ceil_div(n1p, 32)));
+      transpose_kernel<<<tgrid, dim3(32, 8), 0, s>>>(X, N1, C, n1p, Xt);
+    }
     note_launch(s);
     NNC_CUDA_TRY(cudaGetLastError());
     NNC_TRY(make_map(&mapA1, f32, Xt, n1p, C, static_cast<uint64_t>(n1p) * 4, 32, 128));
@@ -764,11 +800,18 @@ int TcPlan::pass1(const float* F1, float* P1, cudaStream_t s, bool convert) cons
   TcEpilogue ep{};
   ep.out = P1;
   ep.q = m1;
-  ep.p1_layout = 1;
   ep.kp = kp3;
   ep.n2 = N2;
   ep.n3 = N3;
   ep.slab = N2 * N3;
+  if (!p1_kj) {
+    ep.p1_layout = 1;
+  } else if (kind == kKindBf16) {
+    ep.p1_layout = 2;  // MN-major tiles of Xb have rows (j, k)
+  } else {
+    ep.p1_layout = 0;  // Xt already has rows (k, j)
+    ep.rows = N2 * N3;
+  }
   const int64_t tiles = ceil_div(N2 * kp3, 128);
   const int stagek = kind == kKindBf16 ? 64 : 32;
   const int nk = static_cast<int>(ceil_div(N1, stagek));

@@ -21,9 +21,12 @@ struct TcEpilogue {
   int64_t rows;
   int64_t rows_per_slice;
   const float* row_scale;
-  // pass X x_1 F1^T (p1_layout): tile row c = (j, k) of the N2 x kp layout
-  // (kp = padded row length of the operand view); out is q x n2 x n3
-  // (slab = n2 n3)
+  // p1_layout 0: out is rows x q, tile row = output row (as above)
+  // p1_layout 1 (pass X x_1 F1^T): tile row c = (j, k) of the N2 x kp layout
+  //   (kp = padded row length of the operand view); out is q x n2 x n3
+  //   (slab = n2 n3)
+  // p1_layout 2 (pass X x_1 F1^T): tile row c = (j, k) of the N2 x kp layout;
+  //   out has rows (k, j): out[(k n2 + j) q + col]
   int p1_layout;
   int64_t kp, n2, n3, slab;
 };
@@ -32,11 +35,14 @@ struct TcEpilogue {
 //   BF16:   a BF16 copy Xb of X (per-slice power-of-two scales, rows padded to a
 //           multiple of 64) and BF16 operands Bt1, Bt3 of F^(1), F^(3).
 //   TF32x3: X itself for pass 1, a transposed copy Xt (N2 N3 x N1p, i
-//           contiguous) so that pass 2 is K-major too, and hi / lo TF32
-//           operands B1hi/B1lo, B3hi/B3lo.
+//           contiguous; rows (j, k), or (k, j) with p1_kj) so that pass 2 is
+//           K-major too, and hi / lo TF32 operands B1hi/B1lo, B3hi/B3lo.
 // B operands are [np x k] row-major, zero outside the factor.
 struct TcPlan {
   int kind = kKindBf16;
+  // Layout of the pass-2 result: false: m1 x N2 x N3; true: rows (k, j),
+  // (N3 N2) x m1 (the nnTD sweep's layout).
+  bool p1_kj = false;
   int64_t N1 = 0, N2 = 0, N3 = 0;
   int m1 = 0, m3 = 0, kp1 = 0, kp3 = 0, kb3 = 0, np1 = 0, np3 = 0;
   __nv_bfloat16 *Xb = nullptr, *Bt1 = nullptr, *Bt3 = nullptr;
@@ -49,13 +55,13 @@ struct TcPlan {
   // UNSUPPORTED when the shape is outside the path (m_n > 64; TF32x3 also
   // needs N3 % 4 == 0 for its TMA row strides).
   int init(int kind, const float* X, int64_t N1, int64_t N2, int64_t N3, int m1, int m3,
-           Scratch& sc, cudaStream_t s);
+           Scratch& sc, cudaStream_t s, bool p1_kj = false);
   // B operands from the current factor (BF16: F^(1) scaled by s).
   int convert_b3(const float* F3, cudaStream_t s) const;
   int convert_b1(const float* F1, cudaStream_t s) const;
   // P3 = X x_3 F3^T ((N1 N2) x m3, FP32); convert first builds the B operand.
   int pass3(const float* F3, float* P3, cudaStream_t s, bool convert = true) const;
-  // P1 = X x_1 F1^T (m1 x N2 x N3, FP32).
+  // P1 = X x_1 F1^T (FP32; m1 x N2 x N3, or rows (k, j) with p1_kj).
   int pass1(const float* F1, float* P1, cudaStream_t s, bool convert = true) const;
   // Synchronises s and turns a device-side pipeline time-out into NNC_ERR_TIMEOUT.
   int check(cudaStream_t s) const;
