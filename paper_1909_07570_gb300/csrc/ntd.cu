@@ -44,6 +44,10 @@ struct NtdState {
   // P3 rows (i, j) x m3; P1 rows (k, j) x m1 (SIMT passes: P1s, laid out
   // (m1, N2, N3), is the pass result that P1 is copied from)
   T *P3, *P1, *P1s, *Y3, *M, *W1, *W3, *G2, *G3, *H[3], *S[3];
+  // Shares of Y1[i] = F2^T P3[i] from the tensor-core pass (y1_nh per slab;
+  // NULL: upd12 forms Y1 from P3)
+  T* Y1p;
+  int y1_nh;
   double *stats_part, *stats, *trace_dummy, *resid2, *dots;
   int* counter;
   int* done;
@@ -51,10 +55,14 @@ struct NtdState {
 };
 
 template <typename T>
-int pass_x3(const T* X, const NtdState<T>& b, const T* F3, const tc::TcPlan* tcp,
+int pass_x3(const T* X, const NtdState<T>& b, const T* F3, const T* F2, const tc::TcPlan* tcp,
             cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
-    if (tcp) return tcp->pass3(F3, b.P3, s, /*convert=*/false);
+    if (tcp) {
+      if (b.Y1p && tcp->y1_fusable(b.m[1]))
+        return tcp->pass3(F3, b.P3, s, /*convert=*/false, F2, b.m[1], b.Y1p);
+      return tcp->pass3(F3, b.P3, s, /*convert=*/false);
+    }
   }
   // No split buffer: the passes fill the GPU without splitting the contraction.
   NNC_CUDA_TRY(launch_ttm<T>(X, b.N[0] * b.N[1], (int)b.N[2], 1, F3, b.m[2], 1, b.m[2], b.P3,
@@ -115,7 +123,7 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     NNC_CUDA_TRY(cudaEventRecord(br.join[0], br.s2));
   }
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->start[0], s, cudaEventRecordExternal));
-  NNC_TRY(pass_x3<T>(X, b, F[2], tcp, s));
+  NNC_TRY(pass_x3<T>(X, b, F[2], F[1], tcp, s));
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->stop[0], s, cudaEventRecordExternal));
   if (prev_core) NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.join[0], 0));
   {
@@ -123,6 +131,10 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     u.P = b.P3;  u.prow = N2 * m3;  u.pstride = m3;  // P3[i, j, c]
     u.Fc = F[1]; u.len = (int)N2;   u.mu = m2;  u.mc = m3;
     u.Gn = G;    // rows a of G are (b, c)-contiguous
+    if (tcp && b.Y1p && tcp->y1_fusable(m2)) {  // the pass formed Y1's shares
+      u.Ypart = b.Y1p;
+      u.nparts = b.y1_nh;
+    }
     u.F = F[0];  u.nrows = N1;  u.mv = m1;  u.H = b.H[0];  u.eps = eps;
     if constexpr (std::is_same<T, float>::value) {
       if (tcp) {
@@ -371,6 +383,15 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   }
   const int n_fast = fast ? o->iters - o->refine_iters : 0;
   if (!exact && o->iters - n_fast > 0) NNC_TRY(sc.get(&b.P1s, (size_t)(m1 * N2 * N3)));
+  if constexpr (std::is_same<T, float>::value) {
+    // The passes form the shares of Y1 when the shape allows it (both plans
+    // see the same shape).
+    const tc::TcPlan* any = exact ? exact : fast;
+    if (any && any->y1_fusable(m2)) {
+      b.y1_nh = (int)(N2 / 128);
+      NNC_TRY(sc.get(&b.Y1p, (size_t)(N1 * b.y1_nh) * m2 * m3));
+    }
+  }
 
   // Prologue: S_k = F_k^T F_k, H1 = unfold_1(G x_2 S2 x_3 S3) unfold_1(G)^T,
   // the BF16 operand of F^(3), the trace counter.

@@ -329,7 +329,8 @@ __host__ __device__ inline bool core_in_smem(int64_t n) {
 
 // ---------------------------------------------------------------------------
 // upd12: factor update of one mode from a pass result, one block per row r.
-//   Y_r = Fc^T P_r or P_r^T Fc (mu x mc);  Num[r, v] = <Y_r, Gn[v]>;
+//   Y_r = Fc^T P_r or P_r^T Fc (mu x mc), or the sum of its shares that the
+//   pass already formed;  Num[r, v] = <Y_r, Gn[v]>;
 //   F[r] <- MU(F[r], Num, F[r] H)
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
   const int MU_ = a.mu, MC = a.mc, MV = a.mv, UC = MU_ * MC;
   const bool gsm = core_in_smem<T>((int64_t)MV * UC);
   T* stage = sm;
-  T* ys = stage + gemm_stage_elems(MU_, MC, (int)sizeof(T), a.len);
+  T* ys = stage + (a.Ypart ? 0 : gemm_stage_elems(MU_, MC, (int)sizeof(T), a.len));
   T* hs = ys + al4(UC);
   T* fo = hs + al4(MV * MV);
   T* nm = fo + al4(MV);
@@ -352,12 +353,23 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
   cp_flat(fo, a.F + r * MV, MV);
   if (gsm) cp_flat(gs, a.Gn, (int64_t)MV * UC);
   cp_commit();
-  const int kch = gemm_kch(MU_, MC, (int)sizeof(T), a.len);
-  const T* pr = a.P + r * a.prow;
-  if (a.p_first)
-    gemm_tn_block(pr, a.pstride, MU_, a.Fc, MC, MC, a.len, kch, ys, stage);
-  else
-    gemm_tn_block(a.Fc, MU_, MU_, pr, a.pstride, MC, a.len, kch, ys, stage);
+  if (a.Ypart) {
+    const T* yp = a.Ypart + r * a.nparts * UC;
+    for (int e = threadIdx.x; e < UC; e += blockDim.x) {
+      T y = yp[e];
+      for (int h = 1; h < a.nparts; ++h) y += yp[(int64_t)h * UC + e];
+      ys[e] = y;
+    }
+    cp_wait<0>();
+    __syncthreads();
+  } else {
+    const int kch = gemm_kch(MU_, MC, (int)sizeof(T), a.len);
+    const T* pr = a.P + r * a.prow;
+    if (a.p_first)
+      gemm_tn_block(pr, a.pstride, MU_, a.Fc, MC, MC, a.len, kch, ys, stage);
+    else
+      gemm_tn_block(a.Fc, MU_, MU_, pr, a.pstride, MC, a.len, kch, ys, stage);
+  }
 
   if (a.Yout)
     for (int e = threadIdx.x; e < UC; e += blockDim.x) a.Yout[r * UC + e] = ys[e];
@@ -603,9 +615,10 @@ template <typename T>
 int launch_upd12(const UpdArgs<T>& a, cudaStream_t s) {
   if (a.mu > 64 || a.mc > 64 || a.mv > 64) return NNC_ERR_UNSUPPORTED;
   const int UC = a.mu * a.mc;
+  const size_t st = a.Ypart ? 0 : gemm_stage_elems(a.mu, a.mc, (int)sizeof(T), a.len);
   const size_t smem =
-      sizeof(T) * (gemm_stage_elems(a.mu, a.mc, (int)sizeof(T), a.len) + al4(UC) + al4(a.mv * a.mv) +
-                   2 * al4(a.mv) + (core_in_smem<T>((int64_t)a.mv * UC) ? (size_t)a.mv * UC : 0));
+      sizeof(T) * (st + al4(UC) + al4(a.mv * a.mv) + 2 * al4(a.mv) +
+                   (core_in_smem<T>((int64_t)a.mv * UC) ? (size_t)a.mv * UC : 0));
   NNC_TRY(set_smem(upd12_kernel<T>, smem));
   upd12_kernel<T><<<(unsigned)a.nrows, kThreads, smem, s>>>(a);
   note_launch(s);

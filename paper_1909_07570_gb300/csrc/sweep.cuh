@@ -20,6 +20,10 @@ struct UpdArgs {
   int len;      // contraction length
   int mu, mc;   // Y_r is mu x mc
   int p_first;
+  // Optional: Y_r given as the sum of nparts shares Ypart[(r nparts + h) mu mc ..]
+  // (h = 0 .. nparts - 1, added in that order) instead of the GEMM.
+  const T* Ypart;
+  int nparts;
   // Num[r, v] = <Y_r, Gn[v, :]> with Gn the core laid out (m_n, u, c)
   const T* Gn;
   // MU on F (nrows x mv) with Den = F H (H mv x mv)

@@ -189,7 +189,7 @@ __device__ __forceinline__ float tf32_lo(float x, float hi) {
   return __uint_as_float(r);
 }
 
-template <int KIND, int NP>
+template <int KIND, int NP, bool FUSE = false>
 struct TcLayout {
   static constexpr bool kTf32 = KIND == kKindTf32x3;
   // TF32x3: K stages rotate over kAcc accumulators that the epilogue adds in
@@ -211,22 +211,44 @@ struct TcLayout {
   static constexpr int kLoSlots = kTf32 ? 3 : 0;
   static constexpr int kLoRing = kLoSlots > 0 ? kLoSlots : 1;  // index modulus
   static constexpr int kLoBytes = kLoSlots * kTileBytes;
-  // As many stages as fit in about 220 KB of shared memory (at most 8).
-  static constexpr int kStagesFit = (220 * 1024 - 1024 - kLoBytes) / kStageBytes;
+  // Fused mode-1 contraction (pass X x_3 F3^T only): the tile's P3 rows and
+  // the matching F2 rows, 128 x 32 FP32 each.
+  static constexpr int kEpiBytes = FUSE ? 2 * 128 * 32 * 4 : 0;
+  // As many stages as fit in the 227 KB of shared memory a CTA may use, less
+  // the static barriers and the 1 KB alignment slack (at most 8).
+  static constexpr int kStagesFit =
+      (227 * 1024 - 512 - 1024 - kLoBytes - kEpiBytes) / kStageBytes;
   static constexpr int kStages = kStagesFit > 8 ? 8 : kStagesFit;
   static constexpr int kOffLo = kStages * kStageBytes;
-  static constexpr int kSmem = 1024 + kOffLo + kLoBytes;
+  static constexpr int kOffEpi = kOffLo + kLoBytes;
+  static constexpr int kSmem = 1024 + kOffEpi + kEpiBytes;
   static_assert(kTmemCols == 32 || kTmemCols == 64 || kTmemCols == 128 || kTmemCols == 256 ||
                 kTmemCols == 512, "TMEM allocation must be a power of two >= 32 columns");
   static_assert(kStageBytes % 1024 == 0, "stages must keep 1024-byte swizzle atoms aligned");
+  static_assert(!FUSE || NP == 32, "the fused contraction covers m3 <= 32");
 };
 
-template <int KIND, bool kMN, int NP>
+// AND of `ok` over the 128 epilogue threads (named barrier 1).
+__device__ __forceinline__ bool epi_all(bool ok) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred q, p;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, 1, 128, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"(ok ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+template <int KIND, bool kMN, int NP, bool FUSE>
 __global__ void __launch_bounds__(kThreadsTc, 1)
 tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmBlo, int nk, int64_t ntiles, TcEpilogue ep,
                int* err) {
-  using L = TcLayout<KIND, NP>;
+  using L = TcLayout<KIND, NP, FUSE>;
   static_assert(!(L::kTf32 && kMN), "TF32x3 passes read A K-major");
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t full[L::kStages], empty[L::kStages], accfull[2], accempty[2];
@@ -234,8 +256,9 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
 
-  unsigned char* base = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  // 1024-byte aligned start, derived from smem_raw by pointer arithmetic so
+  // that the compiler keeps every access through it in the shared space.
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* vfail = &fail;
   // The successor kernel may be scheduled now; it waits for this grid itself.
@@ -391,14 +414,44 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   } else if (warp < 6) {
     // ---- epilogue (warps 2-5) ------------------------------------------------
     const int quarter = warp & 3;  // TMEM lanes 32 quarter .. 32 quarter + 31
+    const int lr = quarter * 32 + lane;  // tile row of this thread
+    float* Ps = reinterpret_cast<float*>(base + L::kOffEpi);  // FUSE: 128 x 32 P3 rows
+    float* Fs = Ps + 128 * 32;                                // FUSE: 128 x 32 F2 rows
     int tcount = 0;
+    int64_t fs_slice = -1;  // FUSE: the j range whose F2 rows Fs holds
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
       const int buf = tcount & 1;
-      // The warp-collective tcgen05.ld needs one decision for the whole warp.
-      if (!__all_sync(0xffffffffu, mbar_wait(&accfull[buf], (tcount >> 1) & 1, vfail))) break;
-      tc_fence_after();
-      const int64_t row = tile * 128 + quarter * 32 + lane;
-      // Output row of the row-major layouts (-1: padding row, nothing stored).
+      if constexpr (FUSE) {
+        if (tile % ep.y_nh != fs_slice) {
+          // F2 rows of this tile's j range (F2 is not written during the pass),
+          // loaded when the range changes (never, when the grid is a multiple of
+          // the tiles per slab); the previous tile ended with a barrier.
+          fs_slice = tile % ep.y_nh;
+          const int64_t j = fs_slice * 128 + lr;
+          const float* f = ep.f2 + j * ep.m2;
+          float fr[32];
+          if ((ep.m2 & 3) == 0 && (reinterpret_cast<uintptr_t>(f) & 15) == 0) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const float4 q = 4 * c < ep.m2 ? *reinterpret_cast<const float4*>(f + 4 * c)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+              fr[4 * c] = q.x; fr[4 * c + 1] = q.y; fr[4 * c + 2] = q.z; fr[4 * c + 3] = q.w;
+            }
+          } else {
+#pragma unroll
+            for (int b = 0; b < 32; ++b) fr[b] = b < ep.m2 ? f[b] : 0.f;
+          }
+          // Rows of 8 float4 chunks, chunk c stored at c ^ (row & 7): the
+          // row-per-thread stores and the chunk reads below avoid bank conflicts.
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<float4*>(Fs + lr * 32 + ((c ^ (lr & 7)) << 2)) =
+                make_float4(fr[4 * c], fr[4 * c + 1], fr[4 * c + 2], fr[4 * c + 3]);
+        }
+      }
+      const int64_t row = tile * 128 + lr;
+      // Output row of the row-major layouts (-1: padding row, nothing stored)
+      // and its scale, read before the wait so that the load is off the path.
       int64_t orow = -1;
       if (ep.p1_layout == 0) {
         if (row < ep.rows) orow = row;
@@ -406,6 +459,17 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int64_t jj = row / ep.kp, k = row % ep.kp;
         if (jj < ep.n2 && k < ep.n3) orow = k * ep.n2 + jj;
       }
+      const float sc = (orow >= 0 && ep.row_scale) ? ep.row_scale[orow / ep.rows_per_slice] : 1.f;
+      const bool got = mbar_wait(&accfull[buf], (tcount >> 1) & 1, vfail);
+      if constexpr (FUSE) {
+        // All four warps take the same branch: the named barriers below need
+        // every epilogue thread.
+        if (!epi_all(got)) break;
+      } else {
+        // The warp-collective tcgen05.ld needs one decision for the whole warp.
+        if (!__all_sync(0xffffffffu, got)) break;
+      }
+      tc_fence_after();
       const int nacc = nk < L::kAcc ? nk : L::kAcc;  // accumulators this tile wrote
       const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
       const uint32_t accb = tmem + buf * L::kAcc * L::kAccCols + lanes;
@@ -437,7 +501,6 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         if (ep.p1_layout != 1) {
           if (orow >= 0) {
-            const float sc = ep.row_scale ? ep.row_scale[orow / ep.rows_per_slice] : 1.f;
             float* o = ep.out + orow * ep.q;
             if ((ep.q & 3) == 0) {
 #pragma unroll
@@ -452,6 +515,16 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 if (c0 + t < ep.q) o[c0 + t] = __uint_as_float(v[t]) * sc;
             }
           }
+          if constexpr (FUSE) {
+            // The stored P3 row (zero past m3) for the contraction below.
+#pragma unroll
+            for (int t = 0; t < 32; t += 4)
+              *reinterpret_cast<float4*>(Ps + lr * 32 + (((t >> 2) ^ (lr & 7)) << 2)) =
+                  make_float4(t < ep.q ? __uint_as_float(v[t]) * sc : 0.f,
+                              t + 1 < ep.q ? __uint_as_float(v[t + 1]) * sc : 0.f,
+                              t + 2 < ep.q ? __uint_as_float(v[t + 2]) * sc : 0.f,
+                              t + 3 < ep.q ? __uint_as_float(v[t + 3]) * sc : 0.f);
+          }
         } else {
           const int64_t jj = row / ep.kp, k = row % ep.kp;
           if (jj < ep.n2 && k < ep.n3) {
@@ -465,6 +538,55 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&accempty[buf]);
+      if constexpr (FUSE) {
+        // Mode-1 contraction of the tile (one slab i, rows j0 .. j0 + 127):
+        //   Y1p[tile][b, c] = sum_r F2[j0 + r, b] P3[i, j0 + r, c]
+        // 4 x 4 output tiles per thread, rows split over `groups` thread
+        // groups whose partial tiles are added in group order.
+        const int et = threadIdx.x - 64;  // 0 .. 127
+        const int m2 = ep.m2, m3 = ep.q, tq = (m3 + 3) / 4;
+        const int tiles = ((m2 + 3) / 4) * tq, groups = 128 / tiles;
+        const int g = et / tiles, t = et % tiles;
+        const int b0 = (t / tq) * 4, cc0 = (t % tq) * 4;
+        float acc[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+        epi_sync();  // Ps and Fs complete
+        if (g < groups) {
+#pragma unroll 4
+          for (int r = g; r < 128; r += groups) {
+            const float4 fb =
+                *reinterpret_cast<const float4*>(Fs + r * 32 + (((b0 >> 2) ^ (r & 7)) << 2));
+            const float4 pc =
+                *reinterpret_cast<const float4*>(Ps + r * 32 + (((cc0 >> 2) ^ (r & 7)) << 2));
+            const float fv[4] = {fb.x, fb.y, fb.z, fb.w}, pv[4] = {pc.x, pc.y, pc.z, pc.w};
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(fv[x], pv[y], acc[x][y]);
+          }
+        }
+        epi_sync();  // Ps is reused for the partial tiles
+        float* red = Ps;  // groups x m2 x m3 <= 16 tiles x 128 threads
+        if (g < groups) {
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y)
+              if (b0 + x < m2 && cc0 + y < m3) red[(g * m2 + b0 + x) * m3 + cc0 + y] = acc[x][y];
+        }
+        epi_sync();
+        const int n = m2 * m3;
+        float* yo = ep.y1 + tile * n;
+        for (int e = et; e < n; e += 128) {
+          float y = 0.f;
+          for (int q = 0; q < groups; ++q) y += red[q * n + e];
+          yo[e] = y;
+        }
+        epi_sync();  // red and Fs are free for the next tile
+      }
     }
   } else if constexpr (L::kTf32) {
     // ---- TF32 split of A (warps 6-9): A <- x_hi in place, x_lo to its ring ----
@@ -651,17 +773,17 @@ int make_map(CUtensorMap* tm, CUtensorMapDataType dt, const void* base, uint64_t
   return NNC_OK;
 }
 
-template <int KIND, bool kMN, int NP>
+template <int KIND, bool kMN, int NP, bool FUSE>
 int launch_pass(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& blo, int nk,
                 int64_t tiles, const TcEpilogue& ep, int* err, cudaStream_t s) {
-  constexpr int smem = TcLayout<KIND, NP>::kSmem;
-  NNC_CUDA_TRY(raise_smem_limit((const void*)tc_pass_kernel<KIND, kMN, NP>, smem));
+  constexpr int smem = TcLayout<KIND, NP, FUSE>::kSmem;
+  NNC_CUDA_TRY(raise_smem_limit((const void*)tc_pass_kernel<KIND, kMN, NP, FUSE>, smem));
   // Fewest CTAs that keep the largest tile count per CTA of a full-GPU grid:
   // the time is the same, and the SMs left over run the small kernels of the
   // sweep that the graph places beside the pass.
   const int64_t per = ceil_div(tiles, (int64_t)device_sm_count());
   const int64_t grid = ceil_div(tiles, per);
-  NNC_CUDA_TRY(launch_pdl(tc_pass_kernel<KIND, kMN, NP>, dim3(static_cast<unsigned>(grid)),
+  NNC_CUDA_TRY(launch_pdl(tc_pass_kernel<KIND, kMN, NP, FUSE>, dim3(static_cast<unsigned>(grid)),
                           dim3(kThreadsTc), smem, s, a, b, blo, nk, tiles, ep, err));
   note_launch(s);
   return NNC_OK;
@@ -670,8 +792,11 @@ int launch_pass(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& b
 template <int KIND, bool kMN>
 int launch_np(int np, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& blo, int nk,
               int64_t tiles, const TcEpilogue& ep, int* err, cudaStream_t s) {
-  if (np == 32) return launch_pass<KIND, kMN, 32>(a, b, blo, nk, tiles, ep, err, s);
-  return launch_pass<KIND, kMN, 64>(a, b, blo, nk, tiles, ep, err, s);
+  if constexpr (!kMN) {
+    if (ep.y1) return launch_pass<KIND, kMN, 32, true>(a, b, blo, nk, tiles, ep, err, s);
+  }
+  if (np == 32) return launch_pass<KIND, kMN, 32, false>(a, b, blo, nk, tiles, ep, err, s);
+  return launch_pass<KIND, kMN, 64, false>(a, b, blo, nk, tiles, ep, err, s);
 }
 
 }  // namespace
@@ -779,7 +904,12 @@ int TcPlan::convert_b1(const float* F1, cudaStream_t s) const {
   return NNC_OK;
 }
 
-int TcPlan::pass3(const float* F3, float* P3, cudaStream_t s, bool convert) const {
+bool TcPlan::y1_fusable(int m2) const {
+  return np3 == 32 && m2 >= 1 && m2 <= 32 && N2 % 128 == 0;
+}
+
+int TcPlan::pass3(const float* F3, float* P3, cudaStream_t s, bool convert, const float* F2,
+                  int m2, float* Y1) const {
   if (convert) NNC_TRY(convert_b3(F3, s));
   TcEpilogue ep{};
   ep.out = P3;
@@ -787,6 +917,13 @@ int TcPlan::pass3(const float* F3, float* P3, cudaStream_t s, bool convert) cons
   ep.rows = N1 * N2;
   ep.rows_per_slice = N2;
   ep.row_scale = kind == kKindBf16 ? scale : nullptr;
+  if (Y1) {
+    if (!F2 || !y1_fusable(m2)) return NNC_ERR_UNSUPPORTED;
+    ep.y1 = Y1;
+    ep.f2 = F2;
+    ep.m2 = m2;
+    ep.y_nh = N2 / 128;
+  }
   const int64_t tiles = ceil_div(N1 * N2, 128);
   const int stagek = kind == kKindBf16 ? 64 : 32;
   const int nk = static_cast<int>(ceil_div(N3, stagek));

@@ -29,6 +29,14 @@ struct TcEpilogue {
   //   out has rows (k, j): out[(k n2 + j) q + col]
   int p1_layout;
   int64_t kp, n2, n3, slab;
+  // Optional, pass X x_3 F3^T with N2 % 128 == 0 and m2, m3 <= 32: each tile
+  // (one slab i, rows j0 .. j0 + 127, j0 = 128 (tile % y_nh)) also writes
+  //   y1[tile m2 m3 + b m3 + c] = sum_r f2[(j0 + r) m2 + b] P3[i, j0 + r, c],
+  // the tile's share of Y1[i] = F2^T P3[i, :, :] (y_nh = N2 / 128 tiles per slab).
+  float* y1;
+  const float* f2;
+  int m2;
+  int64_t y_nh;
 };
 
 // Operands and TMA descriptors of the two passes over a 3-way FP32 X.
@@ -60,7 +68,11 @@ struct TcPlan {
   int convert_b3(const float* F3, cudaStream_t s) const;
   int convert_b1(const float* F1, cudaStream_t s) const;
   // P3 = X x_3 F3^T ((N1 N2) x m3, FP32); convert first builds the B operand.
-  int pass3(const float* F3, float* P3, cudaStream_t s, bool convert = true) const;
+  // With Y1 (y1_fusable(m2) only) the pass also writes the per-tile shares of
+  // Y1[i] = F2^T P3[i, :, :] (see TcEpilogue::y1).
+  int pass3(const float* F3, float* P3, cudaStream_t s, bool convert = true,
+            const float* F2 = nullptr, int m2 = 0, float* Y1 = nullptr) const;
+  bool y1_fusable(int m2) const;
   // P1 = X x_1 F1^T (FP32; m1 x N2 x N3, or rows (k, j) with p1_kj).
   int pass1(const float* F1, float* P1, cudaStream_t s, bool convert = true) const;
   // Synchronises s and turns a device-side pipeline time-out into NNC_ERR_TIMEOUT.

@@ -85,7 +85,8 @@ def test_mode_product_tensor_cores_rejects_middle_mode():
 
 
 @pytest.mark.parametrize("dims,m,iters,refine", [((96, 80, 128), (8, 10, 12), 60, 10),
-                                                 ((150, 64, 200), (16, 12, 20), 40, 0)])
+                                                 ((150, 64, 200), (16, 12, 20), 40, 0),
+                                                 ((96, 128, 128), (8, 10, 12), 60, 10)])
 def test_ntd_bf16_refine_parity(dims, m, iters, refine):
     X, _, F0, G0, _ = inputs.small_problem(dims, 6, m, 4, seed=606, dist="exponential")
     Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
@@ -112,9 +113,11 @@ def test_ntd_bf16_full_size_cp16_512cube():
     assert np.max(np.abs(tr.cpu().numpy() - tro)) <= 1e-3
 
 
-def test_ntd_fp32_tensor_cores_match_simt():
-    # NNC_FP32 (TF32x3 passes) and NNC_FP32_SIMT agree to FP32 rounding.
-    X, _, F0, G0, _ = inputs.small_problem((64, 48, 80), 5, (8, 6, 12), 4, seed=808, noise=0.02)
+@pytest.mark.parametrize("dims,m", [((64, 48, 80), (8, 6, 12)), ((40, 128, 36), (6, 9, 5))])
+def test_ntd_fp32_tensor_cores_match_simt(dims, m):
+    # NNC_FP32 (TF32x3 passes) and NNC_FP32_SIMT agree to FP32 rounding (N2 = 128:
+    # the pass also forms the mode-1 contraction).
+    X, _, F0, G0, _ = inputs.small_problem(dims, 5, m, 4, seed=808, noise=0.02)
     out = {}
     for prec in ("fp32", "fp32_simt"):
         Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
