@@ -223,11 +223,11 @@ int count_kernel_nodes(cudaGraph_t graph, long long* n_kernels) {
 struct GraphRun {
   cudaStream_t cs = nullptr;
   Branch br;
-  cudaGraph_t graph[2] = {};
-  cudaGraphExec_t exec[2] = {};
+  cudaGraph_t graph[3] = {};    // one sweep, the instrumented sweep, kSweepsPerGraph sweeps
+  cudaGraphExec_t exec[3] = {};
   cudaEvent_t fork = nullptr, join = nullptr;
   ~GraphRun() {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
       if (exec[k]) cudaGraphExecDestroy(exec[k]);
       if (graph[k]) cudaGraphDestroy(graph[k]);
     }
@@ -249,13 +249,21 @@ struct GraphRun {
 // same kernels on the same data.
 constexpr int kProfileEvery = 16;
 
+// Sweeps per replay of the plain graph: consecutive graph launches leave the
+// GPU idle for a few microseconds, a kernel boundary inside a graph for less.
+// Five keeps every profiled sweep (the last of kProfileEvery) on its own.
+constexpr int kSweepsPerGraph = 5;
+static_assert(kProfileEvery % kSweepsPerGraph == 1, "sampled sweeps fall between graphs");
+
 template <typename T>
 int capture_sweep(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* trace,
                   const PassEvents* ev, const tc::TcPlan* tcp, bool prev_core, GraphRun& g,
-                  int slot) {
+                  int slot, int nsweeps = 1) {
   NNC_CUDA_TRY(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
-  const int cap_st = sweep3<T>(X, F, G, b, eps, trace ? trace : b.trace_dummy, trace ? 1 : 0, ev,
-                               tcp, prev_core, g.br, g.cs);
+  int cap_st = NNC_OK;
+  for (int k = 0; k < nsweeps && cap_st == NNC_OK; ++k)
+    cap_st = sweep3<T>(X, F, G, b, eps, trace ? trace : b.trace_dummy, trace ? 1 : 0, ev, tcp,
+                       prev_core, g.br, g.cs);
   const cudaError_t end_e = cudaStreamEndCapture(g.cs, &g.graph[slot]);
   if (cap_st != NNC_OK) return cap_st;
   NNC_CUDA_TRY(end_e);
@@ -285,8 +293,12 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
   NNC_CUDA_TRY(cudaStreamWaitEvent(g.cs, g.fork, 0));
 
   NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, nullptr, tcp, true, g, 0));
-  long long kn[2] = {0, 0};
+  long long kn[3] = {0, 0, 0};
   NNC_TRY(count_kernel_nodes(g.graph[0], &kn[0]));
+  if (count >= kSweepsPerGraph) {
+    NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, nullptr, tcp, true, g, 2, kSweepsPerGraph));
+    NNC_TRY(count_kernel_nodes(g.graph[2], &kn[2]));
+  }
 
   // Sampled sweeps: the last of every kProfileEvery (an instrumented copy,
   // captured once the first plain replays are queued, so the device is busy
@@ -295,7 +307,15 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
   const int samples = profile_enabled() ? count / kProfileEvery : 0;
   long long kernels = 0;
   for (int t = 0; t < count; ++t) {
-    if (samples > 0 && t % kProfileEvery == kProfileEvery - 1) {
+    const bool sampled = samples > 0 && t % kProfileEvery == kProfileEvery - 1;
+    if (!sampled && g.exec[2] && t + kSweepsPerGraph <= count &&
+        (samples == 0 || t % kProfileEvery + kSweepsPerGraph <= kProfileEvery - 1)) {
+      NNC_CUDA_TRY(cudaGraphLaunch(g.exec[2], g.cs));
+      kernels += kn[2];
+      t += kSweepsPerGraph - 1;
+      continue;
+    }
+    if (sampled) {
       const int j = t / kProfileEvery;
       if (j == 0) {
         NNC_TRY(prof.init(samples));
