@@ -7,10 +7,11 @@
 //   pass 1   P3 = X x_3 F3^T                          (first read of X)
 //   upd 1    Num1 = unfold_1(P3 x_2 F2^T) unfold_1(G)^T,  Den1 = F1 H1
 //   hmat 2   H2 = unfold_2(G x_1 S1 x_3 S3) unfold_2(G)^T
-//   upd 2    Num2 from P3 x_1 F1^T (new F1),  Den2 = F2 H2
+//   upd 2    Num2 from P3 x_1 F1^T (new F1),  Den2 = F2 H2  (numerator beside H2)
 //   hmat 3   H3 from W3 = G x_1 S1 x_2 S2 (W3 kept)
 //   pass 2   P1 = X x_1 F1^T (new F1), rows (k, j)     (second read of X)
 //   upd 3    Y3 = P1 x_2 F2^T (new F2);  Num3 = unfold_3(Y3) unfold_3(G)^T;  Den3 = F3 H3
+//            (numerator beside H3)
 //   core     M = Y3 x_3 F3^T = X x_1 F1^T x_2 F2^T x_3 F3^T;
 //            G <- MU(G, M, W3 x_3 S3); trace; next H1       (core_a, core_b)
 // with S_k = F_k^T F_k. The kernels are in sweep.cu; the passes are SIMT mode
@@ -18,8 +19,8 @@
 // BF16 copy of X (tc_ttm.cu). Two reads of X per sweep is the minimum under
 // the Gauss-Seidel order: pass 2 needs the F^(1) that pass 1 leads to.
 //
-// The sweep is captured once as a CUDA graph on a private stream and replayed;
-// the trace slot advances through a device counter. NNC_FP32 runs the passes
+// The sweep is captured as a CUDA graph on a private stream (several sweeps to
+// a graph) and replayed; the trace slot advances through a device counter. NNC_FP32 runs the passes
 // as FP32-accurate TF32x3 tensor-core products; NNC_BF16_REFINE replays the
 // BF16 tensor-core sweep for iters - refine_iters sweeps and then the TF32x3
 // sweep for the rest; NNC_FP32_SIMT and NNC_FP64 use the SIMT passes.
@@ -44,10 +45,12 @@ struct NtdState {
   // P3 rows (i, j) x m3; P1 rows (k, j) x m1 (SIMT passes: P1s, laid out
   // (m1, N2, N3), is the pass result that P1 is copied from)
   T *P3, *P1, *P1s, *Y3, *M, *W1, *W3, *G2, *G3, *H[3], *S[3];
-  // Shares of Y1[i] = F2^T P3[i] from the tensor-core pass (y1_nh per slab;
-  // NULL: upd12 forms Y1 from P3)
+  T *num2, *num3;  // numerators of the split mode-2 and mode-3 updates
+  // Shares of Y1[i] = F2^T P3[i] and of Y3[k] = P1[k]^T F2 from the
+  // tensor-core passes (y_nh = N2 / 128 per slab; NULL: upd12 forms them)
   T* Y1p;
-  int y1_nh;
+  T* Y3p;
+  int y_nh;
   double *stats_part, *stats, *trace_dummy, *resid2, *dots;
   int* counter;
   int* done;
@@ -71,10 +74,13 @@ int pass_x3(const T* X, const NtdState<T>& b, const T* F3, const T* F2, const tc
 }
 
 template <typename T>
-int pass_x1(const T* X, const NtdState<T>& b, const T* F1, const tc::TcPlan* tcp,
+int pass_x1(const T* X, const NtdState<T>& b, const T* F1, const T* F2, const tc::TcPlan* tcp,
             cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
-    if (tcp) return tcp->pass1(F1, b.P1, s, /*convert=*/false);
+    if (tcp) {
+      if (F2) return tcp->pass1(F1, b.P1, s, /*convert=*/false, F2, b.m[1], b.Y3p);
+      return tcp->pass1(F1, b.P1, s, /*convert=*/false);
+    }
   }
   NNC_CUDA_TRY(launch_ttm<T>(X, 1, (int)b.N[0], b.N[1] * b.N[2], F1, b.m[0], 1, b.m[0], b.P1s,
                              nullptr, 0, s));
@@ -94,18 +100,19 @@ int launch_sweep_core(T* const* F, T* G, NtdState<T>& b, double eps, double* tra
   return launch_core<T>(c, s);
 }
 
-// Side stream and fork/join events of the two concurrent branches of a sweep.
+// Side streams and fork/join events of the concurrent branches of a sweep.
 struct Branch {
-  cudaStream_t s2 = nullptr;
-  cudaEvent_t fork[2] = {}, join[2] = {};
+  cudaStream_t s2 = nullptr, s3 = nullptr;
+  cudaEvent_t fork[2] = {}, join[2] = {}, mid[2] = {};
 };
 
 // One sweep without its core update, which the next sweep runs (or the caller
-// after the last one). Two pieces run beside the passes on a second stream:
+// after the last one). Beside the passes, on side streams:
 //   pass 1 (X x_3 F3^T)  beside  the previous sweep's core update (G, H1, trace):
 //                        the pass needs only F3;
-//   pass 2 (X x_1 F1^T)  beside  H2, the mode-2 update and H3: the pass needs
-//                        only the new F1.
+//   pass 2 (X x_1 F1^T)  beside  H3 (and, when it forms the mode-3 shares and so
+//                        waits for the new F2, nothing else; otherwise beside
+//                        H2, the mode-2 numerator and the MU step on F2 too).
 // The passes leave SMs free when that costs them nothing (tc_ttm.cu), and the
 // small kernels run there.
 template <typename T>
@@ -133,7 +140,7 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     u.Gn = G;    // rows a of G are (b, c)-contiguous
     if (tcp && b.Y1p && tcp->y1_fusable(m2)) {  // the pass formed Y1's shares
       u.Ypart = b.Y1p;
-      u.nparts = b.y1_nh;
+      u.nparts = b.y_nh;
     }
     u.F = F[0];  u.nrows = N1;  u.mv = m1;  u.H = b.H[0];  u.eps = eps;
     if constexpr (std::is_same<T, float>::value) {
@@ -147,9 +154,24 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     }
     NNC_TRY(launch_upd12<T>(u, s));
   }
-  // ---- modes 2 (side stream) beside pass 2 -------------------------------------
+  // ---- modes 2 and 3 --------------------------------------------------------
+  // The numerators do not need H_n, so the mode-2 update is split in two: the
+  // GEMM and the numerator (upd12, num_only) run beside the kernel forming H2,
+  // and a row-wise MU step follows.
+  //   s2:  H2 ................ MU on F2 | H3 (S2 of the new F2)
+  //   s3:  Num2 (P3, new F1) --^
+  // When pass 2 can also form the shares of Y3[k] = P1[k]^T F2 (TF32x3 with
+  // N2 % 128 == 0, m <= 32), it waits for the new F2 and the mode-3 update
+  // only adds the shares; H3 runs beside the pass:
+  //   s:   pass 2 (new F1, new F2) -- mode 3 (shares, H3)
+  // Otherwise pass 2 runs beside the mode-2 branch and the mode-3 numerator
+  // beside H3:
+  //   s:   pass 2 (new F1) ....... Num3 (P1, new F2) -- MU on F3
+  bool y3f = false;
+  if constexpr (std::is_same<T, float>::value) y3f = tcp && b.Y3p && tcp->y3_fusable(m2);
   NNC_CUDA_TRY(cudaEventRecord(br.fork[1], s));
   NNC_CUDA_TRY(cudaStreamWaitEvent(br.s2, br.fork[1], 0));
+  NNC_CUDA_TRY(cudaStreamWaitEvent(br.s3, br.fork[1], 0));
   {  // H2 from S1 = F1^T F1 (new F1) and S3
     HArgs<T> h{};
     h.Gn = b.G2;  h.mp = m2;  h.mu = m1;  h.mv = m3;
@@ -158,14 +180,19 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     h.H = b.H[1];
     NNC_TRY(launch_hmat<T>(h, br.s2));
   }
-  {
-    UpdArgs<T> u{};
-    u.P = b.P3;  u.prow = m3;  u.pstride = N2 * m3;  // row j, contraction over i
-    u.Fc = F[0]; u.len = (int)N1;  u.mu = m1;  u.mc = m3;
-    u.Gn = b.G2;  // rows b of G2 are (a, c)-contiguous
-    u.F = F[1];  u.nrows = N2;  u.mv = m2;  u.H = b.H[1];  u.eps = eps;
-    NNC_TRY(launch_upd12<T>(u, br.s2));
-  }
+  UpdArgs<T> u2{};
+  u2.P = b.P3;  u2.prow = m3;  u2.pstride = N2 * m3;  // row j, contraction over i
+  u2.Fc = F[0]; u2.len = (int)N1;  u2.mu = m1;  u2.mc = m3;
+  u2.Gn = b.G2;  // rows b of G2 are (a, c)-contiguous
+  u2.F = F[1];  u2.nrows = N2;  u2.mv = m2;  u2.H = b.H[1];  u2.eps = eps;
+  u2.num = b.num2;
+  u2.num_only = 1;
+  NNC_TRY(launch_upd12<T>(u2, br.s3));
+  NNC_CUDA_TRY(cudaEventRecord(br.mid[0], br.s3));
+  NNC_CUDA_TRY(cudaStreamWaitEvent(br.s2, br.mid[0], 0));
+  u2.num_only = 0;
+  NNC_TRY(launch_mu_rows<T>(u2, br.s2));
+  NNC_CUDA_TRY(cudaEventRecord(br.mid[1], br.s2));  // the new F2
   {  // H3 and W3 = G x_1 S1 x_2 S2, with S2 = F2^T F2 (new F2)
     HArgs<T> h{};
     h.Gn = b.G3;  h.mp = m3;  h.mu = m1;  h.mv = m2;
@@ -177,28 +204,40 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     NNC_TRY(launch_hmat<T>(h, br.s2));
   }
   NNC_CUDA_TRY(cudaEventRecord(br.join[1], br.s2));
+  if (y3f) NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.mid[1], 0));
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->start[1], s, cudaEventRecordExternal));
-  NNC_TRY(pass_x1<T>(X, b, F[0], tcp, s));
+  NNC_TRY(pass_x1<T>(X, b, F[0], y3f ? F[1] : nullptr, tcp, s));
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->stop[1], s, cudaEventRecordExternal));
-  NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.join[1], 0));
-  // ---- mode 3 ----------------------------------------------------------------
-  {
-    UpdArgs<T> u{};
-    u.P = b.P1;  u.prow = N2 * m1;  u.pstride = m1;  // P1[k, j, a]
-    u.Fc = F[1]; u.len = (int)N2;   u.mu = m1;  u.mc = m2;  u.p_first = 1;
-    u.Gn = b.G3;  // rows c of G3 are (a, b)-contiguous
-    u.Yout = b.Y3;
-    u.gate_out = b.gate;
-    u.F = F[2];  u.nrows = N3;  u.mv = m3;  u.H = b.H[2];  u.eps = eps;
-    if constexpr (std::is_same<T, float>::value) {
-      if (tcp) {
-        u.bt = tcp->Bt3;
-        u.bhi = tcp->B3hi;
-        u.blo = tcp->B3lo;
-        u.bt_ld = tcp->kb3;
-      }
+  UpdArgs<T> u3{};
+  u3.P = b.P1;  u3.prow = N2 * m1;  u3.pstride = m1;  // P1[k, j, a]
+  u3.Fc = F[1]; u3.len = (int)N2;   u3.mu = m1;  u3.mc = m2;  u3.p_first = 1;
+  u3.Gn = b.G3;  // rows c of G3 are (a, b)-contiguous
+  u3.Yout = b.Y3;
+  u3.F = F[2];  u3.nrows = N3;  u3.mv = m3;  u3.H = b.H[2];  u3.eps = eps;
+  u3.gate_out = b.gate;
+  if constexpr (std::is_same<T, float>::value) {
+    if (tcp) {
+      u3.bt = tcp->Bt3;
+      u3.bhi = tcp->B3hi;
+      u3.blo = tcp->B3lo;
+      u3.bt_ld = tcp->kb3;
     }
-    NNC_TRY(launch_upd12<T>(u, s));
+  }
+  if (y3f) {
+    u3.Ypart = b.Y3p;
+    u3.nparts = b.y_nh;
+    NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.join[1], 0));
+    NNC_TRY(launch_upd12<T>(u3, s));
+  } else {
+    NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.mid[1], 0));
+    u3.num = b.num3;
+    u3.num_only = 1;
+    u3.gate_out = nullptr;
+    NNC_TRY(launch_upd12<T>(u3, s));
+    NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.join[1], 0));
+    u3.num_only = 0;
+    u3.gate_out = b.gate;
+    NNC_TRY(launch_mu_rows<T>(u3, s));
   }
   return NNC_OK;
 }
@@ -234,10 +273,12 @@ struct GraphRun {
     for (int k = 0; k < 2; ++k) {
       if (br.fork[k]) cudaEventDestroy(br.fork[k]);
       if (br.join[k]) cudaEventDestroy(br.join[k]);
+      if (br.mid[k]) cudaEventDestroy(br.mid[k]);
     }
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
     if (br.s2) cudaStreamDestroy(br.s2);
+    if (br.s3) cudaStreamDestroy(br.s3);
     if (cs) cudaStreamDestroy(cs);
   }
 };
@@ -283,9 +324,11 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
   GraphRun g;
   NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
   NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.br.s2, cudaStreamNonBlocking));
+  NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.br.s3, cudaStreamNonBlocking));
   for (int k = 0; k < 2; ++k) {
     NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.br.fork[k], cudaEventDisableTiming));
     NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.br.join[k], cudaEventDisableTiming));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.br.mid[k], cudaEventDisableTiming));
   }
   NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming));
   NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming));
@@ -377,6 +420,8 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   NNC_TRY(sc.get(&b.P3, (size_t)(N1 * N2 * m3)));
   NNC_TRY(sc.get(&b.P1, (size_t)(m1 * N2 * N3)));
   NNC_TRY(sc.get(&b.Y3, (size_t)((int64_t)m1 * m2 * N3)));
+  NNC_TRY(sc.get(&b.num2, (size_t)(N2 * m2)));
+  NNC_TRY(sc.get(&b.num3, (size_t)(N3 * m3)));
   NNC_TRY(sc.get(&b.M, (size_t)nc));
   NNC_TRY(sc.get(&b.W1, (size_t)nc));
   NNC_TRY(sc.get(&b.W3, (size_t)nc));
@@ -408,8 +453,12 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
     // see the same shape).
     const tc::TcPlan* any = exact ? exact : fast;
     if (any && any->y1_fusable(m2)) {
-      b.y1_nh = (int)(N2 / 128);
-      NNC_TRY(sc.get(&b.Y1p, (size_t)(N1 * b.y1_nh) * m2 * m3));
+      b.y_nh = (int)(N2 / 128);
+      NNC_TRY(sc.get(&b.Y1p, (size_t)(N1 * b.y_nh) * m2 * m3));
+    }
+    if ((exact && exact->y3_fusable(m2)) || (fast && fast->y3_fusable(m2))) {
+      b.y_nh = (int)(N2 / 128);
+      NNC_TRY(sc.get(&b.Y3p, (size_t)(N3 * b.y_nh) * m1 * m2));
     }
   }
 

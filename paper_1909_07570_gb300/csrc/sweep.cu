@@ -349,8 +349,10 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
 
   // Everything but the GEMM operands is requested first; the GEMM's waits
   // cover this group too.
-  cp_flat(hs, a.H, MV * MV);
-  cp_flat(fo, a.F + r * MV, MV);
+  if (!a.num_only) {
+    cp_flat(hs, a.H, MV * MV);
+    cp_flat(fo, a.F + r * MV, MV);
+  }
   if (gsm) cp_flat(gs, a.Gn, (int64_t)MV * UC);
   cp_commit();
   if (a.Ypart) {
@@ -373,6 +375,10 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
 
   if (a.Yout)
     for (int e = threadIdx.x; e < UC; e += blockDim.x) a.Yout[r * UC + e] = ys[e];
+  if (a.num_only) {
+    rows_dot(ys, gsm ? (const T*)gs : a.Gn, UC, MV, a.num + r * MV);
+    return;
+  }
   rows_dot(ys, gsm ? (const T*)gs : a.Gn, UC, MV, nm);
   __syncthreads();
   for (int v = threadIdx.x; v < MV; v += blockDim.x) {
@@ -383,6 +389,36 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
     write_operand(a, r, v, nv);
   }
   if (a.gate_out && r == 0 && threadIdx.x == 0) *a.gate_out = 1;
+}
+
+// ---------------------------------------------------------------------------
+// mu_rows: the MU step of a split update, kThreads / mv rows per block.
+//   F[r, v] <- MU(F[r, v], num[r, v], sum_w F[r, w] H[w, v])
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) mu_rows_kernel(UpdArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int MV = a.mv, R = kThreads / MV;
+  T* hs = sm;                  // MV x MV
+  T* fo = hs + al4(MV * MV);   // R x MV: the old rows
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int rn = (int)min((int64_t)R, a.nrows - r0);
+  cp_flat(hs, a.H, MV * MV);
+  cp_flat(fo, a.F + r0 * MV, (int64_t)rn * MV);
+  cp_commit();
+  cp_wait<0>();
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < rn * MV) {
+    const int rr = t / MV, v = t % MV;
+    T den = T(0);
+    for (int w = 0; w < MV; ++w) den = fma(fo[rr * MV + w], hs[w * MV + v], den);
+    const T nv = mu_step(fo[t], a.num[r0 * MV + t], den, (T)a.eps);
+    a.F[r0 * MV + t] = nv;
+    write_operand(a, r0 + rr, v, nv);
+  }
+  if (a.gate_out && r0 == 0 && t == 0) *a.gate_out = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -627,6 +663,18 @@ int launch_upd12(const UpdArgs<T>& a, cudaStream_t s) {
 }
 
 template <typename T>
+int launch_mu_rows(const UpdArgs<T>& a, cudaStream_t s) {
+  if (a.mv > 64 || a.mv < 1 || !a.num) return NNC_ERR_UNSUPPORTED;
+  const int R = kThreads / a.mv;
+  const size_t smem = sizeof(T) * (al4(a.mv * a.mv) + al4((size_t)R * a.mv));
+  NNC_TRY(set_smem(mu_rows_kernel<T>, smem));
+  mu_rows_kernel<T><<<(unsigned)ceil_div(a.nrows, (int64_t)R), kThreads, smem, s>>>(a);
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  return NNC_OK;
+}
+
+template <typename T>
 int launch_hmat(const HArgs<T>& a, cudaStream_t s) {
   if (a.mu > 64 || a.mv > 64) return NNC_ERR_UNSUPPORTED;
   const size_t st_u = a.fu ? gemm_stage_elems(a.mu, a.mu, (int)sizeof(T), (int)a.nu) : 0;
@@ -699,6 +747,7 @@ int launch_permute_core(const T* G, int m1, int m2, int m3, T* G2, T* G3, cudaSt
 #define NNC_SWEEP_INST(T)                                                                   \
   template int launch_upd12<T>(const UpdArgs<T>&, cudaStream_t);                            \
   template int launch_hmat<T>(const HArgs<T>&, cudaStream_t);                               \
+  template int launch_mu_rows<T>(const UpdArgs<T>&, cudaStream_t);                          \
   template int launch_p1_rows<T>(const T*, int, int64_t, int64_t, T*, cudaStream_t);       \
   template int launch_core<T>(const CoreArgs<T>&, cudaStream_t);                            \
   template int launch_gram<T>(const T*, int64_t, int, T*, cudaStream_t);                    \

@@ -41,6 +41,11 @@ struct UpdArgs {
   int64_t bt_ld;
   const float* bt_scale;
   int* gate_out;  // optional: set to 1 (mode 3: the sweep's core update is pending)
+  // Split update: upd12 with num_only stores Num (nrows x mv) in `num` and
+  // leaves F alone; mu_rows then applies the MU step from `num` and H (the
+  // numerator does not need H, so the two can run beside the kernel forming H).
+  int num_only;
+  T* num;
 };
 
 // H_n = unfold_n(G x_u S_u x_v S_v) unfold_n(G)^T, one block per index p of mode n.
@@ -95,6 +100,10 @@ template <typename T>
 int launch_upd12(const UpdArgs<T>& a, cudaStream_t s);
 template <typename T>
 int launch_hmat(const HArgs<T>& a, cudaStream_t s);
+// F[r] <- MU(F[r], num[r], F[r] H) for every row, with the operand writes and
+// gate of UpdArgs (fields P, Fc, Gn, Ypart, Yout unused).
+template <typename T>
+int launch_mu_rows(const UpdArgs<T>& a, cudaStream_t s);
 // P1 rows (k, j): out[(k N2 + j) m1 + a] = in[(a N2 + j) N3 + k].
 template <typename T>
 int launch_p1_rows(const T* in, int m1, int64_t N2, int64_t N3, T* out, cudaStream_t s);

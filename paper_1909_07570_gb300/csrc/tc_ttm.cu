@@ -415,8 +415,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // ---- epilogue (warps 2-5) ------------------------------------------------
     const int quarter = warp & 3;  // TMEM lanes 32 quarter .. 32 quarter + 31
     const int lr = quarter * 32 + lane;  // tile row of this thread
-    float* Ps = reinterpret_cast<float*>(base + L::kOffEpi);  // FUSE: 128 x 32 P3 rows
-    float* Fs = Ps + 128 * 32;                                // FUSE: 128 x 32 F2 rows
+    float* Ps = reinterpret_cast<float*>(base + L::kOffEpi);  // FUSE: 128 x 32 pass rows
+    float* Fs = Ps + 128 * 32;                                // FUSE: 128 x 32 factor rows
+    // FUSE: the factor may come from the preceding grid.
+    if constexpr (FUSE) pdl_wait();
     int tcount = 0;
     int64_t fs_slice = -1;  // FUSE: the j range whose F2 rows Fs holds
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
@@ -428,18 +430,18 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           // the tiles per slab); the previous tile ended with a barrier.
           fs_slice = tile % ep.y_nh;
           const int64_t j = fs_slice * 128 + lr;
-          const float* f = ep.f2 + j * ep.m2;
+          const float* f = ep.yf + j * ep.yf_m;
           float fr[32];
-          if ((ep.m2 & 3) == 0 && (reinterpret_cast<uintptr_t>(f) & 15) == 0) {
+          if ((ep.yf_m & 3) == 0 && (reinterpret_cast<uintptr_t>(f) & 15) == 0) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-              const float4 q = 4 * c < ep.m2 ? *reinterpret_cast<const float4*>(f + 4 * c)
+              const float4 q = 4 * c < ep.yf_m ? *reinterpret_cast<const float4*>(f + 4 * c)
                                              : make_float4(0.f, 0.f, 0.f, 0.f);
               fr[4 * c] = q.x; fr[4 * c + 1] = q.y; fr[4 * c + 2] = q.z; fr[4 * c + 3] = q.w;
             }
           } else {
 #pragma unroll
-            for (int b = 0; b < 32; ++b) fr[b] = b < ep.m2 ? f[b] : 0.f;
+            for (int b = 0; b < 32; ++b) fr[b] = b < ep.yf_m ? f[b] : 0.f;
           }
           // Rows of 8 float4 chunks, chunk c stored at c ^ (row & 7): the
           // row-per-thread stores and the chunk reads below avoid bank conflicts.
@@ -539,12 +541,12 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       __syncwarp();
       if (lane == 0) mbar_arrive(&accempty[buf]);
       if constexpr (FUSE) {
-        // Mode-1 contraction of the tile (one slab i, rows j0 .. j0 + 127):
-        //   Y1p[tile][b, c] = sum_r F2[j0 + r, b] P3[i, j0 + r, c]
+        // Contraction of the tile (one slab s, rows j0 .. j0 + 127):
+        //   share[b, c] = sum_r F[j0 + r, b] P[(s, j0 + r), c]
         // 4 x 4 output tiles per thread, rows split over `groups` thread
         // groups whose partial tiles are added in group order.
         const int et = threadIdx.x - 64;  // 0 .. 127
-        const int m2 = ep.m2, m3 = ep.q, tq = (m3 + 3) / 4;
+        const int m2 = ep.yf_m, m3 = ep.q, tq = (m3 + 3) / 4;
         const int tiles = ((m2 + 3) / 4) * tq, groups = 128 / tiles;
         const int g = et / tiles, t = et % tiles;
         const int b0 = (t / tq) * 4, cc0 = (t % tq) * 4;
@@ -579,11 +581,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         epi_sync();
         const int n = m2 * m3;
-        float* yo = ep.y1 + tile * n;
+        float* yo = ep.ysh + tile * n;
         for (int e = et; e < n; e += 128) {
           float y = 0.f;
           for (int q = 0; q < groups; ++q) y += red[q * n + e];
-          yo[e] = y;
+          yo[ep.y_tr ? (e % m3) * m2 + e / m3 : e] = y;
         }
         epi_sync();  // red and Fs are free for the next tile
       }
@@ -793,7 +795,7 @@ template <int KIND, bool kMN>
 int launch_np(int np, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& blo, int nk,
               int64_t tiles, const TcEpilogue& ep, int* err, cudaStream_t s) {
   if constexpr (!kMN) {
-    if (ep.y1) return launch_pass<KIND, kMN, 32, true>(a, b, blo, nk, tiles, ep, err, s);
+    if (ep.ysh) return launch_pass<KIND, kMN, 32, true>(a, b, blo, nk, tiles, ep, err, s);
   }
   if (np == 32) return launch_pass<KIND, kMN, 32, false>(a, b, blo, nk, tiles, ep, err, s);
   return launch_pass<KIND, kMN, 64, false>(a, b, blo, nk, tiles, ep, err, s);
@@ -908,6 +910,12 @@ bool TcPlan::y1_fusable(int m2) const {
   return np3 == 32 && m2 >= 1 && m2 <= 32 && N2 % 128 == 0;
 }
 
+bool TcPlan::y3_fusable(int m2) const {
+  // Tiles of pass 2 are single (k, j0 .. j0 + 127) row blocks only when read
+  // from the (k, j)-ordered Xt.
+  return kind == kKindTf32x3 && p1_kj && np1 == 32 && m2 >= 1 && m2 <= 32 && N2 % 128 == 0;
+}
+
 int TcPlan::pass3(const float* F3, float* P3, cudaStream_t s, bool convert, const float* F2,
                   int m2, float* Y1) const {
   if (convert) NNC_TRY(convert_b3(F3, s));
@@ -919,9 +927,9 @@ int TcPlan::pass3(const float* F3, float* P3, cudaStream_t s, bool convert, cons
   ep.row_scale = kind == kKindBf16 ? scale : nullptr;
   if (Y1) {
     if (!F2 || !y1_fusable(m2)) return NNC_ERR_UNSUPPORTED;
-    ep.y1 = Y1;
-    ep.f2 = F2;
-    ep.m2 = m2;
+    ep.ysh = Y1;
+    ep.yf = F2;
+    ep.yf_m = m2;
     ep.y_nh = N2 / 128;
   }
   const int64_t tiles = ceil_div(N1 * N2, 128);
@@ -932,7 +940,8 @@ int TcPlan::pass3(const float* F3, float* P3, cudaStream_t s, bool convert, cons
   return launch_np<kKindTf32x3, false>(np3, mapA3, mapB3, mapB3lo, nk, tiles, ep, err, s);
 }
 
-int TcPlan::pass1(const float* F1, float* P1, cudaStream_t s, bool convert) const {
+int TcPlan::pass1(const float* F1, float* P1, cudaStream_t s, bool convert, const float* F2,
+                  int m2, float* Y3) const {
   if (convert) NNC_TRY(convert_b1(F1, s));
   TcEpilogue ep{};
   ep.out = P1;
@@ -948,6 +957,14 @@ int TcPlan::pass1(const float* F1, float* P1, cudaStream_t s, bool convert) cons
   } else {
     ep.p1_layout = 0;  // Xt already has rows (k, j)
     ep.rows = N2 * N3;
+  }
+  if (Y3) {
+    if (!F2 || !y3_fusable(m2)) return NNC_ERR_UNSUPPORTED;
+    ep.ysh = Y3;
+    ep.yf = F2;
+    ep.yf_m = m2;
+    ep.y_tr = 1;  // Y3[k] is stored m1 x m2
+    ep.y_nh = N2 / 128;
   }
   const int64_t tiles = ceil_div(N2 * kp3, 128);
   const int stagek = kind == kKindBf16 ? 64 : 32;

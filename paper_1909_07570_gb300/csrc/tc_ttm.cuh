@@ -29,13 +29,17 @@ struct TcEpilogue {
   //   out has rows (k, j): out[(k n2 + j) q + col]
   int p1_layout;
   int64_t kp, n2, n3, slab;
-  // Optional, pass X x_3 F3^T with N2 % 128 == 0 and m2, m3 <= 32: each tile
-  // (one slab i, rows j0 .. j0 + 127, j0 = 128 (tile % y_nh)) also writes
-  //   y1[tile m2 m3 + b m3 + c] = sum_r f2[(j0 + r) m2 + b] P3[i, j0 + r, c],
-  // the tile's share of Y1[i] = F2^T P3[i, :, :] (y_nh = N2 / 128 tiles per slab).
-  float* y1;
-  const float* f2;
-  int m2;
+  // Optional contraction of each tile with the matching rows of a factor F
+  // (N2 % 128 == 0, q <= 32, yf_m <= 32). Both passes see tiles of 128 rows
+  // (s, j) with j = j0 .. j0 + 127, j0 = 128 (tile % y_nh), y_nh = N2 / 128,
+  // s = i (pass X x_3 F3^T) or k (pass X x_1 F1^T with rows (k, j)). The tile
+  // writes its share of Y[s] = F^T P[s] (yf_m x q), or of its transpose when
+  // y_tr (q x yf_m):
+  //   ysh[tile yf_m q + b q + c] = sum_r yf[(j0 + r) yf_m + b] P[(s, j0 + r), c]
+  float* ysh;
+  const float* yf;
+  int yf_m;
+  int y_tr;
   int64_t y_nh;
 };
 
@@ -69,12 +73,16 @@ struct TcPlan {
   int convert_b1(const float* F1, cudaStream_t s) const;
   // P3 = X x_3 F3^T ((N1 N2) x m3, FP32); convert first builds the B operand.
   // With Y1 (y1_fusable(m2) only) the pass also writes the per-tile shares of
-  // Y1[i] = F2^T P3[i, :, :] (see TcEpilogue::y1).
+  // Y1[i] = F2^T P3[i, :, :] (m2 x m3 each; see TcEpilogue::ysh).
   int pass3(const float* F3, float* P3, cudaStream_t s, bool convert = true,
             const float* F2 = nullptr, int m2 = 0, float* Y1 = nullptr) const;
   bool y1_fusable(int m2) const;
   // P1 = X x_1 F1^T (FP32; m1 x N2 x N3, or rows (k, j) with p1_kj).
-  int pass1(const float* F1, float* P1, cudaStream_t s, bool convert = true) const;
+  // With Y3 (y3_fusable(m2) only: TF32x3 with p1_kj) the pass also writes the
+  // per-tile shares of Y3[k] = P1[k, :, :]^T F2 (m1 x m2 each).
+  int pass1(const float* F1, float* P1, cudaStream_t s, bool convert = true,
+            const float* F2 = nullptr, int m2 = 0, float* Y3 = nullptr) const;
+  bool y3_fusable(int m2) const;
   // Synchronises s and turns a device-side pipeline time-out into NNC_ERR_TIMEOUT.
   int check(cudaStream_t s) const;
 };
