@@ -89,6 +89,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Bounded wait on phase `parity`. False when the limit ran out or another role
 // of this CTA has already failed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
+  if (mbar_try_wait(bar, parity)) return true;  // the common case: no clock read
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*fail) return false;
@@ -196,6 +197,7 @@ struct TcLayout {
   // FP32. The tensor core rounds its FP32 accumulation toward zero once per
   // MMA; shorter chains shrink that bias by kAcc.
   static constexpr int kAcc = kTf32 ? 128 / NP : 1;
+  static_assert((kAcc & (kAcc - 1)) == 0, "accumulator index is taken by a mask");
   // TF32x3 accumulators are 2 NP columns wide: [0, NP) collects x_hi f_hi and
   // x_lo f_hi, [NP, 2 NP) collects x_hi f_lo (one MMA of N = 2 NP against the
   // stacked [f_hi; f_lo] operand).
@@ -361,6 +363,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const uint32_t idesc = instr_desc<KIND, kMN>(NP);
       const uint32_t idesc2 = instr_desc<KIND, kMN>(2 * NP);  // TF32x3: N = 2 NP
       int it = 0, tcount = 0;
+      int rs = 0, rj = 0;         // stage and x_lo slot of `it`
+      uint32_t rph = 0, jph = 0;  // their phase parities
       bool ok = true;
       for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tcount) {
         const int buf = tcount & 1;
@@ -370,42 +374,54 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         tc_fence_after();
         const uint32_t acc0 = tmem + buf * L::kAcc * L::kAccCols;
+        // One thread issues every MMA, so its own instruction count per stage
+        // bounds the stage rate: ring positions advance by counters, and the
+        // descriptors of a stage are formed once and stepped by constants (the
+        // 14-bit address field of a shared-memory descriptor counts 16 bytes).
         for (int kc = 0; kc < nk; ++kc, ++it) {
-          const uint32_t acc = acc0 + (kc % L::kAcc) * L::kAccCols;
-          const int s = it % L::kStages;
-          const int j = it % L::kLoRing;
-          if (!mbar_wait(&full[s], (it / L::kStages) & 1, vfail) ||
-              (L::kTf32 && !mbar_wait(&lofull[j], (it / L::kLoRing) & 1, vfail))) {
+          const uint32_t acc = acc0 + (kc & (L::kAcc - 1)) * L::kAccCols;
+          if (!mbar_wait(&full[rs], rph, vfail) ||
+              (L::kTf32 && !mbar_wait(&lofull[rj], jph, vfail))) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t st = smem_u32(base + s * L::kStageBytes);
+          const uint32_t st = smem_u32(base + rs * L::kStageBytes);
+          const uint64_t bdesc0 = smem_desc(st + L::kOffB, 16, 1024);
+          uint64_t adesc0;
+          if constexpr (kMN) {
+            constexpr uint32_t lbo = L::kTf32 ? kTileBytes / 4 : kTileBytes / 2;
+            adesc0 = smem_desc(st, lbo, 1024);
+          } else {
+            adesc0 = smem_desc(st, 16, 1024);
+          }
+          const uint64_t lodesc0 = smem_desc(smem_u32(base + L::kOffLo + rj * kTileBytes), 16, 1024);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             // K-major: +32 bytes per K step inside the swizzled 128-byte rows.
             // MN-major: +K-step rows of 128 bytes; column pieces LBO apart.
-            uint64_t adesc;
-            if constexpr (kMN) {
-              constexpr uint32_t step = L::kTf32 ? 1024 : 2048;
-              constexpr uint32_t lbo = L::kTf32 ? kTileBytes / 4 : kTileBytes / 2;
-              adesc = smem_desc(st + kk * step, lbo, 1024);
-            } else {
-              adesc = smem_desc(st + kk * 32, 16, 1024);
-            }
-            const uint64_t bdesc = smem_desc(st + L::kOffB + kk * 32, 16, 1024);
+            constexpr uint32_t astep = kMN ? (L::kTf32 ? 1024 : 2048) : 32;
+            const uint64_t adesc = adesc0 + (uint64_t)((kk * astep) >> 4);
+            const uint64_t bdesc = bdesc0 + (uint64_t)((kk * 32) >> 4);
             const uint32_t accum = (kc >= L::kAcc || kk != 0) ? 1u : 0u;
             if constexpr (L::kTf32) {
               // x_hi [f_hi; f_lo] into columns [0, 2 NP), then x_lo f_hi into [0, NP).
-              const uint32_t lo = smem_u32(base + L::kOffLo + j * kTileBytes);
               mma<KIND>(acc, adesc, bdesc, idesc2, accum);
-              mma<KIND>(acc, smem_desc(lo + kk * 32, 16, 1024), bdesc, idesc, 1u);
+              mma<KIND>(acc, lodesc0 + (uint64_t)((kk * 32) >> 4), bdesc, idesc, 1u);
             } else {
               mma<KIND>(acc, adesc, bdesc, idesc, accum);
             }
           }
-          mma_commit(&empty[s]);
-          if constexpr (L::kTf32) mma_commit(&loempty[j]);
+          mma_commit(&empty[rs]);
+          if constexpr (L::kTf32) mma_commit(&loempty[rj]);
+          if (++rs == L::kStages) {
+            rs = 0;
+            rph ^= 1u;
+          }
+          if (++rj == L::kLoRing) {
+            rj = 0;
+            jph ^= 1u;
+          }
         }
         if (!ok) break;
         mma_commit(&accfull[buf]);
