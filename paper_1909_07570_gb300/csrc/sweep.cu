@@ -54,10 +54,10 @@ __device__ __forceinline__ void write_operand(const UpdArgs<T>& a, int64_t r, in
     if (a.bt) a.bt[idx] = __float2bfloat16_rn(x);
     if (a.bhi) {
       const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);  // exact TF32 part
-      uint32_t l;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - h));
+      // The remainder rounded to TF32, to nearest with ties away from zero (as
+      // the pass kernel rounds its operand splits).
       a.bhi[idx] = h;
-      a.blo[idx] = __uint_as_float(l);
+      a.blo[idx] = __uint_as_float((__float_as_uint(x - h) + 0x1000u) & 0xFFFFE000u);
     }
   }
 }

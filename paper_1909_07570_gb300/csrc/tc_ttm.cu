@@ -183,11 +183,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
-// The remainder x - x_hi rounded to TF32 (cvt.rna: to nearest, ties away).
+// The remainder x - x_hi rounded to TF32, to nearest with ties away from zero:
+// adding half of the dropped 13-bit field to the sign-magnitude bits and
+// clearing the field rounds the magnitude (a carry moves into the exponent,
+// as it should). Finite inputs only; this is the inner loop of the split, where
+// integer operations run at full rate.
 __device__ __forceinline__ float tf32_lo(float x, float hi) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x - hi));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x - hi) + 0x1000u) & 0xFFFFE000u);
 }
 
 template <int KIND, int NP, bool FUSE = false>

@@ -1,9 +1,11 @@
 """Host-side checks of the C ABI: the library builds for sm_103a, loads without
-a GPU and exports every function include/nncandelinc.h declares."""
+a GPU and exports every function include/nncandelinc.h declares; and the bit
+rule the pass kernel uses to round TF32 remainders."""
 import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -71,3 +73,23 @@ def test_argument_checks_need_no_gpu(lib):
     st = native._lib.ntd_fit(ctypes.c_void_p(1), 3, dims, bad_m, 1, ctypes.byref(opts), ptrs,
                              ctypes.c_void_p(1), None, None, None)
     assert st == -1
+
+
+def test_tf32_rounding_bit_rule():
+    # The pass kernel rounds the remainder x - x_hi to TF32 by adding half of
+    # the 13 dropped bits to the sign-magnitude pattern and clearing them. Check
+    # that rule against round-to-nearest, ties away from zero, on the TF32 grid
+    # (10 stored mantissa bits), computed exactly in float64.
+    rng = np.random.default_rng(7)
+    x = (rng.standard_normal(20000) * np.exp2(rng.integers(-60, 60, 20000))).astype(np.float32)
+    ties = (np.float32(1.0) + np.float32(2.0 ** -11) * np.arange(1, 64, 2)).astype(np.float32)
+    x = np.concatenate([x, ties, -ties, np.float32([0.0, -0.0, 1.0, 2.0 ** -130, 3.0 * 2.0 ** -140])])
+    bits = x.view(np.uint32)
+    got = ((bits + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32).astype(np.float64)
+    xd = x.astype(np.float64)
+    mant, expo = np.frexp(xd)                       # xd = mant * 2^expo, 0.5 <= |mant| < 1
+    expo = np.maximum(expo, -125)                   # subnormal float32: fixed spacing 2^-136 (11 bits kept)
+    spacing = np.exp2(expo - 11.0)
+    q = xd / spacing
+    ref = np.sign(q) * np.floor(np.abs(q) + 0.5) * spacing
+    np.testing.assert_array_equal(got, ref)
