@@ -346,6 +346,10 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
   T* nm = fo + al4(MV);
   T* gs = nm + al4(MV);  // MV x UC when it fits
   const int64_t r = blockIdx.x;
+  // A programmatic successor (the next sweep's first pass over X) may start
+  // its prologue and its reads of X now; it waits for this grid before it
+  // reads anything this kernel writes.
+  pdl_trigger();
 
   // Everything but the GEMM operands is requested first; the GEMM's waits
   // cover this group too.
@@ -400,6 +404,7 @@ __global__ void __launch_bounds__(kThreads) mu_rows_kernel(UpdArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int MV = a.mv, R = kThreads / MV;
+  pdl_trigger();  // as in upd12
   T* hs = sm;                  // MV x MV
   T* fo = hs + al4(MV * MV);   // R x MV: the old rows
   const int64_t r0 = (int64_t)blockIdx.x * R;
