@@ -224,14 +224,17 @@ __device__ __noinline__ void gemm_tn_block(const T* __restrict__ A, int64_t lda,
   const int g = threadIdx.x / tiles, t = threadIdx.x % tiles;
   const bool act = g < groups;
   const int u0 = (t / tq) * 4, c0 = (t % tq) * 4;
+  // A Gram (B is A) stages its operand once.
+  const bool gram = A == B && lda == ldb && mu == mc;
   T* As = stage;
-  T* Bs = stage + (len > kch ? 2 : 1) * kch * mu4;
+  T* Bs = gram ? As : stage + (len > kch ? 2 : 1) * kch * mu4;
   const bool vecA = aligned16(A, lda, sizeof(T)), vecB = aligned16(B, ldb, sizeof(T));
   const int nch = (len + kch - 1) / kch;
   auto issue = [&](int c, int buf) {
     const int t0 = c * kch, tn = min(kch, len - t0);
     stage_tile(As + buf * kch * mu4, mu4, A + (int64_t)t0 * lda, lda, tn, mu4, tn, mu, vecA);
-    stage_tile(Bs + buf * kch * mc4, mc4, B + (int64_t)t0 * ldb, ldb, tn, mc4, tn, mc, vecB);
+    if (!gram)
+      stage_tile(Bs + buf * kch * mc4, mc4, B + (int64_t)t0 * ldb, ldb, tn, mc4, tn, mc, vecB);
     cp_commit();
   };
   T acc[4][4];
