@@ -1,16 +1,19 @@
 // Fused kernels of one nnTD sweep around the two passes over X.
 //
-// With P3 = X x_3 F3^T ((N1 N2) x m3) and P1 = X x_1 F1^T (m1 x N2 x N3) from
-// the passes, a sweep is (S_k = F_k^T F_k, Eq. unfolding:property):
+// With P3 = X x_3 F3^T ((N1 N2) x m3) and P1 = X x_1 F1^T (rows (k, j) x m1)
+// from the passes, a sweep is (S_k = F_k^T F_k, Eq. unfolding:property):
 //
 //   upd12 (mode 1) per slab i:  Y1[i] = F2^T P3[i, :, :]           (m2 x m3)
+//                               (or the sum of its shares formed by pass 1)
 //                               Num1[i, a] = <Y1[i], G[a, :, :]>
 //                               F1[i, :] <- MU with Den = F1[i, :] H1
 //   hmat  (mode 2) per b:       S1 = F1^T F1;  W[:, b, :] = S1 G[:, b, :] S3
 //                               H2[b, b'] = <W[:, b, :], G[:, b', :]>
-//   upd12 (mode 2) per row j:   Y2[:, j, :] = F1^T P3[:, j, :];  Num2;  MU on F2
+//   upd12 (mode 2) per row j:   Y2[:, j, :] = F1^T P3[:, j, :];  Num2 (numerator only)
+//   mu_rows (mode 2):           MU on F2 with Den = F2 H2
 //   hmat  (mode 3) per c:       S2 = F2^T F2;  W3 = G x_1 S1 x_2 S2 (kept);  H3
-//   upd12 (mode 3) per slab k:  Y3[k] = P1[k, :, :]^T F2  (m1 x m2, kept; P1 has rows (k, j))
+//   upd12 (mode 3) per slab k:  Y3[k] = P1[k, :, :]^T F2  (m1 x m2, kept)
+//                               (or the sum of its shares formed by pass 2)
 //                               Num3[k, c] = <Y3[k], G[:, :, c]>;  MU on F3
 //   core_a (one block per a):   S3 = F3^T F3; M[a] = Y3[:, a, :]^T F3 (= (X x_1 F1^T x_2 F2^T x_3 F3^T)[a]);
 //                               D = W3 x_3 S3;  G <- MU(G, M, D); W1 = G x_2 S2 x_3 S3
