@@ -27,7 +27,7 @@ import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
-# The batching form runs up to 8 concurrent fits of two streams each: give the
+# The batching form runs up to 8 concurrent fits of three streams each: give the
 # process enough hardware work queues (before CUDA starts) so that they do not
 # share queues and serialise.
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")

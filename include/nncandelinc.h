@@ -114,9 +114,10 @@ typedef struct {
  * CUDA stream of its own that first waits for the work already queued on
  * `stream`, so small problems overlap on the GPU; every job runs exactly the
  * kernels of ntd_fit and gives the same bits. Returns when all jobs are done.
- * Each worker drives two streams (the sweep graph has two branches): above 4
- * workers, start the process with CUDA_DEVICE_MAX_CONNECTIONS raised (e.g. to
- * 32), or the streams share hardware queues and partly serialise.
+ * Each worker drives three streams (the sweep graph has side branches): above
+ * two workers, start the process with CUDA_DEVICE_MAX_CONNECTIONS raised (e.g.
+ * to 32), or the streams share the 8 default hardware queues and partly
+ * serialise.
  *
  *  jobs       host array of n_jobs descriptors
  *  rel_errs   host, n_jobs doubles (NaN for a failed job), or NULL

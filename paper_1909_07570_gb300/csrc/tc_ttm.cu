@@ -28,7 +28,9 @@
 //                 TMEM accumulator; tcgen05.commit frees stages and publishes
 //                 finished accumulators
 //   warps 2-5     epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
-//                 lanes 32 (w % 4) ..), scaled stores to global memory
+//                 lanes 32 (w % 4) ..), scaled stores to global memory; with
+//                 TcEpilogue::ysh also the tile's contraction with the
+//                 matching factor rows (the nnTD sweep's mode-1 / mode-3 shares)
 //   warps 6-9     TF32x3 only: split each staged A tile into x_hi (in place)
 //                 and x_lo (into a 3-slot ring of its own)
 // so a tile's epilogue overlaps the next tile's MMAs. The kernel is launched
