@@ -175,55 +175,63 @@ __global__ void hadamard_kernel(HadArgs<T> a) {
 // out_b = lmax(H_b) for the matrix b = blockIdx.x of the launch (H_0: n0 x n0,
 // H_1: n1 x n1, n <= 64): kPowerIters FP64 power iterations from the
 // normalised all-ones vector, then the Rayleigh quotient; 0 if an iterate maps
-// to zero. Rows go to warps, columns to lanes (shuffle sums in a fixed order):
-// FP64 is slow on this GPU, so no long serial chains.
+// to zero. One warp per matrix: lane l owns rows l and l + 32 of H (kept in
+// shared memory with an odd row stride) and the same entries of v, which the
+// products fetch by shuffles. FP64 is slow on this GPU, and an iteration then
+// needs no block barrier: one shuffle sum for the norm and one reciprocal.
 template <typename T>
-__global__ void power_iter_kernel(const T* __restrict__ H0, int n0, double* out0,
-                                  const T* __restrict__ H1, int n1, double* out1) {
-  __shared__ double h[64 * 64];
-  __shared__ double v[64], w[64];
-  __shared__ double nrm;
+__global__ void __launch_bounds__(32) power_iter_kernel(const T* __restrict__ H0, int n0,
+                                                         double* out0, const T* __restrict__ H1,
+                                                         int n1, double* out1) {
+  __shared__ double h[64 * 65];
   const T* H = blockIdx.x == 0 ? H0 : H1;
   const int n = blockIdx.x == 0 ? n0 : n1;
   double* out = blockIdx.x == 0 ? out0 : out1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) h[e] = (double)H[e];
-  if (threadIdx.x < n) v[threadIdx.x] = 1.0 / sqrt((double)n);
-  __syncthreads();
-  auto matvec = [&]() {  // w = h v
-    for (int i = warp; i < n; i += nw) {
-      double a = 0.0;
-      for (int j = lane; j < n; j += 32) a = fma(h[i * n + j], v[j], a);
-      a = warp_sum(a);
-      if (lane == 0) w[i] = a;
+  const int lane = threadIdx.x, ld = n + 1;
+  for (int e = lane; e < n * n; e += 32) h[(e / n) * ld + e % n] = (double)H[e];
+  __syncwarp();
+  const int r0 = lane, r1 = lane + 32;
+  const bool has0 = r0 < n, has1 = r1 < n;
+  const double v0i = 1.0 / sqrt((double)n);
+  double v0 = has0 ? v0i : 0.0, v1 = has1 ? v0i : 0.0;  // v[r0], v[r1]
+  double w0 = 0.0, w1 = 0.0;
+  auto matvec = [&]() {  // (w0, w1) = rows r0, r1 of H v
+    double a0 = 0.0, b0 = 0.0, a1 = 0.0, b1 = 0.0;
+    int j = 0;
+    for (; j + 1 < n; j += 2) {
+      const double x = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31);
+      const double y = __shfl_sync(0xffffffffu, j + 1 < 32 ? v0 : v1, (j + 1) & 31);
+      if (has0) {
+        a0 = fma(h[r0 * ld + j], x, a0);
+        b0 = fma(h[r0 * ld + j + 1], y, b0);
+      }
+      if (has1) {
+        a1 = fma(h[r1 * ld + j], x, a1);
+        b1 = fma(h[r1 * ld + j + 1], y, b1);
+      }
     }
-    __syncthreads();
+    if (j < n) {
+      const double x = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31);
+      if (has0) a0 = fma(h[r0 * ld + j], x, a0);
+      if (has1) a1 = fma(h[r1 * ld + j], x, a1);
+    }
+    w0 = a0 + b0;
+    w1 = a1 + b1;
   };
-  bool zero = false;
-  for (int it = 0; it < kPowerIters && !zero; ++it) {
+  for (int it = 0; it < kPowerIters; ++it) {
     matvec();
-    if (warp == 0) {
-      double a = 0.0;
-      for (int j = lane; j < n; j += 32) a = fma(w[j], w[j], a);
-      a = warp_sum(a);
-      if (lane == 0) nrm = sqrt(a);
+    const double nrm = sqrt(warp_sum(w0 * w0 + w1 * w1));
+    if (!(nrm > 0.0)) {
+      if (lane == 0) out[0] = 0.0;
+      return;
     }
-    __syncthreads();
-    zero = !(nrm > 0.0);
-    if (!zero && threadIdx.x < n) v[threadIdx.x] = w[threadIdx.x] / nrm;
-    __syncthreads();
-  }
-  if (zero) {
-    if (threadIdx.x == 0) out[0] = 0.0;
-    return;
+    const double inv = 1.0 / nrm;
+    v0 = w0 * inv;
+    v1 = w1 * inv;
   }
   matvec();
-  if (warp == 0) {
-    double a = 0.0;
-    for (int j = lane; j < n; j += 32) a = fma(v[j], w[j], a);
-    a = warp_sum(a);
-    if (lane == 0) out[0] = a;
-  }
+  const double q = warp_sum(v0 * w0 + v1 * w1);
+  if (lane == 0) out[0] = q;
 }
 
 // P <- max(P - G / L, 0) when L > 0, with L = L1[0] (times L2[0] if given).
@@ -520,7 +528,7 @@ int pg_mode(Work<T>& w, int n, T* const* F, T* const* B, cudaStream_t s) {
   // L_F = lmax(B V B^T) and lmax(V) (one launch): tmp = B V (m x r), H = tmp B^T (m x m)
   NNC_CUDA_TRY(small_gemm<T>(mn, r, r, B[n], r, 1, w.V, r, 1, nullptr, w.tmp, s));
   NNC_CUDA_TRY(small_gemm<T>(mn, mn, r, w.tmp, r, 1, B[n], 1, r, nullptr, w.H, s));
-  power_iter_kernel<T><<<2, 256, 0, s>>>(w.H, mn, w.Ls + 0, w.V, r, w.Ls + 1);
+  power_iter_kernel<T><<<2, 32, 0, s>>>(w.H, mn, w.Ls + 0, w.V, r, w.Ls + 1);
   note_launch(s);
   NNC_TRY(grad_a(w, n, s));
   // gF = gA B^T (N x m) into tmp
@@ -532,7 +540,7 @@ int pg_mode(Work<T>& w, int n, T* const* F, T* const* B, cudaStream_t s) {
   NNC_CUDA_TRY(launch_lift<T>(F[n], B[n], Nn, mn, r, w.A[n], s));
   // L_B = lmax(F^T F) lmax(V)
   NNC_TRY(launch_gram<T>(F[n], Nn, mn, w.S, s));
-  power_iter_kernel<T><<<1, 256, 0, s>>>(w.S, mn, w.Ls + 2, w.S, mn, w.Ls + 2);
+  power_iter_kernel<T><<<1, 32, 0, s>>>(w.S, mn, w.Ls + 2, w.S, mn, w.Ls + 2);
   note_launch(s);
   NNC_TRY(grad_a(w, n, s));
   // gB = F^T gA (m x r) into tmp
