@@ -79,7 +79,12 @@ typedef struct {
  * (the unfoldings follow Eq. unfolding:property).
  *
  *  X          device, dims[0] x ... x dims[d-1], entries >= 0 and finite
- *  d          3 (this build)
+ *  d          3 or 4. d = 4 runs the same sweep on the d-way mode-product
+ *             machinery of the differentiation form (two passes over X per
+ *             sweep, the FP32 passes on the TF32x3 tensor-core kernel with X
+ *             viewed as dims[0] x dims[1]*dims[2] x dims[3]); it needs every
+ *             core slice prod_{k!=n} m[k] within 200 KB (else UNSUPPORTED)
+ *             and has no NNC_BF16_REFINE form (UNSUPPORTED)
  *  dims, m    host arrays of d entries; 1 <= m[n] <= 64, dims[n] >= 1
  *  F          host array of d device pointers: initial F^(n) (> 0) in,
  *             fitted F^(n) out
@@ -90,7 +95,7 @@ typedef struct {
  *  rel_err    host, or NULL: final relative error from one explicit FP64
  *             pass over X (as recon_residual)
  * Errors: INVALID_ARG, NEGATIVE_INPUT, NONFINITE (checked on X before any
- * sweep), UNSUPPORTED (d != 3), CUDA, ALLOC.
+ * sweep), UNSUPPORTED (the d = 4 limits above), CUDA, ALLOC.
  */
 int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precision,
             const nnc_opts* opts, void* const* F, void* G, double* rel_err_trace,
@@ -98,12 +103,12 @@ int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precisi
 
 /* One nnTD problem of a batch (see ntd_fit for the meaning of each field). */
 typedef struct {
-  const void* X;        /* device, C order, d = 3 modes dims[0..2]                 */
+  const void* X;        /* device, C order, d = 3 or 4 modes dims[0..d-1]          */
   int d;
   int64_t dims[4];
   int m[4];
   void* F[4];           /* device F^(n), dims[n] x m[n]: initial in, fitted out     */
-  void* G;              /* device core, m[0] x m[1] x m[2]: initial in, fitted out  */
+  void* G;              /* device core, m[0] x ... x m[d-1]: initial in, fitted out */
   double* trace;        /* device, opts->iters doubles, or NULL                     */
 } ntd_job;
 
@@ -382,7 +387,8 @@ int candelinc_alg2(const void* X, int d, const int64_t* dims, const int* m, int 
  *  model 1: CP     X_hat = I x_1 A^(1) ... (factors = A, dims[n] x r; G and m
  *           unused)
  *  resid_norm, x_norm  host
- * Errors: INVALID_ARG, UNSUPPORTED (d != 3), CUDA, ALLOC.
+ *  d          3 or 4
+ * Errors: INVALID_ARG, CUDA, ALLOC.
  */
 int recon_residual(const void* X, int d, const int64_t* dims, int precision, int model,
                    const int* m, int r, const void* const* factors, const void* G,
@@ -390,8 +396,8 @@ int recon_residual(const void* X, int d, const int64_t* dims, int precision, int
 
 /*
  * Tracing aid: CUDA-event timing of the two passes over X of nnTD sweeps,
- * the kernels that dominate ntd_fit. While enabled, ntd_fit records an event
- * pair around each pass of every 16th sweep (the 16th, the 32nd, ...) on the
+ * the kernels that dominate ntd_fit. While enabled, ntd_fit (d = 3) records
+ * an event pair around each pass of every 16th sweep (the 16th, the 32nd, ...) on the
  * stream that launches it; the pairs are read (synchronising on them) by
  * nnc_profile_read, not inside ntd_fit.
  * Kinds:

@@ -196,11 +196,29 @@ int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precisi
   g_detail.clear();
   NNC_TRY(check_opts(opts));
   if (X == nullptr || F == nullptr || G == nullptr) return NNC_ERR_INVALID_ARG;
-  if (d != 3) return d == 4 ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
+  if (d != 3 && d != 4) return NNC_ERR_INVALID_ARG;
   NNC_TRY(check_shape(d, dims, m, 64));
   for (int n = 0; n < d; ++n)
     if (F[n] == nullptr) return NNC_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d == 4) {
+    switch (precision) {
+      case NNC_FP64:
+        return ntd_fit_nway<double>(static_cast<const double*>(X), 4, dims, m, false,
+                                    opts->iters, opts->eps, reinterpret_cast<double* const*>(F),
+                                    static_cast<double*>(G), rel_err_trace, rel_err, s);
+      case NNC_FP32:
+      case NNC_FP32_SIMT:
+        return ntd_fit_nway<float>(static_cast<const float*>(X), 4, dims, m,
+                                   precision == NNC_FP32, opts->iters, opts->eps,
+                                   reinterpret_cast<float* const*>(F), static_cast<float*>(G),
+                                   rel_err_trace, rel_err, s);
+      case NNC_BF16_REFINE:
+        return NNC_ERR_UNSUPPORTED;
+      default:
+        return NNC_ERR_INVALID_ARG;
+    }
+  }
   switch (precision) {
     case NNC_FP64:
       return ntd_fit3<double>(static_cast<const double*>(X), dims, m, opts,
@@ -531,7 +549,7 @@ int recon_residual(const void* X, int d, const int64_t* dims, int precision, int
   g_detail.clear();
   if (X == nullptr || factors == nullptr || dims == nullptr) return NNC_ERR_INVALID_ARG;
   if (model != 0 && model != 1) return NNC_ERR_INVALID_ARG;
-  if (d != 3) return d == 4 ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
+  if (d != 3 && d != 4) return NNC_ERR_INVALID_ARG;
   for (int n = 0; n < d; ++n) {
     if (dims[n] < 1 || factors[n] == nullptr) return NNC_ERR_INVALID_ARG;
     if (model == 0 && (m == nullptr || m[n] < 1 || m[n] > 64)) return NNC_ERR_INVALID_ARG;
@@ -543,12 +561,12 @@ int recon_residual(const void* X, int d, const int64_t* dims, int precision, int
   double* out2 = nullptr;
   NNC_TRY(sc.get(&out2, 2));
   if (precision == NNC_FP64) {
-    NNC_TRY(residual3_device<double>(static_cast<const double*>(X), dims, model, m, r,
+    NNC_TRY(residual_device<double>(static_cast<const double*>(X), d, dims, model, m, r,
                                      reinterpret_cast<const double* const*>(factors),
                                      static_cast<const double*>(G), out2, sc, s));
   } else if (precision == NNC_FP32 || precision == NNC_BF16_REFINE ||
              precision == NNC_FP32_SIMT) {
-    NNC_TRY(residual3_device<float>(static_cast<const float*>(X), dims, model, m, r,
+    NNC_TRY(residual_device<float>(static_cast<const float*>(X), d, dims, model, m, r,
                                     reinterpret_cast<const float* const*>(factors),
                                     static_cast<const float*>(G), out2, sc, s));
   } else {

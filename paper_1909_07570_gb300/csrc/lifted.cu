@@ -844,6 +844,118 @@ int nmf_fit(const T* A, int64_t N, int r, int m, int iters, double eps, T* F, T*
   return NNC_OK;
 }
 
+// nnTD of a d-way X (d = 3 or 4) by MU sweeps (Alg. 1, first step), built on
+// the mode-product machinery above with F := F^(k). A sweep updates
+// F^(1), ..., F^(d), then G:
+//   Num_n = unfold_n(Z_n) unfold_n(G)^T           (Z_n from the two passes)
+//   H_n   = unfold_n(G x_{k!=n} S_k) unfold_n(G)^T,  S_k = F^(k)T F^(k)
+//   F^(n) <- max(F^(n) .* Num_n / max(F^(n) H_n, eps), 0),  S_n refreshed
+//   M = Z_d x_d F^(d)T,  D = G x_k S_k,  G <- max(G .* M / max(D, eps), 0)
+// and the trace entry sqrt(max(||X||^2 - 2<M, G> + <G, G x_k S_k>, 0)) / ||X||
+// in FP64. Z_1 .. Z_{d-1} come from T_last = X x_d F^(d)T (U0 after mode 1)
+// and Z_d from T_first = X x_1 F^(1)T formed after mode d-1, so every Z_n sees
+// the factors of modes k < n already updated (Gauss-Seidel) and X is read twice
+// per sweep. The unfolding products hold one slice of Z_n or of G x S in
+// shared memory: prod_{k!=n} m_k entries of T for every n, at most 200 KB.
+template <typename T>
+int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tensor_cores,
+                 int iters, double eps, T* const* F, T* G, double* trace, double* rel_err,
+                 cudaStream_t s) {
+  if (d != 3 && d != 4) return NNC_ERR_INVALID_ARG;
+  int64_t nc = 1;
+  for (int k = 0; k < d; ++k) nc *= m[k];
+  for (int n = 0; n < d; ++n)
+    if (nc / m[n] * (int64_t)sizeof(T) > 200 * 1024) return NNC_ERR_UNSUPPORTED;
+  Scratch sc(s);
+  Work<T> w;
+  NNC_TRY(setup(w, X, d, dims, m, /*r=*/1, tensor_cores, sc, s));
+  double st[3];
+  NNC_CUDA_TRY(cudaMemcpyAsync(st, w.stats, sizeof(st), cudaMemcpyDeviceToHost, s));
+  NNC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (st[1] > 0.0) return NNC_ERR_NEGATIVE_INPUT;
+  if (!(st[0] > 0.0)) return NNC_ERR_INVALID_ARG;  // X == 0: the relative error is undefined
+  int64_t nmax = 1;
+  int mmax = 1;
+  for (int k = 0; k < d; ++k) {
+    nmax = dims[k] > nmax ? dims[k] : nmax;
+    mmax = m[k] > mmax ? m[k] : mmax;
+  }
+  T *num = nullptr, *c0 = nullptr, *c1 = nullptr, *M = nullptr, *D = nullptr;
+  T* S[kMaxD] = {};
+  double* dummy = nullptr;
+  int* counter = nullptr;
+  NNC_TRY(sc.get(&num, (size_t)(nmax * mmax)));
+  NNC_TRY(sc.get(&c0, (size_t)nc));
+  NNC_TRY(sc.get(&c1, (size_t)nc));
+  NNC_TRY(sc.get(&M, (size_t)nc));
+  NNC_TRY(sc.get(&D, (size_t)nc));
+  for (int k = 0; k < d; ++k) NNC_TRY(sc.get(&S[k], (size_t)m[k] * m[k]));
+  NNC_TRY(sc.get(&dummy, 1));
+  NNC_TRY(sc.get(&counter, 1));
+  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+  for (int k = 0; k < d; ++k) NNC_TRY(launch_gram<T>(F[k], dims[k], m[k], S[k], s));
+  double* tr = trace ? trace : dummy;
+  const int stride = trace ? 1 : 0;
+  // out = G x_k S_k over the modes k != skip (all modes when skip < 0).
+  auto core_times_grams = [&](int skip, T* out, cudaStream_t cs) -> int {
+    const T* src = G;
+    int left = 0;
+    for (int k = 0; k < d; ++k) left += k != skip;
+    for (int k = 0; k < d; ++k) {
+      if (k == skip) continue;
+      T* dst = --left == 0 ? out : (src == c0 ? c1 : c0);
+      int64_t pre = 1, post = 1;
+      for (int j = 0; j < k; ++j) pre *= m[j];
+      for (int j = k + 1; j < d; ++j) post *= m[j];
+      NNC_CUDA_TRY(launch_ttm<T>(src, pre, m[k], post, S[k], m[k], 1, m[k], dst, w.split,
+                                 w.split_cap, cs));
+      src = dst;
+    }
+    return NNC_OK;
+  };
+  NNC_TRY(replay(iters, s, [&](cudaStream_t cs) -> int {
+    NNC_TRY(pass_last(w, F[d - 1], cs));
+    const T* Z = nullptr;
+    for (int n = 0; n < d; ++n) {
+      if (n == d - 1) NNC_TRY(pass_first(w, F[0], cs));
+      NNC_TRY(z_chain(w, n, F, &Z, cs));
+      int64_t pre = 1, post = 1;
+      for (int j = 0; j < n; ++j) pre *= m[j];
+      for (int j = n + 1; j < d; ++j) post *= m[j];
+      NNC_CUDA_TRY(launch_pair_contract<T>(Z, G, pre, (int)dims[n], m[n], post, num, cs));
+      // H_n from G x_{k!=n} S_k, formed in M (free until the core update).
+      NNC_TRY(core_times_grams(n, M, cs));
+      NNC_CUDA_TRY(launch_pair_contract<T>(M, G, pre, m[n], m[n], post, w.H, cs));
+      NNC_CUDA_TRY(launch_factor_mu<T>(F[n], num, w.H, dims[n], m[n], eps, cs));
+      NNC_TRY(launch_gram<T>(F[n], dims[n], m[n], S[n], cs));
+      if (n == 0 && d > 2) NNC_TRY(make_u0(w, F[0], cs));
+    }
+    // Core: Z (= Z_d) x_d F^(d)T with the updated F^(d).
+    const int64_t lead = nc / m[d - 1];
+    NNC_CUDA_TRY(launch_ttm<T>(Z, lead, (int)dims[d - 1], 1, F[d - 1], m[d - 1], 1, m[d - 1], M,
+                               w.split, w.split_cap, cs));
+    NNC_TRY(core_times_grams(-1, D, cs));
+    NNC_CUDA_TRY(launch_elementwise_mu<T>(G, M, D, nc, eps, cs));
+    NNC_TRY(core_times_grams(-1, D, cs));
+    NNC_CUDA_TRY(launch_residual_identity<T>(M, G, D, nc, w.stats, tr, stride, counter, cs));
+    return NNC_OK;
+  }));
+  NNC_TRY(check_tc(w, s));
+  if (rel_err) {
+    double* out2 = nullptr;
+    NNC_TRY(sc.get(&out2, 2));
+    const T* fac[kMaxD];
+    for (int k = 0; k < d; ++k) fac[k] = F[k];
+    NNC_TRY(residual_device<T>(X, d, dims, 0, m, 0, fac, G, out2, sc, s));
+    double h[2];
+    NNC_CUDA_TRY(cudaMemcpyAsync(h, out2, sizeof(h), cudaMemcpyDeviceToHost, s));
+    NNC_CUDA_TRY(cudaStreamSynchronize(s));
+    *rel_err = sqrt(h[0] / h[1]);
+  }
+  NNC_CUDA_TRY(cudaStreamSynchronize(s));
+  return NNC_OK;
+}
+
 template int lifted_grad<float>(const float*, int, const int64_t*, const int*, int, bool,
                                 float* const*, float* const*, float* const*, float* const*,
                                 double*, cudaStream_t);
@@ -863,5 +975,10 @@ template int nmf_fit<double>(const double*, int64_t, int, int, int, double, doub
 template int lifted_pg_fit<double>(const double*, int, const int64_t*, const int*, int, bool,
                                    int, double* const*, double* const*, double*, double*,
                                    cudaStream_t);
+template int ntd_fit_nway<float>(const float*, int, const int64_t*, const int*, bool, int, double,
+                                 float* const*, float*, double*, double*, cudaStream_t);
+template int ntd_fit_nway<double>(const double*, int, const int64_t*, const int*, bool, int,
+                                  double, double* const*, double*, double*, double*,
+                                  cudaStream_t);
 
 }  // namespace nnc

@@ -491,7 +491,7 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
 
   if (rel_err) {
     const T* fac[3] = {F[0], F[1], F[2]};
-    NNC_TRY(residual3_device<T>(X, dims, 0, m, 0, fac, G, b.resid2, sc, s));
+    NNC_TRY(residual_device<T>(X, 3, dims, 0, m, 0, fac, G, b.resid2, sc, s));
     double h[2];
     NNC_CUDA_TRY(cudaMemcpyAsync(h, b.resid2, sizeof(h), cudaMemcpyDeviceToHost, s));
     NNC_CUDA_TRY(cudaStreamSynchronize(s));

@@ -1,10 +1,11 @@
 // The lift A^(n) = F^(n) B^(n) and the one-pass reconstruction residual.
 //
-// recon_residual streams X once. For a 3-way X the model is first reduced to
-// rows U[i, j, :] (length K = m_3 for Tucker, r for CP):
-//   Tucker: U = G x_1 F^(1) x_2 F^(2)        X_hat[i, j, k] = sum_c U[i, j, c] F^(3)[k, c]
-//   CP:     U[i, j, q] = A^(1)[i, q] A^(2)[j, q]   X_hat[i, j, k] = sum_q U[i, j, q] A^(3)[k, q]
-// (Eq. TD:matrix-format and Eq. CPD:matrix-format, contracted mode by mode).
+// recon_residual streams X once. The model is first reduced to rows U[t, :]
+// (length K = m_d for Tucker, r for CP), t running over (i_1, ..., i_{d-1}):
+//   Tucker: U = G x_1 F^(1) ... x_{d-1} F^(d-1)
+//   CP:     U[t, q] = A^(1)[i_1, q] ... A^(d-1)[i_{d-1}, q]
+// and X_hat[t, k] = sum_c U[t, c] F^(d)[k, c] (A^(d) for CP), by
+// Eq. TD:matrix-format and Eq. CPD:matrix-format contracted mode by mode.
 // The streaming kernel holds the last factor transposed in shared memory,
 // gives each thread one k of a row, forms X_hat in T and accumulates
 // (x - x_hat)^2 and x^2 in FP64; per-block partials are added in block order.
@@ -128,39 +129,66 @@ cudaError_t launch_lift(const T* F, const T* B, int64_t N, int M, int r, T* A, c
 }
 
 template <typename T>
-int residual3_device(const T* X, const int64_t* dims, int model, const int* m, int r,
-                     const T* const* factors, const T* G, double* out2, Scratch& sc,
-                     cudaStream_t s) {
-  const int64_t N1 = dims[0], N2 = dims[1], N3 = dims[2];
-  const int K = model == 0 ? m[2] : r;
+int residual_device(const T* X, int d, const int64_t* dims, int model, const int* m, int r,
+                    const T* const* factors, const T* G, double* out2, Scratch& sc,
+                    cudaStream_t s) {
+  if (d != 3 && d != 4) return NNC_ERR_INVALID_ARG;
+  const int K = model == 0 ? m[d - 1] : r;
+  int64_t R = 1;  // rows of U: N_1 ... N_{d-1}
+  for (int k = 0; k < d - 1; ++k) R *= dims[k];
   T* U = nullptr;
-  NNC_TRY(sc.get(&U, (size_t)(N1 * N2 * K)));
+  NNC_TRY(sc.get(&U, (size_t)(R * K)));
   if (model == 0) {
-    T* T1 = nullptr;
-    NNC_TRY(sc.get(&T1, (size_t)(N1 * m[1] * m[2])));
-    // T1[i, b, c] = sum_a F1[i, a] G[a, b, c];  U[i, j, c] = sum_b F2[j, b] T1[i, b, c]
-    mode_product_any_kernel<T><<<grid_cap(N1 * m[1] * m[2], 256), 256, 0, s>>>(
-        G, 1, m[0], (int64_t)m[1] * m[2], factors[0], (int)N1, T1);
-    note_launch(s);
-    mode_product_any_kernel<T><<<grid_cap(N1 * N2 * m[2], 256), 256, 0, s>>>(
-        T1, N1, m[1], m[2], factors[1], (int)N2, U);
-    note_launch(s);
+    // Mode products of the core with F^(1) .. F^(d-1), the last one into U:
+    // cur[t_<k, i_k, c_>k] = sum_a F^(k)[i_k, a] prev[t_<k, a, c_>k].
+    int64_t lead = 1;  // N_1 ... N_{k-1}
+    int64_t tail = 1;  // m_{k+1} ... m_d
+    for (int k = 1; k < d; ++k) tail *= m[k];
+    const T* src = G;
+    T* bufs[2] = {nullptr, nullptr};
+    for (int k = 0; k < d - 1; ++k) {
+      const int64_t n_out = lead * dims[k] * tail;
+      T* dst = U;
+      if (k < d - 2) {
+        if (!bufs[k & 1]) NNC_TRY(sc.get(&bufs[k & 1], (size_t)n_out));
+        dst = bufs[k & 1];
+      }
+      mode_product_any_kernel<T><<<grid_cap(n_out, 256), 256, 0, s>>>(
+          src, lead, m[k], tail, factors[k], (int)dims[k], dst);
+      note_launch(s);
+      src = dst;
+      lead *= dims[k];
+      tail /= m[k + 1];
+    }
   } else {
-    cp_rows_kernel<T><<<grid_cap(N1 * N2 * r, 256), 256, 0, s>>>(factors[0], factors[1], N1, N2,
-                                                                   r, U);
-    note_launch(s);
+    // U_k = U_{k-1} (.) A^(k) row by row: (rows of U_{k-1}) x N_k rows.
+    int64_t rows = dims[0];
+    const T* src = factors[0];
+    T* tmp = nullptr;
+    for (int k = 1; k < d - 1; ++k) {
+      T* dst = U;
+      if (k < d - 2) {
+        NNC_TRY(sc.get(&tmp, (size_t)(rows * dims[k] * r)));
+        dst = tmp;
+      }
+      cp_rows_kernel<T><<<grid_cap(rows * dims[k] * r, 256), 256, 0, s>>>(src, factors[k], rows,
+                                                                           dims[k], r, dst);
+      note_launch(s);
+      src = dst;
+      rows *= dims[k];
+    }
   }
   NNC_CUDA_TRY(cudaGetLastError());
-  const T* F3 = factors[2];  // F^(3) (Tucker) or A^(3) (CP): N3 x K
-  const int64_t R = N1 * N2;
-  dim3 grid((unsigned)ceil_div(N3, kResThreads), (unsigned)ceil_div(R, kResRows));
+  const T* Fd = factors[d - 1];  // F^(d) (Tucker) or A^(d) (CP): N_d x K
+  const int64_t Nd = dims[d - 1];
+  dim3 grid((unsigned)ceil_div(Nd, kResThreads), (unsigned)ceil_div(R, kResRows));
   const int64_t nblocks = (int64_t)grid.x * grid.y;
   double* part = nullptr;
   NNC_TRY(sc.get(&part, (size_t)(2 * nblocks)));
   const size_t smem = (size_t)K * kResThreads * sizeof(T);
   if (smem > 48 * 1024)
     NNC_CUDA_TRY(raise_smem_limit((const void*)residual_stream_kernel<T>, smem));
-  residual_stream_kernel<T><<<grid, kResThreads, smem, s>>>(X, R, N3, U, K, F3, part);
+  residual_stream_kernel<T><<<grid, kResThreads, smem, s>>>(X, R, Nd, U, K, Fd, part);
   note_launch(s);
   residual_final_kernel<<<1, 1024, 0, s>>>(part, nblocks, out2);
   note_launch(s);
@@ -172,11 +200,11 @@ template cudaError_t launch_lift<float>(const float*, const float*, int64_t, int
                                         cudaStream_t);
 template cudaError_t launch_lift<double>(const double*, const double*, int64_t, int, int, double*,
                                          cudaStream_t);
-template int residual3_device<float>(const float*, const int64_t*, int, const int*, int,
-                                     const float* const*, const float*, double*, Scratch&,
+template int residual_device<float>(const float*, int, const int64_t*, int, const int*, int,
+                                    const float* const*, const float*, double*, Scratch&,
+                                    cudaStream_t);
+template int residual_device<double>(const double*, int, const int64_t*, int, const int*, int,
+                                     const double* const*, const double*, double*, Scratch&,
                                      cudaStream_t);
-template int residual3_device<double>(const double*, const int64_t*, int, const int*, int,
-                                      const double* const*, const double*, double*, Scratch&,
-                                      cudaStream_t);
 
 }  // namespace nnc

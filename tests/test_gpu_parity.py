@@ -127,6 +127,88 @@ def test_ntd_rejects_bad_input():
 
 
 # ---------------------------------------------------------------------------
+# 4-way nnTD (the d-way mode-product sweep)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,m", [((13, 11, 9, 10), (3, 4, 2, 5)), ((7, 1, 12, 9), (2, 1, 3, 4)),
+                                    ((6, 40, 5, 33), (6, 9, 5, 8))])
+def test_ntd4_one_sweep_fp64_elementwise(dims, m):
+    X, _, F0, G0, _ = inputs.small_problem(dims, 3, m, 2, seed=111)
+    err, tr, F, G = _run_ntd(X, F0, G0, 1, torch.float64)
+    Fo, Go, _ = orc.ntd_sweep(X, F0, G0)
+    for a, b in zip(F, Fo):
+        np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-14 * np.abs(b).max())
+    np.testing.assert_allclose(G, Go, rtol=1e-9, atol=1e-14 * np.abs(Go).max())
+    assert abs(err - orc.rel_err_tucker(X, Go, Fo)) < 1e-11
+    assert abs(tr[0] - err) < 1e-9
+
+
+# (20, 8, 16, 36) takes the TF32x3 tensor-core passes (X viewed as 20 x 128 x 36);
+# N4 = 13 is not a multiple of 4 and runs the SIMT passes; fp32_simt forces them.
+@pytest.mark.parametrize("dims,m,precision", [((20, 8, 16, 36), (4, 3, 5, 6), "fp32"),
+                                              ((17, 9, 11, 13), (5, 4, 3, 2), "fp32"),
+                                              ((20, 8, 16, 36), (4, 3, 5, 6), "fp32_simt")])
+def test_ntd4_fp32_sweep_and_trace(dims, m, precision):
+    X, _, F0, G0, _ = inputs.small_problem(dims, 4, m, 2, seed=212, zero_frac=0.2, noise=0.02)
+    err, tr, F, G = _run_ntd(X, F0, G0, 1, torch.float32, precision=precision)
+    Fo, Go, _ = orc.ntd_sweep(X, F0, G0)
+    for a, b in zip(F, Fo):
+        np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-6 * np.abs(b).max())
+    np.testing.assert_allclose(G, Go, rtol=1e-4, atol=1e-6 * np.abs(Go).max())
+    err, tr, F, G = _run_ntd(X, F0, G0, 40, torch.float32, precision=precision)
+    Fo, Go, tro = orc.ntd_fit(X, F0, G0, 40)
+    assert np.max(np.abs(tr - tro)) <= 1e-5
+    assert abs(err - orc.rel_err_tucker(X, Go, Fo)) <= 1e-5
+    assert all((f >= 0).all() for f in F) and (G >= 0).all()
+
+
+def test_ntd4_trace_fp64_monotone():
+    X, _, F0, G0, _ = inputs.small_problem((12, 10, 14, 9), 3, (3, 3, 4, 3), 2, seed=313)
+    err, tr, F, G = _run_ntd(X, F0, G0, 30, torch.float64)
+    Fo, Go, tro = orc.ntd_fit(X, F0, G0, 30)
+    np.testing.assert_allclose(tr, tro, rtol=1e-8)
+    assert abs(err - orc.rel_err_tucker(X, Go, Fo)) < 1e-9
+    assert np.all(np.diff(tr) <= 1e-12 * tr[:-1])
+
+
+def test_ntd4_full_size_cp12_128x128x128x64_fp32():
+    # The 4-way workload at full size (TF32x3 passes over X viewed as
+    # 128 x 16384 x 64); the oracle runs the same 3 sweeps.
+    w = inputs.WORKLOADS["cp12_128x128x128x64_m24_fp32"]
+    X, _, F0, G0, _ = inputs.make_problem(w)
+    err, tr, F, G = _run_ntd(X, F0, G0, 3, torch.float32)
+    Fo, Go, tro = orc.ntd_fit(X, F0, G0, 3)
+    assert np.max(np.abs(tr - tro)) <= 1e-5
+    assert abs(err - orc.rel_err_tucker(X, Go, Fo)) <= 1e-5
+    for a, b in zip(F, Fo):
+        np.testing.assert_allclose(a, b, rtol=2e-3, atol=1e-5 * np.abs(b).max())
+
+
+def test_ntd4_limits():
+    X, _, F0, G0, _ = inputs.small_problem((6, 5, 4, 8), 2, (2, 2, 2, 2), 2, seed=19)
+    with pytest.raises(native.NncError) as ei:  # no BF16 form for d = 4
+        _run_ntd(X, F0, G0, 2, torch.float32, precision="bf16")
+    assert ei.value.status == -6
+    Xb = X.copy()
+    Xb[1, 2, 3, 4] = -1.0
+    with pytest.raises(native.NncError) as ei:
+        _run_ntd(Xb, F0, G0, 2, torch.float64)
+    assert ei.value.status == -2
+    # A core slice of 64 x 8 x 8 doubles (256 KB) is over the 200 KB limit.
+    m = (64, 64, 8, 8)
+    F0b = [np.ones((n, k)) for n, k in zip((6, 5, 4, 8), m)]
+    with pytest.raises(native.NncError) as ei:
+        _run_ntd(X, F0b, np.ones(m), 2, torch.float64)
+    assert ei.value.status == -6
+    # Zero sweeps leave F and G as given.
+    err0, _, F1, G1 = _run_ntd(X, F0, G0, 0, torch.float64, trace=False)
+    for a, b in zip(F1, F0):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(G1, G0)
+    assert abs(err0 - orc.rel_err_tucker(X, G0, F0)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
 # nnCP of the core, batched fits, lift, residual
 # ---------------------------------------------------------------------------
 
@@ -213,3 +295,18 @@ def test_alg1_end_to_end_fp64():
     Bo, _ = orc.nncp_fit(Go, B0, 60)
     ref = orc.rel_err_cp(X, orc.lift(Fo, Bo))
     assert abs(rn / xn - ref) < 1e-9
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_residual_4way(dtype):
+    dims, m, r = (17, 23, 9, 31), (4, 6, 3, 5), 5
+    X, _, F0, G0, _ = inputs.small_problem(dims, 3, m, r, seed=23)
+    rn, xn = native.recon_residual(_t(X, dtype), [_t(f, dtype) for f in F0], _t(G0, dtype))
+    ref = orc.rel_err_tucker(X, G0, F0)
+    assert abs(rn / xn - ref) <= (1e-11 if dtype == torch.float64 else 1e-5) * ref
+    rng = np.random.default_rng(24)
+    A = [rng.random((n, r)) for n in dims]
+    rn, xn = native.recon_residual(_t(X, dtype), [_t(a, dtype) for a in A])
+    ref = orc.rel_err_cp(X, A)
+    assert abs(rn / xn - ref) <= (1e-12 if dtype == torch.float64 else 1e-6) * max(1.0, ref)
+    assert abs(xn - orc.frobenius(X)) <= 1e-6 * xn
