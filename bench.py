@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-precision-form", action="store_true")
     p.add_argument("--no-differentiation-form", action="store_true")
     p.add_argument("--no-batching-form", action="store_true")
+    p.add_argument("--no-4way-ntd", action="store_true")
     p.add_argument("--no-multirank-study", action="store_true")
     return p.parse_args()
 
@@ -460,6 +461,40 @@ def differentiation_form(dev):
             "final_lifted_rel_err": float(np.sqrt(2 * max(loss, 0.0)) / xn)}
 
 
+def ntd_4way(dev):
+    """nnTD of the 4-way 128^3 x 64 workload (two TF32x3 passes over X per
+    sweep, the d-way mode-product sweep): sweeps/s of device time (marginal
+    over the setup) and the final relative error."""
+    import numpy as np
+    import torch
+
+    from paper_1909_07570_gb300 import inputs, native
+    w = inputs.WORKLOADS["cp12_128x128x128x64_m24_fp32"]
+    X64, _, F0, G0, _ = inputs.make_problem(w)
+    X = torch.tensor(X64, dtype=torch.float32, device=dev)
+    del X64
+    stream = torch.cuda.current_stream()
+
+    def run(sweeps):
+        F = [torch.tensor(f, dtype=torch.float32, device=dev) for f in F0]
+        G = torch.tensor(G0, dtype=torch.float32, device=dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, tr = native.ntd_fit(X, F, G, sweeps, precision="fp32", rel_err=False)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), float(tr[-1])
+
+    run(2)
+    short = min(run(10)[0] for _ in range(2))
+    full, err = min(run(w.iters) for _ in range(2))
+    per_sweep = (full - short) / (w.iters - 10)
+    return {"workload": w.name, "dims": list(w.dims), "m": list(w.m), "sweeps": w.iters,
+            "ms": round(full, 2), "sweeps_per_s": round(1e3 / per_sweep, 2),
+            "x_bytes_per_sweep": 2 * int(np.prod(w.dims)) * 4, "final_rel_err": err}
+
+
 def batching_form(dev):
     """Many uneven nnTD problems (the batching workload: 64 planted tensors with
     modes in [32, 256], m = 2r) through ntd_fit_batched, then every core fitted
@@ -588,6 +623,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_differentiation_form:
         import torch
         result["differentiation_form"] = differentiation_form(torch.device("cuda", 0))
+    if rank == 0 and world == 1 and not args.no_4way_ntd:
+        import torch
+        result["ntd_4way"] = ntd_4way(torch.device("cuda", 0))
     if rank == 0 and world == 1 and not args.no_batching_form:
         import torch
         result["batching_form"] = batching_form(torch.device("cuda", 0))

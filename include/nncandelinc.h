@@ -82,9 +82,8 @@ typedef struct {
  *  d          3 or 4. d = 4 runs the same sweep on the d-way mode-product
  *             machinery of the differentiation form (two passes over X per
  *             sweep, the FP32 passes on the TF32x3 tensor-core kernel with X
- *             viewed as dims[0] x dims[1]*dims[2] x dims[3]); it needs every
- *             core slice prod_{k!=n} m[k] within 200 KB (else UNSUPPORTED)
- *             and has no NNC_BF16_REFINE form (UNSUPPORTED)
+ *             viewed as dims[0] x dims[1]*dims[2] x dims[3]); it has no
+ *             NNC_BF16_REFINE form (UNSUPPORTED)
  *  dims, m    host arrays of d entries; 1 <= m[n] <= 64, dims[n] >= 1
  *  F          host array of d device pointers: initial F^(n) (> 0) in,
  *             fitted F^(n) out
@@ -95,7 +94,7 @@ typedef struct {
  *  rel_err    host, or NULL: final relative error from one explicit FP64
  *             pass over X (as recon_residual)
  * Errors: INVALID_ARG, NEGATIVE_INPUT, NONFINITE (checked on X before any
- * sweep), UNSUPPORTED (the d = 4 limits above), CUDA, ALLOC.
+ * sweep), UNSUPPORTED (NNC_BF16_REFINE with d = 4), CUDA, ALLOC.
  */
 int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precision,
             const nnc_opts* opts, void* const* F, void* G, double* rel_err_trace,

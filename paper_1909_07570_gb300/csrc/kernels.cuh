@@ -19,12 +19,18 @@ cudaError_t launch_ttm(const T* Y, int64_t L, int J, int64_t C, const T* Fm, int
                        cudaStream_t s);
 
 // out[i, a] = sum_{l, c} Y[(l * NI + i) * C + c] * G[(l * MA + a) * C + c]
-// Y is (L, NI, C), G is (L, MA, C), out is NI x MA. It is the product of the
-// mode-n unfoldings unfold_n(Y) unfold_n(G)^T when the tensors are viewed
-// with mode n in the middle.
+// Y is (L, NI, C), G is (L, MA, C), out is NI x MA (MA <= 64, L C < 2^31). It
+// is the product of the mode-n unfoldings unfold_n(Y) unfold_n(G)^T when the
+// tensors are viewed with mode n in the middle. The flattened (l, c) range is
+// split over blocks when the rows alone would not fill the GPU; the partial
+// sums (at most part_cap elements of `part`) are added in split order.
 template <typename T>
 cudaError_t launch_pair_contract(const T* Y, const T* G, int64_t L, int NI, int MA, int64_t C,
-                                 T* out, cudaStream_t s);
+                                 T* out, T* part, size_t part_cap, cudaStream_t s);
+
+// out[i] = sum_{p < splits} part[p n + i], p in order.
+template <typename T>
+cudaError_t launch_reduce_splits(const T* part, int splits, int64_t n, T* out, cudaStream_t s);
 
 // F[i, a] <- max(F[i, a] * Num[i, a] / max(sum_b F[i, b] H[b, a], eps), 0),
 // F and Num N x M, H M x M.
@@ -38,11 +44,13 @@ cudaError_t launch_elementwise_mu(T* theta, const T* num, const T* den, int64_t 
                                   cudaStream_t s);
 
 // trace[(*counter) * stride] = sqrt(max(x2 - 2 <M, G> + <G, Dn>, 0) / x2), FP64
-// sums over n core entries (one block); then *counter += 1.
+// sums over n core entries (per-block partials in `part`, 2 kIdentityBlocks
+// doubles, added in block order); then *counter += 1.
+constexpr int kIdentityBlocks = 128;
 template <typename T>
 cudaError_t launch_residual_identity(const T* M, const T* G, const T* Dn, int64_t n,
                                      const double* x2, double* trace, int stride, int* counter,
-                                     cudaStream_t s);
+                                     double* part, cudaStream_t s);
 
 // One pass over X: sum of squares (FP64) and counts of negative and
 // non-finite entries. part holds >= 3 * kStatBlocks doubles, out 3 doubles:

@@ -855,8 +855,8 @@ int nmf_fit(const T* A, int64_t N, int r, int m, int iters, double eps, T* F, T*
 // in FP64. Z_1 .. Z_{d-1} come from T_last = X x_d F^(d)T (U0 after mode 1)
 // and Z_d from T_first = X x_1 F^(1)T formed after mode d-1, so every Z_n sees
 // the factors of modes k < n already updated (Gauss-Seidel) and X is read twice
-// per sweep. The unfolding products hold one slice of Z_n or of G x S in
-// shared memory: prod_{k!=n} m_k entries of T for every n, at most 200 KB.
+// per sweep. The unfolding products are split-K contractions over the
+// flattened (modes before n, modes after n) index.
 template <typename T>
 int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tensor_cores,
                  int iters, double eps, T* const* F, T* G, double* trace, double* rel_err,
@@ -864,8 +864,6 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
   if (d != 3 && d != 4) return NNC_ERR_INVALID_ARG;
   int64_t nc = 1;
   for (int k = 0; k < d; ++k) nc *= m[k];
-  for (int n = 0; n < d; ++n)
-    if (nc / m[n] * (int64_t)sizeof(T) > 200 * 1024) return NNC_ERR_UNSUPPORTED;
   Scratch sc(s);
   Work<T> w;
   NNC_TRY(setup(w, X, d, dims, m, /*r=*/1, tensor_cores, sc, s));
@@ -890,6 +888,8 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
   NNC_TRY(sc.get(&M, (size_t)nc));
   NNC_TRY(sc.get(&D, (size_t)nc));
   for (int k = 0; k < d; ++k) NNC_TRY(sc.get(&S[k], (size_t)m[k] * m[k]));
+  double* idpart = nullptr;
+  NNC_TRY(sc.get(&idpart, 2 * kIdentityBlocks));
   NNC_TRY(sc.get(&dummy, 1));
   NNC_TRY(sc.get(&counter, 1));
   NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
@@ -922,10 +922,12 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
       int64_t pre = 1, post = 1;
       for (int j = 0; j < n; ++j) pre *= m[j];
       for (int j = n + 1; j < d; ++j) post *= m[j];
-      NNC_CUDA_TRY(launch_pair_contract<T>(Z, G, pre, (int)dims[n], m[n], post, num, cs));
+      NNC_CUDA_TRY(launch_pair_contract<T>(Z, G, pre, (int)dims[n], m[n], post, num, w.split,
+                                           w.split_cap, cs));
       // H_n from G x_{k!=n} S_k, formed in M (free until the core update).
       NNC_TRY(core_times_grams(n, M, cs));
-      NNC_CUDA_TRY(launch_pair_contract<T>(M, G, pre, m[n], m[n], post, w.H, cs));
+      NNC_CUDA_TRY(launch_pair_contract<T>(M, G, pre, m[n], m[n], post, w.H, w.split,
+                                           w.split_cap, cs));
       NNC_CUDA_TRY(launch_factor_mu<T>(F[n], num, w.H, dims[n], m[n], eps, cs));
       NNC_TRY(launch_gram<T>(F[n], dims[n], m[n], S[n], cs));
       if (n == 0 && d > 2) NNC_TRY(make_u0(w, F[0], cs));
@@ -937,7 +939,8 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
     NNC_TRY(core_times_grams(-1, D, cs));
     NNC_CUDA_TRY(launch_elementwise_mu<T>(G, M, D, nc, eps, cs));
     NNC_TRY(core_times_grams(-1, D, cs));
-    NNC_CUDA_TRY(launch_residual_identity<T>(M, G, D, nc, w.stats, tr, stride, counter, cs));
+    NNC_CUDA_TRY(
+        launch_residual_identity<T>(M, G, D, nc, w.stats, tr, stride, counter, idpart, cs));
     return NNC_OK;
   }));
   NNC_TRY(check_tc(w, s));

@@ -31,8 +31,7 @@ int nncp_tensor_fit(const T* X, int d, const int64_t* dims, int r, bool tensor_c
 // nnTD of a d-way X (d = 3 or 4) by `iters` MU sweeps (Alg. 1, first step):
 // F^(n) (dims[n] x m[n]) and G in place; trace (device, optional) gets the
 // relative error after each sweep from the FP64 identity, rel_err (host,
-// optional) the final one from an explicit pass over X. UNSUPPORTED when a
-// slice prod_{k!=n} m_k of the core exceeds 200 KB.
+// optional) the final one from an explicit pass over X.
 template <typename T>
 int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tensor_cores,
                  int iters, double eps, T* const* F, T* G, double* trace, double* rel_err,

@@ -7,30 +7,66 @@
 namespace nnc {
 namespace {
 
-// One block per output row i: the slice Y[:, i, :] is staged in shared memory,
-// then each warp takes outputs a = warp, warp + nwarps, ... and sums
-// Y[l, i, c] * G[l, a, c] over the flattened (l, c) with its lanes.
+// out[i, a] (split s) = sum over k in the split's range of Y[l, i, c] G[l, a, c],
+// k = l C + c. A block takes kCtRows rows i and one k range; chunks of kCtK
+// consecutive k of both operands are staged in shared memory (consecutive k
+// are consecutive c within a row of Y or G, so the loads coalesce when C is
+// large). Thread (ty, tx) keeps rows 2 ty, 2 ty + 1 x a = tx + 16 u (u < 4).
+constexpr int kCtRows = 32, kCtK = 32, kCtThreads = 256, kCtMaxA = 64;
+
 template <typename T>
-__global__ void pair_contract_kernel(const T* __restrict__ Y, const T* __restrict__ G, int64_t L,
-                                     int NI, int MA, int64_t C, T* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ys = reinterpret_cast<T*>(smem_raw);
-  const int i = blockIdx.x;
-  const int64_t LC = L * C;
-  for (int64_t e = threadIdx.x; e < LC; e += blockDim.x) {
-    const int64_t l = e / C, c = e % C;
-    ys[e] = Y[(l * NI + i) * C + c];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int a = warp; a < MA; a += nwarps) {
-    T s = T(0);
-    for (int64_t e = lane; e < LC; e += 32) {
-      const int64_t l = e / C, c = e % C;
-      s = fma(ys[e], G[(l * MA + a) * C + c], s);
+__global__ void __launch_bounds__(kCtThreads)
+contract_kernel(const T* __restrict__ Y, const T* __restrict__ G, int C, int NI, int MA, int K,
+                int k_per_split, T* __restrict__ out) {
+  __shared__ T Ys[kCtK][kCtRows + 1];
+  __shared__ T Gs[kCtK][kCtMaxA + 1];
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * kCtRows;
+  const int kbeg = blockIdx.y * k_per_split;
+  const int kend = min(K, kbeg + k_per_split);
+  const int ty = tid >> 4, tx = tid & 15;
+  const int kk = tid & 31, sub = tid >> 5;  // the loads: one k per lane, rows by warp
+  T acc[2][4];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[r][u] = T(0);
+  for (int k0 = kbeg; k0 < kend; k0 += kCtK) {
+    const int k = k0 + kk;
+    const bool kin = k < kend;
+    const int l = kin ? k / C : 0;
+    const int c = kin ? k - l * C : 0;
+#pragma unroll
+    for (int r = sub; r < kCtRows; r += kCtThreads / 32) {
+      const int i = i0 + r;
+      Ys[kk][r] = (kin && i < NI) ? Y[((int64_t)l * NI + i) * C + c] : T(0);
     }
-    s = warp_sum(s);
-    if (lane == 0) out[(int64_t)i * MA + a] = s;
+#pragma unroll
+    for (int a = sub; a < kCtMaxA; a += kCtThreads / 32)
+      Gs[kk][a] = (kin && a < MA) ? G[((int64_t)l * MA + a) * C + c] : T(0);
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < kCtK; ++q) {
+      const T y0 = Ys[q][2 * ty], y1 = Ys[q][2 * ty + 1];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T g = Gs[q][tx + 16 * u];
+        acc[0][u] = fma(y0, g, acc[0][u]);
+        acc[1][u] = fma(y1, g, acc[1][u]);
+      }
+    }
+    __syncthreads();
+  }
+  T* o = out + (int64_t)blockIdx.y * NI * MA;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int i = i0 + 2 * ty + r;
+    if (i >= NI) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int a = tx + 16 * u;
+      if (a < MA) o[(int64_t)i * MA + a] = acc[r][u];
+    }
   }
 }
 
@@ -68,17 +104,36 @@ __global__ void elementwise_mu_kernel(T* __restrict__ th, const T* __restrict__ 
   }
 }
 
+// Partials of <M, G> and <G, Dn> in FP64: block b sums the entries
+// b, b + B, b + 2B, ... of its grid stride (B = blocks x threads).
 template <typename T>
-__global__ void residual_identity_kernel(const T* __restrict__ M, const T* __restrict__ G,
-                                         const T* __restrict__ Dn, int64_t n,
-                                         const double* __restrict__ x2, double* trace,
-                                         int stride, int* counter) {
+__global__ void identity_part_kernel(const T* __restrict__ M, const T* __restrict__ G,
+                                     const T* __restrict__ Dn, int64_t n, double* part) {
   __shared__ double sh[32];
   double mg = 0.0, gd = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const double g = (double)G[i];
     mg += (double)M[i] * g;
     gd += g * (double)Dn[i];
+  }
+  mg = block_sum(mg, sh);
+  gd = block_sum(gd, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = mg;
+    part[2 * blockIdx.x + 1] = gd;
+  }
+}
+
+// The partials added in block order, then the trace entry.
+__global__ void identity_final_kernel(const double* __restrict__ part, int nb,
+                                      const double* __restrict__ x2, double* trace, int stride,
+                                      int* counter) {
+  __shared__ double sh[32];
+  double mg = 0.0, gd = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    mg += part[2 * b];
+    gd += part[2 * b + 1];
   }
   mg = block_sum(mg, sh);
   gd = block_sum(gd, sh);
@@ -146,16 +201,29 @@ unsigned grid_for(int64_t n, int threads, int64_t cap = 4096) {
 
 template <typename T>
 cudaError_t launch_pair_contract(const T* Y, const T* G, int64_t L, int NI, int MA, int64_t C,
-                                 T* out, cudaStream_t s) {
-  const size_t smem = (size_t)(L * C) * sizeof(T);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  if (smem > 48 * 1024) {
-    cudaError_t e = raise_smem_limit((const void*)pair_contract_kernel<T>, smem);
-    if (e != cudaSuccess) return e;
-  }
-  pair_contract_kernel<T><<<NI, 256, smem, s>>>(Y, G, L, NI, MA, C, out);
+                                 T* out, T* part, size_t part_cap, cudaStream_t s) {
+  if (L < 1 || NI < 1 || MA < 1 || MA > kCtMaxA || C < 1 || L * C > 2147483647LL)
+    return cudaErrorInvalidValue;
+  const int K = (int)(L * C);
+  const int64_t row_tiles = ceil_div((int64_t)NI, kCtRows);
+  if (row_tiles > 65535) return cudaErrorInvalidValue;
+  // Splits of k: about two blocks per SM, at least 4 chunks per split, and
+  // the partials within the scratch.
+  int64_t splits = ceil_div(2LL * device_sm_count(), row_tiles);
+  const int64_t by_k = K / (4 * kCtK);
+  const int64_t by_cap = part ? (int64_t)(part_cap / ((size_t)NI * MA)) : 1;
+  if (splits > by_k) splits = by_k;
+  if (splits > by_cap) splits = by_cap;
+  if (splits < 1) splits = 1;
+  const int per = (int)(ceil_div(ceil_div((int64_t)K, splits), kCtK) * kCtK);
+  splits = ceil_div((int64_t)K, per);
+  T* dst = splits > 1 ? part : out;
+  contract_kernel<T><<<dim3((unsigned)row_tiles, (unsigned)splits), kCtThreads, 0, s>>>(
+      Y, G, (int)C, NI, MA, K, per, dst);
   note_launch(s);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  return launch_reduce_splits<T>(part, (int)splits, (int64_t)NI * MA, out, s);
 }
 
 template <typename T>
@@ -182,8 +250,11 @@ cudaError_t launch_elementwise_mu(T* theta, const T* num, const T* den, int64_t 
 template <typename T>
 cudaError_t launch_residual_identity(const T* M, const T* G, const T* Dn, int64_t n,
                                      const double* x2, double* trace, int stride, int* counter,
-                                     cudaStream_t s) {
-  residual_identity_kernel<T><<<1, 1024, 0, s>>>(M, G, Dn, n, x2, trace, stride, counter);
+                                     double* part, cudaStream_t s) {
+  const unsigned nb = grid_for(n, 256, kIdentityBlocks);
+  identity_part_kernel<T><<<nb, 256, 0, s>>>(M, G, Dn, n, part);
+  note_launch(s);
+  identity_final_kernel<<<1, 256, 0, s>>>(part, (int)nb, x2, trace, stride, counter);
   note_launch(s);
   return cudaGetLastError();
 }
@@ -207,13 +278,13 @@ cudaError_t launch_convert(const T* src, U* dst, int64_t n, cudaStream_t s) {
 
 #define NNC_INST(T)                                                                            \
   template cudaError_t launch_pair_contract<T>(const T*, const T*, int64_t, int, int, int64_t,  \
-                                               T*, cudaStream_t);                              \
+                                               T*, T*, size_t, cudaStream_t);                  \
   template cudaError_t launch_factor_mu<T>(T*, const T*, const T*, int64_t, int, double,       \
                                            cudaStream_t);                                      \
   template cudaError_t launch_elementwise_mu<T>(T*, const T*, const T*, int64_t, double,       \
                                                 cudaStream_t);                                 \
   template cudaError_t launch_residual_identity<T>(const T*, const T*, const T*, int64_t,      \
-                                                   const double*, double*, int, int*,          \
+                                                   const double*, double*, int, int*, double*, \
                                                    cudaStream_t);                              \
   template cudaError_t launch_tensor_stats<T>(const T*, int64_t, double*, double*, cudaStream_t);
 NNC_INST(float)

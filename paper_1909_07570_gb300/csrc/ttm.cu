@@ -241,6 +241,18 @@ cudaError_t launch_ttm(const T* Y, int64_t L, int J, int64_t C, const T* Fm, int
   return cudaErrorInvalidValue;
 }
 
+template <typename T>
+cudaError_t launch_reduce_splits(const T* part, int splits, int64_t n, T* out, cudaStream_t s) {
+  const int64_t blocks = ceil_div(n, 256) < 4096 ? ceil_div(n, 256) : 4096;
+  reduce_splits_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(part, splits, n, out);
+  note_launch(s);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_reduce_splits<float>(const float*, int, int64_t, float*,
+                                                 cudaStream_t);
+template cudaError_t launch_reduce_splits<double>(const double*, int, int64_t, double*,
+                                                  cudaStream_t);
 template cudaError_t launch_ttm<float>(const float*, int64_t, int, int64_t, const float*, int64_t,
                                        int64_t, int, float*, float*, size_t, cudaStream_t);
 template cudaError_t launch_ttm<double>(const double*, int64_t, int, int64_t, const double*,
