@@ -147,4 +147,33 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
   return r;
 }
 
+// ---- cp.async staging (element granularity, zero fill outside the range) ----
+template <typename T>
+__device__ __forceinline__ void cp_elem(T* dst, const T* src, bool valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  const int n = valid ? (int)sizeof(T) : 0;
+  if constexpr (sizeof(T) == 4) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n)
+                 : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n)
+                 : "memory");
+  }
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// 16-byte cp.async of one vector (16 / sizeof(T) elements); the first `valid`
+// elements are copied, the rest of the vector is zero.
+template <typename T>
+__device__ __forceinline__ void cp_vec(T* dst, const T* src, int valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  const int n = valid * (int)sizeof(T);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n)
+               : "memory");
+}
+
 }  // namespace nnc

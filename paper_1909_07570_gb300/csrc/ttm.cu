@@ -12,8 +12,14 @@
 //     flattened (l, c) columns, streams them along j with coalesced loads and
 //     keeps QP outputs per column in registers; Fm rows are broadcast from
 //     shared memory.
+//   * ttm_cols_pipe (C > 1, rows of C 16-byte aligned, C >= half a tile): the
+//     same register tiling, with the block's 256 TC columns of one l staged
+//     through a 3-deep cp.async ring of 16 rows j, so that two chunks of the
+//     slab are in flight while the third is consumed.
 // Both accumulate in T and, when one pass would not fill the GPU, split J
 // across blocks; partial sums are then added in split order (deterministic).
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace nnc {
@@ -153,6 +159,116 @@ ttm_cols_kernel(const T* __restrict__ Y, int64_t L, int J, int64_t C, int j_per_
   }
 }
 
+constexpr int kPipeBJ = 16;
+constexpr int kPipeStages = 3;
+
+template <typename T, int QP, int TC>
+constexpr size_t pipe_smem_bytes() {
+  return (size_t)kPipeStages * kPipeBJ * (kColsThreads * TC + QP) * sizeof(T);
+}
+
+// Columns c0 .. c0 + BC - 1 of slab l (BC = 256 TC; blockIdx.x = l tiles_per_l
+// + tile), rows j of split blockIdx.y. Rows and columns past the ends are
+// staged as zeros (Fm rows too), so every chunk runs all kPipeBJ rows.
+template <typename T, int QP, int TC>
+__global__ void __launch_bounds__(kColsThreads, QP * TC * sizeof(T) < 256 ? 2 : 1)
+ttm_cols_pipe_kernel(const T* __restrict__ Y, int64_t L, int J, int64_t C, int64_t tiles_per_l,
+                     int j_per_split, const T* __restrict__ Fm, int64_t fs_j, int64_t fs_q, int Q,
+                     T* __restrict__ out) {
+  constexpr int BC = kColsThreads * TC;
+  constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte copy
+  constexpr int CPR = BC / V;             // copies per staged row
+  static_assert(QP % V == 0, "QP must be a whole number of 16-byte vectors");
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ys = reinterpret_cast<T*>(smem_raw);      // [stage][kPipeBJ][BC]
+  T* Fs = Ys + kPipeStages * kPipeBJ * BC;     // [stage][kPipeBJ][QP]
+  const int tid = threadIdx.x;
+  const int64_t l = blockIdx.x / tiles_per_l;
+  const int64_t c0 = (int64_t)(blockIdx.x % tiles_per_l) * BC;
+  const int jbeg = blockIdx.y * j_per_split;
+  const int jend = min(J, jbeg + j_per_split);
+  const int nchunks = (jend - jbeg + kPipeBJ - 1) / kPipeBJ;
+  const T* yl = Y + l * (int64_t)J * C;
+
+  // This thread's copies: vector v of the rows jr, jr + RP, ... of a chunk.
+  constexpr int RP = kColsThreads / CPR;
+  static_assert(kColsThreads % CPR == 0 && kPipeBJ % RP == 0, "copy layout");
+  const int v = tid % CPR, jr = tid / CPR;
+  const bool cok = c0 + (int64_t)v * V < C;
+  const T* ysrc = yl + c0 + (int64_t)v * V;
+  auto issue = [&](int chunk) {
+    const int slot = chunk % kPipeStages;
+    const int j0 = jbeg + chunk * kPipeBJ;
+    T* ys = Ys + slot * kPipeBJ * BC + v * V;
+#pragma unroll
+    for (int jj = jr; jj < kPipeBJ; jj += RP) {
+      const int j = j0 + jj;
+      const bool ok = cok && j < jend;
+      cp_vec(ys + jj * BC, ok ? ysrc + (int64_t)j * C : yl, ok ? V : 0);
+    }
+    T* fs = Fs + slot * kPipeBJ * QP;
+    for (int e = tid; e < kPipeBJ * QP; e += kColsThreads) {
+      const int jj = e / QP, q = e % QP;
+      const int j = j0 + jj;
+      fs[e] = (q < Q && j < jend) ? Fm[j * fs_j + q * fs_q] : T(0);
+    }
+  };
+
+  T acc[TC][QP];
+#pragma unroll
+  for (int t = 0; t < TC; ++t)
+#pragma unroll
+    for (int q = 0; q < QP; ++q) acc[t][q] = T(0);
+
+#pragma unroll
+  for (int p = 0; p < kPipeStages - 1; ++p) {
+    if (p < nchunks) issue(p);
+    cp_commit();
+  }
+  for (int it = 0; it < nchunks; ++it) {
+    if (it + kPipeStages - 1 < nchunks) issue(it + kPipeStages - 1);
+    cp_commit();
+    cp_wait<kPipeStages - 1>();
+    __syncthreads();
+    const int slot = it % kPipeStages;
+    const T* ys = Ys + slot * kPipeBJ * BC;
+    const T* fs = Fs + slot * kPipeBJ * QP;
+#pragma unroll 4
+    for (int jj = 0; jj < kPipeBJ; ++jj) {
+      T v[TC];
+#pragma unroll
+      for (int t = 0; t < TC; ++t) v[t] = ys[jj * BC + tid + t * kColsThreads];
+      const Vec* fr = reinterpret_cast<const Vec*>(fs + jj * QP);
+#pragma unroll
+      for (int g = 0; g < QP / V; ++g) {
+        const Vec f4 = fr[g];
+        T f[V];
+        if constexpr (sizeof(T) == 4) {
+          f[0] = f4.x; f[1] = f4.y; f[2] = f4.z; f[3] = f4.w;
+        } else {
+          f[0] = f4.x; f[1] = f4.y;
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u)
+#pragma unroll
+          for (int t = 0; t < TC; ++t) acc[t][g * V + u] = fma(f[u], v[t], acc[t][g * V + u]);
+      }
+    }
+    __syncthreads();
+  }
+
+  T* o = out + (int64_t)blockIdx.y * L * Q * C + l * Q * C;
+#pragma unroll
+  for (int t = 0; t < TC; ++t) {
+    const int64_t c = c0 + tid + t * kColsThreads;
+    if (c >= C) continue;
+#pragma unroll
+    for (int q = 0; q < QP; ++q)
+      if (q < Q) o[(int64_t)q * C + c] = acc[t][q];
+  }
+}
+
 template <typename T>
 __global__ void reduce_splits_kernel(const T* __restrict__ part, int splits, int64_t n,
                                      T* __restrict__ out) {
@@ -203,7 +319,24 @@ cudaError_t ttm_dispatch(const T* Y, int64_t L, int J, int64_t C, const T* Fm, i
   } else {
     const int64_t ncols = L * C;
     const bool wide = (QP <= 32) && ceil_div(ncols, 2 * kColsThreads) >= 2LL * device_sm_count();
-    if (wide) {
+    constexpr int PTC = (sizeof(T) == 4 && QP <= 32) ? 2 : 1;
+    constexpr int PBC = kColsThreads * PTC;
+    constexpr int PV = 16 / (int)sizeof(T);
+    const bool pipe = C % PV == 0 && reinterpret_cast<uintptr_t>(Y) % 16 == 0 && 2 * C >= PBC;
+    if (pipe) {
+      const int64_t tiles_per_l = ceil_div(C, (int64_t)PBC);
+      const int64_t blocks = L * tiles_per_l;
+      if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+      splits = choose_splits(blocks, J, out_elems, split_cap, kColsBJ, &per);
+      T* dst = splits > 1 ? split_buf : out;
+      constexpr size_t smem = pipe_smem_bytes<T, QP, PTC>();
+      const cudaError_t e0 = raise_smem_limit((const void*)ttm_cols_pipe_kernel<T, QP, PTC>, smem);
+      if (e0 != cudaSuccess) return e0;
+      dim3 grid((unsigned)blocks, (unsigned)splits);
+      ttm_cols_pipe_kernel<T, QP, PTC><<<grid, kColsThreads, smem, s>>>(
+          Y, L, J, C, tiles_per_l, per, Fm, fs_j, fs_q, Q, dst);
+      note_launch(s);
+    } else if (wide) {
       const int64_t blocks = ceil_div(ncols, 2 * kColsThreads);
       splits = choose_splits(blocks, J, out_elems, split_cap, kColsBJ, &per);
       T* dst = splits > 1 ? split_buf : out;
@@ -236,6 +369,7 @@ cudaError_t launch_ttm(const T* Y, int64_t L, int J, int64_t C, const T* Fm, int
   if (L <= 0 || J <= 0 || C <= 0 || Q <= 0) return cudaErrorInvalidValue;
   if (Q <= 8) return ttm_dispatch<T, 8>(Y, L, J, C, Fm, fs_j, fs_q, Q, out, split_buf, split_cap, s);
   if (Q <= 16) return ttm_dispatch<T, 16>(Y, L, J, C, Fm, fs_j, fs_q, Q, out, split_buf, split_cap, s);
+  if (Q <= 24) return ttm_dispatch<T, 24>(Y, L, J, C, Fm, fs_j, fs_q, Q, out, split_buf, split_cap, s);
   if (Q <= 32) return ttm_dispatch<T, 32>(Y, L, J, C, Fm, fs_j, fs_q, Q, out, split_buf, split_cap, s);
   if (Q <= 64) return ttm_dispatch<T, 64>(Y, L, J, C, Fm, fs_j, fs_q, Q, out, split_buf, split_cap, s);
   return cudaErrorInvalidValue;
