@@ -12,10 +12,10 @@
 //     flattened (l, c) columns, streams them along j with coalesced loads and
 //     keeps QP outputs per column in registers; Fm rows are broadcast from
 //     shared memory.
-//   * ttm_cols_pipe (C > 1, rows of C 16-byte aligned, C >= half a tile): the
-//     same register tiling, with the block's 256 TC columns of one l staged
-//     through a 3-deep cp.async ring of 16 rows j, so that two chunks of the
-//     slab are in flight while the third is consumed.
+//   * ttm_cols_pipe (C > 1, rows of C 16-byte aligned): the same register
+//     tiling, with the block's 256 TC flattened columns staged through a
+//     3-deep cp.async ring of 16 rows j, so that two chunks are in flight
+//     while the third is consumed.
 // Both accumulate in T and, when one pass would not fill the GPU, split J
 // across blocks; partial sums are then added in split order (deterministic).
 #include <type_traits>
@@ -167,13 +167,13 @@ constexpr size_t pipe_smem_bytes() {
   return (size_t)kPipeStages * kPipeBJ * (kColsThreads * TC + QP) * sizeof(T);
 }
 
-// Columns c0 .. c0 + BC - 1 of slab l (BC = 256 TC; blockIdx.x = l tiles_per_l
-// + tile), rows j of split blockIdx.y. Rows and columns past the ends are
-// staged as zeros (Fm rows too), so every chunk runs all kPipeBJ rows.
+// Flattened columns (l, c) col0 .. col0 + BC - 1 (BC = 256 TC, col0 =
+// blockIdx.x BC), rows j of split blockIdx.y. Each 16-byte copy stays in one
+// row (l, j) because C % V == 0. Rows and columns past the ends are staged as
+// zeros (Fm rows too), so every chunk runs all kPipeBJ rows.
 template <typename T, int QP, int TC>
 __global__ void __launch_bounds__(kColsThreads, QP * TC * sizeof(T) < 256 ? 2 : 1)
-ttm_cols_pipe_kernel(const T* __restrict__ Y, int64_t L, int J, int64_t C, int64_t tiles_per_l,
-                     int j_per_split, const T* __restrict__ Fm, int64_t fs_j, int64_t fs_q, int Q,
+ttm_cols_pipe_kernel(const T* __restrict__ Y, int64_t L, int J, int64_t C, int j_per_split, const T* __restrict__ Fm, int64_t fs_j, int64_t fs_q, int Q,
                      T* __restrict__ out) {
   constexpr int BC = kColsThreads * TC;
   constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte copy
@@ -184,19 +184,20 @@ ttm_cols_pipe_kernel(const T* __restrict__ Y, int64_t L, int J, int64_t C, int64
   T* Ys = reinterpret_cast<T*>(smem_raw);      // [stage][kPipeBJ][BC]
   T* Fs = Ys + kPipeStages * kPipeBJ * BC;     // [stage][kPipeBJ][QP]
   const int tid = threadIdx.x;
-  const int64_t l = blockIdx.x / tiles_per_l;
-  const int64_t c0 = (int64_t)(blockIdx.x % tiles_per_l) * BC;
+  const int64_t ncols = L * C;
+  const int64_t col0 = (int64_t)blockIdx.x * BC;
   const int jbeg = blockIdx.y * j_per_split;
   const int jend = min(J, jbeg + j_per_split);
   const int nchunks = (jend - jbeg + kPipeBJ - 1) / kPipeBJ;
-  const T* yl = Y + l * (int64_t)J * C;
 
   // This thread's copies: vector v of the rows jr, jr + RP, ... of a chunk.
   constexpr int RP = kColsThreads / CPR;
   static_assert(kColsThreads % CPR == 0 && kPipeBJ % RP == 0, "copy layout");
   const int v = tid % CPR, jr = tid / CPR;
-  const bool cok = c0 + (int64_t)v * V < C;
-  const T* ysrc = yl + c0 + (int64_t)v * V;
+  const int64_t vcol = col0 + (int64_t)v * V;
+  const bool cok = vcol < ncols;
+  const int64_t vl = cok ? vcol / C : 0;
+  const T* ysrc = Y + vl * (int64_t)J * C + (cok ? vcol - vl * C : 0);
   auto issue = [&](int chunk) {
     const int slot = chunk % kPipeStages;
     const int j0 = jbeg + chunk * kPipeBJ;
@@ -205,13 +206,16 @@ ttm_cols_pipe_kernel(const T* __restrict__ Y, int64_t L, int J, int64_t C, int64
     for (int jj = jr; jj < kPipeBJ; jj += RP) {
       const int j = j0 + jj;
       const bool ok = cok && j < jend;
-      cp_vec(ys + jj * BC, ok ? ysrc + (int64_t)j * C : yl, ok ? V : 0);
+      cp_vec(ys + jj * BC, ok ? ysrc + (int64_t)j * C : Y, ok ? V : 0);
     }
+    // The Fm rows of the chunk go the same way (element copies), so that no
+    // thread waits for them before the chunk it is about to consume.
     T* fs = Fs + slot * kPipeBJ * QP;
     for (int e = tid; e < kPipeBJ * QP; e += kColsThreads) {
       const int jj = e / QP, q = e % QP;
       const int j = j0 + jj;
-      fs[e] = (q < Q && j < jend) ? Fm[j * fs_j + q * fs_q] : T(0);
+      const bool ok = q < Q && j < jend;
+      cp_elem(fs + e, ok ? Fm + (j * fs_j + q * fs_q) : Fm, ok);
     }
   };
 
@@ -258,14 +262,16 @@ ttm_cols_pipe_kernel(const T* __restrict__ Y, int64_t L, int J, int64_t C, int64
     __syncthreads();
   }
 
-  T* o = out + (int64_t)blockIdx.y * L * Q * C + l * Q * C;
+  T* o = out + (int64_t)blockIdx.y * L * Q * C;
 #pragma unroll
   for (int t = 0; t < TC; ++t) {
-    const int64_t c = c0 + tid + t * kColsThreads;
-    if (c >= C) continue;
+    const int64_t col = col0 + tid + t * kColsThreads;
+    if (col >= ncols) continue;
+    const int64_t l = col / C;
+    T* ot = o + l * Q * C + (col - l * C);
 #pragma unroll
     for (int q = 0; q < QP; ++q)
-      if (q < Q) o[(int64_t)q * C + c] = acc[t][q];
+      if (q < Q) ot[(int64_t)q * C] = acc[t][q];
   }
 }
 
@@ -274,8 +280,17 @@ __global__ void reduce_splits_kernel(const T* __restrict__ part, int splits, int
                                      T* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    // Loads in groups of 8 (all in flight together), added in split order.
     T s = part[i];
-    for (int p = 1; p < splits; ++p) s += part[(int64_t)p * n + i];
+    int p = 1;
+    for (; p + 8 <= splits; p += 8) {
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = part[(int64_t)(p + u) * n + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; p < splits; ++p) s += part[(int64_t)p * n + i];
     out[i] = s;
   }
 }
@@ -319,22 +334,32 @@ cudaError_t ttm_dispatch(const T* Y, int64_t L, int J, int64_t C, const T* Fm, i
   } else {
     const int64_t ncols = L * C;
     const bool wide = (QP <= 32) && ceil_div(ncols, 2 * kColsThreads) >= 2LL * device_sm_count();
-    constexpr int PTC = (sizeof(T) == 4 && QP <= 32) ? 2 : 1;
-    constexpr int PBC = kColsThreads * PTC;
     constexpr int PV = 16 / (int)sizeof(T);
-    const bool pipe = C % PV == 0 && reinterpret_cast<uintptr_t>(Y) % 16 == 0 && 2 * C >= PBC;
+    const bool pipe = C % PV == 0 && reinterpret_cast<uintptr_t>(Y) % 16 == 0;
     if (pipe) {
-      const int64_t tiles_per_l = ceil_div(C, (int64_t)PBC);
-      const int64_t blocks = L * tiles_per_l;
+      // Two columns per thread when the grid still has two blocks per SM.
+      constexpr bool two = sizeof(T) == 4 && QP <= 32;
+      const bool use2 = two && ceil_div(ncols, 2 * kColsThreads) >= 2LL * device_sm_count();
+      const int64_t blocks = ceil_div(ncols, (int64_t)(use2 ? 2 : 1) * kColsThreads);
       if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
       splits = choose_splits(blocks, J, out_elems, split_cap, kColsBJ, &per);
       T* dst = splits > 1 ? split_buf : out;
-      constexpr size_t smem = pipe_smem_bytes<T, QP, PTC>();
-      const cudaError_t e0 = raise_smem_limit((const void*)ttm_cols_pipe_kernel<T, QP, PTC>, smem);
-      if (e0 != cudaSuccess) return e0;
       dim3 grid((unsigned)blocks, (unsigned)splits);
-      ttm_cols_pipe_kernel<T, QP, PTC><<<grid, kColsThreads, smem, s>>>(
-          Y, L, J, C, tiles_per_l, per, Fm, fs_j, fs_q, Q, dst);
+      if (use2) {
+        constexpr int PTC = two ? 2 : 1;
+        constexpr size_t smem = pipe_smem_bytes<T, QP, PTC>();
+        const cudaError_t e0 =
+            raise_smem_limit((const void*)ttm_cols_pipe_kernel<T, QP, PTC>, smem);
+        if (e0 != cudaSuccess) return e0;
+        ttm_cols_pipe_kernel<T, QP, PTC><<<grid, kColsThreads, smem, s>>>(
+            Y, L, J, C, per, Fm, fs_j, fs_q, Q, dst);
+      } else {
+        constexpr size_t smem = pipe_smem_bytes<T, QP, 1>();
+        const cudaError_t e0 = raise_smem_limit((const void*)ttm_cols_pipe_kernel<T, QP, 1>, smem);
+        if (e0 != cudaSuccess) return e0;
+        ttm_cols_pipe_kernel<T, QP, 1><<<grid, kColsThreads, smem, s>>>(Y, L, J, C, per, Fm, fs_j,
+                                                                         fs_q, Q, dst);
+      }
       note_launch(s);
     } else if (wide) {
       const int64_t blocks = ceil_div(ncols, 2 * kColsThreads);
