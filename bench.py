@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-differentiation-form", action="store_true")
     p.add_argument("--no-batching-form", action="store_true")
     p.add_argument("--no-4way-ntd", action="store_true")
+    p.add_argument("--no-paper-batch", action="store_true")
     p.add_argument("--no-multirank-study", action="store_true")
     return p.parse_args()
 
@@ -563,6 +564,26 @@ def multirank_study(dev, starts=1000, iters=5000):
             "summary": study.summary(res)}
 
 
+def paper_batch(dev):
+    """The batch experiment of Sec. 4.3 at the paper's size (1000 planted 40^3
+    tensors, canonical multirank (3, 4, 5), rank 5, 5000 sweeps per stage,
+    both algorithms) in FP32: device time of each batched stage (CUDA events),
+    decompositions per second, and the score summary."""
+    import torch
+
+    from paper_1909_07570_gb300 import inputs, study
+    probs = inputs.paper_batch_problems()
+    study.run_paper_batch(probs[:4], iters=10, dtype=torch.float32, device=dev)
+    t = {}
+    res = study.run_paper_batch(probs, dtype=torch.float32, device=dev, timings=t)
+    gpu_ms = sum(t.values())
+    pb = inputs.PAPER_BATCH
+    return {"workload": pb["name"], "tensors": len(probs), "sweeps_per_stage": pb["iters"],
+            "stage_ms": {k: round(v, 2) for k, v in t.items()}, "gpu_s": round(gpu_ms / 1e3, 3),
+            "decompositions_per_s": round(2 * len(probs) / (gpu_ms / 1e3), 1),
+            "summary": study.summary_batch(res)}
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -629,6 +650,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_batching_form:
         import torch
         result["batching_form"] = batching_form(torch.device("cuda", 0))
+    if rank == 0 and world == 1 and not args.no_paper_batch:
+        import torch
+        result["paper_batch"] = paper_batch(torch.device("cuda", 0))
     if rank == 0 and world == 1 and not args.no_multirank_study:
         import torch
         result["multirank_study"] = multirank_study(torch.device("cuda", 0))

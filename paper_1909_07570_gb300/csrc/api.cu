@@ -111,7 +111,7 @@ int nncp_run(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel_er
     const size_t b = nncp_smem_bytes(j, sizeof(T));
     smem = b > smem ? b : smem;
   }
-  if (smem > 200 * 1024) return NNC_ERR_UNSUPPORTED;
+  if (smem > 200 * 1024) return nncp_l2_batched<T>(n_jobs, jobs, o->iters, o->eps, rel_errs, s);
   Scratch sc(s);
   nncp_job* dev = nullptr;
   NNC_TRY(sc.get(&dev, (size_t)n_jobs));

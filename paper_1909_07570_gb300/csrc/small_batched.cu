@@ -227,6 +227,290 @@ ntd_small_kernel(const ntd_small_job* __restrict__ jobs, int iters, T eps, doubl
   store(static_cast<T*>(jb.G), G, ng);
 }
 
+// ---- problems whose X does not fit in shared memory -------------------------
+//
+// One thread block per problem as above, but X stays in global memory (with
+// two blocks per SM in flight, their tensors stay in L2) and a sweep reads it
+// twice, like ntd_fit: P3 = X x_3 F^(3)T serves modes 1 and 2, P1 = X x_1
+// F^(1)T (new F^(1)) mode 3 and the core. Factors, core, Grams and pass
+// results live in shared memory.
+
+// P[r, p] = sum_k X[r N3 + k] F[k, p], rows r < R of X viewed R x N3, p < Q
+// (F: N3 x Q in shared memory). One thread per row, Q accumulators; the rows
+// a warp walks share their L1 lines.
+template <typename T, int QM>
+__device__ void pass_rows(const T* __restrict__ X, int R, int N3, const T* F, int Q, T* P) {
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    T acc[QM];
+#pragma unroll
+    for (int p = 0; p < QM; ++p) acc[p] = T(0);
+    const T* x = X + (int64_t)r * N3;
+    for (int k = 0; k < N3; ++k) {
+      const T v = __ldg(x + k);
+      const T* f = F + k * Q;
+#pragma unroll
+      for (int p = 0; p < QM; ++p)
+        if (p < Q) acc[p] = fma(v, f[p], acc[p]);
+    }
+#pragma unroll
+    for (int p = 0; p < QM; ++p)
+      if (p < Q) P[r * Q + p] = acc[p];
+  }
+  __syncthreads();
+}
+
+// P[p, c] = sum_i F[i, p] X[i C + c], X viewed N1 x C (F: N1 x Q in shared
+// memory). One thread per column c: consecutive threads read consecutive c.
+template <typename T, int QM>
+__device__ void pass_cols(const T* __restrict__ X, int N1, int C, const T* F, int Q, T* P) {
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    T acc[QM];
+#pragma unroll
+    for (int p = 0; p < QM; ++p) acc[p] = T(0);
+    for (int i = 0; i < N1; ++i) {
+      const T v = __ldg(X + (int64_t)i * C + c);
+      const T* f = F + i * Q;
+#pragma unroll
+      for (int p = 0; p < QM; ++p)
+        if (p < Q) acc[p] = fma(f[p], v, acc[p]);
+    }
+#pragma unroll
+    for (int p = 0; p < QM; ++p)
+      if (p < Q) P[(int64_t)p * C + c] = acc[p];
+  }
+  __syncthreads();
+}
+
+// sum (X - X_hat)^2 and sum X^2 in FP64 with X_hat[r, k] = sum_c U[r, c] W[k, c]
+// (X viewed R x N3 in global memory, U: R x K and W: N3 x K in shared memory).
+template <typename T>
+__device__ void stream_residual(const T* __restrict__ X, int R, int N3, const T* U, const T* W,
+                                int K, double* red, double* out2) {
+  double s = 0.0, x = 0.0;
+  const int n = R * N3;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int r = e / N3, k = e - r * N3;
+    T h = T(0);
+    for (int c = 0; c < K; ++c) h = fma(U[r * K + c], W[k * K + c], h);
+    const double xv = (double)__ldg(X + e), dv = xv - (double)h;
+    s += dv * dv;
+    x += xv * xv;
+  }
+  s = block_sum(s, red);
+  x = block_sum(x, red);
+  if (threadIdx.x == 0) {
+    out2[0] = s;
+    out2[1] = x;
+  }
+  __syncthreads();
+}
+
+struct NtdL2Sizes {
+  int p, y, nm, mm, ng;
+};
+
+__host__ __device__ inline NtdL2Sizes ntd_l2_sizes(const int* N, const int* m) {
+  NtdL2Sizes z;
+  const int p3 = N[0] * N[1] * m[2], p1 = m[0] * N[1] * N[2];
+  z.p = p3 > p1 ? p3 : p1;
+  const int y1 = N[0] * m[1] * m[2], y2 = m[0] * N[1] * m[2], y3 = m[0] * m[1] * N[2];
+  z.y = y1 > y2 ? (y1 > y3 ? y1 : y3) : (y2 > y3 ? y2 : y3);
+  z.nm = 0;
+  z.mm = 0;
+  for (int k = 0; k < 3; ++k) {
+    z.nm = N[k] * m[k] > z.nm ? N[k] * m[k] : z.nm;
+    z.mm = m[k] * m[k] > z.mm ? m[k] * m[k] : z.mm;
+  }
+  z.ng = m[0] * m[1] * m[2];
+  return z;
+}
+
+size_t ntd_l2_elems(const ntd_small_job& j) {
+  const NtdL2Sizes z = ntd_l2_sizes(j.dims, j.m);
+  size_t f = 0, s = 0;
+  for (int k = 0; k < 3; ++k) {
+    f += (size_t)j.dims[k] * j.m[k];
+    s += (size_t)j.m[k] * j.m[k];
+  }
+  return f + s + (size_t)z.p + z.y + 2 * (size_t)z.nm + z.mm + 4 * (size_t)z.ng;
+}
+
+// nnTD of one job per block with X in global memory: the sweep of ntd_fit,
+// F^(1), F^(2), F^(3) by MU (Num_n from the pass results, H_n from the core
+// and the Grams), then G with M = Y3 x_3 F^(3)T and D = (G x_1 S1 x_2 S2) x_3
+// S3; the final relative error by one more stream over X.
+template <typename T, int QM>
+__global__ void __launch_bounds__(kThreads, 2)
+ntd_l2_kernel(const ntd_small_job* __restrict__ jobs, int iters, T eps, double* rel_errs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  __shared__ double nrm[2];
+  const ntd_small_job& jb = jobs[blockIdx.x];
+  const int* N = jb.dims;
+  const int* m = jb.m;
+  const T* X = static_cast<const T*>(jb.X);
+  const NtdL2Sizes z = ntd_l2_sizes(N, m);
+  T* F[3];
+  F[0] = reinterpret_cast<T*>(smem_raw);
+  F[1] = F[0] + N[0] * m[0];
+  F[2] = F[1] + N[1] * m[1];
+  T* G = F[2] + N[2] * m[2];
+  T* S[3];
+  S[0] = G + z.ng;
+  S[1] = S[0] + m[0] * m[0];
+  S[2] = S[1] + m[1] * m[1];
+  T* P = S[2] + m[2] * m[2];
+  T* Y = P + z.p;
+  T* num = Y + z.y;
+  T* den = num + z.nm;
+  T* H = den + z.nm;
+  T* W = H + z.mm;
+  T* W2 = W + z.ng;
+  T* M = W2 + z.ng;
+  for (int k = 0; k < 3; ++k) load(F[k], static_cast<const T*>(jb.F[k]), N[k] * m[k]);
+  load(G, static_cast<const T*>(jb.G), z.ng);
+  __syncthreads();
+  for (int k = 0; k < 3; ++k) sgemm(m[k], m[k], N[k], F[k], 1, m[k], F[k], m[k], 1, S[k]);
+
+  const int d3[3] = {N[0], N[1], m[2]};   // P3
+  const int d1[3] = {m[0], N[1], N[2]};   // P1
+  const int y1[3] = {N[0], m[1], m[2]};
+  const int y2[3] = {m[0], N[1], m[2]};
+  const int y3[3] = {m[0], m[1], N[2]};
+  for (int it = 0; it < iters; ++it) {
+    pass_rows<T, QM>(X, N[0] * N[1], N[2], F[2], m[2], P);  // P3 = X x_3 F3^T
+    // Mode 1: Num1 from Y1 = P3 x_2 F2^T, H1 from G x_2 S2 x_3 S3.
+    mp3(P, d3, 1, F[1], 1, m[1], m[1], Y);
+    unfold_dot(Y, y1, G, m, 0, num);
+    mp3(G, m, 1, S[1], m[1], 1, m[1], W);
+    mp3(W, m, 2, S[2], m[2], 1, m[2], W2);
+    unfold_dot(W2, m, G, m, 0, H);
+    sgemm(N[0], m[0], m[0], F[0], m[0], 1, H, m[0], 1, den);
+    mu(F[0], num, den, N[0] * m[0], eps);
+    sgemm(m[0], m[0], N[0], F[0], 1, m[0], F[0], m[0], 1, S[0]);
+    // Mode 2: Y2 = P3 x_1 F1^T (new F1), H2 from G x_1 S1 x_3 S3.
+    mp3(P, d3, 0, F[0], 1, m[0], m[0], Y);
+    unfold_dot(Y, y2, G, m, 1, num);
+    mp3(G, m, 0, S[0], m[0], 1, m[0], W);
+    mp3(W, m, 2, S[2], m[2], 1, m[2], W2);
+    unfold_dot(W2, m, G, m, 1, H);
+    sgemm(N[1], m[1], m[1], F[1], m[1], 1, H, m[1], 1, den);
+    mu(F[1], num, den, N[1] * m[1], eps);
+    sgemm(m[1], m[1], N[1], F[1], 1, m[1], F[1], m[1], 1, S[1]);
+    // Mode 3: P1 = X x_1 F1^T, Y3 = P1 x_2 F2^T, H3 from W2 = G x_1 S1 x_2 S2.
+    pass_cols<T, QM>(X, N[0], N[1] * N[2], F[0], m[0], P);
+    mp3(P, d1, 1, F[1], 1, m[1], m[1], Y);
+    unfold_dot(Y, y3, G, m, 2, num);
+    mp3(G, m, 0, S[0], m[0], 1, m[0], W);
+    mp3(W, m, 1, S[1], m[1], 1, m[1], W2);
+    unfold_dot(W2, m, G, m, 2, H);
+    sgemm(N[2], m[2], m[2], F[2], m[2], 1, H, m[2], 1, den);
+    mu(F[2], num, den, N[2] * m[2], eps);
+    sgemm(m[2], m[2], N[2], F[2], 1, m[2], F[2], m[2], 1, S[2]);
+    // Core: M = Y3 x_3 F3^T, D = W2 x_3 S3.
+    mp3(Y, y3, 2, F[2], 1, m[2], m[2], M);
+    mp3(W2, m, 2, S[2], m[2], 1, m[2], W);
+    mu(G, M, W, z.ng, eps);
+  }
+  // ||X - G x_k F_k|| / ||X||: U = G x_1 F1 x_2 F2 (N1, N2, m3), then X streamed.
+  const int dg[3] = {m[0], m[1], m[2]};
+  mp3(G, dg, 0, F[0], m[0], 1, N[0], Y);
+  mp3(Y, y1, 1, F[1], m[1], 1, N[1], P);
+  stream_residual(X, N[0] * N[1], N[2], P, F[2], m[2], red, nrm);
+  if (threadIdx.x == 0 && rel_errs) rel_errs[blockIdx.x] = sqrt(nrm[0] / nrm[1]);
+  for (int k = 0; k < 3; ++k) store(static_cast<T*>(jb.F[k]), F[k], N[k] * m[k]);
+  store(static_cast<T*>(jb.G), G, z.ng);
+}
+
+// nnCPD of a 3-way tensor per block with the tensor in global memory (the
+// sweep of nncp_core_fit: A^(n) <- MU(A^(n), MT_n, A^(n) V_n) for n = 1, 2, 3),
+// MT_n from two passes: T = X x_3 A3^T gives MT_1[i, q] = sum_j T[i, j, q]
+// A2[j, q] and MT_2[j, q] = sum_i T[i, j, q] A1[i, q] (new A1); T' = X x_1
+// A1^T gives MT_3[k, q] = sum_j T'[q, j, k] A2[j, q] (new A2).
+size_t cpx_l2_elems(const nncp_job& j) {
+  const size_t N1 = j.m[0], N2 = j.m[1], N3 = j.m[2], r = j.r;
+  const size_t t3 = N1 * N2 * r, t1 = r * N2 * N3;
+  size_t nmax = N1 > N2 ? N1 : N2;
+  nmax = nmax > N3 ? nmax : N3;
+  return (N1 + N2 + N3) * r + 3 * r * r + (t3 > t1 ? t3 : t1) + 2 * nmax * r + r * r;
+}
+
+template <typename T, int QM>
+__global__ void __launch_bounds__(kThreads, 2)
+cpx_l2_kernel(const nncp_job* __restrict__ jobs, int iters, T eps, double* rel_errs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  __shared__ double nrm[2];
+  const nncp_job& jb = jobs[blockIdx.x];
+  const int* N = jb.m;
+  const int r = jb.r;
+  const T* X = static_cast<const T*>(jb.G);
+  int nmax = N[0] > N[1] ? N[0] : N[1];
+  nmax = nmax > N[2] ? nmax : N[2];
+  const int t3 = N[0] * N[1] * r, t1 = r * N[1] * N[2];
+  T* A[3];
+  A[0] = reinterpret_cast<T*>(smem_raw);
+  A[1] = A[0] + N[0] * r;
+  A[2] = A[1] + N[1] * r;
+  T* Gr[3];
+  Gr[0] = A[2] + N[2] * r;
+  Gr[1] = Gr[0] + r * r;
+  Gr[2] = Gr[1] + r * r;
+  T* Tb = Gr[2] + r * r;
+  T* MT = Tb + (t3 > t1 ? t3 : t1);
+  T* den = MT + nmax * r;
+  T* V = den + nmax * r;
+  for (int k = 0; k < 3; ++k) load(A[k], static_cast<const T*>(jb.B[k]), N[k] * r);
+  __syncthreads();
+  for (int k = 0; k < 3; ++k) sgemm(r, r, N[k], A[k], 1, r, A[k], r, 1, Gr[k]);
+  // V = Gr[a] .* Gr[b], den = A[n] V, MU on A[n], Gram of the new A[n].
+  auto update = [&](int n, int a, int b) {
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) V[e] = Gr[a][e] * Gr[b][e];
+    __syncthreads();
+    sgemm(N[n], r, r, A[n], r, 1, V, r, 1, den);
+    mu(A[n], MT, den, N[n] * r, eps);
+    sgemm(r, r, N[n], A[n], 1, r, A[n], r, 1, Gr[n]);
+  };
+  for (int it = 0; it < iters; ++it) {
+    pass_rows<T, QM>(X, N[0] * N[1], N[2], A[2], r, Tb);  // T[i, j, q]
+    for (int e = threadIdx.x; e < N[0] * r; e += blockDim.x) {
+      const int i = e / r, q = e - i * r;
+      T acc = T(0);
+      for (int j = 0; j < N[1]; ++j) acc = fma(Tb[(i * N[1] + j) * r + q], A[1][j * r + q], acc);
+      MT[e] = acc;
+    }
+    __syncthreads();
+    update(0, 1, 2);
+    for (int e = threadIdx.x; e < N[1] * r; e += blockDim.x) {
+      const int j = e / r, q = e - j * r;
+      T acc = T(0);
+      for (int i = 0; i < N[0]; ++i) acc = fma(Tb[(i * N[1] + j) * r + q], A[0][i * r + q], acc);
+      MT[e] = acc;
+    }
+    __syncthreads();
+    update(1, 0, 2);
+    pass_cols<T, QM>(X, N[0], N[1] * N[2], A[0], r, Tb);  // T'[q, j, k]
+    for (int e = threadIdx.x; e < N[2] * r; e += blockDim.x) {
+      const int k = e / r, q = e - k * r;
+      T acc = T(0);
+      for (int j = 0; j < N[1]; ++j)
+        acc = fma(Tb[(q * N[1] + j) * N[2] + k], A[1][j * r + q], acc);
+      MT[e] = acc;
+    }
+    __syncthreads();
+    update(2, 0, 1);
+  }
+  // ||X - I x_k A_k|| / ||X||: U[i, j, q] = A1[i, q] A2[j, q], then X streamed.
+  for (int e = threadIdx.x; e < t3; e += blockDim.x) {
+    const int q = e % r, ij = e / r, j = ij % N[1], i = ij / N[1];
+    Tb[e] = A[0][i * r + q] * A[1][j * r + q];
+  }
+  __syncthreads();
+  stream_residual(X, N[0] * N[1], N[2], Tb, A[2], r, red, nrm);
+  if (threadIdx.x == 0 && rel_errs) rel_errs[blockIdx.x] = sqrt(nrm[0] / nrm[1]);
+  for (int k = 0; k < 3; ++k) store(static_cast<T*>(jb.B[k]), A[k], N[k] * r);
+}
+
 size_t nmf_small_elems(const nmf_job& j) {
   const size_t N = j.N, r = j.r, m = j.m;
   return N * r + N * m + m * r + 2 * m * m + 2 * N * m + 2 * m * r + N * r;
@@ -272,12 +556,9 @@ nmf_small_kernel(const nmf_job* __restrict__ jobs, int iters, T eps, double* rel
 }
 
 size_t lifted_small_elems(const lifted_job& j) {
-  size_t a = 0, nx = 1;
-  for (int k = 0; k < 3; ++k) {
-    a += (size_t)j.dims[k] * j.r;
-    nx *= j.dims[k];
-  }
-  return a + nx;
+  size_t a = 0;
+  for (int k = 0; k < 3; ++k) a += (size_t)j.dims[k] * j.r;
+  return a;
 }
 
 template <typename T>
@@ -293,19 +574,28 @@ lifted_err_kernel(const lifted_job* __restrict__ jobs, double* rel_errs) {
   A[0] = reinterpret_cast<T*>(smem_raw);
   A[1] = A[0] + N[0] * r;
   A[2] = A[1] + N[1] * r;
-  T* Xh = A[2] + N[2] * r;
   for (int k = 0; k < 3; ++k)  // A_k = F_k B_k
     sgemm(N[k], r, jb.m[k], static_cast<const T*>(jb.F[k]), jb.m[k], 1,
           static_cast<const T*>(jb.B[k]), r, 1, A[k]);
+  // X is streamed from global memory; each entry of X_hat is formed on the fly.
+  const T* X = static_cast<const T*>(jb.X);
   const int nx = N[0] * N[1] * N[2];
+  double s2 = 0.0, x2 = 0.0;
   for (int e = threadIdx.x; e < nx; e += blockDim.x) {
     const int k = e % N[2], j = (e / N[2]) % N[1], i = e / (N[1] * N[2]);
-    T s = T(0);
-    for (int q = 0; q < r; ++q) s = fma(A[0][i * r + q] * A[1][j * r + q], A[2][k * r + q], s);
-    Xh[e] = s;
+    T h = T(0);
+    for (int q = 0; q < r; ++q) h = fma(A[0][i * r + q] * A[1][j * r + q], A[2][k * r + q], h);
+    const double xv = (double)X[e], dv = xv - (double)h;
+    s2 += dv * dv;
+    x2 += xv * xv;
+  }
+  s2 = block_sum(s2, red);
+  x2 = block_sum(x2, red);
+  if (threadIdx.x == 0) {
+    nrm[0] = s2;
+    nrm[1] = x2;
   }
   __syncthreads();
-  diff_norms(static_cast<const T*>(jb.X), Xh, nx, red, nrm);
   if (threadIdx.x == 0 && rel_errs) rel_errs[blockIdx.x] = sqrt(nrm[0] / nrm[1]);
 }
 
@@ -333,12 +623,72 @@ int ntd_small_batched(int n_jobs, const ntd_small_job* jobs, int iters, double e
     elems = e > elems ? e : elems;
   }
   const size_t smem = elems * sizeof(T);
-  if (smem > 200 * 1024) return NNC_ERR_UNSUPPORTED;
   Scratch sc(s);
   ntd_small_job* dev = nullptr;
+  if (smem <= 200 * 1024) {
+    NNC_TRY(upload(jobs, n_jobs, sc, &dev, s));
+    NNC_CUDA_TRY(raise_smem_limit((const void*)ntd_small_kernel<T>, smem));
+    ntd_small_kernel<T><<<n_jobs, kThreads, smem, s>>>(dev, iters, (T)eps, rel_errs);
+    note_launch(s);
+    NNC_CUDA_TRY(cudaGetLastError());
+    return NNC_OK;
+  }
+  // Some X does not fit: the whole batch keeps X in global memory.
+  size_t l2 = 0;
+  int mmax = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    const size_t e = ntd_l2_elems(jobs[i]);
+    l2 = e > l2 ? e : l2;
+    for (int k = 0; k < 3; ++k) mmax = jobs[i].m[k] > mmax ? jobs[i].m[k] : mmax;
+  }
+  const size_t smem2 = l2 * sizeof(T);
+  if (smem2 > 200 * 1024 || mmax > 16) {
+    set_error_detail_text("batched nnTD: a job's pass results or multirank exceed one block");
+    return NNC_ERR_UNSUPPORTED;
+  }
   NNC_TRY(upload(jobs, n_jobs, sc, &dev, s));
-  NNC_CUDA_TRY(raise_smem_limit((const void*)ntd_small_kernel<T>, smem));
-  ntd_small_kernel<T><<<n_jobs, kThreads, smem, s>>>(dev, iters, (T)eps, rel_errs);
+  if (mmax <= 8) {
+    NNC_CUDA_TRY(raise_smem_limit((const void*)ntd_l2_kernel<T, 8>, smem2));
+    ntd_l2_kernel<T, 8><<<n_jobs, kThreads, smem2, s>>>(dev, iters, (T)eps, rel_errs);
+  } else {
+    NNC_CUDA_TRY(raise_smem_limit((const void*)ntd_l2_kernel<T, 16>, smem2));
+    ntd_l2_kernel<T, 16><<<n_jobs, kThreads, smem2, s>>>(dev, iters, (T)eps, rel_errs);
+  }
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  return NNC_OK;
+}
+
+template <typename T>
+int nncp_l2_batched(int n_jobs, const nncp_job* jobs, int iters, double eps, double* rel_errs,
+                    cudaStream_t s) {
+  size_t elems = 0;
+  int rmax = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    const nncp_job& j = jobs[i];
+    if (j.d != 3) {
+      set_error_detail_text("batched nnCP: a 4-way job too large for shared memory");
+      return NNC_ERR_UNSUPPORTED;
+    }
+    const size_t e = cpx_l2_elems(j);
+    elems = e > elems ? e : elems;
+    rmax = j.r > rmax ? j.r : rmax;
+  }
+  const size_t smem = elems * sizeof(T);
+  if (smem > 200 * 1024 || rmax > 16) {
+    set_error_detail_text("batched nnCP: a job's pass results or rank exceed one block");
+    return NNC_ERR_UNSUPPORTED;
+  }
+  Scratch sc(s);
+  nncp_job* dev = nullptr;
+  NNC_TRY(upload(jobs, n_jobs, sc, &dev, s));
+  if (rmax <= 8) {
+    NNC_CUDA_TRY(raise_smem_limit((const void*)cpx_l2_kernel<T, 8>, smem));
+    cpx_l2_kernel<T, 8><<<n_jobs, kThreads, smem, s>>>(dev, iters, (T)eps, rel_errs);
+  } else {
+    NNC_CUDA_TRY(raise_smem_limit((const void*)cpx_l2_kernel<T, 16>, smem));
+    cpx_l2_kernel<T, 16><<<n_jobs, kThreads, smem, s>>>(dev, iters, (T)eps, rel_errs);
+  }
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
   return NNC_OK;
@@ -395,7 +745,8 @@ int lifted_small_batched(int n_jobs, const lifted_job* jobs, double* rel_errs, c
   template int ntd_small_batched<T>(int, const ntd_small_job*, int, double, double*,         \
                                     cudaStream_t);                                          \
   template int nmf_small_batched<T>(int, const nmf_job*, int, double, double*, cudaStream_t); \
-  template int lifted_small_batched<T>(int, const lifted_job*, double*, cudaStream_t);
+  template int lifted_small_batched<T>(int, const lifted_job*, double*, cudaStream_t);        \
+  template int nncp_l2_batched<T>(int, const nncp_job*, int, double, double*, cudaStream_t);
 NNC_SMALL_INST(float)
 NNC_SMALL_INST(double)
 #undef NNC_SMALL_INST

@@ -1,4 +1,4 @@
-// Batched fits of tiny problems, one block per problem (small_batched.cu).
+// Batched fits of small problems, one block per problem (small_batched.cu).
 #pragma once
 
 #include "common.cuh"
@@ -13,5 +13,10 @@ int nmf_small_batched(int n_jobs, const nmf_job* jobs, int iters, double eps, do
                       cudaStream_t s);
 template <typename T>
 int lifted_small_batched(int n_jobs, const lifted_job* jobs, double* rel_errs, cudaStream_t s);
+// nnCP of 3-way tensors too large for shared memory (the tensor stays in
+// global memory, two passes over it per sweep), one block per job; r <= 16.
+template <typename T>
+int nncp_l2_batched(int n_jobs, const nncp_job* jobs, int iters, double eps, double* rel_errs,
+                    cudaStream_t s);
 
 }  // namespace nnc

@@ -198,3 +198,49 @@ def study_inits(dims, m, r, starts, seed):
             "B2": [1.0 - rng.random((k, r)) for k in m],
         })
     return out
+
+
+# The batch experiment of Sec. 4.3: many tensors with a unique nnCPD whose
+# factors are rank deficient, A^(i) = F^(i) B^(i) with F^(i) (N x kappa_i) and
+# B^(i) (kappa_i x r) i.i.d. U[0, 1), X = I x_i A^(i) (no noise). A draw is
+# kept only if the Kruskal ranks of the A^(i) add up to at least 2 r + 2
+# (Kruskal's uniqueness condition; the paper's inequality sign is garbled).
+# The paper's size: 1000 tensors of 40^3, kappa = (3, 4, 5), r = 5.
+PAPER_BATCH = {"name": "paper_batch_1000x40cube_k345_r5", "n_tensors": 1000, "N": 40,
+               "kappa": (3, 4, 5), "r": 5, "iters": 5000, "seed": 4300}
+
+
+def kruskal_rank(A, tol=1e-9):
+    """Largest k such that every k columns of A are linearly independent
+    (input validation of the planted factors, by brute force over subsets)."""
+    import itertools
+    r = A.shape[1]
+    for k in range(1, r + 1):
+        for cols in itertools.combinations(range(r), k):
+            if np.linalg.matrix_rank(A[:, cols], tol=tol * np.linalg.norm(A)) < k:
+                return k - 1
+    return r
+
+
+def paper_batch_problems(n_tensors=None, N=None, seed=None):
+    """The Sec. 4.3 batch: a list of dicts {X (float64), A_true, and per tensor
+    the starts of both algorithms: F, G, B (Alg. 1) and A, F2, B2 (Alg. 2)},
+    each U(0, 1], with the multirank m = kappa."""
+    n = PAPER_BATCH["n_tensors"] if n_tensors is None else n_tensors
+    N = PAPER_BATCH["N"] if N is None else N
+    seed = PAPER_BATCH["seed"] if seed is None else seed
+    kappa, r = PAPER_BATCH["kappa"], PAPER_BATCH["r"]
+    dims = (N, N, N)
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        Fp = [rng.random((N, k)) for k in kappa]
+        Bp = [rng.random((k, r)) for k in kappa]
+        A = [f @ b for f, b in zip(Fp, Bp)]
+        if sum(kruskal_rank(a) for a in A) < 2 * r + 2:
+            continue
+        X = _outer_sum(A)
+        start = study_inits(dims, kappa, r, 1, int(rng.integers(1 << 31)))[0]
+        start.update({"X": X, "A_true": A, "dims": dims, "m": kappa, "r": r})
+        out.append(start)
+    return out

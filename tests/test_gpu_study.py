@@ -74,3 +74,93 @@ def test_multirank_study_runs_and_alg_pieces_agree_with_oracle():
     summ = study.summary(res)
     assert set(summ) == {f"{a}_{m}" for a in ("alg1", "alg2")
                          for m in ("3x3x3", "3x4x4", "4x4x4", "5x5x5")}
+
+
+# ---------------------------------------------------------------------------
+# Problems whose X does not fit in shared memory (X read from global memory,
+# two passes per sweep) and the batch experiment of Sec. 4.3
+# ---------------------------------------------------------------------------
+
+L2_SHAPES = [((40, 40, 40), (3, 4, 5)), ((37, 29, 23), (5, 6, 7)), ((9, 50, 33), (2, 8, 3)),
+             ((24, 20, 48), (12, 3, 9))]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_ntd_batched_x_in_global_memory_matches_oracle(dtype):
+    probs = [inputs.small_problem(d, 3, m, 2, seed=31 + i, noise=0.02)
+             for i, (d, m) in enumerate(L2_SHAPES)]
+    Xd = [torch.tensor(p[0], dtype=dtype, device="cuda") for p in probs]
+    F = [[torch.tensor(f, dtype=dtype, device="cuda") for f in p[2]] for p in probs]
+    G = [torch.tensor(p[3], dtype=dtype, device="cuda") for p in probs]
+    errs = native.ntd_fit_small_batched([(Xd[i], F[i], G[i]) for i in range(len(probs))],
+                                        30).cpu().numpy()
+    for i, p in enumerate(probs):
+        Fo, Go, tro = orc.ntd_fit(p[0], p[2], p[3], 30)
+        ref = orc.rel_err_tucker(p[0], Go, Fo)
+        if dtype == torch.float64:
+            for a, b in zip(F[i], Fo):
+                np.testing.assert_allclose(a.cpu().numpy(), b, rtol=1e-9, atol=1e-14 * b.max())
+            np.testing.assert_allclose(G[i].cpu().numpy(), Go, rtol=1e-9, atol=1e-14 * Go.max())
+            assert errs[i] == pytest.approx(ref, rel=1e-9)
+        else:
+            assert abs(errs[i] - ref) <= 1e-5
+        assert abs(ref - tro[-1]) <= 1e-10 * max(1.0, ref)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_nncp_batched_of_x_in_global_memory_matches_oracle(dtype):
+    # nnCPD of X itself (Alg. 2, first step) through nncp_core_fit_batched with
+    # tensors far larger than shared memory.
+    cases = [((40, 40, 40), 5), ((37, 29, 23), 3), ((9, 50, 33), 12)]
+    Xs, A0 = [], []
+    for i, (d, r) in enumerate(cases):
+        X, _ = inputs.planted_tensor(d, 4, 51 + i, noise=0.01)
+        Xs.append(X)
+        A0.append([1.0 - np.random.default_rng(61 + i).random((n, r)) for n in d])
+    Xd = [torch.tensor(x, dtype=dtype, device="cuda") for x in Xs]
+    A = [[torch.tensor(a, dtype=dtype, device="cuda") for a in a0] for a0 in A0]
+    errs = native.nncp_core_fit_batched([(Xd[i], A[i]) for i in range(len(cases))],
+                                        25).cpu().numpy()
+    for i in range(len(cases)):
+        Ao, tro = orc.nncp_fit(Xs[i], A0[i], 25)
+        if dtype == torch.float64:
+            for a, b in zip(A[i], Ao):
+                np.testing.assert_allclose(a.cpu().numpy(), b, rtol=1e-9, atol=1e-14 * b.max())
+            assert errs[i] == pytest.approx(tro[-1], rel=1e-9)
+        else:
+            assert abs(errs[i] - tro[-1]) <= 1e-5
+
+
+def test_lifted_err_streams_a_large_x():
+    X, _ = inputs.planted_tensor((40, 40, 40), 5, 71, noise=0.0)
+    rng = np.random.default_rng(72)
+    F = [rng.random((40, k)) for k in (3, 4, 5)]
+    B = [rng.random((k, 5)) for k in (3, 4, 5)]
+    e = native.lifted_rel_err_batched([(torch.tensor(X, device="cuda"),
+                                        [torch.tensor(f, device="cuda") for f in F],
+                                        [torch.tensor(b, device="cuda") for b in B])])
+    assert float(e[0]) == pytest.approx(orc.rel_err_cp(X, orc.lift(F, B)), rel=1e-12)
+
+
+def test_paper_batch_runs_and_matches_oracle_pipeline():
+    # Six tensors of the Sec. 4.3 batch at 200 sweeps per stage; the first
+    # tensor's whole pipeline (both algorithms) is replayed by the oracle.
+    probs = inputs.paper_batch_problems(6)
+    res = study.run_paper_batch(probs, iters=200)
+    p = probs[0]
+    Fo, Go, _ = orc.ntd_fit(p["X"], p["F"], p["G"], 200)
+    Bo, _ = orc.nncp_fit(Go, p["B"], 200)
+    e1 = orc.rel_err_cp(p["X"], orc.lift(Fo, Bo))
+    assert res["alg1"]["rel_err"][0] == pytest.approx(e1, rel=1e-8, abs=1e-12)
+    Ao, _ = orc.nncp_fit(p["X"], p["A"], 200)
+    F2, B2 = [], []
+    for k in range(3):
+        f, b, _ = orc.nmf_fit(Ao[k], p["F2"][k], p["B2"][k], 200)
+        F2.append(f)
+        B2.append(b)
+    e2 = orc.rel_err_cp(p["X"], orc.lift(F2, B2))
+    assert res["alg2"]["rel_err"][0] == pytest.approx(e2, rel=1e-8, abs=1e-12)
+    for alg in ("alg1", "alg2"):
+        c = res[alg]["congruence"]
+        assert np.all((c >= 0.0) & (c <= 1.0 + 1e-12))
+        assert np.all(np.isfinite(res[alg]["rel_err"]))
