@@ -133,15 +133,19 @@ int ntd_fit_batched(int n_jobs, const ntd_job* jobs, int precision, const nnc_op
                     int concurrency, double* rel_errs, int* statuses, void* stream);
 
 /*
- * Batched fits of tiny problems, one thread block per problem with all its
- * data in shared memory: many random starts of Alg. 1 and Alg. 2 on a small
- * tensor (the multirank study of Sec. 4.3 on Ex. "equal": a 4 x 4 x 4 tensor,
- * several multiranks, many starts). Pointers inside the descriptors are
- * device pointers; the descriptor arrays are host arrays copied by the call.
- * rel_errs: device, n_jobs doubles (final relative error of each job), or
- * NULL. Same update rules as ntd_fit and nmf_fit. Errors: INVALID_ARG,
- * UNSUPPORTED (a job too large for shared memory), CUDA, ALLOC. No host
- * synchronisation.
+ * Batched fits of small problems, one thread block per problem: many random
+ * starts of Alg. 1 and Alg. 2 on a small tensor (the multirank study of
+ * Sec. 4.3 on Ex. "equal": a 4 x 4 x 4 tensor, several multiranks, many
+ * starts) and many small tensors (the 1000 planted 40 x 40 x 40 tensors of
+ * Sec. 4.3). When every job's data fits in shared memory it all goes there;
+ * otherwise (ntd_fit_small_batched) the whole batch keeps X in global memory
+ * and reads it twice per sweep like ntd_fit, with the factors, core and pass
+ * results in shared memory (then m[n] <= 16); lifted_rel_err_batched always
+ * streams X. Pointers inside the descriptors are device pointers; the
+ * descriptor arrays are host arrays copied by the call. rel_errs: device,
+ * n_jobs doubles (final relative error of each job), or NULL. Same update
+ * rules as ntd_fit and nmf_fit. Errors: INVALID_ARG, UNSUPPORTED (a job too
+ * large for one block), CUDA, ALLOC. No host synchronisation.
  */
 typedef struct {
   const void* X;        /* dims[0] x dims[1] x dims[2], C order                    */
@@ -211,12 +215,15 @@ typedef struct {
  * nncp_core_fit_batched - many independent nncp_core_fit problems (uneven
  * shapes and ranks: restarts, candidate ranks, several tensors) in one
  * launch, one thread block per job. Same update rule and options as
- * nncp_core_fit.
+ * nncp_core_fit. A batch with a tensor too large for shared memory (X itself
+ * in Alg. 2, e.g. 40 x 40 x 40) runs with the tensors in global memory, two
+ * passes over each per sweep (d = 3 and r <= 16 there, else UNSUPPORTED).
  *
  *  jobs       host array of n_jobs descriptors (copied by the call)
  *  rel_errs   device array of n_jobs doubles, or NULL: final relative error
  *             of each job
- * Errors: INVALID_ARG (any job), CUDA, ALLOC. No host synchronisation.
+ * Errors: INVALID_ARG (any job), UNSUPPORTED (see above), CUDA, ALLOC. No
+ * host synchronisation.
  */
 int nncp_core_fit_batched(int n_jobs, const nncp_job* jobs, int precision, const nnc_opts* opts,
                           double* rel_errs, void* stream);
