@@ -527,12 +527,24 @@ def batching_form(dev):
     seq = upload()[:8]
     t_seq, _ = timed(lambda: native.ntd_fit_batched(seq, B["iters"], precision="fp32",
                                                      concurrency=1, trace=False))
-    jobs = []
-    for b, (_, _, G) in enumerate(batch):
-        for _, _, B0 in inputs.batch_core_inits(probs[b]["m"], b):
-            jobs.append((G, [torch.tensor(x, dtype=torch.float32, device=dev) for x in B0]))
+    def core_jobs():
+        jobs = []
+        for b, (_, _, G) in enumerate(batch):
+            for _, _, B0 in inputs.batch_core_inits(probs[b]["m"], b):
+                jobs.append((G, [torch.tensor(x, dtype=torch.float32, device=dev) for x in B0]))
+        return jobs
+
+    # The core fits with the launch-shape autotuner off (256 threads per job)
+    # and on (its first call tries 32 .. 256 threads on the fit's first sweeps).
+    was = native.nnc_autotune_enable(False)
+    jobs = core_jobs()
+    t_cp256, _ = timed(lambda: native.nncp_core_fit_batched(jobs, B["cp_iters"],
+                                                            precision="fp32"))
+    native.nnc_autotune_enable(True)
+    jobs = core_jobs()
     t_cp, cp_errs = timed(lambda: native.nncp_core_fit_batched(jobs, B["cp_iters"],
                                                                precision="fp32"))
+    native.nnc_autotune_enable(was)
     n = len(batch)
     return {"workload": B["name"], "tensors": n, "ntd_sweeps": B["iters"], "concurrency": 8,
             "ntd_ms": round(t_ntd * 1e3, 1), "tensors_per_s": round(n / t_ntd, 2),
@@ -541,6 +553,7 @@ def batching_form(dev):
             "batched_speedup_vs_sequential": round((t_seq / 8) / (t_ntd / n), 2),
             "core_fits": len(jobs), "cp_iters": B["cp_iters"],
             "core_fits_ms": round(t_cp * 1e3, 1), "core_fits_per_s": round(len(jobs) / t_cp, 1),
+            "core_fits_ms_untuned_256_threads": round(t_cp256 * 1e3, 1),
             "mean_tucker_rel_err": round(float(sum(errs) / n), 6),
             "mean_core_fit_rel_err": round(float(cp_errs.mean().item()), 6)}
 

@@ -425,6 +425,22 @@ int nnc_profile_read(int kind, long long* launches, double* total_ms);
  * process (a kernel node of a replayed graph counts once per replay). */
 long long nnc_kernel_launches(void);
 
+/*
+ * Launch-shape autotuner of the batched one-block-per-job fits
+ * (nncp_core_fit[_batched], ntd_fit_small_batched, nmf_fit_batched). On (the
+ * default), the first call of a new shape class (kernel, element size, size
+ * classes of the largest job and of the job count; per device) spends its
+ * first sweeps on trial launches at 32, 64, 128 and 256 threads per block,
+ * timed with events (one host wait in that call), and runs the remaining
+ * sweeps, and every later call of the class, at the fastest. The results are
+ * the same bits whatever the choice: the sweeps of a fit may be split over
+ * launches and no sum depends on the block size. Off: 256 threads, no
+ * timing. nncp_core_fit_batched_noalloc uses a cached choice but never
+ * times. nnc_autotune_enable returns the previous setting. Calls made while
+ * the stream is being captured into a graph never time either.
+ */
+int nnc_autotune_enable(int on);
+
 /* Static string naming a status code. */
 const char* nnc_status_string(int status);
 

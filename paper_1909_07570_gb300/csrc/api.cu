@@ -8,6 +8,7 @@
 #include <thread>
 #include <vector>
 
+#include "autotune.cuh"
 #include "kernels.cuh"
 #include "lifted.cuh"
 #include "nncp.cuh"
@@ -120,7 +121,12 @@ int nncp_run(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel_er
   std::vector<nncp_job> host(jobs, jobs + n_jobs);
   NNC_CUDA_TRY(cudaMemcpyAsync(dev, host.data(), sizeof(nncp_job) * n_jobs,
                                cudaMemcpyHostToDevice, s));
-  NNC_CUDA_TRY(launch_nncp<T>(dev, n_jobs, smem, o->iters, o->eps, rel_errs, s));
+  const TuneKey key = nncp_tune_key(jobs, n_jobs, sizeof(T));
+  NNC_TRY(run_tuned(key, o->iters, 256, s, [&](int threads, int sweeps, bool last) -> int {
+    NNC_CUDA_TRY(launch_nncp<T>(dev, n_jobs, smem, sweeps, o->eps, last ? rel_errs : nullptr, s,
+                                threads));
+    return NNC_OK;
+  }));
   return NNC_OK;
 }
 
@@ -189,6 +195,12 @@ const char* nnc_status_string(int status) {
 const char* nnc_last_error_detail(void) { return g_detail.c_str(); }
 
 long long nnc_kernel_launches(void) { return g_kernel_launches.load(); }
+
+int nnc_autotune_enable(int on) {
+  const bool was = autotune_on();
+  autotune_set(on != 0);
+  return was ? 1 : 0;
+}
 
 int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precision,
             const nnc_opts* opts, void* const* F, void* G, double* rel_err_trace,

@@ -147,6 +147,36 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
   return r;
 }
 
+// Two FP64 sums over e < n, sum_e f(e).x and sum_e f(e).y, in an order fixed by
+// n alone (not by the block size): virtual lane v < kFixedLanes adds the terms
+// e = v, v + kFixedLanes, ... in order, then a fixed tree adds the lanes. `part`
+// is 2 kFixedLanes doubles of shared memory. Every thread gets both sums.
+constexpr int kFixedLanes = 256;
+template <typename F>
+__device__ double2 fixed_sums2(int64_t n, F f, double* part) {
+  for (int v = threadIdx.x; v < kFixedLanes; v += blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int64_t e = v; e < n; e += kFixedLanes) {
+      const double2 t = f(e);
+      a += t.x;
+      b += t.y;
+    }
+    part[v] = a;
+    part[kFixedLanes + v] = b;
+  }
+  __syncthreads();
+  for (int h = kFixedLanes / 2; h > 0; h >>= 1) {
+    for (int v = threadIdx.x; v < h; v += blockDim.x) {
+      part[v] += part[v + h];
+      part[kFixedLanes + v] += part[kFixedLanes + v + h];
+    }
+    __syncthreads();
+  }
+  const double2 r = make_double2(part[0], part[kFixedLanes]);
+  __syncthreads();
+  return r;
+}
+
 // ---- cp.async staging (element granularity, zero fill outside the range) ----
 template <typename T>
 __device__ __forceinline__ void cp_elem(T* dst, const T* src, bool valid) {

@@ -56,7 +56,6 @@ __device__ T mttkrp_entry(const T* __restrict__ G, const int* m, const int64_t* 
 template <typename T, int D>
 __device__ void fit_one(const nncp_job& job, int iters, T eps, unsigned char* smem,
                         double* rel_err_out) {
-  __shared__ double red[32];
   const int r = job.r;
   int m[D];
   int64_t st[D];
@@ -150,8 +149,9 @@ __device__ void fit_one(const nncp_job& job, int iters, T eps, unsigned char* sm
     int64_t total = 1;
 #pragma unroll
     for (int k = 0; k < D; ++k) total *= m[k];
-    double d2 = 0.0, g2 = 0.0;
-    for (int64_t e = tid; e < total; e += blockDim.x) {
+    // FP64 sums in an order that does not depend on the block size.
+    __shared__ double fpart[2 * kFixedLanes];
+    const double2 dg = fixed_sums2(total, [&](int64_t e) {
       int idx[D];
       int64_t rem = e;
 #pragma unroll
@@ -168,12 +168,9 @@ __device__ void fit_one(const nncp_job& job, int iters, T eps, unsigned char* sm
       }
       const double g = (double)G[e];
       const double dd = g - (double)hat;
-      d2 += dd * dd;
-      g2 += g * g;
-    }
-    d2 = block_sum(d2, red);
-    g2 = block_sum(g2, red);
-    if (tid == 0) *rel_err_out = g2 > 0.0 ? sqrt(d2 / g2) : sqrt(d2);
+      return make_double2(dd * dd, g * g);
+    }, fpart);
+    if (tid == 0) *rel_err_out = dg.y > 0.0 ? sqrt(dg.x / dg.y) : sqrt(dg.x);
   }
 }
 
@@ -203,19 +200,30 @@ size_t nncp_smem_bytes(const nncp_job& j, size_t elem) {
 
 template <typename T>
 cudaError_t launch_nncp(const nncp_job* jobs_dev, int n_jobs, size_t smem, int iters, double eps,
-                        double* rel_errs, cudaStream_t s) {
+                        double* rel_errs, cudaStream_t s, int threads) {
+  if (threads < 32 || threads > kThreads || threads % 32 != 0) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
     cudaError_t e = raise_smem_limit((const void*)nncp_kernel<T>, smem);
     if (e != cudaSuccess) return e;
   }
-  nncp_kernel<T><<<n_jobs, kThreads, smem, s>>>(jobs_dev, iters, (T)eps, rel_errs);
+  nncp_kernel<T><<<n_jobs, threads, smem, s>>>(jobs_dev, iters, (T)eps, rel_errs);
   note_launch(s);
   return cudaGetLastError();
 }
 
+TuneKey nncp_tune_key(const nncp_job* jobs, int n_jobs, size_t elem) {
+  long long work = 1;
+  for (int i = 0; i < n_jobs; ++i) {
+    long long w = jobs[i].r;  // one sweep: every entry of the core once per mode and q
+    for (int k = 0; k < jobs[i].d; ++k) w *= jobs[i].m[k];
+    work = w > work ? w : work;
+  }
+  return TuneKey{kTuneNncp, (int)elem, size_class(work), size_class(n_jobs)};
+}
+
 template cudaError_t launch_nncp<float>(const nncp_job*, int, size_t, int, double, double*,
-                                        cudaStream_t);
+                                        cudaStream_t, int);
 template cudaError_t launch_nncp<double>(const nncp_job*, int, size_t, int, double, double*,
-                                         cudaStream_t);
+                                         cudaStream_t, int);
 
 }  // namespace nnc

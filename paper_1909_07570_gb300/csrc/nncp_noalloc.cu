@@ -71,7 +71,10 @@ int run_noalloc(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel
   NNC_TRY(job_table_address(&table));
   NNC_CUDA_TRY(cudaMemcpyAsync(table, jobs, sizeof(nncp_job) * (size_t)n_jobs,
                                cudaMemcpyHostToDevice, s));
-  NNC_CUDA_TRY(launch_nncp<T>(table, n_jobs, smem, o->iters, o->eps, rel_errs, s));
+  // A block size tuned by an earlier allocating call of the same class is
+  // reused; this call never times anything.
+  const int threads = tuned_threads(nncp_tune_key(jobs, n_jobs, sizeof(T)), 256);
+  NNC_CUDA_TRY(launch_nncp<T>(table, n_jobs, smem, o->iters, o->eps, rel_errs, s, threads));
   return NNC_OK;
 }
 

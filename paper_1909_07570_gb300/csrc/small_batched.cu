@@ -13,6 +13,7 @@
 // to the device by the call.
 #include <vector>
 
+#include "autotune.cuh"
 #include "small_batched.cuh"
 
 namespace nnc {
@@ -100,20 +101,17 @@ __device__ void store(T* dst, const T* src, int n) {
   for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
 }
 
-// sum (a - b)^2 and sum a^2 in FP64 over n entries (b may be null: 0).
+// sum (a - b)^2 and sum a^2 in FP64 over n entries (b may be null: 0), in an
+// order that does not depend on the block size (`red`: 2 kFixedLanes doubles).
 template <typename T>
 __device__ void diff_norms(const T* a, const T* b, int n, double* red, double* out2) {
-  double s = 0.0, x = 0.0;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+  const double2 r = fixed_sums2(n, [&](int64_t e) {
     const double av = (double)a[e], bv = b ? (double)b[e] : 0.0;
-    s += (av - bv) * (av - bv);
-    x += av * av;
-  }
-  s = block_sum(s, red);
-  x = block_sum(x, red);
+    return make_double2((av - bv) * (av - bv), av * av);
+  }, red);
   if (threadIdx.x == 0) {
-    out2[0] = s;
-    out2[1] = x;
+    out2[0] = r.x;
+    out2[1] = r.y;
   }
   __syncthreads();
 }
@@ -137,7 +135,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 ntd_small_kernel(const ntd_small_job* __restrict__ jobs, int iters, T eps, double* rel_errs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
+  __shared__ double red[2 * kFixedLanes];
   __shared__ double nrm[2];
   const ntd_small_job& jb = jobs[blockIdx.x];
   const int* N = jb.dims;
@@ -286,21 +284,16 @@ __device__ void pass_cols(const T* __restrict__ X, int N1, int C, const T* F, in
 template <typename T>
 __device__ void stream_residual(const T* __restrict__ X, int R, int N3, const T* U, const T* W,
                                 int K, double* red, double* out2) {
-  double s = 0.0, x = 0.0;
-  const int n = R * N3;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int r = e / N3, k = e - r * N3;
+  const double2 r2 = fixed_sums2((int64_t)R * N3, [&](int64_t e) {
+    const int r = (int)(e / N3), k = (int)(e - (int64_t)r * N3);
     T h = T(0);
     for (int c = 0; c < K; ++c) h = fma(U[r * K + c], W[k * K + c], h);
     const double xv = (double)__ldg(X + e), dv = xv - (double)h;
-    s += dv * dv;
-    x += xv * xv;
-  }
-  s = block_sum(s, red);
-  x = block_sum(x, red);
+    return make_double2(dv * dv, xv * xv);
+  }, red);
   if (threadIdx.x == 0) {
-    out2[0] = s;
-    out2[1] = x;
+    out2[0] = r2.x;
+    out2[1] = r2.y;
   }
   __syncthreads();
 }
@@ -343,7 +336,7 @@ template <typename T, int QM>
 __global__ void __launch_bounds__(kThreads, 2)
 ntd_l2_kernel(const ntd_small_job* __restrict__ jobs, int iters, T eps, double* rel_errs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
+  __shared__ double red[2 * kFixedLanes];
   __shared__ double nrm[2];
   const ntd_small_job& jb = jobs[blockIdx.x];
   const int* N = jb.dims;
@@ -439,7 +432,7 @@ template <typename T, int QM>
 __global__ void __launch_bounds__(kThreads, 2)
 cpx_l2_kernel(const nncp_job* __restrict__ jobs, int iters, T eps, double* rel_errs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
+  __shared__ double red[2 * kFixedLanes];
   __shared__ double nrm[2];
   const nncp_job& jb = jobs[blockIdx.x];
   const int* N = jb.m;
@@ -520,7 +513,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 nmf_small_kernel(const nmf_job* __restrict__ jobs, int iters, T eps, double* rel_errs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
+  __shared__ double red[2 * kFixedLanes];
   __shared__ double nrm[2];
   const nmf_job& jb = jobs[blockIdx.x];
   const int N = jb.N, r = jb.r, m = jb.m;
@@ -565,7 +558,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 lifted_err_kernel(const lifted_job* __restrict__ jobs, double* rel_errs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
+  __shared__ double red[2 * kFixedLanes];
   __shared__ double nrm[2];
   const lifted_job& jb = jobs[blockIdx.x];
   const int* N = jb.dims;
@@ -580,20 +573,16 @@ lifted_err_kernel(const lifted_job* __restrict__ jobs, double* rel_errs) {
   // X is streamed from global memory; each entry of X_hat is formed on the fly.
   const T* X = static_cast<const T*>(jb.X);
   const int nx = N[0] * N[1] * N[2];
-  double s2 = 0.0, x2 = 0.0;
-  for (int e = threadIdx.x; e < nx; e += blockDim.x) {
-    const int k = e % N[2], j = (e / N[2]) % N[1], i = e / (N[1] * N[2]);
+  const double2 sx = fixed_sums2(nx, [&](int64_t e) {
+    const int k = (int)(e % N[2]), j = (int)((e / N[2]) % N[1]), i = (int)(e / (N[1] * N[2]));
     T h = T(0);
     for (int q = 0; q < r; ++q) h = fma(A[0][i * r + q] * A[1][j * r + q], A[2][k * r + q], h);
     const double xv = (double)X[e], dv = xv - (double)h;
-    s2 += dv * dv;
-    x2 += xv * xv;
-  }
-  s2 = block_sum(s2, red);
-  x2 = block_sum(x2, red);
+    return make_double2(dv * dv, xv * xv);
+  }, red);
   if (threadIdx.x == 0) {
-    nrm[0] = s2;
-    nrm[1] = x2;
+    nrm[0] = sx.x;
+    nrm[1] = sx.y;
   }
   __syncthreads();
   if (threadIdx.x == 0 && rel_errs) rel_errs[blockIdx.x] = sqrt(nrm[0] / nrm[1]);
@@ -625,13 +614,27 @@ int ntd_small_batched(int n_jobs, const ntd_small_job* jobs, int iters, double e
   const size_t smem = elems * sizeof(T);
   Scratch sc(s);
   ntd_small_job* dev = nullptr;
+  long long work = 1;  // tuning class: largest tensor x largest multirank
+  for (int i = 0; i < n_jobs; ++i) {
+    long long w = 1;
+    int mm = 1;
+    for (int k = 0; k < 3; ++k) {
+      w *= jobs[i].dims[k];
+      mm = jobs[i].m[k] > mm ? jobs[i].m[k] : mm;
+    }
+    work = w * mm > work ? w * mm : work;
+  }
   if (smem <= 200 * 1024) {
     NNC_TRY(upload(jobs, n_jobs, sc, &dev, s));
     NNC_CUDA_TRY(raise_smem_limit((const void*)ntd_small_kernel<T>, smem));
-    ntd_small_kernel<T><<<n_jobs, kThreads, smem, s>>>(dev, iters, (T)eps, rel_errs);
-    note_launch(s);
-    NNC_CUDA_TRY(cudaGetLastError());
-    return NNC_OK;
+    const TuneKey key{kTuneNtdSmall, (int)sizeof(T), size_class(work), size_class(n_jobs)};
+    return run_tuned(key, iters, kThreads, s, [&](int threads, int sweeps, bool last) -> int {
+      ntd_small_kernel<T><<<n_jobs, threads, smem, s>>>(dev, sweeps, (T)eps,
+                                                        last ? rel_errs : nullptr);
+      note_launch(s);
+      NNC_CUDA_TRY(cudaGetLastError());
+      return NNC_OK;
+    });
   }
   // Some X does not fit: the whole batch keeps X in global memory.
   size_t l2 = 0;
@@ -647,16 +650,19 @@ int ntd_small_batched(int n_jobs, const ntd_small_job* jobs, int iters, double e
     return NNC_ERR_UNSUPPORTED;
   }
   NNC_TRY(upload(jobs, n_jobs, sc, &dev, s));
-  if (mmax <= 8) {
-    NNC_CUDA_TRY(raise_smem_limit((const void*)ntd_l2_kernel<T, 8>, smem2));
-    ntd_l2_kernel<T, 8><<<n_jobs, kThreads, smem2, s>>>(dev, iters, (T)eps, rel_errs);
-  } else {
-    NNC_CUDA_TRY(raise_smem_limit((const void*)ntd_l2_kernel<T, 16>, smem2));
-    ntd_l2_kernel<T, 16><<<n_jobs, kThreads, smem2, s>>>(dev, iters, (T)eps, rel_errs);
-  }
-  note_launch(s);
-  NNC_CUDA_TRY(cudaGetLastError());
-  return NNC_OK;
+  const void* kern = mmax <= 8 ? (const void*)ntd_l2_kernel<T, 8> : (const void*)ntd_l2_kernel<T, 16>;
+  NNC_CUDA_TRY(raise_smem_limit(kern, smem2));
+  const TuneKey key{kTuneNtdL2, (int)sizeof(T), size_class(work), size_class(n_jobs)};
+  return run_tuned(key, iters, kThreads, s, [&](int threads, int sweeps, bool last) -> int {
+    double* out = last ? rel_errs : nullptr;
+    if (mmax <= 8)
+      ntd_l2_kernel<T, 8><<<n_jobs, threads, smem2, s>>>(dev, sweeps, (T)eps, out);
+    else
+      ntd_l2_kernel<T, 16><<<n_jobs, threads, smem2, s>>>(dev, sweeps, (T)eps, out);
+    note_launch(s);
+    NNC_CUDA_TRY(cudaGetLastError());
+    return NNC_OK;
+  });
 }
 
 template <typename T>
@@ -682,16 +688,24 @@ int nncp_l2_batched(int n_jobs, const nncp_job* jobs, int iters, double eps, dou
   Scratch sc(s);
   nncp_job* dev = nullptr;
   NNC_TRY(upload(jobs, n_jobs, sc, &dev, s));
-  if (rmax <= 8) {
-    NNC_CUDA_TRY(raise_smem_limit((const void*)cpx_l2_kernel<T, 8>, smem));
-    cpx_l2_kernel<T, 8><<<n_jobs, kThreads, smem, s>>>(dev, iters, (T)eps, rel_errs);
-  } else {
-    NNC_CUDA_TRY(raise_smem_limit((const void*)cpx_l2_kernel<T, 16>, smem));
-    cpx_l2_kernel<T, 16><<<n_jobs, kThreads, smem, s>>>(dev, iters, (T)eps, rel_errs);
+  const void* kern = rmax <= 8 ? (const void*)cpx_l2_kernel<T, 8> : (const void*)cpx_l2_kernel<T, 16>;
+  NNC_CUDA_TRY(raise_smem_limit(kern, smem));
+  long long work = 1;
+  for (int i = 0; i < n_jobs; ++i) {
+    const long long w = (long long)jobs[i].m[0] * jobs[i].m[1] * jobs[i].m[2] * jobs[i].r;
+    work = w > work ? w : work;
   }
-  note_launch(s);
-  NNC_CUDA_TRY(cudaGetLastError());
-  return NNC_OK;
+  const TuneKey key{kTuneCpxL2, (int)sizeof(T), size_class(work), size_class(n_jobs)};
+  return run_tuned(key, iters, kThreads, s, [&](int threads, int sweeps, bool last) -> int {
+    double* out = last ? rel_errs : nullptr;
+    if (rmax <= 8)
+      cpx_l2_kernel<T, 8><<<n_jobs, threads, smem, s>>>(dev, sweeps, (T)eps, out);
+    else
+      cpx_l2_kernel<T, 16><<<n_jobs, threads, smem, s>>>(dev, sweeps, (T)eps, out);
+    note_launch(s);
+    NNC_CUDA_TRY(cudaGetLastError());
+    return NNC_OK;
+  });
 }
 
 template <typename T>
@@ -711,10 +725,19 @@ int nmf_small_batched(int n_jobs, const nmf_job* jobs, int iters, double eps, do
   nmf_job* dev = nullptr;
   NNC_TRY(upload(jobs, n_jobs, sc, &dev, s));
   NNC_CUDA_TRY(raise_smem_limit((const void*)nmf_small_kernel<T>, smem));
-  nmf_small_kernel<T><<<n_jobs, kThreads, smem, s>>>(dev, iters, (T)eps, rel_errs);
-  note_launch(s);
-  NNC_CUDA_TRY(cudaGetLastError());
-  return NNC_OK;
+  long long work = 1;
+  for (int i = 0; i < n_jobs; ++i) {
+    const long long w = (long long)jobs[i].N * jobs[i].m * jobs[i].r;
+    work = w > work ? w : work;
+  }
+  const TuneKey key{kTuneNmfSmall, (int)sizeof(T), size_class(work), size_class(n_jobs)};
+  return run_tuned(key, iters, kThreads, s, [&](int threads, int sweeps, bool last) -> int {
+    nmf_small_kernel<T><<<n_jobs, threads, smem, s>>>(dev, sweeps, (T)eps,
+                                                      last ? rel_errs : nullptr);
+    note_launch(s);
+    NNC_CUDA_TRY(cudaGetLastError());
+    return NNC_OK;
+  });
 }
 
 template <typename T>

@@ -28,7 +28,8 @@ EXPORTED = ("ntd_fit", "ntd_fit_batched", "ntd_fit_small_batched", "nmf_fit_batc
             "recon_residual", "candelinc_lifted_grad", "candelinc_pg_fit",
             "nncp_tensor_fit", "nmf_fit", "candelinc_alg2",
             "nnc_status_string", "nnc_last_error_detail",
-            "nnc_profile_enable", "nnc_profile_read", "nnc_kernel_launches")
+            "nnc_profile_enable", "nnc_profile_read", "nnc_kernel_launches",
+            "nnc_autotune_enable")
 
 
 class NncError(RuntimeError):
@@ -132,6 +133,8 @@ def load(path: str | None = None):
     lib.nnc_profile_read.restype = ctypes.c_int
     lib.nnc_kernel_launches.argtypes = []
     lib.nnc_kernel_launches.restype = ctypes.c_longlong
+    lib.nnc_autotune_enable.argtypes = [ctypes.c_int]
+    lib.nnc_autotune_enable.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -521,3 +524,9 @@ def nnc_profile_read(kind):
 def nnc_kernel_launches():
     """Kernels this library has launched in this process so far."""
     return int(load().nnc_kernel_launches())
+
+
+def nnc_autotune_enable(on=True):
+    """Switch the launch-shape autotuner of the batched fits; returns the
+    previous setting."""
+    return bool(load().nnc_autotune_enable(1 if on else 0))

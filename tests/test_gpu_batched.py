@@ -60,3 +60,48 @@ def test_batched_reports_the_failing_job():
     with pytest.raises(native.NncError) as ei:
         native.ntd_fit_batched(batch, 3)
     assert ei.value.status == -3 and "job 1" in str(ei.value)
+
+
+def _clone(ts):
+    return [t.clone() for t in ts]
+
+
+def test_autotuned_batched_fits_are_bit_identical_to_untuned():
+    # The autotuner splits a fit's sweeps over trial launches at 32 .. 256
+    # threads per block and runs the rest at the fastest; the results must be
+    # the bits of one launch at 256 threads.
+    rng = np.random.default_rng(5)
+    cores, Bs = [], []
+    for i in range(300):
+        m = tuple(int(v) for v in rng.integers(2, 12, size=3))
+        r = int(rng.integers(2, 9))
+        cores.append(torch.tensor(rng.random(m), device="cuda"))
+        Bs.append([torch.tensor(1.0 - rng.random((k, r)), device="cuda") for k in m])
+    A = inputs.example_equal_factors()
+    X = torch.tensor(np.einsum("iq,jq,kq->ijk", *A), device="cuda")
+    inits = inputs.study_inits((4, 4, 4), (3, 4, 4), 4, 200, seed=9)
+    big = inputs.paper_batch_problems(5, seed=77)
+    runs = {}
+    for on in (False, True):
+        native.nnc_autotune_enable(on)
+        B = [_clone(b) for b in Bs]
+        e_cp = native.nncp_core_fit_batched([(cores[i], B[i]) for i in range(300)], 200)
+        F = [[torch.tensor(f, device="cuda") for f in s["F"]] for s in inits]
+        G = [torch.tensor(s["G"], device="cuda") for s in inits]
+        e_ntd = native.ntd_fit_small_batched([(X, F[i], G[i]) for i in range(200)], 200)
+        Xb = [torch.tensor(p["X"], device="cuda") for p in big]
+        Fb = [[torch.tensor(f, device="cuda") for f in p["F"]] for p in big]
+        Gb = [torch.tensor(p["G"], device="cuda") for p in big]
+        e_l2 = native.ntd_fit_small_batched([(Xb[i], Fb[i], Gb[i]) for i in range(5)], 200)
+        Ab = [[torch.tensor(a, device="cuda") for a in p["A"]] for p in big]
+        e_cpx = native.nncp_core_fit_batched([(Xb[i], Ab[i]) for i in range(5)], 200)
+        runs[on] = (e_cp, B, e_ntd, F, G, e_l2, Fb, Gb, e_cpx, Ab)
+    native.nnc_autotune_enable(True)
+
+    def flat(x):
+        if isinstance(x, torch.Tensor):
+            return [x.cpu().numpy()]
+        return [a for y in x for a in flat(y)]
+
+    for a, b in zip(flat(runs[False]), flat(runs[True])):
+        np.testing.assert_array_equal(a, b)
