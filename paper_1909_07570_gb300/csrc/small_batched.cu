@@ -22,24 +22,20 @@ namespace {
 constexpr int kThreads = 256;
 
 // out = in x_k A for a 3-way `in` (dims d[0..2], C order): out has d[k]
-// replaced by P and out[.., p, ..] = sum_j A[p sp + j sj] in[.., j, ..].
+// replaced by P and out[.., p, ..] = sum_j A[p sp + j sj] in[.., j, ..]. The
+// tensor is viewed as (L, J, C) around mode k; j runs in order.
 template <typename T>
 __device__ void mp3(const T* in, const int* d, int k, const T* A, int sp, int sj, int P, T* out) {
-  int od[3] = {d[0], d[1], d[2]};
-  od[k] = P;
-  const int n = od[0] * od[1] * od[2];
+  const int L = k == 0 ? 1 : (k == 1 ? d[0] : d[0] * d[1]);
+  const int C = k == 2 ? 1 : (k == 1 ? d[2] : d[1] * d[2]);
   const int J = d[k];
+  const int n = L * P * C;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    int idx[3];
-    idx[2] = e % od[2];
-    idx[1] = (e / od[2]) % od[1];
-    idx[0] = e / (od[1] * od[2]);
-    const int p = idx[k];
+    const int c = e % C, lp = e / C, p = lp % P, l = lp / P;
+    const T* x = in + l * J * C + c;
+    const T* a = A + p * sp;
     T s = T(0);
-    for (int j = 0; j < J; ++j) {
-      idx[k] = j;
-      s = fma(A[p * sp + j * sj], in[(idx[0] * d[1] + idx[1]) * d[2] + idx[2]], s);
-    }
+    for (int j = 0; j < J; ++j) s = fma(a[j * sj], x[j * C], s);
     out[e] = s;
   }
   __syncthreads();
@@ -47,23 +43,20 @@ __device__ void mp3(const T* in, const int* d, int k, const T* A, int sp, int sj
 
 // out[i, a] = sum over the other two indices of Y[.., i, ..] G[.., a, ..]
 // (unfold_n(Y) unfold_n(G)^T); Y has dims dy, G has dims dg, equal off mode n.
+// Both are viewed as (L, mode n, C); the terms run over l, then c, in order.
 template <typename T>
 __device__ void unfold_dot(const T* Y, const int* dy, const T* G, const int* dg, int n, T* out) {
   const int NI = dy[n], MA = dg[n];
-  const int o0 = n == 0 ? 1 : 0, o1 = n == 2 ? 1 : 2;
+  const int L = n == 0 ? 1 : (n == 1 ? dy[0] : dy[0] * dy[1]);
+  const int C = n == 2 ? 1 : (n == 1 ? dy[2] : dy[1] * dy[2]);
   for (int e = threadIdx.x; e < NI * MA; e += blockDim.x) {
     const int i = e / MA, a = e % MA;
     T s = T(0);
-    for (int u = 0; u < dy[o0]; ++u)
-      for (int v = 0; v < dy[o1]; ++v) {
-        int iy[3], ig[3];
-        iy[n] = i;
-        ig[n] = a;
-        iy[o0] = ig[o0] = u;
-        iy[o1] = ig[o1] = v;
-        s = fma(Y[(iy[0] * dy[1] + iy[1]) * dy[2] + iy[2]],
-                G[(ig[0] * dg[1] + ig[1]) * dg[2] + ig[2]], s);
-      }
+    for (int l = 0; l < L; ++l) {
+      const T* y = Y + (l * NI + i) * C;
+      const T* g = G + (l * MA + a) * C;
+      for (int c = 0; c < C; ++c) s = fma(y[c], g[c], s);
+    }
     out[e] = s;
   }
   __syncthreads();
@@ -243,7 +236,20 @@ __device__ void pass_rows(const T* __restrict__ X, int R, int N3, const T* F, in
 #pragma unroll
     for (int p = 0; p < QM; ++p) acc[p] = T(0);
     const T* x = X + (int64_t)r * N3;
-    for (int k = 0; k < N3; ++k) {
+    int k = 0;
+    for (; k + 8 <= N3; k += 8) {  // 8 loads in flight, then the terms in order
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldg(x + k + u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T* f = F + (k + u) * Q;
+#pragma unroll
+        for (int p = 0; p < QM; ++p)
+          if (p < Q) acc[p] = fma(v[u], f[p], acc[p]);
+      }
+    }
+    for (; k < N3; ++k) {
       const T v = __ldg(x + k);
       const T* f = F + k * Q;
 #pragma unroll
@@ -265,7 +271,20 @@ __device__ void pass_cols(const T* __restrict__ X, int N1, int C, const T* F, in
     T acc[QM];
 #pragma unroll
     for (int p = 0; p < QM; ++p) acc[p] = T(0);
-    for (int i = 0; i < N1; ++i) {
+    int i = 0;
+    for (; i + 8 <= N1; i += 8) {  // 8 loads in flight, then the terms in order
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldg(X + (int64_t)(i + u) * C + c);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T* f = F + (i + u) * Q;
+#pragma unroll
+        for (int p = 0; p < QM; ++p)
+          if (p < Q) acc[p] = fma(f[p], v[u], acc[p]);
+      }
+    }
+    for (; i < N1; ++i) {
       const T v = __ldg(X + (int64_t)i * C + c);
       const T* f = F + i * Q;
 #pragma unroll
