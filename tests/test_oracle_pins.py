@@ -404,3 +404,33 @@ def test_alg2_on_a_planted_canonical_tensor():
     assert cpt[-1] < 0.05 and np.all(np.diff(cpt) <= 1e-12)
     assert all(t[-1] < 0.05 for t in nmft)
     assert orc.rel_err_cp(X, orc.lift(F, B)) < 0.1
+
+
+def test_kruskal_rank_on_known_matrices():
+    # Kruskal rank: the largest k with every k columns independent.
+    assert inputs.kruskal_rank(np.eye(5)) == 5
+    A = np.eye(4)[:, [0, 1, 2, 2]]               # a repeated column
+    assert inputs.kruskal_rank(A) == 1
+    B = np.c_[np.eye(3), np.zeros(3)]            # a zero column
+    assert inputs.kruskal_rank(B) == 0
+    C = np.array([[1.0, 0, 1], [0, 1, 1]])       # any 2 independent, 3 columns in R^2
+    assert inputs.kruskal_rank(C) == 2
+
+
+def test_paper_batch_problems_follow_the_recipe():
+    # The Sec. 4.3 batch generator: rank-deficient planted factors F B with
+    # kappa = (3, 4, 5), Kruskal ranks adding up to at least 2r + 2, X their
+    # CP tensor, positive starts; the same seed gives the same batch.
+    p = inputs.paper_batch_problems(3, N=12, seed=5)
+    q = inputs.paper_batch_problems(3, N=12, seed=5)
+    for a, b in zip(p, q):
+        np.testing.assert_array_equal(a["X"], b["X"])
+    for t in p:
+        A = t["A_true"]
+        assert [np.linalg.matrix_rank(a) for a in A] == [3, 4, 5]
+        assert sum(inputs.kruskal_rank(a) for a in A) >= 2 * 5 + 2
+        np.testing.assert_allclose(t["X"], np.einsum("iq,jq,kq->ijk", *A), rtol=1e-12)
+        assert t["m"] == (3, 4, 5) and t["r"] == 5
+        for key in ("F", "B", "A", "F2", "B2"):
+            assert all((x > 0).all() for x in t[key])
+        assert (t["G"] > 0).all() and t["G"].shape == (3, 4, 5)
