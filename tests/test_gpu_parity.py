@@ -130,11 +130,13 @@ def test_ntd_rejects_bad_input():
 # 4-way nnTD (the d-way mode-product sweep)
 # ---------------------------------------------------------------------------
 
-# The last case has m = 64 and 40 (split-K unfolding products over up to
-# 64 x 8 x 8 = 4096 terms per entry, several 32-row tiles of F^(1)).
+# (70, 45, 9, 10) has m = 64 and 40 (split-K numerators over up to 64 x 8 x 8
+# terms per entry, several 32-row tiles of F^(1)); the last case has a core of
+# 32,000 doubles with slices of up to 4,000 entries per index of mode 4.
 @pytest.mark.parametrize("dims,m", [((13, 11, 9, 10), (3, 4, 2, 5)), ((7, 1, 12, 9), (2, 1, 3, 4)),
                                     ((6, 40, 5, 33), (6, 9, 5, 8)),
-                                    ((70, 45, 9, 10), (64, 40, 8, 8))])
+                                    ((70, 45, 9, 10), (64, 40, 8, 8)),
+                                    ((41, 43, 11, 5), (40, 40, 10, 2))])
 def test_ntd4_one_sweep_fp64_elementwise(dims, m):
     X, _, F0, G0, _ = inputs.small_problem(dims, 3, m, 2, seed=111)
     err, tr, F, G = _run_ntd(X, F0, G0, 1, torch.float64)
