@@ -112,7 +112,20 @@ int nncp_run(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel_er
     const size_t b = nncp_smem_bytes(j, sizeof(T));
     smem = b > smem ? b : smem;
   }
-  if (smem > 200 * 1024) return nncp_l2_batched<T>(n_jobs, jobs, o->iters, o->eps, rel_errs, s);
+  // The core kernel reads the tensor through L1 once per Num entry: r times
+  // per mode and sweep. From kTwoPassMinEntries entries on (tensors past what
+  // L1 holds, such as X itself in Alg. 2) the two-pass kernel, which reads it
+  // twice per sweep, takes the batch when it can.
+  constexpr int64_t kTwoPassMinEntries = 16384;
+  int64_t largest = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    int64_t e = 1;
+    for (int k = 0; k < jobs[i].d; ++k) e *= jobs[i].m[k];
+    largest = e > largest ? e : largest;
+  }
+  if (smem > 200 * 1024 ||
+      (largest >= kTwoPassMinEntries && nncp_l2_fits<T>(n_jobs, jobs)))
+    return nncp_l2_batched<T>(n_jobs, jobs, o->iters, o->eps, rel_errs, s);
   Scratch sc(s);
   nncp_job* dev = nullptr;
   NNC_TRY(sc.get(&dev, (size_t)n_jobs));

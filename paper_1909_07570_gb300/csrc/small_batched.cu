@@ -685,6 +685,17 @@ int ntd_small_batched(int n_jobs, const ntd_small_job* jobs, int iters, double e
 }
 
 template <typename T>
+bool nncp_l2_fits(int n_jobs, const nncp_job* jobs) {
+  size_t elems = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    if (jobs[i].d != 3 || jobs[i].r > 16) return false;
+    const size_t e = cpx_l2_elems(jobs[i]);
+    elems = e > elems ? e : elems;
+  }
+  return elems * sizeof(T) <= 200 * 1024;
+}
+
+template <typename T>
 int nncp_l2_batched(int n_jobs, const nncp_job* jobs, int iters, double eps, double* rel_errs,
                     cudaStream_t s) {
   size_t elems = 0;
@@ -788,7 +799,8 @@ int lifted_small_batched(int n_jobs, const lifted_job* jobs, double* rel_errs, c
                                     cudaStream_t);                                          \
   template int nmf_small_batched<T>(int, const nmf_job*, int, double, double*, cudaStream_t); \
   template int lifted_small_batched<T>(int, const lifted_job*, double*, cudaStream_t);        \
-  template int nncp_l2_batched<T>(int, const nncp_job*, int, double, double*, cudaStream_t);
+  template int nncp_l2_batched<T>(int, const nncp_job*, int, double, double*, cudaStream_t); \
+  template bool nncp_l2_fits<T>(int, const nncp_job*);
 NNC_SMALL_INST(float)
 NNC_SMALL_INST(double)
 #undef NNC_SMALL_INST
