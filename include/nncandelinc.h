@@ -215,9 +215,11 @@ typedef struct {
  * nncp_core_fit_batched - many independent nncp_core_fit problems (uneven
  * shapes and ranks: restarts, candidate ranks, several tensors) in one
  * launch, one thread block per job. Same update rule and options as
- * nncp_core_fit. A batch with a tensor too large for shared memory (X itself
- * in Alg. 2, e.g. 40 x 40 x 40) runs with the tensors in global memory, two
- * passes over each per sweep (d = 3 and r <= 16 there, else UNSUPPORTED).
+ * nncp_core_fit. A batch holding a large tensor (16384 entries or more, such
+ * as X itself in Alg. 2, e.g. 40 x 40 x 40) runs with the tensors read twice
+ * per sweep from global memory when every job is 3-way with r <= 16 and its
+ * arrays fit one block; a batch whose state does not fit shared memory and
+ * that this cannot take is UNSUPPORTED. The same holds for nncp_core_fit.
  *
  *  jobs       host array of n_jobs descriptors (copied by the call)
  *  rel_errs   device array of n_jobs doubles, or NULL: final relative error
