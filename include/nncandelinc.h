@@ -443,6 +443,18 @@ long long nnc_kernel_launches(void);
  */
 int nnc_autotune_enable(int on);
 
+/*
+ * Failure-detection self-test (not a step of the method). Every wait of the
+ * tensor-core pass kernel on an mbarrier is bounded: past its limit the role
+ * that waits flags the CTA as failed, the others stop, and the call returns
+ * NNC_ERR_TIMEOUT instead of hanging. This runs that same wait once, in a
+ * one-CTA kernel, on a barrier that expects one arrival and gets none (no
+ * copy or MMA is in flight), with a limit of `cycles` SM clocks (a few
+ * million: about a millisecond). Returns NNC_ERR_TIMEOUT when the wait gave
+ * up, as it must, and NNC_OK if it returned; the CUDA context stays usable.
+ */
+int nnc_wait_selftest(long long cycles, void* stream);
+
 /* Static string naming a status code. */
 const char* nnc_status_string(int status);
 

@@ -209,6 +209,11 @@ const char* nnc_last_error_detail(void) { return g_detail.c_str(); }
 
 long long nnc_kernel_launches(void) { return g_kernel_launches.load(); }
 
+int nnc_wait_selftest(long long cycles, void* stream) {
+  g_detail.clear();
+  return tc::wait_selftest(cycles, static_cast<cudaStream_t>(stream));
+}
+
 int nnc_autotune_enable(int on) {
   const bool was = autotune_on();
   autotune_set(on != 0);

@@ -90,12 +90,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait on phase `parity`. False when the limit ran out or another role
 // of this CTA has already failed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* fail,
+                                          long long limit = kWaitCycles) {
   if (mbar_try_wait(bar, parity)) return true;  // the common case: no clock read
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*fail) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicExch(const_cast<int*>(fail), 1);
       return false;
     }
@@ -992,6 +993,43 @@ int TcPlan::pass1(const float* F1, float* P1, cudaStream_t s, bool convert, cons
   if (kind == kKindBf16)
     return launch_np<kKindBf16, true>(np1, mapA1, mapB1, mapB1lo, nk, tiles, ep, err, s);
   return launch_np<kKindTf32x3, false>(np1, mapA1, mapB1, mapB1lo, nk, tiles, ep, err, s);
+}
+
+// Self-test of the bounded waits: one CTA waits, with a limit of `cycles`, on
+// the first phase of an mbarrier that expects one arrival and gets none (no
+// copy or MMA is in flight). The wait must give up and flag the failure the
+// way the pass kernel's roles do; status[0] = 1 then, 0 if the wait returned.
+__global__ void wait_selftest_kernel(long long cycles, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int fail;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool got = mbar_wait(&bar, 0, &fail, cycles);
+  __syncthreads();
+  if (threadIdx.x == 0) status[0] = (got && !fail) ? 0 : 1;
+}
+
+int wait_selftest(long long cycles, cudaStream_t s) {
+  if (cycles < 0) return NNC_ERR_INVALID_ARG;
+  Scratch sc(s);
+  int* d = nullptr;
+  NNC_TRY(sc.get(&d, 1));
+  NNC_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(int), s));
+  wait_selftest_kernel<<<1, 32, 0, s>>>(cycles, d);
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  int h = 0;
+  NNC_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NNC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h != 0) {
+    set_error_detail_text("self-test: the bounded wait gave up as it should");
+    return NNC_ERR_TIMEOUT;
+  }
+  return NNC_OK;
 }
 
 int TcPlan::check(cudaStream_t s) const {

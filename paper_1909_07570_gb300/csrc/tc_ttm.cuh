@@ -87,5 +87,10 @@ struct TcPlan {
   int check(cudaStream_t s) const;
 };
 
+// Runs the pass kernel's bounded mbarrier wait once, with a limit of `cycles`,
+// on a barrier that never completes: NNC_ERR_TIMEOUT when it gives up (the
+// expected outcome), NNC_OK if it did not.
+int wait_selftest(long long cycles, cudaStream_t s);
+
 }  // namespace tc
 }  // namespace nnc

@@ -29,7 +29,7 @@ EXPORTED = ("ntd_fit", "ntd_fit_batched", "ntd_fit_small_batched", "nmf_fit_batc
             "nncp_tensor_fit", "nmf_fit", "candelinc_alg2",
             "nnc_status_string", "nnc_last_error_detail",
             "nnc_profile_enable", "nnc_profile_read", "nnc_kernel_launches",
-            "nnc_autotune_enable")
+            "nnc_autotune_enable", "nnc_wait_selftest")
 
 
 class NncError(RuntimeError):
@@ -135,6 +135,8 @@ def load(path: str | None = None):
     lib.nnc_kernel_launches.restype = ctypes.c_longlong
     lib.nnc_autotune_enable.argtypes = [ctypes.c_int]
     lib.nnc_autotune_enable.restype = ctypes.c_int
+    lib.nnc_wait_selftest.argtypes = [ctypes.c_longlong, vp]
+    lib.nnc_wait_selftest.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -530,3 +532,8 @@ def nnc_autotune_enable(on=True):
     """Switch the launch-shape autotuner of the batched fits; returns the
     previous setting."""
     return bool(load().nnc_autotune_enable(1 if on else 0))
+
+
+def nnc_wait_selftest(cycles=2_000_000, stream=None):
+    """Status of the bounded-wait self-test (NNC_ERR_TIMEOUT = -7 expected)."""
+    return int(load().nnc_wait_selftest(int(cycles), _stream(stream)))
