@@ -434,3 +434,33 @@ def test_paper_batch_problems_follow_the_recipe():
         for key in ("F", "B", "A", "F2", "B2"):
             assert all((x > 0).all() for x in t[key])
         assert (t["G"] > 0).all() and t["G"].shape == (3, 4, 5)
+
+
+# 4-way counterparts of the pins above (the d = 4 nnTD and residual on the GPU
+# are checked against these oracle functions).
+
+def test_exact_canonical_tucker_is_a_fixed_point_4way():
+    X, W, H, G = _canonical_solution((7, 6, 5, 4), (3, 2, 4, 2), 4, 13)
+    F1, G1, _ = orc.ntd_sweep(X, W, G)
+    for a, b in zip(F1, W):
+        np.testing.assert_allclose(a, b, rtol=1e-12)
+    np.testing.assert_allclose(G1, G, rtol=1e-12)
+    assert orc.rel_err_cp(X, orc.lift(W, H)) < 1e-14
+    assert orc.rel_err_tucker(X, G, W) < 1e-14
+
+
+def test_residual_identity_matches_brute_force_4way():
+    X, _, F0, G0, _ = inputs.small_problem((6, 5, 4, 7), 3, (3, 2, 2, 3), 3, seed=4)
+    F, G, _ = orc.ntd_sweep(X, F0, G0)
+    M, _ = orc.ntd_core_terms(X, F, G)
+    r2 = orc.residual_sq_identity(np.sum(X * X), M, G, F)
+    brute = np.sum((X - orc.tucker_reconstruct(G, F)) ** 2)
+    np.testing.assert_allclose(r2, brute, rtol=1e-10)
+
+
+def test_ntd_fit_trace_monotone_4way():
+    X, _, F0, G0, _ = inputs.small_problem((8, 7, 6, 5), 3, (3, 3, 2, 2), 3, seed=12, noise=0.05)
+    F, G, trace = orc.ntd_fit(X, F0, G0, 40)
+    np.testing.assert_allclose(trace[-1], orc.rel_err_tucker(X, G, F), rtol=1e-9)
+    assert np.all(np.diff(trace) <= 1e-12 * trace[:-1])
+    assert all((f >= 0).all() for f in F) and (G >= 0).all()
