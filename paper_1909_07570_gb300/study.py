@@ -39,6 +39,24 @@ def mean_congruence(A, A_true):
     return best
 
 
+def batch_mean_congruence(A, A_true):
+    """mean_congruence of many decompositions at once: A is a list over modes of
+    (n, N_k, r) arrays, A_true a list over modes of (N_k, r) or (n, N_k, r)
+    arrays. Returns n values (every permutation tried, as mean_congruence)."""
+    n, r = A[0].shape[0], A[0].shape[2]
+    C = np.ones((n, r, r))
+    for a, t in zip(A, A_true):
+        t = np.broadcast_to(t, (n,) + t.shape[-2:])
+        na = np.linalg.norm(a, axis=1)                    # (n, r)
+        nt = np.linalg.norm(t, axis=1)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            cos = np.einsum("snq,snp->sqp", t, a) / (nt[:, :, None] * na[:, None, :])
+        C = C * np.nan_to_num(cos)
+    perms = np.array(list(itertools.permutations(range(r))))   # (P, r)
+    vals = C[:, np.arange(r)[None, :], perms].mean(axis=2)     # (n, P)
+    return vals.max(axis=1)
+
+
 def run(multiranks=((3, 3, 3), (3, 4, 4), (4, 4, 4), (5, 5, 5)), starts=1000, iters=500,
         seed=2024, device="cuda"):
     """Returns {(alg, multirank): {"rel_err": array, "congruence": array}}."""
@@ -53,7 +71,7 @@ def run(multiranks=((3, 3, 3), (3, 4, 4), (4, 4, 4), (5, 5, 5)), starts=1000, it
 
     def congruences(Fs, Bs):
         A = [np.einsum("snm,smr->snr", f.cpu().numpy(), b.cpu().numpy()) for f, b in zip(Fs, Bs)]
-        return np.array([mean_congruence([a[i] for a in A], A_true) for i in range(starts)])
+        return batch_mean_congruence(A, A_true)
 
     for mi, m in enumerate(multiranks):
         inits = inputs.study_inits(dims, m, r, starts, seed + 101 * mi)
@@ -103,11 +121,12 @@ def run_paper_batch(problems=None, n_tensors=None, iters=None, dtype=torch.float
 
     X = stack("X")
 
+    A_true = [np.stack([p["A_true"][k] for p in problems]) for k in range(3)]
+
     def congruences(Fs, Bs):
         A = [np.einsum("snm,smr->snr", f.double().cpu().numpy(), b.double().cpu().numpy())
              for f, b in zip(Fs, Bs)]
-        return np.array([mean_congruence([a[i] for a in A], problems[i]["A_true"])
-                         for i in range(n)])
+        return batch_mean_congruence(A, A_true)
 
     def timed(name, fn):
         if timings is None:

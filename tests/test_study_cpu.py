@@ -35,3 +35,17 @@ def test_summaries():
     assert rows["congruence_mean"] == pytest.approx(np.mean(c))
     rows = study.summary({("alg2", (4, 4, 4)): {"rel_err": e, "congruence": c}})
     assert rows["alg2_4x4x4"]["share_rel_err_below_1e-3"] == pytest.approx(0.5)
+
+
+def test_batch_congruence_matches_one_at_a_time():
+    n, r = 7, 5
+    A = [RNG.random((n, m, r)) for m in (9, 8, 7)]
+    T = [RNG.random((n, m, r)) for m in (9, 8, 7)]
+    got = study.batch_mean_congruence(A, T)
+    for i in range(n):
+        want = orc.mean_congruence([t[i] for t in T], [a[i] for a in A])
+        assert got[i] == pytest.approx(want, abs=1e-12)
+    T1 = [t[0] for t in T]  # one true decomposition for every fit (the multirank study)
+    got1 = study.batch_mean_congruence(A, T1)
+    for i in range(n):
+        assert got1[i] == pytest.approx(study.mean_congruence([a[i] for a in A], T1), abs=1e-12)
