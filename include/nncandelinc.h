@@ -64,6 +64,21 @@ typedef struct {
   int refine_iters;  /* NNC_BF16_REFINE only: the last refine_iters of the
                         iters sweeps run in FP32 (0 <= refine_iters <= iters) */
   double eps;        /* denominator guard, > 0 (1e-12 in the tests)         */
+  int exact_every;   /* ntd_fit, d = 3, with a trace (other calls ignore it):
+                        0, or k > 0: after every k-th sweep and after the
+                        last, the sweep's trace entry is the relative error
+                        of one explicit pass over X with FP64 sums instead of
+                        the residual identity (exact near convergence, where
+                        the identity cancels; one pass over X per entry)     */
+  double refine_tol; /* NNC_BF16_REFINE with exact_every > 0: 0, or tau > 0:
+                        the BF16 sweeps also end, and the FP32 refinement
+                        sweeps begin, at the first exact checkpoint whose
+                        relative decrease since the previous one is below tau
+                        times the largest such decrease so far in the fit
+                        (progress has slowed to that fraction of its peak);
+                        the host reads each checkpoint (one synchronisation
+                        per checkpoint). nnc_last_refine_sweep() tells where
+                        the switch came                                      */
 } nnc_opts;
 
 /*
@@ -93,8 +108,12 @@ typedef struct {
  *             from the FP64 identity ||X||^2 - 2<Num_G, G> + <G, Den_G(G)>
  *  rel_err    host, or NULL: final relative error from one explicit FP64
  *             pass over X (as recon_residual)
- * Errors: INVALID_ARG, NEGATIVE_INPUT, NONFINITE (checked on X before any
- * sweep), UNSUPPORTED (NNC_BF16_REFINE with d = 4), CUDA, ALLOC.
+ * Errors: INVALID_ARG, NEGATIVE_INPUT, NONFINITE (X holds a NaN or an
+ * infinity, checked before any sweep; or the FP64 residual terms of some
+ * sweep were not finite, i.e. the fit overflowed or produced a NaN: every
+ * sweep's trace entry is checked on the device and the call reports the first
+ * bad sweep in nnc_last_error_detail), UNSUPPORTED (NNC_BF16_REFINE,
+ * exact_every or refine_tol with d = 4), CUDA, ALLOC, TIMEOUT.
  */
 int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precision,
             const nnc_opts* opts, void* const* F, void* G, double* rel_err_trace,
@@ -197,7 +216,8 @@ int lifted_rel_err_batched(int n_jobs, const lifted_job* jobs, int precision, do
  *  B          host array of d device pointers: initial B^(n) (> 0) in,
  *             fitted B^(n) out
  *  rel_err    host, or NULL: final ||G - I x_n B^(n)||_F / ||G||_F (FP64 sums)
- * Errors: INVALID_ARG, UNSUPPORTED, CUDA, ALLOC.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA, ALLOC; NONFINITE when rel_err is
+ * asked for and is not finite (a NaN or an overflow in the fit).
  */
 int nncp_core_fit(const void* G, int d, const int* m, int r, int precision, const nnc_opts* opts,
                   void* const* B, double* rel_err, void* stream);
@@ -224,11 +244,24 @@ typedef struct {
  *  jobs       host array of n_jobs descriptors (copied by the call)
  *  rel_errs   device array of n_jobs doubles, or NULL: final relative error
  *             of each job
- * Errors: INVALID_ARG (any job), UNSUPPORTED (see above), CUDA, ALLOC. No
- * host synchronisation.
+ *  statuses   device array of n_jobs ints, or NULL: the status of each fit,
+ *             written by the fit's own block when the launch ends:
+ *               NNC_OK;
+ *               NNC_ERR_NONFINITE   a NaN or an infinity in the fitted B^(n)
+ *                                   or in the FP64 residual sums (e.g. a NaN
+ *                                   or an overflow in the job's core);
+ *               NNC_ERR_INVALID_ARG the descriptor is bad (d, m, r or a NULL
+ *                                   pointer); the job is skipped, its arrays
+ *                                   are not touched.
+ *             No wait in these kernels is bounded by time (they have none),
+ *             so a fit never reports NNC_ERR_TIMEOUT.
+ * Errors: INVALID_ARG (bad options; with statuses NULL also any bad job
+ * descriptor; with statuses given a bad descriptor only marks its job and the
+ * other jobs run), UNSUPPORTED (see above), CUDA, ALLOC. No host
+ * synchronisation.
  */
 int nncp_core_fit_batched(int n_jobs, const nncp_job* jobs, int precision, const nnc_opts* opts,
-                          double* rel_errs, void* stream);
+                          double* rel_errs, int* statuses, void* stream);
 
 /*
  * nncp_core_fit_batched_noalloc - nncp_core_fit_batched for callers that must
@@ -243,9 +276,17 @@ int nncp_core_fit_batched(int n_jobs, const nncp_job* jobs, int precision, const
  * (4096 descriptors, 256 KiB, held on every GPU that loads the library until
  * the process exits) and calls no allocator at all.
  *
- * Same kernel, arguments, results and errors as nncp_core_fit_batched, except:
+ * Arguments, results, statuses and errors are those of nncp_core_fit_batched,
+ * and every batch it accepts runs the same one-pass kernel with the same sums,
+ * except:
+ *  - batches that nncp_core_fit_batched sends to its two-pass kernel (a tensor
+ *    of 16384 entries or more, such as X in Alg. 2, or state beyond one block:
+ *    see above) are refused with NNC_ERR_UNSUPPORTED, because that kernel's
+ *    table is allocated; nnc_last_error_detail says so;
  *  - n_jobs > 4096 is rejected with NNC_ERR_INVALID_ARG (nnc_last_error_detail
  *    says so);
+ *  - it never times block sizes: it reuses the size an earlier allocating call
+ *    of the same shape class chose (the results are the same bits either way);
  *  - the first call on a device looks up the table's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture;
@@ -257,7 +298,8 @@ int nncp_core_fit_batched(int n_jobs, const nncp_job* jobs, int precision, const
  *    page-locked memory keep `jobs` unchanged until `stream` has reached it.
  */
 int nncp_core_fit_batched_noalloc(int n_jobs, const nncp_job* jobs, int precision,
-                                  const nnc_opts* opts, double* rel_errs, void* stream);
+                                  const nnc_opts* opts, double* rel_errs, int* statuses,
+                                  void* stream);
 
 /*
  * nnc_mode_product - the n-mode product of Appendix A (Def. of n-mode
@@ -332,7 +374,8 @@ int candelinc_lifted_grad(const void* X, int d, const int64_t* dims, const int* 
  *  trace      device, `steps` doubles (L after each step), or NULL
  *  loss       host, L after the last step (NaN for steps = 0), or NULL
  *  (other arguments as candelinc_lifted_grad; F and B are read and written)
- * Errors: as candelinc_lifted_grad.
+ * Errors: as candelinc_lifted_grad; NONFINITE also when the loss of some
+ * step was not finite (an overflow or a NaN during the fit).
  */
 int candelinc_pg_fit(const void* X, int d, const int64_t* dims, const int* m, int r,
                      int precision, int steps, void* const* F, void* const* B, double* trace,
@@ -353,7 +396,8 @@ int candelinc_pg_fit(const void* X, int d, const int64_t* dims, const int* m, in
  *             each sweep (FP64 identity), or NULL
  *  rel_err    host, the last trace value (NaN for 0 sweeps), or NULL
  *  precision  NNC_FP64, NNC_FP32 (TF32x3 tensor-core passes), NNC_FP32_SIMT
- * Errors: INVALID_ARG, NONFINITE, UNSUPPORTED, CUDA, ALLOC, TIMEOUT.
+ * Errors: INVALID_ARG, NONFINITE (X, or a sweep whose FP64 residual terms
+ * were not finite), UNSUPPORTED, CUDA, ALLOC, TIMEOUT.
  */
 int nncp_tensor_fit(const void* X, int d, const int64_t* dims, int r, int precision,
                     const nnc_opts* opts, void* const* A, double* trace, double* rel_err,
@@ -370,7 +414,8 @@ int nncp_tensor_fit(const void* X, int d, const int64_t* dims, int r, int precis
  *  trace      device, opts->iters doubles: ||A - F B||_F / ||A||_F, or NULL
  *  rel_err    host, the last value (NaN for 0 iterations), or NULL
  *  precision  NNC_FP64 (double) or NNC_FP32 / NNC_FP32_SIMT (float)
- * Errors: INVALID_ARG, UNSUPPORTED, CUDA, ALLOC.
+ * Errors: INVALID_ARG, NONFINITE (an iteration's residual was not finite),
+ * UNSUPPORTED, CUDA, ALLOC.
  */
 int nmf_fit(const void* A, int64_t N, int r, int m, int precision, const nnc_opts* opts, void* F,
             void* B, double* trace, double* rel_err, void* stream);
@@ -454,6 +499,21 @@ int nnc_autotune_enable(int on);
  * up, as it must, and NNC_OK if it returned; the CUDA context stays usable.
  */
 int nnc_wait_selftest(long long cycles, void* stream);
+
+/*
+ * Failure-injection hook for tests (not a step of the method; off by
+ * default). Arms the nth scratch allocation from now (nth >= 1; 0 disarms) to
+ * fail on the host as if cudaMallocAsync had returned an error, without
+ * calling the allocator: the call that makes it returns NNC_ERR_ALLOC, releases
+ * the scratch it already holds, and leaves the CUDA context usable. Shared by
+ * every thread of the process. Returns the previous countdown.
+ */
+int nnc_debug_fail_alloc(int nth);
+
+/* The sweep index (0-based) at which the last NNC_BF16_REFINE ntd_fit call of
+ * this thread began its FP32 refinement sweeps (iters when it ran none), or -1
+ * when this thread has made no such call. */
+int nnc_last_refine_sweep(void);
 
 /* Static string naming a status code. */
 const char* nnc_status_string(int status);

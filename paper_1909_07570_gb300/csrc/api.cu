@@ -1,6 +1,7 @@
 // C ABI of the nnCANDELINC library: argument checks and the stream-ordered
 // orchestration of the kernels (Alg. 1 of arXiv 1909.07570).
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -21,6 +22,7 @@ namespace nnc {
 
 namespace {
 thread_local std::string g_detail;
+thread_local int g_refine_sweep = -1;  // nnc_last_refine_sweep()
 }
 
 void set_error_detail(const char* what, cudaError_t e) {
@@ -31,8 +33,42 @@ void set_error_detail(const char* what, cudaError_t e) {
 
 void set_error_detail_text(const std::string& s) { g_detail = s; }
 
+void clear_error_detail() { g_detail.clear(); }
+
+int check_trace_finite(const int* counter, cudaStream_t s, const char* what) {
+  int h[2] = {0, 0};
+  NNC_CUDA_TRY(cudaMemcpyAsync(h, counter, sizeof(h), cudaMemcpyDeviceToHost, s));
+  NNC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h[1] != 0) {
+    g_detail = std::string(what) + ": the residual of sweep " + std::to_string(h[1]) +
+               " is not finite (an overflow or a NaN during the fit)";
+    return NNC_ERR_NONFINITE;
+  }
+  return NNC_OK;
+}
+
+int check_opts(const nnc_opts* o) {
+  if (o == nullptr) return NNC_ERR_INVALID_ARG;
+  if (o->iters < 0 || !(o->eps > 0.0)) return NNC_ERR_INVALID_ARG;
+  if (o->refine_iters < 0 || o->refine_iters > o->iters) return NNC_ERR_INVALID_ARG;
+  if (o->exact_every < 0 || !(o->refine_tol >= 0.0) || !std::isfinite(o->refine_tol))
+    return NNC_ERR_INVALID_ARG;
+  return NNC_OK;
+}
+
 namespace {
 std::atomic<long long> g_kernel_launches{0};
+// Countdown of nnc_debug_fail_alloc: the allocation that takes it from 1 to 0
+// fails; 0 means disarmed.
+std::atomic<int> g_fail_alloc{0};
+}
+
+bool alloc_injection_fires() {
+  int v = g_fail_alloc.load(std::memory_order_relaxed);
+  while (v > 0) {
+    if (g_fail_alloc.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return v == 1;
+  }
+  return false;
 }
 
 void note_launch(cudaStream_t s) {
@@ -83,13 +119,6 @@ int device_sm_count() {
 
 namespace {
 
-int check_opts(const nnc_opts* o) {
-  if (o == nullptr) return NNC_ERR_INVALID_ARG;
-  if (o->iters < 0 || !(o->eps > 0.0)) return NNC_ERR_INVALID_ARG;
-  if (o->refine_iters < 0 || o->refine_iters > o->iters) return NNC_ERR_INVALID_ARG;
-  return NNC_OK;
-}
-
 int check_shape(int d, const int64_t* dims, const int* m, int max_m) {
   if (dims == nullptr || m == nullptr) return NNC_ERR_INVALID_ARG;
   for (int n = 0; n < d; ++n) {
@@ -100,32 +129,12 @@ int check_shape(int d, const int64_t* dims, const int* m, int max_m) {
 }
 
 template <typename T>
-int nncp_run(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel_errs,
+int nncp_run(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel_errs, int* statuses,
              cudaStream_t s) {
-  size_t smem = 0;
-  for (int i = 0; i < n_jobs; ++i) {
-    const nncp_job& j = jobs[i];
-    if (j.G == nullptr || (j.d != 3 && j.d != 4) || j.r < 1 || j.r > 32)
-      return NNC_ERR_INVALID_ARG;
-    for (int k = 0; k < j.d; ++k)
-      if (j.m[k] < 1 || j.m[k] > 64 || j.B[k] == nullptr) return NNC_ERR_INVALID_ARG;
-    const size_t b = nncp_smem_bytes(j, sizeof(T));
-    smem = b > smem ? b : smem;
-  }
-  // The core kernel reads the tensor through L1 once per Num entry: r times
-  // per mode and sweep. From kTwoPassMinEntries entries on (tensors past what
-  // L1 holds, such as X itself in Alg. 2) the two-pass kernel, which reads it
-  // twice per sweep, takes the batch when it can.
-  constexpr int64_t kTwoPassMinEntries = 16384;
-  int64_t largest = 0;
-  for (int i = 0; i < n_jobs; ++i) {
-    int64_t e = 1;
-    for (int k = 0; k < jobs[i].d; ++k) e *= jobs[i].m[k];
-    largest = e > largest ? e : largest;
-  }
-  if (smem > 200 * 1024 ||
-      (largest >= kTwoPassMinEntries && nncp_l2_fits<T>(n_jobs, jobs)))
-    return nncp_l2_batched<T>(n_jobs, jobs, o->iters, o->eps, rel_errs, s);
+  NncpRoute rt;
+  NNC_TRY(nncp_route<T>(n_jobs, jobs, statuses != nullptr, &rt));
+  if (rt.two_pass)
+    return nncp_l2_batched<T>(n_jobs, jobs, o->iters, o->eps, rel_errs, statuses, s);
   Scratch sc(s);
   nncp_job* dev = nullptr;
   NNC_TRY(sc.get(&dev, (size_t)n_jobs));
@@ -136,8 +145,8 @@ int nncp_run(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel_er
                                cudaMemcpyHostToDevice, s));
   const TuneKey key = nncp_tune_key(jobs, n_jobs, sizeof(T));
   NNC_TRY(run_tuned(key, o->iters, 256, s, [&](int threads, int sweeps, bool last) -> int {
-    NNC_CUDA_TRY(launch_nncp<T>(dev, n_jobs, smem, sweeps, o->eps, last ? rel_errs : nullptr, s,
-                                threads));
+    NNC_CUDA_TRY(launch_nncp<T>(dev, n_jobs, rt.smem, sweeps, o->eps, last ? rel_errs : nullptr,
+                                last ? statuses : nullptr, s, threads));
     return NNC_OK;
   }));
   return NNC_OK;
@@ -209,6 +218,12 @@ const char* nnc_last_error_detail(void) { return g_detail.c_str(); }
 
 long long nnc_kernel_launches(void) { return g_kernel_launches.load(); }
 
+int nnc_last_refine_sweep(void) { return g_refine_sweep; }
+
+int nnc_debug_fail_alloc(int nth) {
+  return g_fail_alloc.exchange(nth > 0 ? nth : 0);
+}
+
 int nnc_wait_selftest(long long cycles, void* stream) {
   g_detail.clear();
   return tc::wait_selftest(cycles, static_cast<cudaStream_t>(stream));
@@ -232,6 +247,10 @@ int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precisi
     if (F[n] == nullptr) return NNC_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (d == 4) {
+    if (opts->exact_every > 0 || opts->refine_tol > 0.0) {
+      g_detail = "ntd_fit: exact checkpoints and the refinement trigger serve d = 3 only";
+      return NNC_ERR_UNSUPPORTED;
+    }
     switch (precision) {
       case NNC_FP64:
         return ntd_fit_nway<double>(static_cast<const double*>(X), 4, dims, m, false,
@@ -259,10 +278,14 @@ int ntd_fit(const void* X, int d, const int64_t* dims, const int* m, int precisi
       return ntd_fit3<float>(static_cast<const float*>(X), dims, m, opts,
                              reinterpret_cast<float* const*>(F), static_cast<float*>(G),
                              rel_err_trace, rel_err, precision == NNC_FP32, s);
-    case NNC_BF16_REFINE:
-      return ntd_fit3_bf16(static_cast<const float*>(X), dims, m, opts,
-                           reinterpret_cast<float* const*>(F), static_cast<float*>(G),
-                           rel_err_trace, rel_err, s);
+    case NNC_BF16_REFINE: {
+      int from = -1;
+      const int st = ntd_fit3_bf16(static_cast<const float*>(X), dims, m, opts,
+                                   reinterpret_cast<float* const*>(F), static_cast<float*>(G),
+                                   rel_err_trace, rel_err, &from, s);
+      g_refine_sweep = from;
+      return st;
+    }
     default:
       return NNC_ERR_INVALID_ARG;
   }
@@ -382,29 +405,33 @@ int nncp_core_fit(const void* G, int d, const int* m, int r, int precision, cons
   if (rel_err) NNC_TRY(sc.get(&dev_err, 1));
   int st;
   if (precision == NNC_FP64)
-    st = nncp_run<double>(1, &job, opts, dev_err, s);
+    st = nncp_run<double>(1, &job, opts, dev_err, nullptr, s);
   else if (precision == NNC_FP32 || precision == NNC_BF16_REFINE || precision == NNC_FP32_SIMT)
-    st = nncp_run<float>(1, &job, opts, dev_err, s);
+    st = nncp_run<float>(1, &job, opts, dev_err, nullptr, s);
   else
     return NNC_ERR_INVALID_ARG;
   if (st != NNC_OK) return st;
   if (rel_err) {
     NNC_CUDA_TRY(cudaMemcpyAsync(rel_err, dev_err, sizeof(double), cudaMemcpyDeviceToHost, s));
     NNC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!std::isfinite(*rel_err)) {
+      set_error_detail_text("nncp_core_fit: the fit's residual is not finite");
+      return NNC_ERR_NONFINITE;
+    }
   }
   return NNC_OK;
 }
 
 int nncp_core_fit_batched(int n_jobs, const nncp_job* jobs, int precision, const nnc_opts* opts,
-                          double* rel_errs, void* stream) {
+                          double* rel_errs, int* statuses, void* stream) {
   g_detail.clear();
   NNC_TRY(check_opts(opts));
   if (n_jobs < 0 || (n_jobs > 0 && jobs == nullptr)) return NNC_ERR_INVALID_ARG;
   if (n_jobs == 0) return NNC_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (precision == NNC_FP64) return nncp_run<double>(n_jobs, jobs, opts, rel_errs, s);
+  if (precision == NNC_FP64) return nncp_run<double>(n_jobs, jobs, opts, rel_errs, statuses, s);
   if (precision == NNC_FP32 || precision == NNC_BF16_REFINE || precision == NNC_FP32_SIMT)
-    return nncp_run<float>(n_jobs, jobs, opts, rel_errs, s);
+    return nncp_run<float>(n_jobs, jobs, opts, rel_errs, statuses, s);
   return NNC_ERR_INVALID_ARG;
 }
 

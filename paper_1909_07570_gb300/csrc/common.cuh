@@ -29,6 +29,10 @@ void set_error_detail_text(const std::string& s);
     if (st__ != NNC_OK) return st__;                        \
   } while (0)
 
+// True when the test hook nnc_debug_fail_alloc has armed a failure for this
+// allocation (host-side failure injection; off unless a caller arms it).
+bool alloc_injection_fires();
+
 // Stream-ordered scratch: every block is taken with cudaMallocAsync on the
 // call's stream and returned with cudaFreeAsync when the arena dies.
 class Scratch {
@@ -42,6 +46,10 @@ class Scratch {
   int get(T** out, size_t count) {
     *out = nullptr;
     if (count == 0) count = 1;
+    if (alloc_injection_fires()) {
+      set_error_detail_text("scratch allocation failed (injected by nnc_debug_fail_alloc)");
+      return NNC_ERR_ALLOC;
+    }
     void* p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), stream_);
     if (e != cudaSuccess) {
@@ -72,6 +80,20 @@ class Scratch {
 };
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Dynamic shared memory the one-block-per-job kernels may ask for.
+constexpr size_t kSmemBudget = 200 * 1024;
+
+// Clears this thread's error detail (every ABI call does so on entry).
+void clear_error_detail();
+
+// Checks an nnc_opts: iters >= 0, eps > 0, 0 <= refine_iters <= iters.
+int check_opts(const nnc_opts* o);
+
+// NNC_ERR_NONFINITE (with a detail naming `what` and the first bad sweep) when
+// the trace counter pair of a fit (see trace_record) saw a non-finite entry;
+// synchronises `s`.
+int check_trace_finite(const int* counter, cudaStream_t s, const char* what);
 
 int device_sm_count();
 
@@ -118,6 +140,19 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // Lets the programmatic successor grid be scheduled before this one ends.
 __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// One entry of a fit's per-sweep trace. `counter` points at two ints that the
+// fit clears before its first sweep: counter[0] counts the entries recorded,
+// counter[1] stays 0 until an entry (or a sum it was formed from) is not
+// finite and then holds the 1-based index of the first such sweep. The value
+// goes to trace[counter[0] * stride] when a trace is kept. One thread calls it.
+__device__ __forceinline__ void trace_record(int* counter, double* trace, int stride, double value,
+                                             bool finite) {
+  const int t = counter[0];
+  if (trace) trace[(int64_t)t * stride] = value;
+  if (!(finite && isfinite(value)) && counter[1] == 0) counter[1] = t + 1;
+  counter[0] = t + 1;
 }
 
 template <typename T>

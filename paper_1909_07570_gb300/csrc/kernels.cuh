@@ -45,7 +45,8 @@ cudaError_t launch_elementwise_mu(T* theta, const T* num, const T* den, int64_t 
 
 // trace[(*counter) * stride] = sqrt(max(x2 - 2 <M, G> + <G, Dn>, 0) / x2), FP64
 // sums over n core entries (per-block partials in `part`, 2 kIdentityBlocks
-// doubles, added in block order); then *counter += 1.
+// doubles, added in block order); then *counter += 1. `counter` is the pair of
+// trace_record (the second int flags the first non-finite entry).
 constexpr int kIdentityBlocks = 128;
 template <typename T>
 cudaError_t launch_residual_identity(const T* M, const T* G, const T* Dn, int64_t n,

@@ -146,11 +146,7 @@ __global__ void rel_norm_kernel(const T* __restrict__ R, int64_t n, const double
   if (threadIdx.x == 0) {
     const double v = a ? sqrt(s) / a[0] : sqrt(s);
     out[0] = v;
-    if (trace) {
-      const int t = *counter;
-      trace[t] = v;
-      *counter = t + 1;
-    }
+    if (counter) trace_record(counter, trace, 1, v, true);
   }
 }
 
@@ -263,13 +259,10 @@ __global__ void lifted_loss_kernel(const T* __restrict__ MT, const T* __restrict
   b = block_sum(b, red);
   if (threadIdx.x == 0) {
     double v = 0.5 * x2[0] - a + 0.5 * b;
+    const bool finite = isfinite(v);
     if (rel) v = sqrt((v > 0.0 ? 2.0 * v : 0.0) / x2[0]);  // ||X - X_hat|| / ||X||
     out[0] = v;
-    if (trace) {
-      const int t = *counter;
-      trace[t] = v;
-      *counter = t + 1;
-    }
+    if (counter) trace_record(counter, trace, 1, v, finite);
   }
 }
 
@@ -655,8 +648,8 @@ int lifted_pg_fit(const T* X, int d, const int64_t* dims, const int* m, int r, b
   for (int k = 0; k < d; ++k) NNC_TRY(refresh_a(w, k, F[k], B[k], s));
   double* last = w.Ls + 3;
   int* counter = nullptr;
-  NNC_TRY(sc.get(&counter, 1));
-  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+  NNC_TRY(sc.get(&counter, 2));
+  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
   if (steps > 0) {
     // One step is captured as a CUDA graph on a private stream and replayed;
     // the trace slot advances through the device counter.
@@ -689,6 +682,7 @@ int lifted_pg_fit(const T* X, int d, const int64_t* dims, const int* m, int r, b
     NNC_CUDA_TRY(cudaStreamSynchronize(g.cs));
   }
   NNC_TRY(check_tc(w, s));
+  NNC_TRY(check_trace_finite(counter, s, "candelinc_pg_fit"));
   if (loss) {
     if (steps == 0) {
       *loss = NAN;
@@ -762,8 +756,8 @@ int nncp_tensor_fit(const T* X, int d, const int64_t* dims, int r, bool tensor_c
   for (int k = 0; k < d; ++k) B[k] = I;
   for (int k = 0; k < d; ++k) NNC_TRY(refresh_a(w, k, A[k], B[k], s));
   int* counter = nullptr;
-  NNC_TRY(sc.get(&counter, 1));
-  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+  NNC_TRY(sc.get(&counter, 2));
+  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
   double* last = w.Ls + 3;
   NNC_TRY(replay(iters, s, [&](cudaStream_t cs) -> int {
     NNC_TRY(pass_last(w, A[d - 1], cs));
@@ -781,6 +775,7 @@ int nncp_tensor_fit(const T* X, int d, const int64_t* dims, int r, bool tensor_c
     return loss_into(w, d - 1, last, trace, counter, cs, /*rel=*/1);
   }));
   NNC_TRY(check_tc(w, s));
+  NNC_TRY(check_trace_finite(counter, s, "nncp_tensor_fit"));
   if (rel_err) {
     if (iters == 0) {
       *rel_err = NAN;
@@ -812,8 +807,8 @@ int nmf_fit(const T* A, int64_t N, int r, int m, int iters, double eps, T* F, T*
   NNC_TRY(sc.get(&R, (size_t)(N * r)));
   NNC_TRY(sc.get(&a, 1));
   NNC_TRY(sc.get(&last, 1));
-  NNC_TRY(sc.get(&counter, 1));
-  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+  NNC_TRY(sc.get(&counter, 2));
+  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
   rel_norm_kernel<T><<<1, 256, 0, s>>>(A, N * r, nullptr, a, nullptr, nullptr);  // ||A||
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
@@ -832,6 +827,7 @@ int nmf_fit(const T* A, int64_t N, int r, int m, int iters, double eps, T* F, T*
     NNC_CUDA_TRY(cudaGetLastError());
     return NNC_OK;
   }));
+  NNC_TRY(check_trace_finite(counter, s, "nmf_fit"));
   if (rel_err) {
     if (iters == 0) {
       *rel_err = NAN;
@@ -891,8 +887,8 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
   double* idpart = nullptr;
   NNC_TRY(sc.get(&idpart, 2 * kIdentityBlocks));
   NNC_TRY(sc.get(&dummy, 1));
-  NNC_TRY(sc.get(&counter, 1));
-  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+  NNC_TRY(sc.get(&counter, 2));
+  NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
   for (int k = 0; k < d; ++k) NNC_TRY(launch_gram<T>(F[k], dims[k], m[k], S[k], s));
   double* tr = trace ? trace : dummy;
   const int stride = trace ? 1 : 0;
@@ -944,6 +940,7 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
     return NNC_OK;
   }));
   NNC_TRY(check_tc(w, s));
+  NNC_TRY(check_trace_finite(counter, s, "ntd_fit"));
   if (rel_err) {
     double* out2 = nullptr;
     NNC_TRY(sc.get(&out2, 2));

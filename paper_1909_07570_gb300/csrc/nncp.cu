@@ -8,8 +8,11 @@
 //   B^(n) <- max(B^(n) * Num / max(B^(n) V, eps), 0);  Gram_n <- B^(n)T B^(n)
 // The same kernel serves one fit (nncp_core_fit) and many uneven fits in one
 // launch (nncp_core_fit_batched); no block waits on another.
+#include <string>
+
 #include "kernels.cuh"
 #include "nncp.cuh"
+#include "small_batched.cuh"
 
 namespace nnc {
 namespace {
@@ -55,7 +58,7 @@ __device__ T mttkrp_entry(const T* __restrict__ G, const int* m, const int64_t* 
 
 template <typename T, int D>
 __device__ void fit_one(const nncp_job& job, int iters, T eps, unsigned char* smem,
-                        double* rel_err_out) {
+                        double* rel_err_out, int* status_out) {
   const int r = job.r;
   int m[D];
   int64_t st[D];
@@ -139,13 +142,17 @@ __device__ void fit_one(const nncp_job& job, int iters, T eps, unsigned char* sm
     }
   }
 
+  bool finite = true;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     T* dst = static_cast<T*>(job.B[k]);
-    for (int e = tid; e < m[k] * r; e += blockDim.x) dst[e] = Bs[k][e];
+    for (int e = tid; e < m[k] * r; e += blockDim.x) {
+      dst[e] = Bs[k][e];
+      finite = finite && isfinite(Bs[k][e]);
+    }
   }
 
-  if (rel_err_out != nullptr) {
+  if (rel_err_out != nullptr || status_out != nullptr) {
     int64_t total = 1;
 #pragma unroll
     for (int k = 0; k < D; ++k) total *= m[k];
@@ -170,20 +177,35 @@ __device__ void fit_one(const nncp_job& job, int iters, T eps, unsigned char* sm
       const double dd = g - (double)hat;
       return make_double2(dd * dd, g * g);
     }, fpart);
-    if (tid == 0) *rel_err_out = dg.y > 0.0 ? sqrt(dg.x / dg.y) : sqrt(dg.x);
+    if (tid == 0 && rel_err_out != nullptr)
+      *rel_err_out = dg.y > 0.0 ? sqrt(dg.x / dg.y) : sqrt(dg.x);
+    // The fit's status: a NaN or an overflow anywhere (in the core, or reached
+    // during the sweeps) shows in the fitted factors or in the residual sums.
+    if (status_out != nullptr) {
+      const int ok = __syncthreads_and(finite ? 1 : 0);
+      if (tid == 0)
+        *status_out = (ok && isfinite(dg.x) && isfinite(dg.y)) ? NNC_OK : NNC_ERR_NONFINITE;
+    }
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-nncp_kernel(const nncp_job* __restrict__ jobs, int iters, T eps, double* rel_errs) {
+nncp_kernel(const nncp_job* __restrict__ jobs, int iters, T eps, double* rel_errs,
+            int* statuses) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const nncp_job job = jobs[blockIdx.x];
+  int* st = statuses ? statuses + blockIdx.x : nullptr;
+  // A job the host skipped (its shared memory was not sized for it).
+  if (!nncp_job_valid(job)) {
+    if (st != nullptr && threadIdx.x == 0) *st = NNC_ERR_INVALID_ARG;
+    return;
+  }
   double* out = rel_errs ? rel_errs + blockIdx.x : nullptr;
   if (job.d == 3)
-    fit_one<T, 3>(job, iters, eps, smem_raw, out);
+    fit_one<T, 3>(job, iters, eps, smem_raw, out, st);
   else
-    fit_one<T, 4>(job, iters, eps, smem_raw, out);
+    fit_one<T, 4>(job, iters, eps, smem_raw, out, st);
 }
 
 }  // namespace
@@ -199,14 +221,57 @@ size_t nncp_smem_bytes(const nncp_job& j, size_t elem) {
 }
 
 template <typename T>
+int nncp_route(int n_jobs, const nncp_job* jobs, bool skip_invalid, NncpRoute* rt) {
+  *rt = NncpRoute{};
+  int64_t largest = 0;
+  bool l2_ok = true;  // every valid job within the two-pass kernel's limits
+  size_t l2_elems = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    const nncp_job& j = jobs[i];
+    if (!nncp_job_valid(j)) {
+      if (!skip_invalid) {
+        set_error_detail_text("batched nnCP: job " + std::to_string(i) +
+                              " has a bad descriptor (d, m, r or a null pointer)");
+        return NNC_ERR_INVALID_ARG;
+      }
+      ++rt->invalid;
+      continue;
+    }
+    const size_t b = nncp_smem_bytes(j, sizeof(T));
+    rt->smem = b > rt->smem ? b : rt->smem;
+    int64_t e = 1;
+    for (int k = 0; k < j.d; ++k) e *= j.m[k];
+    largest = e > largest ? e : largest;
+    if (j.d != 3 || j.r > 16) {
+      l2_ok = false;
+    } else {
+      const size_t le = cpx_l2_elems(j);
+      l2_elems = le > l2_elems ? le : l2_elems;
+    }
+  }
+  l2_ok = l2_ok && l2_elems * sizeof(T) <= kSmemBudget;
+  constexpr int64_t kTwoPassMinEntries = 16384;
+  if (rt->smem > kSmemBudget) {
+    if (!l2_ok) {
+      set_error_detail_text("batched nnCP: a job's state exceeds one block of shared memory");
+      return NNC_ERR_UNSUPPORTED;
+    }
+    rt->two_pass = true;
+  } else {
+    rt->two_pass = largest >= kTwoPassMinEntries && l2_ok;
+  }
+  return NNC_OK;
+}
+
+template <typename T>
 cudaError_t launch_nncp(const nncp_job* jobs_dev, int n_jobs, size_t smem, int iters, double eps,
-                        double* rel_errs, cudaStream_t s, int threads) {
+                        double* rel_errs, int* statuses, cudaStream_t s, int threads) {
   if (threads < 32 || threads > kThreads || threads % 32 != 0) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
     cudaError_t e = raise_smem_limit((const void*)nncp_kernel<T>, smem);
     if (e != cudaSuccess) return e;
   }
-  nncp_kernel<T><<<n_jobs, threads, smem, s>>>(jobs_dev, iters, (T)eps, rel_errs);
+  nncp_kernel<T><<<n_jobs, threads, smem, s>>>(jobs_dev, iters, (T)eps, rel_errs, statuses);
   note_launch(s);
   return cudaGetLastError();
 }
@@ -214,6 +279,7 @@ cudaError_t launch_nncp(const nncp_job* jobs_dev, int n_jobs, size_t smem, int i
 TuneKey nncp_tune_key(const nncp_job* jobs, int n_jobs, size_t elem) {
   long long work = 1;
   for (int i = 0; i < n_jobs; ++i) {
+    if (!nncp_job_valid(jobs[i])) continue;
     long long w = jobs[i].r;  // one sweep: every entry of the core once per mode and q
     for (int k = 0; k < jobs[i].d; ++k) w *= jobs[i].m[k];
     work = w > work ? w : work;
@@ -222,8 +288,10 @@ TuneKey nncp_tune_key(const nncp_job* jobs, int n_jobs, size_t elem) {
 }
 
 template cudaError_t launch_nncp<float>(const nncp_job*, int, size_t, int, double, double*,
-                                        cudaStream_t, int);
+                                        int*, cudaStream_t, int);
 template cudaError_t launch_nncp<double>(const nncp_job*, int, size_t, int, double, double*,
-                                         cudaStream_t, int);
+                                         int*, cudaStream_t, int);
+template int nncp_route<float>(int, const nncp_job*, bool, NncpRoute*);
+template int nncp_route<double>(int, const nncp_job*, bool, NncpRoute*);
 
 }  // namespace nnc

@@ -7,8 +7,11 @@
 // allocations behind its back, a real-time or latency-critical loop where an
 // allocation may stall or fail under memory pressure, or a process that has
 // handed nearly all of the GPU's memory to a framework cache. This entry point
-// runs the same kernel with the job table in a fixed array in the library's own
-// device memory instead, so the call allocates nothing.
+// runs the one-pass core kernel with the job table in a fixed array in the
+// library's own device memory instead, so the call allocates nothing. Batches
+// that the allocating call would send to its two-pass kernel (which takes its
+// own table from the allocator) are refused, so every batch this call accepts
+// runs exactly the kernel, launch shape and sums of the allocating call.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds it (kNoAllocMaxJobs descriptors, 256 KiB) until the process
@@ -55,18 +58,17 @@ int job_table_address(nncp_job** out) {
 
 template <typename T>
 int run_noalloc(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel_errs,
-                cudaStream_t s) {
-  size_t smem = 0;
-  for (int i = 0; i < n_jobs; ++i) {
-    const nncp_job& j = jobs[i];
-    if (j.G == nullptr || (j.d != 3 && j.d != 4) || j.r < 1 || j.r > 32)
-      return NNC_ERR_INVALID_ARG;
-    for (int k = 0; k < j.d; ++k)
-      if (j.m[k] < 1 || j.m[k] > 64 || j.B[k] == nullptr) return NNC_ERR_INVALID_ARG;
-    const size_t b = nncp_smem_bytes(j, sizeof(T));
-    smem = b > smem ? b : smem;
+                int* statuses, cudaStream_t s) {
+  // The routing of the allocating call, to the letter (nncp_route).
+  NncpRoute rt;
+  NNC_TRY(nncp_route<T>(n_jobs, jobs, statuses != nullptr, &rt));
+  if (rt.two_pass) {
+    set_error_detail_text(
+        "nncp_core_fit_batched_noalloc: this batch needs the two-pass kernel (a tensor of 16384 "
+        "entries or more, or state beyond one block), which allocates; use "
+        "nncp_core_fit_batched");
+    return NNC_ERR_UNSUPPORTED;
   }
-  if (smem > 200 * 1024) return NNC_ERR_UNSUPPORTED;
   nncp_job* table = nullptr;
   NNC_TRY(job_table_address(&table));
   NNC_CUDA_TRY(cudaMemcpyAsync(table, jobs, sizeof(nncp_job) * (size_t)n_jobs,
@@ -74,7 +76,8 @@ int run_noalloc(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel
   // A block size tuned by an earlier allocating call of the same class is
   // reused; this call never times anything.
   const int threads = tuned_threads(nncp_tune_key(jobs, n_jobs, sizeof(T)), 256);
-  NNC_CUDA_TRY(launch_nncp<T>(table, n_jobs, smem, o->iters, o->eps, rel_errs, s, threads));
+  NNC_CUDA_TRY(launch_nncp<T>(table, n_jobs, rt.smem, o->iters, o->eps, rel_errs, statuses, s,
+                              threads));
   return NNC_OK;
 }
 
@@ -85,9 +88,16 @@ using namespace nnc;
 
 extern "C" int nncp_core_fit_batched_noalloc(int n_jobs, const nncp_job* jobs, int precision,
                                              const nnc_opts* opts, double* rel_errs,
-                                             void* stream) {
-  if (opts == nullptr || opts->iters < 0 || !(opts->eps > 0.0)) return NNC_ERR_INVALID_ARG;
-  if (n_jobs < 0 || (n_jobs > 0 && jobs == nullptr)) return NNC_ERR_INVALID_ARG;
+                                             int* statuses, void* stream) {
+  clear_error_detail();
+  if (check_opts(opts) != NNC_OK) {
+    set_error_detail_text("nncp_core_fit_batched_noalloc: bad options (iters, refine_iters, eps)");
+    return NNC_ERR_INVALID_ARG;
+  }
+  if (n_jobs < 0 || (n_jobs > 0 && jobs == nullptr)) {
+    set_error_detail_text("nncp_core_fit_batched_noalloc: bad job count or NULL job array");
+    return NNC_ERR_INVALID_ARG;
+  }
   if (n_jobs > kNoAllocMaxJobs) {
     char buf[160];
     snprintf(buf, sizeof(buf),
@@ -98,8 +108,9 @@ extern "C" int nncp_core_fit_batched_noalloc(int n_jobs, const nncp_job* jobs, i
   }
   if (n_jobs == 0) return NNC_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (precision == NNC_FP64) return run_noalloc<double>(n_jobs, jobs, opts, rel_errs, s);
+  if (precision == NNC_FP64) return run_noalloc<double>(n_jobs, jobs, opts, rel_errs, statuses, s);
   if (precision == NNC_FP32 || precision == NNC_BF16_REFINE || precision == NNC_FP32_SIMT)
-    return run_noalloc<float>(n_jobs, jobs, opts, rel_errs, s);
+    return run_noalloc<float>(n_jobs, jobs, opts, rel_errs, statuses, s);
+  set_error_detail_text("nncp_core_fit_batched_noalloc: unknown precision");
   return NNC_ERR_INVALID_ARG;
 }

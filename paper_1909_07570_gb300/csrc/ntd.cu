@@ -312,14 +312,43 @@ int capture_sweep(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, dou
   return NNC_OK;
 }
 
+// Exact checkpoints of the trace and the refinement trigger (nnc_opts
+// exact_every, refine_tol). After every exact_every-th sweep of the fit and
+// after its last one, the pending core update runs at once and the sweep's
+// trace entry is replaced by the relative error of one explicit pass over X
+// (FP64 sums, as recon_residual): the residual identity loses accuracy near
+// convergence, where ||X - X_hat||^2 is a small difference of large terms
+// formed from FP32-accurate (or BF16) quantities.
+template <typename T>
+struct Checkpoints {
+  int every = 0;             // 0: none
+  int total = 0;             // sweeps of the whole fit (the last is a checkpoint)
+  const T* X = nullptr;
+  const int64_t* dims = nullptr;
+  const int* m = nullptr;
+  const ResidualWork<T>* rw = nullptr;
+  // Refinement trigger (fast sweeps only): stop the fast phase at a checkpoint
+  // whose relative decrease since the previous checkpoint is below tol times
+  // the largest such decrease seen so far in the fit.
+  double tol = 0.0;
+  double last = -1.0, peak = 0.0;  // host-side history
+  bool at(int sweep) const {
+    return every > 0 && ((sweep + 1) % every == 0 || sweep + 1 == total);
+  }
+};
+
 // Captures the sweep on a private stream and replays it `count` times after
 // the work already queued on `s`, runs the last sweep's core update, and makes
 // `s` wait for all of it. The core update a replay runs first is the previous
 // sweep's; in the first replay there is none, and the core kernels see the
-// pending flag at 0 and return at once.
+// pending flag at 0 and return at once. `first` is the fit's index of the
+// first of these sweeps; *done gets the number of sweeps run, fewer than
+// `count` when the refinement trigger of `ck` stopped them.
 template <typename T>
 int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* trace,
-               int count, const tc::TcPlan* tcp, cudaStream_t s) {
+               int count, int first, Checkpoints<T>* ck, const tc::TcPlan* tcp, cudaStream_t s,
+               int* done) {
+  *done = 0;
   if (count <= 0) return NNC_OK;
   GraphRun g;
   NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
@@ -342,6 +371,7 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
     NNC_TRY(capture_sweep<T>(X, F, G, b, eps, trace, nullptr, tcp, true, g, 2, kSweepsPerGraph));
     NNC_TRY(count_kernel_nodes(g.graph[2], &kn[2]));
   }
+  const bool checkpoints = ck && ck->every > 0 && trace;
 
   // Sampled sweeps: the last of every kProfileEvery (an instrumented copy,
   // captured once the first plain replays are queued, so the device is busy
@@ -349,16 +379,20 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
   PassProfiler prof(tcp ? (tcp->kind == tc::kKindBf16 ? 2 : 4) : 0);
   const int samples = profile_enabled() ? count / kProfileEvery : 0;
   long long kernels = 0;
-  for (int t = 0; t < count; ++t) {
+  int t = 0;
+  while (t < count) {
     const bool sampled = samples > 0 && t % kProfileEvery == kProfileEvery - 1;
-    if (!sampled && g.exec[2] && t + kSweepsPerGraph <= count &&
-        (samples == 0 || t % kProfileEvery + kSweepsPerGraph <= kProfileEvery - 1)) {
+    // A five-sweep replay must not pass a sampled sweep or a checkpoint (its
+    // last sweep may be one).
+    bool five = !sampled && g.exec[2] && t + kSweepsPerGraph <= count &&
+                (samples == 0 || t % kProfileEvery + kSweepsPerGraph <= kProfileEvery - 1);
+    if (five && checkpoints)
+      for (int u = t; u < t + kSweepsPerGraph - 1; ++u) five = five && !ck->at(first + u);
+    if (five) {
       NNC_CUDA_TRY(cudaGraphLaunch(g.exec[2], g.cs));
       kernels += kn[2];
-      t += kSweepsPerGraph - 1;
-      continue;
-    }
-    if (sampled) {
+      t += kSweepsPerGraph;
+    } else if (sampled) {
       const int j = t / kProfileEvery;
       if (j == 0) {
         NNC_TRY(prof.init(samples));
@@ -369,17 +403,41 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
       NNC_TRY(prof.set_launch(g.exec[1], j));
       NNC_CUDA_TRY(cudaGraphLaunch(g.exec[1], g.cs));
       kernels += kn[1];
+      ++t;
     } else {
       NNC_CUDA_TRY(cudaGraphLaunch(g.exec[0], g.cs));
       kernels += kn[0];
+      ++t;
+    }
+    if (checkpoints && ck->at(first + t - 1)) {
+      const int sweep = first + t - 1;
+      NNC_TRY(launch_sweep_core<T>(F, G, b, eps, trace, 1, g.cs));
+      const T* fac[3] = {F[0], F[1], F[2]};
+      NNC_TRY(residual_run<T>(ck->X, 3, ck->dims, 0, ck->m, 0, fac, G, *ck->rw, nullptr,
+                              trace + sweep, g.cs));
+      if (ck->tol > 0.0) {
+        double e = 0.0;
+        NNC_CUDA_TRY(cudaMemcpyAsync(&e, trace + sweep, sizeof(double), cudaMemcpyDeviceToHost,
+                                     g.cs));
+        NNC_CUDA_TRY(cudaStreamSynchronize(g.cs));
+        bool stop = false;
+        if (ck->last > 0.0 && e > 0.0) {
+          const double drop = (ck->last - e) / e;
+          ck->peak = drop > ck->peak ? drop : ck->peak;
+          stop = drop < ck->tol * ck->peak;
+        }
+        ck->last = e;
+        if (stop) break;
+      }
     }
   }
+  *done = t;
   note_graph_launches(kernels);
   NNC_TRY(launch_sweep_core<T>(F, G, b, eps, trace ? trace : b.trace_dummy, trace ? 1 : 0, g.cs));
   NNC_CUDA_TRY(cudaEventRecord(g.join, g.cs));
   NNC_CUDA_TRY(cudaStreamWaitEvent(s, g.join, 0));
   NNC_CUDA_TRY(cudaStreamSynchronize(g.cs));
-  if (samples > 0) NNC_TRY(prof.collect(samples));
+  if (samples > 0) NNC_TRY(prof.collect(t / kProfileEvery < samples ? t / kProfileEvery : samples));
   return NNC_OK;
 }
 
@@ -388,7 +446,8 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
 // A tensor-core plan that the shape does not allow falls back to SIMT passes.
 template <typename T>
 int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T* const* F,
-                  T* G, double* trace, double* rel_err, int passes, cudaStream_t s) {
+                  T* G, double* trace, double* rel_err, int passes, int* refined_from,
+                  cudaStream_t s) {
   const int64_t N1 = dims[0], N2 = dims[1], N3 = dims[2];
   const int m1 = m[0], m2 = m[1], m3 = m[2];
   const int64_t nX = N1 * N2 * N3;
@@ -404,7 +463,7 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   NNC_TRY(sc.get(&b.stats, 3));
   NNC_TRY(sc.get(&b.trace_dummy, 1));
   NNC_TRY(sc.get(&b.resid2, 2));
-  NNC_TRY(sc.get(&b.counter, 1));
+  NNC_TRY(sc.get(&b.counter, 2));
   NNC_TRY(sc.get(&b.dots, 2 * (size_t)m[0]));
   NNC_TRY(sc.get(&b.done, 1));
   NNC_TRY(sc.get(&b.gate, 1));
@@ -435,19 +494,33 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   tc::TcPlan plan16, plan32;
   const tc::TcPlan* fast = nullptr;   // the first iters - refine sweeps
   const tc::TcPlan* exact = nullptr;  // FP32-accurate sweeps
+  // The refinement trigger may end the fast sweeps early (exact checkpoints needed).
+  const bool trigger = passes == 2 && o->refine_tol > 0.0 && o->exact_every > 0 && trace;
   if constexpr (std::is_same<T, float>::value) {
     if (passes == 2 && o->iters > o->refine_iters) {
       NNC_TRY(plan16.init(tc::kKindBf16, X, N1, N2, N3, m1, m3, sc, s, /*p1_kj=*/true));
       fast = &plan16;
     }
-    if (passes >= 1 && (passes == 1 || o->refine_iters > 0)) {
+    if (passes >= 1 && (passes == 1 || o->refine_iters > 0 || trigger)) {
       const int st = plan32.init(tc::kKindTf32x3, X, N1, N2, N3, m1, m3, sc, s, /*p1_kj=*/true);
       if (st == NNC_OK) exact = &plan32;
       else if (st != NNC_ERR_UNSUPPORTED) return st;
     }
   }
-  const int n_fast = fast ? o->iters - o->refine_iters : 0;
-  if (!exact && o->iters - n_fast > 0) NNC_TRY(sc.get(&b.P1s, (size_t)(m1 * N2 * N3)));
+  const int n_fast_max = fast ? o->iters - o->refine_iters : 0;
+  if (!exact && (o->iters - n_fast_max > 0 || trigger))
+    NNC_TRY(sc.get(&b.P1s, (size_t)(m1 * N2 * N3)));
+  ResidualWork<T> rw;
+  Checkpoints<T> ck;
+  if (o->exact_every > 0 && trace) {
+    NNC_TRY(residual_prepare<T>(3, dims, 0, m, 0, sc, &rw));
+    ck.every = o->exact_every;
+    ck.total = o->iters;
+    ck.X = X;
+    ck.dims = dims;
+    ck.m = m;
+    ck.rw = &rw;
+  }
   if constexpr (std::is_same<T, float>::value) {
     // The passes form the shares of Y1 when the shape allows it (both plans
     // see the same shape).
@@ -476,18 +549,25 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
     if (fast) NNC_TRY(fast->convert_b3(F[2], s));
     if (exact && !fast) NNC_TRY(exact->convert_b3(F[2], s));
   }
-  NNC_CUDA_TRY(cudaMemsetAsync(b.counter, 0, sizeof(int), s));
+  NNC_CUDA_TRY(cudaMemsetAsync(b.counter, 0, 2 * sizeof(int), s));
   NNC_CUDA_TRY(cudaMemsetAsync(b.done, 0, sizeof(int), s));
   NNC_CUDA_TRY(cudaMemsetAsync(b.gate, 0, sizeof(int), s));
 
-  NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, n_fast, fast, s));
+  int n_fast = 0;
+  ck.tol = trigger ? o->refine_tol : 0.0;
+  NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, n_fast_max, 0, &ck, fast, s, &n_fast));
   if (fast) NNC_TRY(fast->check(s));
+  if (refined_from) *refined_from = n_fast;
+  ck.tol = 0.0;
   if constexpr (std::is_same<T, float>::value) {
     // The FP32-accurate sweeps start from the factors the fast sweeps left.
     if (exact && fast && o->iters - n_fast > 0) NNC_TRY(exact->convert_b3(F[2], s));
   }
-  NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, o->iters - n_fast, exact, s));
+  int n_rest = 0;
+  NNC_TRY(run_sweeps<T>(X, F, G, b, o->eps, trace, o->iters - n_fast, n_fast, &ck, exact, s,
+                        &n_rest));
   if (exact) NNC_TRY(exact->check(s));
+  NNC_TRY(check_trace_finite(b.counter, s, "ntd_fit"));
 
   if (rel_err) {
     const T* fac[3] = {F[0], F[1], F[2]};
@@ -505,12 +585,13 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
 template <typename T>
 int ntd_fit3(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T* const* F, T* G,
              double* trace, double* rel_err, bool tensor_cores, cudaStream_t s) {
-  return ntd_fit3_impl<T>(X, dims, m, o, F, G, trace, rel_err, tensor_cores ? 1 : 0, s);
+  return ntd_fit3_impl<T>(X, dims, m, o, F, G, trace, rel_err, tensor_cores ? 1 : 0, nullptr, s);
 }
 
 int ntd_fit3_bf16(const float* X, const int64_t* dims, const int* m, const nnc_opts* o,
-                  float* const* F, float* G, double* trace, double* rel_err, cudaStream_t s) {
-  return ntd_fit3_impl<float>(X, dims, m, o, F, G, trace, rel_err, 2, s);
+                  float* const* F, float* G, double* trace, double* rel_err, int* refined_from,
+                  cudaStream_t s) {
+  return ntd_fit3_impl<float>(X, dims, m, o, F, G, trace, rel_err, 2, refined_from, s);
 }
 
 template int ntd_fit3<float>(const float*, const int64_t*, const int*, const nnc_opts*,

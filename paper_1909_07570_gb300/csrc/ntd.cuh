@@ -12,8 +12,10 @@ template <typename T>
 int ntd_fit3(const T* X, const int64_t* dims, const int* m, const nnc_opts* o, T* const* F, T* G,
              double* trace, double* rel_err, bool tensor_cores, cudaStream_t s);
 
-// NNC_BF16_REFINE path.
+// NNC_BF16_REFINE path; *refined_from (may be NULL) gets the index of the
+// first FP32 refinement sweep (iters when there was none).
 int ntd_fit3_bf16(const float* X, const int64_t* dims, const int* m, const nnc_opts* o,
-                  float* const* F, float* G, double* trace, double* rel_err, cudaStream_t s);
+                  float* const* F, float* G, double* trace, double* rel_err, int* refined_from,
+                  cudaStream_t s);
 
 }  // namespace nnc

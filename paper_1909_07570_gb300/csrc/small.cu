@@ -2,6 +2,8 @@
 // (numerators Num_n and the m_n x m_n matrices of the denominators), the
 // multiplicative updates with their nonnegativity projection, the FP64
 // residual identity and the one-pass statistics of X.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace nnc {
@@ -140,34 +142,69 @@ __global__ void identity_final_kernel(const double* __restrict__ part, int nb,
   if (threadIdx.x == 0) {
     const double xx = *x2;
     double r2 = xx - 2.0 * mg + gd;
+    const bool finite = isfinite(r2);
     if (r2 < 0.0) r2 = 0.0;
-    const int t = *counter;
-    trace[(int64_t)t * stride] = sqrt(r2 / xx);
-    *counter = t + 1;
+    trace_record(counter, trace, stride, sqrt(r2 / xx), finite);
   }
 }
 
 template <typename T>
 __global__ void tensor_stats_kernel(const T* __restrict__ X, int64_t n, double* part) {
   __shared__ double sh[32];
-  double s2 = 0.0, bad = 0.0, neg = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  double s2 = 0.0;
+  unsigned neg = 0, bad = 0;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  int64_t head = 0;  // elements handled by the vector loop
+  if constexpr (std::is_same<T, float>::value) {
+    // GB300's FP64 rate is far below its FP32 rate: the squares of each
+    // 8-element chunk (two 16-byte loads) are added in FP32, rounded to
+    // nearest, and only the chunk sums in FP64. The rounding errors are
+    // unbiased, so their sum over the tensor stays far below FP64's own.
+    if ((reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+      const float4* x4 = reinterpret_cast<const float4*>(X);
+      const int64_t nv = n / 8;
+      for (int64_t v = tid; v < nv; v += nth) {
+        const float4 a = x4[2 * v], b = x4[2 * v + 1];
+        const float e[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        float c = 0.f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const float x = e[t];
+          if (!(fabsf(x) <= 3.402823466e38f)) {
+            ++bad;
+          } else {
+            c = fmaf(x, x, c);
+            neg += x < 0.f;
+          }
+        }
+        if (c <= 3.402823466e38f) {
+          s2 += (double)c;
+        } else {  // the FP32 squares overflowed (entries beyond 1.8e19): FP64
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if (fabsf(e[t]) <= 3.402823466e38f) s2 += (double)e[t] * (double)e[t];
+        }
+      }
+      head = nv * 8;
+    }
+  }
+  for (int64_t i = head + tid; i < n; i += nth) {
     const double v = (double)X[i];
     if (!isfinite(v)) {
-      bad += 1.0;
+      ++bad;
     } else {
       s2 += v * v;
-      if (v < 0.0) neg += 1.0;
+      neg += v < 0.0;
     }
   }
   s2 = block_sum(s2, sh);
-  neg = block_sum(neg, sh);
-  bad = block_sum(bad, sh);
+  const double dneg = block_sum((double)neg, sh);
+  const double dbad = block_sum((double)bad, sh);
   if (threadIdx.x == 0) {
     part[3 * blockIdx.x + 0] = s2;
-    part[3 * blockIdx.x + 1] = neg;
-    part[3 * blockIdx.x + 2] = bad;
+    part[3 * blockIdx.x + 1] = dneg;
+    part[3 * blockIdx.x + 2] = dbad;
   }
 }
 

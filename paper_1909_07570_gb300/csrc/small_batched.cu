@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "autotune.cuh"
+#include "nncp.cuh"
 #include "small_batched.cuh"
 
 namespace nnc {
@@ -439,21 +440,20 @@ ntd_l2_kernel(const ntd_small_job* __restrict__ jobs, int iters, T eps, double* 
 // MT_n from two passes: T = X x_3 A3^T gives MT_1[i, q] = sum_j T[i, j, q]
 // A2[j, q] and MT_2[j, q] = sum_i T[i, j, q] A1[i, q] (new A1); T' = X x_1
 // A1^T gives MT_3[k, q] = sum_j T'[q, j, k] A2[j, q] (new A2).
-size_t cpx_l2_elems(const nncp_job& j) {
-  const size_t N1 = j.m[0], N2 = j.m[1], N3 = j.m[2], r = j.r;
-  const size_t t3 = N1 * N2 * r, t1 = r * N2 * N3;
-  size_t nmax = N1 > N2 ? N1 : N2;
-  nmax = nmax > N3 ? nmax : N3;
-  return (N1 + N2 + N3) * r + 3 * r * r + (t3 > t1 ? t3 : t1) + 2 * nmax * r + r * r;
-}
 
 template <typename T, int QM>
 __global__ void __launch_bounds__(kThreads, 2)
-cpx_l2_kernel(const nncp_job* __restrict__ jobs, int iters, T eps, double* rel_errs) {
+cpx_l2_kernel(const nncp_job* __restrict__ jobs, int iters, T eps, double* rel_errs,
+              int* statuses) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[2 * kFixedLanes];
   __shared__ double nrm[2];
   const nncp_job& jb = jobs[blockIdx.x];
+  // A job the host skipped (its shared memory was not sized for it).
+  if (!nncp_job_valid(jb) || jb.d != 3) {
+    if (statuses != nullptr && threadIdx.x == 0) statuses[blockIdx.x] = NNC_ERR_INVALID_ARG;
+    return;
+  }
   const int* N = jb.m;
   const int r = jb.r;
   const T* X = static_cast<const T*>(jb.G);
@@ -521,6 +521,16 @@ cpx_l2_kernel(const nncp_job* __restrict__ jobs, int iters, T eps, double* rel_e
   stream_residual(X, N[0] * N[1], N[2], Tb, A[2], r, red, nrm);
   if (threadIdx.x == 0 && rel_errs) rel_errs[blockIdx.x] = sqrt(nrm[0] / nrm[1]);
   for (int k = 0; k < 3; ++k) store(static_cast<T*>(jb.B[k]), A[k], N[k] * r);
+  if (statuses != nullptr) {
+    // NONFINITE when a NaN or an overflow shows in the factors or the sums.
+    bool finite = true;
+    for (int k = 0; k < 3; ++k)
+      for (int e = threadIdx.x; e < N[k] * r; e += blockDim.x) finite = finite && isfinite(A[k][e]);
+    const int ok = __syncthreads_and(finite ? 1 : 0);
+    if (threadIdx.x == 0)
+      statuses[blockIdx.x] =
+          (ok && isfinite(nrm[0]) && isfinite(nrm[1])) ? NNC_OK : NNC_ERR_NONFINITE;
+  }
 }
 
 size_t nmf_small_elems(const nmf_job& j) {
@@ -617,6 +627,15 @@ int upload(const Job* jobs, int n, Scratch& sc, Job** dev, cudaStream_t s) {
 
 }  // namespace
 
+// Shared-memory elements of one two-pass nnCP job (see cpx_l2_kernel).
+size_t cpx_l2_elems(const nncp_job& j) {
+  const size_t N1 = j.m[0], N2 = j.m[1], N3 = j.m[2], r = j.r;
+  const size_t t3 = N1 * N2 * r, t1 = r * N2 * N3;
+  size_t nmax = N1 > N2 ? N1 : N2;
+  nmax = nmax > N3 ? nmax : N3;
+  return (N1 + N2 + N3) * r + 3 * r * r + (t3 > t1 ? t3 : t1) + 2 * nmax * r + r * r;
+}
+
 template <typename T>
 int ntd_small_batched(int n_jobs, const ntd_small_job* jobs, int iters, double eps,
                       double* rel_errs, cudaStream_t s) {
@@ -643,7 +662,7 @@ int ntd_small_batched(int n_jobs, const ntd_small_job* jobs, int iters, double e
     }
     work = w * mm > work ? w * mm : work;
   }
-  if (smem <= 200 * 1024) {
+  if (smem <= kSmemBudget) {
     NNC_TRY(upload(jobs, n_jobs, sc, &dev, s));
     NNC_CUDA_TRY(raise_smem_limit((const void*)ntd_small_kernel<T>, smem));
     const TuneKey key{kTuneNtdSmall, (int)sizeof(T), size_class(work), size_class(n_jobs)};
@@ -664,7 +683,7 @@ int ntd_small_batched(int n_jobs, const ntd_small_job* jobs, int iters, double e
     for (int k = 0; k < 3; ++k) mmax = jobs[i].m[k] > mmax ? jobs[i].m[k] : mmax;
   }
   const size_t smem2 = l2 * sizeof(T);
-  if (smem2 > 200 * 1024 || mmax > 16) {
+  if (smem2 > kSmemBudget || mmax > 16) {
     set_error_detail_text("batched nnTD: a job's pass results or multirank exceed one block");
     return NNC_ERR_UNSUPPORTED;
   }
@@ -685,23 +704,13 @@ int ntd_small_batched(int n_jobs, const ntd_small_job* jobs, int iters, double e
 }
 
 template <typename T>
-bool nncp_l2_fits(int n_jobs, const nncp_job* jobs) {
-  size_t elems = 0;
-  for (int i = 0; i < n_jobs; ++i) {
-    if (jobs[i].d != 3 || jobs[i].r > 16) return false;
-    const size_t e = cpx_l2_elems(jobs[i]);
-    elems = e > elems ? e : elems;
-  }
-  return elems * sizeof(T) <= 200 * 1024;
-}
-
-template <typename T>
 int nncp_l2_batched(int n_jobs, const nncp_job* jobs, int iters, double eps, double* rel_errs,
-                    cudaStream_t s) {
+                    int* statuses, cudaStream_t s) {
   size_t elems = 0;
   int rmax = 0;
   for (int i = 0; i < n_jobs; ++i) {
     const nncp_job& j = jobs[i];
+    if (!nncp_job_valid(j)) continue;  // the kernel reports it in its status
     if (j.d != 3) {
       set_error_detail_text("batched nnCP: a 4-way job too large for shared memory");
       return NNC_ERR_UNSUPPORTED;
@@ -711,7 +720,7 @@ int nncp_l2_batched(int n_jobs, const nncp_job* jobs, int iters, double eps, dou
     rmax = j.r > rmax ? j.r : rmax;
   }
   const size_t smem = elems * sizeof(T);
-  if (smem > 200 * 1024 || rmax > 16) {
+  if (smem > kSmemBudget || rmax > 16) {
     set_error_detail_text("batched nnCP: a job's pass results or rank exceed one block");
     return NNC_ERR_UNSUPPORTED;
   }
@@ -722,16 +731,18 @@ int nncp_l2_batched(int n_jobs, const nncp_job* jobs, int iters, double eps, dou
   NNC_CUDA_TRY(raise_smem_limit(kern, smem));
   long long work = 1;
   for (int i = 0; i < n_jobs; ++i) {
+    if (!nncp_job_valid(jobs[i])) continue;
     const long long w = (long long)jobs[i].m[0] * jobs[i].m[1] * jobs[i].m[2] * jobs[i].r;
     work = w > work ? w : work;
   }
   const TuneKey key{kTuneCpxL2, (int)sizeof(T), size_class(work), size_class(n_jobs)};
   return run_tuned(key, iters, kThreads, s, [&](int threads, int sweeps, bool last) -> int {
     double* out = last ? rel_errs : nullptr;
+    int* st = last ? statuses : nullptr;
     if (rmax <= 8)
-      cpx_l2_kernel<T, 8><<<n_jobs, threads, smem, s>>>(dev, sweeps, (T)eps, out);
+      cpx_l2_kernel<T, 8><<<n_jobs, threads, smem, s>>>(dev, sweeps, (T)eps, out, st);
     else
-      cpx_l2_kernel<T, 16><<<n_jobs, threads, smem, s>>>(dev, sweeps, (T)eps, out);
+      cpx_l2_kernel<T, 16><<<n_jobs, threads, smem, s>>>(dev, sweeps, (T)eps, out, st);
     note_launch(s);
     NNC_CUDA_TRY(cudaGetLastError());
     return NNC_OK;
@@ -750,7 +761,7 @@ int nmf_small_batched(int n_jobs, const nmf_job* jobs, int iters, double eps, do
     elems = e > elems ? e : elems;
   }
   const size_t smem = elems * sizeof(T);
-  if (smem > 200 * 1024) return NNC_ERR_UNSUPPORTED;
+  if (smem > kSmemBudget) return NNC_ERR_UNSUPPORTED;
   Scratch sc(s);
   nmf_job* dev = nullptr;
   NNC_TRY(upload(jobs, n_jobs, sc, &dev, s));
@@ -783,7 +794,7 @@ int lifted_small_batched(int n_jobs, const lifted_job* jobs, double* rel_errs, c
     elems = e > elems ? e : elems;
   }
   const size_t smem = elems * sizeof(T);
-  if (smem > 200 * 1024) return NNC_ERR_UNSUPPORTED;
+  if (smem > kSmemBudget) return NNC_ERR_UNSUPPORTED;
   Scratch sc(s);
   lifted_job* dev = nullptr;
   NNC_TRY(upload(jobs, n_jobs, sc, &dev, s));
@@ -799,8 +810,8 @@ int lifted_small_batched(int n_jobs, const lifted_job* jobs, double* rel_errs, c
                                     cudaStream_t);                                          \
   template int nmf_small_batched<T>(int, const nmf_job*, int, double, double*, cudaStream_t); \
   template int lifted_small_batched<T>(int, const lifted_job*, double*, cudaStream_t);        \
-  template int nncp_l2_batched<T>(int, const nncp_job*, int, double, double*, cudaStream_t); \
-  template bool nncp_l2_fits<T>(int, const nncp_job*);
+  template int nncp_l2_batched<T>(int, const nncp_job*, int, double, double*, int*,         \
+                                  cudaStream_t);
 NNC_SMALL_INST(float)
 NNC_SMALL_INST(double)
 #undef NNC_SMALL_INST

@@ -56,9 +56,9 @@ __device__ __forceinline__ void write_operand(const UpdArgs<T>& a, int64_t r, in
     const int64_t idx = (int64_t)v * a.bt_ld + r;
     if (a.bt) a.bt[idx] = __float2bfloat16_rn(x);
     if (a.bhi) {
-      const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);  // exact TF32 part
-      // The remainder rounded to TF32, to nearest with ties away from zero (as
-      // the pass kernel rounds its operand splits).
+      // x rounded to TF32, and the remainder rounded to TF32, both to nearest
+      // with ties away from zero (the pass kernel's rule for its operand splits).
+      const float h = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
       a.bhi[idx] = h;
       a.blo[idx] = __uint_as_float((__float_as_uint(x - h) + 0x1000u) & 0xFFFFE000u);
     }
@@ -165,15 +165,20 @@ __host__ __device__ inline int gemm_groups(int mu, int mc) {
   const int g = kThreads / gemm_tiles(mu, mc);
   return g > 1 ? g : 1;
 }
-// Rows per chunk: one chunk of A and B takes at most 64 KB (FP32) or 24 KB
-// (FP64), a multiple of 8, and no more than the contraction length needs; a
-// contraction of up to 256 rows (FP32, m <= 32) is then staged in one round
-// trip into a single buffer, which keeps enough blocks resident per SM.
+// Rows per chunk: the staging buffers of A and B take at most 64 KB (FP32) or
+// 24 KB (FP64) in all, chunks are a multiple of 8 rows and no longer than the
+// contraction needs. A contraction of up to 256 rows (FP32, m <= 32) is staged
+// in one round trip into a single buffer; a longer one is double-buffered in
+// chunks of half that size, so that the staging of a block never exceeds the
+// budget and several blocks stay resident per SM (at 512 rows and m = 32 the
+// two 128-row buffers take 64 KB, three blocks per SM, where two 256-row
+// buffers took 128 KB and one).
 __host__ __device__ inline int gemm_kch(int mu, int mc, int elem, int len) {
-  const int budget = elem > 4 ? 3 * 1024 : 16 * 1024;  // elements of one chunk of A and B
+  const int budget = elem > 4 ? 3 * 1024 : 16 * 1024;  // elements of the staging buffers
   int k = budget / (r4(mu) + r4(mc));
   k = k > 256 ? 256 : k;
   const int need = (len + 7) & ~7;
+  if (need > k) k /= 2;  // two buffers share the budget
   k = k > need ? need : k;
   k &= ~7;
   return k < 8 ? 8 : k;
@@ -562,10 +567,9 @@ __global__ void __launch_bounds__(kThreads) core_b_kernel(CoreArgs<T> a) {
   if (threadIdx.x == 0) {
     const double xx = *a.x2;
     double r2 = xx - 2.0 * pm + pg;
+    const bool finite = isfinite(r2);
     if (r2 < 0.0) r2 = 0.0;
-    const int t = *a.counter;
-    a.trace[(int64_t)t * a.trace_stride] = sqrt(r2 / xx);
-    *a.counter = t + 1;
+    trace_record(a.counter, a.trace, a.trace_stride, sqrt(r2 / xx), finite);
     *a.done = 0;  // ready for the next sweep
     if (a.gate) *a.gate = 0;
   }

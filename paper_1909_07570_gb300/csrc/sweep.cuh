@@ -92,7 +92,7 @@ struct CoreArgs {
   const double* x2;
   double* trace;
   int trace_stride;
-  int* counter;
+  int* counter;         // trace_record pair: entries so far, first non-finite sweep
   int m1, m2, m3;
   double eps;
 };

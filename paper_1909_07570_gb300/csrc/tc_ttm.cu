@@ -7,12 +7,12 @@
 //           Since s_i is a power of two, bf16(x / s_i) s_i == bf16(x): the
 //           scales change no rounding. One BF16 MMA per K step, FP32 accumulate.
 //   TF32x3  FP32-accurate: X is read as FP32 and every operand is split into
-//           exact TF32 parts, x = x_hi + x_lo (x_hi: x with 13 low mantissa
-//           bits cleared; x_lo: x - x_hi rounded to TF32). Each K step issues
-//           two MMAs: x_hi [f_hi; f_lo] (N = 2 NP, the two B parts stacked) and
-//           x_lo f_hi (N = NP, into the f_hi half); the epilogue adds the two
-//           halves. The dropped x_lo f_lo term and the rounding of the lo parts
-//           are about 2^-21 of each product.
+//           exact TF32 parts, x = x_hi + x_lo (x_hi: x rounded to TF32; x_lo:
+//           x - x_hi rounded to TF32). Each K step issues two MMAs: x_hi
+//           [f_hi; f_lo] (N = 2 NP, the two B parts stacked) and x_lo f_hi
+//           (N = NP, into the f_lo half); the epilogue adds the two halves.
+//           The dropped x_lo f_lo term and the rounding of the lo parts are
+//           about 2^-22 of each product and of either sign.
 //
 // Pass 1, P3 = X x_3 F3^T: D[r, q] = sum_k A[r, k] B[q, k], r = (i, j), A K-major.
 // Pass 2, P1 = X x_1 F1^T: D[c, a] = sum_i A[c, i] B[a, i], c = (j, k). BF16:
@@ -182,9 +182,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// x_hi: x with the 13 low mantissa bits cleared (an exact TF32 value).
+// x_hi: x rounded to TF32 (10 stored mantissa bits), to nearest with ties away
+// from zero, by the integer rule of tf32_lo below. x - x_hi is then exact in
+// FP32 and takes either sign, so on nonnegative data the dropped x_lo f_lo
+// terms average out; with x_hi truncated every x_lo, and every dropped term,
+// would be nonnegative and the products biased low. Finite |x| below
+// (2 - 2^-11) 2^127.
 __device__ __forceinline__ float tf32_hi(float x) {
-  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 // The remainder x - x_hi rounded to TF32, to nearest with ties away from zero:
 // adding half of the dropped 13-bit field to the sign-magnitude bits and
@@ -203,9 +208,9 @@ struct TcLayout {
   // MMA; shorter chains shrink that bias by kAcc.
   static constexpr int kAcc = kTf32 ? 128 / NP : 1;
   static_assert((kAcc & (kAcc - 1)) == 0, "accumulator index is taken by a mask");
-  // TF32x3 accumulators are 2 NP columns wide: [0, NP) collects x_hi f_hi and
-  // x_lo f_hi, [NP, 2 NP) collects x_hi f_lo (one MMA of N = 2 NP against the
-  // stacked [f_hi; f_lo] operand).
+  // TF32x3 accumulators are 2 NP columns wide: [0, NP) collects the main term
+  // x_hi f_hi, [NP, 2 NP) the small terms x_hi f_lo (the same MMA of N = 2 NP
+  // against the stacked [f_hi; f_lo] operand) and x_lo f_hi (an MMA of N = NP).
   static constexpr int kAccCols = kTf32 ? 2 * NP : NP;
   static constexpr int kTmemCols = 2 * kAcc * kAccCols;  // double-buffered
   static constexpr int kKStage = kTf32 ? 32 : 64;        // K elements per stage (128 bytes)
@@ -410,9 +415,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const uint64_t bdesc = bdesc0 + (uint64_t)((kk * 32) >> 4);
             const uint32_t accum = (kc >= L::kAcc || kk != 0) ? 1u : 0u;
             if constexpr (L::kTf32) {
-              // x_hi [f_hi; f_lo] into columns [0, 2 NP), then x_lo f_hi into [0, NP).
+              // x_hi [f_hi; f_lo] into columns [0, 2 NP), then x_lo f_hi into
+              // [NP, 2 NP): the accumulator of the main term x_hi f_hi gets one
+              // truncating add per K step, the small terms share the other.
               mma<KIND>(acc, adesc, bdesc, idesc2, accum);
-              mma<KIND>(acc, lodesc0 + (uint64_t)((kk * 32) >> 4), bdesc, idesc, 1u);
+              mma<KIND>(acc + NP, lodesc0 + (uint64_t)((kk * 32) >> 4), bdesc, idesc, 1u);
             } else {
               mma<KIND>(acc, adesc, bdesc, idesc, accum);
             }

@@ -60,6 +60,12 @@ WORKLOADS = {
     "cp16_512x512x512_m32_bf16": Workload(
         "cp16_512x512x512_m32_bf16", (512, 512, 512), 16, (32, 32, 32), 16, 200, 200, "bf16",
         dist="exponential", noise=0.01, seed=1002, refine_iters=20),
+    # The precision workload under the paper's protocol: 5000 iterations per
+    # sub-solve without early stopping (Sec. 4.1); the last 200 nnTD sweeps
+    # are FP32 refinement sweeps.
+    "cp16_512x512x512_m32_bf16_5000": Workload(
+        "cp16_512x512x512_m32_bf16_5000", (512, 512, 512), 16, (32, 32, 32), 16, 5000, 5000,
+        "bf16", dist="exponential", noise=0.01, seed=1002, refine_iters=200),
     "cp12_128x128x128x64_m24_fp32": Workload(
         "cp12_128x128x128x64_m24_fp32", (128, 128, 128, 64), 12, (24, 24, 24, 16), 12, 300, 300,
         "f32", noise=0.01, seed=1004),

@@ -29,7 +29,8 @@ EXPORTED = ("ntd_fit", "ntd_fit_batched", "ntd_fit_small_batched", "nmf_fit_batc
             "nncp_tensor_fit", "nmf_fit", "candelinc_alg2",
             "nnc_status_string", "nnc_last_error_detail",
             "nnc_profile_enable", "nnc_profile_read", "nnc_kernel_launches",
-            "nnc_autotune_enable", "nnc_wait_selftest")
+            "nnc_autotune_enable", "nnc_wait_selftest", "nnc_debug_fail_alloc",
+            "nnc_last_refine_sweep")
 
 
 class NncError(RuntimeError):
@@ -39,7 +40,8 @@ class NncError(RuntimeError):
 
 
 class nnc_opts(ctypes.Structure):
-    _fields_ = [("iters", ctypes.c_int), ("refine_iters", ctypes.c_int), ("eps", ctypes.c_double)]
+    _fields_ = [("iters", ctypes.c_int), ("refine_iters", ctypes.c_int), ("eps", ctypes.c_double),
+                ("exact_every", ctypes.c_int), ("refine_tol", ctypes.c_double)]
 
 
 class ntd_job(ctypes.Structure):
@@ -89,7 +91,7 @@ def load(path: str | None = None):
     lib.nncp_core_fit.argtypes = [vp, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int,
                                   ctypes.POINTER(nnc_opts), vpp, dp, vp]
     lib.nncp_core_fit_batched.argtypes = [ctypes.c_int, ctypes.POINTER(nncp_job), ctypes.c_int,
-                                          ctypes.POINTER(nnc_opts), vp, vp]
+                                          ctypes.POINTER(nnc_opts), vp, vp, vp]
     lib.candelinc_lift.argtypes = [ctypes.c_int, i64p, ip, ctypes.c_int, ctypes.c_int, vpp, vpp,
                                    vpp, vp]
     lib.recon_residual.argtypes = [vp, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, ip,
@@ -137,6 +139,10 @@ def load(path: str | None = None):
     lib.nnc_autotune_enable.restype = ctypes.c_int
     lib.nnc_wait_selftest.argtypes = [ctypes.c_longlong, vp]
     lib.nnc_wait_selftest.restype = ctypes.c_int
+    lib.nnc_debug_fail_alloc.argtypes = [ctypes.c_int]
+    lib.nnc_debug_fail_alloc.restype = ctypes.c_int
+    lib.nnc_last_refine_sweep.argtypes = []
+    lib.nnc_last_refine_sweep.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -187,9 +193,11 @@ def _ptrs(ts):
 
 
 def ntd_fit(X, F, G, iters, precision=None, eps=1e-12, refine_iters=0, trace=True,
-            rel_err=True, stream=None):
+            rel_err=True, stream=None, exact_every=0, refine_tol=0.0):
     """nnTD of X in place on F (list of N_n x m_n) and G. Returns
-    (final relative error or None, per-sweep relative-error trace or None)."""
+    (final relative error or None, per-sweep relative-error trace or None).
+    exact_every / refine_tol: see nnc_opts (exact trace checkpoints, and the
+    switch from BF16 to FP32 sweeps when progress slows)."""
     code, dtype = _precision(X, precision)
     _require(X, dtype, "X")
     for n, f in enumerate(F):
@@ -199,7 +207,7 @@ def ntd_fit(X, F, G, iters, precision=None, eps=1e-12, refine_iters=0, trace=Tru
     m = [f.shape[1] for f in F]
     tr = torch.empty(max(iters, 1), dtype=torch.float64, device=X.device) if trace else None
     err = ctypes.c_double(float("nan"))
-    opts = nnc_opts(int(iters), int(refine_iters), float(eps))
+    opts = nnc_opts(int(iters), int(refine_iters), float(eps), int(exact_every), float(refine_tol))
     st = load().ntd_fit(_ptr(X), d, _i64(X.shape), _i32(m), code, ctypes.byref(opts), _ptrs(F),
                         _ptr(G), _ptr(tr) if trace else None,
                         ctypes.byref(err) if rel_err else None, _stream(stream))
@@ -321,10 +329,11 @@ def nncp_core_fit(G, B, iters, precision=None, eps=1e-12, rel_err=True, stream=N
 
 
 def nncp_core_fit_batched(problems, iters, precision=None, eps=1e-12, stream=None,
-                          _entry="nncp_core_fit_batched"):
+                          statuses=None, _entry="nncp_core_fit_batched"):
     """Many core fits in one launch. ``problems`` is a list of (G, [B^(n)]);
     every B is updated in place. Returns a float64 CUDA tensor of the final
-    relative errors."""
+    relative errors. ``statuses``, if given, is an int32 CUDA tensor of
+    len(problems) entries that receives each fit's status code."""
     if not problems:
         return None
     G0 = problems[0][0]
@@ -341,19 +350,25 @@ def nncp_core_fit_batched(problems, iters, precision=None, eps=1e-12, stream=Non
             j.m[n] = G.shape[n]
             j.B[n] = B[n].data_ptr()
     errs = torch.empty(len(problems), dtype=torch.float64, device=G0.device)
+    if statuses is not None:
+        _require(statuses, torch.int32, "statuses")
+        if statuses.numel() != len(problems):
+            raise ValueError("statuses must have one entry per problem")
     opts = nnc_opts(int(iters), 0, float(eps))
     st = getattr(load(), _entry)(len(problems), jobs, code, ctypes.byref(opts), _ptr(errs),
+                                 _ptr(statuses) if statuses is not None else None,
                                  _stream(stream))
     _check(_entry, st)
     return errs
 
 
-def nncp_core_fit_batched_noalloc(problems, iters, precision=None, eps=1e-12, stream=None):
+def nncp_core_fit_batched_noalloc(problems, iters, precision=None, eps=1e-12, stream=None,
+                                  statuses=None):
     """As nncp_core_fit_batched, through the entry point that allocates no
     device memory (its job table is a fixed array of 4096 descriptors inside the
     library). For callers whose memory manager forbids allocations by a
-    library."""
-    return nncp_core_fit_batched(problems, iters, precision, eps, stream,
+    library. Batches that need the two-pass kernel are refused (UNSUPPORTED)."""
+    return nncp_core_fit_batched(problems, iters, precision, eps, stream, statuses,
                                  _entry="nncp_core_fit_batched_noalloc")
 
 
@@ -532,6 +547,17 @@ def nnc_autotune_enable(on=True):
     """Switch the launch-shape autotuner of the batched fits; returns the
     previous setting."""
     return bool(load().nnc_autotune_enable(1 if on else 0))
+
+
+def nnc_last_refine_sweep():
+    """Sweep at which this thread's last BF16 ntd_fit began its FP32 sweeps."""
+    return int(load().nnc_last_refine_sweep())
+
+
+def nnc_debug_fail_alloc(nth):
+    """Test hook: make the nth scratch allocation from now fail on the host
+    (0 disarms). Returns the previous countdown."""
+    return int(load().nnc_debug_fail_alloc(int(nth)))
 
 
 def nnc_wait_selftest(cycles=2_000_000, stream=None):

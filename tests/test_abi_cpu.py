@@ -76,8 +76,9 @@ def test_argument_checks_need_no_gpu(lib):
 
 
 def test_tf32_rounding_bit_rule():
-    # The pass kernel rounds the remainder x - x_hi to TF32 by adding half of
-    # the 13 dropped bits to the sign-magnitude pattern and clearing them. Check
+    # The pass kernel rounds x to TF32 (its hi part), and the remainder x - x_hi
+    # too, by adding half of the 13 dropped bits to the sign-magnitude pattern
+    # and clearing them. Check
     # that rule against round-to-nearest, ties away from zero, on the TF32 grid
     # (10 stored mantissa bits), computed exactly in float64.
     rng = np.random.default_rng(7)
@@ -93,3 +94,14 @@ def test_tf32_rounding_bit_rule():
     q = xd / spacing
     ref = np.sign(q) * np.floor(np.abs(q) + 0.5) * spacing
     np.testing.assert_array_equal(got, ref)
+    # The split x = x_hi + x_lo with both parts so rounded: the remainder of
+    # x_hi is exact in float32 and takes both signs; x_hi + x_lo is within 2^-22
+    # of x (relative) for normal x.
+    xs = np.abs(x[np.abs(x) > 2.0 ** -100]).astype(np.float32)
+    hi = ((xs.view(np.uint32) + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+    rem = (xs - hi).astype(np.float32)
+    np.testing.assert_array_equal(rem.astype(np.float64), xs.astype(np.float64) - hi.astype(np.float64))
+    assert (rem > 0).any() and (rem < 0).any()
+    lo = ((rem.view(np.uint32) + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+    err = np.abs(hi.astype(np.float64) + lo.astype(np.float64) - xs.astype(np.float64))
+    assert np.all(err <= 2.0 ** -22 * xs.astype(np.float64))

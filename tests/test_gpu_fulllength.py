@@ -1,0 +1,135 @@
+"""Full-length parity: the workloads at their full sizes and sweep counts,
+through the C ABI in the configuration bench.py times, against FP64 oracle
+traces stored under tests/golden/ (written by tests/golden/make_traces.py,
+which calls only the oracle and the seeded input generator).
+
+The FP32 path (TF32x3 tensor-core passes) must stay within 1e-5 of the oracle's
+relative error on every sweep, the BF16 path with FP32 refinement within 1e-3.
+The oracle ran on X rounded to float32, the tensor the GPU computes on.
+
+What is compared is the relative reconstruction error of Sec. 4.1 (the per-sweep
+trace from the residual identity, the final value from one explicit FP64 pass)
+and, for the core and lifted fits, the final relative errors: the fits are
+local (multiplicative updates), the same initial factors and the same
+iteration count fix them, and a relative error is invariant under the scaling
+and permutation freedom the factors themselves have.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import _golden
+from paper_1909_07570_gb300 import inputs, native
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+FP32_TOL = 1e-5
+BF16_TOL = 1e-3
+
+
+def _golden_or_skip(name):
+    if not os.path.exists(os.path.join(_golden.HERE, name + ".txt")):
+        pytest.skip(f"tests/golden/{name}.txt not written yet")
+    return _golden.load(name + ".txt")
+
+
+def _t(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def _ntd(w, iters, precision, refine=0):
+    X64, _, F0, G0, B0 = inputs.make_problem(w)
+    X = _t(X64)
+    del X64
+    F = [_t(f) for f in F0]
+    G = _t(G0)
+    err, tr = native.ntd_fit(X, F, G, iters, precision=precision, refine_iters=refine,
+                             trace=True, rel_err=True)
+    return X, F, G, B0, err, tr.cpu().numpy()
+
+
+def test_ntd_256cube_500_sweeps_fp32_then_core_and_lift():
+    # The whole Alg. 1 step of the benchmark at its full length: 500 nnTD
+    # sweeps, 500 nnCP sweeps of the core, the lift and the lifted residual.
+    g = _golden_or_skip("ntd_cp10_256cube_500")
+    w = inputs.WORKLOADS["cp10_256x256x256_m20_fp32"]
+    X, F, G, B0, err, tr = _ntd(w, w.iters, "fp32")
+    assert tr.shape == g["trace"].shape
+    assert np.abs(tr - g["trace"]).max() <= FP32_TOL
+    assert abs(err - g["final_rel_err"][0]) <= FP32_TOL
+    B = [_t(b) for b in B0]
+    cerr = native.nncp_core_fit(G, B, w.cp_iters, precision="fp32")
+    assert abs(cerr - g["core_trace"][-1]) <= FP32_TOL
+    A = native.candelinc_lift(F, B)
+    rn, xn = native.recon_residual(X, A)
+    assert abs(rn / xn - g["lifted_rel_err"][0]) <= FP32_TOL
+
+
+@pytest.mark.parametrize("precision,refine,tol", [("fp32", 0, FP32_TOL), ("bf16", 20, BF16_TOL),
+                                                  ("bf16", 0, BF16_TOL)])
+def test_ntd_512cube_200_sweeps(precision, refine, tol):
+    # The precision workload at its sweep count: FP32 (TF32x3) passes, and the
+    # BF16 passes with the last 20 sweeps in FP32 (and without them).
+    g = _golden_or_skip("ntd_cp16_512cube_200")
+    w = inputs.WORKLOADS["cp16_512x512x512_m32_bf16"]
+    _, _, _, _, err, tr = _ntd(w, 200, precision, refine)
+    assert np.abs(tr - g["trace"]).max() <= tol
+    assert abs(err - g["final_rel_err"][0]) <= tol
+    if refine:
+        # The refinement sweeps are FP32-accurate: the last one lands within the
+        # FP32 bound of the oracle unless the BF16 sweeps moved the iterate.
+        assert abs(tr[-1] - g["trace"][-1]) <= tol
+
+
+def test_ntd_4way_300_sweeps_fp32():
+    g = _golden_or_skip("ntd4_cp12_128x128x128x64_300")
+    w = inputs.WORKLOADS["cp12_128x128x128x64_m24_fp32"]
+    _, _, _, _, err, tr = _ntd(w, w.iters, "fp32")
+    assert np.abs(tr - g["trace"]).max() <= FP32_TOL
+    assert abs(err - g["final_rel_err"][0]) <= FP32_TOL
+
+
+def test_pg_4way_300_steps_fp32():
+    # The differentiation form at its full length: 300 projected-gradient steps.
+    # Compared as relative errors sqrt(2 L / ||X||^2).
+    g = _golden_or_skip("pg_cp12_128x128x128x64_300")
+    w = inputs.WORKLOADS["cp12_128x128x128x64_m24_fp32"]
+    X64, _, F0, _, B0 = inputs.make_problem(w)
+    X = _t(X64)
+    del X64
+    F = [_t(f) for f in F0]
+    B = [_t(b) for b in B0]
+    loss, tr = native.candelinc_pg_fit(X, F, B, w.iters, precision="fp32")
+    x2 = g["x_norm_sq"][0]
+    rel = np.sqrt(2 * np.maximum(tr.cpu().numpy(), 0) / x2)
+    rel_o = np.sqrt(2 * np.maximum(g["loss"], 0) / x2)
+    assert np.abs(rel - rel_o).max() <= FP32_TOL
+    assert abs(np.sqrt(2 * loss / x2) - rel_o[-1]) <= FP32_TOL
+
+
+def test_batch_subset_500_sweeps_then_core_fits():
+    # Two tensors of the 64-tensor uneven batch through the batched calls:
+    # nnTD at m = 2r for 500 sweeps, then the core fits at CP ranks 2, 5, 8
+    # (restart 0) for 500 sweeps in one launch.
+    g = _golden_or_skip("batch64_subset")
+    Bc = inputs.BATCH
+    probs = inputs.batch_problems()[:2]
+    dev = [(_t(p["X"]), [_t(f) for f in p["F0"]], _t(p["G0"])) for p in probs]
+    errs, traces, sts = native.ntd_fit_batched(dev, Bc["iters"], precision="fp32")
+    assert sts == [0, 0]
+    jobs, keys = [], []
+    for b, (p, (_, _, G)) in enumerate(zip(probs, dev)):
+        assert np.abs(traces[b].cpu().numpy() - g[f"t{b}_trace"]).max() <= FP32_TOL
+        assert abs(errs[b] - g[f"t{b}_final_rel_err"][0]) <= FP32_TOL
+        inits = {(rk, rs): B0 for rk, rs, B0 in inputs.batch_core_inits(p["m"], b)}
+        for rk in (2, 5, 8):
+            jobs.append((G, [_t(x) for x in inits[(rk, 0)]]))
+            keys.append(f"t{b}_core_r{rk}_rel_err")
+    st = torch.full((len(jobs),), 99, dtype=torch.int32, device=DEV)
+    cerr = native.nncp_core_fit_batched(jobs, Bc["cp_iters"], precision="fp32", statuses=st)
+    assert (st.cpu().numpy() == 0).all()
+    for e, k in zip(cerr.cpu().numpy(), keys):
+        assert abs(e - g[k][0]) <= FP32_TOL, k

@@ -9,6 +9,8 @@ allocating entry point returns on the same problems, and that an oversized
 batch is refused. It is collected last so that a stop at the first failure has
 run every other test first; it passes alone in a fresh process as well.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -61,3 +63,42 @@ def test_noalloc_rejects_more_jobs_than_its_table():
         native.nncp_core_fit_batched_noalloc([(G, B)] * 4097, 2)
     assert ei.value.status == -1
     assert "4096" in str(ei.value)
+
+
+def test_noalloc_refuses_batches_for_the_two_pass_kernel():
+    # A 40 x 40 x 40 tensor (64,000 entries) sends the allocating call to its
+    # two-pass kernel; the no-alloc entry refuses the batch instead of running
+    # another kernel, and says why.
+    G = torch.rand(40, 40, 40, device="cuda")
+    B = [torch.rand(40, 3, device="cuda") for _ in range(3)]
+    with pytest.raises(native.NncError) as ei:
+        native.nncp_core_fit_batched_noalloc([(G, B)], 5)
+    assert ei.value.status == -6
+    assert "two-pass" in str(ei.value)
+    # The same batch runs through the allocating entry point.
+    native.nncp_core_fit_batched([(G, B)], 5)
+
+
+def test_noalloc_checks_options_and_clears_the_error_detail():
+    G = torch.rand(4, 5, 3, device="cuda")
+    B = [torch.rand(n, 2, device="cuda") for n in (4, 5, 3)]
+    lib = native.load()
+    jobs = (native.nncp_job * 1)()
+    jobs[0].G, jobs[0].d, jobs[0].r = G.data_ptr(), 3, 2
+    for n in range(3):
+        jobs[0].m[n] = G.shape[n]
+        jobs[0].B[n] = B[n].data_ptr()
+    errs = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = torch.empty(1, dtype=torch.int32, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    bad = native.nnc_opts(3, 4, 1e-12)  # refine_iters > iters, as the allocating call rejects
+    for entry in ("nncp_core_fit_batched", "nncp_core_fit_batched_noalloc"):
+        assert getattr(lib, entry)(1, jobs, native.NNC_FP32, ctypes.byref(bad),
+                                   ctypes.c_void_p(errs.data_ptr()), None, stream) == -1
+    assert lib.nnc_last_error_detail() != b""
+    good = native.nnc_opts(3, 0, 1e-12)
+    assert lib.nncp_core_fit_batched_noalloc(1, jobs, native.NNC_FP32, ctypes.byref(good),
+                                             ctypes.c_void_p(errs.data_ptr()),
+                                             ctypes.c_void_p(st.data_ptr()), stream) == 0
+    assert lib.nnc_last_error_detail() == b""
+    assert int(st.item()) == 0
