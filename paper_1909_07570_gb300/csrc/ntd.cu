@@ -499,6 +499,11 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   if constexpr (std::is_same<T, float>::value) {
     if (passes == 2 && o->iters > o->refine_iters) {
       NNC_TRY(plan16.init(tc::kKindBf16, X, N1, N2, N3, m1, m3, sc, s, /*p1_kj=*/true));
+      // The BF16 passes stream X about twice as fast as the TF32x3 ones and
+      // the small kernels beside them would otherwise hold SMs the pass
+      // waits for: they leave 32 SMs to them (measured at 512^3, m = 32: 258
+      // -> 225 us per sweep; the TF32x3 sweep is fastest with every SM).
+      plan16.reserve_sms = 32;
       fast = &plan16;
     }
     if (passes >= 1 && (passes == 1 || o->refine_iters > 0 || trigger)) {
@@ -522,8 +527,8 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
     ck.rw = &rw;
   }
   if constexpr (std::is_same<T, float>::value) {
-    // The passes form the shares of Y1 when the shape allows it (both plans
-    // see the same shape).
+    // The TF32x3 passes form the shares of Y1 when the shape allows it (see
+    // y1_fusable; the BF16 passes leave Y1 to the update kernel).
     const tc::TcPlan* any = exact ? exact : fast;
     if (any && any->y1_fusable(m2)) {
       b.y_nh = (int)(N2 / 128);

@@ -282,24 +282,65 @@ __device__ __noinline__ void smem_gemm(const T* A, const T* B, T* C, int m, int 
   }
 }
 
-// out[q] = <x, Y[q, :]> for q < nq (rows of length n, row stride n); a warp per q.
+// out0[q] = <x0, Y[q, :]> (and out1[q] = <x1, Y[q, :]> when x1 is given) for
+// q < nq: rows of length n, row stride n; x0, x1 in shared memory, Y in
+// global or shared memory. NS = 8 threads (4 when nq > 32) share a row, so the
+// block reads every Y row with many independent loads in flight (a warp per
+// row, a few loads at a time, left the loop waiting on the latency of the
+// core's reads from L2); thread s of a row takes the 4-element vectors
+// s, s + NS, ... (16-byte loads when Y's rows are 16-byte aligned), and the
+// NS partial sums are added by a fixed shuffle tree.
 template <typename T>
-__device__ __noinline__ void rows_dot(const T* x, const T* Y, int n, int nq, T* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = warp; q < nq; q += nw) {
-    const T* y = Y + (int64_t)q * n;
-    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-    int e = lane;
-    for (; e + 96 < n; e += 128) {
-      s0 = fma(x[e], y[e], s0);
-      s1 = fma(x[e + 32], y[e + 32], s1);
-      s2 = fma(x[e + 64], y[e + 64], s2);
-      s3 = fma(x[e + 96], y[e + 96], s3);
+__device__ __noinline__ void rows_dot2(const T* x0, const T* x1, const T* Y, int n, int nq,
+                                       T* out0, T* out1) {
+  const int NS = nq > 32 ? 4 : 8;
+  const int per = blockDim.x / NS;  // rows at a time
+  const int s = threadIdx.x % NS;
+  const bool vec = (n & 3) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+  for (int q0 = 0; q0 < nq; q0 += per) {
+    const int q = q0 + threadIdx.x / NS;
+    T a0 = T(0), a1 = T(0);
+    if (q < nq) {
+      const T* y = Y + (int64_t)q * n;
+      if (vec) {
+        const int nv = n >> 2;
+#pragma unroll 8
+        for (int v = s; v < nv; v += NS) {
+          T yv[4], xv[4];
+          // Generic loads: Y may be a shared-memory copy of the core.
+          ld4(y + 4 * v, yv);
+          ld4(x0 + 4 * v, xv);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a0 = fma(xv[i], yv[i], a0);
+          if (x1) {
+            ld4(x1 + 4 * v, xv);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a1 = fma(xv[i], yv[i], a1);
+          }
+        }
+      } else {
+        for (int e = s; e < n; e += NS) {
+          const T yy = y[e];
+          a0 = fma(x0[e], yy, a0);
+          if (x1) a1 = fma(x1[e], yy, a1);
+        }
+      }
     }
-    for (; e < n; e += 32) s0 = fma(x[e], y[e], s0);
-    const T v = warp_sum((s0 + s1) + (s2 + s3));
-    if (lane == 0) out[q] = v;
+    // The NS threads of a row are consecutive lanes of one warp.
+    for (int o = NS / 2; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    }
+    if (q < nq && s == 0) {
+      out0[q] = a0;
+      if (x1) out1[q] = a1;
+    }
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void rows_dot(const T* x, const T* Y, int n, int nq, T* out) {
+  rows_dot2<T>(x, nullptr, Y, n, nq, out, nullptr);
 }
 
 // Largest core copy kept in shared memory by the kernels that dot against G.
@@ -375,6 +416,265 @@ __global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
     write_operand(a, r, v, nv);
   }
   if (a.gate_out && r == 0 && threadIdx.x == 0) *a.gate_out = 1;
+}
+
+// ---------------------------------------------------------------------------
+// updm: the update of upd12 for R rows per block, the GEMMs staged by a
+// three-deep cp.async ring shared by the R rows. One operand of the GEMM (the
+// factor Fc) is the same for every row: it is staged once per chunk for all R
+// rows. Each thread owns a TW x TW register tile of one row's Y_r (8 x 8 in
+// FP32: 64 FMAs per four 16-byte shared loads, so the FMA pipe rather than
+// the issue of loads and addresses bounds the GEMM); the contraction is split
+// over thread groups (a warp each in the common case) whose partial tiles are
+// added in group order. Then every warp forms the numerators of its core rows
+// for all R rows at once (each core row read once per block, many loads in
+// flight per thread, rows_dot2), and the MU step follows (or, num_only, the
+// numerators are stored).
+// ---------------------------------------------------------------------------
+constexpr int kUpdmStages = 3;
+constexpr int kUpdmRingBytes = 96 * 1024;
+
+template <typename T>
+struct Updm {
+  static constexpr int TW = sizeof(T) == 4 ? 8 : 4;  // register tile edge
+  static __host__ __device__ int pad(int m) { return (m + TW - 1) / TW * TW; }
+  static __host__ __device__ int tiles_row(int mu, int mc) { return (pad(mu) / TW) * (pad(mc) / TW); }
+  static __host__ __device__ int rows(int mu, int mc) {
+    return 2 * tiles_row(mu, mc) <= kThreads / 2 ? 2 : 1;
+  }
+  // Elements of one staged contraction row: the shared operand once, the
+  // per-row operand R times (the c side, B = P_r, unless p_first, when it is
+  // the u side, A = P_r).
+  static __host__ __device__ int row_elems(int mu, int mc, int R, int p_first) {
+    return pad(mu) + pad(mc) + (R - 1) * (p_first ? pad(mu) : pad(mc));
+  }
+  // Contraction rows per stage: 64, or fewer (a multiple of 8) so that the
+  // ring stays within kUpdmRingBytes.
+  static __host__ __device__ int chunk(int mu, int mc, int R, int p_first) {
+    int k = kUpdmRingBytes / (kUpdmStages * row_elems(mu, mc, R, p_first) * (int)sizeof(T));
+    k = k > 64 ? 64 : k;
+    k &= ~7;
+    return k < 8 ? 8 : k;
+  }
+  static __host__ __device__ int groups(int mu, int mc, int R) {
+    const int g = kThreads / (R * tiles_row(mu, mc));
+    return g > 1 ? g : 1;
+  }
+  // Shared-memory elements: the ring (or the group partials, if larger), Y of
+  // the R rows, H, and the old rows and numerators.
+  static __host__ __device__ size_t stage_elems(int mu, int mc, int mv, int p_first, size_t* ring_out) {
+    const int R = rows(mu, mc);
+    const size_t ring = (size_t)kUpdmStages * chunk(mu, mc, R, p_first) * row_elems(mu, mc, R, p_first);
+    const size_t red = (size_t)groups(mu, mc, R) * R * mu * (mc + 1);
+    const size_t st = al4(ring > red ? ring : red);
+    if (ring_out) *ring_out = st;
+    return st + al4((size_t)R * mu * mc) + al4((size_t)mv * mv) + 2 * al4((size_t)R * mv);
+  }
+};
+
+// Loads TW consecutive values (16-byte aligned) from shared memory.
+template <int TW, typename T>
+__device__ __forceinline__ void ldw(const T* p, T (&v)[TW]) {
+#pragma unroll
+  for (int i = 0; i < TW; i += 4) {
+    T t[4];
+    ld4(p + i, t);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[i + j] = t[j];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) updm_kernel(UpdArgs<T> a) {
+  using U = Updm<T>;
+  constexpr int TW = U::TW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int MU_ = a.mu, MC = a.mc, MV = a.mv, UC = MU_ * MC;
+  const int mup = U::pad(MU_), mcp = U::pad(MC);
+  const int R = U::rows(MU_, MC);
+  const int KC = U::chunk(MU_, MC, R, a.p_first);
+  const int per = KC * U::row_elems(MU_, MC, R, a.p_first);
+  const int tqc = mcp / TW, tiles_row = (mup / TW) * tqc, tiles = R * tiles_row;
+  const int groups = U::groups(MU_, MC, R);
+  size_t ring = 0;
+  U::stage_elems(MU_, MC, MV, a.p_first, &ring);
+  T* stage = sm;
+  T* ys = stage + ring;                         // R x UC
+  T* hs = ys + al4((size_t)R * UC);
+  T* fo = hs + al4(MV * MV);                    // R x MV old rows
+  T* nm = fo + al4((size_t)R * MV);             // R x MV numerators
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int rn = (int)min((int64_t)R, a.nrows - r0);
+  pdl_trigger();  // as in upd12
+
+  // The row operand is P (rows of P_r) and the shared one Fc; in the chunk
+  // buffers the u-side operand (A) comes first, then the c-side one (B).
+  const bool a_shared = !a.p_first;  // Y = Fc^T P_r: A = Fc shared, B = P_r per row
+  const int64_t lda = a_shared ? MU_ : a.pstride, ldb = a_shared ? a.pstride : MC;
+  const bool vecP = aligned16(a.P, a.pstride, sizeof(T)) && ((a.prow * sizeof(T)) & 15) == 0;
+  const bool vecF = aligned16(a.Fc, a_shared ? MU_ : MC, sizeof(T));
+  const int na = a_shared ? 1 : R, nb = a_shared ? R : 1;
+  const int nch = (a.len + KC - 1) / KC;
+  // 16-byte staging: this thread's first vector (row, column) of a chunk and
+  // its stride, formed once (the divisions would otherwise be redone for
+  // every chunk and operand).
+  constexpr int W = 16 / (int)sizeof(T);
+  const int vpa = mup / W, vpb = mcp / W;
+  const int ra0 = threadIdx.x / vpa, ca0 = (threadIdx.x % vpa) * W;
+  const int dra = blockDim.x / vpa, dca = (blockDim.x % vpa) * W;
+  const int rb0 = threadIdx.x / vpb, cb0 = (threadIdx.x % vpb) * W;
+  const int drb = blockDim.x / vpb, dcb = (blockDim.x % vpb) * W;
+  // Offsets within a chunk in 32 bits (used when KC row strides fit).
+  auto stage_fast = [&](T* dst, int lds, const T* src, int64_t ldg, int tn, int vrows, int vcols,
+                        int r, int cc, int dr, int dc) {
+    const int nv = tn * (lds / W);
+    const int ldg32 = (int)ldg;
+    int so = r * ldg32 + cc, doff = r * lds + cc;
+    const int dso = dr * ldg32 + dc, ddo = dr * lds + dc;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      int valid = r < vrows ? vcols - cc : 0;
+      valid = valid < 0 ? 0 : (valid > W ? W : valid);
+      cp_vec(dst + doff, valid ? src + so : src, valid);
+      r += dr;
+      cc += dc;
+      so += dso;
+      doff += ddo;
+      if (cc >= lds) {
+        cc -= lds;
+        ++r;
+        so += ldg32 - lds;  // (the shared offset needs no correction: its rows are lds long)
+      }
+    }
+  };
+  auto issue = [&](int c) {
+    T* st = stage + (c % kUpdmStages) * per;
+    const int t0 = c * KC, tn = min(KC, a.len - t0);
+    for (int i = 0; i < na; ++i) {
+      const T* src = a_shared ? a.Fc : a.P + (r0 + (i < rn ? i : 0)) * a.prow;
+      const bool vec = a_shared ? vecF : vecP;
+      const int vr = i < rn || a_shared ? tn : 0;
+      if (vec && (mup % W) == 0 && lda * KC < (1LL << 31))
+        stage_fast(st + i * KC * mup, mup, src + (int64_t)t0 * lda, lda, tn, vr, MU_, ra0, ca0,
+                   dra, dca);
+      else
+        stage_tile(st + i * KC * mup, mup, src + (int64_t)t0 * lda, lda, tn, mup, vr, MU_, vec);
+    }
+    T* sb = st + na * KC * mup;
+    for (int i = 0; i < nb; ++i) {
+      const T* src = a_shared ? a.P + (r0 + (i < rn ? i : 0)) * a.prow : a.Fc;
+      const bool vec = a_shared ? vecP : vecF;
+      const int vr = i < rn || !a_shared ? tn : 0;
+      if (vec && (mcp % W) == 0 && ldb * KC < (1LL << 31))
+        stage_fast(sb + i * KC * mcp, mcp, src + (int64_t)t0 * ldb, ldb, tn, vr, MC, rb0, cb0,
+                   drb, dcb);
+      else
+        stage_tile(sb + i * KC * mcp, mcp, src + (int64_t)t0 * ldb, ldb, tn, mcp, vr, MC, vec);
+    }
+    cp_commit();
+  };
+  // Everything but the GEMM operands is requested first; the first wait
+  // covers it.
+  if (!a.num_only) {
+    cp_flat(hs, a.H, MV * MV);
+    cp_flat(fo, a.F + r0 * MV, (int64_t)rn * MV);
+  }
+  cp_commit();
+  for (int c = 0; c < kUpdmStages - 1; ++c) {
+    if (c < nch) issue(c);
+    else cp_commit();  // empty groups keep the wait count uniform
+  }
+  const int g = threadIdx.x / tiles, tl = threadIdx.x % tiles;
+  const bool act = g < groups;
+  const int ri = tl / tiles_row, tt = tl % tiles_row;
+  const int u0 = (tt / tqc) * TW, c0 = (tt % tqc) * TW;
+  T acc[TW][TW];
+#pragma unroll
+  for (int i = 0; i < TW; ++i)
+#pragma unroll
+    for (int j = 0; j < TW; ++j) acc[i][j] = T(0);
+  for (int c = 0; c < nch; ++c) {
+    if (c + kUpdmStages - 1 < nch) issue(c + kUpdmStages - 1);
+    else cp_commit();
+    cp_wait<kUpdmStages - 1>();
+    __syncthreads();
+    if (act) {
+      const T* st = stage + (c % kUpdmStages) * per;
+      const T* A = st + (a_shared ? 0 : ri * KC * mup) + u0;
+      const T* B = st + na * KC * mup + (a_shared ? ri * KC * mcp : 0) + c0;
+      const int kn = min(KC, a.len - c * KC);
+      // One k at a time: TW x TW independent accumulators already hide the
+      // FMA latency, and the registers stay free for them.
+#pragma unroll 1
+      for (int k = g; k < kn; k += groups) {
+        T x[TW], y[TW];
+        ldw<TW>(A + k * mup, x);
+        ldw<TW>(B + k * mcp, y);
+#pragma unroll
+        for (int i = 0; i < TW; ++i)
+#pragma unroll
+          for (int j = 0; j < TW; ++j) acc[i][j] = fma(x[i], y[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+  cp_wait<0>();
+  __syncthreads();
+  // The group partials, rows padded to MC + 1 so that the threads of a warp
+  // (tiles TW rows apart) store to different banks.
+  T* red = stage;  // the ring is free after the last barrier
+  const int ldr = MC + 1, plane = MU_ * ldr;
+  if (act) {
+#pragma unroll
+    for (int i = 0; i < TW; ++i)
+#pragma unroll
+      for (int j = 0; j < TW; ++j)
+        if (u0 + i < MU_ && c0 + j < MC)
+          red[((size_t)g * R + ri) * plane + (u0 + i) * ldr + c0 + j] = acc[i][j];
+  }
+  __syncthreads();
+  {
+    // e = (i, u, cc) walked by increments (no division per entry).
+    int i = threadIdx.x / UC, u = (threadIdx.x % UC) / MC, cc = threadIdx.x % MC;
+    const int di = blockDim.x / UC, du = (blockDim.x % UC) / MC, dc = blockDim.x % MC;
+    for (int e = threadIdx.x; e < R * UC; e += blockDim.x) {
+      T v = T(0);
+      for (int q = 0; q < groups; ++q) v += red[((size_t)q * R + i) * plane + u * ldr + cc];
+      ys[e] = v;
+      i += di;
+      u += du;
+      cc += dc;
+      if (cc >= MC) {
+        cc -= MC;
+        ++u;
+      }
+      if (u >= MU_) {
+        u -= MU_;
+        ++i;
+      }
+    }
+  }
+  __syncthreads();
+  if (a.Yout)
+    for (int e = threadIdx.x; e < rn * UC; e += blockDim.x) a.Yout[r0 * UC + e] = ys[e];
+  // Numerators of the R rows, each core row read once for the block.
+  if (a.num_only) {
+    rows_dot2<T>(ys, R > 1 ? ys + UC : nullptr, a.Gn, UC, MV, nm, nm + MV);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rn * MV; e += blockDim.x) a.num[r0 * MV + e] = nm[e];
+    return;
+  }
+  rows_dot2<T>(ys, R > 1 ? ys + UC : nullptr, a.Gn, UC, MV, nm, nm + MV);
+  __syncthreads();
+  for (int e = threadIdx.x; e < rn * MV; e += blockDim.x) {
+    const int i = e / MV, v = e % MV;
+    T den = T(0);
+    for (int w = 0; w < MV; ++w) den = fma(fo[i * MV + w], hs[w * MV + v], den);
+    const T nv = mu_step(fo[e], nm[e], den, (T)a.eps);
+    a.F[(r0 + i) * MV + v] = nv;
+    write_operand(a, r0 + i, v, nv);
+  }
+  if (a.gate_out && r0 == 0 && threadIdx.x == 0) *a.gate_out = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -637,6 +937,16 @@ template <typename T>
 int launch_upd12(const UpdArgs<T>& a, cudaStream_t s) {
   if (a.mu > 64 || a.mc > 64 || a.mv > 64) return NNC_ERR_UNSUPPORTED;
   const int UC = a.mu * a.mc;
+  if (!a.Ypart) {
+    // The GEMM form: R rows per block (updm_kernel).
+    const int R = Updm<T>::rows(a.mu, a.mc);
+    const size_t smem = sizeof(T) * Updm<T>::stage_elems(a.mu, a.mc, a.mv, a.p_first, nullptr);
+    NNC_TRY(set_smem(updm_kernel<T>, smem));
+    updm_kernel<T><<<(unsigned)ceil_div(a.nrows, (int64_t)R), kThreads, smem, s>>>(a);
+    note_launch(s);
+    NNC_CUDA_TRY(cudaGetLastError());
+    return NNC_OK;
+  }
   const size_t st = a.Ypart ? 0 : gemm_stage_elems(a.mu, a.mc, (int)sizeof(T), a.len);
   const size_t smem =
       sizeof(T) * (st + al4(UC) + al4(a.mv * a.mv) + 2 * al4(a.mv) +

@@ -805,13 +805,16 @@ int make_map(CUtensorMap* tm, CUtensorMapDataType dt, const void* base, uint64_t
 
 template <int KIND, bool kMN, int NP, bool FUSE>
 int launch_pass(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& blo, int nk,
-                int64_t tiles, const TcEpilogue& ep, int* err, cudaStream_t s) {
+                int64_t tiles, const TcEpilogue& ep, int* err, int reserve, cudaStream_t s) {
   constexpr int smem = TcLayout<KIND, NP, FUSE>::kSmem;
   NNC_CUDA_TRY(raise_smem_limit((const void*)tc_pass_kernel<KIND, kMN, NP, FUSE>, smem));
-  // Fewest CTAs that keep the largest tile count per CTA of a full-GPU grid:
-  // the time is the same, and the SMs left over run the small kernels of the
-  // sweep that the graph places beside the pass.
-  const int64_t per = ceil_div(tiles, (int64_t)device_sm_count());
+  // Fewest CTAs that keep the largest tile count per CTA of a grid over the
+  // SMs the pass may take: the time is the same, and the SMs left over run
+  // the small kernels of the sweep that the graph places beside the pass.
+  // With at least 8 tiles per SM the pass leaves `reserve` SMs to them.
+  const int sms = device_sm_count();
+  const int avail = (tiles >= 8LL * sms && reserve > 0 && reserve < sms / 2) ? sms - reserve : sms;
+  const int64_t per = ceil_div(tiles, (int64_t)avail);
   const int64_t grid = ceil_div(tiles, per);
   NNC_CUDA_TRY(launch_pdl(tc_pass_kernel<KIND, kMN, NP, FUSE>, dim3(static_cast<unsigned>(grid)),
                           dim3(kThreadsTc), smem, s, a, b, blo, nk, tiles, ep, err));
@@ -821,12 +824,13 @@ int launch_pass(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& b
 
 template <int KIND, bool kMN>
 int launch_np(int np, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& blo, int nk,
-              int64_t tiles, const TcEpilogue& ep, int* err, cudaStream_t s) {
+              int64_t tiles, const TcEpilogue& ep, int* err, int reserve, cudaStream_t s) {
   if constexpr (!kMN) {
-    if (ep.ysh) return launch_pass<KIND, kMN, 32, true>(a, b, blo, nk, tiles, ep, err, s);
+    if (ep.ysh)
+      return launch_pass<KIND, kMN, 32, true>(a, b, blo, nk, tiles, ep, err, reserve, s);
   }
-  if (np == 32) return launch_pass<KIND, kMN, 32, false>(a, b, blo, nk, tiles, ep, err, s);
-  return launch_pass<KIND, kMN, 64, false>(a, b, blo, nk, tiles, ep, err, s);
+  if (np == 32) return launch_pass<KIND, kMN, 32, false>(a, b, blo, nk, tiles, ep, err, reserve, s);
+  return launch_pass<KIND, kMN, 64, false>(a, b, blo, nk, tiles, ep, err, reserve, s);
 }
 
 }  // namespace
@@ -935,7 +939,11 @@ int TcPlan::convert_b1(const float* F1, cudaStream_t s) const {
 }
 
 bool TcPlan::y1_fusable(int m2) const {
-  return np3 == 32 && m2 >= 1 && m2 <= 32 && N2 % 128 == 0;
+  // The TF32x3 pass has time for the tile contraction in its epilogue (its
+  // stage rate is set by the split and the MMAs); the BF16 pass streams X
+  // about twice as fast and the contraction would hold it back (measured 79
+  // against 49 us at 512^3, m = 32), so BF16 leaves Y1 to the update kernel.
+  return kind == kKindTf32x3 && np3 == 32 && m2 >= 1 && m2 <= 32 && N2 % 128 == 0;
 }
 
 bool TcPlan::y3_fusable(int m2) const {
@@ -964,8 +972,10 @@ int TcPlan::pass3(const float* F3, float* P3, cudaStream_t s, bool convert, cons
   const int stagek = kind == kKindBf16 ? 64 : 32;
   const int nk = static_cast<int>(ceil_div(N3, stagek));
   if (kind == kKindBf16)
-    return launch_np<kKindBf16, false>(np3, mapA3, mapB3, mapB3lo, nk, tiles, ep, err, s);
-  return launch_np<kKindTf32x3, false>(np3, mapA3, mapB3, mapB3lo, nk, tiles, ep, err, s);
+    return launch_np<kKindBf16, false>(np3, mapA3, mapB3, mapB3lo, nk, tiles, ep, err,
+                                       reserve_sms, s);
+  return launch_np<kKindTf32x3, false>(np3, mapA3, mapB3, mapB3lo, nk, tiles, ep, err,
+                                       reserve_sms, s);
 }
 
 int TcPlan::pass1(const float* F1, float* P1, cudaStream_t s, bool convert, const float* F2,
@@ -998,8 +1008,10 @@ int TcPlan::pass1(const float* F1, float* P1, cudaStream_t s, bool convert, cons
   const int stagek = kind == kKindBf16 ? 64 : 32;
   const int nk = static_cast<int>(ceil_div(N1, stagek));
   if (kind == kKindBf16)
-    return launch_np<kKindBf16, true>(np1, mapA1, mapB1, mapB1lo, nk, tiles, ep, err, s);
-  return launch_np<kKindTf32x3, false>(np1, mapA1, mapB1, mapB1lo, nk, tiles, ep, err, s);
+    return launch_np<kKindBf16, true>(np1, mapA1, mapB1, mapB1lo, nk, tiles, ep, err,
+                                      reserve_sms, s);
+  return launch_np<kKindTf32x3, false>(np1, mapA1, mapB1, mapB1lo, nk, tiles, ep, err,
+                                       reserve_sms, s);
 }
 
 // Self-test of the bounded waits: one CTA waits, with a limit of `cycles`, on

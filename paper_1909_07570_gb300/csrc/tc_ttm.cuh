@@ -61,6 +61,9 @@ struct TcPlan {
   float *B1hi = nullptr, *B1lo = nullptr, *B3hi = nullptr, *B3lo = nullptr, *Xt = nullptr;
   float *scale = nullptr, *inv_scale = nullptr;
   int* err = nullptr;
+  // SMs a pass of at least 8 tiles per SM leaves to kernels that run beside
+  // it (the nnTD sweep's small kernels); 0: every SM.
+  int reserve_sms = 0;
   CUtensorMap mapA3, mapB3, mapB3lo, mapA1, mapB1, mapB1lo;
 
   // Builds the operand buffers (BF16: Xb and the scales) from X, stream-ordered.
