@@ -227,11 +227,41 @@ ntd_small_kernel(const ntd_small_job* __restrict__ jobs, int iters, T eps, doubl
 // F^(1)T (new F^(1)) mode 3 and the core. Factors, core, Grams and pass
 // results live in shared memory.
 
+// acc[p] += v f[p] for p < Q (Q <= QM); with vec, f is 16-byte aligned and
+// Q % 4 == 0, and the factor row comes in 16-byte shared loads (a warp reads
+// the same row: one broadcast per load), four times fewer loads than the FMAs
+// would issue one by one.
+template <typename T, int QM>
+__device__ __forceinline__ void axpy_row(T v, const T* f, int Q, bool vec, T (&acc)[QM]) {
+  if (vec) {
+#pragma unroll
+    for (int p = 0; p < QM; p += 4) {
+      if (p < Q) {
+        T w[4];
+        if constexpr (sizeof(T) == 4) {
+          const float4 t = *reinterpret_cast<const float4*>(f + p);
+          w[0] = t.x; w[1] = t.y; w[2] = t.z; w[3] = t.w;
+        } else {
+          const double2 a = *reinterpret_cast<const double2*>(f + p);
+          const double2 b = *reinterpret_cast<const double2*>(f + p + 2);
+          w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[p + u] = fma(v, w[u], acc[p + u]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < QM; ++p)
+      if (p < Q) acc[p] = fma(v, f[p], acc[p]);
+  }
+}
+
 // P[r, p] = sum_k X[r N3 + k] F[k, p], rows r < R of X viewed R x N3, p < Q
 // (F: N3 x Q in shared memory). One thread per row, Q accumulators; the rows
 // a warp walks share their L1 lines.
-template <typename T, int QM>
-__device__ void pass_rows(const T* __restrict__ X, int R, int N3, const T* F, int Q, T* P) {
+template <typename T, int QM, bool VEC>
+__device__ void pass_rows_impl(const T* __restrict__ X, int R, int N3, const T* F, int Q, T* P) {
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     T acc[QM];
 #pragma unroll
@@ -243,20 +273,9 @@ __device__ void pass_rows(const T* __restrict__ X, int R, int N3, const T* F, in
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = __ldg(x + k + u);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const T* f = F + (k + u) * Q;
-#pragma unroll
-        for (int p = 0; p < QM; ++p)
-          if (p < Q) acc[p] = fma(v[u], f[p], acc[p]);
-      }
+      for (int u = 0; u < 8; ++u) axpy_row<T, QM>(v[u], F + (k + u) * Q, Q, VEC, acc);
     }
-    for (; k < N3; ++k) {
-      const T v = __ldg(x + k);
-      const T* f = F + k * Q;
-#pragma unroll
-      for (int p = 0; p < QM; ++p)
-        if (p < Q) acc[p] = fma(v, f[p], acc[p]);
-    }
+    for (; k < N3; ++k) axpy_row<T, QM>(__ldg(x + k), F + k * Q, Q, VEC, acc);
 #pragma unroll
     for (int p = 0; p < QM; ++p)
       if (p < Q) P[r * Q + p] = acc[p];
@@ -264,10 +283,18 @@ __device__ void pass_rows(const T* __restrict__ X, int R, int N3, const T* F, in
   __syncthreads();
 }
 
+template <typename T, int QM>
+__device__ void pass_rows(const T* __restrict__ X, int R, int N3, const T* F, int Q, T* P) {
+  if ((Q & 3) == 0 && (reinterpret_cast<uintptr_t>(F) & 15) == 0)
+    pass_rows_impl<T, QM, true>(X, R, N3, F, Q, P);
+  else
+    pass_rows_impl<T, QM, false>(X, R, N3, F, Q, P);
+}
+
 // P[p, c] = sum_i F[i, p] X[i C + c], X viewed N1 x C (F: N1 x Q in shared
 // memory). One thread per column c: consecutive threads read consecutive c.
-template <typename T, int QM>
-__device__ void pass_cols(const T* __restrict__ X, int N1, int C, const T* F, int Q, T* P) {
+template <typename T, int QM, bool VEC>
+__device__ void pass_cols_impl(const T* __restrict__ X, int N1, int C, const T* F, int Q, T* P) {
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
     T acc[QM];
 #pragma unroll
@@ -278,25 +305,22 @@ __device__ void pass_cols(const T* __restrict__ X, int N1, int C, const T* F, in
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = __ldg(X + (int64_t)(i + u) * C + c);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const T* f = F + (i + u) * Q;
-#pragma unroll
-        for (int p = 0; p < QM; ++p)
-          if (p < Q) acc[p] = fma(f[p], v[u], acc[p]);
-      }
+      for (int u = 0; u < 8; ++u) axpy_row<T, QM>(v[u], F + (i + u) * Q, Q, VEC, acc);
     }
-    for (; i < N1; ++i) {
-      const T v = __ldg(X + (int64_t)i * C + c);
-      const T* f = F + i * Q;
-#pragma unroll
-      for (int p = 0; p < QM; ++p)
-        if (p < Q) acc[p] = fma(f[p], v, acc[p]);
-    }
+    for (; i < N1; ++i) axpy_row<T, QM>(__ldg(X + (int64_t)i * C + c), F + i * Q, Q, VEC, acc);
 #pragma unroll
     for (int p = 0; p < QM; ++p)
       if (p < Q) P[(int64_t)p * C + c] = acc[p];
   }
   __syncthreads();
+}
+
+template <typename T, int QM>
+__device__ void pass_cols(const T* __restrict__ X, int N1, int C, const T* F, int Q, T* P) {
+  if ((Q & 3) == 0 && (reinterpret_cast<uintptr_t>(F) & 15) == 0)
+    pass_cols_impl<T, QM, true>(X, N1, C, F, Q, P);
+  else
+    pass_cols_impl<T, QM, false>(X, N1, C, F, Q, P);
 }
 
 // sum (X - X_hat)^2 and sum X^2 in FP64 with X_hat[r, k] = sum_c U[r, c] W[k, c]
