@@ -535,6 +535,31 @@ def oracle_sample(X64, F0, G0, sweeps):
     return time.perf_counter() - t0
 
 
+def line_40cube(dev, steps=5):
+    """The 40^3 FP64 workload (planted rank 3, m = 5, 200 + 200 sweeps): the
+    whole Alg. 1 step on the FP64 SIMT path (latency-bound: no roofline)."""
+    import torch
+
+    from paper_1909_07570_gb300 import inputs
+    w = inputs.WORKLOADS["cp3_40x40x40_m5_fp64"]
+    X64, _, F0, G0, B0 = inputs.make_problem(w)
+    X = torch.tensor(X64, dtype=torch.float64, device=dev)
+    F0d = [torch.tensor(f, dtype=torch.float64, device=dev) for f in F0]
+    G0d = torch.tensor(G0, dtype=torch.float64, device=dev)
+    B0d = [torch.tensor(b, dtype=torch.float64, device=dev) for b in B0]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    step = Alg1Step(w, X, F0d, G0d, B0d, "fp64", 0)
+    for _ in range(2):
+        step()
+    ms = timed_steps(step, steps, flush, torch.cuda.current_stream())
+    return {"workload": w.name, "dims": list(w.dims), "m": list(w.m), "r": w.r,
+            "ntd_sweeps_per_step": w.iters, "nncp_sweeps_per_step": w.cp_iters, "steps": steps,
+            "value": round(w.iters * steps / (sum(ms) / 1e3), 3), "unit": "iters/s",
+            "ms_per_step": round(sum(ms) / steps, 4),
+            "final_tucker_rel_err": step.tucker_rel_err(),
+            "final_lifted_rel_err": step.out["lifted_rel_err"]}
+
+
 def line_256cube(dev, steps=5):
     """The 256^3 FP32 workload (rank 10, m = 20, 500 + 500 sweeps): the whole
     Alg. 1 step on the TF32x3 passes, device time, and its pass rooflines."""
@@ -836,6 +861,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_256cube:
         import torch
         result["fp32_256cube"] = line_256cube(torch.device("cuda", 0))
+        result["fp64_40cube"] = line_40cube(torch.device("cuda", 0))
     if rank == 0 and world == 1 and not args.no_precision_form:
         import torch
         result["precision_form"] = precision_form(torch.device("cuda", 0))

@@ -64,7 +64,8 @@ typedef struct {
   int refine_iters;  /* NNC_BF16_REFINE only: the last refine_iters of the
                         iters sweeps run in FP32 (0 <= refine_iters <= iters) */
   double eps;        /* denominator guard, > 0 (1e-12 in the tests)         */
-  int exact_every;   /* ntd_fit, d = 3, with a trace (other calls ignore it):
+  int exact_every;   /* ntd_fit (d = 3) and nncp_tensor_fit, with a trace
+                        (other calls ignore it):
                         0, or k > 0: after every k-th sweep and after the
                         last, the sweep's trace entry is the relative error
                         of one explicit pass over X with FP64 sums instead of
@@ -393,8 +394,11 @@ int candelinc_pg_fit(const void* X, int d, const int64_t* dims, const int* m, in
  *  A          host array of d device pointers, A^(n) dims[n] x r (1 <= r <= 64),
  *             initial values on entry, result on exit
  *  trace      device, opts->iters doubles: ||X - I x_k A^(k)||_F / ||X||_F after
- *             each sweep (FP64 identity), or NULL
- *  rel_err    host, the last trace value (NaN for 0 sweeps), or NULL
+ *             each sweep (FP64 identity; with opts->exact_every = k > 0 every
+ *             k-th entry and the last from one explicit FP64 pass over X), or
+ *             NULL
+ *  rel_err    host, the final relative error from one explicit FP64 pass over
+ *             X (NaN for 0 sweeps), or NULL
  *  precision  NNC_FP64, NNC_FP32 (TF32x3 tensor-core passes), NNC_FP32_SIMT
  * Errors: INVALID_ARG, NONFINITE (X, or a sweep whose FP64 residual terms
  * were not finite), UNSUPPORTED, CUDA, ALLOC, TIMEOUT.

@@ -543,8 +543,8 @@ int nncp_tensor_fit(const void* X, int d, const int64_t* dims, int r, int precis
                     const nnc_opts* opts, void* const* A, double* trace, double* rel_err,
                     void* stream) {
   g_detail.clear();
-  if (X == nullptr || A == nullptr || opts == nullptr || opts->iters < 0 || !(opts->eps > 0.0))
-    return NNC_ERR_INVALID_ARG;
+  if (X == nullptr || A == nullptr) return NNC_ERR_INVALID_ARG;
+  NNC_TRY(check_opts(opts));
   if ((d != 3 && d != 4) || r < 1 || r > 64) return NNC_ERR_INVALID_ARG;
   int m[4] = {r, r, r, r};
   NNC_TRY(check_shape(d, dims, m, 64));
@@ -555,14 +555,14 @@ int nncp_tensor_fit(const void* X, int d, const int64_t* dims, int r, int precis
     double* a[4];
     for (int n = 0; n < d; ++n) a[n] = static_cast<double*>(A[n]);
     return nncp_tensor_fit<double>(static_cast<const double*>(X), d, dims, r, false, opts->iters,
-                                   opts->eps, a, trace, rel_err, s);
+                                   opts->eps, opts->exact_every, a, trace, rel_err, s);
   }
   if (precision == NNC_FP32 || precision == NNC_FP32_SIMT) {
     float* a[4];
     for (int n = 0; n < d; ++n) a[n] = static_cast<float*>(A[n]);
     return nncp_tensor_fit<float>(static_cast<const float*>(X), d, dims, r,
-                                  precision == NNC_FP32, opts->iters, opts->eps, a, trace,
-                                  rel_err, s);
+                                  precision == NNC_FP32, opts->iters, opts->eps,
+                                  opts->exact_every, a, trace, rel_err, s);
   }
   return precision == NNC_BF16_REFINE ? NNC_ERR_UNSUPPORTED : NNC_ERR_INVALID_ARG;
 }

@@ -697,9 +697,13 @@ int lifted_pg_fit(const T* X, int d, const int64_t* dims, const int* m, int r, b
 namespace {
 
 // Captures `body` (stream-ordered work on a private stream) once as a CUDA
-// graph and replays it `count` times after the work queued on s.
-template <typename Body>
-int replay(int count, cudaStream_t s, Body body) {
+// graph and replays it `count` times after the work queued on s; `after(t,
+// cs)`, if given, queues work on the private stream after replay t.
+struct NoAfter {
+  int operator()(int, cudaStream_t) const { return NNC_OK; }
+};
+template <typename Body, typename After = NoAfter>
+int replay(int count, cudaStream_t s, Body body, After after = After()) {
   if (count <= 0) return NNC_OK;
   PgGraph g;
   NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
@@ -723,7 +727,10 @@ int replay(int count, cudaStream_t s, Body body) {
     NNC_CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
     if (ty == cudaGraphNodeTypeKernel) ++kernels;
   }
-  for (int t = 0; t < count; ++t) NNC_CUDA_TRY(cudaGraphLaunch(g.exec, g.cs));
+  for (int t = 0; t < count; ++t) {
+    NNC_CUDA_TRY(cudaGraphLaunch(g.exec, g.cs));
+    NNC_TRY(after(t, g.cs));
+  }
   note_graph_launches(kernels * count);
   NNC_CUDA_TRY(cudaEventRecord(g.join, g.cs));
   NNC_CUDA_TRY(cudaStreamWaitEvent(s, g.join, 0));
@@ -741,7 +748,8 @@ int replay(int count, cudaStream_t s, Body body) {
 // = ||X - I x_k A^(k)|| / ||X|| after sweep t by the identity in FP64.
 template <typename T>
 int nncp_tensor_fit(const T* X, int d, const int64_t* dims, int r, bool tensor_cores, int iters,
-                    double eps, T* const* A, double* trace, double* rel_err, cudaStream_t s) {
+                    double eps, int exact_every, T* const* A, double* trace, double* rel_err,
+                    cudaStream_t s) {
   Scratch sc(s);
   Work<T> w;
   int m[kMaxD];
@@ -759,6 +767,19 @@ int nncp_tensor_fit(const T* X, int d, const int64_t* dims, int r, bool tensor_c
   NNC_TRY(sc.get(&counter, 2));
   NNC_CUDA_TRY(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s));
   double* last = w.Ls + 3;
+  // Exact checkpoints (nnc_opts exact_every): after every exact_every-th sweep
+  // and the last, the trace entry is replaced by the relative error of one
+  // explicit pass over X with FP64 sums (the identity cancels near a good fit).
+  ResidualWork<T> rw;
+  const bool exact = exact_every > 0 && trace;
+  if (exact || rel_err) NNC_TRY(residual_prepare<T>(d, dims, 1, m, r, sc, &rw));
+  const T* fac[kMaxD];
+  for (int k = 0; k < d; ++k) fac[k] = A[k];
+  auto after = [&](int t, cudaStream_t cs) -> int {
+    if (exact && ((t + 1) % exact_every == 0 || t + 1 == iters))
+      NNC_TRY(residual_run<T>(X, d, dims, 1, m, r, fac, nullptr, rw, nullptr, trace + t, cs));
+    return NNC_OK;
+  };
   NNC_TRY(replay(iters, s, [&](cudaStream_t cs) -> int {
     NNC_TRY(pass_last(w, A[d - 1], cs));
     for (int n = 0; n < d; ++n) {
@@ -773,13 +794,15 @@ int nncp_tensor_fit(const T* X, int d, const int64_t* dims, int r, bool tensor_c
       if (n == 0 && d > 2) NNC_TRY(make_u0(w, A[0], cs));
     }
     return loss_into(w, d - 1, last, trace, counter, cs, /*rel=*/1);
-  }));
+  }, after));
   NNC_TRY(check_tc(w, s));
   NNC_TRY(check_trace_finite(counter, s, "nncp_tensor_fit"));
   if (rel_err) {
     if (iters == 0) {
       *rel_err = NAN;
     } else {
+      // The final error from an explicit FP64 pass over X, as ntd_fit reports it.
+      NNC_TRY(residual_run<T>(X, d, dims, 1, m, r, fac, nullptr, rw, nullptr, last, s));
       NNC_CUDA_TRY(cudaMemcpyAsync(rel_err, last, sizeof(double), cudaMemcpyDeviceToHost, s));
       NNC_CUDA_TRY(cudaStreamSynchronize(s));
     }
@@ -964,9 +987,9 @@ template int lifted_grad<double>(const double*, int, const int64_t*, const int*,
                                  double*, cudaStream_t);
 template int lifted_pg_fit<float>(const float*, int, const int64_t*, const int*, int, bool, int,
                                   float* const*, float* const*, double*, double*, cudaStream_t);
-template int nncp_tensor_fit<float>(const float*, int, const int64_t*, int, bool, int, double,
+template int nncp_tensor_fit<float>(const float*, int, const int64_t*, int, bool, int, double, int,
                                     float* const*, double*, double*, cudaStream_t);
-template int nncp_tensor_fit<double>(const double*, int, const int64_t*, int, bool, int, double,
+template int nncp_tensor_fit<double>(const double*, int, const int64_t*, int, bool, int, double, int,
                                      double* const*, double*, double*, cudaStream_t);
 template int nmf_fit<float>(const float*, int64_t, int, int, int, double, float*, float*,
                             double*, double*, cudaStream_t);

@@ -23,10 +23,13 @@ int lifted_pg_fit(const T* X, int d, const int64_t* dims, const int* m, int r, b
 
 // nnCPD of X itself (Alg. 2, first step): `iters` MU sweeps on the CP factors
 // A^(n) (dims[n] x r) in place; trace (device, optional) and rel_err (host,
-// optional) get ||X - I x_k A^(k)|| / ||X||.
+// optional) get ||X - I x_k A^(k)|| / ||X||: the trace from the FP64 identity
+// (exact_every > 0: every exact_every-th entry and the last from an explicit
+// FP64 pass), rel_err from an explicit pass.
 template <typename T>
 int nncp_tensor_fit(const T* X, int d, const int64_t* dims, int r, bool tensor_cores, int iters,
-                    double eps, T* const* A, double* trace, double* rel_err, cudaStream_t s);
+                    double eps, int exact_every, T* const* A, double* trace, double* rel_err,
+                    cudaStream_t s);
 
 // nnTD of a d-way X (d = 3 or 4) by `iters` MU sweeps (Alg. 1, first step):
 // F^(n) (dims[n] x m[n]) and G in place; trace (device, optional) gets the

@@ -447,15 +447,17 @@ def candelinc_pg_fit(X, F, B, steps, precision=None, trace=True, stream=None):
     return loss.value, (tr[:steps] if trace else None)
 
 
-def nncp_tensor_fit(X, A, iters, precision=None, eps=1e-12, trace=True, stream=None):
+def nncp_tensor_fit(X, A, iters, precision=None, eps=1e-12, trace=True, stream=None,
+                    exact_every=0):
     """nnCPD of X itself (Alg. 2, first step), in place on A (list of N_n x r).
-    Returns (relative error, device FP64 trace or None)."""
+    Returns (relative error, device FP64 trace or None); exact_every as in
+    nnc_opts (exact trace checkpoints)."""
     code, dtype = _precision(X, precision)
     _require(X, dtype, "X")
     for n, a in enumerate(A):
         _require(a, dtype, f"A[{n}]")
     r = A[0].shape[1]
-    opts = nnc_opts(int(iters), 0, float(eps))
+    opts = nnc_opts(int(iters), 0, float(eps), int(exact_every), 0.0)
     tr = torch.empty(max(iters, 1), dtype=torch.float64, device=X.device) if trace else None
     err = ctypes.c_double()
     st = load().nncp_tensor_fit(_ptr(X), X.dim(), _i64(X.shape), r, code, ctypes.byref(opts),
