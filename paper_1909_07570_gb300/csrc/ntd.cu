@@ -24,6 +24,7 @@
 // as FP32-accurate TF32x3 tensor-core products; NNC_BF16_REFINE replays the
 // BF16 tensor-core sweep for iters - refine_iters sweeps and then the TF32x3
 // sweep for the rest; NNC_FP32_SIMT and NNC_FP64 use the SIMT passes.
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -46,8 +47,9 @@ struct NtdState {
   // (m1, N2, N3), is the pass result that P1 is copied from)
   T *P3, *P1, *P1s, *Y3, *M, *W1, *W3, *G2, *G3, *H[3], *S[3];
   T *num2, *num3;  // numerators of the split mode-2 and mode-3 updates
+  T* Yb;           // Y_r of the mode-1 and mode-2 tensor-core updates (UpdArgs::ybuf)
   // Shares of Y1[i] = F2^T P3[i] and of Y3[k] = P1[k]^T F2 from the
-  // tensor-core passes (y_nh = N2 / 128 per slab; NULL: upd12 forms them)
+  // tensor-core passes (y_nh = N2 / 128 per slab; NULL: the update kernel forms them)
   T* Y1p;
   T* Y3p;
   int y_nh;
@@ -85,6 +87,13 @@ int pass_x1(const T* X, const NtdState<T>& b, const T* F1, const T* F2, const tc
   NNC_CUDA_TRY(launch_ttm<T>(X, 1, (int)b.N[0], b.N[1] * b.N[2], F1, b.m[0], 1, b.m[0], b.P1s,
                              nullptr, 0, s));
   return launch_p1_rows<T>(b.P1s, b.m[0], b.N[1], b.N[2], b.P1, s);
+}
+
+// The tensor-core form of the factor updates' GEMMs (UpdArgs::tc): TF32
+// beside BF16 passes, whose rounding of X dominates; split TF32 (FP32-accurate)
+// beside TF32x3 passes; none on the SIMT path.
+inline int upd_tc(const tc::TcPlan* tcp) {
+  return tcp ? (tcp->kind == tc::kKindBf16 ? 1 : 3) : 0;
 }
 
 // The core update of a sweep (G, the next H1, the trace entry).
@@ -143,6 +152,9 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
       u.nparts = b.y_nh;
     }
     u.F = F[0];  u.nrows = N1;  u.mv = m1;  u.H = b.H[0];  u.eps = eps;
+    u.tc = upd_tc(tcp);
+    u.err = tcp ? tcp->err : nullptr;
+    u.ybuf = b.Yb;
     if constexpr (std::is_same<T, float>::value) {
       if (tcp) {
         u.bt = tcp->Bt1;
@@ -156,8 +168,10 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
   }
   // ---- modes 2 and 3 --------------------------------------------------------
   // The numerators do not need H_n, so the mode-2 update is split in two: the
-  // GEMM and the numerator (upd12, num_only) run beside the kernel forming H2,
-  // and a row-wise MU step follows.
+  // GEMM and the numerator (launch_upd12, num_only) run beside the kernel
+  // forming H2, and a row-wise MU step follows; in the tensor-core form the
+  // GEMM runs beside H2 and one kernel forms the numerators and takes the MU
+  // step.
   //   s2:  H2 ................ MU on F2 | H3 (S2 of the new F2)
   //   s3:  Num2 (P3, new F1) --^
   // When pass 2 can also form the shares of Y3[k] = P1[k]^T F2 (TF32x3 with
@@ -187,11 +201,27 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
   u2.F = F[1];  u2.nrows = N2;  u2.mv = m2;  u2.H = b.H[1];  u2.eps = eps;
   u2.num = b.num2;
   u2.num_only = 1;
-  NNC_TRY(launch_upd12<T>(u2, br.s3));
-  NNC_CUDA_TRY(cudaEventRecord(br.mid[0], br.s3));
-  NNC_CUDA_TRY(cudaStreamWaitEvent(br.s2, br.mid[0], 0));
-  u2.num_only = 0;
-  NNC_TRY(launch_mu_rows<T>(u2, br.s2));
+  u2.tc = upd_tc(tcp);
+  u2.err = tcp ? tcp->err : nullptr;
+  u2.ybuf = b.Yb;
+  bool tc2 = false;
+  if constexpr (std::is_same<T, float>::value) tc2 = upd_tc_form(u2);
+  if (tc2) {
+    // Tensor-core form: the GEMM beside H2, then numerators and MU in one.
+    if constexpr (std::is_same<T, float>::value) {
+      NNC_TRY(launch_upd_gemm(u2, br.s3));
+      NNC_CUDA_TRY(cudaEventRecord(br.mid[0], br.s3));
+      NNC_CUDA_TRY(cudaStreamWaitEvent(br.s2, br.mid[0], 0));
+      u2.num_only = 0;
+      NNC_TRY(launch_upd_num(u2, br.s2));
+    }
+  } else {
+    NNC_TRY(launch_upd12<T>(u2, br.s3));
+    NNC_CUDA_TRY(cudaEventRecord(br.mid[0], br.s3));
+    NNC_CUDA_TRY(cudaStreamWaitEvent(br.s2, br.mid[0], 0));
+    u2.num_only = 0;
+    NNC_TRY(launch_mu_rows<T>(u2, br.s2));
+  }
   NNC_CUDA_TRY(cudaEventRecord(br.mid[1], br.s2));  // the new F2
   {  // H3 and W3 = G x_1 S1 x_2 S2, with S2 = F2^T F2 (new F2)
     HArgs<T> h{};
@@ -215,6 +245,8 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
   u3.Yout = b.Y3;
   u3.F = F[2];  u3.nrows = N3;  u3.mv = m3;  u3.H = b.H[2];  u3.eps = eps;
   u3.gate_out = b.gate;
+  u3.tc = upd_tc(tcp);
+  u3.err = tcp ? tcp->err : nullptr;
   if constexpr (std::is_same<T, float>::value) {
     if (tcp) {
       u3.bt = tcp->Bt3;
@@ -223,11 +255,21 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
       u3.bt_ld = tcp->kb3;
     }
   }
+  u3.ybuf = b.Y3;  // the tensor-core form's Y3 is the one the core update keeps
+  bool tc3 = false;
+  if constexpr (std::is_same<T, float>::value) tc3 = !y3f && upd_tc_form(u3);
   if (y3f) {
     u3.Ypart = b.Y3p;
     u3.nparts = b.y_nh;
     NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.join[1], 0));
     NNC_TRY(launch_upd12<T>(u3, s));
+  } else if (tc3) {
+    if constexpr (std::is_same<T, float>::value) {
+      NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.mid[1], 0));
+      NNC_TRY(launch_upd_gemm(u3, s));
+      NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.join[1], 0));
+      NNC_TRY(launch_upd_num(u3, s));
+    }
   } else {
     NNC_CUDA_TRY(cudaStreamWaitEvent(s, br.mid[1], 0));
     u3.num = b.num3;
@@ -481,6 +523,7 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
   NNC_TRY(sc.get(&b.Y3, (size_t)((int64_t)m1 * m2 * N3)));
   NNC_TRY(sc.get(&b.num2, (size_t)(N2 * m2)));
   NNC_TRY(sc.get(&b.num3, (size_t)(N3 * m3)));
+  NNC_TRY(sc.get(&b.Yb, (size_t)std::max(N1 * m2 * m3, N2 * m1 * m3)));
   NNC_TRY(sc.get(&b.M, (size_t)nc));
   NNC_TRY(sc.get(&b.W1, (size_t)nc));
   NNC_TRY(sc.get(&b.W3, (size_t)nc));
@@ -527,8 +570,8 @@ int ntd_fit3_impl(const T* X, const int64_t* dims, const int* m, const nnc_opts*
     ck.rw = &rw;
   }
   if constexpr (std::is_same<T, float>::value) {
-    // The TF32x3 passes form the shares of Y1 when the shape allows it (see
-    // y1_fusable; the BF16 passes leave Y1 to the update kernel).
+    // The tensor-core passes form the shares of Y1 when the shape allows it
+    // (y1_fusable), the TF32x3 passes also those of Y3 (y3_fusable).
     const tc::TcPlan* any = exact ? exact : fast;
     if (any && any->y1_fusable(m2)) {
       b.y_nh = (int)(N2 / 128);

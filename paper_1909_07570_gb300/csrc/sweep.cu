@@ -3,16 +3,16 @@
 // With P3 = X x_3 F3^T ((N1 N2) x m3) and P1 = X x_1 F1^T (rows (k, j) x m1)
 // from the passes, a sweep is (S_k = F_k^T F_k, Eq. unfolding:property):
 //
-//   upd12 (mode 1) per slab i:  Y1[i] = F2^T P3[i, :, :]           (m2 x m3)
+//   update (mode 1) per slab i: Y1[i] = F2^T P3[i, :, :]           (m2 x m3)
 //                               (or the sum of its shares formed by pass 1)
 //                               Num1[i, a] = <Y1[i], G[a, :, :]>
 //                               F1[i, :] <- MU with Den = F1[i, :] H1
 //   hmat  (mode 2) per b:       S1 = F1^T F1;  W[:, b, :] = S1 G[:, b, :] S3
 //                               H2[b, b'] = <W[:, b, :], G[:, b', :]>
-//   upd12 (mode 2) per row j:   Y2[:, j, :] = F1^T P3[:, j, :];  Num2 (numerator only)
+//   update (mode 2) per row j:  Y2[:, j, :] = F1^T P3[:, j, :];  Num2 (numerator only)
 //   mu_rows (mode 2):           MU on F2 with Den = F2 H2
 //   hmat  (mode 3) per c:       S2 = F2^T F2;  W3 = G x_1 S1 x_2 S2 (kept);  H3
-//   upd12 (mode 3) per slab k:  Y3[k] = P1[k, :, :]^T F2  (m1 x m2, kept)
+//   update (mode 3) per slab k: Y3[k] = P1[k, :, :]^T F2  (m1 x m2, kept)
 //                               (or the sum of its shares formed by pass 2)
 //                               Num3[k, c] = <Y3[k], G[:, :, c]>;  MU on F3
 //   core_a (one block per a):   S3 = F3^T F3; M[a] = Y3[:, a, :]^T F3 (= (X x_1 F1^T x_2 F2^T x_3 F3^T)[a]);
@@ -21,10 +21,14 @@
 //                               trace = sqrt(||X||^2 - 2<M,G> + <G, G x_k S_k>)/||X||
 //                               with <G, G x_k S_k> = sum S1 .* H1^T (last block)
 //
-// These kernels are latency-bound (a few MFLOP each on L2-resident data), so
-// each block requests everything it needs up front (cp.async) and spreads every
-// contraction over all its threads: the block GEMM splits the contraction
-// across thread groups (4 x 4 register tiles per thread). Most blocks run
+// An update runs as updt_kernel (the GEMM Y_r on the tensor cores, FP32 data
+// with m <= 32), updm_kernel (the GEMM on the SIMT pipes) or upds_kernel (Y_r
+// from the pass's shares), two rows per block; all three end in the same
+// numerators and MU step. The other kernels are latency-bound (a few MFLOP
+// each on L2-resident data), so each block requests everything it needs up
+// front (cp.async) and spreads every contraction over all its threads: the
+// block GEMM splits the contraction across thread groups (4 x 4 register
+// tiles per thread). Most blocks run
 // their code once per sweep with a cold instruction cache, so the shared
 // helpers are kept out of line and not unrolled (one copy of the code per
 // kernel). Every reduction runs in a fixed order, so results are
@@ -35,7 +39,9 @@
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "mma32.cuh"
 #include "sweep.cuh"
+#include "tma.cuh"
 
 namespace nnc {
 namespace {
@@ -289,18 +295,25 @@ __device__ __noinline__ void smem_gemm(const T* A, const T* B, T* C, int m, int 
 // row, a few loads at a time, left the loop waiting on the latency of the
 // core's reads from L2); thread s of a row takes the 4-element vectors
 // s, s + NS, ... (16-byte loads when Y's rows are 16-byte aligned), and the
-// NS partial sums are added by a fixed shuffle tree.
+// NS partial sums are added by a fixed shuffle tree. Blocks that run this at
+// the same time on the same Y start at different rows (row (k + blockIdx.x)
+// % nq where a lone block would take row k): hundreds of blocks requesting
+// the same lines of L2 at once otherwise queue behind each other. Each row's
+// arithmetic is the same either way.
 template <typename T>
 __device__ __noinline__ void rows_dot2(const T* x0, const T* x1, const T* Y, int n, int nq,
                                        T* out0, T* out1) {
   const int NS = nq > 32 ? 4 : 8;
   const int per = blockDim.x / NS;  // rows at a time
   const int s = threadIdx.x % NS;
+  const int rot = (int)(blockIdx.x % (unsigned)nq);
   const bool vec = (n & 3) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
   for (int q0 = 0; q0 < nq; q0 += per) {
-    const int q = q0 + threadIdx.x / NS;
+    int q = q0 + threadIdx.x / NS;
+    const bool live = q < nq;
+    if (live) q = q + rot >= nq ? q + rot - nq : q + rot;
     T a0 = T(0), a1 = T(0);
-    if (q < nq) {
+    if (live) {
       const T* y = Y + (int64_t)q * n;
       if (vec) {
         const int nv = n >> 2;
@@ -331,7 +344,7 @@ __device__ __noinline__ void rows_dot2(const T* x0, const T* x1, const T* Y, int
       a0 += __shfl_xor_sync(0xffffffffu, a0, o);
       a1 += __shfl_xor_sync(0xffffffffu, a1, o);
     }
-    if (q < nq && s == 0) {
+    if (live && s == 0) {
       out0[q] = a0;
       if (x1) out1[q] = a1;
     }
@@ -350,76 +363,36 @@ __host__ __device__ inline bool core_in_smem(int64_t n) {
   return (size_t)n * sizeof(T) <= kCoreSmemBytes;
 }
 
-// ---------------------------------------------------------------------------
-// upd12: factor update of one mode from a pass result, one block per row r.
-//   Y_r = Fc^T P_r or P_r^T Fc (mu x mc), or the sum of its shares that the
-//   pass already formed;  Num[r, v] = <Y_r, Gn[v]>;
-//   F[r] <- MU(F[r], Num, F[r] H)
-// ---------------------------------------------------------------------------
+// The part of a multi-row update after Y: Y_r of the R <= 2 rows of the
+// block (r0 .. r0 + rn - 1) is in ys (R x mu mc, Y_r[u, c] at u mc + c; rows
+// past rn zero), H in hs and the old rows in fo (unless num_only). Stores Y
+// (Yout), forms the numerators of the R rows with each core row read once for
+// the block, then stores them (num_only) or takes the MU step.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) upd12_kernel(UpdArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int MU_ = a.mu, MC = a.mc, MV = a.mv, UC = MU_ * MC;
-  const bool gsm = core_in_smem<T>((int64_t)MV * UC);
-  T* stage = sm;
-  T* ys = stage + (a.Ypart ? 0 : gemm_stage_elems(MU_, MC, (int)sizeof(T), a.len));
-  T* hs = ys + al4(UC);
-  T* fo = hs + al4(MV * MV);
-  T* nm = fo + al4(MV);
-  T* gs = nm + al4(MV);  // MV x UC when it fits
-  const int64_t r = blockIdx.x;
-  // A programmatic successor (the next sweep's first pass over X) may start
-  // its prologue and its reads of X now; it waits for this grid before it
-  // reads anything this kernel writes.
-  pdl_trigger();
-
-  // Everything but the GEMM operands is requested first; the GEMM's waits
-  // cover this group too.
-  if (!a.num_only) {
-    cp_flat(hs, a.H, MV * MV);
-    cp_flat(fo, a.F + r * MV, MV);
-  }
-  if (gsm) cp_flat(gs, a.Gn, (int64_t)MV * UC);
-  cp_commit();
-  if (a.Ypart) {
-    const T* yp = a.Ypart + r * a.nparts * UC;
-    for (int e = threadIdx.x; e < UC; e += blockDim.x) {
-      T y = yp[e];
-      for (int h = 1; h < a.nparts; ++h) y += yp[(int64_t)h * UC + e];
-      ys[e] = y;
-    }
-    cp_wait<0>();
-    __syncthreads();
-  } else {
-    const int kch = gemm_kch(MU_, MC, (int)sizeof(T), a.len);
-    const T* pr = a.P + r * a.prow;
-    if (a.p_first)
-      gemm_tn_block(pr, a.pstride, MU_, a.Fc, MC, MC, a.len, kch, ys, stage);
-    else
-      gemm_tn_block(a.Fc, MU_, MU_, pr, a.pstride, MC, a.len, kch, ys, stage);
-  }
-
+__device__ __forceinline__ void upd_rows_tail(const UpdArgs<T>& a, const T* ys, const T* hs,
+                                              const T* fo, T* nm, int64_t r0, int rn, int R) {
+  const int UC = a.mu * a.mc, MV = a.mv;
   if (a.Yout)
-    for (int e = threadIdx.x; e < UC; e += blockDim.x) a.Yout[r * UC + e] = ys[e];
+    for (int e = threadIdx.x; e < rn * UC; e += blockDim.x) a.Yout[r0 * UC + e] = ys[e];
+  rows_dot2<T>(ys, R > 1 ? ys + UC : nullptr, a.Gn, UC, MV, nm, nm + MV);
+  __syncthreads();
   if (a.num_only) {
-    rows_dot(ys, gsm ? (const T*)gs : a.Gn, UC, MV, a.num + r * MV);
+    for (int e = threadIdx.x; e < rn * MV; e += blockDim.x) a.num[r0 * MV + e] = nm[e];
     return;
   }
-  rows_dot(ys, gsm ? (const T*)gs : a.Gn, UC, MV, nm);
-  __syncthreads();
-  for (int v = threadIdx.x; v < MV; v += blockDim.x) {
+  for (int e = threadIdx.x; e < rn * MV; e += blockDim.x) {
+    const int i = e / MV, v = e % MV;
     T den = T(0);
-    for (int w = 0; w < MV; ++w) den = fma(fo[w], hs[w * MV + v], den);
-    const T nv = mu_step(fo[v], nm[v], den, (T)a.eps);
-    a.F[r * MV + v] = nv;
-    write_operand(a, r, v, nv);
+    for (int w = 0; w < MV; ++w) den = fma(fo[i * MV + w], hs[w * MV + v], den);
+    const T nv = mu_step(fo[e], nm[e], den, (T)a.eps);
+    a.F[(r0 + i) * MV + v] = nv;
+    write_operand(a, r0 + i, v, nv);
   }
-  if (a.gate_out && r == 0 && threadIdx.x == 0) *a.gate_out = 1;
+  if (a.gate_out && r0 == 0 && threadIdx.x == 0) *a.gate_out = 1;
 }
 
 // ---------------------------------------------------------------------------
-// updm: the update of upd12 for R rows per block, the GEMMs staged by a
+// updm: a factor update (launch_upd12) for R rows per block, the GEMMs staged by a
 // three-deep cp.async ring shared by the R rows. One operand of the GEMM (the
 // factor Fc) is the same for every row: it is staged once per chunk for all R
 // rows. Each thread owns a TW x TW register tile of one row's Y_r (8 x 8 in
@@ -506,7 +479,10 @@ __global__ void __launch_bounds__(kThreads) updm_kernel(UpdArgs<T> a) {
   T* nm = fo + al4((size_t)R * MV);             // R x MV numerators
   const int64_t r0 = (int64_t)blockIdx.x * R;
   const int rn = (int)min((int64_t)R, a.nrows - r0);
-  pdl_trigger();  // as in upd12
+  // A programmatic successor (the next sweep's first pass over X) may start
+  // its prologue and its reads of X now; it waits for this grid before it
+  // reads anything this kernel writes.
+  pdl_trigger();
 
   // The row operand is P (rows of P_r) and the shared one Fc; in the chunk
   // buffers the u-side operand (A) comes first, then the c-side one (B).
@@ -655,26 +631,393 @@ __global__ void __launch_bounds__(kThreads) updm_kernel(UpdArgs<T> a) {
     }
   }
   __syncthreads();
-  if (a.Yout)
-    for (int e = threadIdx.x; e < rn * UC; e += blockDim.x) a.Yout[r0 * UC + e] = ys[e];
-  // Numerators of the R rows, each core row read once for the block.
-  if (a.num_only) {
-    rows_dot2<T>(ys, R > 1 ? ys + UC : nullptr, a.Gn, UC, MV, nm, nm + MV);
-    __syncthreads();
-    for (int e = threadIdx.x; e < rn * MV; e += blockDim.x) a.num[r0 * MV + e] = nm[e];
+  upd_rows_tail<T>(a, ys, hs, fo, nm, r0, rn, R);
+}
+
+// ---------------------------------------------------------------------------
+// updt: the update of updm with the GEMMs on the tensor cores, for FP32 data
+// with mu, mc <= 32. A block takes two rows; warp w works on row w / 4 and on
+// every fourth 8-deep step of the contraction, holding the whole zero-padded
+// 32 x 32 tile Z_r = Fc^T P_r (Y_r, or Y_r^T when p_first) in registers. A
+// step is eight mma.sync m16n8k8 (TF32 operands, FP32 accumulation), or 24
+// with SPLIT = 3, which splits every operand x into x_hi = tf32(x) and x_lo =
+// tf32(x - x_hi) and accumulates x_lo y_hi + x_hi y_lo + x_hi y_hi (the
+// dropped x_lo y_lo is below FP32 rounding). The four partial tiles of a row
+// are added in warp order, so results are deterministic. One thread stages
+// the operands with the TMA unit, 64 contraction rows of Fc and of both rows'
+// P_r per stage, three stages deep (the tensor maps zero-fill every edge).
+// Y_r goes to UpdArgs::ybuf, where numu_kernel takes it. The fragments and
+// the layout of a tile in registers are mma32.cuh's.
+// ---------------------------------------------------------------------------
+constexpr int kTcRows = 2;                               // rows per block
+constexpr int kTcWarpsPerRow = kThreads / 32 / kTcRows;  // contraction split
+constexpr int kTcKC = 64;                                // contraction rows per stage
+constexpr int kTcStages = 3;
+constexpr int kTcBox = kTcKC * 32;                       // one operand's box (floats)
+constexpr int kTcStage = (1 + kTcRows) * kTcBox;         // Fc's box, then the rows'
+constexpr uint32_t kTcStageBytes = kTcStage * 4;
+constexpr int kTcZ = 32 * 32;                            // one partial tile (mma32::tile_index)
+
+__host__ __device__ inline size_t updt_ring_floats() {
+  const size_t ring = (size_t)kTcStages * kTcStage;
+  const size_t red = (size_t)kTcRows * kTcWarpsPerRow * kTcZ;
+  return al4(ring > red ? ring : red);
+}
+// Floats of dynamic shared memory, with 1024 bytes of slack to align the ring.
+__host__ __device__ inline size_t updt_smem_floats(int mu, int mc) {
+  return 256 + updt_ring_floats() + al4((size_t)kTcRows * mu * mc);
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(kThreads, 2)
+    updt_kernel(UpdArgs<float> a, const __grid_constant__ CUtensorMap map_f,
+                const __grid_constant__ CUtensorMap map_p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[kTcStages];
+  constexpr int R = kTcRows;
+  const int MU_ = a.mu, MC = a.mc, UC = MU_ * MC;
+  // The ring starts on a 1024-byte boundary (the swizzle's period).
+  const uint32_t pad = (1024u - (tma::smem_u32(smem_raw) & 1023u)) & 1023u;
+  float* stage = reinterpret_cast<float*>(smem_raw + pad);
+  float* ys = stage + updt_ring_floats();       // R x UC
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int rn = (int)min((int64_t)R, a.nrows - r0);
+  pdl_trigger();  // as in updm
+
+  // Stage c holds contraction rows c KC .. c KC + KC - 1 of Fc (box 32 x KC)
+  // and of the block's two row operands (box 32 x KC x 2); the TMA unit reads
+  // entries outside Fc, P or the contraction as zero.
+  const int nch = (a.len + kTcKC - 1) / kTcKC;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kTcStages; ++k) tma::mbar_init(&full[k], 1);
+    tma::mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int c) {  // one thread
+    float* st = stage + (c % kTcStages) * kTcStage;
+    uint64_t* bar = &full[c % kTcStages];
+    tma::mbar_expect_tx(bar, kTcStageBytes);
+    tma::load_2d(st, &map_f, 0, c * kTcKC, bar);
+    tma::load_3d(st + kTcBox, &map_p, 0, c * kTcKC, (int)r0, bar);
+  };
+  if (threadIdx.x == 0)
+    for (int c = 0; c < kTcStages - 1 && c < nch; ++c) issue(c);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int ri = warp / kTcWarpsPerRow, wk = warp % kTcWarpsPerRow;
+  const int off0 = mma32::frag_off(lane, 0), off1 = mma32::frag_off(lane, 1);
+  float acc[2][4][4];
+  mma32::zero(acc);
+  for (int c = 0; c < nch; ++c) {
+    // The slot of stage c + 2 was released by the barrier ending step c - 1.
+    if (threadIdx.x == 0 && c + kTcStages - 1 < nch) issue(c + kTcStages - 1);
+    bool ok = tma::mbar_wait(&full[c % kTcStages], (c / kTcStages) & 1, a.err);
+    if (ok) {
+      const float* sa = stage + (c % kTcStages) * kTcStage;
+      const float* sb = sa + (1 + ri) * kTcBox;
+      const int kn8 = (min(kTcKC, a.len - c * kTcKC) + 7) / 8;
+#pragma unroll 2
+      for (int ks = wk; ks < kn8; ks += kTcWarpsPerRow)
+        mma32::step<SPLIT>(acc, sa + ks * 256, sb + ks * 256, off0, off1);
+    }
+    if (!__syncthreads_and(ok)) {
+      // A copy did not arrive (the flag is raised): wait, bounded, for the
+      // stages still in flight so that none lands after the block has exited.
+      if (threadIdx.x == 0)
+        for (int d = c; d < nch && d < c + kTcStages; ++d)
+          tma::mbar_wait(&full[d % kTcStages], (d / kTcStages) & 1, nullptr);
+      return;
+    }
+  }
+  // The partial tiles, then the row's four partials added in warp order into
+  // Y_r (Z_r, or Z_r^T when p_first) in ys.
+  float* red = stage;  // every stage has landed and been read
+  mma32::store(red + (ri * kTcWarpsPerRow + wk) * kTcZ, acc, lane);
+  __syncthreads();
+  for (int row = warp; row < R * MU_; row += kThreads / 32) {
+    const int i = row / MU_, u = row - i * MU_;
+    const float* zi = red + i * kTcWarpsPerRow * kTcZ;
+    for (int cc = lane; cc < MC; cc += 32) {
+      const int o = a.p_first ? mma32::tile_index(cc, u) : mma32::tile_index(u, cc);
+      float v = zi[o];
+#pragma unroll
+      for (int w = 1; w < kTcWarpsPerRow; ++w) v += zi[o + w * kTcZ];
+      ys[i * UC + u * MC + cc] = v;
+    }
+  }
+  __syncthreads();
+  // Y of the block's rows to the numerator kernel (UC % 4 == 0).
+  float4* yo = reinterpret_cast<float4*>(a.ybuf + r0 * UC);
+  for (int e = threadIdx.x; e < rn * UC / 4; e += kThreads)
+    yo[e] = reinterpret_cast<const float4*>(ys)[e];
+}
+
+// ---------------------------------------------------------------------------
+// numu: the numerators and the MU step of the tensor-core update form, eight
+// rows per block. Num[r, v] = <Y_r, Gn[v]> for the block's rows is one GEMM,
+// Num (8 x mv) = Y (8 x UC) Gn^T, on the tensor cores (mma.sync m16n8k8 with
+// the rows as M rows 0..7 and zeros as rows 8..15): warp w of 16 takes every
+// 16th 16-deep step of the contraction with all mv <= 32 columns, and the 16
+// partial results are added in warp order. The core arrives in shared memory
+// by one bulk copy per row (rows padded to a pitch of 4 mod 8 16-byte units,
+// so the fragment loads below are free of bank conflicts) while every thread
+// loads its entries of Y: from the GEMM form's buffer (ybuf) or as the sum of
+// the pass's shares (added in share order, and stored to Yout when asked),
+// all of a thread's loads in flight at once. Then the MU step of the rows, or
+// (num_only) their numerators. SPLIT as in mma32::step.
+//
+// Fragments: thread (g, t) = (lane / 4, lane % 4) takes entries k0 + 4t ..
+// k0 + 4t + 3 of row g of Y and of rows 8j + g of Gn (16-byte loads); MMA
+// h = 0, 1 of the step takes k = t from entry 4t + 2h and k = t + 4 from
+// entry 4t + 2h + 1, the same for both operands.
+// ---------------------------------------------------------------------------
+constexpr int kNuRows = 8;
+constexpr int kNuThreads = 512;
+constexpr int kNuWarps = kNuThreads / 32;
+constexpr int kNuSteps = 4;  // 16-deep steps per warp at most (UC <= 1024)
+
+// Row pitch (floats) of the core in shared memory.
+__host__ __device__ inline int numu_pitch(int uc) {
+  const int u = uc / 4;
+  return 4 * (u + ((4 - u % 8) + 8) % 8);
+}
+__host__ __device__ inline size_t numu_smem_floats(int mu, int mc, int mv) {
+  return (size_t)mv * numu_pitch(mu * mc) + (size_t)kNuWarps * kNuRows * 32 +
+         al4((size_t)mv * mv) + 2 * al4((size_t)kNuRows * mv);
+}
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+template <int SPLIT>
+__device__ __forceinline__ void numu_mma(float (&acc)[4][4], float4 y, const float4 (&gv)[4]) {
+  const float ya[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t ah[4] = {mma32::tf32_rn(ya[2 * h]), 0u, mma32::tf32_rn(ya[2 * h + 1]), 0u};
+    uint32_t al[4] = {0u, 0u, 0u, 0u};
+    if constexpr (SPLIT == 3) {
+      al[0] = mma32::tf32_rn(ya[2 * h] - __uint_as_float(ah[0]));
+      al[2] = mma32::tf32_rn(ya[2 * h + 1] - __uint_as_float(ah[2]));
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float g0 = h ? gv[j].z : gv[j].x, g1 = h ? gv[j].w : gv[j].y;
+      const uint32_t bh0 = mma32::tf32_rn(g0), bh1 = mma32::tf32_rn(g1);
+      if constexpr (SPLIT == 3) {
+        const uint32_t bl0 = mma32::tf32_rn(g0 - __uint_as_float(bh0));
+        const uint32_t bl1 = mma32::tf32_rn(g1 - __uint_as_float(bh1));
+        mma32::mma_tf32(acc[j], al, bh0, bh1);
+        mma32::mma_tf32(acc[j], ah, bl0, bl1);
+      }
+      mma32::mma_tf32(acc[j], ah, bh0, bh1);
+    }
+  }
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(kNuThreads, 1) numu_kernel(UpdArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t gbar;
+  const int UC = a.mu * a.mc, MV = a.mv, pitch = numu_pitch(UC);
+  float* gs = reinterpret_cast<float*>(smem_raw);     // MV rows of the core, pitch apart
+  float* red = gs + (size_t)MV * pitch;              // 16 warps x 8 rows x 32
+  float* hs = red + kNuWarps * kNuRows * 32;
+  float* fo = hs + al4((size_t)MV * MV);             // old rows
+  float* nm = fo + al4((size_t)kNuRows * MV);        // numerators
+  const int64_t r0 = (int64_t)blockIdx.x * kNuRows;
+  const int rn = (int)min((int64_t)kNuRows, a.nrows - r0);
+  pdl_trigger();  // as in updm
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&gbar, 1);
+    tma::mbar_init_fence();
+  }
+  __syncthreads();  // the barrier is initialised before anyone waits on it
+  if (threadIdx.x == 0) {
+    tma::mbar_expect_tx(&gbar, (uint32_t)(MV * UC * 4));
+    for (int v = 0; v < MV; ++v)
+      tma::load_bulk(gs + (size_t)v * pitch, a.Gn + (int64_t)v * UC, (uint32_t)(UC * 4), &gbar);
+  }
+  if (!a.num_only) {
+    cp_flat(hs, a.H, MV * MV);
+    cp_flat(fo, a.F + r0 * MV, (int64_t)rn * MV);
+  }
+  cp_commit();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int g = lane >> 2, t = lane & 3;
+  const int np = a.Ypart ? a.nparts : 1;
+  const bool rowok = g < rn;
+  const float* yrow = (a.Ypart ? a.Ypart : a.ybuf) + (rowok ? (r0 + g) * np * UC : 0);
+  float* yout = (a.Ypart && a.Yout && rowok) ? a.Yout + (r0 + g) * UC : nullptr;
+  const int nsteps = (UC + 15) / 16;
+  // This thread's entries of Y for its steps, all loads in flight together.
+  float4 y[kNuSteps];
+  bool live[kNuSteps];
+#pragma unroll
+  for (int q = 0; q < kNuSteps; ++q) {
+    const int k = (warp + q * kNuWarps) * 16 + 4 * t;
+    live[q] = warp + q * kNuWarps < nsteps && k < UC && rowok;  // UC % 4 == 0
+    y[q] = live[q] ? *reinterpret_cast<const float4*>(yrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  for (int h0 = 1; h0 < np; h0 += 4) {
+    float4 z[kNuSteps][4];
+#pragma unroll
+    for (int q = 0; q < kNuSteps; ++q) {
+      const int k = (warp + q * kNuWarps) * 16 + 4 * t;
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+        z[q][p] = live[q] && h0 + p < np
+                      ? *reinterpret_cast<const float4*>(yrow + (int64_t)(h0 + p) * UC + k)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < kNuSteps; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+        if (h0 + p < np) y[q] = add4(y[q], z[q][p]);
+  }
+  if (yout) {
+#pragma unroll
+    for (int q = 0; q < kNuSteps; ++q)
+      if (live[q]) *reinterpret_cast<float4*>(yout + (warp + q * kNuWarps) * 16 + 4 * t) = y[q];
+  }
+  const bool ok = tma::mbar_wait(&gbar, 0, a.err);
+  if (!__syncthreads_and(ok)) {
+    // The core did not arrive (the flag is raised): wait, bounded, for the
+    // copies still in flight so that none lands after the block has exited.
+    if (threadIdx.x == 0) tma::mbar_wait(&gbar, 0, nullptr);
+    cp_wait<0>();
     return;
   }
-  rows_dot2<T>(ys, R > 1 ? ys + UC : nullptr, a.Gn, UC, MV, nm, nm + MV);
+  float acc[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+#pragma unroll
+  for (int q = 0; q < kNuSteps; ++q) {
+    const int st = warp + q * kNuWarps;
+    if (st >= nsteps) break;
+    const int k = st * 16 + 4 * t;
+    float4 gv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = 8 * j + g;
+      gv[j] = (k < UC && n < MV) ? *reinterpret_cast<const float4*>(gs + n * pitch + k)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    numu_mma<SPLIT>(acc, y[q], gv);
+  }
+  // Partial numerators of the warp: rows g (c0, c1; rows 8..15 are padding).
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    red[(warp * kNuRows + g) * 32 + 8 * j + 2 * t] = acc[j][0];
+    red[(warp * kNuRows + g) * 32 + 8 * j + 2 * t + 1] = acc[j][1];
+  }
+  cp_wait<0>();
   __syncthreads();
-  for (int e = threadIdx.x; e < rn * MV; e += blockDim.x) {
-    const int i = e / MV, v = e % MV;
-    T den = T(0);
-    for (int w = 0; w < MV; ++w) den = fma(fo[i * MV + w], hs[w * MV + v], den);
-    const T nv = mu_step(fo[e], nm[e], den, (T)a.eps);
+  for (int e = threadIdx.x; e < rn * MV; e += kNuThreads) {
+    const int r = e / MV, v = e - r * MV;
+    float n = red[r * 32 + v];
+#pragma unroll
+    for (int w = 1; w < kNuWarps; ++w) n += red[(w * kNuRows + r) * 32 + v];
+    nm[e] = n;
+  }
+  __syncthreads();
+  if (a.num_only) {
+    for (int e = threadIdx.x; e < rn * MV; e += kNuThreads) a.num[r0 * MV + e] = nm[e];
+    return;
+  }
+  for (int e = threadIdx.x; e < rn * MV; e += kNuThreads) {
+    const int i = e / MV, v = e - i * MV;
+    float den = 0.f;
+    for (int w = 0; w < MV; ++w) den = fmaf(fo[i * MV + w], hs[w * MV + v], den);
+    const float nv = mu_step(fo[e], nm[e], den, (float)a.eps);
     a.F[(r0 + i) * MV + v] = nv;
     write_operand(a, r0 + i, v, nv);
   }
   if (a.gate_out && r0 == 0 && threadIdx.x == 0) *a.gate_out = 1;
+}
+
+// ---------------------------------------------------------------------------
+// upds: a factor update from the pass's shares of Y_r, two rows per block
+// (each core row read once for both, as in updm): Y_r = the sum of its
+// nparts shares in order h = 0 .. nparts - 1, then upd_rows_tail.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) upds_kernel(UpdArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  constexpr int R = 2;
+  const int UC = a.mu * a.mc, MV = a.mv;
+  T* ys = sm;                                  // R x UC
+  T* hs = ys + al4((size_t)R * UC);
+  T* fo = hs + al4((size_t)MV * MV);           // R x MV old rows
+  T* nm = fo + al4((size_t)R * MV);            // R x MV numerators
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int rn = (int)min((int64_t)R, a.nrows - r0);
+  pdl_trigger();  // as in updm
+  if (!a.num_only) {
+    cp_flat(hs, a.H, MV * MV);
+    cp_flat(fo, a.F + r0 * MV, (int64_t)rn * MV);
+  }
+  cp_commit();
+  bool done = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if ((UC & 3) == 0 && (reinterpret_cast<uintptr_t>(a.Ypart) & 15) == 0) {
+      // 16-byte vectors, two per thread at a time, with the loads of four
+      // shares of both in flight before they are added (in share order).
+      const int nv = R * UC / 4;
+      for (int v0 = threadIdx.x; v0 < nv; v0 += 2 * blockDim.x) {
+        float4 y[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+        for (int h0 = 0; h0 < a.nparts; h0 += 4) {
+          float4 t[2][4];
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int v = v0 + k * blockDim.x, i = 4 * v / UC;
+            const float* yp = a.Ypart + ((r0 + i) * a.nparts + h0) * UC + (4 * v - i * UC);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              t[k][q] = (v < nv && i < rn && h0 + q < a.nparts)
+                            ? *reinterpret_cast<const float4*>(yp + (int64_t)q * UC)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              if (h0 + q == 0) {
+                y[k] = t[k][q];
+              } else if (h0 + q < a.nparts) {
+                y[k].x += t[k][q].x; y[k].y += t[k][q].y;
+                y[k].z += t[k][q].z; y[k].w += t[k][q].w;
+              }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          if (v0 + k * blockDim.x < nv)
+            *reinterpret_cast<float4*>(ys + 4 * (v0 + k * blockDim.x)) = y[k];
+      }
+      done = true;
+    }
+  }
+  if (!done) {
+    for (int e = threadIdx.x; e < R * UC; e += blockDim.x) {
+      const int i = e / UC, f = e - i * UC;
+      T y = T(0);
+      if (i < rn) {
+        const T* yp = a.Ypart + (r0 + i) * a.nparts * UC + f;
+        y = yp[0];
+        for (int h = 1; h < a.nparts; ++h) y += yp[(int64_t)h * UC];
+      }
+      ys[e] = y;
+    }
+  }
+  cp_wait<0>();
+  __syncthreads();
+  upd_rows_tail<T>(a, ys, hs, fo, nm, r0, rn, R);
 }
 
 // ---------------------------------------------------------------------------
@@ -686,7 +1029,7 @@ __global__ void __launch_bounds__(kThreads) mu_rows_kernel(UpdArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int MV = a.mv, R = kThreads / MV;
-  pdl_trigger();  // as in upd12
+  pdl_trigger();  // as in updm
   T* hs = sm;                  // MV x MV
   T* fo = hs + al4(MV * MV);   // R x MV: the old rows
   const int64_t r0 = (int64_t)blockIdx.x * R;
@@ -933,11 +1276,95 @@ int set_smem(K kernel, size_t bytes) {
 }
 }  // namespace
 
+// The shapes updt_kernel takes: mu, mc <= 32, the contraction rows of Fc and
+// of every P_r starting on 16-byte boundaries (the tensor maps' rule for
+// their base and strides), coordinates within int, and a flag for a copy that
+// does not arrive.
+static bool updt_fits(const UpdArgs<float>& a) {
+  const int ms = a.p_first ? a.mc : a.mu;
+  const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  return a.mu >= 1 && a.mc >= 1 && a.mu <= 32 && a.mc <= 32 && a.len >= 1 && a.nrows >= 1 &&
+         a.nrows < (1LL << 31) && ms % 4 == 0 && a.prow % 4 == 0 && a.pstride % 4 == 0 &&
+         a.prow > 0 && a.pstride > 0 && al16(a.P) && al16(a.Fc) && a.err != nullptr;
+}
+
+bool upd_tc_form(const UpdArgs<float>& a) {
+  const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const int UC = a.mu * a.mc;
+  if (!a.tc || a.mu < 1 || a.mc < 1 || a.mu > 32 || a.mc > 32 || a.mv < 1 || a.mv > 32 ||
+      (UC & 3) != 0 || a.nrows < 1 || !al16(a.Gn) || a.err == nullptr)
+    return false;
+  if (a.Ypart) return a.nparts >= 1 && al16(a.Ypart) && (!a.Yout || al16(a.Yout));
+  return a.ybuf != nullptr && al16(a.ybuf) && updt_fits(a);
+}
+
+int launch_upd_gemm(const UpdArgs<float>& a, cudaStream_t s) {
+  if (a.Ypart || !upd_tc_form(a)) return NNC_ERR_UNSUPPORTED;
+  const size_t smem = sizeof(float) * updt_smem_floats(a.mu, a.mc);
+  const unsigned grid = (unsigned)ceil_div(a.nrows, (int64_t)kTcRows);
+  // Fc: (ms, len), row pitch ms; P: (mr, len, nrows), strides pstride, prow.
+  const int ms = a.p_first ? a.mc : a.mu, mr = a.p_first ? a.mu : a.mc;
+  CUtensorMap map_f, map_p;
+  {
+    const uint64_t dims[2] = {(uint64_t)ms, (uint64_t)a.len};
+    const uint64_t strides[1] = {(uint64_t)ms * 4};
+    const uint32_t box[2] = {32, (uint32_t)kTcKC};
+    NNC_TRY(tma::encode_f32(&map_f, a.Fc, 2, dims, strides, box));
+  }
+  {
+    const uint64_t dims[3] = {(uint64_t)mr, (uint64_t)a.len, (uint64_t)a.nrows};
+    const uint64_t strides[2] = {(uint64_t)a.pstride * 4, (uint64_t)a.prow * 4};
+    const uint32_t box[3] = {32, (uint32_t)kTcKC, (uint32_t)kTcRows};
+    NNC_TRY(tma::encode_f32(&map_p, a.P, 3, dims, strides, box));
+  }
+  if (a.tc == 3) {
+    NNC_TRY(set_smem(updt_kernel<3>, smem));
+    updt_kernel<3><<<grid, kThreads, smem, s>>>(a, map_f, map_p);
+  } else {
+    NNC_TRY(set_smem(updt_kernel<1>, smem));
+    updt_kernel<1><<<grid, kThreads, smem, s>>>(a, map_f, map_p);
+  }
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  return NNC_OK;
+}
+
+int launch_upd_num(const UpdArgs<float>& a, cudaStream_t s) {
+  if (!upd_tc_form(a) || (a.num_only && !a.num)) return NNC_ERR_UNSUPPORTED;
+  const size_t smem = sizeof(float) * numu_smem_floats(a.mu, a.mc, a.mv);
+  const unsigned grid = (unsigned)ceil_div(a.nrows, (int64_t)kNuRows);
+  if (a.tc == 3) {
+    NNC_TRY(set_smem(numu_kernel<3>, smem));
+    numu_kernel<3><<<grid, kNuThreads, smem, s>>>(a);
+  } else {
+    NNC_TRY(set_smem(numu_kernel<1>, smem));
+    numu_kernel<1><<<grid, kNuThreads, smem, s>>>(a);
+  }
+  note_launch(s);
+  NNC_CUDA_TRY(cudaGetLastError());
+  return NNC_OK;
+}
+
 template <typename T>
 int launch_upd12(const UpdArgs<T>& a, cudaStream_t s) {
   if (a.mu > 64 || a.mc > 64 || a.mv > 64) return NNC_ERR_UNSUPPORTED;
   const int UC = a.mu * a.mc;
-  if (!a.Ypart) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (upd_tc_form(a)) {
+      if (!a.Ypart) NNC_TRY(launch_upd_gemm(a, s));
+      return launch_upd_num(a, s);
+    }
+  }
+  if (a.Ypart) {
+    const size_t smem = sizeof(T) * (al4((size_t)2 * UC) + al4((size_t)a.mv * a.mv) +
+                                     2 * al4((size_t)2 * a.mv));
+    NNC_TRY(set_smem(upds_kernel<T>, smem));
+    upds_kernel<T><<<(unsigned)ceil_div(a.nrows, (int64_t)2), kThreads, smem, s>>>(a);
+    note_launch(s);
+    NNC_CUDA_TRY(cudaGetLastError());
+    return NNC_OK;
+  }
+  {
     // The GEMM form: R rows per block (updm_kernel).
     const int R = Updm<T>::rows(a.mu, a.mc);
     const size_t smem = sizeof(T) * Updm<T>::stage_elems(a.mu, a.mc, a.mv, a.p_first, nullptr);
@@ -947,15 +1374,6 @@ int launch_upd12(const UpdArgs<T>& a, cudaStream_t s) {
     NNC_CUDA_TRY(cudaGetLastError());
     return NNC_OK;
   }
-  const size_t st = a.Ypart ? 0 : gemm_stage_elems(a.mu, a.mc, (int)sizeof(T), a.len);
-  const size_t smem =
-      sizeof(T) * (st + al4(UC) + al4(a.mv * a.mv) + 2 * al4(a.mv) +
-                   (core_in_smem<T>((int64_t)a.mv * UC) ? (size_t)a.mv * UC : 0));
-  NNC_TRY(set_smem(upd12_kernel<T>, smem));
-  upd12_kernel<T><<<(unsigned)a.nrows, kThreads, smem, s>>>(a);
-  note_launch(s);
-  NNC_CUDA_TRY(cudaGetLastError());
-  return NNC_OK;
 }
 
 template <typename T>

@@ -41,11 +41,21 @@ struct UpdArgs {
   int64_t bt_ld;
   const float* bt_scale;
   int* gate_out;  // optional: set to 1 (mode 3: the sweep's core update is pending)
-  // Split update: upd12 with num_only stores Num (nrows x mv) in `num` and
+  // Split update: launch_upd12 with num_only stores Num (nrows x mv) in `num` and
   // leaves F alone; mu_rows then applies the MU step from `num` and H (the
   // numerator does not need H, so the two can run beside the kernel forming H).
   int num_only;
   T* num;
+  // FP32 only: the GEMM on the tensor cores when the shape allows it (mu, mc
+  // <= 32, 16-byte aligned rows): 1 with TF32 operands, 3 with each operand
+  // split into two TF32 parts (FP32-accurate); 0 on the SIMT pipes. Its
+  // operands arrive through the TMA unit; a copy that has not arrived after
+  // about 2 s sets *err (required for this form) and the block gives up.
+  int tc;
+  int* err;
+  // The tensor-core form's Y_r (nrows x mu mc), from its GEMM to its
+  // numerator kernel; Yout (where Y is kept) may serve.
+  T* ybuf;
 };
 
 // H_n = unfold_n(G x_u S_u x_v S_v) unfold_n(G)^T, one block per index p of mode n.
@@ -98,6 +108,13 @@ struct CoreArgs {
 };
 template <typename T>
 int launch_upd12(const UpdArgs<T>& a, cudaStream_t s);
+// The tensor-core form of an update in its two parts (launch_upd12 runs both
+// when upd_tc_form(a)): launch_upd_gemm forms Y_r into a.ybuf (not with
+// a.Ypart); launch_upd_num forms the numerators from a.ybuf or the shares
+// a.Ypart and takes the MU step (num_only: stores the numerators).
+bool upd_tc_form(const UpdArgs<float>& a);
+int launch_upd_gemm(const UpdArgs<float>& a, cudaStream_t s);
+int launch_upd_num(const UpdArgs<float>& a, cudaStream_t s);
 template <typename T>
 int launch_hmat(const HArgs<T>& a, cudaStream_t s);
 // F[r] <- MU(F[r], num[r], F[r] H) for every row, with the operand writes and

@@ -30,7 +30,8 @@
 //   warps 2-5     epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //                 lanes 32 (w % 4) ..), scaled stores to global memory; with
 //                 TcEpilogue::ysh also the tile's contraction with the
-//                 matching factor rows (the nnTD sweep's mode-1 / mode-3 shares)
+//                 matching factor rows (the nnTD sweep's mode-1 / mode-3 shares),
+//                 by mma.sync on the tile staged in shared memory (mma32.cuh)
 //   warps 6-9     TF32x3 only: split each staged A tile into x_hi (in place)
 //                 and x_lo (into a 3-slot ring of its own)
 // so a tile's epilogue overlaps the next tile's MMAs. The kernel is launched
@@ -47,6 +48,7 @@
 #include <mutex>
 
 #include "kernels.cuh"
+#include "mma32.cuh"
 #include "tc_ttm.cuh"
 
 namespace nnc {
@@ -571,49 +573,29 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if constexpr (FUSE) {
         // Contraction of the tile (one slab s, rows j0 .. j0 + 127):
         //   share[b, c] = sum_r F[j0 + r, b] P[(s, j0 + r), c]
-        // 4 x 4 output tiles per thread, rows split over `groups` thread
-        // groups whose partial tiles are added in group order.
+        // on the tensor cores (mma32.cuh: TF32 operands beside the BF16
+        // rounding of X, split TF32 in the FP32-accurate pass). The warp of
+        // quarter q takes rows 32 q .. 32 q + 31 with the whole 32 x 32 share
+        // (zero past m2, m3) in registers; the four partial shares are added
+        // in quarter order.
         const int et = threadIdx.x - 64;  // 0 .. 127
-        const int m2 = ep.yf_m, m3 = ep.q, tq = (m3 + 3) / 4;
-        const int tiles = ((m2 + 3) / 4) * tq, groups = 128 / tiles;
-        const int g = et / tiles, t = et % tiles;
-        const int b0 = (t / tq) * 4, cc0 = (t % tq) * 4;
-        float acc[4][4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+        const int o0 = mma32::frag_off(lane, 0), o1 = mma32::frag_off(lane, 1);
+        float acc[2][4][4];
+        mma32::zero(acc);
         epi_sync();  // Ps and Fs complete
-        if (g < groups) {
-#pragma unroll 4
-          for (int r = g; r < 128; r += groups) {
-            const float4 fb =
-                *reinterpret_cast<const float4*>(Fs + r * 32 + (((b0 >> 2) ^ (r & 7)) << 2));
-            const float4 pc =
-                *reinterpret_cast<const float4*>(Ps + r * 32 + (((cc0 >> 2) ^ (r & 7)) << 2));
-            const float fv[4] = {fb.x, fb.y, fb.z, fb.w}, pv[4] = {pc.x, pc.y, pc.z, pc.w};
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
-#pragma unroll
-              for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(fv[x], pv[y], acc[x][y]);
-          }
-        }
-        epi_sync();  // Ps is reused for the partial tiles
-        float* red = Ps;  // groups x m2 x m3 <= 16 tiles x 128 threads
-        if (g < groups) {
-#pragma unroll
-          for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y)
-              if (b0 + x < m2 && cc0 + y < m3) red[(g * m2 + b0 + x) * m3 + cc0 + y] = acc[x][y];
-        }
+        for (int ks = 4 * quarter; ks < 4 * quarter + 4; ++ks)
+          mma32::step<L::kTf32 ? 3 : 1>(acc, Fs + ks * 256, Ps + ks * 256, o0, o1);
+        epi_sync();  // Ps is reused for the partial shares
+        float* red = Ps;  // 4 x 32 x 32
+        mma32::store(red + quarter * 1024, acc, lane);
         epi_sync();
-        const int n = m2 * m3;
+        const int m2 = ep.yf_m, m3 = ep.q, n = m2 * m3;
         float* yo = ep.ysh + tile * n;
         for (int e = et; e < n; e += 128) {
-          float y = 0.f;
-          for (int q = 0; q < groups; ++q) y += red[q * n + e];
-          yo[ep.y_tr ? (e % m3) * m2 + e / m3 : e] = y;
+          const int bb = e / m3, cc = e % m3, o = mma32::tile_index(bb, cc);
+          const float y = ((red[o] + red[o + 1024]) + red[o + 2048]) + red[o + 3072];
+          yo[ep.y_tr ? cc * m2 + bb : e] = y;
         }
         epi_sync();  // red and Fs are free for the next tile
       }
@@ -815,7 +797,14 @@ int launch_pass(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& b
   const int sms = device_sm_count();
   const int avail = (tiles >= 8LL * sms && reserve > 0 && reserve < sms / 2) ? sms - reserve : sms;
   const int64_t per = ceil_div(tiles, (int64_t)avail);
-  const int64_t grid = ceil_div(tiles, per);
+  int64_t grid = ceil_div(tiles, per);
+  if (FUSE && ep.y_nh > 1) {
+    // A grid that is a multiple of the tiles per slab gives every CTA tiles
+    // of one j range only, so it loads its factor rows once per pass.
+    const int64_t up = ceil_div(grid, ep.y_nh) * ep.y_nh;
+    if (up <= avail) grid = up;
+    else if (avail >= ep.y_nh) grid = avail / ep.y_nh * ep.y_nh;
+  }
   NNC_CUDA_TRY(launch_pdl(tc_pass_kernel<KIND, kMN, NP, FUSE>, dim3(static_cast<unsigned>(grid)),
                           dim3(kThreadsTc), smem, s, a, b, blo, nk, tiles, ep, err));
   note_launch(s);
@@ -939,11 +928,10 @@ int TcPlan::convert_b1(const float* F1, cudaStream_t s) const {
 }
 
 bool TcPlan::y1_fusable(int m2) const {
-  // The TF32x3 pass has time for the tile contraction in its epilogue (its
-  // stage rate is set by the split and the MMAs); the BF16 pass streams X
-  // about twice as fast and the contraction would hold it back (measured 79
-  // against 49 us at 512^3, m = 32), so BF16 leaves Y1 to the update kernel.
-  return kind == kKindTf32x3 && np3 == 32 && m2 >= 1 && m2 <= 32 && N2 % 128 == 0;
+  // Tiles of pass 1 are single (i, j0 .. j0 + 127) row blocks when N2 % 128
+  // == 0; the tile contraction runs on the tensor cores, which keeps it off
+  // the BF16 pass's stage rate too.
+  return np3 == 32 && m2 >= 1 && m2 <= 32 && N2 % 128 == 0;
 }
 
 bool TcPlan::y3_fusable(int m2) const {
