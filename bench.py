@@ -292,7 +292,7 @@ def pass_rooflines(prof, w, dt_bytes, peaks, peak_src, workload):
         alg_flops = 2.0 * nX * (w.m[2] if kind % 2 == 0 else w.m[0])
         achieved = alg_bytes / avg_s / 1e9
         sources = ["paper_1909_07570_gb300/csrc/ttm.cu"] if kind in (0, 1) else \
-            ["paper_1909_07570_gb300/csrc/tc_ttm.cu"]
+            ["paper_1909_07570_gb300/csrc/tc_ttm.cu", "paper_1909_07570_gb300/csrc/mma32.cuh"]
         recs.append({
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4),
