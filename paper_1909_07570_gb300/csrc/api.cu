@@ -133,6 +133,8 @@ int nncp_run(int n_jobs, const nncp_job* jobs, const nnc_opts* o, double* rel_er
              cudaStream_t s) {
   NncpRoute rt;
   NNC_TRY(nncp_route<T>(n_jobs, jobs, statuses != nullptr, &rt));
+  if (rt.cluster)
+    return nncp_cluster_batched<T>(n_jobs, jobs, o->iters, o->eps, rel_errs, statuses, s);
   if (rt.two_pass)
     return nncp_l2_batched<T>(n_jobs, jobs, o->iters, o->eps, rel_errs, statuses, s);
   Scratch sc(s);

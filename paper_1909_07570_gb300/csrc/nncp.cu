@@ -250,6 +250,17 @@ int nncp_route(int n_jobs, const nncp_job* jobs, bool skip_invalid, NncpRoute* r
     }
   }
   l2_ok = l2_ok && l2_elems * sizeof(T) <= kSmemBudget;
+  // The cluster form: every valid job 3-way with slabs within a CTA, and a
+  // cluster per valid job on the GPU at once.
+  bool cl_ok = true;
+  int valid = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    const nncp_job& j = jobs[i];
+    if (!nncp_job_valid(j)) continue;
+    ++valid;
+    if (j.d != 3 || cpx_cluster_elems(j) * sizeof(T) > kSmemBudget) cl_ok = false;
+  }
+  cl_ok = cl_ok && valid >= 1 && (int64_t)valid * cpx_cluster_ctas() <= device_sm_count();
   constexpr int64_t kTwoPassMinEntries = 16384;
   if (rt->smem > kSmemBudget) {
     if (!l2_ok) {
@@ -260,6 +271,7 @@ int nncp_route(int n_jobs, const nncp_job* jobs, bool skip_invalid, NncpRoute* r
   } else {
     rt->two_pass = largest >= kTwoPassMinEntries && l2_ok;
   }
+  rt->cluster = rt->two_pass && cl_ok;
   return NNC_OK;
 }
 

@@ -26,7 +26,8 @@ size_t nncp_smem_bytes(const nncp_job& j, size_t elem);
 // so they cannot drift apart.
 struct NncpRoute {
   size_t smem = 0;        // one-pass kernel: dynamic shared memory (largest valid job)
-  bool two_pass = false;  // the two-pass kernel (tensor read from global memory) takes the batch
+  bool two_pass = false;  // the two-pass sweep (two passes over the tensor) takes the batch
+  bool cluster = false;   // ... as one thread-block cluster per fit (nncp_cluster_batched)
   int invalid = 0;        // jobs that fail nncp_job_valid
 };
 
@@ -36,9 +37,12 @@ struct NncpRoute {
 // to the two-pass kernel when that kernel can take it (every valid job 3-way,
 // r <= 16, its arrays within one block), and so does a batch whose one-pass
 // state exceeds 200 KiB of shared memory. UNSUPPORTED (with a detail) when
-// neither kernel takes the batch. With skip_invalid false an invalid job makes
-// the call INVALID_ARG (the detail names the job); with it true the invalid
-// jobs are only counted.
+// neither kernel takes the batch. A two-pass batch runs one cluster of
+// cpx_cluster_ctas() CTAs per fit when the clusters of all its valid jobs fit
+// on the GPU at once and every job's slabs fit in a CTA's shared memory (a
+// few large fits, as in Alg. 1's core fit), else one block per fit. With
+// skip_invalid false an invalid job makes the call INVALID_ARG (the detail
+// names the job); with it true the invalid jobs are only counted.
 template <typename T>
 int nncp_route(int n_jobs, const nncp_job* jobs, bool skip_invalid, NncpRoute* rt);
 
@@ -52,6 +56,17 @@ int nncp_route(int n_jobs, const nncp_job* jobs, bool skip_invalid, NncpRoute* r
 template <typename T>
 cudaError_t launch_nncp(const nncp_job* jobs_dev, int n_jobs, size_t smem, int iters, double eps,
                         double* rel_errs, int* statuses, cudaStream_t s, int threads = 256);
+
+// The two-pass sweep with one thread-block cluster per fit (nncp_cluster.cu):
+// 3-way jobs, any r <= 32; jobs that fail nncp_job_valid are skipped
+// (statuses: INVALID_ARG); statuses and rel_errs as in nncp_l2_batched.
+template <typename T>
+int nncp_cluster_batched(int n_jobs, const nncp_job* jobs, int iters, double eps,
+                         double* rel_errs, int* statuses, cudaStream_t s);
+// Shared-memory elements of one CTA of a cluster fit of job j, and the CTAs
+// of a cluster.
+size_t cpx_cluster_elems(const nncp_job& j);
+int cpx_cluster_ctas();
 
 // The tuning class of a batch (largest per-sweep work over the valid jobs,
 // number of jobs).
