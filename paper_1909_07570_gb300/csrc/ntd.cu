@@ -99,13 +99,15 @@ inline int upd_tc(const tc::TcPlan* tcp) {
 // The core update of a sweep (G, the next H1, the trace entry).
 template <typename T>
 int launch_sweep_core(T* const* F, T* G, NtdState<T>& b, double eps, double* trace,
-                      int trace_stride, cudaStream_t s) {
+                      int trace_stride, const tc::TcPlan* tcp, cudaStream_t s) {
   CoreArgs<T> c{};
   c.G = G;  c.G2 = b.G2;  c.G3 = b.G3;  c.Y3 = b.Y3;  c.Mout = b.M;  c.W3 = b.W3;
   c.S1 = b.S[0];  c.S2 = b.S[1];  c.F3 = F[2];  c.n3 = b.N[2];  c.S3_out = b.S[2];
   c.W1 = b.W1;  c.H1 = b.H[0];  c.dots = b.dots;  c.done = b.done;  c.x2 = b.stats;
   c.trace = trace;  c.trace_stride = trace_stride;  c.counter = b.counter;  c.gate = b.gate;
   c.m1 = b.m[0];  c.m2 = b.m[1];  c.m3 = b.m[2];  c.eps = eps;
+  c.tc = upd_tc(tcp);
+  c.err = tcp ? tcp->err : nullptr;
   return launch_core<T>(c, s);
 }
 
@@ -135,7 +137,7 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
   if (prev_core) {
     NNC_CUDA_TRY(cudaEventRecord(br.fork[0], s));
     NNC_CUDA_TRY(cudaStreamWaitEvent(br.s2, br.fork[0], 0));
-    NNC_TRY(launch_sweep_core<T>(F, G, b, eps, trace, trace_stride, br.s2));
+    NNC_TRY(launch_sweep_core<T>(F, G, b, eps, trace, trace_stride, tcp, br.s2));
     NNC_CUDA_TRY(cudaEventRecord(br.join[0], br.s2));
   }
   if (ev) NNC_CUDA_TRY(cudaEventRecordWithFlags(ev->start[0], s, cudaEventRecordExternal));
@@ -192,6 +194,8 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     h.fu = F[0];  h.nu = N1;  h.su_out = b.S[0];
     h.sv = b.S[2];
     h.H = b.H[1];
+    h.tc = upd_tc(tcp);
+    h.err = tcp ? tcp->err : nullptr;
     NNC_TRY(launch_hmat<T>(h, br.s2));
   }
   UpdArgs<T> u2{};
@@ -231,6 +235,8 @@ int sweep3(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double* tr
     h.fv = F[1];  h.nv = N2;  h.sv_out = b.S[1];
     h.H = b.H[2];
     h.Wout = b.W3;
+    h.tc = upd_tc(tcp);
+    h.err = tcp ? tcp->err : nullptr;
     NNC_TRY(launch_hmat<T>(h, br.s2));
   }
   NNC_CUDA_TRY(cudaEventRecord(br.join[1], br.s2));
@@ -453,7 +459,7 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
     }
     if (checkpoints && ck->at(first + t - 1)) {
       const int sweep = first + t - 1;
-      NNC_TRY(launch_sweep_core<T>(F, G, b, eps, trace, 1, g.cs));
+      NNC_TRY(launch_sweep_core<T>(F, G, b, eps, trace, 1, tcp, g.cs));
       const T* fac[3] = {F[0], F[1], F[2]};
       NNC_TRY(residual_run<T>(ck->X, 3, ck->dims, 0, ck->m, 0, fac, G, *ck->rw, nullptr,
                               trace + sweep, g.cs));
@@ -475,7 +481,8 @@ int run_sweeps(const T* X, T* const* F, T* G, NtdState<T>& b, double eps, double
   }
   *done = t;
   note_graph_launches(kernels);
-  NNC_TRY(launch_sweep_core<T>(F, G, b, eps, trace ? trace : b.trace_dummy, trace ? 1 : 0, g.cs));
+  NNC_TRY(launch_sweep_core<T>(F, G, b, eps, trace ? trace : b.trace_dummy, trace ? 1 : 0, tcp,
+                               g.cs));
   NNC_CUDA_TRY(cudaEventRecord(g.join, g.cs));
   NNC_CUDA_TRY(cudaStreamWaitEvent(s, g.join, 0));
   NNC_CUDA_TRY(cudaStreamSynchronize(g.cs));

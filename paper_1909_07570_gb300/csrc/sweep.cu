@@ -645,14 +645,14 @@ __global__ void __launch_bounds__(kThreads) updm_kernel(UpdArgs<T> a) {
 // dropped x_lo y_lo is below FP32 rounding). The four partial tiles of a row
 // are added in warp order, so results are deterministic. One thread stages
 // the operands with the TMA unit, 64 contraction rows of Fc and of both rows'
-// P_r per stage, three stages deep (the tensor maps zero-fill every edge).
+// P_r per stage, four stages deep (the tensor maps zero-fill every edge).
 // Y_r goes to UpdArgs::ybuf, where numu_kernel takes it. The fragments and
 // the layout of a tile in registers are mma32.cuh's.
 // ---------------------------------------------------------------------------
 constexpr int kTcRows = 2;                               // rows per block
 constexpr int kTcWarpsPerRow = kThreads / 32 / kTcRows;  // contraction split
 constexpr int kTcKC = 64;                                // contraction rows per stage
-constexpr int kTcStages = 3;
+constexpr int kTcStages = 4;
 constexpr int kTcBox = kTcKC * 32;                       // one operand's box (floats)
 constexpr int kTcStage = (1 + kTcRows) * kTcBox;         // Fc's box, then the rows'
 constexpr uint32_t kTcStageBytes = kTcStage * 4;
@@ -839,6 +839,11 @@ __global__ void __launch_bounds__(kNuThreads, 1) numu_kernel(UpdArgs<float> a) {
     for (int v = 0; v < MV; ++v)
       tma::load_bulk(gs + (size_t)v * pitch, a.Gn + (int64_t)v * UC, (uint32_t)(UC * 4), &gbar);
   }
+  // Launched as a programmatic dependent: the kernel before it on the stream
+  // (a pass, the GEMM form, a Gram kernel) may still run until here. None of
+  // them writes the core, so its copy above overlaps their tail; everything
+  // below may be theirs.
+  pdl_wait();
   if (!a.num_only) {
     cp_flat(hs, a.H, MV * MV);
     cp_flat(fo, a.F + r0 * MV, (int64_t)rn * MV);
@@ -1158,6 +1163,210 @@ __global__ void __launch_bounds__(kThreads) core_a_kernel(CoreArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
+// Block GEMMs on the tensor cores for the kernels beside the passes (hmat,
+// core_a): Z_p = A_p^T B for p < NP (32 x 32, zero past the operands' width),
+// summed over `len` contraction rows. B and every A_p are row sets of at most
+// 32 FP32 entries that the TMA unit reads (box of 32 entries x 64 rows at
+// (0, t0) of a 2-D map, or (0, t0, row) of a 3-D one) into a three-deep ring,
+// one stage per 64 rows; an A_p without a map is B itself (a Gram). The eight
+// warps split over the products and over every (8 / NP)-th 8-deep step of the
+// contraction (mma32::step, SPLIT as there) and their partial tiles are added
+// in warp order into out[p] (entry (s, c) at s ld + c, for s < ms[p], c < mc).
+// Called once per block, by every thread; false (with *err raised) when a
+// copy did not arrive, after waiting (bounded) for the stages in flight.
+// ---------------------------------------------------------------------------
+struct TcOperand {
+  const CUtensorMap* map;  // NULL: the B operand itself
+  int row;                 // third coordinate of a 3-D map, -1 for a 2-D map
+};
+
+constexpr int kTbBox = 64 * 32;  // floats in one operand box
+constexpr int kTbStages = 3;
+
+// Ring floats for NP products (also room for the partial tiles).
+__host__ __device__ inline size_t tc_block_ring_floats(int np) {
+  const size_t ring = (size_t)kTbStages * (1 + np) * kTbBox, red = (size_t)8 * 1024;
+  return ring > red ? ring : red;
+}
+
+__device__ __forceinline__ void tma_box(float* dst, const TcOperand& o, int t0, uint64_t* bar) {
+  if (o.row < 0) tma::load_2d(dst, o.map, 0, t0, bar);
+  else tma::load_3d(dst, o.map, 0, t0, o.row, bar);
+}
+
+template <int SPLIT, int NP>
+__device__ bool tc_block_gemm(const TcOperand (&A)[NP], const TcOperand& B, int len,
+                              float* ring, uint64_t* bars, float* const (&out)[NP], int ld,
+                              const int (&ms)[NP], int mc, int* err) {
+  constexpr int WPP = 8 / NP;  // warps per product
+  int nbox = 1;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) nbox += A[p].map ? 1 : 0;
+  const int per = (1 + NP) * kTbBox;
+  const uint32_t bytes = (uint32_t)nbox * kTbBox * 4;
+  const int nch = (len + 63) / 64;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kTbStages; ++k) tma::mbar_init(&bars[k], 1);
+    tma::mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int c) {  // one thread
+    float* st = ring + (c % kTbStages) * per;
+    uint64_t* bar = &bars[c % kTbStages];
+    tma::mbar_expect_tx(bar, bytes);
+    tma_box(st, B, c * 64, bar);
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (A[p].map) tma_box(st + (1 + p) * kTbBox, A[p], c * 64, bar);
+  };
+  if (threadIdx.x == 0)
+    for (int c = 0; c < kTbStages - 1 && c < nch; ++c) issue(c);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int p = warp / WPP, wk = warp % WPP;
+  const int off0 = mma32::frag_off(lane, 0), off1 = mma32::frag_off(lane, 1);
+  float acc[2][4][4];
+  mma32::zero(acc);
+  bool aself = true;
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+    if (q == p) aself = A[q].map == nullptr;
+  for (int c = 0; c < nch; ++c) {
+    if (threadIdx.x == 0 && c + kTbStages - 1 < nch) issue(c + kTbStages - 1);
+    const bool ok = tma::mbar_wait(&bars[c % kTbStages], (c / kTbStages) & 1, err);
+    if (ok) {
+      const float* sb = ring + (c % kTbStages) * per;
+      const float* sa = aself ? sb : sb + (1 + p) * kTbBox;
+      const int kn8 = (min(64, len - c * 64) + 7) / 8;
+      for (int ks = wk; ks < kn8; ks += WPP)
+        mma32::step<SPLIT>(acc, sa + ks * 256, sb + ks * 256, off0, off1);
+    }
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0)
+        for (int d = c; d < nch && d < c + kTbStages; ++d)
+          tma::mbar_wait(&bars[d % kTbStages], (d / kTbStages) & 1, nullptr);
+      return false;
+    }
+  }
+  float* red = ring;  // every stage has landed and been read
+  mma32::store(red + warp * 1024, acc, lane);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    for (int e = threadIdx.x; e < ms[q] * mc; e += blockDim.x) {
+      const int s = e / mc, cc = e - s * mc, o = mma32::tile_index(s, cc);
+      const float* z = red + q * WPP * 1024 + o;
+      float v = z[0];
+#pragma unroll
+      for (int w = 1; w < WPP; ++w) v += z[w * 1024];
+      out[q][s * ld + cc] = v;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// hmat on the tensor cores: the Gram of the factor given (fu or fv) by
+// tc_block_gemm, the rest as in hmat_kernel. FP32, U, V, P <= 32.
+template <int SPLIT>
+__global__ void __launch_bounds__(kThreads)
+    hmat_tc_kernel(HArgs<float> a, const __grid_constant__ CUtensorMap map_f) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kTbStages];
+  const uint32_t pad = (1024u - (tma::smem_u32(smem_raw) & 1023u)) & 1023u;
+  float* ring = reinterpret_cast<float*>(smem_raw + pad);
+  const int U = a.mu, V = a.mv, P = a.mp, UV = U * V;
+  float* su = ring + tc_block_ring_floats(1);
+  float* sv = su + al4(U * U);
+  float* gp = sv + al4(V * V);
+  float* tp = gp + al4(UV);
+  float* wp = tp + al4(UV);
+  const int p = blockIdx.x;
+  if (!a.fu) cp_flat(su, a.su, U * U);
+  if (!a.fv) cp_flat(sv, a.sv, V * V);
+  cp_flat(gp, a.Gn + (int64_t)p * UV, UV);
+  cp_commit();
+  const TcOperand self[1] = {{nullptr, -1}};
+  const TcOperand fb{&map_f, -1};
+  float* const outs[1] = {a.fu ? su : sv};
+  const int mss[1] = {a.fu ? U : V};
+  const bool ok = tc_block_gemm<SPLIT, 1>(self, fb, (int)(a.fu ? a.nu : a.nv), ring, bars, outs,
+                                          a.fu ? U : V, mss, a.fu ? U : V, a.err);
+  cp_wait<0>();
+  __syncthreads();
+  if (!ok) return;
+  if (p == 0 && a.su_out && a.fu)
+    for (int e = threadIdx.x; e < U * U; e += blockDim.x) a.su_out[e] = su[e];
+  if (p == 0 && a.sv_out && a.fv)
+    for (int e = threadIdx.x; e < V * V; e += blockDim.x) a.sv_out[e] = sv[e];
+  smem_gemm(su, gp, tp, U, U, V);  // S_u G[p]
+  __syncthreads();
+  smem_gemm(tp, sv, wp, U, V, V);  // (S_u G[p]) S_v
+  __syncthreads();
+  if (a.Wout)
+    for (int e = threadIdx.x; e < UV; e += blockDim.x)
+      a.Wout[(int64_t)p * a.w_sp + (int64_t)(e / V) * a.w_su + (int64_t)(e % V) * a.w_sv] = wp[e];
+  rows_dot(wp, a.Gn, UV, P, a.H + (int64_t)p * P);
+}
+
+// core_a on the tensor cores: S3 = F3^T F3 and M[a] = Y3[:, a, :]^T F3 in one
+// tc_block_gemm (both products share F3's boxes), the rest as in core_a_kernel.
+template <int SPLIT>
+__global__ void __launch_bounds__(kThreads)
+    core_a_tc_kernel(CoreArgs<float> a, const __grid_constant__ CUtensorMap map_f3,
+                     const __grid_constant__ CUtensorMap map_y3) {
+  if (a.gate && *a.gate == 0) return;  // no sweep since the last core update
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kTbStages];
+  const uint32_t pad = (1024u - (tma::smem_u32(smem_raw) & 1023u)) & 1023u;
+  float* ring = reinterpret_cast<float*>(smem_raw + pad);
+  const int m1 = a.m1, m2 = a.m2, m3 = a.m3;
+  const int bc = m2 * m3;
+  float* s2 = ring + tc_block_ring_floats(2);  // m2 x m2
+  float* s3 = s2 + al4(m2 * m2);              // m3 x m3
+  float* ma = s3 + al4(m3 * m3);              // bc: M[a]
+  float* wa = ma + al4(bc);                   // bc: W3[a], then scratch
+  float* ga = wa + al4(bc);                   // bc: G[a]
+  const int aa = blockIdx.x;
+  const int64_t off = (int64_t)aa * bc;
+  cp_flat(s2, a.S2, m2 * m2);
+  cp_flat(wa, a.W3 + off, bc);
+  cp_flat(ga, a.G + off, bc);
+  cp_commit();
+  const TcOperand As[2] = {{&map_y3, aa}, {nullptr, -1}};
+  const TcOperand fb{&map_f3, -1};
+  // M[a] rows b (m2 x m3, pitch m3) and S3 (m3 x m3, pitch m3).
+  float* const outs[2] = {ma, s3};
+  const int mss[2] = {m2, m3};
+  const bool ok =
+      tc_block_gemm<SPLIT, 2>(As, fb, (int)a.n3, ring, bars, outs, m3, mss, m3, a.err);
+  cp_wait<0>();
+  __syncthreads();
+  if (!ok) return;
+  if (aa == 0)
+    for (int e = threadIdx.x; e < m3 * m3; e += blockDim.x) a.S3_out[e] = s3[e];
+  for (int e = threadIdx.x; e < bc; e += blockDim.x) {
+    const int b = e / m3, c = e % m3;
+    float d = 0.f;
+    for (int w = 0; w < m3; ++w) d = fmaf(wa[b * m3 + w], s3[w * m3 + c], d);
+    const float gv = mu_step(ga[e], ma[e], d, (float)a.eps);
+    ga[e] = gv;
+    a.G[off + e] = gv;
+    a.G2[((int64_t)b * m1 + aa) * m3 + c] = gv;  // G permuted to (m2, m1, m3)
+    a.G3[((int64_t)c * m1 + aa) * m2 + b] = gv;  // G permuted to (m3, m1, m2)
+    a.Mout[off + e] = ma[e];
+  }
+  __syncthreads();
+  smem_gemm(s2, ga, wa, m2, m2, m3);  // S2 G[a]
+  __syncthreads();
+  for (int e = threadIdx.x; e < bc; e += blockDim.x) {  // W1[a] = (S2 G[a]) S3
+    const int b = e / m3, c = e % m3;
+    float v = 0.f;
+    for (int w = 0; w < m3; ++w) v = fmaf(wa[b * m3 + w], s3[w * m3 + c], v);
+    a.W1[off + e] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // core_b: one block per a: H1[a, q] = <W1[a], G[q]> (next sweep's H1) and
 // <M[a], G[a]>. The residual also needs <G, G x_k S_k> = sum_{a,w} S1[a, w]
 // H1[w, a] (Dn[a] = sum_w S1[a, w] W1[w], so <G[a], Dn[a]> = sum_w S1[a, w]
@@ -1335,10 +1544,10 @@ int launch_upd_num(const UpdArgs<float>& a, cudaStream_t s) {
   const unsigned grid = (unsigned)ceil_div(a.nrows, (int64_t)kNuRows);
   if (a.tc == 3) {
     NNC_TRY(set_smem(numu_kernel<3>, smem));
-    numu_kernel<3><<<grid, kNuThreads, smem, s>>>(a);
+    NNC_CUDA_TRY(launch_pdl(numu_kernel<3>, dim3(grid), dim3(kNuThreads), smem, s, a));
   } else {
     NNC_TRY(set_smem(numu_kernel<1>, smem));
-    numu_kernel<1><<<grid, kNuThreads, smem, s>>>(a);
+    NNC_CUDA_TRY(launch_pdl(numu_kernel<1>, dim3(grid), dim3(kNuThreads), smem, s, a));
   }
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
@@ -1388,9 +1597,44 @@ int launch_mu_rows(const UpdArgs<T>& a, cudaStream_t s) {
   return NNC_OK;
 }
 
+static bool al16p(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// hmat_tc_kernel's shapes: one Gram to form (fu or fv), every dimension <=
+// 32, the factor's rows 16-byte aligned.
+static bool hmat_tc_fits(const HArgs<float>& a) {
+  if (!a.tc || !a.err || (a.fu != nullptr) == (a.fv != nullptr)) return false;
+  const float* f = a.fu ? a.fu : a.fv;
+  const int m = a.fu ? a.mu : a.mv;
+  const int64_t n = a.fu ? a.nu : a.nv;
+  return a.mp >= 1 && a.mp <= 32 && a.mu >= 1 && a.mu <= 32 && a.mv >= 1 && a.mv <= 32 &&
+         m % 4 == 0 && n >= 1 && n < (1LL << 31) && al16p(f);
+}
+
 template <typename T>
 int launch_hmat(const HArgs<T>& a, cudaStream_t s) {
   if (a.mu > 64 || a.mv > 64) return NNC_ERR_UNSUPPORTED;
+  if constexpr (std::is_same<T, float>::value) {
+    if (hmat_tc_fits(a)) {
+      const int m = a.fu ? a.mu : a.mv;
+      const uint64_t dims[2] = {(uint64_t)m, (uint64_t)(a.fu ? a.nu : a.nv)};
+      const uint64_t strides[1] = {(uint64_t)m * 4};
+      const uint32_t box[2] = {32, 64};
+      CUtensorMap map_f;
+      NNC_TRY(tma::encode_f32(&map_f, a.fu ? a.fu : a.fv, 2, dims, strides, box));
+      const size_t smem = sizeof(float) * (256 + tc_block_ring_floats(1) + al4(a.mu * a.mu) +
+                                           al4(a.mv * a.mv) + 3 * al4(a.mu * a.mv));
+      if (a.tc == 3) {
+        NNC_TRY(set_smem(hmat_tc_kernel<3>, smem));
+        hmat_tc_kernel<3><<<a.mp, kThreads, smem, s>>>(a, map_f);
+      } else {
+        NNC_TRY(set_smem(hmat_tc_kernel<1>, smem));
+        hmat_tc_kernel<1><<<a.mp, kThreads, smem, s>>>(a, map_f);
+      }
+      note_launch(s);
+      NNC_CUDA_TRY(cudaGetLastError());
+      return NNC_OK;
+    }
+  }
   const size_t st_u = a.fu ? gemm_stage_elems(a.mu, a.mu, (int)sizeof(T), (int)a.nu) : 0;
   const size_t st_v = a.fv ? gemm_stage_elems(a.mv, a.mv, (int)sizeof(T), (int)a.nv) : 0;
   const int64_t guv = (int64_t)a.mp * a.mu * a.mv;
@@ -1416,18 +1660,58 @@ int launch_p1_rows(const T* in, int m1, int64_t N2, int64_t N3, T* out, cudaStre
   return NNC_OK;
 }
 
+// core_a_tc_kernel's shapes: every m <= 32, m2 and m3 multiples of 4 (the
+// rows of F3 and Y3 16-byte aligned).
+static bool core_tc_fits(const CoreArgs<float>& a) {
+  return a.tc && a.err && a.m1 >= 1 && a.m1 <= 32 && a.m2 >= 4 && a.m2 <= 32 && a.m3 >= 4 &&
+         a.m3 <= 32 && a.m2 % 4 == 0 && a.m3 % 4 == 0 && a.n3 >= 1 && a.n3 < (1LL << 31) &&
+         al16p(a.F3) && al16p(a.Y3);
+}
+
 template <typename T>
 int launch_core(const CoreArgs<T>& a, cudaStream_t s) {
   if (a.m1 > 64 || a.m2 > 64 || a.m3 > 64) return NNC_ERR_UNSUPPORTED;
   const int bc = a.m2 * a.m3;
-  const size_t st3 = gemm_stage_elems(a.m3, a.m3, (int)sizeof(T), (int)a.n3);
-  const size_t stm = gemm_stage_elems(a.m2, a.m3, (int)sizeof(T), (int)a.n3);
-  const size_t smem_a = sizeof(T) * ((st3 > stm ? st3 : stm) + al4(a.m2 * a.m2) +
-                                     al4(a.m3 * a.m3) + 3 * al4(bc));
-  NNC_TRY(set_smem(core_a_kernel<T>, smem_a));
-  core_a_kernel<T><<<a.m1, kThreads, smem_a, s>>>(a);
-  note_launch(s);
-  NNC_CUDA_TRY(cudaGetLastError());
+  bool tc_done = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (core_tc_fits(a)) {
+      CUtensorMap map_f3, map_y3;
+      {
+        const uint64_t dims[2] = {(uint64_t)a.m3, (uint64_t)a.n3};
+        const uint64_t strides[1] = {(uint64_t)a.m3 * 4};
+        const uint32_t box[2] = {32, 64};
+        NNC_TRY(tma::encode_f32(&map_f3, a.F3, 2, dims, strides, box));
+      }
+      {  // Y3 laid out (N3, m1, m2): entry (b, k, a) of the map
+        const uint64_t dims[3] = {(uint64_t)a.m2, (uint64_t)a.n3, (uint64_t)a.m1};
+        const uint64_t strides[2] = {(uint64_t)a.m1 * a.m2 * 4, (uint64_t)a.m2 * 4};
+        const uint32_t box[3] = {32, 64, 1};
+        NNC_TRY(tma::encode_f32(&map_y3, a.Y3, 3, dims, strides, box));
+      }
+      const size_t smem = sizeof(float) * (256 + tc_block_ring_floats(2) + al4(a.m2 * a.m2) +
+                                           al4(a.m3 * a.m3) + 3 * al4(bc));
+      if (a.tc == 3) {
+        NNC_TRY(set_smem(core_a_tc_kernel<3>, smem));
+        core_a_tc_kernel<3><<<a.m1, kThreads, smem, s>>>(a, map_f3, map_y3);
+      } else {
+        NNC_TRY(set_smem(core_a_tc_kernel<1>, smem));
+        core_a_tc_kernel<1><<<a.m1, kThreads, smem, s>>>(a, map_f3, map_y3);
+      }
+      note_launch(s);
+      NNC_CUDA_TRY(cudaGetLastError());
+      tc_done = true;
+    }
+  }
+  if (!tc_done) {
+    const size_t st3 = gemm_stage_elems(a.m3, a.m3, (int)sizeof(T), (int)a.n3);
+    const size_t stm = gemm_stage_elems(a.m2, a.m3, (int)sizeof(T), (int)a.n3);
+    const size_t smem_a = sizeof(T) * ((st3 > stm ? st3 : stm) + al4(a.m2 * a.m2) +
+                                       al4(a.m3 * a.m3) + 3 * al4(bc));
+    NNC_TRY(set_smem(core_a_kernel<T>, smem_a));
+    core_a_kernel<T><<<a.m1, kThreads, smem_a, s>>>(a);
+    note_launch(s);
+    NNC_CUDA_TRY(cudaGetLastError());
+  }
   const int64_t g = (int64_t)a.m1 * bc;
   const size_t smem_b = sizeof(T) * (al4(bc) + (core_in_smem<T>(g) ? (size_t)g : 0));
   NNC_TRY(set_smem(core_b_kernel<T>, smem_b));

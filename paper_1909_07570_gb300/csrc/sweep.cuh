@@ -77,6 +77,11 @@ struct HArgs {
   T* sv_out;
   T* H;                 // mp x mp
   T* Wout;              // optional: the W slices, laid out like G
+  // FP32 only: the Gram on the tensor cores (UpdArgs::tc's values) when the
+  // shape allows it (mp, mu, mv <= 32, the factor's rows 16-byte aligned);
+  // err as UpdArgs::err (required for that form).
+  int tc;
+  int* err;
 };
 
 template <typename T>
@@ -105,6 +110,10 @@ struct CoreArgs {
   int* counter;         // trace_record pair: entries so far, first non-finite sweep
   int m1, m2, m3;
   double eps;
+  // FP32 only: S3 and M on the tensor cores (UpdArgs::tc's values) when the
+  // shape allows it (m <= 32, m2 and m3 multiples of 4); err as UpdArgs::err.
+  int tc;
+  int* err;
 };
 template <typename T>
 int launch_upd12(const UpdArgs<T>& a, cudaStream_t s);
