@@ -239,8 +239,12 @@ typedef struct {
  * nncp_core_fit. A batch holding a large tensor (16384 entries or more, such
  * as X itself in Alg. 2, e.g. 40 x 40 x 40) runs with the tensors read twice
  * per sweep from global memory when every job is 3-way with r <= 16 and its
- * arrays fit one block; a batch whose state does not fit shared memory and
- * that this cannot take is UNSUPPORTED. The same holds for nncp_core_fit.
+ * arrays fit one block; when, besides, each job's slabs fit a block and one
+ * cluster of eight blocks per job fits on the GPU at once (a few large fits,
+ * such as the 32 x 32 x 32 core of Alg. 1), each job runs on such a cluster,
+ * its blocks sharing the sweep through distributed shared memory. A batch
+ * whose state does not fit shared memory and that neither form can take is
+ * UNSUPPORTED. The same holds for nncp_core_fit.
  *
  *  jobs       host array of n_jobs descriptors (copied by the call)
  *  rel_errs   device array of n_jobs doubles, or NULL: final relative error
