@@ -212,7 +212,11 @@ def test_ntd4_limits():
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("m,r", [((5, 6, 7), 4), ((20, 20, 20), 10), ((3, 4, 2, 5), 3),
-                                 ((32, 32, 32), 16)])
+                                 ((32, 32, 32), 16),
+                                 # one thread-block cluster per fit (16384 entries or more,
+                                 # 3-way, r <= 16): the last CTAs' slabs short or empty,
+                                 # ranks that are not multiples of 4, the threshold itself
+                                 ((27, 31, 26), 5), ((40, 24, 33), 13), ((64, 16, 16), 8)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_nncp_core_fit(m, r, dtype):
     rng = np.random.default_rng(sum(m) + r)
@@ -231,6 +235,38 @@ def test_nncp_core_fit(m, r, dtype):
         for a, b in zip(B, Bo):
             np.testing.assert_allclose(_np(a), b, rtol=2e-3, atol=1e-5 * np.abs(b).max())
         assert abs(err - tro[-1]) < 1e-5
+
+
+@pytest.mark.parametrize("count", [3, 20])
+def test_nncp_batched_large_cores(count):
+    # Large 3-way cores: a few run one cluster each (3 x 8 CTAs), a batch whose
+    # clusters would not all fit on the GPU at once one block each (20 x 8 CTAs
+    # > the SM count); either way every fit matches the oracle, and a single
+    # fit of a batch of three gives the batch's bits.
+    rng = np.random.default_rng(40 + count)
+    problems, ref = [], []
+    for i in range(count):
+        m = tuple(int(v) for v in rng.integers(26, 34, size=3))
+        r = int(rng.integers(3, 17))
+        G0 = rng.random(m)
+        B0 = inputs.initial_cp(m, r, 300 + i)
+        problems.append((_t(G0, torch.float32), [_t(b, torch.float32) for b in B0]))
+        ref.append((G0, B0))
+    errs = native.nncp_core_fit_batched(problems, 25).cpu().numpy()
+    for i in range(0, count, 4 if count > 3 else 1):
+        G0, B0 = ref[i]
+        Bo, tro = orc.nncp_fit(G0, B0, 25)
+        assert abs(errs[i] - tro[-1]) < 1e-5, i
+        for a, b in zip(problems[i][1], Bo):
+            np.testing.assert_allclose(_np(a), b, rtol=2e-3, atol=1e-5 * np.abs(b).max())
+    if count == 3:
+        G0, B0 = ref[1]
+        G = _t(G0, torch.float32)
+        B = [_t(b, torch.float32) for b in B0]
+        e = native.nncp_core_fit(G, B, 25)
+        assert e == errs[1]
+        for a, b in zip(B, problems[1][1]):
+            np.testing.assert_array_equal(_np(a), _np(b))
 
 
 def test_nncp_batched_matches_single_fits():

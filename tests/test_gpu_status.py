@@ -45,11 +45,13 @@ def _dev(problems, dtype=torch.float32):
              [torch.tensor(b, dtype=dtype, device="cuda") for b in B]) for G, B in problems]
 
 
-@pytest.mark.parametrize("dims", [None, (30, 30, 30)])
-def test_nan_core_marks_only_its_fit(dims):
+@pytest.mark.parametrize("dims,count", [(None, 11), ((30, 30, 30), 11), ((30, 30, 30), 20)])
+def test_nan_core_marks_only_its_fit(dims, count):
     # dims None: small cores, the one-pass kernel; 30^3 cores (27,000 entries,
-    # 3-way, r <= 16): the two-pass kernel.
-    probs = _problems(11, 9, dims)
+    # 3-way, r <= 16): the two-pass sweep, as one thread-block cluster per fit
+    # (11 fits) or, when the clusters would not all fit on the GPU at once (20
+    # fits), one block per fit.
+    probs = _problems(11, count, dims)
     ref = _dev(probs)
     native.nncp_core_fit_batched(ref, 30)
     bad = _dev(probs)
