@@ -25,6 +25,7 @@
 // MT_n does not involve mode n, so one Z_n serves both blocks of mode n; the
 // Gauss-Seidel order still needs only two passes over X per step (T_last before
 // mode 1, T_first after mode d-1).
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -863,6 +864,26 @@ int nmf_fit(const T* A, int64_t N, int r, int m, int iters, double eps, T* F, T*
   return NNC_OK;
 }
 
+namespace {
+// A side stream and a fork/join pair of events for the branches captured in a
+// replayed sweep (each record of an event marks the point the next wait joins).
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  int init() {
+    NNC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    return NNC_OK;
+  }
+  ~SideStream() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (s) cudaStreamDestroy(s);
+  }
+};
+}  // namespace
+
 // nnTD of a d-way X (d = 3 or 4) by MU sweeps (Alg. 1, first step), built on
 // the mode-product machinery above with F := F^(k). A sweep updates
 // F^(1), ..., F^(d), then G:
@@ -915,8 +936,27 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
   for (int k = 0; k < d; ++k) NNC_TRY(launch_gram<T>(F[k], dims[k], m[k], S[k], s));
   double* tr = trace ? trace : dummy;
   const int stride = trace ? 1 : 0;
+  // The H_n branch (the core times the Grams, then its unfolding product)
+  // needs neither Z_n nor the passes, so it runs on a side stream beside the
+  // mode products and contractions of Z_n, with split-K scratch of its own.
+  // (Leaving the passes SMs for it as well cost more than it saved: 0, 16 and
+  // 32 SMs left free gave 713, 748 and 787 us per sweep at 128^3 x 64.)
+  T* split2 = nullptr;
+  NNC_TRY(sc.get(&split2, w.split_cap));
+  SideStream side;
+  NNC_TRY(side.init());
+  auto fork = [&](cudaStream_t cs) -> int {
+    NNC_CUDA_TRY(cudaEventRecord(side.fork, cs));
+    NNC_CUDA_TRY(cudaStreamWaitEvent(side.s, side.fork, 0));
+    return NNC_OK;
+  };
+  auto join = [&](cudaStream_t cs) -> int {
+    NNC_CUDA_TRY(cudaEventRecord(side.join, side.s));
+    NNC_CUDA_TRY(cudaStreamWaitEvent(cs, side.join, 0));
+    return NNC_OK;
+  };
   // out = G x_k S_k over the modes k != skip (all modes when skip < 0).
-  auto core_times_grams = [&](int skip, T* out, cudaStream_t cs) -> int {
+  auto core_times_grams = [&](int skip, T* out, T* c0, T* c1, T* split, cudaStream_t cs) -> int {
     const T* src = G;
     int left = 0;
     for (int k = 0; k < d; ++k) left += k != skip;
@@ -926,16 +966,30 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
       int64_t pre = 1, post = 1;
       for (int j = 0; j < k; ++j) pre *= m[j];
       for (int j = k + 1; j < d; ++j) post *= m[j];
-      NNC_CUDA_TRY(launch_ttm<T>(src, pre, m[k], post, S[k], m[k], 1, m[k], dst, w.split,
+      NNC_CUDA_TRY(launch_ttm<T>(src, pre, m[k], post, S[k], m[k], 1, m[k], dst, split,
                                  w.split_cap, cs));
       src = dst;
     }
     return NNC_OK;
   };
+  // H_n = unfold_n(G x_{k!=n} S_k) unfold_n(G)^T on the side stream, formed in
+  // M (free until the core update).
+  auto h_branch = [&](int n) -> int {
+    int64_t pre = 1, post = 1;
+    for (int j = 0; j < n; ++j) pre *= m[j];
+    for (int j = n + 1; j < d; ++j) post *= m[j];
+    NNC_TRY(core_times_grams(n, M, c0, c1, split2, side.s));
+    NNC_CUDA_TRY(launch_pair_contract<T>(M, G, pre, m[n], m[n], post, w.H, split2, w.split_cap,
+                                         side.s));
+    return NNC_OK;
+  };
   NNC_TRY(replay(iters, s, [&](cudaStream_t cs) -> int {
-    NNC_TRY(pass_last(w, F[d - 1], cs));
     const T* Z = nullptr;
     for (int n = 0; n < d; ++n) {
+      // H_n beside Z_n, forked after the previous mode's Gram.
+      NNC_TRY(fork(cs));
+      NNC_TRY(h_branch(n));
+      if (n == 0) NNC_TRY(pass_last(w, F[d - 1], cs));
       if (n == d - 1) NNC_TRY(pass_first(w, F[0], cs));
       NNC_TRY(z_chain(w, n, F, &Z, cs));
       int64_t pre = 1, post = 1;
@@ -943,21 +997,21 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
       for (int j = n + 1; j < d; ++j) post *= m[j];
       NNC_CUDA_TRY(launch_pair_contract<T>(Z, G, pre, (int)dims[n], m[n], post, num, w.split,
                                            w.split_cap, cs));
-      // H_n from G x_{k!=n} S_k, formed in M (free until the core update).
-      NNC_TRY(core_times_grams(n, M, cs));
-      NNC_CUDA_TRY(launch_pair_contract<T>(M, G, pre, m[n], m[n], post, w.H, w.split,
-                                           w.split_cap, cs));
+      NNC_TRY(join(cs));
       NNC_CUDA_TRY(launch_factor_mu<T>(F[n], num, w.H, dims[n], m[n], eps, cs));
       NNC_TRY(launch_gram<T>(F[n], dims[n], m[n], S[n], cs));
       if (n == 0 && d > 2) NNC_TRY(make_u0(w, F[0], cs));
     }
-    // Core: Z (= Z_d) x_d F^(d)T with the updated F^(d).
+    // Core: Z (= Z_d) x_d F^(d)T with the updated F^(d), beside the
+    // denominator G x_k S_k of the old core.
+    NNC_TRY(fork(cs));
+    NNC_TRY(core_times_grams(-1, D, c0, c1, split2, side.s));
     const int64_t lead = nc / m[d - 1];
     NNC_CUDA_TRY(launch_ttm<T>(Z, lead, (int)dims[d - 1], 1, F[d - 1], m[d - 1], 1, m[d - 1], M,
                                w.split, w.split_cap, cs));
-    NNC_TRY(core_times_grams(-1, D, cs));
+    NNC_TRY(join(cs));
     NNC_CUDA_TRY(launch_elementwise_mu<T>(G, M, D, nc, eps, cs));
-    NNC_TRY(core_times_grams(-1, D, cs));
+    NNC_TRY(core_times_grams(-1, D, c0, c1, w.split, cs));
     NNC_CUDA_TRY(
         launch_residual_identity<T>(M, G, D, nc, w.stats, tr, stride, counter, idpart, cs));
     return NNC_OK;
