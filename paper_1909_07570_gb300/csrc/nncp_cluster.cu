@@ -33,7 +33,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kCl = 8;  // CTAs per fit (the portable cluster size)
-constexpr int kClThreads = 256;
+constexpr int kClThreads = 512;
 
 __host__ __device__ constexpr size_t al4(size_t x) { return (x + 3) & ~static_cast<size_t>(3); }
 
