@@ -86,7 +86,11 @@ def test_mode_product_tensor_cores_rejects_middle_mode():
 
 @pytest.mark.parametrize("dims,m,iters,refine", [((96, 80, 128), (8, 10, 12), 60, 10),
                                                  ((150, 64, 200), (16, 12, 20), 40, 0),
-                                                 ((96, 128, 128), (8, 10, 12), 60, 10)])
+                                                 ((96, 128, 128), (8, 10, 12), 60, 10),
+                                                 # every update, H and core kernel on the
+                                                 # tensor cores, odd row counts, ragged
+                                                 # contraction lengths
+                                                 ((151, 72, 99), (12, 16, 28), 40, 5)])
 def test_ntd_bf16_refine_parity(dims, m, iters, refine):
     X, _, F0, G0, _ = inputs.small_problem(dims, 6, m, 4, seed=606, dist="exponential")
     Xd = torch.tensor(X, dtype=torch.float32, device="cuda")

@@ -54,9 +54,13 @@ def test_ntd_one_sweep_fp64_elementwise(dims, m):
 
 # N2 = 128 and 256 (with N3 % 4 == 0) take the tensor-core pass that also forms
 # the mode-1 contraction per tile: m2 % 4 != 0, m3 % 4 != 0 and m = 32 included.
+# The last two shapes run every factor update, H kernel and core kernel on the
+# tensor cores (m <= 32, multiples of 4) with odd row counts (a last block of
+# one row) and contraction lengths off multiples of 64 and of 8.
 @pytest.mark.parametrize("dims,m", [((37, 29, 23), (5, 6, 7)), ((70, 45, 133), (9, 17, 20)),
                                     ((257, 130, 97), (32, 24, 16)), ((70, 66, 68), (64, 64, 64)),
-                                    ((23, 256, 44), (5, 7, 6)), ((19, 128, 40), (4, 32, 32))])
+                                    ((23, 256, 44), (5, 7, 6)), ((19, 128, 40), (4, 32, 32)),
+                                    ((257, 130, 100), (32, 24, 16)), ((45, 67, 36), (12, 20, 8))])
 def test_ntd_one_sweep_fp32_elementwise(dims, m):
     X, _, F0, G0, _ = inputs.small_problem(dims, 5, m, 3, seed=202, zero_frac=0.2, noise=0.02)
     err, tr, F, G = _run_ntd(X, F0, G0, 1, torch.float32)
