@@ -23,7 +23,8 @@
 // Persistent CTAs, at most one per SM, each looping over 128-row tiles with
 // warp roles:
 //   warp 0        TMA producer: A tile and B slice of each K stage (a ring of as
-//                 many stages as fit in shared memory, at most 8)
+//                 many stages as fit in shared memory, at most 8); the A tiles
+//                 with an L2 evict-first hint (X is read once per pass)
 //   warp 1        MMA issuer (one thread): tcgen05.mma into a double-buffered
 //                 TMEM accumulator; tcgen05.commit frees stages and publishes
 //                 finished accumulators
@@ -104,6 +105,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     }
   }
   return true;
+}
+
+// An L2 policy that makes lines evicted first: the A tiles of a pass (X, its
+// copies) are read once, so they should not push out the data the kernels
+// after the pass read again (the pass result, the shares, factors and core).
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* tm, int x, int y,
+                                                 uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y,
@@ -315,19 +333,21 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       // Stages this CTA runs: tiles blockIdx.x, blockIdx.x + gridDim.x, ...
       const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
       const int64_t total = my_tiles * nk;
+      const uint64_t stream_once = l2_evict_first();
       auto load_a = [&](int it_, unsigned char* st, uint64_t* bar) {
         const int64_t tile = blockIdx.x + static_cast<int64_t>(it_ / nk) * gridDim.x;
         const int m0 = static_cast<int>(tile * 128);
         const int k0 = (it_ % nk) * L::kKStage;
         if (!kMN) {
-          tma_load_2d(st, &tmA, k0, m0, bar);
+          tma_load_2d_hint(st, &tmA, k0, m0, bar, stream_once);
         } else {
           // 128 columns in 128-byte pieces: 2 (BF16) or 4 (TF32) boxes.
           constexpr int pieces = L::kTf32 ? 4 : 2;
           constexpr int piece_cols = 128 / pieces;
 #pragma unroll
           for (int h = 0; h < pieces; ++h)
-            tma_load_2d(st + h * (kTileBytes / pieces), &tmA, m0 + h * piece_cols, k0, bar);
+            tma_load_2d_hint(st + h * (kTileBytes / pieces), &tmA, m0 + h * piece_cols, k0, bar,
+                             stream_once);
         }
       };
       auto load_b = [&](int it_, unsigned char* st, uint64_t* bar) {
