@@ -318,8 +318,10 @@ int nncp_core_fit_batched_noalloc(int n_jobs, const nncp_job* jobs, int precisio
  *  F          device, dims[mode] x Q row-major; 1 <= Q <= 64
  *  out        device, dims with dims[mode] replaced by Q, C order
  *  precision  NNC_FP64 (double), NNC_FP32_SIMT (float): SIMT kernels.
- *             NNC_FP32 (float): TF32x3 tensor cores for modes 0 and 2 (SIMT
- *             for mode 1 or when N3 % 4 != 0).
+ *             NNC_FP32 (float): TF32x3 tensor cores: tcgen05 passes for
+ *             modes 0 and 2, mma.sync column products for mode 1 when
+ *             N3 % 4 == 0 and Q <= 32; SIMT otherwise (N3 % 4 != 0, or
+ *             mode 1 with Q > 32).
  *             NNC_BF16_REFINE (float X, F, out): tensor cores on BF16 copies
  *             of X and F (X scaled per mode-1 slice by a power of two, which
  *             changes no rounding) with FP32 accumulation; modes 0 and 2 only.

@@ -476,9 +476,10 @@ int nnc_mode_product(const void* X, int d, const int64_t* dims, int mode, const 
   } else if (precision == NNC_FP32 || precision == NNC_FP32_SIMT) {
     float* split = nullptr;
     NNC_TRY(sc.get(&split, cap));
-    NNC_CUDA_TRY(launch_ttm<float>(static_cast<const float*>(X), L, J, C,
-                                   static_cast<const float*>(F), Q, 1, Q, static_cast<float*>(out),
-                                   split, cap, s));
+    // NNC_FP32, mode 1: the column product on the tensor cores where it applies.
+    auto ttm = precision == NNC_FP32 ? launch_ttm_tc<float> : launch_ttm<float>;
+    NNC_CUDA_TRY(ttm(static_cast<const float*>(X), L, J, C, static_cast<const float*>(F), Q, 1, Q,
+                     static_cast<float*>(out), split, cap, s));
   } else {
     return NNC_ERR_INVALID_ARG;
   }

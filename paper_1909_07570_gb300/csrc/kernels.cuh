@@ -18,6 +18,14 @@ cudaError_t launch_ttm(const T* Y, int64_t L, int J, int64_t C, const T* Fm, int
                        int64_t fs_q, int Q, T* out, T* split_buf, size_t split_cap,
                        cudaStream_t s);
 
+// The same mode product on the tensor cores for float tensors with C > 1,
+// C % 4 == 0, Q <= 32 and Y 16-byte aligned (TF32x3 operands on mma.sync,
+// FP32-accurate); every other case, and double, goes to launch_ttm.
+template <typename T>
+cudaError_t launch_ttm_tc(const T* Y, int64_t L, int J, int64_t C, const T* Fm, int64_t fs_j,
+                          int64_t fs_q, int Q, T* out, T* split_buf, size_t split_cap,
+                          cudaStream_t s);
+
 // out[i, a] = sum_{l, c} Y[(l * NI + i) * C + c] * G[(l * MA + a) * C + c]
 // Y is (L, NI, C), G is (L, MA, C), out is NI x MA (MA <= 64, L C < 2^31). It
 // is the product of the mode-n unfoldings unfold_n(Y) unfold_n(G)^T when the

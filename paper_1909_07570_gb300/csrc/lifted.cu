@@ -400,8 +400,9 @@ int pass_first(Work<T>& w, const T* F1, cudaStream_t s) {
 template <typename T>
 int make_u0(Work<T>& w, const T* F1, cudaStream_t s) {
   const int d = w.d;
-  NNC_CUDA_TRY(launch_ttm<T>(w.Tlast, 1, (int)w.N[0], prod(w.N, 1, d - 1) * w.m[d - 1], F1,
-                             w.m[0], 1, w.m[0], w.U0, w.split, w.split_cap, s));
+  auto ttm = w.tc ? launch_ttm_tc<T> : launch_ttm<T>;
+  NNC_CUDA_TRY(ttm(w.Tlast, 1, (int)w.N[0], prod(w.N, 1, d - 1) * w.m[d - 1], F1, w.m[0], 1,
+                   w.m[0], w.U0, w.split, w.split_cap, s));
   return NNC_OK;
 }
 
@@ -432,10 +433,11 @@ int z_chain(Work<T>& w, int n, T* const* F, const T** zout, cudaStream_t s) {
   }
   T* bufs[2] = {w.Z0, w.Z1};
   int b = 0;
+  auto ttm = w.tc ? launch_ttm_tc<T> : launch_ttm<T>;
   for (int k = first; k < last; ++k) {
     if (k == n) continue;
-    NNC_CUDA_TRY(launch_ttm<T>(src, prod(cur, 0, k), (int)cur[k], prod(cur, k + 1, d), F[k],
-                               w.m[k], 1, w.m[k], bufs[b], w.split, w.split_cap, s));
+    NNC_CUDA_TRY(ttm(src, prod(cur, 0, k), (int)cur[k], prod(cur, k + 1, d), F[k], w.m[k], 1,
+                     w.m[k], bufs[b], w.split, w.split_cap, s));
     cur[k] = w.m[k];
     src = bufs[b];
     b ^= 1;

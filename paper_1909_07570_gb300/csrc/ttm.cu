@@ -16,11 +16,15 @@
 //     tiling, with the block's 256 TC flattened columns staged through a
 //     3-deep cp.async ring of 16 rows j, so that two chunks are in flight
 //     while the third is consumed.
-// Both accumulate in T and, when one pass would not fill the GPU, split J
+//   * ttm_cols_tc (float, C % 4 == 0, Q <= 32): the column product as a GEMM on
+//     the tensor cores (TF32x3 on mma.sync, FP32-accurate), for the mode
+//     products of the compressed tensors in the tensor-core paths.
+// All accumulate in T and, when one pass would not fill the GPU, split J
 // across blocks; partial sums are then added in split order (deterministic).
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "mma32.cuh"
 
 namespace nnc {
 namespace {
@@ -275,6 +279,159 @@ ttm_cols_pipe_kernel(const T* __restrict__ Y, int64_t L, int J, int64_t C, int j
   }
 }
 
+// Tensor-core column mode product (float, C % 4 == 0, Q <= 32): per block the
+// GEMM D (kTcCols columns (l, c) x QP) = A (columns x rows j) B (rows j x QP),
+// A the staged rows of Y (a column is an MMA row, j the MMA k), B the rows of
+// Fm, on mma.sync m16n8k8 with TF32x3 operands (x = x_hi + x_lo, the three
+// products lo*hi, hi*lo, hi*hi; the dropped lo*lo is below FP32 rounding) and
+// FP32 accumulation. Each chunk of kTcBJ rows is summed in a fresh fragment
+// and then added to the running sum with round-to-nearest, so the tensor
+// core's truncating accumulation only ever acts on one chunk's sum. The rows
+// are staged as in ttm_cols_pipe (a cp.async ring; rows and columns past the
+// ends are zeros). Warp w owns columns 32 w .. 32 w + 31 (two M-tiles).
+constexpr int kTcCols = 256;
+constexpr int kTcBJ = 16;
+constexpr int kTcStages = 4;
+constexpr int kTcYS = kTcCols + 8;  // row stride: the A fragments hit 32 distinct banks
+
+template <int QP>
+__host__ __device__ constexpr int tc_fs() { return QP == 24 ? 24 : QP + 8; }
+template <int QP>
+constexpr size_t tc_smem_bytes() {
+  return (size_t)kTcStages * kTcBJ * (kTcYS + tc_fs<QP>()) * sizeof(float);
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = mma32::tf32_rn(x);
+  lo = mma32::tf32_rn(x - __uint_as_float(hi));
+}
+
+template <int QP>
+__global__ void __launch_bounds__(kColsThreads, 2)
+ttm_cols_tc_kernel(const float* __restrict__ Y, int64_t L, int J, int64_t C, int j_per_split,
+                   const float* __restrict__ Fm, int64_t fs_j, int64_t fs_q, int Q,
+                   float* __restrict__ out) {
+  static_assert(kColsThreads == 256 && kTcCols == 256, "eight warps of 32 columns");
+  constexpr int NT = QP / 8;
+  constexpr int FS = tc_fs<QP>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ys = reinterpret_cast<float*>(smem_raw);  // [stage][kTcBJ][kTcYS]
+  float* Fs = Ys + kTcStages * kTcBJ * kTcYS;       // [stage][kTcBJ][FS]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int64_t ncols = L * C;
+  const int64_t col0 = (int64_t)blockIdx.x * kTcCols;
+  const int jbeg = blockIdx.y * j_per_split;
+  const int jend = min(J, jbeg + j_per_split);
+  const int nchunks = (jend - jbeg + kTcBJ - 1) / kTcBJ;
+
+  // This thread's copies: 16-byte vector v of rows jr, jr + 4, ... of a chunk
+  // (a vector never crosses a row (l, j) because C % 4 == 0).
+  const int v = tid & 63, jr = tid >> 6;
+  const int64_t vcol = col0 + (int64_t)v * 4;
+  const bool cok = vcol < ncols;
+  const int64_t vl = cok ? vcol / C : 0;
+  const float* ysrc = Y + vl * (int64_t)J * C + (cok ? vcol - vl * C : 0);
+  auto issue = [&](int chunk) {
+    const int slot = chunk % kTcStages;
+    const int j0 = jbeg + chunk * kTcBJ;
+    float* ys = Ys + slot * kTcBJ * kTcYS + v * 4;
+#pragma unroll
+    for (int jj = jr; jj < kTcBJ; jj += 4) {
+      const int j = j0 + jj;
+      const bool ok = cok && j < jend;
+      cp_vec(ys + jj * kTcYS, ok ? ysrc + (int64_t)j * C : Y, ok ? 4 : 0);
+    }
+    float* fs = Fs + slot * kTcBJ * FS;
+    for (int e = tid; e < kTcBJ * QP; e += kColsThreads) {
+      const int jj = e / QP, q = e % QP;
+      const int j = j0 + jj;
+      const bool ok = q < Q && j < jend;
+      cp_elem(fs + jj * FS + q, ok ? Fm + (j * fs_j + q * fs_q) : Fm, ok);
+    }
+  };
+
+  float acc[2][NT][4], part[2][NT][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][n][e] = part[i][n][e] = 0.f;
+
+#pragma unroll
+  for (int p = 0; p < kTcStages - 1; ++p) {
+    if (p < nchunks) issue(p);
+    cp_commit();
+  }
+  for (int it = 0; it < nchunks; ++it) {
+    if (it + kTcStages - 1 < nchunks) issue(it + kTcStages - 1);
+    cp_commit();
+    cp_wait<kTcStages - 1>();
+    __syncthreads();
+    const int slot = it % kTcStages;
+    const float* ys = Ys + slot * kTcBJ * kTcYS + warp * 32 + g;
+    const float* fs = Fs + slot * kTcBJ * FS + g;
+#pragma unroll
+    for (int ks = 0; ks < kTcBJ / 8; ++ks) {
+      const float* y0 = ys + (ks * 8 + t) * kTcYS;
+      const float* y1 = y0 + 4 * kTcYS;
+      uint32_t ah[2][4], al[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        split_tf32(y0[16 * i], ah[i][0], al[i][0]);
+        split_tf32(y0[16 * i + 8], ah[i][1], al[i][1]);
+        split_tf32(y1[16 * i], ah[i][2], al[i][2]);
+        split_tf32(y1[16 * i + 8], ah[i][3], al[i][3]);
+      }
+      const float* f0 = fs + (ks * 8 + t) * FS;
+      const float* f1 = f0 + 4 * FS;
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        uint32_t bh0, bl0, bh1, bl1;
+        split_tf32(f0[8 * n], bh0, bl0);
+        split_tf32(f1[8 * n], bh1, bl1);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          mma32::mma_tf32(part[i][n], al[i], bh0, bh1);
+          mma32::mma_tf32(part[i][n], ah[i], bl0, bl1);
+          mma32::mma_tf32(part[i][n], ah[i], bh0, bh1);
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int n = 0; n < NT; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          acc[i][n][e] += part[i][n][e];
+          part[i][n][e] = 0.f;
+        }
+  }
+
+  // D fragment: entry e of tile (i, n) is column 32 warp + 16 i + g + 8 (e / 2),
+  // q = 8 n + 2 t + e % 2.
+  float* o = out + (int64_t)blockIdx.y * L * Q * C;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t col = col0 + warp * 32 + 16 * i + g + 8 * h;
+      if (col >= ncols) continue;
+      const int64_t l = col / C;
+      float* ot = o + l * Q * C + (col - l * C);
+#pragma unroll
+      for (int n = 0; n < NT; ++n)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int q = 8 * n + 2 * t + u;
+          if (q < Q) ot[(int64_t)q * C] = acc[i][n][2 * h + u];
+        }
+    }
+}
+
 template <typename T>
 __global__ void reduce_splits_kernel(const T* __restrict__ part, int splits, int64_t n,
                                      T* __restrict__ out) {
@@ -385,6 +542,30 @@ cudaError_t ttm_dispatch(const T* Y, int64_t L, int J, int64_t C, const T* Fm, i
   return cudaGetLastError();
 }
 
+template <int QP>
+cudaError_t ttm_tc_dispatch(const float* Y, int64_t L, int J, int64_t C, const float* Fm,
+                            int64_t fs_j, int64_t fs_q, int Q, float* out, float* split_buf,
+                            size_t split_cap, cudaStream_t s) {
+  const int64_t ncols = L * C, out_elems = L * Q * C;
+  const int64_t blocks = ceil_div(ncols, kTcCols);
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  int per = J;
+  const int splits = choose_splits(blocks, J, out_elems, split_cap, kColsBJ, &per);
+  float* dst = splits > 1 ? split_buf : out;
+  constexpr size_t smem = tc_smem_bytes<QP>();
+  const cudaError_t e0 = raise_smem_limit((const void*)ttm_cols_tc_kernel<QP>, smem);
+  if (e0 != cudaSuccess) return e0;
+  dim3 grid((unsigned)blocks, (unsigned)splits);
+  ttm_cols_tc_kernel<QP><<<grid, kColsThreads, smem, s>>>(Y, L, J, C, per, Fm, fs_j, fs_q, Q, dst);
+  note_launch(s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  const int64_t rb = ceil_div(out_elems, 256) < 4096 ? ceil_div(out_elems, 256) : 4096;
+  reduce_splits_kernel<float><<<(unsigned)rb, 256, 0, s>>>(split_buf, splits, out_elems, out);
+  note_launch(s);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 template <typename T>
@@ -401,6 +582,23 @@ cudaError_t launch_ttm(const T* Y, int64_t L, int J, int64_t C, const T* Fm, int
 }
 
 template <typename T>
+cudaError_t launch_ttm_tc(const T* Y, int64_t L, int J, int64_t C, const T* Fm, int64_t fs_j,
+                          int64_t fs_q, int Q, T* out, T* split_buf, size_t split_cap,
+                          cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (L > 0 && J > 0 && C > 1 && Q > 0 && Q <= 32 && C % 4 == 0 &&
+        reinterpret_cast<uintptr_t>(Y) % 16 == 0) {
+      if (Q <= 16)
+        return ttm_tc_dispatch<16>(Y, L, J, C, Fm, fs_j, fs_q, Q, out, split_buf, split_cap, s);
+      if (Q <= 24)
+        return ttm_tc_dispatch<24>(Y, L, J, C, Fm, fs_j, fs_q, Q, out, split_buf, split_cap, s);
+      return ttm_tc_dispatch<32>(Y, L, J, C, Fm, fs_j, fs_q, Q, out, split_buf, split_cap, s);
+    }
+  }
+  return launch_ttm<T>(Y, L, J, C, Fm, fs_j, fs_q, Q, out, split_buf, split_cap, s);
+}
+
+template <typename T>
 cudaError_t launch_reduce_splits(const T* part, int splits, int64_t n, T* out, cudaStream_t s) {
   const int64_t blocks = ceil_div(n, 256) < 4096 ? ceil_div(n, 256) : 4096;
   reduce_splits_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(part, splits, n, out);
@@ -412,6 +610,12 @@ template cudaError_t launch_reduce_splits<float>(const float*, int, int64_t, flo
                                                  cudaStream_t);
 template cudaError_t launch_reduce_splits<double>(const double*, int, int64_t, double*,
                                                   cudaStream_t);
+template cudaError_t launch_ttm_tc<float>(const float*, int64_t, int, int64_t, const float*,
+                                          int64_t, int64_t, int, float*, float*, size_t,
+                                          cudaStream_t);
+template cudaError_t launch_ttm_tc<double>(const double*, int64_t, int, int64_t, const double*,
+                                           int64_t, int64_t, int, double*, double*, size_t,
+                                           cudaStream_t);
 template cudaError_t launch_ttm<float>(const float*, int64_t, int, int64_t, const float*, int64_t,
                                        int64_t, int, float*, float*, size_t, cudaStream_t);
 template cudaError_t launch_ttm<double>(const double*, int64_t, int, int64_t, const double*,

@@ -60,6 +60,30 @@ def test_mode_product_tf32x3_is_fp32_accurate(dims, Q):
         _close(Y.double().cpu().numpy(), ref, 1e-5)
 
 
+@pytest.mark.parametrize("dims,Q", [((37, 29, 24), 5), ((200, 150, 132), 20), ((64, 128, 2048), 24),
+                                    ((24, 128, 16), 16), ((9, 33, 8), 32), ((3, 1000, 4), 24),
+                                    ((11, 7, 4), 1), ((5, 300, 2), 24), ((20, 40, 12), 33)])
+def test_mode_product_middle_mode_tf32x3_is_fp32_accurate(dims, Q):
+    # Mode 1 (the middle mode, strided in memory) with NNC_FP32: the column
+    # product on mma.sync with TF32x3 operands, each 16-row chunk summed apart
+    # and added with round-to-nearest; N3 % 4 != 0 or Q > 32 take the SIMT
+    # kernel. Ragged column blocks (L N3 not a multiple of 256), ragged row
+    # chunks (N2 % 16 != 0) and the split-J launches of narrow grids included.
+    rng = np.random.default_rng(29 + Q + dims[1])
+    X = rng.random(dims) * np.exp2(rng.integers(-6, 7, size=(dims[0], 1, 1)))
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    X32 = Xd.double().cpu().numpy()
+    F = rng.random((dims[1], Q)).astype(np.float32).astype(np.float64)
+    ref = orc.mode_product(X32, F.T, 1)
+    Y = native.mode_product(Xd, torch.tensor(F, dtype=torch.float32, device="cuda"), 1,
+                            precision="fp32")
+    got = Y.double().cpu().numpy()
+    _close(got, ref, 1e-5)
+    # per slice too: the slices differ in magnitude by up to 2^12
+    for i in range(dims[0]):
+        _close(got[i], ref[i], 1e-5)
+
+
 @pytest.mark.parametrize("dims,Q", [((37, 29, 23), 5), ((200, 150, 130), 20), ((256, 256, 256), 32),
                                     ((70, 45, 600), 64), ((129, 3, 64), 17)])
 def test_mode_product_tensor_cores(dims, Q):
