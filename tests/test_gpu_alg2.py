@@ -43,7 +43,7 @@ def test_nncp_tensor_fit_fp64_matches_oracle(dims, r):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
-@pytest.mark.parametrize("dims,r", [((48, 40, 36), 6), ((12, 10, 9, 16), 3)])
+@pytest.mark.parametrize("dims,r", [((48, 40, 36), 6), ((12, 10, 9, 16), 3), ((4, 3, 128, 8), 3)])
 def test_nncp_tensor_fit_fp32_trace_matches_oracle(dims, r, precision):
     # With exact checkpoints at every sweep the trace is the explicit FP64
     # residual of each iterate: within the plain FP32 bound of the oracle, as

@@ -22,7 +22,11 @@ pytestmark = pytest.mark.gpu
 SHAPES = [((37, 29, 24), (5, 6, 7), 4),      # TF32x3 passes (N3 % 4 == 0)
           ((23, 17, 30), (4, 3, 5), 3),      # N3 % 4 != 0: SIMT passes
           ((12, 10, 9, 16), (3, 4, 2, 5), 3),
-          ((9, 14, 11, 8), (6, 2, 5, 3), 5)]
+          ((9, 14, 11, 8), (6, 2, 5, 3), 5),
+          # TF32x3 passes over X viewed as N1 x N2 N3 x N4 with N2 N3 a
+          # multiple of the 128-row tile, and ragged ranks
+          ((6, 5, 128, 12), (3, 4, 5, 6), 3),
+          ((4, 3, 256, 8), (3, 2, 24, 4), 2)]
 
 
 def _problem(dims, m, r, seed):
@@ -123,8 +127,9 @@ def test_pg_fit_fp64_matches_oracle(dims, m, r):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
-def test_pg_fit_fp32_trace_matches_oracle_and_descends(precision):
-    dims, m, r = (40, 36, 32), (6, 5, 7), 4
+@pytest.mark.parametrize("dims,m,r", [((40, 36, 32), (6, 5, 7), 4),
+                                      ((6, 5, 128, 12), (3, 4, 5, 6), 3)])
+def test_pg_fit_fp32_trace_matches_oracle_and_descends(precision, dims, m, r):
     X, F0, B0 = _problem(dims, m, r, 59)
     X32 = X.astype(np.float32).astype(np.float64)
     F32 = [f.astype(np.float32).astype(np.float64) for f in F0]

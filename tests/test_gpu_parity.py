@@ -154,7 +154,11 @@ def test_ntd4_one_sweep_fp64_elementwise(dims, m):
 
 # (20, 8, 16, 36) takes the TF32x3 tensor-core passes (X viewed as 20 x 128 x 36);
 # N4 = 13 is not a multiple of 4 and runs the SIMT passes; fp32_simt forces them.
+# N3 = 128 and 256: whole 128-row tiles of the pass X x_4 F4^T per (i, j), and
+# a mode-2 column product with a single row chunk.
 @pytest.mark.parametrize("dims,m,precision", [((20, 8, 16, 36), (4, 3, 5, 6), "fp32"),
+                                              ((6, 5, 128, 12), (3, 4, 5, 6), "fp32"),
+                                              ((4, 3, 256, 8), (3, 2, 24, 4), "fp32"),
                                               ((17, 9, 11, 13), (5, 4, 3, 2), "fp32"),
                                               ((20, 8, 16, 36), (4, 3, 5, 6), "fp32_simt")])
 def test_ntd4_fp32_sweep_and_trace(dims, m, precision):
