@@ -741,6 +741,57 @@ int replay(int count, cudaStream_t s, Body body, After after = After()) {
   return NNC_OK;
 }
 
+// Kernel nodes of a captured graph.
+int graph_kernels(cudaGraph_t graph, long long* kernels) {
+  size_t nn = 0;
+  NNC_CUDA_TRY(cudaGraphGetNodes(graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  NNC_CUDA_TRY(cudaGraphGetNodes(graph, nodes.data(), &nn));
+  *kernels = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    NNC_CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
+    if (ty == cudaGraphNodeTypeKernel) ++*kernels;
+  }
+  return NNC_OK;
+}
+
+// Captures `first`, `rest` and `last` (stream-ordered work on one private
+// stream) as three CUDA graphs and runs first once, rest count - 1 times and
+// last once, after the work queued on s (count >= 1).
+template <typename First, typename Rest, typename Last>
+int replay_pipelined(int count, cudaStream_t s, First first, Rest rest, Last last) {
+  if (count <= 0) return NNC_OK;
+  PgGraph g[3];
+  NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g[0].cs, cudaStreamNonBlocking));
+  NNC_CUDA_TRY(cudaEventCreateWithFlags(&g[0].fork, cudaEventDisableTiming));
+  NNC_CUDA_TRY(cudaEventCreateWithFlags(&g[0].join, cudaEventDisableTiming));
+  cudaStream_t cs = g[0].cs;
+  NNC_CUDA_TRY(cudaEventRecord(g[0].fork, s));
+  NNC_CUDA_TRY(cudaStreamWaitEvent(cs, g[0].fork, 0));
+  long long kernels[3] = {0, 0, 0};
+  auto capture = [&](int i, auto& body) -> int {
+    NNC_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const int st = body(cs);
+    const cudaError_t e = cudaStreamEndCapture(cs, &g[i].graph);
+    if (st != NNC_OK) return st;
+    NNC_CUDA_TRY(e);
+    NNC_CUDA_TRY(cudaGraphInstantiate(&g[i].exec, g[i].graph, 0));
+    return graph_kernels(g[i].graph, &kernels[i]);
+  };
+  NNC_TRY(capture(0, first));
+  NNC_TRY(capture(1, rest));
+  NNC_TRY(capture(2, last));
+  NNC_CUDA_TRY(cudaGraphLaunch(g[0].exec, cs));
+  for (int t = 1; t < count; ++t) NNC_CUDA_TRY(cudaGraphLaunch(g[1].exec, cs));
+  NNC_CUDA_TRY(cudaGraphLaunch(g[2].exec, cs));
+  note_graph_launches(kernels[0] + kernels[1] * (count - 1) + kernels[2]);
+  NNC_CUDA_TRY(cudaEventRecord(g[0].join, cs));
+  NNC_CUDA_TRY(cudaStreamWaitEvent(s, g[0].join, 0));
+  NNC_CUDA_TRY(cudaStreamSynchronize(cs));
+  return NNC_OK;
+}
+
 }  // namespace
 
 // nnCPD of X itself (Alg. 2, first step): the MU sweep of the core nnCPD with
@@ -872,15 +923,20 @@ namespace {
 struct SideStream {
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t m_ready = nullptr, g_ready = nullptr;  // the pending core update's steps
   int init() {
     NNC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     NNC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     NNC_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&m_ready, cudaEventDisableTiming));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&g_ready, cudaEventDisableTiming));
     return NNC_OK;
   }
   ~SideStream() {
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
+    if (m_ready) cudaEventDestroy(m_ready);
+    if (g_ready) cudaEventDestroy(g_ready);
     if (s) cudaStreamDestroy(s);
   }
 };
@@ -985,15 +1041,41 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
                                          side.s));
     return NNC_OK;
   };
-  NNC_TRY(replay(iters, s, [&](cudaStream_t cs) -> int {
+  // The core update of a sweep (M = Z_d x_d F^(d)T with the updated F^(d),
+  // D = G x_k S_k, the MU step on G, then G x_k S_k of the new core and the
+  // trace entry) needs neither the next sweep's pass X x_d F^(d)T nor its Z_1
+  // chain, so it runs on the side stream at the start of the next sweep,
+  // beside them (m_ready: M is formed, so Z_d's buffer may be reused; g_ready:
+  // the new G, which Num_1 needs); the last sweep's runs after the replays.
+  // Each step is the same launch as in a sweep that ends with its own core
+  // update, so the results are the same.
+  const T* zlast = nullptr;  // Z_d of the sweep whose core update is pending
+  auto core_update = [&](cudaStream_t cs, T* split, bool mark) -> int {
+    const int64_t lead = nc / m[d - 1];
+    NNC_CUDA_TRY(launch_ttm<T>(zlast, lead, (int)dims[d - 1], 1, F[d - 1], m[d - 1], 1,
+                               m[d - 1], M, split, w.split_cap, cs));
+    if (mark) NNC_CUDA_TRY(cudaEventRecord(side.m_ready, cs));
+    NNC_TRY(core_times_grams(-1, D, c0, c1, split, cs));
+    NNC_CUDA_TRY(launch_elementwise_mu<T>(G, M, D, nc, eps, cs));
+    if (mark) NNC_CUDA_TRY(cudaEventRecord(side.g_ready, cs));
+    NNC_TRY(core_times_grams(-1, D, c0, c1, split, cs));
+    NNC_CUDA_TRY(
+        launch_residual_identity<T>(M, G, D, nc, w.stats, tr, stride, counter, idpart, cs));
+    return NNC_OK;
+  };
+  auto sweep = [&](cudaStream_t cs, bool pending) -> int {
     const T* Z = nullptr;
     for (int n = 0; n < d; ++n) {
-      // H_n beside Z_n, forked after the previous mode's Gram.
+      // H_n beside Z_n, forked after the previous mode's Gram (mode 1: after
+      // the previous sweep's core update).
       NNC_TRY(fork(cs));
+      if (n == 0 && pending) NNC_TRY(core_update(side.s, split2, true));
       NNC_TRY(h_branch(n));
       if (n == 0) NNC_TRY(pass_last(w, F[d - 1], cs));
       if (n == d - 1) NNC_TRY(pass_first(w, F[0], cs));
+      if (n == 0 && pending) NNC_CUDA_TRY(cudaStreamWaitEvent(cs, side.m_ready, 0));
       NNC_TRY(z_chain(w, n, F, &Z, cs));
+      if (n == 0 && pending) NNC_CUDA_TRY(cudaStreamWaitEvent(cs, side.g_ready, 0));
       int64_t pre = 1, post = 1;
       for (int j = 0; j < n; ++j) pre *= m[j];
       for (int j = n + 1; j < d; ++j) post *= m[j];
@@ -1004,20 +1086,13 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
       NNC_TRY(launch_gram<T>(F[n], dims[n], m[n], S[n], cs));
       if (n == 0 && d > 2) NNC_TRY(make_u0(w, F[0], cs));
     }
-    // Core: Z (= Z_d) x_d F^(d)T with the updated F^(d), beside the
-    // denominator G x_k S_k of the old core.
-    NNC_TRY(fork(cs));
-    NNC_TRY(core_times_grams(-1, D, c0, c1, split2, side.s));
-    const int64_t lead = nc / m[d - 1];
-    NNC_CUDA_TRY(launch_ttm<T>(Z, lead, (int)dims[d - 1], 1, F[d - 1], m[d - 1], 1, m[d - 1], M,
-                               w.split, w.split_cap, cs));
-    NNC_TRY(join(cs));
-    NNC_CUDA_TRY(launch_elementwise_mu<T>(G, M, D, nc, eps, cs));
-    NNC_TRY(core_times_grams(-1, D, c0, c1, w.split, cs));
-    NNC_CUDA_TRY(
-        launch_residual_identity<T>(M, G, D, nc, w.stats, tr, stride, counter, idpart, cs));
+    zlast = Z;
     return NNC_OK;
-  }));
+  };
+  NNC_TRY(replay_pipelined(
+      iters, s, [&](cudaStream_t cs) -> int { return sweep(cs, false); },
+      [&](cudaStream_t cs) -> int { return sweep(cs, true); },
+      [&](cudaStream_t cs) -> int { return core_update(cs, w.split, false); }));
   NNC_TRY(check_tc(w, s));
   NNC_TRY(check_trace_finite(counter, s, "ntd_fit"));
   if (rel_err) {
