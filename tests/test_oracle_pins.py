@@ -283,6 +283,35 @@ def test_congruence_is_permutation_invariant():
             assert C[q, p] == pytest.approx(expect, rel=1e-12)
 
 
+def test_congruence_closed_forms_and_best_assignment():
+    # Columns orthonormal in every mode: a factor set's congruence with itself
+    # is the identity. Rotating component q0 by theta within the plane of two
+    # unit vectors (in each of the three modes) gives cong(q0, q0) = cos^3
+    # theta, so the best mean is (r - 1 + cos^3 theta) / r (Sec. 4.1).
+    r, theta, q0 = 5, 0.7, 2
+    A = [np.linalg.qr(RNG.standard_normal((n, r + 1)))[0] for n in (8, 9, 10)]
+    A_hat = [a[:, :r].copy() for a in A]
+    for a_hat, a in zip(A_hat, A):
+        a_hat[:, q0] = np.cos(theta) * a[:, q0] + np.sin(theta) * a[:, r]
+    A = [a[:, :r] for a in A]
+    np.testing.assert_allclose(orc.congruence_matrix(A, A), np.eye(r), atol=1e-12)
+    C = orc.congruence_matrix(A, A_hat)
+    assert C[q0, q0] == pytest.approx(np.cos(theta) ** 3, rel=1e-12)
+    assert orc.mean_congruence(A, A_hat) == pytest.approx((r - 1 + np.cos(theta) ** 3) / r,
+                                                          rel=1e-12)
+    # The exhaustive search over permutations agrees with a linear assignment
+    # solver on random nonnegative factors (the best permutation is unique).
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    for seed in range(3):
+        rng = np.random.default_rng(900 + seed)
+        A = [rng.random((n, 7)) for n in (6, 7, 8)]
+        A_hat = [rng.random((n, 7)) for n in (6, 7, 8)]
+        C = orc.congruence_matrix(A, A_hat)
+        rows, cols = scipy_opt.linear_sum_assignment(-C)
+        assert orc.mean_congruence(A, A_hat) == pytest.approx(float(C[rows, cols].mean()),
+                                                              rel=1e-12)
+
+
 def test_recovery_of_a_planted_canonical_tucker():
     # Sec. 4.3 in miniature: noise-free planted rank-3 data, multirank above the
     # canonical one. A quality check of the whole Alg. 1 (MU is a local method),
