@@ -31,20 +31,24 @@ cudaError_t launch_ttm_tc(const T* Y, int64_t L, int J, int64_t C, const T* Fm, 
 // is the product of the mode-n unfoldings unfold_n(Y) unfold_n(G)^T when the
 // tensors are viewed with mode n in the middle. The flattened (l, c) range is
 // split over blocks when the rows alone would not fill the GPU; the partial
-// sums (at most part_cap elements of `part`) are added in split order.
+// sums (at most part_cap elements of `part`) are added in split order. With
+// parts_out, the sums are left to the consumer: *parts_out = the number of
+// partials, in `part` (NI MA apart) when it is above 1, else the result is in out.
 template <typename T>
 cudaError_t launch_pair_contract(const T* Y, const T* G, int64_t L, int NI, int MA, int64_t C,
-                                 T* out, T* part, size_t part_cap, cudaStream_t s);
+                                 T* out, T* part, size_t part_cap, cudaStream_t s,
+                                 int* parts_out = nullptr);
 
 // out[i] = sum_{p < splits} part[p n + i], p in order.
 template <typename T>
 cudaError_t launch_reduce_splits(const T* part, int splits, int64_t n, T* out, cudaStream_t s);
 
 // F[i, a] <- max(F[i, a] * Num[i, a] / max(sum_b F[i, b] H[b, a], eps), 0),
-// F and Num N x M, H M x M.
+// F and Num N x M, H M x M; with parts > 1, Num[i, a] is the sum of the
+// partials Num[p N M + i M + a], p = 0 .. parts - 1 added in order.
 template <typename T>
 cudaError_t launch_factor_mu(T* F, const T* Num, const T* H, int64_t N, int M, double eps,
-                             cudaStream_t s);
+                             cudaStream_t s, int parts = 1);
 
 // theta <- max(theta * num / max(den, eps), 0), elementwise over n entries.
 template <typename T>

@@ -1079,10 +1079,13 @@ int ntd_fit_nway(const T* X, int d, const int64_t* dims, const int* m, bool tens
       int64_t pre = 1, post = 1;
       for (int j = 0; j < n; ++j) pre *= m[j];
       for (int j = n + 1; j < d; ++j) post *= m[j];
+      // Num_n's split partials are added by the MU kernel (in split order).
+      int parts = 1;
       NNC_CUDA_TRY(launch_pair_contract<T>(Z, G, pre, (int)dims[n], m[n], post, num, w.split,
-                                           w.split_cap, cs));
+                                           w.split_cap, cs, &parts));
       NNC_TRY(join(cs));
-      NNC_CUDA_TRY(launch_factor_mu<T>(F[n], num, w.H, dims[n], m[n], eps, cs));
+      NNC_CUDA_TRY(launch_factor_mu<T>(F[n], parts > 1 ? w.split : num, w.H, dims[n], m[n], eps,
+                                       cs, parts));
       NNC_TRY(launch_gram<T>(F[n], dims[n], m[n], S[n], cs));
       if (n == 0 && d > 2) NNC_TRY(make_u0(w, F[0], cs));
     }

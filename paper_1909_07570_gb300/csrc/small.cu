@@ -74,9 +74,12 @@ contract_kernel(const T* __restrict__ Y, const T* __restrict__ G, int C, int NI,
 
 // Rows of F are updated by one group of M' = roundup(M, 32) threads each; the
 // old row is staged in shared memory before any entry of it is overwritten.
+// The numerator is the sum of `parts` partial numerators `part_stride` apart,
+// added in order p = 0, 1, ... (as reduce_splits_kernel adds them).
 template <typename T>
-__global__ void factor_mu_kernel(T* __restrict__ F, const T* __restrict__ Num,
-                                 const T* __restrict__ H, int64_t N, int M, int MP, T eps) {
+__global__ void factor_mu_kernel(T* __restrict__ F, const T* __restrict__ Num, int parts,
+                                 int64_t part_stride, const T* __restrict__ H, int64_t N, int M,
+                                 int MP, T eps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* hs = reinterpret_cast<T*>(smem_raw);  // M x M
   T* fs = hs + M * M;                      // rows_per_block x M
@@ -90,8 +93,19 @@ __global__ void factor_mu_kernel(T* __restrict__ F, const T* __restrict__ Num,
   if (!act) return;
   T den = T(0);
   for (int b = 0; b < M; ++b) den = fma(fs[rr * M + b], hs[b * M + a], den);
+  const T* np = Num + i * M + a;
+  T num = np[0];
+  int p = 1;
+  for (; p + 8 <= parts; p += 8) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = np[(int64_t)(p + u) * part_stride];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) num += v[u];
+  }
+  for (; p < parts; ++p) num += np[(int64_t)p * part_stride];
   const T f = fs[rr * M + a];
-  const T v = f * Num[i * M + a] / (den > eps ? den : eps);
+  const T v = f * num / (den > eps ? den : eps);
   F[i * M + a] = v > T(0) ? v : T(0);
 }
 
@@ -238,7 +252,8 @@ unsigned grid_for(int64_t n, int threads, int64_t cap = 4096) {
 
 template <typename T>
 cudaError_t launch_pair_contract(const T* Y, const T* G, int64_t L, int NI, int MA, int64_t C,
-                                 T* out, T* part, size_t part_cap, cudaStream_t s) {
+                                 T* out, T* part, size_t part_cap, cudaStream_t s,
+                                 int* parts_out) {
   if (L < 1 || NI < 1 || MA < 1 || MA > kCtMaxA || C < 1 || L * C > 2147483647LL)
     return cudaErrorInvalidValue;
   const int K = (int)(L * C);
@@ -258,20 +273,22 @@ cudaError_t launch_pair_contract(const T* Y, const T* G, int64_t L, int NI, int 
   contract_kernel<T><<<dim3((unsigned)row_tiles, (unsigned)splits), kCtThreads, 0, s>>>(
       Y, G, (int)C, NI, MA, K, per, dst);
   note_launch(s);
+  if (parts_out) *parts_out = (int)splits;
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || splits == 1) return e;
+  if (e != cudaSuccess || splits == 1 || parts_out) return e;
   return launch_reduce_splits<T>(part, (int)splits, (int64_t)NI * MA, out, s);
 }
 
 template <typename T>
 cudaError_t launch_factor_mu(T* F, const T* Num, const T* H, int64_t N, int M, double eps,
-                             cudaStream_t s) {
+                             cudaStream_t s, int parts) {
+  if (parts < 1) return cudaErrorInvalidValue;
   const int MP = (M + 31) / 32 * 32;
   const int threads = MP > 256 ? MP : 256;
   const int rows = threads / MP;
   const size_t smem = ((size_t)M * M + (size_t)rows * M) * sizeof(T);
-  factor_mu_kernel<T><<<(unsigned)ceil_div(N, rows), threads, smem, s>>>(F, Num, H, N, M, MP,
-                                                                          (T)eps);
+  factor_mu_kernel<T><<<(unsigned)ceil_div(N, rows), threads, smem, s>>>(
+      F, Num, parts, N * M, H, N, M, MP, (T)eps);
   note_launch(s);
   return cudaGetLastError();
 }
@@ -315,9 +332,9 @@ cudaError_t launch_convert(const T* src, U* dst, int64_t n, cudaStream_t s) {
 
 #define NNC_INST(T)                                                                            \
   template cudaError_t launch_pair_contract<T>(const T*, const T*, int64_t, int, int, int64_t,  \
-                                               T*, T*, size_t, cudaStream_t);                  \
+                                               T*, T*, size_t, cudaStream_t, int*);            \
   template cudaError_t launch_factor_mu<T>(T*, const T*, const T*, int64_t, int, double,       \
-                                           cudaStream_t);                                      \
+                                           cudaStream_t, int);                                 \
   template cudaError_t launch_elementwise_mu<T>(T*, const T*, const T*, int64_t, double,       \
                                                 cudaStream_t);                                 \
   template cudaError_t launch_residual_identity<T>(const T*, const T*, const T*, int64_t,      \
