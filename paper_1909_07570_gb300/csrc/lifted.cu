@@ -269,6 +269,29 @@ __global__ void lifted_loss_kernel(const T* __restrict__ MT, const T* __restrict
 
 // ---- the workspace -------------------------------------------------------------
 
+// A side stream and a fork/join pair of events for the branches captured in a
+// replayed sweep (each record of an event marks the point the next wait joins).
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t m_ready = nullptr, g_ready = nullptr;  // the pending core update's steps
+  int init() {
+    NNC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&m_ready, cudaEventDisableTiming));
+    NNC_CUDA_TRY(cudaEventCreateWithFlags(&g_ready, cudaEventDisableTiming));
+    return NNC_OK;
+  }
+  ~SideStream() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (m_ready) cudaEventDestroy(m_ready);
+    if (g_ready) cudaEventDestroy(g_ready);
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
 template <typename T>
 struct Work {
   int d = 0, r = 0;
@@ -281,6 +304,7 @@ struct Work {
   T* W = nullptr;
   T *Kpre = nullptr, *Kpost = nullptr, *MT = nullptr, *gA = nullptr, *tmp = nullptr;
   T *V = nullptr, *H = nullptr, *S = nullptr;
+  T* tmp2 = nullptr;  // B V of a projected-gradient block, beside the gradient chain in tmp
   T* split = nullptr;  // partial sums of mode products whose grid would not fill the GPU
   size_t split_cap = 0;
   T* A[kMaxD] = {};
@@ -343,6 +367,7 @@ int setup(Work<T>& w, const T* X, int d, const int64_t* dims, const int* m, int 
   NNC_TRY(sc.get(&w.MT, (size_t)(nmax * r)));
   NNC_TRY(sc.get(&w.gA, (size_t)(nmax * r)));
   NNC_TRY(sc.get(&w.tmp, (size_t)(nmax * (mmax > r ? mmax : r))));
+  NNC_TRY(sc.get(&w.tmp2, (size_t)mmax * r));
   NNC_TRY(sc.get(&w.V, (size_t)(r * r)));
   NNC_TRY(sc.get(&w.H, (size_t)(mmax * mmax > r * r ? mmax * mmax : r * r)));
   NNC_TRY(sc.get(&w.S, (size_t)(mmax * mmax)));
@@ -516,31 +541,53 @@ int grad_a(Work<T>& w, int n, cudaStream_t s) {
   return NNC_OK;
 }
 
-// One block pair (F^(n), then B^(n)) of the projected-gradient step.
+// One block pair (F^(n), then B^(n)) of the projected-gradient step. The step
+// sizes (power iterations on small FP64 chains) need nothing from the
+// gradient chain, so with a side stream each runs beside it and is joined
+// before the update that uses it (the same launches either way).
 template <typename T>
-int pg_mode(Work<T>& w, int n, T* const* F, T* const* B, cudaStream_t s) {
+int pg_mode(Work<T>& w, int n, T* const* F, T* const* B, cudaStream_t s, SideStream* side) {
   const int r = w.r, mn = w.m[n];
   const int64_t Nn = w.N[n];
-  // L_F = lmax(B V B^T) and lmax(V) (one launch): tmp = B V (m x r), H = tmp B^T (m x m)
-  NNC_CUDA_TRY(small_gemm<T>(mn, r, r, B[n], r, 1, w.V, r, 1, nullptr, w.tmp, s));
-  NNC_CUDA_TRY(small_gemm<T>(mn, mn, r, w.tmp, r, 1, B[n], 1, r, nullptr, w.H, s));
-  power_iter_kernel<T><<<2, 32, 0, s>>>(w.H, mn, w.Ls + 0, w.V, r, w.Ls + 1);
-  note_launch(s);
+  const cudaStream_t ls = side ? side->s : s;
+  auto fork = [&]() -> int {
+    if (!side) return NNC_OK;
+    NNC_CUDA_TRY(cudaEventRecord(side->fork, s));
+    NNC_CUDA_TRY(cudaStreamWaitEvent(side->s, side->fork, 0));
+    return NNC_OK;
+  };
+  auto join = [&]() -> int {
+    if (!side) return NNC_OK;
+    NNC_CUDA_TRY(cudaEventRecord(side->join, side->s));
+    NNC_CUDA_TRY(cudaStreamWaitEvent(s, side->join, 0));
+    return NNC_OK;
+  };
+  // L_F = lmax(B V B^T) and lmax(V) (one launch): tmp2 = B V (m x r), H = tmp2 B^T (m x m)
+  NNC_TRY(fork());
+  NNC_CUDA_TRY(small_gemm<T>(mn, r, r, B[n], r, 1, w.V, r, 1, nullptr, w.tmp2, ls));
+  NNC_CUDA_TRY(small_gemm<T>(mn, mn, r, w.tmp2, r, 1, B[n], 1, r, nullptr, w.H, ls));
+  power_iter_kernel<T><<<2, 32, 0, ls>>>(w.H, mn, w.Ls + 0, w.V, r, w.Ls + 1);
+  note_launch(ls);
+  NNC_CUDA_TRY(cudaGetLastError());
   NNC_TRY(grad_a(w, n, s));
   // gF = gA B^T (N x m) into tmp
   NNC_CUDA_TRY(small_gemm<T>((int)Nn, mn, r, w.gA, r, 1, B[n], 1, r, nullptr, w.tmp, s));
+  NNC_TRY(join());
   pg_update_kernel<T><<<grid_for(Nn * mn, 256), 256, 0, s>>>(F[n], w.tmp, Nn * mn, w.Ls + 0,
                                                                nullptr);
   note_launch(s);
   NNC_CUDA_TRY(cudaGetLastError());
   NNC_CUDA_TRY(launch_lift<T>(F[n], B[n], Nn, mn, r, w.A[n], s));
   // L_B = lmax(F^T F) lmax(V)
-  NNC_TRY(launch_gram<T>(F[n], Nn, mn, w.S, s));
-  power_iter_kernel<T><<<1, 32, 0, s>>>(w.S, mn, w.Ls + 2, w.S, mn, w.Ls + 2);
-  note_launch(s);
+  NNC_TRY(fork());
+  NNC_TRY(launch_gram<T>(F[n], Nn, mn, w.S, ls));
+  power_iter_kernel<T><<<1, 32, 0, ls>>>(w.S, mn, w.Ls + 2, w.S, mn, w.Ls + 2);
+  note_launch(ls);
+  NNC_CUDA_TRY(cudaGetLastError());
   NNC_TRY(grad_a(w, n, s));
   // gB = F^T gA (m x r) into tmp
   NNC_CUDA_TRY(small_gemm<T>(mn, r, (int)Nn, F[n], 1, mn, w.gA, r, 1, nullptr, w.tmp, s));
+  NNC_TRY(join());
   pg_update_kernel<T><<<grid_for((int64_t)mn * r, 256), 256, 0, s>>>(B[n], w.tmp, (int64_t)mn * r,
                                                                       w.Ls + 2, w.Ls + 1);
   note_launch(s);
@@ -609,7 +656,7 @@ namespace {
 // One projected-gradient step (two passes over X), stream-ordered on s.
 template <typename T>
 int pg_step(Work<T>& w, T* const* F, T* const* B, double* last, double* trace, int* counter,
-            cudaStream_t s) {
+            cudaStream_t s, SideStream* side) {
   const int d = w.d;
   NNC_TRY(pass_last(w, F[d - 1], s));
   for (int n = 0; n < d; ++n) {
@@ -617,7 +664,7 @@ int pg_step(Work<T>& w, T* const* F, T* const* B, double* last, double* trace, i
     const T* Z = nullptr;
     NNC_TRY(z_chain(w, n, F, &Z, s));
     NNC_TRY(mttkrp_and_v(w, n, Z, B, s));
-    NNC_TRY(pg_mode(w, n, F, B, s));
+    NNC_TRY(pg_mode(w, n, F, B, s, side));
     if (n == 0 && d > 2) NNC_TRY(make_u0(w, F[0], s));
   }
   // MT_d and V_d do not involve mode d: the loss at the new point.
@@ -657,13 +704,15 @@ int lifted_pg_fit(const T* X, int d, const int64_t* dims, const int* m, int r, b
     // One step is captured as a CUDA graph on a private stream and replayed;
     // the trace slot advances through the device counter.
     PgGraph g;
+    SideStream side;
+    NNC_TRY(side.init());
     NNC_CUDA_TRY(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
     NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming));
     NNC_CUDA_TRY(cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming));
     NNC_CUDA_TRY(cudaEventRecord(g.fork, s));
     NNC_CUDA_TRY(cudaStreamWaitEvent(g.cs, g.fork, 0));
     NNC_CUDA_TRY(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
-    const int cap = pg_step(w, F, B, last, trace, counter, g.cs);
+    const int cap = pg_step(w, F, B, last, trace, counter, g.cs, &side);
     const cudaError_t end_e = cudaStreamEndCapture(g.cs, &g.graph);
     if (cap != NNC_OK) return cap;
     NNC_CUDA_TRY(end_e);
@@ -917,30 +966,6 @@ int nmf_fit(const T* A, int64_t N, int r, int m, int iters, double eps, T* F, T*
   return NNC_OK;
 }
 
-namespace {
-// A side stream and a fork/join pair of events for the branches captured in a
-// replayed sweep (each record of an event marks the point the next wait joins).
-struct SideStream {
-  cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-  cudaEvent_t m_ready = nullptr, g_ready = nullptr;  // the pending core update's steps
-  int init() {
-    NNC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    NNC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    NNC_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-    NNC_CUDA_TRY(cudaEventCreateWithFlags(&m_ready, cudaEventDisableTiming));
-    NNC_CUDA_TRY(cudaEventCreateWithFlags(&g_ready, cudaEventDisableTiming));
-    return NNC_OK;
-  }
-  ~SideStream() {
-    if (fork) cudaEventDestroy(fork);
-    if (join) cudaEventDestroy(join);
-    if (m_ready) cudaEventDestroy(m_ready);
-    if (g_ready) cudaEventDestroy(g_ready);
-    if (s) cudaStreamDestroy(s);
-  }
-};
-}  // namespace
 
 // nnTD of a d-way X (d = 3 or 4) by MU sweeps (Alg. 1, first step), built on
 // the mode-product machinery above with F := F^(k). A sweep updates
