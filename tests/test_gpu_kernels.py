@@ -62,13 +62,15 @@ def test_mode_product_tf32x3_is_fp32_accurate(dims, Q):
 
 @pytest.mark.parametrize("dims,Q", [((37, 29, 24), 5), ((200, 150, 132), 20), ((64, 128, 2048), 24),
                                     ((24, 128, 16), 16), ((9, 33, 8), 32), ((3, 1000, 4), 24),
-                                    ((11, 7, 4), 1), ((5, 300, 2), 24), ((20, 40, 12), 33)])
+                                    ((11, 7, 4), 1), ((5, 300, 2), 24), ((20, 40, 12), 33),
+                                    ((2, 200, 20000), 24)])
 def test_mode_product_middle_mode_tf32x3_is_fp32_accurate(dims, Q):
     # Mode 1 (the middle mode, strided in memory) with NNC_FP32: the column
     # product on mma.sync with TF32x3 operands, each 16-row chunk summed apart
     # and added with round-to-nearest; N3 % 4 != 0 or Q > 32 take the SIMT
     # kernel. Ragged column blocks (L N3 not a multiple of 256), ragged row
-    # chunks (N2 % 16 != 0) and the split-J launches of narrow grids included.
+    # chunks (N2 % 16 != 0) and the split-J launches of narrow grids included;
+    # (2, 200, 20000) runs unsplit over 200 rows (13 chunks through the ring).
     rng = np.random.default_rng(29 + Q + dims[1])
     X = rng.random(dims) * np.exp2(rng.integers(-6, 7, size=(dims[0], 1, 1)))
     Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
